@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 3DGS training step.
+
+Metric: train steps/s (forward + backward + Adam) at 1M Gaussians, 1080p.
+Workload: 2^20 Gaussians in 64 anisotropic clusters (SH degree 3), 16 ring
+cameras at 1920x1080, 16x16 tiles, loss 0.8 L1 + 0.2 (1 - SSIM); one view
+per step, round robin.  Synthetic, seeded inputs stand in for the paper's
+Tanks-and-Temples / challenge scenes (not available).
+
+One step = preprocess, bin + sort, forward blend, loss, per-Gaussian
+backward, preprocess backward, Adam, all on the GPU through libgs.so.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank trains its own replica on its own GPU (the
+step has no cross-GPU exchange); the value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "train steps/s (fwd+bwd+Adam) @1M Gaussians 1080p"
+UNIT = "steps/s"
+# Peak numbers: measured by the pool's driver (MEASURED_PEAKS.json) where it
+# exists; FP32 ALU peak = 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz.
+FALLBACK_HBM_GBS = 6800.0
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Algorithmic floating-point work per evaluated pixel-splat pair, counted
+# from the kernels' arithmetic (FMA = 2): forward blend 25, backward 62.
+FLOP_PER_PAIR = {"render_fwd": 25.0, "render_bwd_blend": 62.0}
+# DRAM bytes per launch from one ncu capture, valid only for the kernel
+# source they were taken on (sha256 of the .cu file, first 16 hex digits).
+NCU_TRAFFIC: dict = {}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--views", type=int, default=16)
+    ap.add_argument("--lam", type=float, default=0.2)
+    ap.add_argument("--sq", action="store_true", help="sequential tile-key write instead of load-balanced")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    import synth
+
+    scene = synth.scene_clustered(args.n, seed=0, sh_degree=3)
+    cams = synth.ring_cameras(args.views, args.width, args.height)
+    return scene, cams
+
+
+def config_of(args):
+    return {"workload": f"clustered {args.n} Gaussians SH3, {args.views} ring views {args.width}x{args.height}, "
+                        f"16x16 tiles, loss {1 - args.lam:.1f} L1 + {args.lam:.1f} D-SSIM, one view per step",
+            "gaussians": args.n, "views": args.views, "width": args.width, "height": args.height,
+            "tile": 16, "bucket": 32, "sh_degree": 3, "binning": "sequential" if args.sq else "load_balanced",
+            "l2": "working set > L2 (params + Adam state ~1 GB, instances, checkpoints); no flush"}
+
+
+# ------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def src_sha(name: str) -> str:
+    p = os.path.join(ROOT, "paper_2601_19489_gb300", "csrc", name)
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample(scene, cam, target, window_px: int, pre_sample: int, n_threads: int, seed: int = 0):
+    """Time the float64 oracle on a bounded sample of one training step and
+    extrapolate to the whole step.  Returns (seconds per full step, detail).
+
+    preprocess fwd+bwd and Adam: a random subset of `pre_sample` Gaussians,
+    scaled by N / pre_sample; blend fwd + loss + per-pixel bwd: a window of
+    window_px^2 pixels at the image centre, scaled by H*W / window_px^2."""
+    import torch
+
+    from oracle import preprocess as opre
+    from oracle import render as oren
+    from oracle import loss as oloss
+    from oracle import adam as oadam
+    import synth
+
+    torch.set_num_threads(n_threads)
+    rng = np.random.default_rng(seed)
+    N = scene.n
+    sub = np.sort(rng.choice(N, size=min(pre_sample, N), replace=False))
+    sub_scene = synth.Scene(*(a[sub] for a in scene.arrays()), sh_degree=scene.sh_degree)
+    # full records for the window render (setup, untimed: the subset's time
+    # below stands for the preprocess of every Gaussian)
+    with torch.no_grad():
+        rec = opre.pack_for_render(opre.project(opre.params_from_scene(scene), cam, scene.sh_degree))
+    W, H = cam.width, cam.height
+    x0 = W // 2 - window_px // 2
+    y0 = H // 2 - window_px // 2
+    win = (x0, y0, x0 + window_px, y0 + window_px)
+    t0 = time.perf_counter()
+    with torch.no_grad():
+        opre.project(opre.params_from_scene(sub_scene), cam, scene.sh_degree)
+    g2d = rng.standard_normal((sub.size, 10))
+    grads = opre.preprocess_backward(sub_scene, cam, g2d)
+    t1 = time.perf_counter()
+    f = oren.render_fwd(rec, (0.0, 0.0, 0.0), win, amb=None, n_threads=n_threads)
+    tgt = np.asarray(target, dtype=np.float64).reshape(3, H, W)[:, win[1]:win[3], win[0]:win[2]]
+    _, g_rgb = oloss.photometric(f["rgb"], tgt, 0.2)
+    oren.render_bwd(rec, (0.0, 0.0, 0.0), win, g_rgb, np.zeros_like(f["disp"]), n_threads=n_threads)
+    t2 = time.perf_counter()
+    for k, v in grads.items():
+        oadam.adam_step(getattr(sub_scene, k), v, np.zeros_like(v), np.zeros_like(v), 1, 1e-3)
+    t3 = time.perf_counter()
+    scale_g = N / sub.size
+    scale_p = (W * H) / float(window_px * window_px)
+    est = (t1 - t0) * scale_g + (t2 - t1) * scale_p + (t3 - t2) * scale_g
+    detail = {"preprocess_s": (t1 - t0) * scale_g, "render_s": (t2 - t1) * scale_p,
+              "adam_s": (t3 - t2) * scale_g, "measured_s": t3 - t0, "pairs": f["pairs"]}
+    return est, detail
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the float64 oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    scene, cams = workload(args)
+    import synth
+
+    n_threads = os.cpu_count() or 1
+    times = []
+    for s in range(args.warmup + args.steps):
+        cam = cams[s % len(cams)]
+        target = synth.target_uniform(1000 + s % len(cams), cam.width, cam.height)
+        est, _ = oracle_sample(scene, cam, target, window_px=24, pre_sample=1 << 14, n_threads=n_threads, seed=s)
+        if s >= args.warmup:
+            times.append(est)
+    value = 1.0 / float(np.mean(times))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_threads, "kind": "oracle",
+                             "sample": "per step: preprocess fwd+bwd and Adam on 16384 random Gaussians "
+                                       "(x N/16384), blend fwd+loss+bwd on a 24x24 centre window (x H*W/576)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ GPU arm
+
+def kernels_per_step(trainer) -> int:
+    tile_passes = -(-trainer.plan_tile_bits // 8)
+    loss_k = 3 if trainer.lam > 0 else 2
+    # preprocess 1; depth sort 4 passes x 3; count 2; keys 1; tile sort 3/pass;
+    # ranges 1; buckets 1; forward 1; loss; blend bwd 1; preprocess bwd 1; adam 1
+    return 1 + 12 + 2 + 1 + 3 * tile_passes + 2 + 1 + loss_k + 1 + 1 + 1
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300 import _lib as L
+    from paper_2601_19489_gb300.trainer import Trainer
+    import synth
+
+    L.load()
+    scene, cams = workload(args)
+    params = api.Gaussians.from_scene(scene, device=dev)
+    trainer = Trainer(params, args.width, args.height, lam=args.lam, load_balanced=not args.sq, device=dev)
+    ntiles = ((args.width + 15) // 16) * ((args.height + 15) // 16)
+    trainer.plan_tile_bits = max(1, int(np.ceil(np.log2(ntiles))))
+    targets_h = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1))
+                 .pin_memory() for v in range(len(cams))]
+    targets_d = [t.to(dev) for t in targets_h]
+    torch.cuda.synchronize()
+    worst = trainer.ensure_capacity(cams)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for s in range(args.warmup):
+        trainer.step(cams[s % len(cams)], targets_d[s % len(cams)])
+    barrier()
+    st0 = trainer.plan.status()
+    assert st0["rc"] == 0, st0
+
+    n_st = len(Trainer.STAGES)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_st + 1)] for _ in range(args.steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        start.record(stream)
+        for s in range(args.steps):
+            v = (args.warmup + s) % len(cams)
+            trainer.step(cams[v], targets_d[v], events=evs[s])
+        end.record(stream)
+        barrier()
+    clocks = clk.summary()
+    elapsed = start.elapsed_time(end) / 1e3
+    st1 = trainer.plan.status()
+    if st1["rc"] != 0:
+        raise RuntimeError(f"device status after the timed region: {st1}")
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    stage_ms = {name: float(np.mean([evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps)]))
+                for i, name in enumerate(Trainer.STAGES)}
+
+    # algorithmic work of the blend kernels: evaluated pairs up to each
+    # pixel's last contributor, summed over the views of the timed steps
+    pairs = []
+    for s in range(args.steps):
+        v = (args.warmup + s) % len(cams)
+        if len(pairs) >= len(cams):
+            break
+        trainer.forward(cams[v])
+        nc = trainer.plan.view(L.GS_WS_N_CONTRIB, torch.int32)[: args.width * args.height]
+        pairs.append(float(nc.double().sum().item()))
+    mean_pairs = float(np.mean(pairs))
+    st2 = trainer.plan.status()
+
+    # e2e: through the public API with host buffers, the target copied in and
+    # the loss read back every step
+    e2e = None
+    if not args.no_e2e:
+        loss_h = torch.empty(1, pin_memory=True)
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            v = s % len(cams)
+            tgt = targets_d[v]
+            tgt.copy_(targets_h[v], non_blocking=True)
+            trainer.step(cams[v], tgt)
+            loss_h.copy_(trainer.loss, non_blocking=True)
+        barrier()
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(targets_h[0].numel() * 4), "d2h_bytes_per_step": 4}
+
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    dominant = max(stage_ms, key=stage_ms.get)
+    roof = None
+    kname = {"render_bwd_blend": "k_render_bwd", "render_fwd": "k_render_fwd"}.get(dominant, dominant)
+    if dominant in FLOP_PER_PAIR:
+        ach = FLOP_PER_PAIR[dominant] * mean_pairs / (stage_ms[dominant] / 1e3) / 1e12
+        tr = NCU_TRAFFIC.get(kname)
+        src = {"k_render_bwd": "render_bwd.cu", "k_render_fwd": "render_fwd.cu"}[kname]
+        traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == src_sha(src) else None
+        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": kname,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "work": f"{FLOP_PER_PAIR[dominant]:.0f} FLOP x {mean_pairs:.4g} pixel-splat pairs per launch"}
+    value = world * args.steps / elapsed
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_of(args), "clocks": clocks, "e2e": e2e,
+            "gpu_launches": kernels_per_step(trainer) * args.steps,
+            "roofline": roof,
+            "stages_ms": stage_ms,
+            "work": {"instances_max": worst, "instances_last": st2["n_instances"],
+                     "buckets_last": st2["n_buckets"], "pairs_per_view": mean_pairs},
+            "peaks": {"hbm_gbs": hbm or FALLBACK_HBM_GBS, "hbm_source": "measured" if hbm else "fallback",
+                      "fp32_tflops": FP32_PEAK_TFLOPS}}
+    if world == 1 and not args.no_cpu_baseline:
+        scene_h = scene
+        cam = cams[0]
+        n_threads = os.cpu_count() or 1
+        target = synth.target_uniform(1000, cam.width, cam.height)
+        est, detail = oracle_sample(scene_h, cam, target, window_px=64, pre_sample=1 << 17, n_threads=n_threads)
+        line["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": n_threads, "kind": "oracle",
+                                "sample": "preprocess fwd+bwd and Adam on 131072 random Gaussians (x N/131072), "
+                                          "blend fwd + loss + per-pixel bwd on a 64x64 centre window "
+                                          "(x H*W/4096); float64",
+                                "detail": detail}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl == "ours":
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

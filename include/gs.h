@@ -1,0 +1,250 @@
+/*
+ * gs.h — C ABI of the GB300 (sm_103a) differentiable 3D Gaussian Splatting
+ * training step.
+ *
+ * Paper: "Fast Converging 3D Gaussian Splatting for 1-Minute Reconstruction"
+ * (arXiv 2601.19489).  The step follows Sec. 2.1 (preprocessCUDA: projection,
+ * compact SnugBox, per-column tile test, load-balanced tile-key write, depth
+ * sort; renderCUDA: front-to-back alpha blending) and Sec. 2.2 (checkpoints
+ * every 32 splats, per-Gaussian parallel backward), followed by Adam.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named d_* are DEVICE pointers; pointers named h_* (and the
+ *    camera / parameter structs themselves) are HOST pointers read during the
+ *    call only.  The library never allocates device memory: the caller owns
+ *    every device buffer, including the workspace `ws`.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Every call only enqueues work on that stream and returns
+ *    without synchronising, except gs_read_status which synchronises it.
+ *  - Return value: GS_OK (0) or a negative GS_ERR_* code.  Argument errors are
+ *    detected on the host before anything is enqueued.  Errors that only the
+ *    device can see (instance-capacity overflow, a timed-out wait, an
+ *    internal consistency check) are recorded in the workspace status words
+ *    and reported by gs_read_status.
+ *  - Images are planar float32: colour is [view][3][height][width], single
+ *    channel maps are [view][height][width], views concatenated in order.
+ *  - Cameras use OpenCV axes (x right, y down, z forward); w2c is the
+ *    row-major 3x4 world-to-camera matrix [R | t]; the pixel (i, j) has its
+ *    centre at (i + 0.5, j + 0.5) in the same units as (cx, cy).
+ *  - Gaussian parameters are float32 arrays of n rows: means n x 3,
+ *    log_scales n x 3, quats n x 4 as (w, x, y, z), opacity_logits n,
+ *    sh n x K x 3 with K = (sh_degree + 1)^2 (coefficient-major per Gaussian,
+ *    real spherical harmonics with the Condon-Shortley phase).
+ *  - Gradients are ACCUMULATED (+=) into the caller's gradient arrays, so
+ *    several views or calls sum.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Every entry point is exported from the shared library (which otherwise
+ * builds with hidden visibility). */
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+#define GS_MAX_VIEWS 16
+#define GS_TILE 16       /* tile edge in pixels (Sec. 2.2: 16x16 tiles) */
+#define GS_BUCKET 32     /* splats per checkpoint bucket (Sec. 2.2) */
+
+enum {
+    GS_OK = 0,
+    GS_ERR_ARG = -1,      /* bad argument (null pointer, size, degree, alignment) */
+    GS_ERR_CAPACITY = -2, /* more tile instances than the workspace holds */
+    GS_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+    GS_ERR_TIMEOUT = -4,  /* a bounded device-side wait gave up */
+    GS_ERR_INTERNAL = -5  /* a device-side consistency check failed */
+};
+
+typedef struct {
+    float fx, fy, cx, cy;  /* pinhole intrinsics, pixels */
+    float w2c[12];         /* row-major [R | t], world -> camera */
+    int32_t width, height; /* image size in pixels */
+    float near_z;          /* Gaussians with camera z <= near_z are culled (0.2) */
+} gs_camera;
+
+typedef struct {
+    int64_t n;              /* number of Gaussians */
+    int32_t sh_degree;      /* 0..3 */
+    float *means;           /* device, n x 3 */
+    float *log_scales;      /* device, n x 3 */
+    float *quats;           /* device, n x 4 */
+    float *opacity_logits;  /* device, n */
+    float *sh;              /* device, n x K x 3 */
+} gs_params;
+
+typedef struct {
+    int64_t n_instances;     /* Gaussian-tile pairs of the last gs_bin_sort */
+    int64_t n_buckets;       /* 32-splat buckets of the last gs_bin_sort */
+    int64_t inst_capacity;   /* capacity the plan was made with */
+    int32_t overflow;        /* 1: n_instances > inst_capacity, result truncated */
+    int32_t error;           /* 0 or a GS_ERR_* code seen on the device */
+} gs_status;
+
+/* ------------------------------------------------------------------ plan
+ * A plan is a small HOST object that fixes the sizes of one training step:
+ * the Gaussian count, SH degree, the views (1..GS_MAX_VIEWS, each with its
+ * own resolution) and the capacity for tile instances.  It computes the
+ * workspace layout; it owns no device memory.
+ *
+ * gs_plan_create returns NULL on bad arguments (n <= 0, degree outside 0..3,
+ * n_views outside 1..GS_MAX_VIEWS, non-positive sizes, capacity <= 0 or
+ * >= 2^31).  inst_capacity bounds the number of (Gaussian, tile) pairs; a
+ * step that needs more sets the overflow status (see gs_read_status) and
+ * renders only the pairs that fit. */
+typedef struct gs_plan gs_plan;
+
+GS_API gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views, const int32_t *h_widths,
+                               const int32_t *h_heights, int64_t inst_capacity);
+GS_API void gs_plan_destroy(gs_plan *plan);
+/* Bytes of device workspace the plan needs (256-byte aligned base required). */
+GS_API size_t gs_plan_workspace_bytes(const gs_plan *plan);
+/* Pixels summed over views (the length of one image channel). */
+GS_API int64_t gs_plan_pixels(const gs_plan *plan);
+
+/* Device address and size of an internal workspace buffer, for inspection
+ * by tests and tools.  `which` is one of GS_WS_*.  Returns GS_ERR_ARG for an
+ * unknown id. */
+enum {
+    GS_WS_RECORDS = 0,    /* float4 x 3 per (view, Gaussian): projected record */
+    GS_WS_TILES_TOUCHED,  /* uint32 per (view, Gaussian) */
+    GS_WS_RECTS,          /* uint16 x 4 per (view, Gaussian): candidate tile box */
+    GS_WS_DEPTH_ORDER,    /* uint32 per rank: item id v*n + g in ascending depth */
+    GS_WS_INST_TILE,      /* uint32 per instance, sorted global tile id */
+    GS_WS_INST_GID,       /* uint32 per instance, item id v*n + g */
+    GS_WS_TILE_RANGES,    /* uint32 x 2 per global tile: [start, end) */
+    GS_WS_N_CONTRIB,      /* uint32 per pixel: list position of last blended splat + 1 */
+    GS_WS_GRAD2D,         /* float x 12 per (view, Gaussian): 2D gradients */
+    GS_WS_STATUS,         /* status words */
+    GS_WS_COUNT
+};
+GS_API int gs_workspace_view(const gs_plan *plan, void *ws, int which, void **d_ptr, size_t *bytes);
+
+/* Synchronise `stream` and read the status words of `ws` (see gs_status).
+ * Returns GS_OK, GS_ERR_CAPACITY when the last bin/sort overflowed, or the
+ * device-recorded error. */
+GS_API int gs_read_status(const gs_plan *plan, const void *ws, gs_status *out, void *stream);
+
+GS_API const char *gs_error_string(int code);
+
+/* ------------------------------------------------------- a1: preprocess
+ * Sec. 2.1 (preprocessCUDA) with Eq. 1-2: per (view, Gaussian) project the
+ * mean, build the 2D covariance with the local affine (EWA) approximation,
+ * invert it to the conic, evaluate the SH colour along the viewing direction,
+ * take the opacity-aware level set t = 2 ln(255 o), bound it by the SnugBox
+ * and count the touched tiles exactly with the per-column test.
+ * h_cams: n_views cameras (host), sizes must match the plan.
+ * Writes the projected records, tile counts and boxes into ws. */
+GS_API int gs_preprocess(const gs_plan *plan, void *ws, const gs_params *params, const gs_camera *h_cams,
+                         void *stream);
+
+/* ---------------------------------------------- a2-a4: bin, sort, ranges
+ * Sec. 2.1: order the visible Gaussians of every view by depth (on-device
+ * radix sort), scan their tile counts, write one (tile, Gaussian) instance
+ * per touched tile — load_balanced = 1: a warp tests one Gaussian's candidate
+ * tiles lane-parallel and compacts with ballot/popc (Fig. "LB"); 0: one
+ * thread walks its columns sequentially ("Sq") — then stably radix-sort the
+ * instances by tile so each tile's list is in (depth, id) order, and record
+ * each tile's [start, end) range and 32-splat bucket count. */
+GS_API int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, void *stream);
+
+/* --------------------------------------------------------- a5: forward
+ * Sec. 2.1 (renderCUDA) and Sec. 2.2: per pixel, front-to-back blending of
+ * its tile's depth-sorted splats with alpha = min(0.99, o e^power), skipping
+ * alpha < 1/255 and stopping before T (1 - alpha) < 1e-4; every 32 splats the
+ * per-pixel T, C and D are checkpointed in ws for the backward.
+ * h_bg: 3 floats (host) background colour.  Outputs (device, may not alias):
+ * d_out_rgb  colour C + T bg, planar per view;  d_out_disp  blended
+ * disparity sum(alpha T / z);  d_out_T  final transmittance. */
+GS_API int gs_render_fwd(const gs_plan *plan, void *ws, const float *h_bg, float *d_out_rgb,
+                         float *d_out_disp, float *d_out_T, void *stream);
+
+/* ------------------------------------------- a7 + a8: backward
+ * Sec. 2.2: per-Gaussian parallel backward.  One warp per 32-splat bucket,
+ * lane = splat, iterates the tile's pixels seeded from the forward's
+ * checkpoints, accumulates in registers and issues one atomic per splat
+ * parameter; then the per-Gaussian preprocess backward chains the 2D
+ * gradients to the parameters.
+ * d_rgb, d_disp: the forward's outputs for the same ws (device).
+ * d_dL_drgb, d_dL_ddisp: upstream gradients, same layouts (d_dL_ddisp may be
+ * NULL: no disparity loss).  h_cams: the cameras given to gs_preprocess.
+ * grads: device arrays with the layout of params, ACCUMULATED (+=). */
+GS_API int gs_render_bwd(const gs_plan *plan, void *ws, const gs_params *params, const gs_camera *h_cams,
+                         const float *h_bg, const float *d_rgb, const float *d_disp, const float *d_dL_drgb,
+                         const float *d_dL_ddisp, gs_params *grads, void *stream);
+
+/* The two halves of gs_render_bwd, for callers that time or schedule them
+ * separately.  gs_render_bwd_blend (a7) overwrites the per-(view, Gaussian)
+ * 2D gradients in ws (GS_WS_GRAD2D: dL/d mean2d, conic a b c, opacity,
+ * 1/z, rgb); gs_preprocess_bwd (a8) chains them to the parameters and
+ * ACCUMULATES into grads.  Same arguments and rules as gs_render_bwd. */
+GS_API int gs_render_bwd_blend(const gs_plan *plan, void *ws, const float *d_rgb, const float *d_disp,
+                               const float *d_dL_drgb, const float *d_dL_ddisp, void *stream);
+GS_API int gs_preprocess_bwd(const gs_plan *plan, void *ws, const gs_params *params,
+                             const gs_camera *h_cams, gs_params *grads, void *stream);
+
+/* ------------------------------------------------------------ a6: loss
+ * Eq. 5: loss = (1 - lambda) L1 + lambda (1 - SSIM) over all views' colour
+ * pixels, SSIM with an 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2,
+ * C2 = 0.03^2, zero-padded same-size windows, averaged over channels and
+ * pixels; L1 = mean absolute difference.  Sec. 3.1: optional disparity term
+ * disp_weight * mean |disp - target_disp| (d_disp may be NULL to skip).
+ * Writes dL/d(rgb) to d_dL_drgb and, if d_disp is given, dL/d(disp) to
+ * d_dL_ddisp (both overwritten), and the scalar loss to d_loss (device, one
+ * float).  d_scratch: device float scratch of gs_loss_scratch_floats(plan).
+ * lambda = 0 gives plain L1 and skips the SSIM passes. */
+GS_API int64_t gs_loss_scratch_floats(const gs_plan *plan);
+GS_API int gs_loss(const gs_plan *plan, const float *d_rgb, const float *d_target, float lambda,
+                   const float *d_disp, const float *d_target_disp, float disp_weight, float *d_dL_drgb,
+                   float *d_dL_ddisp, float *d_loss, float *d_scratch, void *stream);
+
+/* ------------------------------------------------------------ a9: Adam
+ * Adam with bias correction (the optimiser of the 3DGS training the paper
+ * builds on; the paper names none): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps); then g = 0.
+ * All arrays device float32 of n elements; step >= 1.  At most 8 groups per
+ * call. */
+GS_API int gs_adam_step(float *d_p, float *d_g, float *d_m, float *d_v, int64_t n, float lr, float b1,
+                        float b2, float eps, int32_t step, void *stream);
+
+/* The same update over several parameter groups in one launch.  Within a
+ * group, when period > 0 the first `head` elements of every `period`
+ * consecutive elements use lr_head instead of lr (e.g. the DC coefficients
+ * of an n x K x 3 SH array: period = 3K, head = 3). */
+typedef struct {
+    float *p, *g, *m, *v;  /* device */
+    int64_t n;
+    float lr;
+    int64_t period;
+    int64_t head;
+    float lr_head;
+} gs_adam_group;
+GS_API int gs_adam_step_multi(const gs_adam_group *h_groups, int32_t n_groups, float b1, float b2,
+                              float eps, int32_t step, void *stream);
+
+/* -------------------------------------------------- building blocks
+ * Stable LSD radix sort of (uint32 key, uint32 value) pairs on bits
+ * [begin_bit, end_bit) of the key; used by gs_bin_sort and exported for
+ * testing.  n pairs from d_keys_in/d_vals_in are written sorted to
+ * d_keys_out/d_vals_out (may not alias the inputs; the inputs are used as
+ * ping-pong buffers and are clobbered).  d_scratch: device bytes of
+ * gs_sort_scratch_bytes(n). */
+GS_API size_t gs_sort_scratch_bytes(int64_t n);
+GS_API int gs_sort_pairs_u32(uint32_t *d_keys_in, uint32_t *d_vals_in, uint32_t *d_keys_out,
+                             uint32_t *d_vals_out, int64_t n, int32_t begin_bit, int32_t end_bit,
+                             void *d_scratch, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

@@ -1,0 +1,215 @@
+"""Torch-facing wrappers of the C ABI (same names as include/gs.h).
+
+PyTorch only provides device memory and streams here: each function checks
+tensor placement, passes raw device pointers and the current CUDA stream to
+libgs.so and raises GsError on a non-zero status.  No computation of the
+training step happens in Python.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t: torch.Tensor | None, dtype=torch.float32) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def camera_struct(cam) -> L.GsCamera:
+    """GsCamera from any object with fx, fy, cx, cy, w2c() (3x4), width,
+    height and optional near."""
+    c = L.GsCamera()
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    w = cam.w2c().reshape(-1)
+    for i in range(12):
+        c.w2c[i] = float(w[i])
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.near_z = float(getattr(cam, "near", 0.2))
+    return c
+
+
+def cameras_array(cams) -> ctypes.Array:
+    arr = (L.GsCamera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = camera_struct(c)
+    return arr
+
+
+@dataclass
+class Gaussians:
+    """Gaussian parameter arrays (float32, contiguous, one device)."""
+
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logits: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    def tensors(self):
+        return (self.means, self.log_scales, self.quats, self.opacity_logits, self.sh)
+
+    def struct(self) -> L.GsParams:
+        p = L.GsParams()
+        p.n = self.n
+        p.sh_degree = self.sh_degree
+        p.means, p.log_scales, p.quats, p.opacity_logits, p.sh = (_ptr(t) for t in self.tensors())
+        return p
+
+    def zeros_like(self) -> "Gaussians":
+        return Gaussians(*(torch.zeros_like(t) for t in self.tensors()), sh_degree=self.sh_degree)
+
+    @staticmethod
+    def from_scene(scene, device="cuda") -> "Gaussians":
+        t = lambda a: torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
+        return Gaussians(t(scene.means), t(scene.log_scales), t(scene.quats), t(scene.opacity_logits),
+                         t(scene.sh), int(scene.sh_degree))
+
+
+class Plan:
+    """A gs_plan plus the device workspace it describes."""
+
+    def __init__(self, n: int, sh_degree: int, sizes, inst_capacity: int, device="cuda"):
+        lib = L.lib()
+        self.sizes = [(int(w), int(h)) for (w, h) in sizes]
+        V = len(self.sizes)
+        ws_ = (ctypes.c_int32 * V)(*[w for w, _ in self.sizes])
+        hs_ = (ctypes.c_int32 * V)(*[h for _, h in self.sizes])
+        self.handle = lib.gs_plan_create(int(n), int(sh_degree), V, ws_, hs_, int(inst_capacity))
+        if not self.handle:
+            raise L.GsError(L.GS_ERR_ARG, "gs_plan_create")
+        self.n, self.sh_degree, self.inst_capacity = int(n), int(sh_degree), int(inst_capacity)
+        self.bytes = int(lib.gs_plan_workspace_bytes(self.handle))
+        self.pixels = int(lib.gs_plan_pixels(self.handle))
+        self.ws = torch.empty(self.bytes, dtype=torch.uint8, device=device)
+        self.ws.zero_()
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and L._lib is not None:
+            L._lib.gs_plan_destroy(h)
+            self.handle = None
+
+    @property
+    def n_views(self) -> int:
+        return len(self.sizes)
+
+    def image_shape(self):
+        """(3 * total pixels,) is the flat colour layout; per view planar CHW."""
+        return (3 * self.pixels,)
+
+    def view(self, which: int, dtype=torch.uint8) -> torch.Tensor:
+        """A tensor aliasing one workspace buffer (GS_WS_*)."""
+        ptr = ctypes.c_void_p()
+        nb = ctypes.c_size_t()
+        L.check(L.lib().gs_workspace_view(self.handle, self.ws.data_ptr(), which, ctypes.byref(ptr),
+                                          ctypes.byref(nb)), "gs_workspace_view")
+        off = ptr.value - self.ws.data_ptr()
+        return self.ws[off:off + nb.value].view(dtype)
+
+    def status(self, stream=None) -> dict:
+        st = L.GsStatus()
+        rc = L.lib().gs_read_status(self.handle, self.ws.data_ptr(), ctypes.byref(st), _stream(stream))
+        return {"rc": rc, "n_instances": st.n_instances, "n_buckets": st.n_buckets,
+                "inst_capacity": st.inst_capacity, "overflow": st.overflow, "error": st.error}
+
+
+# ---------------------------------------------------------------- the ABI
+
+def gs_preprocess(plan: Plan, params: Gaussians, cams, stream=None) -> None:
+    ca = cameras_array(cams)
+    p = params.struct()
+    L.check(L.lib().gs_preprocess(plan.handle, plan.ws.data_ptr(), ctypes.byref(p), ca, _stream(stream)),
+            "gs_preprocess")
+
+
+def gs_bin_sort(plan: Plan, load_balanced: bool = True, stream=None) -> None:
+    L.check(L.lib().gs_bin_sort(plan.handle, plan.ws.data_ptr(), int(bool(load_balanced)), _stream(stream)),
+            "gs_bin_sort")
+
+
+def gs_render_fwd(plan: Plan, bg, out_rgb, out_disp, out_T, stream=None) -> None:
+    bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
+    L.check(L.lib().gs_render_fwd(plan.handle, plan.ws.data_ptr(), bgc, _ptr(out_rgb), _ptr(out_disp),
+                                  _ptr(out_T), _stream(stream)), "gs_render_fwd")
+
+
+def gs_render_bwd(plan: Plan, params: Gaussians, cams, bg, rgb, disp, dL_drgb, dL_ddisp,
+                  grads: Gaussians, stream=None) -> None:
+    ca = cameras_array(cams)
+    bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
+    p = params.struct()
+    g = grads.struct()
+    L.check(L.lib().gs_render_bwd(plan.handle, plan.ws.data_ptr(), ctypes.byref(p), ca, bgc, _ptr(rgb),
+                                  _ptr(disp), _ptr(dL_drgb), _ptr(dL_ddisp), ctypes.byref(g),
+                                  _stream(stream)), "gs_render_bwd")
+
+
+def gs_loss_scratch(plan: Plan, device="cuda") -> torch.Tensor:
+    return torch.empty(int(L.lib().gs_loss_scratch_floats(plan.handle)), dtype=torch.float32, device=device)
+
+
+def gs_loss(plan: Plan, rgb, target, lam: float, dL_drgb, loss, scratch, disp=None, target_disp=None,
+            disp_weight: float = 0.0, dL_ddisp=None, stream=None) -> None:
+    L.check(L.lib().gs_loss(plan.handle, _ptr(rgb), _ptr(target), float(lam), _ptr(disp), _ptr(target_disp),
+                            float(disp_weight), _ptr(dL_drgb), _ptr(dL_ddisp), _ptr(loss), _ptr(scratch),
+                            _stream(stream)), "gs_loss")
+
+
+def gs_adam_step(p, g, m, v, lr: float, step: int, b1=0.9, b2=0.999, eps=1e-15, stream=None) -> None:
+    L.check(L.lib().gs_adam_step(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), float(lr), float(b1),
+                                 float(b2), float(eps), int(step), _stream(stream)), "gs_adam_step")
+
+
+def adam_groups_array(groups) -> ctypes.Array:
+    """groups: list of dicts p, g, m, v, lr and optional period, head, lr_head."""
+    arr = (L.GsAdamGroup * len(groups))()
+    for i, gr in enumerate(groups):
+        a = arr[i]
+        a.p, a.g, a.m, a.v = _ptr(gr["p"]), _ptr(gr["g"]), _ptr(gr["m"]), _ptr(gr["v"])
+        a.n = gr["p"].numel()
+        a.lr = float(gr["lr"])
+        a.period = int(gr.get("period", 0))
+        a.head = int(gr.get("head", 0))
+        a.lr_head = float(gr.get("lr_head", 0.0))
+    return arr
+
+
+def gs_adam_step_multi(groups, step: int, b1=0.9, b2=0.999, eps=1e-15, stream=None, _arr=None) -> None:
+    arr = _arr if _arr is not None else adam_groups_array(groups)
+    L.check(L.lib().gs_adam_step_multi(arr, len(arr), float(b1), float(b2), float(eps), int(step),
+                                       _stream(stream)), "gs_adam_step_multi")
+
+
+def gs_sort_pairs_u32(keys_in, vals_in, keys_out, vals_out, begin_bit: int, end_bit: int, scratch=None,
+                      stream=None) -> None:
+    n = keys_in.numel()
+    if scratch is None:
+        scratch = torch.empty(int(L.lib().gs_sort_scratch_bytes(n)), dtype=torch.uint8, device=keys_in.device)
+    for t in (keys_in, vals_in, keys_out, vals_out):
+        if t.dtype not in (torch.int32, torch.uint32):
+            raise TypeError("sort buffers are 32-bit integers")
+    L.check(L.lib().gs_sort_pairs_u32(_ptr(keys_in, None), _ptr(vals_in, None), _ptr(keys_out, None),
+                                      _ptr(vals_out, None), n, int(begin_bit), int(end_bit),
+                                      _ptr(scratch, None), _stream(stream)), "gs_sort_pairs_u32")

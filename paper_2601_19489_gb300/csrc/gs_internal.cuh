@@ -1,0 +1,219 @@
+// Internal definitions shared by the CUDA translation units of libgs:
+// the host plan (workspace layout), the per-view constants passed to kernels
+// by value, and the few device functions whose float32 results must be
+// bit-identical wherever they are evaluated (the tile-column test used by
+// both the tile count and the tile-key write; the alpha evaluation used by
+// both the forward blend and the backward).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+namespace gs {
+
+constexpr int kTile = GS_TILE;             // 16 x 16 pixel tiles
+constexpr int kTilePix = kTile * kTile;    // 256 pixels
+constexpr int kBucket = GS_BUCKET;         // 32 splats per checkpoint
+constexpr int kCkptCh = 5;                 // T, C.r, C.g, C.b, D
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTStop = 1e-4f;
+constexpr float kLog2e = 1.4426950408889634f;
+// The stored conic is (a, b, c) * kH so that e^power = 2^(-(A dx^2 + 2 B dx dy + C dy^2)).
+constexpr float kH = 0.5f * kLog2e;
+constexpr float kInvH = 1.0f / kH;
+// Binning uses a level set widened by a relative 2^-10 and an absolute 2^-12
+// (in units of t), so every pixel the float32 blend can reach lies in a
+// touched tile; the extra tiles only hold pairs with alpha < 1/255.
+constexpr float kLevelRel = 1.0f + 1.0f / 1024.0f;
+constexpr float kLevelAbs = 1.0f / 4096.0f;
+constexpr int kSortBlocks = 608;           // 4 x 152 SMs: fixed grid of the sort/scan passes
+constexpr int kSortThreads = 256;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+// Per-view constants, copied into kernel parameters by value.
+struct ViewDev {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float campos[3];
+    float limx, limy, near_z;
+    int W, H, tiles_x, tiles_y;
+    int tile_off, pix_off;
+};
+
+struct ViewsDev {
+    int V;
+    int total_tiles;
+    ViewDev v[GS_MAX_VIEWS];
+};
+
+// Device status words at the start of the workspace.
+struct StatusDev {
+    uint32_t n_inst;      // instances required by the last bin/sort
+    uint32_t n_buckets;   // buckets of the last bin/sort
+    uint32_t overflow;    // 1 if n_inst > capacity
+    int32_t error;        // first device-side error code
+    uint32_t bucket_next; // dynamic work counter of the backward
+    uint32_t pad[59];
+};
+
+}  // namespace gs
+
+// Workspace layout: byte offsets of every buffer from the workspace base.
+struct gs_plan {
+    int64_t n;
+    int32_t sh_degree, K;
+    int32_t V;
+    int32_t W[GS_MAX_VIEWS], H[GS_MAX_VIEWS];
+    int32_t tiles_x[GS_MAX_VIEWS], tiles_y[GS_MAX_VIEWS];
+    int32_t tile_off[GS_MAX_VIEWS + 1];
+    int64_t pix_off[GS_MAX_VIEWS + 1];
+    int64_t VN;
+    int32_t total_tiles;
+    int32_t tile_bits;
+    int64_t total_pixels;
+    int64_t inst_cap;
+    int64_t bucket_cap;
+    // offsets
+    size_t o_status, o_rec, o_touched, o_rect, o_dkey[2], o_dval[2];
+    size_t o_ikey[2], o_ival[2], o_ranges, o_tile_maxc, o_bucket_off, o_ncontrib;
+    size_t o_ckpt, o_grad2d, o_sort_scratch, o_block_sums;
+    size_t sort_scratch_bytes;
+    size_t bytes;
+    int inst_final;   // which ping-pong buffer holds the sorted instances
+    int depth_final;  // which ping-pong buffer holds the depth-sorted ids
+};
+
+namespace gs {
+
+template <typename T>
+__host__ __device__ inline T *ws_at(void *ws, size_t off) {
+    return reinterpret_cast<T *>(reinterpret_cast<char *>(ws) + off);
+}
+
+ViewsDev make_views(const gs_plan *plan, const gs_camera *cams);
+int check_cuda(cudaError_t e);
+int launch_error();
+
+// Radix sort internals (radix_sort.cu), usable with a device-resident count.
+size_t sort_scratch_bytes();
+int sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b,
+               int64_t n_host, const uint32_t *n_dev, int begin_bit, int end_bit, void *scratch,
+               cudaStream_t s, int *final_buf);
+
+// ----------------------------------------------------------------------------
+// Tile-column test.  For the tile column [xa, xb] (pixel-centre x range of the
+// column, clipped to the image) return the inclusive tile-row range
+// [*ty_lo, *ty_hi] whose pixel-centre rectangles meet the ellipse
+//   A dx^2 + 2 B dx dy + C dy^2 <= tb,   (dx, dy) = (x - mx, y - my),
+// clipped to the rows [ty0, ty1).  detc = A C - B^2 (> 0), rx/ry the ellipse's
+// half extents.  The ellipse's y-range over a column is an interval: its top
+// is the concave upper branch maximised at the tangent point dx = -B ry / A
+// clamped into the column, its bottom the convex lower branch minimised at
+// dx = +B ry / A (Eq. 2, with the sign of its radicand corrected).  Every
+// operation is an explicitly rounded intrinsic so the tile count and the
+// tile-key write compute the same rows.
+__device__ __forceinline__ int column_rows(float mx, float my, float A, float B, float C,
+                                           float detc, float tb, float rx, float ry, float xa,
+                                           float xb, float img_h, int ty0, int ty1, int *ty_lo,
+                                           int *ty_hi) {
+    float dxa = fmaxf(__fsub_rn(xa, mx), -rx);
+    float dxb = fminf(__fsub_rn(xb, mx), rx);
+    if (dxa > dxb) return 0;
+    float tC = __fmul_rn(tb, C);
+    float invC = __frcp_rn(C);
+    float dx_top = __fdiv_rn(__fmul_rn(-B, ry), A);
+    float d = fminf(fmaxf(dx_top, dxa), dxb);
+    float disc = fmaxf(__fsub_rn(tC, __fmul_rn(detc, __fmul_rn(d, d))), 0.0f);
+    float y_hi = __fadd_rn(my, __fmul_rn(__fadd_rn(__fmul_rn(-B, d), __fsqrt_rn(disc)), invC));
+    d = fminf(fmaxf(-dx_top, dxa), dxb);
+    disc = fmaxf(__fsub_rn(tC, __fmul_rn(detc, __fmul_rn(d, d))), 0.0f);
+    float y_lo = __fadd_rn(my, __fmul_rn(__fsub_rn(__fmul_rn(-B, d), __fsqrt_rn(disc)), invC));
+    y_lo = fmaxf(y_lo, 0.5f);
+    y_hi = fminf(y_hi, __fsub_rn(img_h, 0.5f));
+    if (!(y_lo <= y_hi)) return 0;
+    int lo = (int)ceilf(__fmul_rn(__fsub_rn(y_lo, 15.5f), 0.0625f));
+    int hi = (int)floorf(__fmul_rn(__fsub_rn(y_hi, 0.5f), 0.0625f));
+    lo = max(lo, ty0);
+    hi = min(hi, ty1 - 1);
+    if (lo > hi) return 0;
+    *ty_lo = lo;
+    *ty_hi = hi;
+    return hi - lo + 1;
+}
+
+// Half extents of the ellipse A dx^2 + 2 B dx dy + C dy^2 <= tb along x and
+// y: sqrt(tb C / detc) and sqrt(tb A / detc) (Eq. 2's tangent points, i.e.
+// sqrt(t Sxx) and sqrt(t Syy) of the 2D covariance).
+__device__ __forceinline__ void ellipse_extent(float A, float C, float detc, float tb, float *rx,
+                                               float *ry) {
+    *rx = __fsqrt_rn(__fdiv_rn(__fmul_rn(tb, C), detc));
+    *ry = __fsqrt_rn(__fdiv_rn(__fmul_rn(tb, A), detc));
+}
+
+// Tile rectangle [tx0, tx1) x [ty0, ty1) of the SnugBox (pixel-centre bounds
+// of the ellipse, clipped to the image).  Returns false when it is empty.
+__device__ __forceinline__ bool snug_rect(float mx, float my, float rx, float ry, float img_w,
+                                          float img_h, int *tx0, int *ty0, int *tx1, int *ty1) {
+    float xl = fmaxf(__fsub_rn(mx, rx), 0.5f), xh = fminf(__fadd_rn(mx, rx), __fsub_rn(img_w, 0.5f));
+    float yl = fmaxf(__fsub_rn(my, ry), 0.5f), yh = fminf(__fadd_rn(my, ry), __fsub_rn(img_h, 0.5f));
+    if (!(xl <= xh) || !(yl <= yh)) return false;
+    *tx0 = (int)ceilf(__fmul_rn(__fsub_rn(xl, 15.5f), 0.0625f));
+    *tx1 = (int)floorf(__fmul_rn(__fsub_rn(xh, 0.5f), 0.0625f)) + 1;
+    *ty0 = (int)ceilf(__fmul_rn(__fsub_rn(yl, 15.5f), 0.0625f));
+    *ty1 = (int)floorf(__fmul_rn(__fsub_rn(yh, 0.5f), 0.0625f)) + 1;
+    return *tx0 < *tx1 && *ty0 < *ty1;
+}
+
+__device__ __forceinline__ uint2 pack_rect(int tx0, int ty0, int tx1, int ty1) {
+    return make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
+}
+
+__device__ __forceinline__ void unpack_rect(uint2 r, int *tx0, int *ty0, int *tx1, int *ty1) {
+    *tx0 = (int)(r.x & 0xffffu);
+    *ty0 = (int)(r.x >> 16);
+    *tx1 = (int)(r.y & 0xffffu);
+    *ty1 = (int)(r.y >> 16);
+}
+
+// Pixel-centre x range of tile column tx, clipped to the image width.
+__device__ __forceinline__ void column_span(int tx, float img_w, float *xa, float *xb) {
+    *xa = (float)(tx * kTile) + 0.5f;
+    *xb = fminf((float)(tx * kTile) + 15.5f, __fsub_rn(img_w, 0.5f));
+}
+
+// ----------------------------------------------------------------------------
+// Alpha of one (splat, pixel) pair, shared by the forward blend and the
+// backward so both take identical float32 decisions.
+//   r0 = (mx, my, A, B), r1 = (C, log2 o, 1/z, level)   (A, B, C = kH * conic)
+// power2 = -(A dx^2 + 2 B dx dy + C dy^2) is the exponent in base 2; the pair
+// is skipped when power2 > 0 (never for a positive-definite conic) and
+// alpha = min(0.99, 2^(power2 + log2 o)).
+// 2^x with the hardware approximation (PTX ex2.approx.ftz.f32: relative error
+// about 2^-22, subnormal results flushed to zero).
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct PairEval {
+    float dx, dy, power2, raw, alpha;
+};
+
+__device__ __forceinline__ void eval_pair(const float4 &r0, const float4 &r1, float px, float py,
+                                          PairEval &e) {
+    e.dx = __fsub_rn(px, r0.x);
+    e.dy = __fsub_rn(py, r0.y);
+    float u = __fmaf_rn(r0.z, e.dx, __fmul_rn(__fmul_rn(2.0f, r0.w), e.dy));  // A dx + 2B dy
+    float w = __fmul_rn(__fmul_rn(r1.x, e.dy), e.dy);                         // C dy^2
+    e.power2 = -__fmaf_rn(u, e.dx, w);
+    e.raw = fast_exp2(__fadd_rn(e.power2, r1.y));
+    e.alpha = fminf(kAlphaMax, e.raw);
+}
+
+}  // namespace gs

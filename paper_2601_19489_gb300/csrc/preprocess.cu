@@ -1,0 +1,445 @@
+// a1: per-(view, Gaussian) preprocess (Sec. 2.1, Eq. 1-2) and
+// a8: its backward (the per-Gaussian parallel chain rule of Sec. 2.2).
+//
+// Forward, per (view v, Gaussian g):
+//   camera-space mean pc = W p + t; culled when pc.z <= near
+//   Sigma = R(q/|q|) diag(e^{2s}) R^T  written as M M^T with M = R diag(e^s)
+//   J = [[fx/z, 0, -fx x'/z], [0, fy/z, -fy y'/z]] with x' = clamp(x/z, +-1.3 tan(fov_x/2))
+//   Sigma' = (J W M)(J W M)^T + 0.3 I = U U^T + 0.3 I; its determinant is
+//   |U0 x U1|^2 + 0.3 (|U0|^2 + |U1|^2) + 0.09, a sum of non-negative terms,
+//   so the conic Sigma'^{-1} is formed without cancellation
+//   mean2d = (fx x/z + cx, fy y/z + cy);  o = sigmoid(logit);  t = 2 ln(255 o)
+//   colour = max(0, sum_k sh_k Y_k(d) + 0.5), d = (p - camera centre)/|.|
+//   SnugBox of the widened level set and the exact per-column tile count.
+// The record written for the blend is r0 = (mx, my, A, B), r1 = (C, log2 o,
+// 1/z, tb), r2 = (r, g, b, detc) with (A, B, C) = kH * conic, tb = kH * t_bin
+// and detc = A C - B^2 = kH^2 / det(Sigma').
+#include "gs_internal.cuh"
+
+namespace gs {
+
+// Real spherical harmonics (Condon-Shortley phase) up to degree 3.
+constexpr float kSH0 = 0.28209479177387814f;   // 1 / (2 sqrt(pi))
+constexpr float kSH1 = 0.48860251190291992f;   // sqrt(3 / (4 pi))
+constexpr float kSH2a = 1.0925484305920792f;   // sqrt(15 / pi) / 2
+constexpr float kSH2b = 0.31539156525252005f;  // sqrt(5 / pi) / 4
+constexpr float kSH2c = 0.54627421529603959f;  // sqrt(15 / pi) / 4
+constexpr float kSH3a = 0.59004358992664352f;  // sqrt(35 / (2 pi)) / 4
+constexpr float kSH3b = 2.8906114426405538f;   // sqrt(105 / pi) / 2
+constexpr float kSH3c = 0.45704579946446572f;  // sqrt(21 / (2 pi)) / 4
+constexpr float kSH3d = 0.37317633259011540f;  // sqrt(7 / pi) / 4
+constexpr float kSH3e = 1.4453057213202769f;   // sqrt(105 / pi) / 4
+
+template <int D>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float *Y) {
+    Y[0] = kSH0;
+    if (D >= 1) {
+        Y[1] = -kSH1 * y;
+        Y[2] = kSH1 * z;
+        Y[3] = -kSH1 * x;
+    }
+    if (D >= 2) {
+        Y[4] = kSH2a * x * y;
+        Y[5] = -kSH2a * y * z;
+        Y[6] = kSH2b * (3.0f * z * z - 1.0f);
+        Y[7] = -kSH2a * x * z;
+        Y[8] = kSH2c * (x * x - y * y);
+    }
+    if (D >= 3) {
+        Y[9] = -kSH3a * y * (3.0f * x * x - y * y);
+        Y[10] = kSH3b * x * y * z;
+        Y[11] = -kSH3c * y * (5.0f * z * z - 1.0f);
+        Y[12] = kSH3d * z * (5.0f * z * z - 3.0f);
+        Y[13] = -kSH3c * x * (5.0f * z * z - 1.0f);
+        Y[14] = kSH3e * z * (x * x - y * y);
+        Y[15] = -kSH3a * x * (x * x - 3.0f * y * y);
+    }
+}
+
+// Gradient of the basis polynomials w.r.t. (x, y, z); the radial part is
+// removed afterwards by the normalisation's Jacobian.
+template <int D>
+__device__ __forceinline__ void sh_grad(float x, float y, float z, float3 *G) {
+    G[0] = make_float3(0.f, 0.f, 0.f);
+    if (D >= 1) {
+        G[1] = make_float3(0.f, -kSH1, 0.f);
+        G[2] = make_float3(0.f, 0.f, kSH1);
+        G[3] = make_float3(-kSH1, 0.f, 0.f);
+    }
+    if (D >= 2) {
+        G[4] = make_float3(kSH2a * y, kSH2a * x, 0.f);
+        G[5] = make_float3(0.f, -kSH2a * z, -kSH2a * y);
+        G[6] = make_float3(0.f, 0.f, 6.0f * kSH2b * z);
+        G[7] = make_float3(-kSH2a * z, 0.f, -kSH2a * x);
+        G[8] = make_float3(2.0f * kSH2c * x, -2.0f * kSH2c * y, 0.f);
+    }
+    if (D >= 3) {
+        G[9] = make_float3(-6.0f * kSH3a * x * y, -3.0f * kSH3a * (x * x - y * y), 0.f);
+        G[10] = make_float3(kSH3b * y * z, kSH3b * x * z, kSH3b * x * y);
+        G[11] = make_float3(0.f, -kSH3c * (5.0f * z * z - 1.0f), -10.0f * kSH3c * y * z);
+        G[12] = make_float3(0.f, 0.f, kSH3d * (15.0f * z * z - 3.0f));
+        G[13] = make_float3(-kSH3c * (5.0f * z * z - 1.0f), 0.f, -10.0f * kSH3c * x * z);
+        G[14] = make_float3(2.0f * kSH3e * x * z, -2.0f * kSH3e * y * z, kSH3e * (x * x - y * y));
+        G[15] = make_float3(-3.0f * kSH3a * (x * x - y * y), 6.0f * kSH3a * x * y, 0.f);
+    }
+}
+
+__device__ __forceinline__ float3 f3(const float *p) { return make_float3(p[0], p[1], p[2]); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 add3(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 mul3(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Forward quantities shared by the preprocess and its backward.
+struct Proj {
+    float3 pc;          // camera-space mean
+    float iz;           // 1 / z
+    float xz, yz;       // clamped x/z, y/z used in J
+    bool clx, cly;      // clamp active
+    float3 W0, W1, W2;  // rows of the camera rotation
+    float qn[4];        // normalised quaternion (w, x, y, z)
+    float qlen;
+    float Rg[9];        // rotation of the Gaussian, row-major
+    float s[3];         // scales
+    float3 T0, T1;      // rows of J W
+    float3 U0, U1;      // rows of J W R diag(s)
+    float Sxx, Sxy, Syy, det;
+};
+
+__device__ __forceinline__ void project_cov(const ViewDev &cam, float3 p, float4 q, float3 ls, Proj &P) {
+    P.W0 = f3(cam.R);
+    P.W1 = f3(cam.R + 3);
+    P.W2 = f3(cam.R + 6);
+    P.pc = make_float3(dot3(P.W0, p) + cam.t[0], dot3(P.W1, p) + cam.t[1], dot3(P.W2, p) + cam.t[2]);
+    P.iz = 1.0f / P.pc.z;
+    const float ux = P.pc.x * P.iz, uy = P.pc.y * P.iz;
+    P.xz = fminf(fmaxf(ux, -cam.limx), cam.limx);
+    P.yz = fminf(fmaxf(uy, -cam.limy), cam.limy);
+    P.clx = !(ux >= -cam.limx && ux <= cam.limx);
+    P.cly = !(uy >= -cam.limy && uy <= cam.limy);
+    P.qlen = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    const float il = 1.0f / P.qlen;
+    const float w = q.x * il, x = q.y * il, y = q.z * il, z = q.w * il;
+    P.qn[0] = w; P.qn[1] = x; P.qn[2] = y; P.qn[3] = z;
+    P.Rg[0] = 1.f - 2.f * (y * y + z * z); P.Rg[1] = 2.f * (x * y - w * z); P.Rg[2] = 2.f * (x * z + w * y);
+    P.Rg[3] = 2.f * (x * y + w * z); P.Rg[4] = 1.f - 2.f * (x * x + z * z); P.Rg[5] = 2.f * (y * z - w * x);
+    P.Rg[6] = 2.f * (x * z - w * y); P.Rg[7] = 2.f * (y * z + w * x); P.Rg[8] = 1.f - 2.f * (x * x + y * y);
+    P.s[0] = expf(ls.x);
+    P.s[1] = expf(ls.y);
+    P.s[2] = expf(ls.z);
+    P.T0 = mul3(sub3(P.W0, mul3(P.W2, P.xz)), cam.fx * P.iz);
+    P.T1 = mul3(sub3(P.W1, mul3(P.W2, P.yz)), cam.fy * P.iz);
+    // U = T M, M[k][j] = Rg[k][j] s[j]
+    float u0[3], u1[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        u0[j] = (P.T0.x * P.Rg[j] + P.T0.y * P.Rg[3 + j] + P.T0.z * P.Rg[6 + j]) * P.s[j];
+        u1[j] = (P.T1.x * P.Rg[j] + P.T1.y * P.Rg[3 + j] + P.T1.z * P.Rg[6 + j]) * P.s[j];
+    }
+    P.U0 = make_float3(u0[0], u0[1], u0[2]);
+    P.U1 = make_float3(u1[0], u1[1], u1[2]);
+    const float aa = dot3(P.U0, P.U0), cc = dot3(P.U1, P.U1);
+    P.Sxx = aa + 0.3f;
+    P.Syy = cc + 0.3f;
+    P.Sxy = dot3(P.U0, P.U1);
+    const float3 cr = cross3(P.U0, P.U1);
+    P.det = dot3(cr, cr) + 0.3f * (aa + cc) + 0.09f;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256)
+k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
+             const float *__restrict__ log_scales, const float4 *__restrict__ quats,
+             const float *__restrict__ logits, const float *__restrict__ sh, float4 *__restrict__ rec,
+             uint32_t *__restrict__ touched, uint2 *__restrict__ rects, uint32_t *__restrict__ dkey,
+             uint32_t *__restrict__ dval) {
+    constexpr int K = (D + 1) * (D + 1);
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= (int64_t)views.V * n) return;
+    const int v = (int)(item / n);
+    const int64_t g = item - (int64_t)v * n;
+    const ViewDev &cam = views.v[v];
+    dval[item] = (uint32_t)item;
+
+    const float3 p = make_float3(means[3 * g], means[3 * g + 1], means[3 * g + 2]);
+    const float pz = cam.R[6] * p.x + cam.R[7] * p.y + cam.R[8] * p.z + cam.t[2];
+    if (!(pz > cam.near_z)) {
+        touched[item] = 0;
+        rects[item] = make_uint2(0, 0);
+        dkey[item] = 0xffffffffu;
+        return;
+    }
+    Proj P;
+    project_cov(cam, p, quats[g], make_float3(log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2]), P);
+    const float a = P.Syy / P.det, b = -P.Sxy / P.det, c = P.Sxx / P.det;
+    const float mx = cam.fx * P.pc.x * P.iz + cam.cx;
+    const float my = cam.fy * P.pc.y * P.iz + cam.cy;
+    const float o = 1.0f / (1.0f + expf(-logits[g]));
+    const float t = 2.0f * logf(255.0f * o);
+    const float A = kH * a, B = kH * b, C = kH * c;
+    const float detc = (kH * kH) / P.det;
+    const float tb = kH * (t * kLevelRel + kLevelAbs);
+
+    // colour from SH along the viewing direction
+    float3 dir = sub3(p, make_float3(cam.campos[0], cam.campos[1], cam.campos[2]));
+    dir = mul3(dir, rsqrtf(dot3(dir, dir)));
+    float Y[K];
+    sh_eval<D>(dir.x, dir.y, dir.z, Y);
+    const float *shg = sh + g * (K * 3);
+    float r = 0.5f, gg = 0.5f, bb = 0.5f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        r += Y[k] * __ldg(shg + 3 * k);
+        gg += Y[k] * __ldg(shg + 3 * k + 1);
+        bb += Y[k] * __ldg(shg + 3 * k + 2);
+    }
+    r = fmaxf(r, 0.f);
+    gg = fmaxf(gg, 0.f);
+    bb = fmaxf(bb, 0.f);
+
+    rec[3 * item + 0] = make_float4(mx, my, A, B);
+    rec[3 * item + 1] = make_float4(C, log2f(o), P.iz, tb);
+    rec[3 * item + 2] = make_float4(r, gg, bb, detc);
+
+    uint32_t count = 0;
+    int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
+    if (t > 0.0f) {
+        float rx, ry;
+        ellipse_extent(A, C, detc, tb, &rx, &ry);
+        if (snug_rect(mx, my, rx, ry, (float)cam.W, (float)cam.H, &tx0, &ty0, &tx1, &ty1)) {
+            for (int tx = tx0; tx < tx1; ++tx) {
+                float xa, xb;
+                column_span(tx, (float)cam.W, &xa, &xb);
+                int lo, hi;
+                count += column_rows(mx, my, A, B, C, detc, tb, rx, ry, xa, xb, (float)cam.H, ty0, ty1,
+                                     &lo, &hi);
+            }
+        }
+    }
+    if (count == 0) tx0 = ty0 = tx1 = ty1 = 0;
+    touched[item] = count;
+    rects[item] = pack_rect(tx0, ty0, tx1, ty1);
+    dkey[item] = count ? __float_as_uint(P.pc.z) : 0xffffffffu;
+}
+
+// a8: one thread per Gaussian, summing over the views where it touched tiles.
+// grad2d per (view, Gaussian): {d mx, d my, d a, d b}, {d c, d o, d(1/z), -},
+// {d r, d g, d b, -} with (a, b, c) the conic of q = a dx^2 + 2 b dx dy + c dy^2.
+template <int D>
+__global__ void __launch_bounds__(128)
+k_preprocess_bwd(ViewsDev views, int64_t n, const float *__restrict__ means,
+                 const float *__restrict__ log_scales, const float4 *__restrict__ quats,
+                 const float *__restrict__ logits, const float *__restrict__ sh,
+                 const uint32_t *__restrict__ touched, const float4 *__restrict__ grad2d,
+                 float *__restrict__ g_means, float *__restrict__ g_log_scales,
+                 float *__restrict__ g_quats, float *__restrict__ g_logits, float *__restrict__ g_sh) {
+    constexpr int K = (D + 1) * (D + 1);
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const float3 p = make_float3(means[3 * g], means[3 * g + 1], means[3 * g + 2]);
+    const float4 q = quats[g];
+    const float3 ls = make_float3(log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2]);
+    const float o = 1.0f / (1.0f + expf(-logits[g]));
+    float3 dp = make_float3(0.f, 0.f, 0.f);
+    float dRg[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float ds[3] = {0.f, 0.f, 0.f};
+    float dlogit = 0.f;
+    bool any = false;
+    Proj P;
+    for (int v = 0; v < views.V; ++v) {
+        const int64_t item = (int64_t)v * n + g;
+        if (touched[item] == 0) continue;
+        any = true;
+        const ViewDev &cam = views.v[v];
+        project_cov(cam, p, q, ls, P);
+        const float4 ga = grad2d[3 * item + 0];
+        const float4 gb = grad2d[3 * item + 1];
+        const float4 gc = grad2d[3 * item + 2];
+        // ---- opacity
+        dlogit += gb.y * o * (1.0f - o);
+        // ---- colour: SH coefficients and the viewing direction
+        {
+            float3 dv = sub3(p, make_float3(cam.campos[0], cam.campos[1], cam.campos[2]));
+            const float inv_len = rsqrtf(dot3(dv, dv));
+            const float3 dir = mul3(dv, inv_len);
+            float Y[K];
+            float3 G[K];
+            sh_eval<D>(dir.x, dir.y, dir.z, Y);
+            sh_grad<D>(dir.x, dir.y, dir.z, G);
+            const float *shg = sh + g * (K * 3);
+            float *gsh = g_sh + g * (K * 3);
+            float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) raw[ch] += Y[k] * __ldg(shg + 3 * k + ch);
+            const float gr[3] = {raw[0] > 0.f ? gc.x : 0.f, raw[1] > 0.f ? gc.y : 0.f,
+                                 raw[2] > 0.f ? gc.z : 0.f};
+            float3 ddir = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float wk = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    gsh[3 * k + ch] += gr[ch] * Y[k];
+                    wk += gr[ch] * __ldg(shg + 3 * k + ch);
+                }
+                ddir = add3(ddir, mul3(G[k], wk));
+            }
+            // d = dv / |dv|:  d(dv) = (ddir - d (d . ddir)) / |dv|
+            dp = add3(dp, mul3(sub3(ddir, mul3(dir, dot3(dir, ddir))), inv_len));
+        }
+        // ---- conic (a, b, c) = (Syy, -Sxy, Sxx) / det  ->  Sigma' entries
+        const float det2 = P.det * P.det;
+        const float dA = (-ga.z * P.Syy * P.Syy + ga.w * P.Sxy * P.Syy - gb.x * P.Sxy * P.Sxy) / det2;
+        const float dB = (2.f * ga.z * P.Sxy * P.Syy - ga.w * (P.Sxx * P.Syy + P.Sxy * P.Sxy) +
+                          2.f * gb.x * P.Sxx * P.Sxy) / det2;
+        const float dC = (-ga.z * P.Sxy * P.Sxy + ga.w * P.Sxx * P.Sxy - gb.x * P.Sxx * P.Sxx) / det2;
+        // ---- Sigma' = U U^T + 0.3 I
+        const float3 dU0 = add3(mul3(P.U0, 2.f * dA), mul3(P.U1, dB));
+        const float3 dU1 = add3(mul3(P.U1, 2.f * dC), mul3(P.U0, dB));
+        // ---- U = T M, M = Rg diag(s):  dT_k = sum_j dU_j Rg[k][j] s_j;  dM[k][j] = T_k dU_j
+        const float du0[3] = {dU0.x, dU0.y, dU0.z}, du1[3] = {dU1.x, dU1.y, dU1.z};
+        const float t0[3] = {P.T0.x, P.T0.y, P.T0.z}, t1[3] = {P.T1.x, P.T1.y, P.T1.z};
+        float dT0[3], dT1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float m = P.Rg[3 * k + j] * P.s[j];
+                a0 += du0[j] * m;
+                a1 += du1[j] * m;
+                const float dM = t0[k] * du0[j] + t1[k] * du1[j];
+                dRg[3 * k + j] += dM * P.s[j];
+                ds[j] += dM * P.Rg[3 * k + j];
+            }
+            dT0[k] = a0;
+            dT1[k] = a1;
+        }
+        // ---- T0 = fx iz (W0 - xz W2), T1 = fy iz (W1 - yz W2)
+        const float3 vdT0 = make_float3(dT0[0], dT0[1], dT0[2]);
+        const float3 vdT1 = make_float3(dT1[0], dT1[1], dT1[2]);
+        float d_iz = cam.fx * dot3(vdT0, sub3(P.W0, mul3(P.W2, P.xz))) +
+                     cam.fy * dot3(vdT1, sub3(P.W1, mul3(P.W2, P.yz)));
+        const float d_xz = -cam.fx * P.iz * dot3(vdT0, P.W2);
+        const float d_yz = -cam.fy * P.iz * dot3(vdT1, P.W2);
+        float dx = 0.f, dy = 0.f;
+        if (!P.clx) {  // xz = x * iz
+            dx += d_xz * P.iz;
+            d_iz += d_xz * P.pc.x;
+        }
+        if (!P.cly) {
+            dy += d_yz * P.iz;
+            d_iz += d_yz * P.pc.y;
+        }
+        // ---- mean2d = (fx x iz + cx, fy y iz + cy), disparity 1/z
+        dx += ga.x * cam.fx * P.iz;
+        dy += ga.y * cam.fy * P.iz;
+        d_iz += ga.x * cam.fx * P.pc.x + ga.y * cam.fy * P.pc.y + gb.z;
+        const float dz = -d_iz * P.iz * P.iz;
+        // ---- pc = W p + t
+        dp = add3(dp, add3(add3(mul3(P.W0, dx), mul3(P.W1, dy)), mul3(P.W2, dz)));
+    }
+    if (!any) return;
+    // ---- scales: s = exp(log_scale)
+    g_log_scales[3 * g + 0] += ds[0] * P.s[0];
+    g_log_scales[3 * g + 1] += ds[1] * P.s[1];
+    g_log_scales[3 * g + 2] += ds[2] * P.s[2];
+    // ---- rotation of the unit quaternion, then its normalisation
+    const float w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
+    const float *R = dRg;
+    float dqn[4];
+    dqn[0] = 2.f * (-z * R[1] + y * R[2] + z * R[3] - x * R[5] - y * R[6] + x * R[7]);
+    dqn[1] = 2.f * (y * R[1] + z * R[2] + y * R[3] - 2.f * x * R[4] - w * R[5] + z * R[6] + w * R[7] -
+                    2.f * x * R[8]);
+    dqn[2] = 2.f * (-2.f * y * R[0] + x * R[1] + w * R[2] + x * R[3] + z * R[5] - w * R[6] + z * R[7] -
+                    2.f * y * R[8]);
+    dqn[3] = 2.f * (-2.f * z * R[0] - w * R[1] + x * R[2] + w * R[3] - 2.f * z * R[4] + y * R[5] + x * R[6] +
+                    y * R[7]);
+    const float proj = dqn[0] * w + dqn[1] * x + dqn[2] * y + dqn[3] * z;
+    const float il = 1.0f / P.qlen;
+    g_quats[4 * g + 0] += (dqn[0] - w * proj) * il;
+    g_quats[4 * g + 1] += (dqn[1] - x * proj) * il;
+    g_quats[4 * g + 2] += (dqn[2] - y * proj) * il;
+    g_quats[4 * g + 3] += (dqn[3] - z * proj) * il;
+    g_means[3 * g + 0] += dp.x;
+    g_means[3 * g + 1] += dp.y;
+    g_means[3 * g + 2] += dp.z;
+    g_logits[g] += dlogit;
+}
+
+template <int D>
+static void launch_preprocess(const gs_plan *plan, void *ws, const gs_params *pr, const ViewsDev &vd,
+                              cudaStream_t s) {
+    const int64_t total = plan->VN;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    k_preprocess<D><<<blocks, 256, 0, s>>>(
+        vd, plan->n, pr->means, pr->log_scales, (const float4 *)pr->quats, pr->opacity_logits, pr->sh,
+        ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_touched), ws_at<uint2>(ws, plan->o_rect),
+        ws_at<uint32_t>(ws, plan->o_dkey[0]), ws_at<uint32_t>(ws, plan->o_dval[0]));
+}
+
+template <int D>
+static void launch_preprocess_bwd(const gs_plan *plan, void *ws, const gs_params *pr, const ViewsDev &vd,
+                                  gs_params *gr, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((plan->n + 127) / 128);
+    k_preprocess_bwd<D><<<blocks, 128, 0, s>>>(
+        vd, plan->n, pr->means, pr->log_scales, (const float4 *)pr->quats, pr->opacity_logits, pr->sh,
+        ws_at<uint32_t>(ws, plan->o_touched), ws_at<float4>(ws, plan->o_grad2d), gr->means,
+        gr->log_scales, gr->quats, gr->opacity_logits, gr->sh);
+}
+
+int check_params(const gs_plan *plan, const gs_params *p) {
+    if (!p || p->n != plan->n || p->sh_degree != plan->sh_degree || !p->means || !p->log_scales ||
+        !p->quats || !p->opacity_logits || !p->sh)
+        return GS_ERR_ARG;
+    if (((uintptr_t)p->quats) & 15) return GS_ERR_ARG;  // read as float4
+    return GS_OK;
+}
+
+int check_cams(const gs_plan *plan, const gs_camera *cams) {
+    if (!cams) return GS_ERR_ARG;
+    for (int v = 0; v < plan->V; ++v)
+        if (cams[v].width != plan->W[v] || cams[v].height != plan->H[v] || !(cams[v].fx > 0.f) ||
+            !(cams[v].fy > 0.f))
+            return GS_ERR_ARG;
+    return GS_OK;
+}
+
+int preprocess_bwd(const gs_plan *plan, void *ws, const gs_params *params, const gs_camera *cams,
+                   gs_params *grads, cudaStream_t s) {
+    const ViewsDev vd = make_views(plan, cams);
+    switch (plan->sh_degree) {
+        case 0: launch_preprocess_bwd<0>(plan, ws, params, vd, grads, s); break;
+        case 1: launch_preprocess_bwd<1>(plan, ws, params, vd, grads, s); break;
+        case 2: launch_preprocess_bwd<2>(plan, ws, params, vd, grads, s); break;
+        default: launch_preprocess_bwd<3>(plan, ws, params, vd, grads, s); break;
+    }
+    return launch_error();
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" int gs_preprocess(const gs_plan *plan, void *ws, const gs_params *params,
+                             const gs_camera *cams, void *stream) {
+    if (!plan || !ws) return GS_ERR_ARG;
+    int rc = check_params(plan, params);
+    if (rc) return rc;
+    rc = check_cams(plan, cams);
+    if (rc) return rc;
+    const ViewsDev vd = make_views(plan, cams);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (plan->sh_degree) {
+        case 0: launch_preprocess<0>(plan, ws, params, vd, s); break;
+        case 1: launch_preprocess<1>(plan, ws, params, vd, s); break;
+        case 2: launch_preprocess<2>(plan, ws, params, vd, s); break;
+        default: launch_preprocess<3>(plan, ws, params, vd, s); break;
+    }
+    return launch_error();
+}

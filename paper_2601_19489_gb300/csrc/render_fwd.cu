@@ -1,0 +1,129 @@
+// a5: forward blend (Sec. 2.1 renderCUDA) with the 32-splat checkpoints of
+// Sec. 2.2.
+//
+// One CTA of 256 threads per 16x16 tile, one pixel per thread.  The tile's
+// depth-sorted instance list is staged in shared memory in batches of 256
+// records (each thread gathers one record, 48 bytes, from the per-Gaussian
+// record buffer, which stays L2-resident).  Each pixel blends front to back
+// until its transmittance would fall below 1e-4; a warp whose pixels are all
+// done skips the rest of the batch and the CTA leaves when all 256 are done.
+// Before list positions 0, 32, 64, ... every pixel still running stores its
+// (T, C, D) in bucket-major, channel-planar layout [bucket][5][256] so the
+// backward's warps read them coalesced.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+__device__ __forceinline__ int view_of_tile(const ViewsDev &vd, int t) {
+    int v = 0;
+    while (v + 1 < vd.V && t >= vd.v[v + 1].tile_off) ++v;
+    return v;
+}
+
+__global__ void __launch_bounds__(kTilePix)
+k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ inst_item,
+             const float4 *__restrict__ rec, const uint32_t *__restrict__ bucket_off, float bg_r,
+             float bg_g, float bg_b, float *__restrict__ out_rgb, float *__restrict__ out_disp,
+             float *__restrict__ out_T, uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ tile_maxc,
+             float *__restrict__ ckpt) {
+    __shared__ float4 s_r0[kTilePix];
+    __shared__ float4 s_r1[kTilePix];
+    __shared__ float4 s_r2[kTilePix];
+    __shared__ uint32_t s_maxc;
+
+    const int t = blockIdx.x;
+    const int v = view_of_tile(views, t);
+    const ViewDev &cam = views.v[v];
+    const int lt = t - cam.tile_off;
+    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+    const int tid = threadIdx.x;
+    const int ix = tx * kTile + (tid & (kTile - 1)), iy = ty * kTile + (tid >> 4);
+    const bool inside = ix < cam.W && iy < cam.H;
+    const float px = (float)ix + 0.5f, py = (float)iy + 0.5f;
+    const uint2 range = ranges[t];
+    const int n = (int)(range.y - range.x);
+    float *ck = ckpt + (size_t)bucket_off[t] * (kCkptCh * kTilePix) + tid;
+    if (tid == 0) s_maxc = 0;
+
+    float T = 1.0f, Cr = 0.f, Cg = 0.f, Cb = 0.f, D = 0.f;
+    uint32_t last = 0;
+    bool done = !inside;
+    for (int b0 = 0; b0 < n; b0 += kTilePix) {
+        if (__syncthreads_count(!done) == 0) break;  // also fences the previous batch
+        if (b0 + tid < n) {
+            const size_t it = inst_item[range.x + b0 + tid];
+            s_r0[tid] = rec[3 * it];
+            s_r1[tid] = rec[3 * it + 1];
+            s_r2[tid] = rec[3 * it + 2];
+        }
+        __syncthreads();
+        const int cnt = min(kTilePix, n - b0);
+        for (int j0 = 0; j0 < cnt; j0 += kBucket) {
+            if (__all_sync(0xffffffffu, done)) break;
+            if (!done) {  // checkpoint before list position b0 + j0
+                float *c = ck + (size_t)((b0 + j0) / kBucket) * (kCkptCh * kTilePix);
+                c[0] = T;
+                c[kTilePix] = Cr;
+                c[2 * kTilePix] = Cg;
+                c[3 * kTilePix] = Cb;
+                c[4 * kTilePix] = D;
+            }
+            const int j1 = min(j0 + kBucket, cnt);
+            for (int j = j0; j < j1 && !done; ++j) {
+                const float4 r0 = s_r0[j], r1 = s_r1[j];
+                PairEval e;
+                eval_pair(r0, r1, px, py, e);
+                if (e.power2 > 0.0f || e.alpha < kAlphaMin) continue;
+                const float test_T = T * (1.0f - e.alpha);
+                if (test_T < kTStop) {
+                    done = true;
+                    break;
+                }
+                const float4 r2 = s_r2[j];
+                const float w = e.alpha * T;
+                Cr += r2.x * w;
+                Cg += r2.y * w;
+                Cb += r2.z * w;
+                D += r1.z * w;
+                T = test_T;
+                last = (uint32_t)(b0 + j + 1);
+            }
+        }
+    }
+    if (inside) {
+        const size_t npix = (size_t)cam.W * cam.H;
+        const size_t pix = (size_t)iy * cam.W + ix;
+        const size_t base = (size_t)cam.pix_off;
+        out_rgb[3 * base + pix] = Cr + T * bg_r;
+        out_rgb[3 * base + npix + pix] = Cg + T * bg_g;
+        out_rgb[3 * base + 2 * npix + pix] = Cb + T * bg_b;
+        out_disp[base + pix] = D;
+        out_T[base + pix] = T;
+        n_contrib[base + pix] = last;
+    }
+    // tile maximum of n_contrib: buckets at or beyond it have no work
+    uint32_t m = last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if ((tid & 31) == 0) atomicMax(&s_maxc, m);
+    __syncthreads();
+    if (tid == 0) tile_maxc[t] = s_maxc;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" int gs_render_fwd(const gs_plan *plan, void *ws, const float *bg, float *out_rgb,
+                             float *out_disp, float *out_T, void *stream) {
+    if (!plan || !ws || !bg || !out_rgb || !out_disp || !out_T) return GS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const ViewsDev vd = make_views(plan, nullptr);
+    k_render_fwd<<<plan->total_tiles, kTilePix, 0, s>>>(
+        vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
+        ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off), bg[0], bg[1], bg[2],
+        out_rgb, out_disp, out_T, ws_at<uint32_t>(ws, plan->o_ncontrib),
+        ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt));
+    return launch_error();
+}

@@ -1,0 +1,101 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every entry point include/gs.h declares, and the pure-host
+calls (plan creation, sizes, error strings) behave as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^GS_API[^(;]*?\b(gs_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2601_19489_gb300 import _lib
+
+    return _lib.load()
+
+
+def test_header_declares_the_path(lib):
+    names = _declared()
+    for required in ("gs_preprocess", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd", "gs_adam_step"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2601_19489_gb300 import _lib
+
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert name in _lib.EXPORTS, name
+    assert set(_lib.EXPORTS) == _declared()
+
+
+def test_plan_rejects_bad_arguments(lib):
+    w = (ctypes.c_int32 * 2)(64, 32)
+    h = (ctypes.c_int32 * 2)(48, 16)
+    assert lib.gs_plan_create(0, 0, 1, w, h, 100) is None
+    assert lib.gs_plan_create(10, 4, 1, w, h, 100) is None
+    assert lib.gs_plan_create(10, 0, 0, w, h, 100) is None
+    assert lib.gs_plan_create(10, 0, 17, w, h, 100) is None
+    assert lib.gs_plan_create(10, 0, 1, w, h, 0) is None
+    assert lib.gs_plan_create(10, 0, 1, w, h, 1 << 31) is None
+    bad = (ctypes.c_int32 * 1)(0)
+    assert lib.gs_plan_create(10, 0, 1, bad, h, 100) is None
+
+
+def test_plan_sizes(lib):
+    w = (ctypes.c_int32 * 2)(1920, 333)
+    h = (ctypes.c_int32 * 2)(1080, 187)
+    p = lib.gs_plan_create(1 << 20, 3, 2, w, h, 1 << 24)
+    assert p
+    try:
+        assert lib.gs_plan_pixels(p) == 1920 * 1080 + 333 * 187
+        nbytes = lib.gs_plan_workspace_bytes(p)
+        # at least the per-instance buffers, checkpoints and records
+        assert nbytes > 4 * 4 * (1 << 24) + 48 * 2 * (1 << 20)
+        ptr = ctypes.c_void_p()
+        nb = ctypes.c_size_t()
+        base = 1 << 40
+        seen = []
+        for which in range(10):
+            assert lib.gs_workspace_view(p, base, which, ctypes.byref(ptr), ctypes.byref(nb)) == 0
+            assert (ptr.value - base) % 256 == 0 and ptr.value - base + nb.value <= nbytes
+            seen.append((ptr.value, nb.value))
+        assert lib.gs_workspace_view(p, base, 99, ctypes.byref(ptr), ctypes.byref(nb)) == -1
+        # distinct buffers do not overlap
+        seen.sort()
+        for (a, na), (b, _) in zip(seen[:-1], seen[1:]):
+            assert a + na <= b
+        assert lib.gs_loss_scratch_floats(p) >= 9 * lib.gs_plan_pixels(p)
+    finally:
+        lib.gs_plan_destroy(p)
+
+
+def test_error_strings(lib):
+    for code in (0, -1, -2, -3, -4, -5):
+        assert lib.gs_error_string(code)
+    assert lib.gs_error_string(-99) == b"unknown error"
+
+
+def test_argument_errors_are_caught_on_the_host(lib):
+    assert lib.gs_preprocess(None, None, None, None, None) == -1
+    assert lib.gs_bin_sort(None, None, 1, None) == -1
+    assert lib.gs_render_fwd(None, None, None, None, None, None, None) == -1
+    assert lib.gs_sort_pairs_u32(None, None, None, None, -1, 0, 8, None, None) == -1
+    assert lib.gs_sort_pairs_u32(None, None, None, None, 0, 0, 8, None, None) == 0  # empty: no-op
+    from paper_2601_19489_gb300 import _lib
+
+    assert lib.gs_adam_step_multi(None, 0, 0.9, 0.999, 1e-15, 1, None) == -1
+    g = (_lib.GsAdamGroup * 1)()
+    assert lib.gs_adam_step_multi(g, 1, 0.9, 0.999, 1e-15, 0, None) == -1  # step < 1

@@ -1,0 +1,379 @@
+"""Parity of the CUDA path (called through the C ABI) with the float64
+oracle on seeded inputs.  Tolerances are stated in tests/parity.py."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import adam as oadam
+from oracle import binning as obin
+from oracle import loss as oloss
+from oracle import preprocess as opre
+from oracle import render as oren
+from tests.parity import grad_mismatch, pixel_mismatch, to_np, view_image
+
+pytestmark = pytest.mark.gpu
+
+BG = (0.3, 0.1, 0.6)
+AMB = (3e-5, 3e-5, 3e-5, 1e-6)
+
+
+def _run_forward(gs, scene, cams, cap=1 << 22, lb=True):
+    from paper_2601_19489_gb300 import api
+
+    plan = api.Plan(scene.n, scene.sh_degree, [(c.width, c.height) for c in cams], cap)
+    params = api.Gaussians.from_scene(scene)
+    P = plan.pixels
+    rgb = torch.empty(3 * P, device="cuda")
+    disp = torch.empty(P, device="cuda")
+    T = torch.empty(P, device="cuda")
+    api.gs_preprocess(plan, params, cams)
+    api.gs_bin_sort(plan, lb)
+    api.gs_render_fwd(plan, BG, rgb, disp, T)
+    st = plan.status()
+    assert st["rc"] == 0, st
+    return plan, params, rgb, disp, T
+
+
+def _oracle_records(scene, cam):
+    pr = opre.project(opre.params_from_scene(scene), cam, scene.sh_degree)
+    return pr, opre.pack_for_render(pr)
+
+
+# ------------------------------------------------------------------ sort
+
+@pytest.mark.parametrize("n,begin,end", [(1, 0, 8), (5, 0, 0), (2049, 0, 13), (100003, 0, 32),
+                                         (1 << 20, 3, 19), (3000, 8, 16)])
+def test_sort_pairs_matches_stable_sort(gs, n, begin, end):
+    from paper_2601_19489_gb300 import api
+
+    rng = np.random.default_rng(n + begin)
+    keys = rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+    if n > 1000:
+        keys[: n // 3] = keys[0]  # long runs of equal digits
+    vals = rng.permutation(n).astype(np.uint32)
+    kt = torch.from_numpy(keys.view(np.int32)).cuda()
+    vt = torch.from_numpy(vals.view(np.int32)).cuda()
+    ko = torch.empty_like(kt)
+    vo = torch.empty_like(vt)
+    api.gs_sort_pairs_u32(kt, vt, ko, vo, begin, end)
+    torch.cuda.synchronize()
+    mask = np.uint32(((1 << (end - begin)) - 1) << begin) if end > begin else np.uint32(0)
+    order = np.argsort(keys & mask, kind="stable")
+    np.testing.assert_array_equal(to_np(ko).view(np.uint32), keys[order])
+    np.testing.assert_array_equal(to_np(vo).view(np.uint32), vals[order])
+
+
+# ------------------------------------------------------------ preprocess
+
+@pytest.mark.parametrize("which", ["c1", "clustered"])
+def test_preprocess_matches_oracle(gs, which):
+    from paper_2601_19489_gb300 import _lib as L
+
+    if which == "c1":
+        scene, cam = synth.scene_c1(0), synth.camera_c1()
+    else:
+        scene = synth.scene_clustered(20000, seed=3, sh_degree=3)
+        cam = synth.ring_cameras(4, 328, 200)[1]
+    plan, params, *_ = _run_forward(gs, scene, [cam])
+    rec = to_np(plan.view(L.GS_WS_RECORDS, torch.float32)).reshape(-1, 12).astype(np.float64)
+    touched = to_np(plan.view(L.GS_WS_TILES_TOUCHED, torch.int32))
+    pr, orec = _oracle_records(scene, cam)
+    kH = 0.5 * math.log2(math.e)
+    ok = (orec[:, 11] > 0) & (orec[:, 10] > 0) & (touched > 0)
+    assert ok.sum() > 0.3 * scene.n
+    np.testing.assert_allclose(rec[ok, 0:2], orec[ok, 0:2], rtol=1e-5, atol=2e-4)
+    scale = np.maximum(np.abs(orec[ok, 2]), np.abs(orec[ok, 4]))[:, None]
+    conic = np.stack([rec[ok, 2], rec[ok, 3], rec[ok, 4]], 1) / kH
+    assert np.all(np.abs(conic - orec[ok, 2:5]) <= 2e-4 * scale)
+    np.testing.assert_allclose(2.0 ** rec[ok, 5], orec[ok, 5], rtol=2e-6)
+    np.testing.assert_allclose(rec[ok, 6], 1.0 / orec[ok, 9], rtol=2e-6)
+    np.testing.assert_allclose(rec[ok, 8:11], orec[ok, 6:9], atol=2e-5)
+    # exact tile count: every tile the level set reaches, none beyond the
+    # widened level set used for binning
+    tiles = obin.tile_min_q(orec, cam.width, cam.height)
+    for gid in np.nonzero(orec[:, 11] > 0)[0][:: max(1, scene.n // 1500)]:
+        ids, mq, t = tiles.get(gid, (np.zeros(0, int), np.zeros(0), 0.0))
+        required = int((mq <= t).sum())
+        allowed = int((mq <= (t * (1 + 2 ** -10) + 2 ** -12) * (1 + 1e-4)).sum())
+        assert required <= touched[gid] <= allowed, (gid, required, touched[gid], allowed)
+
+
+# --------------------------------------------------------------- binning
+
+def test_binning_lists_match_oracle_and_lb_equals_sq(gs):
+    from paper_2601_19489_gb300 import _lib as L
+
+    scene = synth.scene_clustered(30000, seed=5, sh_degree=0)
+    cam = synth.ring_cameras(8, 400, 248)[3]
+    plan_lb, *_ = _run_forward(gs, scene, [cam], lb=True)
+    plan_sq, *_ = _run_forward(gs, scene, [cam], lb=False)
+    n_inst = plan_lb.status()["n_instances"]
+    assert n_inst == plan_sq.status()["n_instances"] > 0
+    for which in (L.GS_WS_INST_TILE, L.GS_WS_INST_GID, L.GS_WS_TILE_RANGES):
+        a = to_np(plan_lb.view(which, torch.int32))
+        b = to_np(plan_sq.view(which, torch.int32))
+        n = n_inst if which != L.GS_WS_TILE_RANGES else a.size
+        np.testing.assert_array_equal(a[:n], b[:n])
+    tile = to_np(plan_lb.view(L.GS_WS_INST_TILE, torch.int32))[:n_inst]
+    item = to_np(plan_lb.view(L.GS_WS_INST_GID, torch.int32))[:n_inst]
+    ranges = to_np(plan_lb.view(L.GS_WS_TILE_RANGES, torch.int32)).reshape(-1, 2)
+    assert np.all(np.diff(tile) >= 0)
+    _, orec = _oracle_records(scene, cam)
+    tiles = obin.tile_min_q(orec, cam.width, cam.height)
+    req = {}
+    allow = {}
+    for gid, (ids, mq, t) in tiles.items():
+        for tid, q in zip(ids.tolist(), mq.tolist()):
+            if q <= t:
+                req.setdefault(tid, set()).add(gid)
+            if q <= (t * (1 + 2 ** -10) + 2 ** -12) * (1 + 1e-4):
+                allow.setdefault(tid, set()).add(gid)
+    z = orec[:, 9]
+    for tid in range(ranges.shape[0]):
+        s, e = ranges[tid]
+        got = item[s:e].tolist()
+        assert np.all(tile[s:e] == tid)
+        gs_set = set(got)
+        assert len(gs_set) == len(got)
+        assert req.get(tid, set()) <= gs_set <= allow.get(tid, set()), tid
+        # depth order, ties by index (float32 near-ties may swap)
+        for a, b in zip(got[:-1], got[1:]):
+            if abs(z[a] - z[b]) > 1e-6 * z[a]:
+                assert (z[a], a) < (z[b], b), (tid, a, b)
+
+
+# --------------------------------------------------------------- forward
+
+@pytest.mark.parametrize("which", ["c1", "clustered_ragged"])
+def test_render_fwd_matches_oracle(gs, which):
+    if which == "c1":
+        scene, cam = synth.scene_c1(0), synth.camera_c1()
+    else:
+        scene = synth.scene_clustered(40000, seed=7, sh_degree=3)
+        cam = synth.ring_cameras(4, 333, 187)[2]  # ragged: partial tiles on both edges
+    plan, params, rgb, disp, T = _run_forward(gs, scene, [cam])
+    _, orec = _oracle_records(scene, cam)
+    ref = oren.render_fwd(orec, BG, (0, 0, cam.width, cam.height), amb=AMB)
+    ok = ~ref["amb"]
+    assert ref["amb"].mean() < 2e-3, ref["amb"].mean()
+    W, H = cam.width, cam.height
+    g_rgb = view_image(rgb, W, H)
+    g_disp = view_image(disp, W, H, channels=1)[0]
+    g_T = view_image(T, W, H, channels=1)[0]
+    for ch in range(3):
+        bad = pixel_mismatch(g_rgb[ch], ref["rgb"][ch], ok)
+        assert bad.sum() == 0, (ch, bad.sum(), np.abs(g_rgb[ch] - ref["rgb"][ch])[bad].max())
+    assert pixel_mismatch(g_disp, ref["disp"], ok).sum() == 0
+    assert pixel_mismatch(g_T, ref["T"], ok).sum() == 0
+
+
+# -------------------------------------------------------------- backward
+
+@pytest.mark.parametrize("which", ["c1", "clustered_ragged"])
+def test_render_bwd_matches_oracle(gs, which):
+    from paper_2601_19489_gb300 import _lib as L
+    from paper_2601_19489_gb300 import api
+
+    if which == "c1":
+        scene, cam = synth.scene_c1(1), synth.camera_c1()
+    else:
+        scene = synth.scene_clustered(30000, seed=9, sh_degree=3)
+        cam = synth.ring_cameras(4, 272, 165)[0]
+    W, H = cam.width, cam.height
+    plan, params, rgb, disp, T = _run_forward(gs, scene, [cam])
+    _, orec = _oracle_records(scene, cam)
+    ref = oren.render_fwd(orec, BG, (0, 0, W, H), amb=AMB)
+    g, gd = synth.upstream_grads(11, W, H)
+    g[:, ref["amb"]] = 0.0
+    gd[ref["amb"]] = 0.0
+    grads = params.zeros_like()
+    api.gs_render_bwd(plan, params, [cam], BG, rgb, disp, torch.from_numpy(g.reshape(-1)).cuda(),
+                      torch.from_numpy(gd.reshape(-1)).cuda(), grads)
+    assert plan.status()["rc"] == 0
+    g2d = to_np(plan.view(L.GS_WS_GRAD2D, torch.float32)).reshape(-1, 12)
+    gpu10 = np.stack([g2d[:, 0], g2d[:, 1], g2d[:, 2], g2d[:, 3], g2d[:, 4], g2d[:, 5], g2d[:, 8],
+                      g2d[:, 9], g2d[:, 10], g2d[:, 6]], 1)
+    ref2d = oren.render_bwd(orec, BG, (0, 0, W, H), g.astype(np.float64), gd.astype(np.float64))
+    names = ["mx", "my", "a", "b", "c", "o", "r", "g", "b", "invz"]
+    for k in range(10):
+        bad = grad_mismatch(gpu10[:, k], ref2d[:, k])
+        assert bad.sum() == 0, (names[k], bad.sum(), np.nonzero(bad)[0][:5])
+    # parameters: oracle preprocess backward of the oracle's 2D gradients
+    ref_p = opre.preprocess_backward(scene, cam, ref2d)
+    for name, t in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), grads.tensors()):
+        got = to_np(t)
+        bad = grad_mismatch(got, ref_p[name])
+        assert bad.sum() == 0, (name, bad.sum())
+
+
+# ------------------------------------------------------------------ loss
+
+@pytest.mark.parametrize("lam", [0.0, 0.2])
+def test_loss_matches_oracle(gs, lam):
+    from paper_2601_19489_gb300 import api
+
+    sizes = [(200, 120), (77, 45)]
+    plan = api.Plan(16, 0, sizes, 1024)
+    P = plan.pixels
+    rng = np.random.default_rng(3)
+    x = rng.uniform(size=3 * P).astype(np.float32)
+    y = rng.uniform(size=3 * P).astype(np.float32)
+    d = rng.uniform(size=P).astype(np.float32)
+    dt = rng.uniform(size=P).astype(np.float32)
+    xt, yt, dtt, dtt2 = (torch.from_numpy(a).cuda() for a in (x, y, d, dt))
+    grad = torch.empty_like(xt)
+    gdisp = torch.empty_like(dtt)
+    loss = torch.zeros(1, device="cuda")
+    api.gs_loss(plan, xt, yt, lam, grad, loss, api.gs_loss_scratch(plan), disp=dtt, target_disp=dtt2,
+                disp_weight=0.1, dL_ddisp=gdisp)
+    torch.cuda.synchronize()
+    # oracle: the loss is a pixel-weighted mean over both views
+    tot_loss = 0.0
+    off = 0
+    ref_grad = np.zeros(3 * P)
+    for (w, h) in sizes:
+        n = w * h
+        xi = x[3 * off: 3 * off + 3 * n].reshape(3, h, w)
+        yi = y[3 * off: 3 * off + 3 * n].reshape(3, h, w)
+        Li, gi = oloss.photometric(xi, yi, lam)
+        frac = n / P
+        tot_loss += Li * frac
+        ref_grad[3 * off: 3 * off + 3 * n] = gi.reshape(-1) * frac
+        off += n
+    Ld, gd = oloss.disparity_l1(d, dt, 0.1)
+    np.testing.assert_allclose(loss.item(), tot_loss + Ld, rtol=1e-5)
+    assert grad_mismatch(to_np(grad), ref_grad).sum() == 0
+    np.testing.assert_allclose(to_np(gdisp), gd, rtol=1e-5, atol=1e-12)
+
+
+# ------------------------------------------------------------------ adam
+
+def test_adam_matches_oracle_and_torch(gs):
+    from paper_2601_19489_gb300 import api
+
+    rng = np.random.default_rng(4)
+    n = 10007  # ragged for the float4 path
+    p0 = rng.standard_normal(n).astype(np.float32)
+    pt = torch.from_numpy(p0.copy()).cuda()
+    m = torch.zeros_like(pt)
+    v = torch.zeros_like(pt)
+    ref_p, ref_m, ref_v = p0.astype(np.float64), np.zeros(n), np.zeros(n)
+    tp = torch.nn.Parameter(torch.from_numpy(p0.copy()).cuda())
+    opt = torch.optim.Adam([tp], lr=1e-2, betas=(0.9, 0.999), eps=1e-15)
+    for step in range(1, 4):
+        g0 = rng.standard_normal(n).astype(np.float32)
+        g = torch.from_numpy(g0.copy()).cuda()
+        api.gs_adam_step(pt, g, m, v, 1e-2, step)
+        ref_p, ref_m, ref_v = oadam.adam_step(ref_p, g0, ref_m, ref_v, step, lr=1e-2)
+        tp.grad = torch.from_numpy(g0.copy()).cuda()
+        opt.step()
+        assert float(g.abs().max()) == 0.0  # gradient zeroed
+    np.testing.assert_allclose(to_np(pt), ref_p, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(to_np(pt), to_np(tp), rtol=1e-6, atol=1e-7)
+
+
+def test_adam_multi_group_period_lr(gs):
+    from paper_2601_19489_gb300 import api
+
+    K3 = 48
+    n = 100 * K3
+    g0 = np.random.default_rng(5).standard_normal(n).astype(np.float32)
+    p = torch.zeros(n, device="cuda")
+    g = torch.from_numpy(g0).cuda()
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    q = torch.zeros(7, device="cuda")
+    gq = torch.ones(7, device="cuda")
+    mq = torch.zeros_like(q)
+    vq = torch.zeros_like(q)
+    api.gs_adam_step_multi([{"p": p, "g": g, "m": m, "v": v, "lr": 1e-3, "period": K3, "head": 3,
+                             "lr_head": 5e-2},
+                            {"p": q, "g": gq, "m": mq, "v": vq, "lr": 0.5}], step=1)
+    torch.cuda.synchronize()
+    want = -np.sign(g0) * np.where(np.arange(n) % K3 < 3, 5e-2, 1e-3)
+    np.testing.assert_allclose(to_np(p), want, rtol=1e-5)
+    np.testing.assert_allclose(to_np(q), -0.5, rtol=1e-6)
+
+
+# --------------------------------------------------------- multi-view
+
+def test_multiview_plan_equals_single_views(gs):
+    from paper_2601_19489_gb300 import api
+
+    scene = synth.scene_clustered(20000, seed=12, sh_degree=2)
+    cams = [synth.ring_cameras(4, 200, 120)[0], synth.ring_cameras(4, 96, 70)[1],
+            synth.ring_cameras(4, 150, 150)[2]]
+    plan, params, rgb, disp, T = _run_forward(gs, scene, cams)
+    g_all = torch.randn(3 * plan.pixels, device="cuda")
+    grads = params.zeros_like()
+    api.gs_render_bwd(plan, params, cams, BG, rgb, disp, g_all, None, grads)
+    off = 0
+    acc = [torch.zeros_like(t) for t in params.tensors()]
+    for cam in cams:
+        p1, params1, rgb1, disp1, T1 = _run_forward(gs, scene, [cam])
+        n = cam.width * cam.height
+        np.testing.assert_array_equal(to_np(rgb1), to_np(rgb[3 * off: 3 * off + 3 * n]))
+        np.testing.assert_array_equal(to_np(T1), to_np(T[off: off + n]))
+        gr1 = params1.zeros_like()
+        api.gs_render_bwd(p1, params1, [cam], BG, rgb1, disp1, g_all[3 * off: 3 * off + 3 * n].contiguous(),
+                          None, gr1)
+        for a, b in zip(acc, gr1.tensors()):
+            a += b
+        off += n
+    for a, b in zip(acc, grads.tensors()):
+        assert grad_mismatch(to_np(b), to_np(a).astype(np.float64), rtol=1e-5).sum() == 0
+
+
+# ------------------------------------------------------------ edge cases
+
+def test_all_culled_scene_renders_background(gs):
+    from paper_2601_19489_gb300 import api
+
+    scene = synth.scene_c1(2, n=100)
+    scene.means[:, 2] = -3.0  # behind the camera
+    cam = synth.camera_c1()
+    plan, params, rgb, disp, T = _run_forward(gs, scene, [cam])
+    assert plan.status()["n_instances"] == 0
+    img = view_image(rgb, 256, 256)
+    for ch in range(3):
+        assert np.all(img[ch] == np.float32(BG[ch]))
+    assert np.all(to_np(T) == 1.0) and np.all(to_np(disp) == 0.0)
+    grads = params.zeros_like()
+    api.gs_render_bwd(plan, params, [cam], BG, rgb, disp, torch.ones_like(rgb), None, grads)
+    assert all(float(t.abs().max()) == 0.0 for t in grads.tensors())
+
+
+def test_capacity_overflow_is_reported_not_written_past(gs):
+    from paper_2601_19489_gb300 import _lib as L
+    from paper_2601_19489_gb300 import api
+
+    scene, cam = synth.scene_c1(0), synth.camera_c1()
+    plan = api.Plan(scene.n, 0, [(256, 256)], 1000)
+    params = api.Gaussians.from_scene(scene)
+    api.gs_preprocess(plan, params, [cam])
+    api.gs_bin_sort(plan)
+    P = plan.pixels
+    rgb, disp, T = (torch.empty(k * P, device="cuda") for k in (3, 1, 1))
+    api.gs_render_fwd(plan, BG, rgb, disp, T)
+    st = plan.status()
+    assert st["rc"] == L.GS_ERR_CAPACITY and st["overflow"] == 1 and st["n_instances"] > 1000
+    # the forward still ran on the truncated lists and produced finite values
+    assert torch.isfinite(rgb).all()
+
+
+def test_single_gaussian_and_nan_parameters_do_not_hang(gs):
+    from paper_2601_19489_gb300 import api
+
+    scene = synth.scene_c1(3, n=1)
+    scene.means[0] = [0.0, 0.0, 3.0]
+    cam = synth.camera_c1()
+    plan, params, rgb, disp, T = _run_forward(gs, scene, [cam])
+    assert plan.status()["n_instances"] >= 1
+    scene2 = synth.scene_c1(3, n=64)
+    scene2.means[5] = np.nan
+    scene2.log_scales[7] = np.nan
+    plan2, params2, rgb2, disp2, T2 = _run_forward(gs, scene2, [cam])
+    assert plan2.status()["rc"] == 0
