@@ -115,7 +115,9 @@ GS_API int64_t gs_plan_pixels(const gs_plan *plan);
  * by tests and tools.  `which` is one of GS_WS_*.  Returns GS_ERR_ARG for an
  * unknown id. */
 enum {
-    GS_WS_RECORDS = 0,    /* float4 x 3 per (view, Gaussian): projected record */
+    GS_WS_RECORDS = 0,    /* float4 x 3 per (view, Gaussian): {mx, my, A, B}, {C, log2 o, 1/z,
+                             mx_lo}, {r, g, b, my_lo}; (A, B, C) = conic * log2(e) / 2,
+                             mean2d = (mx + mx_lo, my + my_lo) */
     GS_WS_TILES_TOUCHED,  /* uint32 per (view, Gaussian) */
     GS_WS_RECTS,          /* uint16 x 4 per (view, Gaussian): candidate tile box */
     GS_WS_DEPTH_ORDER,    /* uint32 per rank: item id v*n + g in ascending depth */
@@ -125,6 +127,7 @@ enum {
     GS_WS_N_CONTRIB,      /* uint32 per pixel: list position of last blended splat + 1 */
     GS_WS_GRAD2D,         /* float x 12 per (view, Gaussian): 2D gradients */
     GS_WS_STATUS,         /* status words */
+    GS_WS_BIN,            /* float2 per (view, Gaussian): binning level set, A C - B^2 */
     GS_WS_COUNT
 };
 GS_API int gs_workspace_view(const gs_plan *plan, void *ws, int which, void **d_ptr, size_t *bytes);

@@ -30,9 +30,17 @@
  *
  * Ambiguity flags: a pixel is flagged when a float32 evaluation of the same
  * definition could take another branch: some candidate has alpha within a
- * relative band of the 1/255 cut, the clamp switches within a band of 0.99,
- * the stop test T (1 - alpha) is within a band of 1e-4, or two blended
- * candidates have depths within a relative band (their order could flip).
+ * band of the 1/255 cut, the clamp switches within a band of 0.99, the stop
+ * test T (1 - alpha) is within a band of 1e-4, or two blended candidates have
+ * depths within a relative band (their order could flip).  The alpha and
+ * clamp bands are a relative part plus the change of ln(alpha) that a shift
+ * of the projected mean by pos_abs pixels causes (|d power / d mean| pos_abs);
+ * the stop band adds the same shifts, propagated through T.  A pixel is also
+ * flagged when its value is ill-conditioned: when relative errors of cond_eps
+ * in every blended alpha could move a colour channel, D or T by more than half
+ * of the per-pixel tolerance 1e-4 |v| + 1e-7 (first-order bound
+ * sum_k alpha_k |dv/dalpha_k| cond_eps, where a long chain of high-alpha
+ * splats amplifies the error of T through the factors 1 / (1 - alpha)).
  */
 #include <math.h>
 #include <stdint.h>
@@ -57,6 +65,8 @@ typedef struct {
     double clamp_rel;  /* band around the 0.99 clamp, relative */
     double tstop_rel;  /* band around the 1e-4 stop, relative */
     double depth_rel;  /* relative depth gap under which order may flip */
+    double pos_abs;    /* absolute uncertainty of a float32 mean2d, pixels */
+    double cond_eps;   /* relative float32 error of each alpha (conditioning flag) */
 } orc_amb;
 
 typedef struct {
@@ -166,35 +176,98 @@ int64_t orc_render_fwd(int64_t n, const double *proj, const double *bg,
     int64_t npix = (int64_t)w * h;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel
+#endif
+    {
+    int64_t cap = 64;
+    int64_t *blist = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    double *bal = (double *)malloc(sizeof(double) * (size_t)cap);
+    double *bT = (double *)malloc(sizeof(double) * (size_t)cap);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
 #endif
     for (int64_t p = 0; p < npix; ++p) {
         double px = (double)(x0 + p % w) + 0.5, py = (double)(y0 + p / w) + 0.5;
-        double T = 1.0, C[3] = {0.0, 0.0, 0.0}, D = 0.0, prev_z = -1.0;
+        double T = 1.0, C[3] = {0.0, 0.0, 0.0}, D = 0.0, prev_z = -1.0, t_sens = 0.0;
+        int64_t ncand = L.start[p + 1] - L.start[p];
+        if (ncand > cap) {
+            cap = ncand;
+            blist = (int64_t *)realloc(blist, sizeof(int64_t) * (size_t)cap);
+            bal = (double *)realloc(bal, sizeof(double) * (size_t)cap);
+            bT = (double *)realloc(bT, sizeof(double) * (size_t)cap);
+        }
         int32_t count = 0;
         uint8_t flag = 0;
         for (int64_t k = L.start[p]; k < L.start[p + 1]; ++k) {
             const double *g = proj + L.ids[k] * ORC_STRIDE;
             orc_pair e;
             orc_eval(g, px, py, &e);
+            double shift = 0.0;
             if (amb) {
-                if (fabs(e.raw * 255.0 - 1.0) < amb->alpha_rel) flag = 1;
-                if (fabs(e.raw / ORC_ALPHA_MAX - 1.0) < amb->clamp_rel) flag = 1;
+                /* |d ln alpha| for a mean2d shift of pos_abs in x and y */
+                shift = amb->pos_abs * (fabs(g[ORC_A] * e.dx + g[ORC_B] * e.dy) +
+                                        fabs(g[ORC_B] * e.dx + g[ORC_C] * e.dy));
+                if (fabs(log(e.raw * 255.0)) < amb->alpha_rel + shift) flag = 1;
+                if (fabs(log(e.raw / ORC_ALPHA_MAX)) < amb->clamp_rel + shift) flag = 1;
+            }
+            if (amb && e.raw * 255.0 >= 1.0 - 2.0 * (amb->alpha_rel + shift)) {
+                /* a candidate that blends (or nearly does) with a depth tie
+                 * against the previous such candidate: float32 may swap them */
+                if (prev_z > 0.0 && fabs(g[ORC_Z] - prev_z) < amb->depth_rel * g[ORC_Z]) flag = 1;
+                prev_z = g[ORC_Z];
             }
             if (e.power > 0.0) continue;
             if (e.alpha < ORC_ALPHA_MIN) continue;
             double test_T = T * (1.0 - e.alpha);
-            if (amb && fabs(test_T / ORC_T_STOP - 1.0) < amb->tstop_rel) flag = 1;
-            if (test_T < ORC_T_STOP) break;
-            if (amb && prev_z > 0.0 && fabs(g[ORC_Z] - prev_z) < amb->depth_rel * g[ORC_Z]) flag = 1;
-            prev_z = g[ORC_Z];
+            if (amb) {
+                double s_here = t_sens + (e.clamped ? 0.0 : e.alpha / (1.0 - e.alpha) * shift);
+                if (fabs(log(test_T / ORC_T_STOP)) < amb->tstop_rel + s_here) flag = 1;
+                t_sens = s_here;
+            }
+            if (test_T < ORC_T_STOP) {
+                /* the candidate right after the stopping one could take its
+                 * place under a depth tie */
+                for (int64_t k2 = k + 1; amb && k2 < L.start[p + 1]; ++k2) {
+                    const double *g2 = proj + L.ids[k2] * ORC_STRIDE;
+                    orc_pair e2;
+                    orc_eval(g2, px, py, &e2);
+                    if (e2.raw * 255.0 < 1.0 - 2.0 * amb->alpha_rel) continue;
+                    if (fabs(g2[ORC_Z] - g[ORC_Z]) < amb->depth_rel * g2[ORC_Z]) flag = 1;
+                    break;
+                }
+                break;
+            }
             double wgt = e.alpha * T;
             C[0] += g[ORC_R] * wgt;
             C[1] += g[ORC_G] * wgt;
             C[2] += g[ORC_BL] * wgt;
             D += wgt / g[ORC_Z];
+            blist[count] = e.clamped ? -1 - L.ids[k] : L.ids[k];
+            bal[count] = e.alpha;
+            bT[count] = T;
             T = test_T;
             ++count;
+        }
+        if (amb && amb->cond_eps > 0.0 && !flag) {
+            /* first-order sensitivity of C (3), D and T to relative alpha errors */
+            double behind[4] = {T * bg[0], T * bg[1], T * bg[2], 0.0};
+            double sens[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            double sumT = 0.0;
+            for (int32_t j = count - 1; j >= 0; --j) {
+                int64_t id = blist[j] < 0 ? -1 - blist[j] : blist[j];
+                const double *g = proj + id * ORC_STRIDE;
+                double vals[4] = {g[ORC_R], g[ORC_G], g[ORC_BL], 1.0 / g[ORC_Z]};
+                double a = bal[j], Tj = bT[j];
+                for (int c = 0; c < 4; ++c) {
+                    if (blist[j] >= 0) sens[c] += a * fabs(vals[c] * Tj - behind[c] / (1.0 - a));
+                    behind[c] += vals[c] * a * Tj;
+                }
+                if (blist[j] >= 0) sumT += a / (1.0 - a);
+            }
+            sens[4] = T * sumT;
+            double v[5] = {C[0] + T * bg[0], C[1] + T * bg[1], C[2] + T * bg[2], D, T};
+            for (int c = 0; c < 5; ++c)
+                if (sens[c] * amb->cond_eps > 0.5 * (1e-4 * fabs(v[c]) + 1e-7)) flag = 1;
         }
         if (out_rgb) {
             out_rgb[p] = C[0] + T * bg[0];
@@ -205,6 +278,10 @@ int64_t orc_render_fwd(int64_t n, const double *proj, const double *bg,
         if (out_T) out_T[p] = T;
         if (out_count) out_count[p] = count;
         if (out_amb) out_amb[p] = flag;
+    }
+    free(blist);
+    free(bal);
+    free(bT);
     }
     int64_t total = L.start[npix];
     orc_free_lists(&L);

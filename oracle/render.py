@@ -25,10 +25,26 @@ G2D = 10
 class Amb(ctypes.Structure):
     """Relative bands inside which a float32 evaluation may branch differently."""
     _fields_ = [("alpha_rel", ctypes.c_double), ("clamp_rel", ctypes.c_double),
-                ("tstop_rel", ctypes.c_double), ("depth_rel", ctypes.c_double)]
+                ("tstop_rel", ctypes.c_double), ("depth_rel", ctypes.c_double),
+                ("pos_abs", ctypes.c_double), ("cond_eps", ctypes.c_double)]
 
 
-DEFAULT_AMB = (2e-5, 2e-5, 2e-4, 2e-6)
+# relative bands for alpha, clamp and stop; depth band (one float32 ulp, two
+# sided); no position uncertainty and no conditioning flag (set both with
+# float32_bands for an image)
+DEFAULT_AMB = (2e-5, 2e-5, 2e-5, 2.4e-7, 0.0, 0.0)
+
+
+def float32_bands(width: int, height: int, rel: float = 2e-5, ulps: float = 1.0,
+                  cond_eps: float = 3e-6):
+    """Bands for comparing with a float32 evaluation on a width x height image:
+    the projected mean is uncertain by `ulps` float32 ulps of the largest
+    pixel coordinate, and every alpha by a relative cond_eps."""
+    import math
+
+    top = max(int(width), int(height), 1)
+    ulp = 2.0 ** (math.floor(math.log2(top)) - 23)
+    return (rel, rel, rel, 2.4e-7, ulps * ulp, cond_eps)
 
 
 def build(force: bool = False) -> str:
@@ -82,6 +98,8 @@ def render_fwd(proj: np.ndarray, bg, window, amb=DEFAULT_AMB, n_threads: int = 0
     T = np.zeros((h, w))
     count = np.zeros((h, w), dtype=np.int32)
     flags = np.zeros((h, w), dtype=np.uint8)
+    if amb is not None and len(amb) < 6:
+        amb = tuple(amb) + (0.0,) * (6 - len(amb))
     a = Amb(*amb) if amb is not None else None
     total = lib.orc_render_fwd(proj.shape[0], _ptr(proj), _ptr(bg), x0, y0, x1, y1,
                                ctypes.cast(ctypes.pointer(a), ctypes.c_void_p) if a else None,

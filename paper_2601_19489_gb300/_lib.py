@@ -21,7 +21,7 @@ GS_BUCKET = 32
 GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_INTERNAL = 0, -1, -2, -3, -4, -5
 
 (GS_WS_RECORDS, GS_WS_TILES_TOUCHED, GS_WS_RECTS, GS_WS_DEPTH_ORDER, GS_WS_INST_TILE,
- GS_WS_INST_GID, GS_WS_TILE_RANGES, GS_WS_N_CONTRIB, GS_WS_GRAD2D, GS_WS_STATUS) = range(10)
+ GS_WS_INST_GID, GS_WS_TILE_RANGES, GS_WS_N_CONTRIB, GS_WS_GRAD2D, GS_WS_STATUS, GS_WS_BIN) = range(11)
 
 EXPORTS = (
     "gs_plan_create", "gs_plan_destroy", "gs_plan_workspace_bytes", "gs_plan_pixels",

@@ -99,6 +99,7 @@ template <bool kLB>
 __global__ void __launch_bounds__(kScanThreads)
 k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ order,
              const uint32_t *__restrict__ touched, const float4 *__restrict__ rec,
+             const float2 *__restrict__ bin,
              const uint2 *__restrict__ rects, const unsigned long long *__restrict__ block_offs, int64_t n,
              int64_t capacity, uint32_t *__restrict__ inst_tile, uint32_t *__restrict__ inst_item,
              StatusDev *st) {
@@ -124,18 +125,20 @@ k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ or
             if (cnt == 0) continue;
             const int v = (int)(item / (uint32_t)n_per_view);
             const ViewDev &cam = views.v[v];
-            const float4 r0v = rec[3 * (size_t)item], r1v = rec[3 * (size_t)item + 1];
-            const float detc = rec[3 * (size_t)item + 2].w;
+            const float4 r0v = rec[3 * (size_t)item];
+            const float Cc = rec[3 * (size_t)item + 1].x;
+            const float2 bv = bin[item];
+            const float tb = bv.x, detc = bv.y;
             int tx0, ty0, tx1, ty1;
             unpack_rect(rects[item], &tx0, &ty0, &tx1, &ty1);
             float rx, ry;
-            ellipse_extent(r0v.z, r1v.x, detc, r1v.w, &rx, &ry);
+            ellipse_extent(r0v.z, Cc, detc, tb, &rx, &ry);
             uint32_t w = 0;
             for (int tx = tx0; tx < tx1; ++tx) {
                 float xa, xb;
                 column_span(tx, (float)cam.W, &xa, &xb);
                 int lo, hi;
-                if (!column_rows(r0v.x, r0v.y, r0v.z, r0v.w, r1v.x, detc, r1v.w, rx, ry, xa, xb,
+                if (!column_rows(r0v.x, r0v.y, r0v.z, r0v.w, Cc, detc, tb, rx, ry, xa, xb,
                                  (float)cam.H, ty0, ty1, &lo, &hi))
                     continue;
                 for (int ty = lo; ty <= hi; ++ty, ++w) {
@@ -172,12 +175,14 @@ k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ or
                 const unsigned long long o0 = s_off[slot];
                 const int v = (int)(it / (uint32_t)n_per_view);
                 const ViewDev &cam = views.v[v];
-                const float4 r0v = rec[3 * (size_t)it], r1v = rec[3 * (size_t)it + 1];
-                const float detc = rec[3 * (size_t)it + 2].w;
+                const float4 r0v = rec[3 * (size_t)it];
+                const float Cc = rec[3 * (size_t)it + 1].x;
+                const float2 bv = bin[it];
+                const float tb = bv.x, detc = bv.y;
                 int tx0, ty0, tx1, ty1;
                 unpack_rect(rects[it], &tx0, &ty0, &tx1, &ty1);
                 float rx, ry;
-                ellipse_extent(r0v.z, r1v.x, detc, r1v.w, &rx, &ry);
+                ellipse_extent(r0v.z, Cc, detc, tb, &rx, &ry);
                 const int wdt = tx1 - tx0;
                 const int cand = wdt * (ty1 - ty0);
                 uint32_t written = 0;
@@ -191,7 +196,7 @@ k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ or
                         float xa, xb;
                         column_span(tx, (float)cam.W, &xa, &xb);
                         int lo, hi;
-                        if (column_rows(r0v.x, r0v.y, r0v.z, r0v.w, r1v.x, detc, r1v.w, rx, ry, xa, xb,
+                        if (column_rows(r0v.x, r0v.y, r0v.z, r0v.w, Cc, detc, tb, rx, ry, xa, xb,
                                         (float)cam.H, ty0, ty1, &lo, &hi))
                             hit = ty >= lo && ty <= hi;
                     }
@@ -311,11 +316,13 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
     uint32_t *ik1 = ws_at<uint32_t>(ws, plan->o_ikey[1]), *iv1 = ws_at<uint32_t>(ws, plan->o_ival[1]);
     if (load_balanced)
         k_write_keys<true><<<kSortBlocks, kScanThreads, 0, s>>>(
-            vd, plan->n, order, touched, ws_at<float4>(ws, plan->o_rec), ws_at<uint2>(ws, plan->o_rect),
+            vd, plan->n, order, touched, ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin),
+            ws_at<uint2>(ws, plan->o_rect),
             block_offs, VN, plan->inst_cap, ik0, iv0, st);
     else
         k_write_keys<false><<<kSortBlocks, kScanThreads, 0, s>>>(
-            vd, plan->n, order, touched, ws_at<float4>(ws, plan->o_rec), ws_at<uint2>(ws, plan->o_rect),
+            vd, plan->n, order, touched, ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin),
+            ws_at<uint2>(ws, plan->o_rect),
             block_offs, VN, plan->inst_cap, ik0, iv0, st);
     rc = launch_error();
     if (rc) return rc;

@@ -81,7 +81,7 @@ struct gs_plan {
     // offsets
     size_t o_status, o_rec, o_touched, o_rect, o_dkey[2], o_dval[2];
     size_t o_ikey[2], o_ival[2], o_ranges, o_tile_maxc, o_bucket_off, o_ncontrib;
-    size_t o_ckpt, o_grad2d, o_sort_scratch, o_block_sums;
+    size_t o_ckpt, o_grad2d, o_sort_scratch, o_block_sums, o_bin;
     size_t sort_scratch_bytes;
     size_t bytes;
     int inst_final;   // which ping-pong buffer holds the sorted instances
@@ -189,7 +189,9 @@ __device__ __forceinline__ void column_span(int tx, float img_w, float *xa, floa
 // ----------------------------------------------------------------------------
 // Alpha of one (splat, pixel) pair, shared by the forward blend and the
 // backward so both take identical float32 decisions.
-//   r0 = (mx, my, A, B), r1 = (C, log2 o, 1/z, level)   (A, B, C = kH * conic)
+//   r0 = (mx, my, A, B), r1 = (C, log2 o, ...)   (A, B, C = kH * conic)
+// with (mx, my) and (px, py) in tile-local pixel coordinates (see
+// tile_local_mean), so dx, dy carry no rounding of large image coordinates.
 // power2 = -(A dx^2 + 2 B dx dy + C dy^2) is the exponent in base 2; the pair
 // is skipped when power2 > 0 (never for a positive-definite conic) and
 // alpha = min(0.99, 2^(power2 + log2 o)).
@@ -199,6 +201,13 @@ __device__ __forceinline__ float fast_exp2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Tile-local mean: (hi - x0) + lo from the record's compensated mean
+// (r0.xy = high parts, r1.w / r2.w = low parts) and the tile origin x0, y0.
+__device__ __forceinline__ float2 tile_local_mean(const float4 &r0, float mx_lo, float my_lo, float x0,
+                                                  float y0) {
+    return make_float2(__fadd_rn(__fsub_rn(r0.x, x0), mx_lo), __fadd_rn(__fsub_rn(r0.y, y0), my_lo));
 }
 
 struct PairEval {

@@ -109,6 +109,7 @@ extern "C" gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views
     p->o_rec = take(VN * 3 * sizeof(float4));
     p->o_touched = take(VN * sizeof(uint32_t));
     p->o_rect = take(VN * sizeof(uint2));
+    p->o_bin = take(VN * sizeof(float2));
     for (int b = 0; b < 2; ++b) {
         p->o_dkey[b] = take(VN * sizeof(uint32_t));
         p->o_dval[b] = take(VN * sizeof(uint32_t));
@@ -154,6 +155,7 @@ extern "C" int gs_workspace_view(const gs_plan *p, void *ws, int which, void **p
         case GS_WS_N_CONTRIB: off = p->o_ncontrib; nb = (size_t)p->total_pixels * 4; break;
         case GS_WS_GRAD2D: off = p->o_grad2d; nb = VN * 3 * sizeof(float4); break;
         case GS_WS_STATUS: off = p->o_status; nb = sizeof(StatusDev); break;
+        case GS_WS_BIN: off = p->o_bin; nb = VN * sizeof(float2); break;
         default: return GS_ERR_ARG;
     }
     *ptr = (char *)ws + off;

@@ -12,8 +12,9 @@
 //   colour = max(0, sum_k sh_k Y_k(d) + 0.5), d = (p - camera centre)/|.|
 //   SnugBox of the widened level set and the exact per-column tile count.
 // The record written for the blend is r0 = (mx, my, A, B), r1 = (C, log2 o,
-// 1/z, tb), r2 = (r, g, b, detc) with (A, B, C) = kH * conic, tb = kH * t_bin
-// and detc = A C - B^2 = kH^2 / det(Sigma').
+// 1/z, mx_lo), r2 = (r, g, b, my_lo) with (A, B, C) = kH * conic and the
+// projected mean as the float-float (mx + mx_lo, my + my_lo); binning also
+// reads (tb, detc) with tb = kH * t_bin and detc = A C - B^2 = kH^2 / det(Sigma').
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -82,6 +83,57 @@ __device__ __forceinline__ void sh_grad(float x, float y, float z, float3 *G) {
         G[14] = make_float3(2.0f * kSH3e * x * z, -2.0f * kSH3e * y * z, kSH3e * (x * x - y * y));
         G[15] = make_float3(-3.0f * kSH3a * (x * x - y * y), 6.0f * kSH3a * x * y, 0.f);
     }
+}
+
+// Float-float ("double-float") helpers for the few per-Gaussian quantities
+// whose rounding decides pixel-level branches: the camera depth that orders
+// the blend and the projected mean.  Error-free transforms (Knuth's TwoSum,
+// the FMA TwoProduct) and a compensated dot product (Ogita, Rump, Oishi,
+// "Accurate sum and dot product", 2005) give results within about half an
+// ulp of the exact value of the float32 inputs.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ FF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// r . p + t, compensated
+__device__ __forceinline__ FF dot3_plus(const float *r, float3 p, float t) {
+    FF acc = two_prod(r[0], p.x);
+    FF q = two_prod(r[1], p.y);
+    FF s = two_sum(acc.hi, q.hi);
+    float lo = __fadd_rn(__fadd_rn(acc.lo, q.lo), s.lo);
+    q = two_prod(r[2], p.z);
+    FF s2 = two_sum(s.hi, q.hi);
+    lo = __fadd_rn(__fadd_rn(lo, q.lo), s2.lo);
+    FF s3 = two_sum(s2.hi, t);
+    lo = __fadd_rn(lo, s3.lo);
+    return two_sum(s3.hi, lo);
+}
+
+// (x.hi + x.lo) / (z.hi + z.lo)
+__device__ __forceinline__ FF div_ff(FF x, FF z) {
+    const float q = __fdiv_rn(x.hi, z.hi);
+    float r = __fmaf_rn(-q, z.hi, x.hi);
+    r = __fadd_rn(r, __fsub_rn(x.lo, __fmul_rn(q, z.lo)));
+    return two_sum(q, __fdiv_rn(r, z.hi));
+}
+
+// f * u + c as a normalised float-float
+__device__ __forceinline__ FF affine_ff(float f, FF u, float c) {
+    const FF p = two_prod(f, u.hi);
+    const FF s = two_sum(p.hi, c);
+    return two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, p.lo), __fmul_rn(f, u.lo)));
 }
 
 __device__ __forceinline__ float3 f3(const float *p) { return make_float3(p[0], p[1], p[2]); }
@@ -154,8 +206,8 @@ __global__ void __launch_bounds__(256)
 k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
              const float *__restrict__ log_scales, const float4 *__restrict__ quats,
              const float *__restrict__ logits, const float *__restrict__ sh, float4 *__restrict__ rec,
-             uint32_t *__restrict__ touched, uint2 *__restrict__ rects, uint32_t *__restrict__ dkey,
-             uint32_t *__restrict__ dval) {
+             float2 *__restrict__ bin, uint32_t *__restrict__ touched, uint2 *__restrict__ rects,
+             uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval) {
     constexpr int K = (D + 1) * (D + 1);
     const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= (int64_t)views.V * n) return;
@@ -165,7 +217,11 @@ k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
     dval[item] = (uint32_t)item;
 
     const float3 p = make_float3(means[3 * g], means[3 * g + 1], means[3 * g + 2]);
-    const float pz = cam.R[6] * p.x + cam.R[7] * p.y + cam.R[8] * p.z + cam.t[2];
+    // The depth that orders the blend is compensated, so the float32 key is
+    // the camera depth rounded once: two Gaussians can only leave exact depth
+    // order when their depths round to the same float (ties go by index).
+    const FF zf = dot3_plus(cam.R + 6, p, cam.t[2]);
+    const float pz = zf.hi;
     if (!(pz > cam.near_z)) {
         touched[item] = 0;
         rects[item] = make_uint2(0, 0);
@@ -175,8 +231,12 @@ k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
     Proj P;
     project_cov(cam, p, quats[g], make_float3(log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2]), P);
     const float a = P.Syy / P.det, b = -P.Sxy / P.det, c = P.Sxx / P.det;
-    const float mx = cam.fx * P.pc.x * P.iz + cam.cx;
-    const float my = cam.fy * P.pc.y * P.iz + cam.cy;
+    // projected mean, compensated (rounded once from the exact projection of
+    // the float32 mean), so pixel-level decisions do not inherit the rounding
+    // of the camera transform at large pixel coordinates
+    const FF mxf = affine_ff(cam.fx, div_ff(dot3_plus(cam.R, p, cam.t[0]), zf), cam.cx);
+    const FF myf = affine_ff(cam.fy, div_ff(dot3_plus(cam.R + 3, p, cam.t[1]), zf), cam.cy);
+    const float mx = mxf.hi, my = myf.hi;
     const float o = 1.0f / (1.0f + expf(-logits[g]));
     const float t = 2.0f * logf(255.0f * o);
     const float A = kH * a, B = kH * b, C = kH * c;
@@ -201,8 +261,9 @@ k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
     bb = fmaxf(bb, 0.f);
 
     rec[3 * item + 0] = make_float4(mx, my, A, B);
-    rec[3 * item + 1] = make_float4(C, log2f(o), P.iz, tb);
-    rec[3 * item + 2] = make_float4(r, gg, bb, detc);
+    rec[3 * item + 1] = make_float4(C, log2f(o), P.iz, mxf.lo);
+    rec[3 * item + 2] = make_float4(r, gg, bb, myf.lo);
+    bin[item] = make_float2(tb, detc);
 
     uint32_t count = 0;
     int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
@@ -222,7 +283,7 @@ k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
     if (count == 0) tx0 = ty0 = tx1 = ty1 = 0;
     touched[item] = count;
     rects[item] = pack_rect(tx0, ty0, tx1, ty1);
-    dkey[item] = count ? __float_as_uint(P.pc.z) : 0xffffffffu;
+    dkey[item] = count ? __float_as_uint(pz) : 0xffffffffu;
 }
 
 // a8: one thread per Gaussian, summing over the views where it touched tiles.
@@ -292,15 +353,21 @@ k_preprocess_bwd(ViewsDev views, int64_t n, const float *__restrict__ means,
             // d = dv / |dv|:  d(dv) = (ddir - d (d . ddir)) / |dv|
             dp = add3(dp, mul3(sub3(ddir, mul3(dir, dot3(dir, ddir))), inv_len));
         }
-        // ---- conic (a, b, c) = (Syy, -Sxy, Sxx) / det  ->  Sigma' entries
-        const float det2 = P.det * P.det;
-        const float dA = (-ga.z * P.Syy * P.Syy + ga.w * P.Sxy * P.Syy - gb.x * P.Sxy * P.Sxy) / det2;
-        const float dB = (2.f * ga.z * P.Sxy * P.Syy - ga.w * (P.Sxx * P.Syy + P.Sxy * P.Sxy) +
-                          2.f * gb.x * P.Sxx * P.Sxy) / det2;
-        const float dC = (-ga.z * P.Sxy * P.Sxy + ga.w * P.Sxx * P.Sxy - gb.x * P.Sxx * P.Sxx) / det2;
-        // ---- Sigma' = U U^T + 0.3 I
-        const float3 dU0 = add3(mul3(P.U0, 2.f * dA), mul3(P.U1, dB));
-        const float3 dU1 = add3(mul3(P.U1, 2.f * dC), mul3(P.U0, dB));
+        // ---- conic Q = Sigma'^-1 with Sigma' = U U^T + 0.3 I:
+        //   dL/dSigma' = -Q G Q  (G: gradient w.r.t. the symmetric conic matrix,
+        //   off-diagonal gb / 2), so dL/dU = 2 dL/dSigma' U = -2 Q G (Q U).
+        // Forming W = Q U first keeps a long axis's column small instead of
+        // cancelling large entries of dL/dSigma' against it (needle-like
+        // Gaussians would otherwise lose most float32 digits).
+        const float inv_det = 1.0f / P.det;
+        const float qa = P.Syy * inv_det, qb = -P.Sxy * inv_det, qc = P.Sxx * inv_det;
+        const float3 W0 = add3(mul3(P.U0, qa), mul3(P.U1, qb));
+        const float3 W1 = add3(mul3(P.U0, qb), mul3(P.U1, qc));
+        const float hb = 0.5f * ga.w;
+        const float3 GW0 = add3(mul3(W0, ga.z), mul3(W1, hb));
+        const float3 GW1 = add3(mul3(W0, hb), mul3(W1, gb.x));
+        const float3 dU0 = mul3(add3(mul3(GW0, qa), mul3(GW1, qb)), -2.f);
+        const float3 dU1 = mul3(add3(mul3(GW0, qb), mul3(GW1, qc)), -2.f);
         // ---- U = T M, M = Rg diag(s):  dT_k = sum_j dU_j Rg[k][j] s_j;  dM[k][j] = T_k dU_j
         const float du0[3] = {dU0.x, dU0.y, dU0.z}, du1[3] = {dU1.x, dU1.y, dU1.z};
         const float t0[3] = {P.T0.x, P.T0.y, P.T0.z}, t1[3] = {P.T1.x, P.T1.y, P.T1.z};
@@ -379,8 +446,8 @@ static void launch_preprocess(const gs_plan *plan, void *ws, const gs_params *pr
     const unsigned blocks = (unsigned)((total + 255) / 256);
     k_preprocess<D><<<blocks, 256, 0, s>>>(
         vd, plan->n, pr->means, pr->log_scales, (const float4 *)pr->quats, pr->opacity_logits, pr->sh,
-        ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_touched), ws_at<uint2>(ws, plan->o_rect),
-        ws_at<uint32_t>(ws, plan->o_dkey[0]), ws_at<uint32_t>(ws, plan->o_dval[0]));
+        ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin), ws_at<uint32_t>(ws, plan->o_touched),
+        ws_at<uint2>(ws, plan->o_rect), ws_at<uint32_t>(ws, plan->o_dkey[0]), ws_at<uint32_t>(ws, plan->o_dval[0]));
 }
 
 template <int D>

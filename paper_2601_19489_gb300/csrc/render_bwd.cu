@@ -110,12 +110,15 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
             r0 = rec[3 * (size_t)item];
             r1 = rec[3 * (size_t)item + 1];
             r2 = rec[3 * (size_t)item + 2];
+            // the same tile-local mean the forward staged
+            const float2 m = tile_local_mean(r0, r1.w, r2.w, (float)(tx * kTile), (float)(ty * kTile));
+            r0.x = m.x;
+            r0.y = m.y;
         }
         const uint32_t k = j0 + (uint32_t)lane;
         float g_mx = 0.f, g_my = 0.f, g_xx = 0.f, g_xy = 0.f, g_yy = 0.f, g_pw = 0.f;
         float g_r = 0.f, g_g = 0.f, g_b = 0.f, g_iz = 0.f;
         float T_out = 0.f, S_out = 0.f;
-        const float fx0 = (float)(tx * kTile) + 0.5f, fy0 = (float)(ty * kTile) + 0.5f;
 
         for (int s = 0; s < m_total + 31; ++s) {
             float T_in = __shfl_up_sync(0xffffffffu, T_out, 1);
@@ -132,7 +135,7 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
                 const float2 fin = S.fin[m];
                 if (k < __float_as_uint(fin.y)) {
                     const int p = S.pix[m];
-                    const float px = fx0 + (float)(p & (kTile - 1)), py = fy0 + (float)(p >> 4);
+                    const float px = (float)(p & (kTile - 1)) + 0.5f, py = (float)(p >> 4) + 0.5f;
                     PairEval e;
                     eval_pair(r0, r1, px, py, e);
                     if (e.power2 <= 0.0f && e.alpha >= kAlphaMin) {

@@ -4,7 +4,9 @@
 // One CTA of 256 threads per 16x16 tile, one pixel per thread.  The tile's
 // depth-sorted instance list is staged in shared memory in batches of 256
 // records (each thread gathers one record, 48 bytes, from the per-Gaussian
-// record buffer, which stays L2-resident).  Each pixel blends front to back
+// record buffer, which stays L2-resident), with the projected mean moved to
+// tile-local coordinates once per splat so the per-pair offsets are exact
+// to float32 at any image size.  Each pixel blends front to back
 // until its transmittance would fall below 1e-4; a warp whose pixels are all
 // done skips the rest of the batch and the CTA leaves when all 256 are done.
 // Before list positions 0, 32, 64, ... every pixel still running stores its
@@ -39,7 +41,9 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
     const int tid = threadIdx.x;
     const int ix = tx * kTile + (tid & (kTile - 1)), iy = ty * kTile + (tid >> 4);
     const bool inside = ix < cam.W && iy < cam.H;
-    const float px = (float)ix + 0.5f, py = (float)iy + 0.5f;
+    // tile-local pixel centre; the staged means are tile-local too
+    const float px = (float)(tid & (kTile - 1)) + 0.5f, py = (float)(tid >> 4) + 0.5f;
+    const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
     const uint2 range = ranges[t];
     const int n = (int)(range.y - range.x);
     float *ck = ckpt + (size_t)bucket_off[t] * (kCkptCh * kTilePix) + tid;
@@ -52,9 +56,14 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
         if (__syncthreads_count(!done) == 0) break;  // also fences the previous batch
         if (b0 + tid < n) {
             const size_t it = inst_item[range.x + b0 + tid];
-            s_r0[tid] = rec[3 * it];
-            s_r1[tid] = rec[3 * it + 1];
-            s_r2[tid] = rec[3 * it + 2];
+            float4 r0 = rec[3 * it];
+            const float4 r1 = rec[3 * it + 1], r2 = rec[3 * it + 2];
+            const float2 m = tile_local_mean(r0, r1.w, r2.w, x0, y0);
+            r0.x = m.x;
+            r0.y = m.y;
+            s_r0[tid] = r0;
+            s_r1[tid] = r1;
+            s_r2[tid] = r2;
         }
         __syncthreads();
         const int cnt = min(kTilePix, n - b0);

@@ -3,8 +3,13 @@ C ABI on seeded inputs, and the comparison rules.
 
 Tolerances (stated by the method's float32 precision target):
   per pixel     |gpu - ref| <= 1e-4 |ref| + 1e-7   on pixels the oracle does
-                not flag as threshold-ambiguous
-  per gradient  |gpu - ref| <= 1e-3 max(|ref|, 1e-3 max|ref|)  per array
+                not flag as threshold-ambiguous or ill-conditioned
+  per gradient  |gpu - ref| <= 1e-3 max(|ref|, 1e-3 max|ref|), elementwise
+                over each gradient array (the ten per-Gaussian 2D gradients
+                and the parameter gradients)
+  block_mismatch  the normwise variant per Gaussian block (max over a
+                Gaussian's entries of one parameter), used where the same sums
+                are compared in two association orders
 """
 from __future__ import annotations
 
@@ -29,6 +34,15 @@ def grad_mismatch(gpu: np.ndarray, ref: np.ndarray, rtol: float = GRAD_RTOL):
     scale = max(np.abs(ref).max(), 1e-30)
     tol = rtol * np.maximum(np.abs(ref), 1e-3 * scale)
     return np.abs(gpu - ref) > tol
+
+
+def block_mismatch(gpu: np.ndarray, ref: np.ndarray, rtol: float = GRAD_RTOL):
+    """Rows (one per Gaussian) whose normwise error exceeds the tolerance."""
+    g = np.asarray(gpu, dtype=np.float64).reshape(gpu.shape[0], -1)
+    r = np.asarray(ref, dtype=np.float64).reshape(ref.shape[0], -1)
+    top = max(np.abs(r).max(), 1e-30)
+    scale = np.maximum(np.abs(r).max(axis=1), 1e-3 * top)
+    return np.abs(g - r).max(axis=1) > rtol * scale
 
 
 def to_np(t: torch.Tensor) -> np.ndarray:

@@ -12,12 +12,13 @@ from oracle import binning as obin
 from oracle import loss as oloss
 from oracle import preprocess as opre
 from oracle import render as oren
-from tests.parity import grad_mismatch, pixel_mismatch, to_np, view_image
+from tests.parity import block_mismatch, grad_mismatch, pixel_mismatch, to_np, view_image
 
 pytestmark = pytest.mark.gpu
 
 BG = (0.3, 0.1, 0.6)
-AMB = (3e-5, 3e-5, 3e-5, 1e-6)
+def AMB_FOR(cam):
+    return oren.float32_bands(cam.width, cam.height)
 
 
 def _run_forward(gs, scene, cams, cap=1 << 22, lb=True):
@@ -141,7 +142,7 @@ def test_binning_lists_match_oracle_and_lb_equals_sq(gs):
         assert req.get(tid, set()) <= gs_set <= allow.get(tid, set()), tid
         # depth order, ties by index (float32 near-ties may swap)
         for a, b in zip(got[:-1], got[1:]):
-            if abs(z[a] - z[b]) > 1e-6 * z[a]:
+            if abs(z[a] - z[b]) > 2.4e-7 * z[a]:
                 assert (z[a], a) < (z[b], b), (tid, a, b)
 
 
@@ -156,9 +157,9 @@ def test_render_fwd_matches_oracle(gs, which):
         cam = synth.ring_cameras(4, 333, 187)[2]  # ragged: partial tiles on both edges
     plan, params, rgb, disp, T = _run_forward(gs, scene, [cam])
     _, orec = _oracle_records(scene, cam)
-    ref = oren.render_fwd(orec, BG, (0, 0, cam.width, cam.height), amb=AMB)
+    ref = oren.render_fwd(orec, BG, (0, 0, cam.width, cam.height), amb=AMB_FOR(cam))
     ok = ~ref["amb"]
-    assert ref["amb"].mean() < 2e-3, ref["amb"].mean()
+    assert ref["amb"].mean() < 5e-3, ref["amb"].mean()
     W, H = cam.width, cam.height
     g_rgb = view_image(rgb, W, H)
     g_disp = view_image(disp, W, H, channels=1)[0]
@@ -185,7 +186,7 @@ def test_render_bwd_matches_oracle(gs, which):
     W, H = cam.width, cam.height
     plan, params, rgb, disp, T = _run_forward(gs, scene, [cam])
     _, orec = _oracle_records(scene, cam)
-    ref = oren.render_fwd(orec, BG, (0, 0, W, H), amb=AMB)
+    ref = oren.render_fwd(orec, BG, (0, 0, W, H), amb=AMB_FOR(cam))
     g, gd = synth.upstream_grads(11, W, H)
     g[:, ref["amb"]] = 0.0
     gd[ref["amb"]] = 0.0
@@ -200,13 +201,16 @@ def test_render_bwd_matches_oracle(gs, which):
     names = ["mx", "my", "a", "b", "c", "o", "r", "g", "b", "invz"]
     for k in range(10):
         bad = grad_mismatch(gpu10[:, k], ref2d[:, k])
-        assert bad.sum() == 0, (names[k], bad.sum(), np.nonzero(bad)[0][:5])
+        idx = np.nonzero(bad)[0][:5]
+        assert bad.sum() == 0, (names[k], bad.sum(), idx, gpu10[idx, k], ref2d[idx, k],
+                                np.abs(ref2d[:, k]).max())
     # parameters: oracle preprocess backward of the oracle's 2D gradients
     ref_p = opre.preprocess_backward(scene, cam, ref2d)
     for name, t in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), grads.tensors()):
         got = to_np(t)
         bad = grad_mismatch(got, ref_p[name])
-        assert bad.sum() == 0, (name, bad.sum())
+        idx = np.nonzero(bad.reshape(bad.shape[0], -1).any(axis=1))[0][:3]
+        assert bad.sum() == 0, (name, bad.sum(), idx, got[idx], ref_p[name][idx])
 
 
 # ------------------------------------------------------------------ loss
@@ -324,7 +328,8 @@ def test_multiview_plan_equals_single_views(gs):
             a += b
         off += n
     for a, b in zip(acc, grads.tensors()):
-        assert grad_mismatch(to_np(b), to_np(a).astype(np.float64), rtol=1e-5).sum() == 0
+        # the same sums in another atomic order
+        assert block_mismatch(to_np(b), to_np(a), rtol=1e-4).sum() == 0
 
 
 # ------------------------------------------------------------ edge cases
