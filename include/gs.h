@@ -246,6 +246,33 @@ GS_API int gs_sort_pairs_u32(uint32_t *d_keys_in, uint32_t *d_vals_in, uint32_t 
                              uint32_t *d_vals_out, int64_t n, int32_t begin_bit, int32_t end_bit,
                              void *d_scratch, void *stream);
 
+/* The same sort for callers that cannot allocate device memory, such as code
+ * running inside a CUDA graph capture in global mode (where cudaMalloc is
+ * refused), plug-ins whose host framework owns all device memory through its
+ * own pool, or loops that cannot take cudaMalloc's implicit device
+ * synchronisation.  The paper has no counterpart to this entry point; it is a
+ * convenience of this library.
+ *
+ * The caller passes only the key and value buffers (same rules as
+ * gs_sort_pairs_u32).  The scratch lives in a static device array inside the
+ * library, 609 KiB per GPU that loads the library, held until the process
+ * exits.  n may not exceed GS_SORT_NOALLOC_MAX_N (2^31 - 1, the reach of the
+ * sort's 32-bit counters); larger n returns GS_ERR_ARG before any work is
+ * enqueued.  The call makes no allocation: no cudaMalloc, no cudaFree, no
+ * allocating library routine.
+ *
+ * The first call on each device looks up the array's device address with
+ * that device current (cudaGetSymbolAddress) and caches it; make that first
+ * call before any stream capture.  All calls on a device share the one
+ * array, which keeps the previous call's contents (every pass rewrites it in
+ * full, so nothing needs clearing): calls that may overlap on the GPU — on
+ * different streams without ordering between them — race on it and must be
+ * serialised by the caller. */
+#define GS_SORT_NOALLOC_MAX_N 2147483647LL
+GS_API int gs_sort_pairs_u32_noalloc(uint32_t *d_keys_in, uint32_t *d_vals_in, uint32_t *d_keys_out,
+                                     uint32_t *d_vals_out, int64_t n, int32_t begin_bit,
+                                     int32_t end_bit, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

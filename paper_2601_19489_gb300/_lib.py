@@ -28,7 +28,7 @@ EXPORTS = (
     "gs_workspace_view", "gs_read_status", "gs_error_string", "gs_preprocess", "gs_bin_sort",
     "gs_render_fwd", "gs_render_bwd", "gs_render_bwd_blend", "gs_preprocess_bwd",
     "gs_loss_scratch_floats", "gs_loss", "gs_adam_step",
-    "gs_adam_step_multi", "gs_sort_scratch_bytes", "gs_sort_pairs_u32",
+    "gs_adam_step_multi", "gs_sort_scratch_bytes", "gs_sort_pairs_u32", "gs_sort_pairs_u32_noalloc",
 )
 
 
@@ -93,6 +93,8 @@ _SIGS = {
     "gs_sort_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "gs_sort_pairs_u32": (ctypes.c_int, [P, P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          P, P]),
+    "gs_sort_pairs_u32_noalloc": (ctypes.c_int, [P, P, P, P, ctypes.c_int64, ctypes.c_int32,
+                                                 ctypes.c_int32, P]),
 }
 
 

@@ -276,3 +276,60 @@ extern "C" int gs_sort_pairs_u32(uint32_t *keys_in, uint32_t *vals_in, uint32_t 
     }
     return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of gs_sort_pairs_u32.
+//
+// Some callers cannot hand the sort a scratch buffer: code that runs while a
+// CUDA graph is captured in global mode (where cudaMalloc is not allowed),
+// plug-ins living inside a framework whose memory pool owns all device
+// memory, and latency-critical loops that cannot afford cudaMalloc's implicit
+// device synchronisation.  This entry point keeps its scratch in a file-scope
+// __device__ array instead.  The array holds the per-pass digit histogram of
+// the fixed-grid sort, kRadix * kSortBlocks + kRadix 32-bit counters
+// (609 KiB); it does not grow with n, and every GPU that loads the library
+// keeps it until the process exits.
+#include <mutex>
+
+namespace gs {
+
+__device__ __align__(256) uint32_t g_noalloc_sort_scratch[kHist + kRadix];
+
+constexpr int kNoallocMaxDevices = 64;
+static uint32_t *g_noalloc_ptr[kNoallocMaxDevices];
+static std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array for the current device, looked up once
+// per device (with that device current) and cached.
+static int noalloc_scratch(uint32_t **out) {
+    int dev = 0;
+    int rc = check_cuda(cudaGetDevice(&dev));
+    if (rc) return rc;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return GS_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        rc = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_sort_scratch));
+        if (rc) return rc;
+        g_noalloc_ptr[dev] = (uint32_t *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return GS_OK;
+}
+
+}  // namespace gs
+
+extern "C" int gs_sort_pairs_u32_noalloc(uint32_t *keys_in, uint32_t *vals_in, uint32_t *keys_out,
+                                         uint32_t *vals_out, int64_t n, int32_t begin_bit,
+                                         int32_t end_bit, void *stream) {
+    if (n < 0 || n > GS_SORT_NOALLOC_MAX_N || begin_bit < 0 || end_bit > 32 || begin_bit > end_bit)
+        return GS_ERR_ARG;
+    if (n == 0) return GS_OK;
+    if (!keys_in || !vals_in || !keys_out || !vals_out) return GS_ERR_ARG;
+    uint32_t *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    // The histogram is fully rewritten by every pass, so no clearing is needed.
+    return gs_sort_pairs_u32(keys_in, vals_in, keys_out, vals_out, n, begin_bit, end_bit, scratch,
+                             stream);
+}
