@@ -43,29 +43,35 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam(AdamGroups G) {
         const int64_t i = (slot - G.slot_off[gi]) * 4;
         const int64_t n = G.n[gi];
         const float step = G.step_size[gi];
-        if (G.period[gi] > 0) {  // per-element learning rate by position in the period
-            for (int64_t j = i; j < i + 4 && j < n; ++j) {
-                const float st = (j % G.period[gi]) < G.head[gi] ? G.step_head[gi] : step;
-                adam1(G.p[gi][j], G.g[gi][j], G.m[gi][j], G.v[gi][j], G.b1, G.b2, G.eps, st,
-                      G.inv_bc2_sqrt);
+        if (G.vec_ok[gi] && i + 3 < n) {
+            float st[4] = {step, step, step, step};
+            if (G.period[gi] > 0) {  // per-element rate by position in the period
+                const int64_t per = G.period[gi];
+                int64_t r = i < 0xffffffffll && per < 0xffffffffll ? (int64_t)((uint32_t)i % (uint32_t)per)
+                                                                    : i % per;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    st[c] = r < G.head[gi] ? G.step_head[gi] : step;
+                    if (++r == per) r = 0;
+                }
             }
-        } else if (G.vec_ok[gi] && i + 3 < n) {
             float4 p = *reinterpret_cast<float4 *>(G.p[gi] + i);
             float4 g = *reinterpret_cast<float4 *>(G.g[gi] + i);
             float4 m = *reinterpret_cast<float4 *>(G.m[gi] + i);
             float4 v = *reinterpret_cast<float4 *>(G.v[gi] + i);
-            adam1(p.x, g.x, m.x, v.x, G.b1, G.b2, G.eps, step, G.inv_bc2_sqrt);
-            adam1(p.y, g.y, m.y, v.y, G.b1, G.b2, G.eps, step, G.inv_bc2_sqrt);
-            adam1(p.z, g.z, m.z, v.z, G.b1, G.b2, G.eps, step, G.inv_bc2_sqrt);
-            adam1(p.w, g.w, m.w, v.w, G.b1, G.b2, G.eps, step, G.inv_bc2_sqrt);
+            adam1(p.x, g.x, m.x, v.x, G.b1, G.b2, G.eps, st[0], G.inv_bc2_sqrt);
+            adam1(p.y, g.y, m.y, v.y, G.b1, G.b2, G.eps, st[1], G.inv_bc2_sqrt);
+            adam1(p.z, g.z, m.z, v.z, G.b1, G.b2, G.eps, st[2], G.inv_bc2_sqrt);
+            adam1(p.w, g.w, m.w, v.w, G.b1, G.b2, G.eps, st[3], G.inv_bc2_sqrt);
             *reinterpret_cast<float4 *>(G.p[gi] + i) = p;
             *reinterpret_cast<float4 *>(G.g[gi] + i) = g;
             *reinterpret_cast<float4 *>(G.m[gi] + i) = m;
             *reinterpret_cast<float4 *>(G.v[gi] + i) = v;
         } else {
-            for (int64_t j = i; j < i + 4 && j < n; ++j)
-                adam1(G.p[gi][j], G.g[gi][j], G.m[gi][j], G.v[gi][j], G.b1, G.b2, G.eps, step,
-                      G.inv_bc2_sqrt);
+            for (int64_t j = i; j < i + 4 && j < n; ++j) {
+                const float st = G.period[gi] > 0 && (j % G.period[gi]) < G.head[gi] ? G.step_head[gi] : step;
+                adam1(G.p[gi][j], G.g[gi][j], G.m[gi][j], G.v[gi][j], G.b1, G.b2, G.eps, st, G.inv_bc2_sqrt);
+            }
         }
     }
 }

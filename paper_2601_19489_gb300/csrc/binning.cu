@@ -9,13 +9,17 @@
 //     and the capacity overflow flag), and the key-write pass that rescans
 //     inside each block.
 //  3. key write, one (global tile id, item) instance per touched tile:
-//     load-balanced (Fig. "LB"): a warp takes one Gaussian at a time, its
-//     lanes test one candidate tile of the SnugBox each (per-column ellipse
-//     test) and compact the hits with ballot/popc;
+//     load-balanced (Fig. "LB"): the SnugBox columns of a warp's 32 Gaussians
+//     form one flat list that the lanes walk one column each, so every lane
+//     evaluates a per-column ellipse test whatever the Gaussians' sizes, and
+//     a segmented warp scan places each column's tiles;
 //     sequential ("Sq"): one thread walks its Gaussian's columns.
+//     Each round of Gaussians assembles its (contiguous) run of instances in
+//     shared memory and writes it out coalesced.
 //  4. stable radix sort of the instances by tile id: every tile's list keeps
 //     the depth order of step 1, ties in depth by ascending Gaussian index.
-//  5. tile ranges from the run boundaries, and the 32-splat bucket offsets.
+//  5. tile ranges by binary search in the sorted ids and the 32-splat bucket
+//     offsets.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -89,29 +93,74 @@ k_count_top(const uint32_t *__restrict__ block_sums, unsigned long long *__restr
     if (tid == 0) {
         st->n_inst = all > 0xffffffffull ? 0xffffffffu : (uint32_t)all;
         st->overflow = all > (unsigned long long)capacity ? 1u : 0u;
-        st->bucket_next = 0;
     }
 }
 
-// Instance key write.  Block b rescans the counts of its chunk of depth ranks
-// in rounds of kScanThreads and writes each Gaussian's touched tiles.
+// Instance key write.  Block b takes the chunk of depth ranks whose count it
+// summed, in rounds of kWriteRound ranks: a block scan of their tile counts
+// gives each Gaussian its slot range, the round's instances are assembled in
+// shared memory (they form one contiguous run of the output) and written out
+// coalesced.  A round with more instances than the staging holds writes
+// straight to global memory instead.
+constexpr int kWriteRound = 128;
+constexpr int kStageCap = 5504;  // instances staged per round (43 KB)
+
+__device__ __forceinline__ uint32_t block_exclusive_scan128(uint32_t x, uint32_t *warp_tmp, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tmp[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kWriteRound / 32; ++w) {
+        const uint32_t v = warp_tmp[w];
+        before += w < warp ? v : 0u;
+        all += v;
+    }
+    __syncthreads();
+    *total = all;
+    return inc - x + before;
+}
+
+struct WriteSink {
+    uint32_t *s_tile, *s_item;       // staging (shared)
+    uint32_t *g_tile, *g_item;       // output (global)
+    unsigned long long round_base;   // global position of the round's first instance
+    unsigned long long capacity;
+    bool staged;
+    __device__ __forceinline__ void put(uint32_t local, uint32_t tile, uint32_t item) const {
+        if (staged) {
+            s_tile[local] = tile;
+            s_item[local] = item;
+        } else {
+            const unsigned long long pos = round_base + local;
+            if (pos < capacity) {
+                g_tile[pos] = tile;
+                g_item[pos] = item;
+            }
+        }
+    }
+};
+
 template <bool kLB>
-__global__ void __launch_bounds__(kScanThreads)
+__global__ void __launch_bounds__(kWriteRound)
 k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ order,
              const uint32_t *__restrict__ touched, const float4 *__restrict__ rec,
-             const float2 *__restrict__ bin,
-             const uint2 *__restrict__ rects, const unsigned long long *__restrict__ block_offs, int64_t n,
-             int64_t capacity, uint32_t *__restrict__ inst_tile, uint32_t *__restrict__ inst_item,
-             StatusDev *st) {
-    __shared__ uint32_t tmp[kScanThreads / 32];
-    __shared__ uint32_t s_item[kScanThreads];
-    __shared__ unsigned long long s_off[kScanThreads];
-    __shared__ uint32_t s_cnt[kScanThreads];
+             const float2 *__restrict__ bin, const uint2 *__restrict__ rects,
+             const unsigned long long *__restrict__ block_offs, int64_t n, int64_t capacity,
+             uint32_t *__restrict__ inst_tile, uint32_t *__restrict__ inst_item, StatusDev *st) {
+    __shared__ uint32_t tmp[kWriteRound / 32];
+    __shared__ uint32_t s_tile_out[kStageCap], s_item_out[kStageCap];
     int64_t beg, end;
     chunk_of(n, &beg, &end);
     unsigned long long base = block_offs[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t r0 = beg; r0 < end; r0 += kScanThreads) {
+    for (int64_t r0 = beg; r0 < end; r0 += kWriteRound) {
         const int64_t r = r0 + threadIdx.x;
         uint32_t item = 0, cnt = 0;
         if (r < end) {
@@ -119,127 +168,172 @@ k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ or
             cnt = touched[item];
         }
         uint32_t total;
-        const unsigned long long off = base + block_exclusive_scan(cnt, tmp, &total);
-        base += total;
+        const uint32_t off = block_exclusive_scan128(cnt, tmp, &total);
+        WriteSink sink{s_tile_out, s_item_out, inst_tile, inst_item, base, (unsigned long long)capacity,
+                       total <= (uint32_t)kStageCap};
         if (!kLB) {
-            if (cnt == 0) continue;
-            const int v = (int)(item / (uint32_t)n_per_view);
-            const ViewDev &cam = views.v[v];
-            const float4 r0v = rec[3 * (size_t)item];
-            const float Cc = rec[3 * (size_t)item + 1].x;
-            const float2 bv = bin[item];
-            const float tb = bv.x, detc = bv.y;
-            int tx0, ty0, tx1, ty1;
-            unpack_rect(rects[item], &tx0, &ty0, &tx1, &ty1);
-            float rx, ry;
-            ellipse_extent(r0v.z, Cc, detc, tb, &rx, &ry);
-            uint32_t w = 0;
-            for (int tx = tx0; tx < tx1; ++tx) {
-                float xa, xb;
-                column_span(tx, (float)cam.W, &xa, &xb);
-                int lo, hi;
-                if (!column_rows(r0v.x, r0v.y, r0v.z, r0v.w, Cc, detc, tb, rx, ry, xa, xb,
-                                 (float)cam.H, ty0, ty1, &lo, &hi))
-                    continue;
-                for (int ty = lo; ty <= hi; ++ty, ++w) {
-                    const unsigned long long pos = off + w;
-                    if (w < cnt && pos < (unsigned long long)capacity) {
-                        inst_tile[pos] = (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx);
-                        inst_item[pos] = item;
-                    }
+            // one thread per Gaussian walks its columns
+            if (cnt) {
+                const int v = (int)(item / (uint32_t)n_per_view);
+                const ViewDev &cam = views.v[v];
+                const float4 r0v = rec[3 * (size_t)item];
+                const float2 bv = bin[item];
+                BinGeom bg;
+                bin_geom(r0v.x, r0v.y, r0v.z, r0v.w, rec[3 * (size_t)item + 1].x, bv.y, bv.x, bg);
+                int tx0, ty0, tx1, ty1;
+                unpack_rect(rects[item], &tx0, &ty0, &tx1, &ty1);
+                uint32_t w = 0;
+                for (int tx = tx0; tx < tx1; ++tx) {
+                    float xa, xb;
+                    column_span(tx, (float)cam.W, &xa, &xb);
+                    int lo, hi;
+                    if (!column_rows(bg, xa, xb, (float)cam.H, ty0, ty1, &lo, &hi)) continue;
+                    for (int ty = lo; ty <= hi; ++ty, ++w)
+                        if (w < cnt) sink.put(off + w, (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx), item);
                 }
-            }
-            if (w != cnt) {
-                // keep every slot of this Gaussian valid (never happens when the
-                // count and the write agree, which the shared column test ensures)
-                atomicCAS(&st->error, 0, GS_ERR_INTERNAL);
-                for (; w < cnt; ++w) {
-                    const unsigned long long pos = off + w;
-                    if (pos < (unsigned long long)capacity) {
-                        inst_tile[pos] = (uint32_t)(cam.tile_off + ty0 * cam.tiles_x + tx0);
-                        inst_item[pos] = item;
-                    }
+                if (w != cnt) {
+                    // keep every slot valid (cannot happen while the count and
+                    // the write share column_rows)
+                    atomicCAS(&st->error, 0, GS_ERR_INTERNAL);
+                    for (; w < cnt; ++w) sink.put(off + w, (uint32_t)(cam.tile_off + ty0 * cam.tiles_x + tx0), item);
                 }
             }
         } else {
-            s_item[threadIdx.x] = item;
-            s_off[threadIdx.x] = off;
-            s_cnt[threadIdx.x] = cnt;
-            __syncthreads();
-            // warp `warp` takes the Gaussians of lanes warp*32 .. warp*32+31 in turn
-            for (int j = 0; j < 32; ++j) {
-                const int slot = warp * 32 + j;
-                const uint32_t c = s_cnt[slot];
-                if (c == 0) continue;
-                const uint32_t it = s_item[slot];
-                const unsigned long long o0 = s_off[slot];
-                const int v = (int)(it / (uint32_t)n_per_view);
+            // load-balanced: the columns of the warp's 32 Gaussians are laid out
+            // in one flat list and every lane takes one column at a time, so
+            // all lanes work whatever the Gaussians' sizes; a segmented warp
+            // scan of the row counts places each column's tiles.
+            __shared__ uint32_t s_carry[kWriteRound];  // tiles placed so far, per Gaussian
+            BinGeom my{};
+            int mtx0 = 0, mty0 = 0, mtx1 = 0, mty1 = 0, mtoff = 0, mtiles_x = 0, mW = 0, mH = 0;
+            if (cnt) {
+                const int v = (int)(item / (uint32_t)n_per_view);
                 const ViewDev &cam = views.v[v];
-                const float4 r0v = rec[3 * (size_t)it];
-                const float Cc = rec[3 * (size_t)it + 1].x;
-                const float2 bv = bin[it];
-                const float tb = bv.x, detc = bv.y;
-                int tx0, ty0, tx1, ty1;
-                unpack_rect(rects[it], &tx0, &ty0, &tx1, &ty1);
-                float rx, ry;
-                ellipse_extent(r0v.z, Cc, detc, tb, &rx, &ry);
-                const int wdt = tx1 - tx0;
-                const int cand = wdt * (ty1 - ty0);
-                uint32_t written = 0;
-                for (int c0 = 0; c0 < cand; c0 += 32) {
-                    const int ci = c0 + lane;
-                    bool hit = false;
-                    int tx = 0, ty = 0;
-                    if (ci < cand) {
-                        tx = tx0 + ci % wdt;
-                        ty = ty0 + ci / wdt;
-                        float xa, xb;
-                        column_span(tx, (float)cam.W, &xa, &xb);
-                        int lo, hi;
-                        if (column_rows(r0v.x, r0v.y, r0v.z, r0v.w, Cc, detc, tb, rx, ry, xa, xb,
-                                        (float)cam.H, ty0, ty1, &lo, &hi))
-                            hit = ty >= lo && ty <= hi;
-                    }
-                    const uint32_t ballot = __ballot_sync(0xffffffffu, hit);
-                    if (hit) {
-                        const uint32_t w = written + __popc(ballot & ((1u << lane) - 1u));
-                        const unsigned long long pos = o0 + w;
-                        if (w < c && pos < (unsigned long long)capacity) {
-                            inst_tile[pos] = (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx);
-                            inst_item[pos] = it;
-                        }
-                    }
-                    written += __popc(ballot);
+                const float4 r0v = rec[3 * (size_t)item];
+                const float2 bv = bin[item];
+                bin_geom(r0v.x, r0v.y, r0v.z, r0v.w, rec[3 * (size_t)item + 1].x, bv.y, bv.x, my);
+                unpack_rect(rects[item], &mtx0, &mty0, &mtx1, &mty1);
+                mtoff = cam.tile_off;
+                mtiles_x = cam.tiles_x;
+                mW = cam.W;
+                mH = cam.H;
+            }
+            s_carry[threadIdx.x] = 0;
+            const uint32_t ncols = cnt ? (uint32_t)(mtx1 - mtx0) : 0u;
+            uint32_t colpref = ncols;  // inclusive, then exclusive scan of column counts
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, colpref, o);
+                if (lane >= o) colpref += y;
+            }
+            const uint32_t n_cols = __shfl_sync(0xffffffffu, colpref, 31);
+            colpref -= ncols;
+            __syncwarp();
+            for (uint32_t c0 = 0; c0 < n_cols; c0 += 32) {
+                const uint32_t f = c0 + lane;
+                const bool has = f < n_cols;
+                // owner: the last lane j with colpref_j <= f (binary search)
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t cp = __shfl_sync(0xffffffffu, colpref, j + step);
+                    if (cp <= f) j += step;
                 }
-                if (written != c) {  // see the sequential path
-                    if (lane == 0) atomicCAS(&st->error, 0, GS_ERR_INTERNAL);
-                    for (uint32_t w = written + lane; w < c; w += 32) {
-                        const unsigned long long pos = o0 + w;
-                        if (pos < (unsigned long long)capacity) {
-                            inst_tile[pos] = (uint32_t)(cam.tile_off + ty0 * cam.tiles_x + tx0);
-                            inst_item[pos] = it;
-                        }
-                    }
+                BinGeom bg;
+                bg.mx = __shfl_sync(0xffffffffu, my.mx, j);
+                bg.my = __shfl_sync(0xffffffffu, my.my, j);
+                bg.B = __shfl_sync(0xffffffffu, my.B, j);
+                bg.detc = __shfl_sync(0xffffffffu, my.detc, j);
+                bg.tC = __shfl_sync(0xffffffffu, my.tC, j);
+                bg.invC = __shfl_sync(0xffffffffu, my.invC, j);
+                bg.dx_top = __shfl_sync(0xffffffffu, my.dx_top, j);
+                bg.rx = __shfl_sync(0xffffffffu, my.rx, j);
+                bg.ry = __shfl_sync(0xffffffffu, my.ry, j);
+                const int tx0 = __shfl_sync(0xffffffffu, mtx0, j), ty0 = __shfl_sync(0xffffffffu, mty0, j);
+                const int ty1 = __shfl_sync(0xffffffffu, mty1, j);
+                const int toff = __shfl_sync(0xffffffffu, mtoff, j);
+                const int tiles_x = __shfl_sync(0xffffffffu, mtiles_x, j);
+                const float fW = (float)__shfl_sync(0xffffffffu, mW, j);
+                const float fH = (float)__shfl_sync(0xffffffffu, mH, j);
+                const uint32_t cp_j = __shfl_sync(0xffffffffu, colpref, j);
+                const uint32_t it = __shfl_sync(0xffffffffu, item, j);
+                const uint32_t o0 = __shfl_sync(0xffffffffu, off, j);
+                const uint32_t c_j = __shfl_sync(0xffffffffu, cnt, j);
+                const int tx = tx0 + (int)(f - cp_j);
+                int lo = 0, hi = -1, rows = 0;
+                if (has) {
+                    float xa, xb;
+                    column_span(tx, fW, &xa, &xb);
+                    rows = column_rows(bg, xa, xb, fH, ty0, ty1, &lo, &hi);
+                }
+                // segmented exclusive scan of rows over the chunk (segments =
+                // runs of equal owner)
+                uint32_t inc = (uint32_t)rows;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                const bool head = lane == 0 || f == cp_j;
+                const uint32_t heads = __ballot_sync(0xffffffffu, head);
+                const int seg_lane = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+                const uint32_t before_seg = __shfl_sync(0xffffffffu, inc, seg_lane > 0 ? seg_lane - 1 : 0);
+                const uint32_t seg_excl = inc - (uint32_t)rows - (seg_lane > 0 ? before_seg : 0u);
+                const uint32_t w0 = s_carry[warp * 32 + j] + seg_excl;
+                for (int ty = lo; ty <= hi; ++ty) {
+                    const uint32_t w = w0 + (uint32_t)(ty - lo);
+                    if (w < c_j) sink.put(o0 + w, (uint32_t)(toff + ty * tiles_x + tx), it);
+                }
+                __syncwarp();
+                // the last column of each segment advances its Gaussian's count
+                const bool tail = has && (lane == 31 || ((heads >> (lane + 1)) & 1u) || f + 1 == n_cols);
+                if (tail) s_carry[warp * 32 + j] += seg_excl + (uint32_t)rows;
+                __syncwarp();
+            }
+            if (cnt && s_carry[threadIdx.x] != cnt) {
+                // keep every slot valid (cannot happen while the count and the
+                // write share column_rows)
+                atomicCAS(&st->error, 0, GS_ERR_INTERNAL);
+                for (uint32_t w = s_carry[threadIdx.x]; w < cnt; ++w)
+                    sink.put(off + w, (uint32_t)(mtoff + mty0 * mtiles_x + mtx0), item);
+            }
+        }
+        __syncthreads();
+        if (sink.staged) {
+            for (uint32_t i = threadIdx.x; i < total; i += kWriteRound) {
+                const unsigned long long pos = base + i;
+                if (pos < (unsigned long long)capacity) {
+                    inst_tile[pos] = s_tile_out[i];
+                    inst_item[pos] = s_item_out[i];
                 }
             }
             __syncthreads();
         }
+        base += total;
     }
 }
 
-// Run boundaries of the sorted tile ids -> [start, end) per tile.
+// [start, end) of every tile in the sorted tile ids by binary search (one
+// thread per tile): every range is written, empty tiles get start == end.
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *__restrict__ a, uint32_t n, uint32_t v) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 __global__ void __launch_bounds__(256)
 k_tile_ranges(const uint32_t *__restrict__ keys, const StatusDev *st, int64_t capacity,
               uint32_t total_tiles, uint2 *__restrict__ ranges) {
-    int64_t n = st->n_inst;
-    if (n > capacity) n = capacity;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = keys[i];
-        if (k >= total_tiles) continue;  // cannot happen for keys written by k_write_keys
-        if (i == 0 || keys[i - 1] != k) ranges[k].x = (uint32_t)i;
-        if (i == n - 1 || keys[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
-    }
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total_tiles) return;
+    int64_t n64 = st->n_inst;
+    if (n64 > capacity) n64 = capacity;
+    const uint32_t n = (uint32_t)n64;
+    ranges[t] = make_uint2(lower_bound_u32(keys, n, t), lower_bound_u32(keys, n, t + 1));
 }
 
 // One block: bucket_off[t] = sum over tiles before t of ceil(len / 32).
@@ -261,7 +355,7 @@ k_bucket_offsets(const uint2 *__restrict__ ranges, int total_tiles, uint32_t *__
         uint32_t inc = nb;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
         if (lane == 31) tmp[warp] = inc;
@@ -315,12 +409,12 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
     uint32_t *ik0 = ws_at<uint32_t>(ws, plan->o_ikey[0]), *iv0 = ws_at<uint32_t>(ws, plan->o_ival[0]);
     uint32_t *ik1 = ws_at<uint32_t>(ws, plan->o_ikey[1]), *iv1 = ws_at<uint32_t>(ws, plan->o_ival[1]);
     if (load_balanced)
-        k_write_keys<true><<<kSortBlocks, kScanThreads, 0, s>>>(
+        k_write_keys<true><<<kSortBlocks, kWriteRound, 0, s>>>(
             vd, plan->n, order, touched, ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin),
             ws_at<uint2>(ws, plan->o_rect),
             block_offs, VN, plan->inst_cap, ik0, iv0, st);
     else
-        k_write_keys<false><<<kSortBlocks, kScanThreads, 0, s>>>(
+        k_write_keys<false><<<kSortBlocks, kWriteRound, 0, s>>>(
             vd, plan->n, order, touched, ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin),
             ws_at<uint2>(ws, plan->o_rect),
             block_offs, VN, plan->inst_cap, ik0, iv0, st);
@@ -335,10 +429,8 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
 
     // 5. ranges and buckets
     uint2 *ranges = ws_at<uint2>(ws, plan->o_ranges);
-    rc = check_cuda(cudaMemsetAsync(ranges, 0, (size_t)plan->total_tiles * sizeof(uint2), s));
-    if (rc) return rc;
-    k_tile_ranges<<<4 * 152, 256, 0, s>>>(ws_at<uint32_t>(ws, plan->o_ikey[ifinal]), st, plan->inst_cap,
-                                          (uint32_t)plan->total_tiles, ranges);
+    k_tile_ranges<<<(plan->total_tiles + 255) / 256, 256, 0, s>>>(
+        ws_at<uint32_t>(ws, plan->o_ikey[ifinal]), st, plan->inst_cap, (uint32_t)plan->total_tiles, ranges);
     k_bucket_offsets<<<1, 1024, 0, s>>>(ranges, plan->total_tiles, ws_at<uint32_t>(ws, plan->o_bucket_off),
                                         st);
     return launch_error();

@@ -57,8 +57,7 @@ struct StatusDev {
     uint32_t n_buckets;   // buckets of the last bin/sort
     uint32_t overflow;    // 1 if n_inst > capacity
     int32_t error;        // first device-side error code
-    uint32_t bucket_next; // dynamic work counter of the backward
-    uint32_t pad[59];
+    uint32_t pad[60];
 };
 
 }  // namespace gs
@@ -106,33 +105,54 @@ int sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *v
                cudaStream_t s, int *final_buf);
 
 // ----------------------------------------------------------------------------
+// Half extents of the ellipse A dx^2 + 2 B dx dy + C dy^2 <= tb along x and
+// y: sqrt(tb C / detc) and sqrt(tb A / detc) (Eq. 2's tangent points, i.e.
+// sqrt(t Sxx) and sqrt(t Syy) of the 2D covariance).
+__device__ __forceinline__ void ellipse_extent(float A, float C, float detc, float tb, float *rx,
+                                               float *ry) {
+    *rx = __fsqrt_rn(__fdiv_rn(__fmul_rn(tb, C), detc));
+    *ry = __fsqrt_rn(__fdiv_rn(__fmul_rn(tb, A), detc));
+}
+
+// Per-Gaussian constants of the tile-column test.
+struct BinGeom {
+    float mx, my, B, detc, tC, invC, dx_top, rx, ry;
+};
+
+__device__ __forceinline__ void bin_geom(float mx, float my, float A, float B, float C, float detc, float tb,
+                                         BinGeom &g) {
+    ellipse_extent(A, C, detc, tb, &g.rx, &g.ry);
+    g.mx = mx;
+    g.my = my;
+    g.B = B;
+    g.detc = detc;
+    g.tC = __fmul_rn(tb, C);
+    g.invC = __frcp_rn(C);
+    g.dx_top = __fdiv_rn(__fmul_rn(-B, g.ry), A);
+}
+
 // Tile-column test.  For the tile column [xa, xb] (pixel-centre x range of the
 // column, clipped to the image) return the inclusive tile-row range
 // [*ty_lo, *ty_hi] whose pixel-centre rectangles meet the ellipse
 //   A dx^2 + 2 B dx dy + C dy^2 <= tb,   (dx, dy) = (x - mx, y - my),
-// clipped to the rows [ty0, ty1).  detc = A C - B^2 (> 0), rx/ry the ellipse's
-// half extents.  The ellipse's y-range over a column is an interval: its top
-// is the concave upper branch maximised at the tangent point dx = -B ry / A
-// clamped into the column, its bottom the convex lower branch minimised at
-// dx = +B ry / A (Eq. 2, with the sign of its radicand corrected).  Every
-// operation is an explicitly rounded intrinsic so the tile count and the
-// tile-key write compute the same rows.
-__device__ __forceinline__ int column_rows(float mx, float my, float A, float B, float C,
-                                           float detc, float tb, float rx, float ry, float xa,
-                                           float xb, float img_h, int ty0, int ty1, int *ty_lo,
-                                           int *ty_hi) {
-    float dxa = fmaxf(__fsub_rn(xa, mx), -rx);
-    float dxb = fminf(__fsub_rn(xb, mx), rx);
+// clipped to the rows [ty0, ty1).  With detc = A C - B^2 > 0 the y-range of
+// the ellipse over a column is an interval: its top is the concave upper
+// branch  (-B dx + sqrt(tb C - detc dx^2)) / C  maximised at the tangent point
+// dx = -B ry / A clamped into the column, its bottom the convex lower branch
+// minimised at dx = +B ry / A (Eq. 2, with the sign of its radicand
+// corrected).  Every operation is an explicitly rounded intrinsic so the tile
+// count and the tile-key write compute the same rows.
+__device__ __forceinline__ int column_rows(const BinGeom &g, float xa, float xb, float img_h, int ty0, int ty1,
+                                           int *ty_lo, int *ty_hi) {
+    const float dxa = fmaxf(__fsub_rn(xa, g.mx), -g.rx);
+    const float dxb = fminf(__fsub_rn(xb, g.mx), g.rx);
     if (dxa > dxb) return 0;
-    float tC = __fmul_rn(tb, C);
-    float invC = __frcp_rn(C);
-    float dx_top = __fdiv_rn(__fmul_rn(-B, ry), A);
-    float d = fminf(fmaxf(dx_top, dxa), dxb);
-    float disc = fmaxf(__fsub_rn(tC, __fmul_rn(detc, __fmul_rn(d, d))), 0.0f);
-    float y_hi = __fadd_rn(my, __fmul_rn(__fadd_rn(__fmul_rn(-B, d), __fsqrt_rn(disc)), invC));
-    d = fminf(fmaxf(-dx_top, dxa), dxb);
-    disc = fmaxf(__fsub_rn(tC, __fmul_rn(detc, __fmul_rn(d, d))), 0.0f);
-    float y_lo = __fadd_rn(my, __fmul_rn(__fsub_rn(__fmul_rn(-B, d), __fsqrt_rn(disc)), invC));
+    float d = fminf(fmaxf(g.dx_top, dxa), dxb);
+    float disc = fmaxf(__fsub_rn(g.tC, __fmul_rn(g.detc, __fmul_rn(d, d))), 0.0f);
+    float y_hi = __fadd_rn(g.my, __fmul_rn(__fadd_rn(__fmul_rn(-g.B, d), __fsqrt_rn(disc)), g.invC));
+    d = fminf(fmaxf(-g.dx_top, dxa), dxb);
+    disc = fmaxf(__fsub_rn(g.tC, __fmul_rn(g.detc, __fmul_rn(d, d))), 0.0f);
+    float y_lo = __fadd_rn(g.my, __fmul_rn(__fsub_rn(__fmul_rn(-g.B, d), __fsqrt_rn(disc)), g.invC));
     y_lo = fmaxf(y_lo, 0.5f);
     y_hi = fminf(y_hi, __fsub_rn(img_h, 0.5f));
     if (!(y_lo <= y_hi)) return 0;
@@ -144,15 +164,6 @@ __device__ __forceinline__ int column_rows(float mx, float my, float A, float B,
     *ty_lo = lo;
     *ty_hi = hi;
     return hi - lo + 1;
-}
-
-// Half extents of the ellipse A dx^2 + 2 B dx dy + C dy^2 <= tb along x and
-// y: sqrt(tb C / detc) and sqrt(tb A / detc) (Eq. 2's tangent points, i.e.
-// sqrt(t Sxx) and sqrt(t Syy) of the 2D covariance).
-__device__ __forceinline__ void ellipse_extent(float A, float C, float detc, float tb, float *rx,
-                                               float *ry) {
-    *rx = __fsqrt_rn(__fdiv_rn(__fmul_rn(tb, C), detc));
-    *ry = __fsqrt_rn(__fdiv_rn(__fmul_rn(tb, A), detc));
 }
 
 // Tile rectangle [tx0, tx1) x [ty0, ty1) of the SnugBox (pixel-centre bounds

@@ -268,15 +268,14 @@ k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
     uint32_t count = 0;
     int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
     if (t > 0.0f) {
-        float rx, ry;
-        ellipse_extent(A, C, detc, tb, &rx, &ry);
-        if (snug_rect(mx, my, rx, ry, (float)cam.W, (float)cam.H, &tx0, &ty0, &tx1, &ty1)) {
+        BinGeom bg;
+        bin_geom(mx, my, A, B, C, detc, tb, bg);
+        if (snug_rect(mx, my, bg.rx, bg.ry, (float)cam.W, (float)cam.H, &tx0, &ty0, &tx1, &ty1)) {
             for (int tx = tx0; tx < tx1; ++tx) {
                 float xa, xb;
                 column_span(tx, (float)cam.W, &xa, &xb);
                 int lo, hi;
-                count += column_rows(mx, my, A, B, C, detc, tb, rx, ry, xa, xb, (float)cam.H, ty0, ty1,
-                                     &lo, &hi);
+                count += column_rows(bg, xa, xb, (float)cam.H, ty0, ty1, &lo, &hi);
             }
         }
     }

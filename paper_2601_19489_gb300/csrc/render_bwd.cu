@@ -13,7 +13,10 @@
 // accumulate in registers over all pixels; each lane then adds its splat's
 // 10 values to the per-(view, Gaussian) accumulator with three float4 atomics.
 // Pixels whose blend ended before the bucket are compacted away first, so the
-// pipeline only steps through pixels the bucket can affect.
+// pipeline only steps through pixels the bucket can affect, and the list is
+// walked as two interleaved chains (its halves) to hide the shuffle latency.
+// A CTA takes one tile at a time, stages the tile's per-pixel gradients once
+// and its warps share the tile's buckets round robin.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -21,21 +24,51 @@ namespace gs {
 constexpr int kBwdWarps = 4;
 constexpr int kBwdThreads = kBwdWarps * 32;
 
-struct PixStage {
-    float4 g[kTilePix];      // (g_r, g_g, g_b, g_D)
-    float2 fin[kTilePix];    // (S_fin, n_contrib as float bits)
-    float2 ck[kTilePix];     // checkpoint (T, S) in front of the bucket
-    uint8_t pix[kTilePix];   // pixel index within the tile
+// Per CTA: the current tile's per-pixel data (staged once for all warps) and
+// each warp's compacted pixel list for the bucket it is working on.
+struct BwdShared {
+    float4 g[kTilePix];                 // (g_r, g_g, g_b, g_D), zero outside the image
+    float2 fin[kTilePix];               // (S_fin, n_contrib as bits)
+    float2 ck[kBwdWarps][kTilePix];     // per warp, compacted: (T, S) in front of its bucket
+    uint8_t pix[kBwdWarps][kTilePix];   // per warp, compacted: pixel index in the tile
+    uint32_t next;                      // next unclaimed bucket of the tile
 };
 
-__device__ __forceinline__ int find_tile(const uint32_t *bucket_off, int total_tiles, uint32_t b) {
-    int lo = 0, hi = total_tiles;  // bucket_off[lo] <= b < bucket_off[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(bucket_off + mid) <= b) lo = mid;
-        else hi = mid;
+struct SplatGrad {
+    float mx, my, xx, xy, yy, pw, r, g, b, iz;
+};
+
+// One (splat, pixel) pair of the pipeline: T, S enter as the state in front
+// of the splat and leave as the state behind it.
+__device__ __forceinline__ void bwd_pair(const BwdShared &S, int warp, int m, uint32_t k, const float4 &r0,
+                                         const float4 &r1, const float4 &r2, float &T, float &Sv,
+                                         SplatGrad &acc) {
+    const int p = S.pix[warp][m];
+    const float2 fin = S.fin[p];
+    if (k >= __float_as_uint(fin.y)) return;  // beyond this pixel's last blended splat
+    PairEval e;
+    eval_pair(r0, r1, (float)(p & (kTile - 1)) + 0.5f, (float)(p >> 4) + 0.5f, e);
+    if (e.power2 > 0.0f || e.alpha < kAlphaMin) return;
+    const float4 g = S.g[p];
+    const float w = e.alpha * T;
+    const float gdot = g.x * r2.x + g.y * r2.y + g.z * r2.z + g.w * r1.z;
+    acc.r += w * g.x;
+    acc.g += w * g.y;
+    acc.b += w * g.z;
+    acc.iz += w * g.w;
+    const float S_in = Sv;
+    Sv = S_in + w * gdot;
+    if (e.raw <= kAlphaMax) {  // the clamp passes no gradient
+        const float dL_da = T * gdot - __fdividef(fin.x - Sv, 1.0f - e.alpha);
+        const float dpw = dL_da * e.raw;  // dL/dpower (natural log units)
+        acc.pw += dpw;
+        acc.mx += dpw * (r0.z * e.dx + r0.w * e.dy);
+        acc.my += dpw * (r0.w * e.dx + r1.x * e.dy);
+        acc.xx += dpw * e.dx * e.dx;
+        acc.xy += dpw * e.dx * e.dy;
+        acc.yy += dpw * e.dy * e.dy;
     }
-    return lo;
+    T = T * (1.0f - e.alpha);
 }
 
 __global__ void __launch_bounds__(kBwdThreads)
@@ -44,21 +77,16 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
              const uint32_t *__restrict__ tile_maxc, const float *__restrict__ ckpt,
              const uint32_t *__restrict__ n_contrib, const float *__restrict__ img_rgb,
              const float *__restrict__ img_disp, const float *__restrict__ dL_drgb,
-             const float *__restrict__ dL_ddisp, StatusDev *st, float4 *__restrict__ grad2d) {
-    __shared__ PixStage stage[kBwdWarps];
+             const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d) {
+    __shared__ BwdShared S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    PixStage &S = stage[warp];
-    const uint32_t n_buckets = st->n_buckets;
     const uint32_t lt_mask = (1u << lane) - 1u;
 
-    const uint32_t n_warps = gridDim.x * kBwdWarps;
-    for (uint32_t b = blockIdx.x * kBwdWarps + warp; b < n_buckets; b += n_warps) {
-        const int t = find_tile(bucket_off, views.total_tiles, b);
-        const uint32_t j0 = (b - bucket_off[t]) * kBucket;
-        if (j0 >= tile_maxc[t]) continue;  // no pixel blended anything at or after j0
+    for (int t = blockIdx.x; t < views.total_tiles; t += gridDim.x) {
         const uint2 range = ranges[t];
-        const int nsplat = min((int)(range.y - range.x) - (int)j0, kBucket);
-        const bool valid = lane < nsplat;
+        const uint32_t maxc = min(tile_maxc[t], range.y - range.x);
+        const uint32_t nb = (maxc + kBucket - 1) / kBucket;  // buckets that hold blended splats
+        if (nb == 0) continue;  // uniform
         int v = 0;
         while (v + 1 < views.V && t >= views.v[v + 1].tile_off) ++v;
         const ViewDev &cam = views.v[v];
@@ -66,113 +94,114 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
         const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
         const size_t npix = (size_t)cam.W * cam.H;
         const size_t base = (size_t)cam.pix_off;
-        const float *ckb = ckpt + (size_t)b * (kCkptCh * kTilePix);
 
-        // ---- stage the pixels still running at j0, compacted in pixel order
-        int m_total = 0;
-        for (int p0 = 0; p0 < kTilePix; p0 += 32) {
-            const int p = p0 + lane;
+        // ---- the tile's pixels, shared by the CTA's warps
+        for (int p = threadIdx.x; p < kTilePix; p += kBwdThreads) {
             const int ix = tx * kTile + (p & (kTile - 1)), iy = ty * kTile + (p >> 4);
-            bool alive = false;
-            uint32_t nc = 0;
-            size_t pix = 0;
+            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 fin = make_float2(0.f, __uint_as_float(0u));
             if (ix < cam.W && iy < cam.H) {
-                pix = (size_t)iy * cam.W + ix;
-                nc = n_contrib[base + pix];
-                alive = nc > j0;
+                const size_t pix = (size_t)iy * cam.W + ix;
+                g.x = dL_drgb[3 * base + pix];
+                g.y = dL_drgb[3 * base + npix + pix];
+                g.z = dL_drgb[3 * base + 2 * npix + pix];
+                g.w = dL_ddisp ? dL_ddisp[base + pix] : 0.0f;
+                fin.x = g.x * img_rgb[3 * base + pix] + g.y * img_rgb[3 * base + npix + pix] +
+                        g.z * img_rgb[3 * base + 2 * npix + pix] + (dL_ddisp ? g.w * img_disp[base + pix] : 0.0f);
+                fin.y = __uint_as_float(n_contrib[base + pix]);
             }
-            const uint32_t bal = __ballot_sync(0xffffffffu, alive);
-            if (alive) {
-                const int m = m_total + __popc(bal & lt_mask);
-                const float gr = dL_drgb[3 * base + pix];
-                const float gg = dL_drgb[3 * base + npix + pix];
-                const float gb = dL_drgb[3 * base + 2 * npix + pix];
-                const float gd = dL_ddisp ? dL_ddisp[base + pix] : 0.0f;
-                const float sfin = gr * img_rgb[3 * base + pix] + gg * img_rgb[3 * base + npix + pix] +
-                                   gb * img_rgb[3 * base + 2 * npix + pix] +
-                                   (dL_ddisp ? gd * img_disp[base + pix] : 0.0f);
-                const float sck = gr * ckb[kTilePix + p] + gg * ckb[2 * kTilePix + p] +
-                                  gb * ckb[3 * kTilePix + p] + gd * ckb[4 * kTilePix + p];
-                S.g[m] = make_float4(gr, gg, gb, gd);
-                S.fin[m] = make_float2(sfin, __uint_as_float(nc));
-                S.ck[m] = make_float2(ckb[p], sck);
-                S.pix[m] = (uint8_t)p;
-            }
-            m_total += __popc(bal);
+            S.g[p] = g;
+            S.fin[p] = fin;
         }
-        __syncwarp();
+        if (threadIdx.x == 0) S.next = kBwdWarps;  // buckets 0..kBwdWarps-1 are taken
+        __syncthreads();
 
-        // ---- this lane's splat
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
-        uint32_t item = 0;
-        if (valid) {
-            item = inst_item[range.x + j0 + lane];
-            r0 = rec[3 * (size_t)item];
-            r1 = rec[3 * (size_t)item + 1];
-            r2 = rec[3 * (size_t)item + 2];
-            // the same tile-local mean the forward staged
-            const float2 m = tile_local_mean(r0, r1.w, r2.w, (float)(tx * kTile), (float)(ty * kTile));
-            r0.x = m.x;
-            r0.y = m.y;
-        }
-        const uint32_t k = j0 + (uint32_t)lane;
-        float g_mx = 0.f, g_my = 0.f, g_xx = 0.f, g_xy = 0.f, g_yy = 0.f, g_pw = 0.f;
-        float g_r = 0.f, g_g = 0.f, g_b = 0.f, g_iz = 0.f;
-        float T_out = 0.f, S_out = 0.f;
-
-        for (int s = 0; s < m_total + 31; ++s) {
-            float T_in = __shfl_up_sync(0xffffffffu, T_out, 1);
-            float S_in = __shfl_up_sync(0xffffffffu, S_out, 1);
-            const int m = s - lane;
-            if (lane == 0 && m < m_total) {
-                const float2 c = S.ck[m];
-                T_in = c.x;
-                S_in = c.y;
+        // ---- the warps take the tile's buckets greedily (the first, fullest
+        // buckets first) without synchronising until the tile is done
+        for (uint32_t lb = warp; lb < nb;) {
+            const uint32_t j0 = lb * kBucket;
+            // pixels still running at j0, compacted, seeded from the checkpoint
+            const float *ckb = ckpt + (size_t)(bucket_off[t] + lb) * (kCkptCh * kTilePix);
+            int m_total = 0;
+            for (int p0 = 0; p0 < kTilePix; p0 += 32) {
+                const int p = p0 + lane;
+                const bool alive = __float_as_uint(S.fin[p].y) > j0;
+                const uint32_t bal = __ballot_sync(0xffffffffu, alive);
+                if (alive) {
+                    const int m = m_total + __popc(bal & lt_mask);
+                    const float4 g = S.g[p];
+                    const float sck = g.x * ckb[kTilePix + p] + g.y * ckb[2 * kTilePix + p] +
+                                      g.z * ckb[3 * kTilePix + p] + g.w * ckb[4 * kTilePix + p];
+                    S.ck[warp][m] = make_float2(ckb[p], sck);
+                    S.pix[warp][m] = (uint8_t)p;
+                }
+                m_total += __popc(bal);
             }
-            T_out = T_in;
-            S_out = S_in;
-            if (valid && m >= 0 && m < m_total) {
-                const float2 fin = S.fin[m];
-                if (k < __float_as_uint(fin.y)) {
-                    const int p = S.pix[m];
-                    const float px = (float)(p & (kTile - 1)) + 0.5f, py = (float)(p >> 4) + 0.5f;
-                    PairEval e;
-                    eval_pair(r0, r1, px, py, e);
-                    if (e.power2 <= 0.0f && e.alpha >= kAlphaMin) {
-                        const float4 g = S.g[m];
-                        const float w = e.alpha * T_in;
-                        const float gdot = g.x * r2.x + g.y * r2.y + g.z * r2.z + g.w * r1.z;
-                        g_r += w * g.x;
-                        g_g += w * g.y;
-                        g_b += w * g.z;
-                        g_iz += w * g.w;
-                        S_out = S_in + w * gdot;
-                        T_out = T_in * (1.0f - e.alpha);
-                        if (e.raw <= kAlphaMax) {  // the clamp passes no gradient
-                            const float dL_da = T_in * gdot - (fin.x - S_out) / (1.0f - e.alpha);
-                            const float dpw = dL_da * e.raw;  // dL/dpower (natural log units)
-                            g_pw += dpw;
-                            g_mx += dpw * (r0.z * e.dx + r0.w * e.dy);
-                            g_my += dpw * (r0.w * e.dx + r1.x * e.dy);
-                            g_xx += dpw * e.dx * e.dx;
-                            g_xy += dpw * e.dx * e.dy;
-                            g_yy += dpw * e.dy * e.dy;
-                        }
+            __syncwarp();
+
+            // this lane's splat, in the tile-local frame of the forward
+            const int nsplat = min((int)(range.y - range.x) - (int)j0, kBucket);
+            const bool valid = lane < nsplat;
+            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+            uint32_t item = 0;
+            if (valid) {
+                item = inst_item[range.x + j0 + lane];
+                r0 = rec[3 * (size_t)item];
+                r1 = rec[3 * (size_t)item + 1];
+                r2 = rec[3 * (size_t)item + 2];
+                const float2 mm = tile_local_mean(r0, r1.w, r2.w, (float)(tx * kTile), (float)(ty * kTile));
+                r0.x = mm.x;
+                r0.y = mm.y;
+            }
+            const uint32_t k = j0 + (uint32_t)lane;
+            SplatGrad acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            // two independent pixel chains (first and second half of the
+            // compacted list) interleave to hide the shuffle latency
+            const int h = (m_total + 1) >> 1;
+            float TA = 0.f, SA = 0.f, TB = 0.f, SB = 0.f;
+            for (int s = 0; s < h + 31; ++s) {
+                float tA = __shfl_up_sync(0xffffffffu, TA, 1);
+                float sA = __shfl_up_sync(0xffffffffu, SA, 1);
+                float tB = __shfl_up_sync(0xffffffffu, TB, 1);
+                float sB = __shfl_up_sync(0xffffffffu, SB, 1);
+                const int mA = s - lane, mB = h + s - lane;
+                if (lane == 0) {
+                    if (mA < h) {
+                        const float2 c = S.ck[warp][mA];
+                        tA = c.x;
+                        sA = c.y;
+                    }
+                    if (mB < m_total) {
+                        const float2 c = S.ck[warp][mB];
+                        tB = c.x;
+                        sB = c.y;
                     }
                 }
+                TA = tA;
+                SA = sA;
+                TB = tB;
+                SB = sB;
+                if (valid && mA >= 0) {
+                    if (mA < h) bwd_pair(S, warp, mA, k, r0, r1, r2, TA, SA, acc);
+                    if (mB < m_total) bwd_pair(S, warp, mB, k, r0, r1, r2, TB, SB, acc);
+                }
             }
+            if (valid) {
+                // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2 and (A, B, C) = kH (a, b, c):
+                //   d power / d mx = (A dx + B dy) / kH, d power / d a = -dx^2 / 2, ...
+                //   d alpha / d o = alpha_raw / o, so dL/do = sum(dL/dpower) / o
+                const float inv_o = fast_exp2(-r1.y);
+                float4 *gp = grad2d + 3 * (size_t)item;
+                atomicAdd(gp, make_float4(acc.mx * kInvH, acc.my * kInvH, -0.5f * acc.xx, -acc.xy));
+                atomicAdd(gp + 1, make_float4(-0.5f * acc.yy, acc.pw * inv_o, acc.iz, 0.0f));
+                atomicAdd(gp + 2, make_float4(acc.r, acc.g, acc.b, 0.0f));
+            }
+            __syncwarp();  // the next bucket overwrites this warp's lists
+            uint32_t next = 0;
+            if (lane == 0) next = atomicAdd(&S.next, 1u);
+            lb = __shfl_sync(0xffffffffu, next, 0);
         }
-        if (valid) {
-            // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2 and (A, B, C) = kH (a, b, c):
-            //   d power / d mx = (A dx + B dy) / kH, d power / d a = -dx^2 / 2, ...
-            //   d alpha / d o = alpha_raw / o = dpower-weight / o
-            const float inv_o = fast_exp2(-r1.y);
-            float4 *gp = grad2d + 3 * (size_t)item;
-            atomicAdd(gp, make_float4(g_mx * kInvH, g_my * kInvH, -0.5f * g_xx, -g_xy));
-            atomicAdd(gp + 1, make_float4(-0.5f * g_yy, g_pw * inv_o, g_iz, 0.0f));
-            atomicAdd(gp + 2, make_float4(g_r, g_g, g_b, 0.0f));
-        }
-        __syncwarp();
+        __syncthreads();  // the next tile overwrites the staging
     }
 }
 
@@ -189,19 +218,22 @@ extern "C" int gs_render_bwd_blend(const gs_plan *plan, void *ws, const float *d
                                    const float *d_dL_drgb, const float *d_dL_ddisp, void *stream) {
     if (!plan || !ws || !d_rgb || !d_disp || !d_dL_drgb) return GS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    StatusDev *st = ws_at<StatusDev>(ws, plan->o_status);
     float4 *g2d = ws_at<float4>(ws, plan->o_grad2d);
     int rc = check_cuda(cudaMemsetAsync(g2d, 0, (size_t)plan->VN * 3 * sizeof(float4), s));
     if (rc) return rc;
     const ViewsDev vd = make_views(plan, nullptr);
-    int dev = 0, sms = 152;
+    // persistent grid: as many CTAs as fit on the device at once
+    int dev = 0, sms = 152, per_sm = 8;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_render_bwd<<<sms * 8, kBwdThreads, 0, s>>>(
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd, kBwdThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 8;
+    k_render_bwd<<<sms * per_sm, kBwdThreads, 0, s>>>(
         vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
         ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off),
         ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt),
-        ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, st, g2d);
+        ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d);
     return launch_error();
 }
 
