@@ -351,11 +351,11 @@ def run_ours(args, rank, world):
         cam = cams[0]
         n_threads = os.cpu_count() or 1
         target = synth.target_uniform(1000, cam.width, cam.height)
-        est, detail = oracle_sample(scene_h, cam, target, window_px=64, pre_sample=1 << 17, n_threads=n_threads)
+        est, detail = oracle_sample(scene_h, cam, target, window_px=128, pre_sample=1 << 18, n_threads=n_threads)
         line["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": n_threads, "kind": "oracle",
-                                "sample": "preprocess fwd+bwd and Adam on 131072 random Gaussians (x N/131072), "
-                                          "blend fwd + loss + per-pixel bwd on a 64x64 centre window "
-                                          "(x H*W/4096); float64",
+                                "sample": "preprocess fwd+bwd and Adam on 262144 random Gaussians (x N/262144), "
+                                          "blend fwd + loss + per-pixel bwd on a 128x128 centre window "
+                                          "(x H*W/16384); float64",
                                 "detail": detail}
     print(json.dumps(line), flush=True)
 
