@@ -11,6 +11,7 @@ from .scenes import (  # noqa: F401
     camera_c1,
     ring_cameras,
     mixed_ring_cameras,
+    ng_anchors,
     scene_c1,
     scene_clustered,
     scene_tiny,

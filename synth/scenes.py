@@ -225,3 +225,27 @@ def upstream_grads(seed: int, width: int, height: int) -> tuple[np.ndarray, np.n
     g = rng.normal(0.0, 1.0, size=(3, height, width)).astype(np.float32)
     gd = rng.normal(0.0, 1.0, size=(height, width)).astype(np.float32)
     return g, gd
+
+
+def ng_anchors(points: np.ndarray, n_anchors: int, seed: int = 0, feat_dim: int = 32, hidden: int = 32,
+               k_children: int = 10) -> dict:
+    """Seeded neural-Gaussian anchor set: positions subsampled from `points`,
+    features N(0, 0.1), offset log-scale log(0.02), child log-scale log(0.01),
+    MLP weights N(0, 1 / fan_in), biases 0 except the rotation outputs'
+    first component (1: identity rotation) and the opacity outputs (0.5)."""
+    rng = _rng(seed)
+    idx = rng.choice(points.shape[0], size=n_anchors, replace=False)
+    xyz = points[idx].astype(np.float32)
+    feat = rng.normal(0.0, 0.1, size=(n_anchors, feat_dim)).astype(np.float32)
+    ls = np.empty((n_anchors, 6), dtype=np.float32)
+    ls[:, 0:3] = np.log(0.02)
+    ls[:, 3:6] = np.log(0.01)
+    in_dim = feat_dim + 3
+    out_dim = k_children * 14
+    w1 = (rng.normal(0.0, 1.0, size=(hidden, in_dim)) / np.sqrt(in_dim)).astype(np.float32)
+    b1 = np.zeros(hidden, dtype=np.float32)
+    w2 = (rng.normal(0.0, 1.0, size=(out_dim, hidden)) / np.sqrt(hidden)).astype(np.float32)
+    b2 = np.zeros(out_dim, dtype=np.float32)
+    b2.reshape(k_children, 14)[:, 10] = 1.0
+    b2.reshape(k_children, 14)[:, 3] = 0.5
+    return {"anchor_xyz": xyz, "feat": feat, "anchor_ls": ls, "w1": w1, "b1": b1, "w2": w2, "b2": b2}
