@@ -246,6 +246,52 @@ GS_API int gs_sort_pairs_u32(uint32_t *d_keys_in, uint32_t *d_vals_in, uint32_t 
                              uint32_t *d_vals_out, int64_t n, int32_t begin_bit, int32_t end_bit,
                              void *d_scratch, void *stream);
 
+/* ------------------------------------------ a10: neural-Gaussian decoder
+ * Sec. 2.3: anchors with learnable features and a shallow MLP shared by all
+ * anchors infer the attributes of the anchors' child Gaussians; only the
+ * features (and the anchors' log-scales) and the MLP are trained.  The paper
+ * fixes no architecture; this library's decoder is
+ *   x = [feature (32), unit view direction anchor - camera centre (3)]
+ *   h = ReLU(W1 x + b1) (32),  y = W2 h + b2 (140 = 10 children x 14)
+ *   per child (u = its 14 outputs): mean = anchor + tanh(u0..2) e^{s_off},
+ *   opacity = tanh(u3) (children with opacity <= 0 are not rendered),
+ *   colour = sigmoid(u4..6), log-scale = s_scale + log sigmoid(u7..9),
+ *   rotation = u10..13.
+ * The GEMMs run on the tensor cores with bf16 operands (features, view
+ * direction, weights, h; in the backward dL/dy and dL/dh) and fp32 sums. */
+#define GS_NG_FEAT 32
+#define GS_NG_HIDDEN 32
+#define GS_NG_CHILDREN 10
+
+typedef struct {
+    int64_t n_anchors;
+    float *anchor_xyz;  /* device, n x 3 (fixed; no gradient) */
+    float *feat;        /* device, n x 32 */
+    float *anchor_ls;   /* device, n x 6: offset log-scales (3), child log-scales (3) */
+    float *w1, *b1;     /* device, 32 x 35 (row-major, output-major), 32 */
+    float *w2, *b2;     /* device, 140 x 32, 140 */
+} gs_ng_params;
+
+/* Device workspace the decoder needs for n anchors (bf16 weights, the hidden
+ * activations kept from the forward for the backward, per-CTA partial sums
+ * of the weight gradients, a status word). */
+GS_API size_t gs_ng_workspace_bytes(int64_t n_anchors);
+/* Decode the children for one camera into `children` (n = 10 * n_anchors,
+ * sh_degree 0; arrays overwritten): child i of anchor a is Gaussian 10 a + i,
+ * its opacity as a logit (-30 when opacity <= 0) and its colour as the SH DC
+ * coefficient (colour - 0.5) * 2 sqrt(pi). */
+GS_API int gs_ng_decode_fwd(const gs_ng_params *ng, const gs_camera *h_cam, gs_params *children, void *d_ws,
+                            void *stream);
+/* Backward of gs_ng_decode_fwd for the same camera and workspace: maps the
+ * children's parameter gradients to the anchors' feature and log-scale
+ * gradients and the MLP gradients, ACCUMULATED (+=) into `grads` (its
+ * anchor_xyz may be NULL). */
+GS_API int gs_ng_decode_bwd(const gs_ng_params *ng, const gs_camera *h_cam, const gs_params *child_grads,
+                            gs_ng_params *grads, void *d_ws, void *stream);
+/* Synchronise `stream` and read the decoder's device status (GS_ERR_TIMEOUT
+ * if a bounded wait for the tensor cores gave up). */
+GS_API int gs_ng_read_status(void *d_ws, int32_t *out_error, void *stream);
+
 /* The same sort for callers that cannot allocate device memory, such as code
  * running inside a CUDA graph capture in global mode (where cudaMalloc is
  * refused), plug-ins whose host framework owns all device memory through its

@@ -84,6 +84,7 @@ def decode_forward(anchor_xyz, feat, anchor_ls, w1, b1, w2, b2, campos, bf16: bo
     x = torch.cat([_maybe(feat, bf16), _maybe(d, bf16)], 1)
     w1r, w2r = _maybe(w1, bf16), _maybe(w2, bf16)
     h_pre = x @ w1r.T + b1
+    h_absum = x.abs() @ w1r.abs().T + b1.abs()  # scale of the float32 rounding of h_pre
     h = _maybe(torch.clamp(h_pre, min=0.0), bf16)
     y = h @ w2r.T + b2
     u = y.reshape(A, K_CHILD, OUT_PER_CHILD)
@@ -102,7 +103,8 @@ def decode_forward(anchor_xyz, feat, anchor_ls, w1, b1, w2, b2, campos, bf16: bo
         "sh": ((rgb - 0.5) * DC_SCALE).reshape(-1, 1, 3),
     }
     cache = {k: v.detach() for k, v in {"x": x, "h_pre": h_pre, "h": h, "y": y, "u": u, "o": o, "rgb": rgb,
-                                         "off": off, "s_off": s_off, "w1r": w1r, "w2r": w2r}.items()}
+                                         "off": off, "s_off": s_off, "w1r": w1r, "w2r": w2r,
+                                         "h_absum": h_absum}.items()}
     cache["A"] = A
     return out, cache
 
@@ -142,4 +144,18 @@ def decode_backward(cache, grads: dict, bf16: bool = True) -> dict:
         "b2": dy.sum(0).numpy().copy(),
         "w1": (dh_r.T @ cache["x"]).numpy().copy(),
         "b1": dh_pre.sum(0).numpy().copy(),
+        "_dy": dy.numpy().copy(),
+        "_dh_pre": dh_pre.numpy().copy(),
+        "_dh_absum": (dy_r.abs() @ cache["w2r"].abs()).numpy().copy(),
     }
+
+
+def bf16_midpoint_distance(v) -> np.ndarray:
+    """Absolute distance of v to the nearest bfloat16 rounding midpoint (a
+    float32 evaluation of v that is off by less than this rounds to the same
+    bfloat16 value)."""
+    a = np.asarray(v, dtype=np.float64)
+    m, e = np.frexp(a)
+    t = np.abs(m) * 256.0
+    frac = t - np.floor(t)
+    return np.where(a != 0.0, np.abs(frac - 0.5) * np.ldexp(1.0, e - 8), np.inf)

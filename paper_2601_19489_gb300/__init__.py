@@ -21,4 +21,9 @@ from .api import (  # noqa: F401
     gs_render_bwd,
     gs_render_fwd,
     gs_sort_pairs_u32,
+    NgParams,
+    gs_ng_decode_bwd,
+    gs_ng_decode_fwd,
+    gs_ng_workspace,
+    ng_children,
 )

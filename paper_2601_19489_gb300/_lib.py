@@ -15,6 +15,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgs.so")
 
 GS_MAX_VIEWS = 16
+GS_NG_FEAT = 32
+GS_NG_HIDDEN = 32
+GS_NG_CHILDREN = 10
 GS_TILE = 16
 GS_BUCKET = 32
 
@@ -29,6 +32,7 @@ EXPORTS = (
     "gs_render_fwd", "gs_render_bwd", "gs_render_bwd_blend", "gs_preprocess_bwd",
     "gs_loss_scratch_floats", "gs_loss", "gs_adam_step",
     "gs_adam_step_multi", "gs_sort_scratch_bytes", "gs_sort_pairs_u32", "gs_sort_pairs_u32_noalloc",
+    "gs_ng_workspace_bytes", "gs_ng_decode_fwd", "gs_ng_decode_bwd", "gs_ng_read_status",
 )
 
 
@@ -55,6 +59,12 @@ class GsAdamGroup(ctypes.Structure):
     _fields_ = [("p", ctypes.c_void_p), ("g", ctypes.c_void_p), ("m", ctypes.c_void_p),
                 ("v", ctypes.c_void_p), ("n", ctypes.c_int64), ("lr", ctypes.c_float),
                 ("period", ctypes.c_int64), ("head", ctypes.c_int64), ("lr_head", ctypes.c_float)]
+
+
+class GsNgParams(ctypes.Structure):
+    _fields_ = [("n_anchors", ctypes.c_int64), ("anchor_xyz", ctypes.c_void_p), ("feat", ctypes.c_void_p),
+                ("anchor_ls", ctypes.c_void_p), ("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p),
+                ("w2", ctypes.c_void_p), ("b2", ctypes.c_void_p)]
 
 
 class GsError(RuntimeError):
@@ -95,6 +105,11 @@ _SIGS = {
                                          P, P]),
     "gs_sort_pairs_u32_noalloc": (ctypes.c_int, [P, P, P, P, ctypes.c_int64, ctypes.c_int32,
                                                  ctypes.c_int32, P]),
+    "gs_ng_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
+    "gs_ng_decode_fwd": (ctypes.c_int, [ctypes.POINTER(GsNgParams), P, ctypes.POINTER(GsParams), P, P]),
+    "gs_ng_decode_bwd": (ctypes.c_int, [ctypes.POINTER(GsNgParams), P, ctypes.POINTER(GsParams),
+                                        ctypes.POINTER(GsNgParams), P, P]),
+    "gs_ng_read_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), P]),
 }
 
 

@@ -213,3 +213,75 @@ def gs_sort_pairs_u32(keys_in, vals_in, keys_out, vals_out, begin_bit: int, end_
     L.check(L.lib().gs_sort_pairs_u32(_ptr(keys_in, None), _ptr(vals_in, None), _ptr(keys_out, None),
                                       _ptr(vals_out, None), n, int(begin_bit), int(end_bit),
                                       _ptr(scratch, None), _stream(stream)), "gs_sort_pairs_u32")
+
+
+# ------------------------------------------------------ neural Gaussians
+
+@dataclass
+class NgParams:
+    """Anchor set and MLP of the neural-Gaussian decoder (float32, device)."""
+
+    anchor_xyz: torch.Tensor
+    feat: torch.Tensor
+    anchor_ls: torch.Tensor
+    w1: torch.Tensor
+    b1: torch.Tensor
+    w2: torch.Tensor
+    b2: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.anchor_xyz.shape[0])
+
+    def tensors(self):
+        return (self.anchor_xyz, self.feat, self.anchor_ls, self.w1, self.b1, self.w2, self.b2)
+
+    def struct(self) -> L.GsNgParams:
+        p = L.GsNgParams()
+        p.n_anchors = self.n
+        p.anchor_xyz = None if self.anchor_xyz is None else _ptr(self.anchor_xyz)
+        p.feat, p.anchor_ls, p.w1, p.b1, p.w2, p.b2 = (_ptr(t) for t in self.tensors()[1:])
+        return p
+
+    def zeros_like(self) -> "NgParams":
+        return NgParams(*(torch.zeros_like(t) for t in self.tensors()))
+
+    @staticmethod
+    def from_dict(d: dict, device="cuda") -> "NgParams":
+        t = lambda a: torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
+        return NgParams(t(d["anchor_xyz"]), t(d["feat"]), t(d["anchor_ls"]), t(d["w1"]), t(d["b1"]), t(d["w2"]),
+                        t(d["b2"]))
+
+
+def gs_ng_workspace(n_anchors: int, device="cuda") -> torch.Tensor:
+    ws = torch.zeros(int(L.lib().gs_ng_workspace_bytes(int(n_anchors))), dtype=torch.uint8, device=device)
+    return ws
+
+
+def ng_children(n_anchors: int, device="cuda") -> "Gaussians":
+    n = n_anchors * L.GS_NG_CHILDREN
+    z = lambda *s: torch.zeros(*s, device=device)
+    return Gaussians(z(n, 3), z(n, 3), z(n, 4), z(n), z(n, 1, 3), 0)
+
+
+def gs_ng_decode_fwd(ng: NgParams, cam, children: "Gaussians", ws: torch.Tensor, stream=None) -> None:
+    c = (L.GsCamera * 1)(camera_struct(cam))
+    p = ng.struct()
+    ch = children.struct()
+    L.check(L.lib().gs_ng_decode_fwd(ctypes.byref(p), c, ctypes.byref(ch), ws.data_ptr(), _stream(stream)),
+            "gs_ng_decode_fwd")
+
+
+def gs_ng_decode_bwd(ng: NgParams, cam, child_grads: "Gaussians", grads: NgParams, ws: torch.Tensor,
+                     stream=None) -> None:
+    c = (L.GsCamera * 1)(camera_struct(cam))
+    p = ng.struct()
+    cg = child_grads.struct()
+    g = grads.struct()
+    L.check(L.lib().gs_ng_decode_bwd(ctypes.byref(p), c, ctypes.byref(cg), ctypes.byref(g), ws.data_ptr(),
+                                     _stream(stream)), "gs_ng_decode_bwd")
+
+
+def gs_ng_status(ws: torch.Tensor, stream=None) -> int:
+    e = ctypes.c_int32(0)
+    return int(L.lib().gs_ng_read_status(ws.data_ptr(), ctypes.byref(e), _stream(stream)))

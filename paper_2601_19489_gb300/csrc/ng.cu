@@ -1,0 +1,724 @@
+// a10: neural-Gaussian decoder (Sec. 2.3) on the 5th-generation tensor cores.
+//
+// An anchor carries a feature f (32), an offset log-scale (3) and a child
+// log-scale (3); a shallow MLP shared by all anchors maps x = [f, view
+// direction] (35) through h = ReLU(W1 x + b1) (32) to y = W2 h + b2 (140),
+// 14 outputs for each of 10 child Gaussians:
+//   mean = anchor + tanh(y0..2) e^{s_off};  opacity = tanh(y3) (children with
+//   opacity <= 0 are not rendered);  colour = sigmoid(y4..6);
+//   log-scale = s_scale + log sigmoid(y7..9);  rotation = y10..13.
+// The children are written as ordinary Gaussian parameters (opacity logit,
+// SH degree 0) for the splatting step, and the backward maps the children's
+// parameter gradients back to the anchors and the MLP.
+//
+// Both GEMMs of the forward and both per-anchor GEMMs of the backward run as
+// tcgen05.mma kind::f16 (bf16 operands, fp32 accumulators in tensor memory),
+// M = 128 anchors per CTA, operands staged in shared memory in the canonical
+// no-swizzle K-major layout (8 x 16-byte core matrices).  One thread issues
+// the MMAs; tcgen05.commit arrives on an mbarrier that the CTA waits on with
+// a bounded spin.  The weight gradients (sums over anchors) are formed per CTA
+// on the CUDA cores and reduced over CTAs in a fixed order.
+#include <cuda_bf16.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace ng {
+
+constexpr int kTileA = 128;             // anchors per CTA = UMMA M
+constexpr int kFeat = GS_NG_FEAT;       // 32
+constexpr int kIn = kFeat + 3;          // 35
+constexpr int kInPad = 48;              // GEMM 1 K (3 x 16)
+constexpr int kHid = GS_NG_HIDDEN;      // 32
+constexpr int kChild = GS_NG_CHILDREN;  // 10
+constexpr int kPer = 14;                // outputs per child
+constexpr int kOut = kChild * kPer;     // 140
+constexpr int kOutPad = 144;            // GEMM 2 N, backward GEMM K (9 x 16)
+constexpr int kThreads = 128;
+constexpr int kTmemCols = 256;
+constexpr float kLogitFloor = -30.0f;
+constexpr float kOpacityCeil = 1.0f - 1e-6f;
+constexpr float kDcScale = 3.5449077018110318f;  // 2 sqrt(pi): SH DC coefficient per unit colour
+constexpr int kPartial = kOut * kHid + kHid * kIn + kOut + kHid;  // dW2, dW1, db2, db1 per CTA
+constexpr long long kWaitLimit = 1ll << 22;                       // bounded mbarrier spin
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, int ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, int ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Wait for the mbarrier phase with the given parity; false after kWaitLimit tries.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading
+// (K-direction) and stride (8-row direction) byte offsets, version 1.
+__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint32_t sbo) {
+    const uint32_t a = smem_u32(p);
+    uint64_t d = (uint64_t)((a & 0x3ffffu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3fffu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3fffu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Element (r, k) of an R x K bf16 operand in the canonical no-swizzle
+// K-major layout: 8 x 8 core matrices of 128 contiguous bytes, the K chunks of
+// a row group adjacent (LBO = 128 B), row groups K * 16 B apart (SBO).
+__host__ __device__ constexpr int canon(int r, int k, int K) {
+    return (r >> 3) * (K * 8) + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// log(sigmoid(x)) = -softplus(-x), stable for large |x|
+__device__ __forceinline__ float log_sigmoidf(float x) {
+    return x >= 0.0f ? -log1pf(expf(-x)) : x - log1pf(expf(x));
+}
+
+struct Args {
+    int64_t n;  // anchors
+    const float *xyz, *feat, *ls, *b1, *b2;
+    float cam[3];
+    const __nv_bfloat16 *w1b, *w2b, *w2tb, *w1tb;  // prepared bf16 weights (row-major, padded)
+    __nv_bfloat16 *h_store;                        // bf16 h per anchor (forward -> backward)
+    // forward outputs (children)
+    float *c_means, *c_ls, *c_quats, *c_logits, *c_sh;
+    // backward inputs (children's gradients) and outputs
+    const float *g_means, *g_ls, *g_quats, *g_logits, *g_sh;
+    float *d_feat, *d_ls, *partial;
+    int *err;
+};
+
+// ------------------------------------------------------------ weight prep
+__global__ void __launch_bounds__(256) k_ng_prep(const float *__restrict__ w1, const float *__restrict__ w2,
+                                                 __nv_bfloat16 *w1b, __nv_bfloat16 *w2b, __nv_bfloat16 *w2tb,
+                                                 __nv_bfloat16 *w1tb) {
+    for (int i = threadIdx.x; i < kHid * kInPad; i += blockDim.x) {  // W1 (32 x 48), K-major in the input
+        const int r = i / kInPad, k = i % kInPad;
+        w1b[i] = __float2bfloat16_rn(k < kIn ? w1[r * kIn + k] : 0.0f);
+    }
+    for (int i = threadIdx.x; i < kOutPad * kHid; i += blockDim.x) {  // W2 (144 x 32)
+        const int r = i / kHid, k = i % kHid;
+        w2b[i] = __float2bfloat16_rn(r < kOut ? w2[r * kHid + k] : 0.0f);
+    }
+    for (int i = threadIdx.x; i < kHid * kOutPad; i += blockDim.x) {  // W2^T (32 x 144)
+        const int r = i / kOutPad, k = i % kOutPad;
+        w2tb[i] = __float2bfloat16_rn(k < kOut ? w2[k * kHid + r] : 0.0f);
+    }
+    for (int i = threadIdx.x; i < kInPad * kHid; i += blockDim.x) {  // W1^T (48 x 32)
+        const int r = i / kHid, k = i % kHid;
+        w1tb[i] = __float2bfloat16_rn(r < kIn ? w1[k * kIn + r] : 0.0f);
+    }
+}
+
+// x row of anchor a (bf16-rounded feature and view direction, zero padded)
+__device__ __forceinline__ void anchor_input(const Args &A, int64_t a, bool valid, float *x) {
+    if (!valid) {
+#pragma unroll
+        for (int k = 0; k < kInPad; ++k) x[k] = 0.0f;
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < kFeat; ++k) x[k] = bf16r(A.feat[a * kFeat + k]);
+    float d0 = A.xyz[3 * a] - A.cam[0], d1 = A.xyz[3 * a + 1] - A.cam[1], d2 = A.xyz[3 * a + 2] - A.cam[2];
+    const float inv = 1.0f / sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    x[kFeat] = bf16r(d0 * inv);
+    x[kFeat + 1] = bf16r(d1 * inv);
+    x[kFeat + 2] = bf16r(d2 * inv);
+#pragma unroll
+    for (int k = kIn; k < kInPad; ++k) x[k] = 0.0f;
+}
+
+// ---------------------------------------------------------------- forward
+struct FwdSmem {
+    __nv_bfloat16 X[kTileA * kInPad];    // GEMM 1 A (M = 128, K = 48)
+    __nv_bfloat16 W1[kHid * kInPad];     // GEMM 1 B (N = 32, K = 48)
+    __nv_bfloat16 H[kTileA * kHid];      // GEMM 2 A (M = 128, K = 32)
+    __nv_bfloat16 W2[kOutPad * kHid];    // GEMM 2 B (N = 144, K = 32)
+    float Y[kTileA][kOutPad + 1];        // y = W2 h + b2
+    float xyz[kTileA][3], ls[kTileA][6];
+    uint64_t mbar;
+    uint32_t tmem;
+    int fail;
+};
+
+__global__ void __launch_bounds__(kThreads) k_ng_fwd(Args A) {
+    extern __shared__ uint8_t smem_raw[];
+    FwdSmem &S = *reinterpret_cast<FwdSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t a0 = (int64_t)blockIdx.x * kTileA;
+    const int64_t a = a0 + tid;
+    const bool valid = a < A.n;
+
+    if (warp == 0) tmem_alloc(&S.tmem, kTmemCols);
+    if (tid == 0) {
+        mbar_init(&S.mbar, 1);
+        S.fail = 0;
+    }
+    // operands
+    {
+        float x[kInPad];
+        anchor_input(A, a, valid, x);
+#pragma unroll
+        for (int k = 0; k < kInPad; ++k) S.X[canon(tid, k, kInPad)] = __float2bfloat16_rn(x[k]);
+    }
+    for (int i = tid; i < kHid * kInPad; i += kThreads) S.W1[canon(i / kInPad, i % kInPad, kInPad)] = A.w1b[i];
+    for (int i = tid; i < kOutPad * kHid; i += kThreads) S.W2[canon(i / kHid, i % kHid, kHid)] = A.w2b[i];
+    for (int j = 0; j < 3; ++j) S.xyz[tid][j] = valid ? A.xyz[3 * a + j] : 0.0f;
+    for (int j = 0; j < 6; ++j) S.ls[tid][j] = valid ? A.ls[6 * a + j] : 0.0f;
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+
+    // GEMM 1: D[0:32) = X W1^T
+    if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < kInPad / 16; ++kk)
+            mma_bf16(tmem, smem_desc(S.X + kk * 128, 128, kInPad * 16), smem_desc(S.W1 + kk * 128, 128, kInPad * 16),
+                     idesc_bf16(kTileA, kHid), kk > 0);
+        mma_commit(&S.mbar);
+    }
+    if (!mbar_wait(&S.mbar, 0)) S.fail = 1;
+    tc_fence_after();
+    __syncthreads();
+    if (S.fail) goto cleanup;
+    {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+#pragma unroll
+        for (int c = 0; c < kHid; ++c) {
+            const __nv_bfloat16 hb = __float2bfloat16_rn(fmaxf(v[c] + A.b1[c], 0.0f));
+            S.H[canon(tid, c, kHid)] = hb;
+            if (valid) A.h_store[a * kHid + c] = hb;
+        }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    // GEMM 2: D[32:176) = H W2^T
+    if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < kHid / 16; ++kk)
+            mma_bf16(tmem + 32, smem_desc(S.H + kk * 128, 128, kHid * 16), smem_desc(S.W2 + kk * 128, 128, kHid * 16),
+                     idesc_bf16(kTileA, kOutPad), kk > 0);
+        mma_commit(&S.mbar);
+    }
+    if (!mbar_wait(&S.mbar, 1)) S.fail = 1;
+    tc_fence_after();
+    __syncthreads();
+    if (S.fail) goto cleanup;
+    {
+        const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16) + 32;
+        float v[32];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            tmem_ld32(row + ch * 32, v);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) S.Y[tid][ch * 32 + c] = v[c] + (ch * 32 + c < kOut ? A.b2[ch * 32 + c] : 0.f);
+        }
+        tmem_ld16(row + 128, v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) S.Y[tid][128 + c] = v[c] + (128 + c < kOut ? A.b2[128 + c] : 0.f);
+    }
+    __syncthreads();
+    {
+        // children of the tile, written array by array so consecutive threads
+        // store consecutive floats
+        const int na = (int)min((int64_t)kTileA, A.n - a0);
+        const int nch = na * kChild;
+        const int64_t c0 = a0 * kChild;
+        for (int i = tid; i < nch * 3; i += kThreads) {
+            const int ch = i / 3, j = i - 3 * ch, r = ch / kChild, c = ch - r * kChild;
+            const float u = S.Y[r][c * kPer + j];
+            A.c_means[3 * c0 + i] = S.xyz[r][j] + tanhf(u) * expf(S.ls[r][j]);
+            A.c_ls[3 * c0 + i] = S.ls[r][3 + j] + log_sigmoidf(S.Y[r][c * kPer + 7 + j]);
+            A.c_sh[3 * c0 + i] = (sigmoidf_(S.Y[r][c * kPer + 4 + j]) - 0.5f) * kDcScale;
+        }
+        for (int i = tid; i < nch * 4; i += kThreads) {
+            const int ch = i >> 2, j = i & 3, r = ch / kChild, c = ch - r * kChild;
+            A.c_quats[4 * c0 + i] = S.Y[r][c * kPer + 10 + j];
+        }
+        for (int ch = tid; ch < nch; ch += kThreads) {
+            const int r = ch / kChild, c = ch - r * kChild;
+            const float o = tanhf(S.Y[r][c * kPer + 3]);
+            const float oc = fminf(o, kOpacityCeil);
+            A.c_logits[c0 + ch] = o > 0.0f ? logf(oc) - log1pf(-oc) : kLogitFloor;
+        }
+    }
+cleanup:
+    if (S.fail) {
+        // give the tensor cores one more bounded wait before the memory goes
+        if (tid == 0) atomicCAS(A.err, 0, GS_ERR_TIMEOUT);
+        mbar_wait(&S.mbar, 0);
+        mbar_wait(&S.mbar, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// --------------------------------------------------------------- backward
+struct BwdSmem {
+    __nv_bfloat16 H[kTileA * kHid];      // GEMM 2 A (recompute of y)
+    __nv_bfloat16 W2[kOutPad * kHid];    // GEMM 2 B
+    __nv_bfloat16 DY[kTileA * kOutPad];  // dh GEMM A (M = 128, K = 144)
+    __nv_bfloat16 W2T[kHid * kOutPad];   // dh GEMM B (N = 32, K = 144)
+    __nv_bfloat16 DH[kTileA * kHid];     // dx GEMM A (M = 128, K = 32)
+    __nv_bfloat16 W1T[kInPad * kHid];    // dx GEMM B (N = 48, K = 32)
+    float Y[kTileA][kOutPad + 1];        // y, then dL/dy (fp32)
+    float hf[kTileA][kHid + 1];          // h (bf16 values) as float
+    float dhf[kTileA][kHid + 1];         // dL/dh after the ReLU mask, rounded to bf16, as float
+    float x[kTileA][kIn + 1];            // x (bf16 values) as float
+    float xyz[kTileA][3], ls[kTileA][6], dls[kTileA][6];
+    float db1[kHid];
+    uint64_t mbar;
+    uint32_t tmem;
+    int fail;
+};
+
+__global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
+    extern __shared__ uint8_t smem_raw[];
+    BwdSmem &S = *reinterpret_cast<BwdSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t a0 = (int64_t)blockIdx.x * kTileA;
+    const int64_t a = a0 + tid;
+    const bool valid = a < A.n;
+    const int na = (int)min((int64_t)kTileA, A.n - a0);
+    float *part = A.partial + (size_t)blockIdx.x * kPartial;
+
+    if (warp == 0) tmem_alloc(&S.tmem, kTmemCols);
+    if (tid == 0) {
+        mbar_init(&S.mbar, 1);
+        S.fail = 0;
+    }
+    if (tid < kHid) S.db1[tid] = 0.0f;
+    {
+        float x[kInPad];
+        anchor_input(A, a, valid, x);
+#pragma unroll
+        for (int k = 0; k < kIn; ++k) S.x[tid][k] = x[k];
+#pragma unroll
+        for (int c = 0; c < kHid; ++c) {
+            const __nv_bfloat16 hb = valid ? A.h_store[a * kHid + c] : __float2bfloat16_rn(0.0f);
+            S.H[canon(tid, c, kHid)] = hb;
+            S.hf[tid][c] = __bfloat162float(hb);
+        }
+    }
+    for (int i = tid; i < kOutPad * kHid; i += kThreads) S.W2[canon(i / kHid, i % kHid, kHid)] = A.w2b[i];
+    for (int i = tid; i < kHid * kOutPad; i += kThreads) S.W2T[canon(i / kOutPad, i % kOutPad, kOutPad)] = A.w2tb[i];
+    for (int i = tid; i < kInPad * kHid; i += kThreads) S.W1T[canon(i / kHid, i % kHid, kHid)] = A.w1tb[i];
+    for (int j = 0; j < 3; ++j) S.xyz[tid][j] = valid ? A.xyz[3 * a + j] : 0.0f;
+    for (int j = 0; j < 6; ++j) {
+        S.ls[tid][j] = valid ? A.ls[6 * a + j] : 0.0f;
+        S.dls[tid][j] = 0.0f;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t my_lanes = tmem + ((uint32_t)(warp * 32) << 16);
+
+    // y = W2 h + b2, recomputed exactly as in the forward
+    if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < kHid / 16; ++kk)
+            mma_bf16(tmem, smem_desc(S.H + kk * 128, 128, kHid * 16), smem_desc(S.W2 + kk * 128, 128, kHid * 16),
+                     idesc_bf16(kTileA, kOutPad), kk > 0);
+        mma_commit(&S.mbar);
+    }
+    if (!mbar_wait(&S.mbar, 0)) S.fail = 1;
+    tc_fence_after();
+    __syncthreads();
+    if (S.fail) goto cleanup;
+    {
+        float v[32];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            tmem_ld32(my_lanes + ch * 32, v);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) S.Y[tid][ch * 32 + c] = v[c] + (ch * 32 + c < kOut ? A.b2[ch * 32 + c] : 0.f);
+        }
+        tmem_ld16(my_lanes + 128, v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) S.Y[tid][128 + c] = v[c] + (128 + c < kOut ? A.b2[128 + c] : 0.f);
+    }
+    tc_fence_before();
+    __syncthreads();
+    {
+        // dL/dy from the children's gradients, in place of y (every element
+        // depends on its own y only); anchor log-scale gradients in shared memory
+        const int nch = na * kChild;
+        const int64_t c0 = a0 * kChild;
+        for (int i = tid; i < nch * 3; i += kThreads) {
+            const int ch = i / 3, j = i - 3 * ch, r = ch / kChild, c = ch - r * kChild;
+            float &y0 = S.Y[r][c * kPer + j];
+            const float th = tanhf(y0), so = expf(S.ls[r][j]);
+            const float gm = A.g_means[3 * c0 + i];
+            atomicAdd(&S.dls[r][j], gm * th * so);
+            y0 = gm * so * (1.0f - th * th);
+            float &y4 = S.Y[r][c * kPer + 4 + j];
+            const float rgb = sigmoidf_(y4);
+            y4 = A.g_sh[3 * c0 + i] * kDcScale * rgb * (1.0f - rgb);
+            float &y7 = S.Y[r][c * kPer + 7 + j];
+            const float gl = A.g_ls[3 * c0 + i];
+            atomicAdd(&S.dls[r][3 + j], gl);
+            y7 = gl * sigmoidf_(-y7);
+        }
+        for (int i = tid; i < nch * 4; i += kThreads) {
+            const int ch = i >> 2, j = i & 3, r = ch / kChild, c = ch - r * kChild;
+            S.Y[r][c * kPer + 10 + j] = A.g_quats[4 * c0 + i];
+        }
+        for (int ch = tid; ch < nch; ch += kThreads) {
+            const int r = ch / kChild, c = ch - r * kChild;
+            float &y3 = S.Y[r][c * kPer + 3];
+            const float o = tanhf(y3);
+            const float oc = fminf(o, kOpacityCeil);
+            y3 = (o > 0.0f && o < kOpacityCeil) ? A.g_logits[c0 + ch] / (oc * (1.0f - oc)) * (1.0f - o * o) : 0.0f;
+        }
+        // rows of absent anchors and the padding columns carry no gradient
+        for (int i = tid; i < kTileA * kOutPad; i += kThreads) {
+            const int r = i / kOutPad, o = i - r * kOutPad;
+            if (r >= na || o >= kOut) S.Y[r][o] = 0.0f;
+        }
+    }
+    __syncthreads();
+    // db2 (unrounded dy) and the rounded dy as the dh GEMM operand
+    for (int o = tid; o < kOut; o += kThreads) {
+        float s = 0.0f;
+        for (int r = 0; r < kTileA; ++r) s += S.Y[r][o];
+        part[kOut * kHid + kHid * kIn + o] = s;
+    }
+    for (int i = tid; i < kTileA * kOutPad; i += kThreads) {
+        const int r = i / kOutPad, o = i - r * kOutPad;
+        S.DY[canon(r, o, kOutPad)] = __float2bfloat16_rn(S.Y[r][o]);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // dh = dy W2 (contraction over the 144 outputs)
+    if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < kOutPad / 16; ++kk)
+            mma_bf16(tmem, smem_desc(S.DY + kk * 128, 128, kOutPad * 16), smem_desc(S.W2T + kk * 128, 128, kOutPad * 16),
+                     idesc_bf16(kTileA, kHid), kk > 0);
+        mma_commit(&S.mbar);
+    }
+    if (!mbar_wait(&S.mbar, 1)) S.fail = 1;
+    tc_fence_after();
+    __syncthreads();
+    if (S.fail) goto cleanup;
+    {
+        float v[32];
+        tmem_ld32(my_lanes, v);
+#pragma unroll
+        for (int c = 0; c < kHid; ++c) {
+            const float dh = S.hf[tid][c] > 0.0f ? v[c] : 0.0f;
+            atomicAdd(&S.db1[c], dh);
+            const __nv_bfloat16 db = __float2bfloat16_rn(dh);
+            S.DH[canon(tid, c, kHid)] = db;
+            S.dhf[tid][c] = __bfloat162float(db);
+        }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // dx = dh W1 (contraction over the 32 hidden units)
+    if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < kHid / 16; ++kk)
+            mma_bf16(tmem + 32, smem_desc(S.DH + kk * 128, 128, kHid * 16), smem_desc(S.W1T + kk * 128, 128, kHid * 16),
+                     idesc_bf16(kTileA, kInPad), kk > 0);
+        mma_commit(&S.mbar);
+    }
+    if (!mbar_wait(&S.mbar, 0)) S.fail = 1;
+    tc_fence_after();
+    __syncthreads();
+    if (S.fail) goto cleanup;
+    {
+        float v[32];
+        tmem_ld32(my_lanes + 32, v);
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < kFeat; ++c) A.d_feat[a * kFeat + c] += v[c];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) A.d_ls[6 * a + j] += S.dls[tid][j];
+        }
+    }
+    // weight gradients of the tile: dW2 = dy_bf^T h, dW1 = dh_bf^T x
+    for (int i = tid; i < kOut * kHid; i += kThreads) {
+        const int o = i / kHid, k = i - o * kHid;
+        float s = 0.0f;
+        for (int r = 0; r < kTileA; ++r) s += bf16r(S.Y[r][o]) * S.hf[r][k];
+        part[i] = s;
+    }
+    for (int i = tid; i < kHid * kIn; i += kThreads) {
+        const int h = i / kIn, k = i - h * kIn;
+        float s = 0.0f;
+        for (int r = 0; r < kTileA; ++r) s += S.dhf[r][h] * S.x[r][k];
+        part[kOut * kHid + i] = s;
+    }
+    if (tid < kHid) part[kOut * kHid + kHid * kIn + kOut + tid] = S.db1[tid];
+cleanup:
+    if (S.fail) {
+        // give the tensor cores one more bounded wait before the memory goes
+        if (tid == 0) atomicCAS(A.err, 0, GS_ERR_TIMEOUT);
+        mbar_wait(&S.mbar, 0);
+        mbar_wait(&S.mbar, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// Sum of the per-CTA partials in CTA order (deterministic), added to the grads.
+__global__ void __launch_bounds__(256) k_ng_reduce(const float *__restrict__ partial, int n_tiles, float *dw2,
+                                                   float *dw1, float *db2, float *db1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kPartial) return;
+    float s = 0.0f;
+    for (int t = 0; t < n_tiles; ++t) s += partial[(size_t)t * kPartial + i];
+    if (i < kOut * kHid) dw2[i] += s;
+    else if (i < kOut * kHid + kHid * kIn) dw1[i - kOut * kHid] += s;
+    else if (i < kOut * kHid + kHid * kIn + kOut) db2[i - kOut * kHid - kHid * kIn] += s;
+    else db1[i - kOut * kHid - kHid * kIn - kOut] += s;
+}
+
+// ---------------------------------------------------------------- workspace
+struct Layout {
+    size_t w1b, w2b, w2tb, w1tb, h, partial, err, bytes;
+};
+
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Layout layout(int64_t n) {
+    Layout L;
+    size_t o = 0;
+    const int64_t tiles = (n + kTileA - 1) / kTileA;
+    L.err = o;
+    o = al(o + 256);
+    L.w1b = o;
+    o = al(o + kHid * kInPad * 2);
+    L.w2b = o;
+    o = al(o + kOutPad * kHid * 2);
+    L.w2tb = o;
+    o = al(o + kHid * kOutPad * 2);
+    L.w1tb = o;
+    o = al(o + kInPad * kHid * 2);
+    L.h = o;
+    o = al(o + (size_t)n * kHid * 2);
+    L.partial = o;
+    o = al(o + (size_t)tiles * kPartial * 4);
+    L.bytes = o;
+    return L;
+}
+
+static int check_ng(const gs_ng_params *p) {
+    if (!p || p->n_anchors <= 0 || p->n_anchors * (int64_t)kChild >= (1ll << 31) || !p->anchor_xyz || !p->feat ||
+        !p->anchor_ls || !p->w1 || !p->b1 || !p->w2 || !p->b2)
+        return GS_ERR_ARG;
+    return GS_OK;
+}
+
+static int smem_opt_in(const void *kernel, size_t bytes) {
+    return check_cuda(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+static Args base_args(const gs_ng_params *p, const gs_camera *cam, void *ws) {
+    const Layout L = layout(p->n_anchors);
+    Args A{};
+    A.n = p->n_anchors;
+    A.xyz = p->anchor_xyz;
+    A.feat = p->feat;
+    A.ls = p->anchor_ls;
+    A.b1 = p->b1;
+    A.b2 = p->b2;
+    // camera centre = -R^T t
+    for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < 3; ++i) s -= (double)cam->w2c[i * 4 + j] * (double)cam->w2c[i * 4 + 3];
+        A.cam[j] = (float)s;
+    }
+    char *w = (char *)ws;
+    A.w1b = (const __nv_bfloat16 *)(w + L.w1b);
+    A.w2b = (const __nv_bfloat16 *)(w + L.w2b);
+    A.w2tb = (const __nv_bfloat16 *)(w + L.w2tb);
+    A.w1tb = (const __nv_bfloat16 *)(w + L.w1tb);
+    A.h_store = (__nv_bfloat16 *)(w + L.h);
+    A.partial = (float *)(w + L.partial);
+    A.err = (int *)(w + L.err);
+    return A;
+}
+
+}  // namespace ng
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" size_t gs_ng_workspace_bytes(int64_t n_anchors) {
+    return n_anchors > 0 ? ng::layout(n_anchors).bytes : 0;
+}
+
+extern "C" int gs_ng_decode_fwd(const gs_ng_params *p, const gs_camera *cam, gs_params *children, void *ws,
+                                void *stream) {
+    int rc = ng::check_ng(p);
+    if (rc) return rc;
+    if (!cam || !ws || !children || children->n != p->n_anchors * ng::kChild || children->sh_degree != 0 ||
+        !children->means || !children->log_scales || !children->quats || !children->opacity_logits || !children->sh)
+        return GS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = sizeof(ng::FwdSmem) + 1024;
+    static bool opted = false;
+    if (!opted) {
+        rc = ng::smem_opt_in((const void *)ng::k_ng_fwd, smem);
+        if (rc) return rc;
+        opted = true;
+    }
+    ng::Args A = ng::base_args(p, cam, ws);
+    char *w = (char *)ws;
+    const ng::Layout L = ng::layout(p->n_anchors);
+    ng::k_ng_prep<<<1, 256, 0, s>>>(p->w1, p->w2, (__nv_bfloat16 *)(w + L.w1b), (__nv_bfloat16 *)(w + L.w2b),
+                                    (__nv_bfloat16 *)(w + L.w2tb), (__nv_bfloat16 *)(w + L.w1tb));
+    A.c_means = children->means;
+    A.c_ls = children->log_scales;
+    A.c_quats = children->quats;
+    A.c_logits = children->opacity_logits;
+    A.c_sh = children->sh;
+    const unsigned tiles = (unsigned)((p->n_anchors + ng::kTileA - 1) / ng::kTileA);
+    ng::k_ng_fwd<<<tiles, ng::kThreads, smem, s>>>(A);
+    return launch_error();
+}
+
+extern "C" int gs_ng_decode_bwd(const gs_ng_params *p, const gs_camera *cam, const gs_params *child_grads,
+                                gs_ng_params *grads, void *ws, void *stream) {
+    int rc = ng::check_ng(p);
+    if (rc) return rc;
+    if (!cam || !ws || !child_grads || !grads || child_grads->n != p->n_anchors * ng::kChild ||
+        child_grads->sh_degree != 0 || !child_grads->means || !child_grads->log_scales || !child_grads->quats ||
+        !child_grads->opacity_logits || !child_grads->sh || !grads->feat || !grads->anchor_ls || !grads->w1 ||
+        !grads->b1 || !grads->w2 || !grads->b2)
+        return GS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = sizeof(ng::BwdSmem) + 1024;
+    static bool opted = false;
+    if (!opted) {
+        rc = ng::smem_opt_in((const void *)ng::k_ng_bwd, smem);
+        if (rc) return rc;
+        opted = true;
+    }
+    ng::Args A = ng::base_args(p, cam, ws);
+    A.g_means = child_grads->means;
+    A.g_ls = child_grads->log_scales;
+    A.g_quats = child_grads->quats;
+    A.g_logits = child_grads->opacity_logits;
+    A.g_sh = child_grads->sh;
+    A.d_feat = grads->feat;
+    A.d_ls = grads->anchor_ls;
+    const int tiles = (int)((p->n_anchors + ng::kTileA - 1) / ng::kTileA);
+    ng::k_ng_bwd<<<tiles, ng::kThreads, smem, s>>>(A);
+    ng::k_ng_reduce<<<(ng::kPartial + 255) / 256, 256, 0, s>>>(A.partial, tiles, grads->w2, grads->w1, grads->b2,
+                                                              grads->b1);
+    return launch_error();
+}
+
+extern "C" int gs_ng_read_status(void *ws, int32_t *out_error, void *stream) {
+    if (!ws || !out_error) return GS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int e = 0;
+    int rc = check_cuda(cudaMemcpyAsync(&e, ws, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (rc) return rc;
+    rc = check_cuda(cudaStreamSynchronize(s));
+    if (rc) return rc;
+    *out_error = e;
+    return e ? e : GS_OK;
+}
