@@ -57,6 +57,12 @@ def parse_args():
     ap.add_argument("--lam", type=float, default=0.2)
     ap.add_argument("--sq", action="store_true", help="sequential tile-key write instead of load-balanced")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched CUDA-graph measurement")
+    ap.add_argument("--batched-steps", type=int, default=60)
+    ap.add_argument("--workload", choices=("explicit", "batched"), default="explicit",
+                    help="batched: only the 8-view CUDA-graph step, one line per --batched-n")
+    ap.add_argument("--batched-n", type=str, default="",
+                    help="comma-separated Gaussian counts for --workload batched (default: --n)")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -220,8 +226,9 @@ def kernels_per_step(trainer) -> int:
     tile_passes = -(-trainer.plan_tile_bits // 8)
     loss_k = 3 if trainer.lam > 0 else 2
     # preprocess 1; depth sort 4 passes x 3; count 2; keys 1; tile sort 3/pass;
-    # ranges 1; buckets 1; forward 1; loss; blend bwd 1; preprocess bwd 1; adam 1
-    return 1 + 12 + 2 + 1 + 3 * tile_passes + 2 + 1 + loss_k + 1 + 1 + 1
+    # ranges 1; buckets 1; forward 1; loss; blend bwd 1; preprocess bwd 1;
+    # adam 2 (step-count tick + update)
+    return 1 + 12 + 2 + 1 + 3 * tile_passes + 2 + 1 + loss_k + 1 + 1 + 2
 
 
 def run_ours(args, rank, world):
@@ -346,6 +353,10 @@ def run_ours(args, rank, world):
                      "buckets_last": st2["n_buckets"], "pairs_per_view": mean_pairs},
             "peaks": {"hbm_gbs": hbm or FALLBACK_HBM_GBS, "hbm_source": "measured" if hbm else "fallback",
                       "fp32_tflops": FP32_PEAK_TFLOPS}}
+    if world == 1 and not args.no_batched:
+        del trainer
+        torch.cuda.empty_cache()
+        line["batched_graph"] = run_batched(args, dev, args.n, args.batched_steps)
     if world == 1 and not args.no_cpu_baseline:
         scene_h = scene
         cam = cams[0]
@@ -360,8 +371,104 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ batched graph step
+
+def run_batched(args, dev, n: int, steps: int, warmup: int = 3) -> dict:
+    """8 views of uneven resolution per step (3 x 960x540, 3 x 1280x720,
+    2 x 1920x1080 from the ring), launch shapes from the autotuner, the whole
+    step captured in one CUDA graph per batch; two batches alternate.
+    Compared with the same batch run eagerly and with the same 8 views as 8
+    sequential single-view steps."""
+    import torch
+
+    import synth
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.autotune import autotune
+    from paper_2601_19489_gb300.trainer import Trainer
+
+    scene = synth.scene_clustered(n, seed=0, sh_degree=3)
+    batches = [synth.mixed_ring_cameras(8, seed=s) for s in (0, 1)]
+    targets = [torch.cat([torch.from_numpy(synth.target_uniform(2000 + 8 * b + i, c.width, c.height).reshape(-1))
+                          for i, c in enumerate(cams)]).to(dev) for b, cams in enumerate(batches)]
+    params = api.Gaussians.from_scene(scene, device=dev)
+    best, table = autotune(params, batches, targets, lam=args.lam, device=dev)
+    tr = Trainer(params, lam=args.lam, load_balanced=best["load_balanced"],
+                 tuning={"bucket": best["bucket"], "bwd_warps": best["bwd_warps"]}, device=dev)
+    tr.ensure_capacity(batches)
+    # eager batched steps (also the warm-up before capture)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(k):
+            fn(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    for i in range(warmup):
+        tr.step(batches[i % 2], targets[i % 2])
+    t_eager = timed(lambda i: tr.step(batches[i % 2], targets[i % 2]), steps)
+    graphs = [tr.capture(batches[b], targets[b]) for b in (0, 1)]
+    for i in range(warmup):
+        graphs[i % 2].replay()
+    with ClockSampler(dev.index or 0) as clk:
+        t_graph = timed(lambda i: graphs[i % 2].replay(), steps)
+    st = tr.slot_for(batches[0]).plan.status()
+    if st["rc"] != 0:
+        raise RuntimeError(f"device status after the batched steps: {st}")
+    # the same views one at a time (single-view plans, eager)
+    singles = [[c] for cams in batches for c in cams]
+    seq = Trainer(params, lam=args.lam, load_balanced=best["load_balanced"],
+                  tuning={"bucket": best["bucket"], "bwd_warps": best["bwd_warps"]}, device=dev)
+    seq.ensure_capacity(singles)
+    offs = []
+    for b, cams in enumerate(batches):
+        o = 0
+        for c in cams:
+            offs.append((b, o, 3 * c.width * c.height))
+            o += 3 * c.width * c.height
+    single_t = [targets[b][o:o + k] for (b, o, k) in offs]
+    for i in range(len(singles)):
+        seq.step(singles[i], single_t[i])
+    t_seq = timed(lambda i: seq.step(singles[i % 16], single_t[i % 16]), 8 * steps)
+    views = 8 * steps
+    return {"gaussians": n, "views_per_step": 8,
+            "views": "3 x 960x540, 3 x 1280x720, 2 x 1920x1080 ring views; two batches alternate",
+            "graph_steps_per_s": steps / t_graph, "graph_views_per_s": views / t_graph,
+            "eager_batched_views_per_s": views / t_eager, "sequential_views_per_s": views / t_seq,
+            "graph_ms_per_step": 1e3 * t_graph / steps, "sequential_ms_per_8_views": 1e3 * t_seq / steps,
+            "tuning": best, "autotune_ms_per_step": table, "clocks": clk.summary(),
+            "instances_last": st["n_instances"]}
+
+
+def run_batched_only(args):
+    import torch
+
+    from paper_2601_19489_gb300 import _lib as L
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    L.load()
+    ns = [int(float(x)) for x in args.batched_n.split(",") if x] or [args.n]
+    for n in ns:
+        r = run_batched(args, dev, n, args.batched_steps)
+        line = {"metric": "train views/s (8-view batched step, CUDA graph)", "value": r["graph_views_per_s"],
+                "unit": "views/s", "n_gpus": 1, "steps": args.batched_steps, "warmup": 3,
+                "ms_per_step": r["graph_ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"clustered {n} Gaussians SH3, 8 mixed-resolution ring views per step"},
+                "batched_graph": r}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == "batched":
+        run_batched_only(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and args.impl == "ours":

@@ -54,7 +54,7 @@ extern "C" {
 
 #define GS_MAX_VIEWS 16
 #define GS_TILE 16       /* tile edge in pixels (Sec. 2.2: 16x16 tiles) */
-#define GS_BUCKET 32     /* splats per checkpoint bucket (Sec. 2.2) */
+#define GS_BUCKET 32     /* default splats per checkpoint bucket (Sec. 2.2) */
 
 enum {
     GS_OK = 0,
@@ -84,7 +84,7 @@ typedef struct {
 
 typedef struct {
     int64_t n_instances;     /* Gaussian-tile pairs of the last gs_bin_sort */
-    int64_t n_buckets;       /* 32-splat buckets of the last gs_bin_sort */
+    int64_t n_buckets;       /* checkpoint buckets of the last gs_bin_sort */
     int64_t inst_capacity;   /* capacity the plan was made with */
     int32_t overflow;        /* 1: n_instances > inst_capacity, result truncated */
     int32_t error;           /* 0 or a GS_ERR_* code seen on the device */
@@ -105,6 +105,25 @@ typedef struct gs_plan gs_plan;
 
 GS_API gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views, const int32_t *h_widths,
                                const int32_t *h_heights, int64_t inst_capacity);
+
+/* Launch-shape choices that change speed but not results (beyond float32
+ * summation order), for an autotuner to pick per workload:
+ *   bucket     splats per checkpoint bucket of the forward and per unit of
+ *              work of the per-Gaussian backward (Sec. 2.2 uses 32): 32 or
+ *              64.  At 64 one warp walks a bucket as two 32-splat passes,
+ *              carrying the per-pixel state between them in shared memory;
+ *              checkpoint memory and traffic halve.
+ *   bwd_warps  warps per CTA of the per-Gaussian backward (the warps of a CTA
+ *              share one tile's staged pixel data): 2, 4 or 8.
+ * A zero field takes the default (32, 4).  gs_plan_create uses the defaults.
+ * Returns NULL on the same conditions as gs_plan_create or an unsupported
+ * choice. */
+typedef struct {
+    int32_t bucket;
+    int32_t bwd_warps;
+} gs_tuning;
+GS_API gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n_views, const int32_t *h_widths,
+                                     const int32_t *h_heights, int64_t inst_capacity, const gs_tuning *tuning);
 GS_API void gs_plan_destroy(gs_plan *plan);
 /* Bytes of device workspace the plan needs (256-byte aligned base required). */
 GS_API size_t gs_plan_workspace_bytes(const gs_plan *plan);
@@ -233,6 +252,15 @@ typedef struct {
 } gs_adam_group;
 GS_API int gs_adam_step_multi(const gs_adam_group *h_groups, int32_t n_groups, float b1, float b2,
                               float eps, int32_t step, void *stream);
+
+/* The same update with the step count in device memory, so that a training
+ * step captured once in a CUDA graph can be replayed: d_step (device int32,
+ * 0 before the first update) is incremented on the stream first, and the
+ * incremented value is the t of the bias corrections, evaluated in float32
+ * as 1 - b^t = -expm1(t log1p(b - 1)).  b1 and b2 must lie in [0.5, 1).
+ * Two launches; the groups are captured by value. */
+GS_API int gs_adam_step_multi_dev(const gs_adam_group *h_groups, int32_t n_groups, float b1, float b2,
+                                  float eps, int32_t *d_step, void *stream);
 
 /* -------------------------------------------------- building blocks
  * Stable LSD radix sort of (uint32 key, uint32 value) pairs on bits

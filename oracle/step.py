@@ -80,6 +80,27 @@ def forward_backward(scene, cam, target, bg=(0.0, 0.0, 0.0), lam: float = 0.2,
     return L, grads, f
 
 
+def forward_backward_batch(scene, cams, targets, bg=(0.0, 0.0, 0.0), lam: float = 0.2,
+                           disp_targets=None, disp_weight: float = 0.0, n_threads: int = 0):
+    """Loss and parameter gradients of a batch of views (Sec. 2.2 trains on
+    several views per step; the paper gives no weighting).  Reading: the
+    batch loss is the mean over all the batch's pixels, i.e. each view's own
+    loss weighted by its share of the pixels,
+        L = sum_v (P_v / P) L_v,   P = sum_v P_v,
+    so that views of equal size enter equally and the gradients of the views
+    add up before one optimiser update."""
+    P = float(sum(c.width * c.height for c in cams))
+    total, acc = 0.0, None
+    for i, cam in enumerate(cams):
+        w = cam.width * cam.height / P
+        dt = disp_targets[i] if disp_targets is not None else None
+        L, g, _ = forward_backward(scene, cam, targets[i], bg=bg, lam=lam, n_threads=n_threads,
+                                   disp_target=dt, disp_weight=disp_weight)
+        total += w * L
+        acc = {k: w * v for k, v in g.items()} if acc is None else {k: acc[k] + w * g[k] for k in acc}
+    return total, acc
+
+
 def adam_update(state: dict, grads: dict, lrs: dict) -> None:
     state["step"] += 1
     g = _split(grads)

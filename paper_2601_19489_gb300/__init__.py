@@ -14,6 +14,7 @@ from .api import (  # noqa: F401
     camera_struct,
     gs_adam_step,
     gs_adam_step_multi,
+    gs_adam_step_multi_dev,
     gs_bin_sort,
     gs_loss,
     gs_loss_scratch,

@@ -27,11 +27,11 @@ GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_INTERNAL
  GS_WS_INST_GID, GS_WS_TILE_RANGES, GS_WS_N_CONTRIB, GS_WS_GRAD2D, GS_WS_STATUS, GS_WS_BIN) = range(11)
 
 EXPORTS = (
-    "gs_plan_create", "gs_plan_destroy", "gs_plan_workspace_bytes", "gs_plan_pixels",
+    "gs_plan_create", "gs_plan_create_tuned", "gs_plan_destroy", "gs_plan_workspace_bytes", "gs_plan_pixels",
     "gs_workspace_view", "gs_read_status", "gs_error_string", "gs_preprocess", "gs_bin_sort",
     "gs_render_fwd", "gs_render_bwd", "gs_render_bwd_blend", "gs_preprocess_bwd",
     "gs_loss_scratch_floats", "gs_loss", "gs_adam_step",
-    "gs_adam_step_multi", "gs_sort_scratch_bytes", "gs_sort_pairs_u32", "gs_sort_pairs_u32_noalloc",
+    "gs_adam_step_multi", "gs_adam_step_multi_dev", "gs_sort_scratch_bytes", "gs_sort_pairs_u32", "gs_sort_pairs_u32_noalloc",
     "gs_ng_workspace_bytes", "gs_ng_decode_fwd", "gs_ng_decode_bwd", "gs_ng_read_status",
 )
 
@@ -47,6 +47,10 @@ class GsParams(ctypes.Structure):
                 ("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
                 ("quats", ctypes.c_void_p), ("opacity_logits", ctypes.c_void_p),
                 ("sh", ctypes.c_void_p)]
+
+
+class GsTuning(ctypes.Structure):
+    _fields_ = [("bucket", ctypes.c_int32), ("bwd_warps", ctypes.c_int32)]
 
 
 class GsStatus(ctypes.Structure):
@@ -80,6 +84,8 @@ _lock = threading.Lock()
 P = ctypes.c_void_p
 _SIGS = {
     "gs_plan_create": (P, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int64]),
+    "gs_plan_create_tuned": (P, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int64,
+                                 ctypes.POINTER(GsTuning)]),
     "gs_plan_destroy": (None, [P]),
     "gs_plan_workspace_bytes": (ctypes.c_size_t, [P]),
     "gs_plan_pixels": (ctypes.c_int64, [P]),
@@ -100,6 +106,8 @@ _SIGS = {
                                     ctypes.c_float, ctypes.c_float, ctypes.c_int32, P]),
     "gs_adam_step_multi": (ctypes.c_int, [ctypes.POINTER(GsAdamGroup), ctypes.c_int32, ctypes.c_float,
                                           ctypes.c_float, ctypes.c_float, ctypes.c_int32, P]),
+    "gs_adam_step_multi_dev": (ctypes.c_int, [ctypes.POINTER(GsAdamGroup), ctypes.c_int32, ctypes.c_float,
+                                              ctypes.c_float, ctypes.c_float, P, P]),
     "gs_sort_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "gs_sort_pairs_u32": (ctypes.c_int, [P, P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          P, P]),

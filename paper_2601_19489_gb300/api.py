@@ -90,13 +90,18 @@ class Gaussians:
 class Plan:
     """A gs_plan plus the device workspace it describes."""
 
-    def __init__(self, n: int, sh_degree: int, sizes, inst_capacity: int, device="cuda"):
+    def __init__(self, n: int, sh_degree: int, sizes, inst_capacity: int, device="cuda",
+                 tuning: dict | None = None):
+        """tuning: optional {"bucket": 32 | 64, "bwd_warps": 2 | 4 | 8}."""
         lib = L.lib()
         self.sizes = [(int(w), int(h)) for (w, h) in sizes]
         V = len(self.sizes)
         ws_ = (ctypes.c_int32 * V)(*[w for w, _ in self.sizes])
         hs_ = (ctypes.c_int32 * V)(*[h for _, h in self.sizes])
-        self.handle = lib.gs_plan_create(int(n), int(sh_degree), V, ws_, hs_, int(inst_capacity))
+        self.tuning = {"bucket": 32, "bwd_warps": 4, **(tuning or {})}
+        tu = L.GsTuning(int(self.tuning["bucket"]), int(self.tuning["bwd_warps"]))
+        self.handle = lib.gs_plan_create_tuned(int(n), int(sh_degree), V, ws_, hs_, int(inst_capacity),
+                                               ctypes.byref(tu))
         if not self.handle:
             raise L.GsError(L.GS_ERR_ARG, "gs_plan_create")
         self.n, self.sh_degree, self.inst_capacity = int(n), int(sh_degree), int(inst_capacity)
@@ -200,6 +205,17 @@ def gs_adam_step_multi(groups, step: int, b1=0.9, b2=0.999, eps=1e-15, stream=No
     arr = _arr if _arr is not None else adam_groups_array(groups)
     L.check(L.lib().gs_adam_step_multi(arr, len(arr), float(b1), float(b2), float(eps), int(step),
                                        _stream(stream)), "gs_adam_step_multi")
+
+
+def gs_adam_step_multi_dev(groups, d_step: torch.Tensor, b1=0.9, b2=0.999, eps=1e-15, stream=None,
+                           _arr=None) -> None:
+    """Adam over groups with the step count kept on the device (int32
+    tensor of one element, incremented by the call)."""
+    if d_step.dtype != torch.int32 or not d_step.is_cuda:
+        raise TypeError("d_step must be a CUDA int32 tensor")
+    arr = _arr if _arr is not None else adam_groups_array(groups)
+    L.check(L.lib().gs_adam_step_multi_dev(arr, len(arr), float(b1), float(b2), float(eps), _ptr(d_step, None),
+                                           _stream(stream)), "gs_adam_step_multi_dev")
 
 
 def gs_sort_pairs_u32(keys_in, vals_in, keys_out, vals_out, begin_bit: int, end_bit: int, scratch=None,

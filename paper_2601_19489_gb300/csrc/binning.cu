@@ -336,10 +336,10 @@ k_tile_ranges(const uint32_t *__restrict__ keys, const StatusDev *st, int64_t ca
     ranges[t] = make_uint2(lower_bound_u32(keys, n, t), lower_bound_u32(keys, n, t + 1));
 }
 
-// One block: bucket_off[t] = sum over tiles before t of ceil(len / 32).
+// One block: bucket_off[t] = sum over tiles before t of ceil(len / bucket).
 __global__ void __launch_bounds__(1024)
-k_bucket_offsets(const uint2 *__restrict__ ranges, int total_tiles, uint32_t *__restrict__ bucket_off,
-                 StatusDev *st) {
+k_bucket_offsets(const uint2 *__restrict__ ranges, int total_tiles, int bucket_shift,
+                 uint32_t *__restrict__ bucket_off, StatusDev *st) {
     __shared__ uint32_t tmp[32];
     __shared__ uint32_t carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -350,7 +350,7 @@ k_bucket_offsets(const uint2 *__restrict__ ranges, int total_tiles, uint32_t *__
         uint32_t nb = 0;
         if (t < total_tiles) {
             const uint2 r = ranges[t];
-            nb = (r.y - r.x + kBucket - 1) / kBucket;
+            nb = (r.y - r.x + (1u << bucket_shift) - 1) >> bucket_shift;
         }
         uint32_t inc = nb;
 #pragma unroll
@@ -431,7 +431,7 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
     uint2 *ranges = ws_at<uint2>(ws, plan->o_ranges);
     k_tile_ranges<<<(plan->total_tiles + 255) / 256, 256, 0, s>>>(
         ws_at<uint32_t>(ws, plan->o_ikey[ifinal]), st, plan->inst_cap, (uint32_t)plan->total_tiles, ranges);
-    k_bucket_offsets<<<1, 1024, 0, s>>>(ranges, plan->total_tiles, ws_at<uint32_t>(ws, plan->o_bucket_off),
-                                        st);
+    k_bucket_offsets<<<1, 1024, 0, s>>>(ranges, plan->total_tiles, plan->bucket_shift,
+                                        ws_at<uint32_t>(ws, plan->o_bucket_off), st);
     return launch_error();
 }

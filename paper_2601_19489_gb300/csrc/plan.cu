@@ -54,9 +54,12 @@ using namespace gs;
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-extern "C" gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views,
-                                   const int32_t *widths, const int32_t *heights,
-                                   int64_t inst_capacity) {
+extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n_views,
+                                         const int32_t *widths, const int32_t *heights,
+                                         int64_t inst_capacity, const gs_tuning *tuning) {
+    const int32_t bucket = tuning && tuning->bucket ? tuning->bucket : kBucket;
+    const int32_t bwd_warps = tuning && tuning->bwd_warps ? tuning->bwd_warps : 4;
+    if ((bucket != 32 && bucket != 64) || (bwd_warps != 2 && bwd_warps != 4 && bwd_warps != 8)) return nullptr;
     if (n <= 0 || n >= (1ll << 31) || sh_degree < 0 || sh_degree > 3 || n_views < 1 ||
         n_views > GS_MAX_VIEWS || !widths || !heights || inst_capacity <= 0 ||
         inst_capacity >= (1ll << 31))
@@ -95,7 +98,10 @@ extern "C" gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views
     while ((1ll << bits) < tiles) ++bits;
     p->tile_bits = bits;
     p->inst_cap = inst_capacity;
-    p->bucket_cap = inst_capacity / kBucket + tiles + 1;
+    p->bucket = bucket;
+    p->bucket_shift = bucket == 64 ? 6 : 5;
+    p->bwd_warps = bwd_warps;
+    p->bucket_cap = inst_capacity / bucket + tiles + 1;
     p->sort_scratch_bytes = sort_scratch_bytes();
 
     size_t o = 0;
@@ -132,6 +138,11 @@ extern "C" gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views
     p->depth_final = (32 / kRadixBits) % 2;
     p->inst_final = ((p->tile_bits + kRadixBits - 1) / kRadixBits) % 2;
     return p;
+}
+
+extern "C" gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views, const int32_t *widths,
+                                   const int32_t *heights, int64_t inst_capacity) {
+    return gs_plan_create_tuned(n, sh_degree, n_views, widths, heights, inst_capacity, nullptr);
 }
 
 extern "C" void gs_plan_destroy(gs_plan *plan) { free(plan); }

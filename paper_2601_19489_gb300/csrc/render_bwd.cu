@@ -1,8 +1,9 @@
 // a7: per-Gaussian parallel backward of the blend (Sec. 2.2).
 //
-// One warp per 32-splat bucket; lane l owns splat k = bucket start + l of the
-// tile's list.  The warp walks the tile's pixels as a pipeline: at step s lane
-// l handles the s-l th pixel, receiving from lane l-1 (shuffle) the state in
+// One warp per bucket of 32 (or 64: two passes of 32) splats; lane l owns
+// splat k = pass start + l of the tile's list.  The warp walks the tile's
+// pixels as a pipeline: at step s lane l handles the s-l th pixel, receiving
+// from lane l-1 (shuffle) the state in
 // front of its splat — transmittance T and the running sum
 //   S = sum_{j<=k} alpha_j T_j (g . rgb_j + g_D / z_j)
 // — while lane 0 seeds each pixel from the forward's checkpoint.  With
@@ -21,17 +22,17 @@
 
 namespace gs {
 
-constexpr int kBwdWarps = 4;
-constexpr int kBwdThreads = kBwdWarps * 32;
-
 // Per CTA: the current tile's per-pixel data (staged once for all warps) and
-// each warp's compacted pixel list for the bucket it is working on.
+// each warp's compacted pixel list for the bucket it is working on.  With
+// 64-splat buckets (kSub = 2 passes of 32) the state behind a pass's last
+// splat is carried to the next pass through the second `ck` buffer.
+template <int kWarps, int kSub>
 struct BwdShared {
-    float4 g[kTilePix];                 // (g_r, g_g, g_b, g_D), zero outside the image
-    float2 fin[kTilePix];               // (S_fin, n_contrib as bits)
-    float2 ck[kBwdWarps][kTilePix];     // per warp, compacted: (T, S) in front of its bucket
-    uint8_t pix[kBwdWarps][kTilePix];   // per warp, compacted: pixel index in the tile
-    uint32_t next;                      // next unclaimed bucket of the tile
+    float4 g[kTilePix];                       // (g_r, g_g, g_b, g_D), zero outside the image
+    float2 fin[kTilePix];                     // (S_fin, n_contrib as bits)
+    float2 ck[kWarps][kSub > 1 ? 2 : 1][kTilePix];  // per warp, compacted: (T, S) in front of its pass
+    uint8_t pix[kWarps][kTilePix];            // per warp, compacted: pixel index in the tile
+    uint32_t next;                            // next unclaimed bucket of the tile
 };
 
 struct SplatGrad {
@@ -40,16 +41,17 @@ struct SplatGrad {
 
 // One (splat, pixel) pair of the pipeline: T, S enter as the state in front
 // of the splat and leave as the state behind it.
-__device__ __forceinline__ void bwd_pair(const BwdShared &S, int warp, int m, uint32_t k, const float4 &r0,
+__device__ __forceinline__ void bwd_pair(const float4 *__restrict__ sg, const float2 *__restrict__ sfin,
+                                         const uint8_t *__restrict__ spix, int m, uint32_t k, const float4 &r0,
                                          const float4 &r1, const float4 &r2, float &T, float &Sv,
                                          SplatGrad &acc) {
-    const int p = S.pix[warp][m];
-    const float2 fin = S.fin[p];
+    const int p = spix[m];
+    const float2 fin = sfin[p];
     if (k >= __float_as_uint(fin.y)) return;  // beyond this pixel's last blended splat
     PairEval e;
     eval_pair(r0, r1, (float)(p & (kTile - 1)) + 0.5f, (float)(p >> 4) + 0.5f, e);
     if (e.power2 > 0.0f || e.alpha < kAlphaMin) return;
-    const float4 g = S.g[p];
+    const float4 g = sg[p];
     const float w = e.alpha * T;
     const float gdot = g.x * r2.x + g.y * r2.y + g.z * r2.z + g.w * r1.z;
     acc.r += w * g.x;
@@ -71,21 +73,25 @@ __device__ __forceinline__ void bwd_pair(const BwdShared &S, int warp, int m, ui
     T = T * (1.0f - e.alpha);
 }
 
-__global__ void __launch_bounds__(kBwdThreads)
+template <int kWarps, int kSub>
+__global__ void __launch_bounds__(kWarps * 32)
 k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ inst_item,
              const float4 *__restrict__ rec, const uint32_t *__restrict__ bucket_off,
              const uint32_t *__restrict__ tile_maxc, const float *__restrict__ ckpt,
              const uint32_t *__restrict__ n_contrib, const float *__restrict__ img_rgb,
              const float *__restrict__ img_disp, const float *__restrict__ dL_drgb,
              const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d) {
-    __shared__ BwdShared S;
+    constexpr int kThreads = kWarps * 32;
+    constexpr int kBucketSplats = 32 * kSub;
+    __shared__ BwdShared<kWarps, kSub> S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint8_t *spix = S.pix[warp];
 
     for (int t = blockIdx.x; t < views.total_tiles; t += gridDim.x) {
         const uint2 range = ranges[t];
         const uint32_t maxc = min(tile_maxc[t], range.y - range.x);
-        const uint32_t nb = (maxc + kBucket - 1) / kBucket;  // buckets that hold blended splats
+        const uint32_t nb = (maxc + kBucketSplats - 1) / kBucketSplats;  // buckets that hold blended splats
         if (nb == 0) continue;  // uniform
         int v = 0;
         while (v + 1 < views.V && t >= views.v[v + 1].tile_off) ++v;
@@ -96,7 +102,7 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
         const size_t base = (size_t)cam.pix_off;
 
         // ---- the tile's pixels, shared by the CTA's warps
-        for (int p = threadIdx.x; p < kTilePix; p += kBwdThreads) {
+        for (int p = threadIdx.x; p < kTilePix; p += kThreads) {
             const int ix = tx * kTile + (p & (kTile - 1)), iy = ty * kTile + (p >> 4);
             float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
             float2 fin = make_float2(0.f, __uint_as_float(0u));
@@ -113,13 +119,13 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
             S.g[p] = g;
             S.fin[p] = fin;
         }
-        if (threadIdx.x == 0) S.next = kBwdWarps;  // buckets 0..kBwdWarps-1 are taken
+        if (threadIdx.x == 0) S.next = kWarps;  // buckets 0..kWarps-1 are taken
         __syncthreads();
 
         // ---- the warps take the tile's buckets greedily (the first, fullest
         // buckets first) without synchronising until the tile is done
         for (uint32_t lb = warp; lb < nb;) {
-            const uint32_t j0 = lb * kBucket;
+            const uint32_t j0 = lb * kBucketSplats;
             // pixels still running at j0, compacted, seeded from the checkpoint
             const float *ckb = ckpt + (size_t)(bucket_off[t] + lb) * (kCkptCh * kTilePix);
             int m_total = 0;
@@ -132,77 +138,110 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
                     const float4 g = S.g[p];
                     const float sck = g.x * ckb[kTilePix + p] + g.y * ckb[2 * kTilePix + p] +
                                       g.z * ckb[3 * kTilePix + p] + g.w * ckb[4 * kTilePix + p];
-                    S.ck[warp][m] = make_float2(ckb[p], sck);
+                    S.ck[warp][0][m] = make_float2(ckb[p], sck);
                     S.pix[warp][m] = (uint8_t)p;
                 }
                 m_total += __popc(bal);
             }
             __syncwarp();
-
-            // this lane's splat, in the tile-local frame of the forward
-            const int nsplat = min((int)(range.y - range.x) - (int)j0, kBucket);
-            const bool valid = lane < nsplat;
-            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
-            uint32_t item = 0;
-            if (valid) {
-                item = inst_item[range.x + j0 + lane];
-                r0 = rec[3 * (size_t)item];
-                r1 = rec[3 * (size_t)item + 1];
-                r2 = rec[3 * (size_t)item + 2];
-                const float2 mm = tile_local_mean(r0, r1.w, r2.w, (float)(tx * kTile), (float)(ty * kTile));
-                r0.x = mm.x;
-                r0.y = mm.y;
-            }
-            const uint32_t k = j0 + (uint32_t)lane;
-            SplatGrad acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            // two independent pixel chains (first and second half of the
-            // compacted list) interleave to hide the shuffle latency
             const int h = (m_total + 1) >> 1;
-            float TA = 0.f, SA = 0.f, TB = 0.f, SB = 0.f;
-            for (int s = 0; s < h + 31; ++s) {
-                float tA = __shfl_up_sync(0xffffffffu, TA, 1);
-                float sA = __shfl_up_sync(0xffffffffu, SA, 1);
-                float tB = __shfl_up_sync(0xffffffffu, TB, 1);
-                float sB = __shfl_up_sync(0xffffffffu, SB, 1);
-                const int mA = s - lane, mB = h + s - lane;
-                if (lane == 0) {
-                    if (mA < h) {
-                        const float2 c = S.ck[warp][mA];
-                        tA = c.x;
-                        sA = c.y;
+
+#pragma unroll 1
+            for (int sub = 0; sub < kSub; ++sub) {
+                const uint32_t js = j0 + 32u * (uint32_t)sub;
+                const int nsplat = min((int)(range.y - range.x) - (int)js, 32);
+                if (nsplat <= 0) break;  // uniform
+                const float2 *ck_in = S.ck[warp][sub & 1];
+                float2 *ck_out = S.ck[warp][(sub + 1) & 1];
+                const bool carry = sub + 1 < kSub && lane == 31;
+                // this lane's splat, in the tile-local frame of the forward
+                const bool valid = lane < nsplat;
+                float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+                uint32_t item = 0;
+                if (valid) {
+                    item = inst_item[range.x + js + lane];
+                    r0 = rec[3 * (size_t)item];
+                    r1 = rec[3 * (size_t)item + 1];
+                    r2 = rec[3 * (size_t)item + 2];
+                    const float2 mm = tile_local_mean(r0, r1.w, r2.w, (float)(tx * kTile), (float)(ty * kTile));
+                    r0.x = mm.x;
+                    r0.y = mm.y;
+                }
+                const uint32_t k = js + (uint32_t)lane;
+                SplatGrad acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                // two independent pixel chains (first and second half of the
+                // compacted list) interleave to hide the shuffle latency
+                float TA = 0.f, SA = 0.f, TB = 0.f, SB = 0.f;
+                for (int s = 0; s < h + 31; ++s) {
+                    float tA = __shfl_up_sync(0xffffffffu, TA, 1);
+                    float sA = __shfl_up_sync(0xffffffffu, SA, 1);
+                    float tB = __shfl_up_sync(0xffffffffu, TB, 1);
+                    float sB = __shfl_up_sync(0xffffffffu, SB, 1);
+                    const int mA = s - lane, mB = h + s - lane;
+                    if (lane == 0) {
+                        if (mA < h) {
+                            const float2 c = ck_in[mA];
+                            tA = c.x;
+                            sA = c.y;
+                        }
+                        if (mB < m_total) {
+                            const float2 c = ck_in[mB];
+                            tB = c.x;
+                            sB = c.y;
+                        }
                     }
-                    if (mB < m_total) {
-                        const float2 c = S.ck[warp][mB];
-                        tB = c.x;
-                        sB = c.y;
+                    TA = tA;
+                    SA = sA;
+                    TB = tB;
+                    SB = sB;
+                    if (valid && mA >= 0) {
+                        if (mA < h) bwd_pair(S.g, S.fin, spix, mA, k, r0, r1, r2, TA, SA, acc);
+                        if (mB < m_total) bwd_pair(S.g, S.fin, spix, mB, k, r0, r1, r2, TB, SB, acc);
+                    }
+                    // the state behind the pass's last splat seeds the next pass
+                    if (carry && mA >= 0) {
+                        if (mA < h) ck_out[mA] = make_float2(TA, SA);
+                        if (mB < m_total) ck_out[mB] = make_float2(TB, SB);
                     }
                 }
-                TA = tA;
-                SA = sA;
-                TB = tB;
-                SB = sB;
-                if (valid && mA >= 0) {
-                    if (mA < h) bwd_pair(S, warp, mA, k, r0, r1, r2, TA, SA, acc);
-                    if (mB < m_total) bwd_pair(S, warp, mB, k, r0, r1, r2, TB, SB, acc);
+                if (valid) {
+                    // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2 and (A, B, C) = kH (a, b, c):
+                    //   d power / d mx = (A dx + B dy) / kH, d power / d a = -dx^2 / 2, ...
+                    //   d alpha / d o = alpha_raw / o, so dL/do = sum(dL/dpower) / o
+                    const float inv_o = fast_exp2(-r1.y);
+                    float4 *gp = grad2d + 3 * (size_t)item;
+                    atomicAdd(gp, make_float4(acc.mx * kInvH, acc.my * kInvH, -0.5f * acc.xx, -acc.xy));
+                    atomicAdd(gp + 1, make_float4(-0.5f * acc.yy, acc.pw * inv_o, acc.iz, 0.0f));
+                    atomicAdd(gp + 2, make_float4(acc.r, acc.g, acc.b, 0.0f));
                 }
+                __syncwarp();  // the carried states are visible to lane 0 of the next pass
             }
-            if (valid) {
-                // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2 and (A, B, C) = kH (a, b, c):
-                //   d power / d mx = (A dx + B dy) / kH, d power / d a = -dx^2 / 2, ...
-                //   d alpha / d o = alpha_raw / o, so dL/do = sum(dL/dpower) / o
-                const float inv_o = fast_exp2(-r1.y);
-                float4 *gp = grad2d + 3 * (size_t)item;
-                atomicAdd(gp, make_float4(acc.mx * kInvH, acc.my * kInvH, -0.5f * acc.xx, -acc.xy));
-                atomicAdd(gp + 1, make_float4(-0.5f * acc.yy, acc.pw * inv_o, acc.iz, 0.0f));
-                atomicAdd(gp + 2, make_float4(acc.r, acc.g, acc.b, 0.0f));
-            }
-            __syncwarp();  // the next bucket overwrites this warp's lists
             uint32_t next = 0;
             if (lane == 0) next = atomicAdd(&S.next, 1u);
             lb = __shfl_sync(0xffffffffu, next, 0);
         }
         __syncthreads();  // the next tile overwrites the staging
     }
+}
+
+template <int kWarps, int kSub>
+static int launch_bwd(const gs_plan *plan, void *ws, const float *d_rgb, const float *d_disp,
+                      const float *d_dL_drgb, const float *d_dL_ddisp, float4 *g2d, cudaStream_t s) {
+    const ViewsDev vd = make_views(plan, nullptr);
+    // persistent grid: as many CTAs as fit on the device at once
+    int dev = 0, sms = 152, per_sm = 8;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<kWarps, kSub>, kWarps * 32, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    k_render_bwd<kWarps, kSub><<<sms * per_sm, kWarps * 32, 0, s>>>(
+        vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
+        ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off),
+        ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt),
+        ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d);
+    return launch_error();
 }
 
 int preprocess_bwd(const gs_plan *plan, void *ws, const gs_params *params, const gs_camera *cams,
@@ -221,20 +260,15 @@ extern "C" int gs_render_bwd_blend(const gs_plan *plan, void *ws, const float *d
     float4 *g2d = ws_at<float4>(ws, plan->o_grad2d);
     int rc = check_cuda(cudaMemsetAsync(g2d, 0, (size_t)plan->VN * 3 * sizeof(float4), s));
     if (rc) return rc;
-    const ViewsDev vd = make_views(plan, nullptr);
-    // persistent grid: as many CTAs as fit on the device at once
-    int dev = 0, sms = 152, per_sm = 8;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd, kBwdThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 8;
-    k_render_bwd<<<sms * per_sm, kBwdThreads, 0, s>>>(
-        vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
-        ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off),
-        ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt),
-        ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d);
-    return launch_error();
+    const bool two = plan->bucket == 64;
+    switch (plan->bwd_warps) {
+        case 2: return two ? launch_bwd<2, 2>(plan, ws, d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, s)
+                           : launch_bwd<2, 1>(plan, ws, d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, s);
+        case 8: return two ? launch_bwd<8, 2>(plan, ws, d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, s)
+                           : launch_bwd<8, 1>(plan, ws, d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, s);
+        default: return two ? launch_bwd<4, 2>(plan, ws, d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, s)
+                            : launch_bwd<4, 1>(plan, ws, d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, s);
+    }
 }
 
 extern "C" int gs_preprocess_bwd(const gs_plan *plan, void *ws, const gs_params *params,

@@ -9,9 +9,9 @@
 // to float32 at any image size.  Each pixel blends front to back
 // until its transmittance would fall below 1e-4; a warp whose pixels are all
 // done skips the rest of the batch and the CTA leaves when all 256 are done.
-// Before list positions 0, 32, 64, ... every pixel still running stores its
-// (T, C, D) in bucket-major, channel-planar layout [bucket][5][256] so the
-// backward's warps read them coalesced.
+// Before list positions 0, B, 2B, ... (B = 32 or 64 splats per bucket) every
+// pixel still running stores its (T, C, D) in bucket-major, channel-planar
+// layout [bucket][5][256] so the backward's warps read them coalesced.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -24,7 +24,7 @@ __device__ __forceinline__ int view_of_tile(const ViewsDev &vd, int t) {
 
 __global__ void __launch_bounds__(kTilePix)
 k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ inst_item,
-             const float4 *__restrict__ rec, const uint32_t *__restrict__ bucket_off, float bg_r,
+             const float4 *__restrict__ rec, const uint32_t *__restrict__ bucket_off, int bucket_shift, float bg_r,
              float bg_g, float bg_b, float *__restrict__ out_rgb, float *__restrict__ out_disp,
              float *__restrict__ out_T, uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ tile_maxc,
              float *__restrict__ ckpt) {
@@ -67,17 +67,18 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
         }
         __syncthreads();
         const int cnt = min(kTilePix, n - b0);
-        for (int j0 = 0; j0 < cnt; j0 += kBucket) {
+        const int bucket = 1 << bucket_shift;
+        for (int j0 = 0; j0 < cnt; j0 += bucket) {
             if (__all_sync(0xffffffffu, done)) break;
             if (!done) {  // checkpoint before list position b0 + j0
-                float *c = ck + (size_t)((b0 + j0) / kBucket) * (kCkptCh * kTilePix);
+                float *c = ck + (size_t)((b0 + j0) >> bucket_shift) * (kCkptCh * kTilePix);
                 c[0] = T;
                 c[kTilePix] = Cr;
                 c[2 * kTilePix] = Cg;
                 c[3 * kTilePix] = Cb;
                 c[4 * kTilePix] = D;
             }
-            const int j1 = min(j0 + kBucket, cnt);
+            const int j1 = min(j0 + bucket, cnt);
             for (int j = j0; j < j1 && !done; ++j) {
                 const float4 r0 = s_r0[j], r1 = s_r1[j];
                 PairEval e;
@@ -131,7 +132,8 @@ extern "C" int gs_render_fwd(const gs_plan *plan, void *ws, const float *bg, flo
     const ViewsDev vd = make_views(plan, nullptr);
     k_render_fwd<<<plan->total_tiles, kTilePix, 0, s>>>(
         vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
-        ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off), bg[0], bg[1], bg[2],
+        ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off), plan->bucket_shift, bg[0],
+        bg[1], bg[2],
         out_rgb, out_disp, out_T, ws_at<uint32_t>(ws, plan->o_ncontrib),
         ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt));
     return launch_error();

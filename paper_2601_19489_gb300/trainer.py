@@ -1,6 +1,12 @@
-"""One training step of 3DGS through the C ABI: preprocess -> bin/sort ->
+"""The 3DGS training step through the C ABI: preprocess -> bin/sort ->
 forward blend -> loss -> per-Gaussian backward (+ preprocess backward) ->
 Adam, all enqueued on one CUDA stream with no host synchronisation.
+
+A step takes one view or a batch of views of uneven resolution; a batch goes
+through every stage as one launch (the plan lays the views' tiles and pixels
+end to end), its gradients sum over the views, and one Adam update follows.
+The Adam step count lives on the device, so a step can be captured once in a
+CUDA graph (``Trainer.capture``) and replayed.
 
 Learning rates default to the 3DGS values the paper trains with (its Sec. 4
 builds on 3DGS and names no optimiser settings); SH DC coefficients and the
@@ -13,7 +19,7 @@ import ctypes
 import torch
 
 from . import _lib as L
-from .api import Gaussians, Plan, _stream, adam_groups_array, camera_struct
+from .api import Gaussians, Plan, adam_groups_array, camera_struct
 
 
 def default_lrs(extent: float = 1.0) -> dict:
@@ -21,41 +27,80 @@ def default_lrs(extent: float = 1.0) -> dict:
             "sh_dc": 2.5e-3, "sh_rest": 2.5e-3 / 20.0}
 
 
-class Trainer:
-    """Explicit-3DGS trainer over views of one resolution (one view per step)."""
+def _as_list(cams):
+    return list(cams) if isinstance(cams, (list, tuple)) else [cams]
 
-    def __init__(self, params: Gaussians, width: int, height: int, lam: float = 0.2,
-                 bg=(0.0, 0.0, 0.0), lrs: dict | None = None, inst_capacity: int | None = None,
-                 load_balanced: bool = True, device="cuda"):
+
+class _Slot:
+    """Plan and image buffers for one tuple of view sizes."""
+
+    def __init__(self, params: Gaussians, sizes, cap: int, device, tuning=None):
+        self.sizes = sizes
+        self.plan = Plan(params.n, params.sh_degree, list(sizes), cap, device=device, tuning=tuning)
+        P = self.plan.pixels
+        self.rgb = torch.empty(3 * P, device=device)
+        self.disp = torch.empty(P, device=device)
+        self.T = torch.empty(P, device=device)
+        self.dL_drgb = torch.empty(3 * P, device=device)
+        self.dL_ddisp = torch.empty(P, device=device)
+        self.scratch = torch.empty(int(L.lib().gs_loss_scratch_floats(self.plan.handle)), device=device)
+
+
+class Trainer:
+    """Explicit-3DGS trainer.  ``Trainer(params, W, H)`` prepares single views
+    of W x H; other sizes and batches get their own plan on first use (or in
+    ``ensure_capacity``, which should see every batch before timing or
+    capture)."""
+
+    STAGES = ("preprocess", "bin_sort", "render_fwd", "loss", "render_bwd_blend", "preprocess_bwd", "adam")
+
+    def __init__(self, params: Gaussians, width: int | None = None, height: int | None = None, *,
+                 lam: float = 0.2, bg=(0.0, 0.0, 0.0), lrs: dict | None = None,
+                 inst_capacity: int | None = None, load_balanced: bool = True, disp_weight: float = 0.0,
+                 tuning: dict | None = None, device="cuda"):
+        """tuning: launch shapes of the plans ({"bucket": 32 | 64,
+        "bwd_warps": 2 | 4 | 8}), e.g. from autotune.autotune."""
         self.params = params
+        self.tuning = dict(tuning or {})
         self.grads = params.zeros_like()
         self.m = params.zeros_like()
         self.v = params.zeros_like()
-        self.width, self.height = int(width), int(height)
         self.lam = float(lam)
+        self.disp_weight = float(disp_weight)
         self.bg = tuple(float(b) for b in bg)
         self.lrs = dict(lrs or default_lrs())
         self.load_balanced = bool(load_balanced)
         self.device = device
         self.step_count = 0
-        P = self.width * self.height
-        self.rgb = torch.empty(3 * P, device=device)
-        self.disp = torch.empty(P, device=device)
-        self.T = torch.empty(P, device=device)
-        self.dL_drgb = torch.empty(3 * P, device=device)
+        self.d_step = torch.zeros(1, dtype=torch.int32, device=device)
         self.loss = torch.zeros(1, device=device)
-        cap = inst_capacity if inst_capacity is not None else max(1 << 20, 16 * params.n)
-        self._make_plan(cap)
+        self.cap = int(inst_capacity) if inst_capacity is not None else max(1 << 20, 16 * params.n)
+        self._slots: dict = {}
+        self._default = None
+        if width is not None:
+            self._default = self._slot(((int(width), int(height)),))
         self._bg = (ctypes.c_float * 3)(*self.bg)
         self._build_adam()
         self._cam_cache = {}
 
     # ------------------------------------------------------------ set-up
-    def _make_plan(self, cap: int) -> None:
-        self.plan = Plan(self.params.n, self.params.sh_degree, [(self.width, self.height)], cap,
-                         device=self.device)
-        self.scratch = torch.empty(int(L.lib().gs_loss_scratch_floats(self.plan.handle)),
-                                   device=self.device)
+    def _slot(self, sizes) -> _Slot:
+        s = self._slots.get(sizes)
+        if s is None:
+            s = _Slot(self.params, sizes, self.cap, self.device, self.tuning)
+            self._slots[sizes] = s
+        return s
+
+    @property
+    def plan(self) -> Plan:
+        return self._default.plan
+
+    @property
+    def rgb(self):
+        return self._default.rgb
+
+    def slot_for(self, cams) -> _Slot:
+        return self._slot(tuple((int(c.width), int(c.height)) for c in _as_list(cams)))
 
     def _build_adam(self) -> None:
         K = (self.params.sh_degree + 1) ** 2
@@ -70,75 +115,126 @@ class Trainer:
         self._pstruct = p.struct()
         self._gstruct = g.struct()
 
-    def _cam(self, cam):
-        key = id(cam)
+    def set_lr(self, name: str, lr: float) -> None:
+        """Change one learning rate (takes effect for eager steps; a captured
+        graph keeps the rates it was captured with)."""
+        self.lrs[name] = float(lr)
+        self._build_adam()
+
+    def _cam(self, cams):
+        cams = _as_list(cams)
+        key = tuple(id(c) for c in cams)
         c = self._cam_cache.get(key)
         if c is None:
-            c = (L.GsCamera * 1)(camera_struct(cam))
-            self._cam_cache[key] = (c, cam)
-            return c
+            arr = (L.GsCamera * len(cams))(*[camera_struct(x) for x in cams])
+            self._cam_cache[key] = (arr, cams)
+            return arr
         return c[0]
 
-    def ensure_capacity(self, cams, slack: float = 1.25) -> int:
-        """Bin every camera once and grow the instance capacity to fit the
-        largest view with `slack` to spare.  Synchronises; call outside timed
-        regions.  Returns the largest instance count seen."""
+    def ensure_capacity(self, batches, slack: float = 1.25) -> int:
+        """Bin every camera or batch once and grow the instance capacity to
+        fit the largest with `slack` to spare (all plans are rebuilt then).
+        Synchronises; call outside timed regions and before any capture.
+        Returns the largest instance count seen."""
         worst = 0
-        for cam in cams:
-            self.forward(cam)
-            st = self.plan.status()
+        for cams in batches:
+            self.forward(cams)
+            st = self.slot_for(cams).plan.status()
             if st["error"]:
                 raise L.GsError(st["error"], "device status")
             worst = max(worst, st["n_instances"])
-        if worst * slack > self.plan.inst_capacity:
-            self._make_plan(int(worst * slack) + 1024)
+        if worst * slack > self.cap:
+            self.cap = int(worst * slack) + 1024
+            sizes = list(self._slots)
+            default = self._default.sizes if self._default is not None else None
+            self._slots = {}
+            for sz in sizes:
+                self._slot(sz)
+            if default is not None:
+                self._default = self._slots[default]
         return worst
 
     # ------------------------------------------------------------ step
-    def forward(self, cam, stream=None) -> None:
+    def forward(self, cams, stream=None) -> _Slot:
         lib = L.lib()
-        s = _stream(stream)
-        ws = self.plan.ws.data_ptr()
-        c = self._cam(cam)
-        L.check(lib.gs_preprocess(self.plan.handle, ws, ctypes.byref(self._pstruct), c, s), "gs_preprocess")
-        L.check(lib.gs_bin_sort(self.plan.handle, ws, int(self.load_balanced), s), "gs_bin_sort")
-        L.check(lib.gs_render_fwd(self.plan.handle, ws, self._bg, self.rgb.data_ptr(), self.disp.data_ptr(),
-                                  self.T.data_ptr(), s), "gs_render_fwd")
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        sl = self.slot_for(cams)
+        h, ws = sl.plan.handle, sl.plan.ws.data_ptr()
+        c = self._cam(cams)
+        L.check(lib.gs_preprocess(h, ws, ctypes.byref(self._pstruct), c, s), "gs_preprocess")
+        L.check(lib.gs_bin_sort(h, ws, int(self.load_balanced), s), "gs_bin_sort")
+        L.check(lib.gs_render_fwd(h, ws, self._bg, sl.rgb.data_ptr(), sl.disp.data_ptr(), sl.T.data_ptr(), s),
+                "gs_render_fwd")
+        return sl
 
-    STAGES = ("preprocess", "bin_sort", "render_fwd", "loss", "render_bwd_blend", "preprocess_bwd", "adam")
-
-    def step(self, cam, target: torch.Tensor, stream=None, events=None) -> None:
-        """One full training step on view `cam` against `target` (flat planar
-        3*H*W float32 on the device).  The loss lands in self.loss.
+    def step(self, cams, target: torch.Tensor, target_disp: torch.Tensor | None = None, stream=None,
+             events=None) -> None:
+        """One full training step on a view or a batch of views against
+        `target` (flat planar colour, the views end to end, float32 on the
+        device) and optionally `target_disp` (disparity, weighted by
+        disp_weight).  The loss lands in self.loss.
 
         events: optional list of len(STAGES) + 1 CUDA events recorded on the
         stream around the stages, for per-stage timing."""
         lib = L.lib()
         st = stream if stream is not None else torch.cuda.current_stream()
         s = st.cuda_stream
-        h = self.plan.handle
-        ws = self.plan.ws.data_ptr()
-        c = self._cam(cam)
+        sl = self.slot_for(cams)
+        h, ws = sl.plan.handle, sl.plan.ws.data_ptr()
+        c = self._cam(cams)
         ev = (lambda i: events[i].record(st)) if events is not None else (lambda i: None)
+        use_disp = target_disp is not None and self.disp_weight > 0.0
         ev(0)
         L.check(lib.gs_preprocess(h, ws, ctypes.byref(self._pstruct), c, s), "gs_preprocess")
         ev(1)
         L.check(lib.gs_bin_sort(h, ws, int(self.load_balanced), s), "gs_bin_sort")
         ev(2)
-        L.check(lib.gs_render_fwd(h, ws, self._bg, self.rgb.data_ptr(), self.disp.data_ptr(),
-                                  self.T.data_ptr(), s), "gs_render_fwd")
+        L.check(lib.gs_render_fwd(h, ws, self._bg, sl.rgb.data_ptr(), sl.disp.data_ptr(), sl.T.data_ptr(), s),
+                "gs_render_fwd")
         ev(3)
-        L.check(lib.gs_loss(h, self.rgb.data_ptr(), target.data_ptr(), self.lam, None, None, 0.0,
-                            self.dL_drgb.data_ptr(), None, self.loss.data_ptr(), self.scratch.data_ptr(), s),
-                "gs_loss")
+        L.check(lib.gs_loss(h, sl.rgb.data_ptr(), target.data_ptr(), self.lam,
+                            sl.disp.data_ptr() if use_disp else None,
+                            target_disp.data_ptr() if use_disp else None, self.disp_weight if use_disp else 0.0,
+                            sl.dL_drgb.data_ptr(), sl.dL_ddisp.data_ptr() if use_disp else None,
+                            self.loss.data_ptr(), sl.scratch.data_ptr(), s), "gs_loss")
         ev(4)
-        L.check(lib.gs_render_bwd_blend(h, ws, self.rgb.data_ptr(), self.disp.data_ptr(),
-                                        self.dL_drgb.data_ptr(), None, s), "gs_render_bwd_blend")
+        L.check(lib.gs_render_bwd_blend(h, ws, sl.rgb.data_ptr(), sl.disp.data_ptr(), sl.dL_drgb.data_ptr(),
+                                        sl.dL_ddisp.data_ptr() if use_disp else None, s), "gs_render_bwd_blend")
         ev(5)
         L.check(lib.gs_preprocess_bwd(h, ws, ctypes.byref(self._pstruct), c, ctypes.byref(self._gstruct), s),
                 "gs_preprocess_bwd")
         ev(6)
         self.step_count += 1
-        L.check(lib.gs_adam_step_multi(self._adam, len(self._adam), 0.9, 0.999, 1e-15, self.step_count, s),
-                "gs_adam_step_multi")
+        L.check(lib.gs_adam_step_multi_dev(self._adam, len(self._adam), 0.9, 0.999, 1e-15,
+                                           self.d_step.data_ptr(), s), "gs_adam_step_multi_dev")
         ev(7)
+
+    def capture(self, cams, target: torch.Tensor, target_disp: torch.Tensor | None = None) -> "StepGraph":
+        """Capture one training step on `cams` into a CUDA graph.  The graph
+        reads the parameters, the optimiser state and `target` (and
+        `target_disp`) in place, so refilling those tensors between replays
+        is seen; the cameras, learning rates and buffer addresses are fixed
+        at capture.  Call ensure_capacity (and one eager step) first."""
+        return StepGraph(self, cams, target, target_disp)
+
+
+class StepGraph:
+    """A captured training step; ``replay()`` enqueues the whole step (every
+    launch of it) as one graph launch on the current stream."""
+
+    def __init__(self, trainer: Trainer, cams, target, target_disp=None):
+        self.trainer = trainer
+        self.cams = _as_list(cams)
+        trainer.slot_for(self.cams)  # plan and buffers exist before capture
+        trainer._cam(self.cams)
+        self.graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(self.graph, stream=side):
+            trainer.step(self.cams, target, target_disp)
+        trainer.step_count -= 1  # capture does not run the step
+        torch.cuda.current_stream().wait_stream(side)
+
+    def replay(self) -> None:
+        self.graph.replay()
+        self.trainer.step_count += 1

@@ -54,6 +54,26 @@ def test_plan_rejects_bad_arguments(lib):
     assert lib.gs_plan_create(10, 0, 1, bad, h, 100) is None
 
 
+def test_tuned_plan_choices(lib):
+    from paper_2601_19489_gb300 import _lib as L
+
+    w = (ctypes.c_int32 * 1)(1920)
+    h = (ctypes.c_int32 * 1)(1080)
+    for bucket, warps in ((16, 4), (128, 4), (32, 3), (64, 16)):
+        assert lib.gs_plan_create_tuned(1000, 0, 1, w, h, 1 << 20, ctypes.byref(L.GsTuning(bucket, warps))) is None
+    sizes = {}
+    for bucket in (0, 32, 64):
+        p = lib.gs_plan_create_tuned(1000, 0, 1, w, h, 1 << 22, ctypes.byref(L.GsTuning(bucket, 0)))
+        assert p
+        sizes[bucket] = lib.gs_plan_workspace_bytes(p)
+        lib.gs_plan_destroy(p)
+    p = lib.gs_plan_create(1000, 0, 1, w, h, 1 << 22)
+    assert lib.gs_plan_workspace_bytes(p) == sizes[0] == sizes[32]
+    lib.gs_plan_destroy(p)
+    # 64-splat buckets halve the checkpoint store: 20 bytes x 256 pixels per bucket
+    assert sizes[32] - sizes[64] >= 20 * 256 * ((1 << 22) // 64) - 4096
+
+
 def test_plan_sizes(lib):
     w = (ctypes.c_int32 * 2)(1920, 333)
     h = (ctypes.c_int32 * 2)(1080, 187)

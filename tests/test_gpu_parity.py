@@ -21,10 +21,10 @@ def AMB_FOR(cam):
     return oren.float32_bands(cam.width, cam.height)
 
 
-def _run_forward(gs, scene, cams, cap=1 << 22, lb=True):
+def _run_forward(gs, scene, cams, cap=1 << 22, lb=True, tuning=None):
     from paper_2601_19489_gb300 import api
 
-    plan = api.Plan(scene.n, scene.sh_degree, [(c.width, c.height) for c in cams], cap)
+    plan = api.Plan(scene.n, scene.sh_degree, [(c.width, c.height) for c in cams], cap, tuning=tuning)
     params = api.Gaussians.from_scene(scene)
     P = plan.pixels
     rgb = torch.empty(3 * P, device="cuda")
@@ -148,6 +148,9 @@ def test_binning_lists_match_oracle_and_lb_equals_sq(gs):
 
 # --------------------------------------------------------------- forward
 
+TUNINGS = [None, {"bucket": 64, "bwd_warps": 2}, {"bucket": 64, "bwd_warps": 8}, {"bucket": 32, "bwd_warps": 8}]
+
+
 @pytest.mark.parametrize("which", ["c1", "clustered_ragged"])
 def test_render_fwd_matches_oracle(gs, which):
     if which == "c1":
@@ -173,8 +176,11 @@ def test_render_fwd_matches_oracle(gs, which):
 
 # -------------------------------------------------------------- backward
 
+@pytest.mark.parametrize("tuning", TUNINGS)
 @pytest.mark.parametrize("which", ["c1", "clustered_ragged"])
-def test_render_bwd_matches_oracle(gs, which):
+def test_render_bwd_matches_oracle(gs, which, tuning):
+    """Every bucket size and backward CTA width the autotuner may pick gives
+    the oracle's gradients."""
     from paper_2601_19489_gb300 import _lib as L
     from paper_2601_19489_gb300 import api
 
@@ -184,7 +190,7 @@ def test_render_bwd_matches_oracle(gs, which):
         scene = synth.scene_clustered(30000, seed=9, sh_degree=3)
         cam = synth.ring_cameras(4, 272, 165)[0]
     W, H = cam.width, cam.height
-    plan, params, rgb, disp, T = _run_forward(gs, scene, [cam])
+    plan, params, rgb, disp, T = _run_forward(gs, scene, [cam], tuning=tuning)
     _, orec = _oracle_records(scene, cam)
     ref = oren.render_fwd(orec, BG, (0, 0, W, H), amb=AMB_FOR(cam))
     g, gd = synth.upstream_grads(11, W, H)

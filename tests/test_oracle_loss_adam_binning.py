@@ -208,3 +208,44 @@ def test_full_step_gradient_matches_finite_differences():
             arr[idx] = old
             fd = (fp - fm) / (2 * h)
             assert abs(grads[name][idx] - fd) <= 2e-5 * max(1e-3, abs(fd)), (name, idx, grads[name][idx], fd)
+
+
+def test_batch_loss_is_pixel_weighted_and_matches_finite_differences():
+    """A batch of views of unequal size: the batch gradient is the gradient
+    of the pooled per-pixel mean, and two copies of one view give exactly
+    that view's loss and gradient."""
+    sc = synth.scene_tiny(4, seed=32, sh_degree=1)
+    sc64 = synth.Scene(*(a.astype(np.float64) for a in sc.arrays()), sh_degree=1)
+    cams = [synth.camera_tiny(16, 16), synth.camera_tiny(24, 12)]
+    rng = np.random.default_rng(3)
+    targets = [rng.uniform(1.5, 2.0, size=(3, c.height, c.width)) for c in cams]
+    dts = [rng.uniform(0.0, 0.05, size=(c.height, c.width)) for c in cams]
+    kw = dict(bg=(0.1, 0.2, 0.3), lam=0.2, disp_targets=dts, disp_weight=0.1)
+    L, g = step.forward_backward_batch(sc64, cams, targets, **kw)
+    for c in cams:
+        amb = render.render_fwd(preprocess.pack_for_render(preprocess.project(
+            preprocess.params_from_scene(sc64), c, 1)), kw["bg"], (0, 0, c.width, c.height),
+            amb=(1e-3, 1e-3, 1e-3, 1e-6))["amb"]
+        assert not amb.any()
+    for name, idx in (("means", (1, 0)), ("log_scales", (2, 1)), ("opacity_logits", (3,)), ("sh", (0, 1, 2))):
+        arr = getattr(sc64, name)
+        h = 1e-6
+        old = arr[idx]
+        arr[idx] = old + h
+        fp = step.forward_backward_batch(sc64, cams, targets, **kw)[0]
+        arr[idx] = old - h
+        fm = step.forward_backward_batch(sc64, cams, targets, **kw)[0]
+        arr[idx] = old
+        fd = (fp - fm) / (2 * h)
+        assert abs(g[name][idx] - fd) <= 2e-5 * max(1e-3, abs(fd)), (name, idx, g[name][idx], fd)
+    # the pooled mean differs from the plain mean of the two views' losses
+    L0 = step.forward_backward(sc64, cams[0], targets[0], bg=kw["bg"], lam=0.2, disp_target=dts[0],
+                               disp_weight=0.1)
+    L1 = step.forward_backward(sc64, cams[1], targets[1], bg=kw["bg"], lam=0.2, disp_target=dts[1],
+                               disp_weight=0.1)
+    assert abs(L - (256 * L0[0] + 288 * L1[0]) / 544) < 1e-12
+    L2, g2 = step.forward_backward_batch(sc64, [cams[0], cams[0]], [targets[0]] * 2, bg=kw["bg"], lam=0.2,
+                                         disp_targets=[dts[0]] * 2, disp_weight=0.1)
+    assert abs(L2 - L0[0]) < 1e-12
+    for k in g2:
+        np.testing.assert_allclose(g2[k], L0[1][k], rtol=1e-12, atol=1e-15)
