@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched CUDA-graph measurement")
     ap.add_argument("--batched-steps", type=int, default=60)
+    ap.add_argument("--no-ng", action="store_true", help="skip the neural-Gaussian step measurement")
     ap.add_argument("--workload", choices=("explicit", "batched"), default="explicit",
                     help="batched: only the 8-view CUDA-graph step, one line per --batched-n")
     ap.add_argument("--batched-n", type=str, default="",
@@ -353,10 +354,14 @@ def run_ours(args, rank, world):
                      "buckets_last": st2["n_buckets"], "pairs_per_view": mean_pairs},
             "peaks": {"hbm_gbs": hbm or FALLBACK_HBM_GBS, "hbm_source": "measured" if hbm else "fallback",
                       "fp32_tflops": FP32_PEAK_TFLOPS}}
-    if world == 1 and not args.no_batched:
+    if world == 1 and not (args.no_batched and args.no_ng):
         del trainer
         torch.cuda.empty_cache()
+    if world == 1 and not args.no_batched:
         line["batched_graph"] = run_batched(args, dev, args.n, args.batched_steps)
+        torch.cuda.empty_cache()
+    if world == 1 and not args.no_ng:
+        line["neural_gaussians"] = run_ng(args, dev, max(1, args.n // 10), max(20, args.steps // 3))
     if world == 1 and not args.no_cpu_baseline:
         scene_h = scene
         cam = cams[0]
@@ -442,6 +447,43 @@ def run_batched(args, dev, n: int, steps: int, warmup: int = 3) -> dict:
             "graph_ms_per_step": 1e3 * t_graph / steps, "sequential_ms_per_8_views": 1e3 * t_seq / steps,
             "tuning": best, "autotune_ms_per_step": table, "clocks": clk.summary(),
             "instances_last": st["n_instances"]}
+
+
+def run_ng(args, dev, n_anchors: int, steps: int, warmup: int = 5) -> dict:
+    """Neural-Gaussian step: n_anchors anchors subsampled from the clustered
+    scene's points, 10 children each, the same 16 ring views at full size,
+    one view per step (decode, splat, loss, backward, decoder backward, Adam
+    on features, anchor scales and MLP)."""
+    import torch
+
+    import synth
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import NgTrainer
+
+    pts = synth.scene_clustered(args.n, seed=0, sh_degree=0).means
+    d = synth.ng_anchors(pts, n_anchors, seed=0)
+    cams = synth.ring_cameras(args.views, args.width, args.height)
+    targets = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1)).to(dev)
+               for v in range(len(cams))]
+    tr = NgTrainer(api.NgParams.from_dict(d, device=dev), args.width, args.height, lam=args.lam, device=dev)
+    tr.ensure_capacity(cams)
+    for s in range(warmup):
+        tr.step(cams[s % len(cams)], targets[s % len(cams)])
+    n_st = len(NgTrainer.STAGES)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_st + 1)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    for s in range(steps):
+        v = s % len(cams)
+        tr.step(cams[v], targets[v], events=evs[s])
+    torch.cuda.synchronize()
+    if tr.status() != 0 or tr.plan.status()["rc"] != 0:
+        raise RuntimeError("device status after the neural-Gaussian steps")
+    total = sum(evs[s][0].elapsed_time(evs[s][n_st]) for s in range(steps)) / steps
+    stage_ms = {name: float(np.mean([evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(steps)]))
+                for i, name in enumerate(NgTrainer.STAGES)}
+    return {"anchors": n_anchors, "children": 10 * n_anchors, "steps_per_s": 1e3 / total, "ms_per_step": total,
+            "stages_ms": stage_ms, "loss_last": tr.loss.item(),
+            "decoder": "x = [feature 32, view dir 3] -> 32 ReLU -> 140 = 10 children x 14; bf16 tcgen05 MMAs"}
 
 
 def run_batched_only(args):

@@ -313,9 +313,13 @@ GS_API int gs_ng_decode_fwd(const gs_ng_params *ng, const gs_camera *h_cam, gs_p
 /* Backward of gs_ng_decode_fwd for the same camera and workspace: maps the
  * children's parameter gradients to the anchors' feature and log-scale
  * gradients and the MLP gradients, ACCUMULATED (+=) into `grads` (its
- * anchor_xyz may be NULL). */
+ * anchor_xyz may be NULL).  With zero_child_grads != 0 the children's
+ * gradient arrays are set to zero as they are read (they are accumulators
+ * of the splatting backward, so the next step starts from zero without a
+ * separate pass); the arrays are written through the pointers in
+ * child_grads even though the struct itself is not modified. */
 GS_API int gs_ng_decode_bwd(const gs_ng_params *ng, const gs_camera *h_cam, const gs_params *child_grads,
-                            gs_ng_params *grads, void *d_ws, void *stream);
+                            int32_t zero_child_grads, gs_ng_params *grads, void *d_ws, void *stream);
 /* Synchronise `stream` and read the decoder's device status (GS_ERR_TIMEOUT
  * if a bounded wait for the tensor cores gave up). */
 GS_API int gs_ng_read_status(void *d_ws, int32_t *out_error, void *stream);

@@ -115,8 +115,8 @@ _SIGS = {
                                                  ctypes.c_int32, P]),
     "gs_ng_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "gs_ng_decode_fwd": (ctypes.c_int, [ctypes.POINTER(GsNgParams), P, ctypes.POINTER(GsParams), P, P]),
-    "gs_ng_decode_bwd": (ctypes.c_int, [ctypes.POINTER(GsNgParams), P, ctypes.POINTER(GsParams),
-                                        ctypes.POINTER(GsNgParams), P, P]),
+    "gs_ng_decode_bwd": (ctypes.c_int, [ctypes.POINTER(GsNgParams), P, ctypes.POINTER(GsParams), ctypes.c_int32,
+                                         ctypes.POINTER(GsNgParams), P, P]),
     "gs_ng_read_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), P]),
 }
 

@@ -289,13 +289,13 @@ def gs_ng_decode_fwd(ng: NgParams, cam, children: "Gaussians", ws: torch.Tensor,
 
 
 def gs_ng_decode_bwd(ng: NgParams, cam, child_grads: "Gaussians", grads: NgParams, ws: torch.Tensor,
-                     stream=None) -> None:
+                     zero_child_grads: bool = False, stream=None) -> None:
     c = (L.GsCamera * 1)(camera_struct(cam))
     p = ng.struct()
     cg = child_grads.struct()
     g = grads.struct()
-    L.check(L.lib().gs_ng_decode_bwd(ctypes.byref(p), c, ctypes.byref(cg), ctypes.byref(g), ws.data_ptr(),
-                                     _stream(stream)), "gs_ng_decode_bwd")
+    L.check(L.lib().gs_ng_decode_bwd(ctypes.byref(p), c, ctypes.byref(cg), int(bool(zero_child_grads)),
+                                     ctypes.byref(g), ws.data_ptr(), _stream(stream)), "gs_ng_decode_bwd")
 
 
 def gs_ng_status(ws: torch.Tensor, stream=None) -> int:

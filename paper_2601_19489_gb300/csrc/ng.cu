@@ -163,12 +163,14 @@ struct Args {
     int64_t n;  // anchors
     const float *xyz, *feat, *ls, *b1, *b2;
     float cam[3];
-    const __nv_bfloat16 *w1b, *w2b, *w2tb, *w1tb;  // prepared bf16 weights (row-major, padded)
+    const __nv_bfloat16 *w1b, *w2b, *w2tb, *w1tb;  // prepared bf16 weights (canonical operand layout, padded)
     __nv_bfloat16 *h_store;                        // bf16 h per anchor (forward -> backward)
     // forward outputs (children)
     float *c_means, *c_ls, *c_quats, *c_logits, *c_sh;
     // backward inputs (children's gradients) and outputs
-    const float *g_means, *g_ls, *g_quats, *g_logits, *g_sh;
+    float *g_means, *g_ls, *g_quats, *g_logits, *g_sh;
+    int zero_g;  // zero the children's gradients after reading them
+    int feat_vec;  // feat and d_feat are 16-byte aligned (float4 rows)
     float *d_feat, *d_ls, *partial;
     int *err;
 };
@@ -179,19 +181,19 @@ __global__ void __launch_bounds__(256) k_ng_prep(const float *__restrict__ w1, c
                                                  __nv_bfloat16 *w1tb) {
     for (int i = threadIdx.x; i < kHid * kInPad; i += blockDim.x) {  // W1 (32 x 48), K-major in the input
         const int r = i / kInPad, k = i % kInPad;
-        w1b[i] = __float2bfloat16_rn(k < kIn ? w1[r * kIn + k] : 0.0f);
+        w1b[canon(r, k, kInPad)] = __float2bfloat16_rn(k < kIn ? w1[r * kIn + k] : 0.0f);
     }
     for (int i = threadIdx.x; i < kOutPad * kHid; i += blockDim.x) {  // W2 (144 x 32)
         const int r = i / kHid, k = i % kHid;
-        w2b[i] = __float2bfloat16_rn(r < kOut ? w2[r * kHid + k] : 0.0f);
+        w2b[canon(r, k, kHid)] = __float2bfloat16_rn(r < kOut ? w2[r * kHid + k] : 0.0f);
     }
     for (int i = threadIdx.x; i < kHid * kOutPad; i += blockDim.x) {  // W2^T (32 x 144)
         const int r = i / kOutPad, k = i % kOutPad;
-        w2tb[i] = __float2bfloat16_rn(k < kOut ? w2[k * kHid + r] : 0.0f);
+        w2tb[canon(r, k, kOutPad)] = __float2bfloat16_rn(k < kOut ? w2[k * kHid + r] : 0.0f);
     }
     for (int i = threadIdx.x; i < kInPad * kHid; i += blockDim.x) {  // W1^T (48 x 32)
         const int r = i / kHid, k = i % kHid;
-        w1tb[i] = __float2bfloat16_rn(r < kIn ? w1[k * kIn + r] : 0.0f);
+        w1tb[canon(r, k, kHid)] = __float2bfloat16_rn(r < kIn ? w1[k * kIn + r] : 0.0f);
     }
 }
 
@@ -202,8 +204,20 @@ __device__ __forceinline__ void anchor_input(const Args &A, int64_t a, bool vali
         for (int k = 0; k < kInPad; ++k) x[k] = 0.0f;
         return;
     }
+    if (A.feat_vec) {
+        const float4 *f4 = reinterpret_cast<const float4 *>(A.feat + a * kFeat);
 #pragma unroll
-    for (int k = 0; k < kFeat; ++k) x[k] = bf16r(A.feat[a * kFeat + k]);
+        for (int q = 0; q < kFeat / 4; ++q) {
+            const float4 f = f4[q];
+            x[4 * q] = bf16r(f.x);
+            x[4 * q + 1] = bf16r(f.y);
+            x[4 * q + 2] = bf16r(f.z);
+            x[4 * q + 3] = bf16r(f.w);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kFeat; ++k) x[k] = bf16r(A.feat[a * kFeat + k]);
+    }
     float d0 = A.xyz[3 * a] - A.cam[0], d1 = A.xyz[3 * a + 1] - A.cam[1], d2 = A.xyz[3 * a + 2] - A.cam[2];
     const float inv = 1.0f / sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
     x[kFeat] = bf16r(d0 * inv);
@@ -211,6 +225,25 @@ __device__ __forceinline__ void anchor_input(const Args &A, int64_t a, bool vali
     x[kFeat + 2] = bf16r(d2 * inv);
 #pragma unroll
     for (int k = kIn; k < kInPad; ++k) x[k] = 0.0f;
+}
+
+// Block copy of a prepared operand (already in the canonical layout) into
+// shared memory, 16 bytes per thread and step.
+__device__ __forceinline__ void copy16(void *dst, const void *src, int bytes, int tid) {
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    for (int i = tid; i < bytes / 16; i += kThreads) d[i] = s[i];
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&p);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // ---------------------------------------------------------------- forward
@@ -221,6 +254,7 @@ struct FwdSmem {
     __nv_bfloat16 W2[kOutPad * kHid];    // GEMM 2 B (N = 144, K = 32)
     float Y[kTileA][kOutPad + 1];        // y = W2 h + b2
     float xyz[kTileA][3], ls[kTileA][6];
+    float b1[kHid], b2[kOutPad];
     uint64_t mbar;
     uint32_t tmem;
     int fail;
@@ -246,8 +280,10 @@ __global__ void __launch_bounds__(kThreads) k_ng_fwd(Args A) {
 #pragma unroll
         for (int k = 0; k < kInPad; ++k) S.X[canon(tid, k, kInPad)] = __float2bfloat16_rn(x[k]);
     }
-    for (int i = tid; i < kHid * kInPad; i += kThreads) S.W1[canon(i / kInPad, i % kInPad, kInPad)] = A.w1b[i];
-    for (int i = tid; i < kOutPad * kHid; i += kThreads) S.W2[canon(i / kHid, i % kHid, kHid)] = A.w2b[i];
+    copy16(S.W1, A.w1b, kHid * kInPad * 2, tid);
+    copy16(S.W2, A.w2b, kOutPad * kHid * 2, tid);
+    if (tid < kHid) S.b1[tid] = A.b1[tid];
+    for (int i = tid; i < kOutPad; i += kThreads) S.b2[i] = i < kOut ? A.b2[i] : 0.0f;
     for (int j = 0; j < 3; ++j) S.xyz[tid][j] = valid ? A.xyz[3 * a + j] : 0.0f;
     for (int j = 0; j < 6; ++j) S.ls[tid][j] = valid ? A.ls[6 * a + j] : 0.0f;
     fence_async_smem();
@@ -271,11 +307,18 @@ __global__ void __launch_bounds__(kThreads) k_ng_fwd(Args A) {
     {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+        uint32_t pk[kHid / 2];
 #pragma unroll
-        for (int c = 0; c < kHid; ++c) {
-            const __nv_bfloat16 hb = __float2bfloat16_rn(fmaxf(v[c] + A.b1[c], 0.0f));
-            S.H[canon(tid, c, kHid)] = hb;
-            if (valid) A.h_store[a * kHid + c] = hb;
+        for (int c = 0; c < kHid; c += 2) {
+            pk[c / 2] = pack_bf16x2(fmaxf(v[c] + S.b1[c], 0.0f), fmaxf(v[c + 1] + S.b1[c + 1], 0.0f));
+            // canonical layout: columns c, c + 1 are adjacent (c even)
+            *reinterpret_cast<uint32_t *>(&S.H[canon(tid, c, kHid)]) = pk[c / 2];
+        }
+        if (valid) {
+            uint4 *dst = reinterpret_cast<uint4 *>(A.h_store + a * kHid);
+#pragma unroll
+            for (int q = 0; q < kHid / 8; ++q)
+                dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         }
     }
     fence_async_smem();
@@ -302,11 +345,11 @@ __global__ void __launch_bounds__(kThreads) k_ng_fwd(Args A) {
         for (int ch = 0; ch < 4; ++ch) {
             tmem_ld32(row + ch * 32, v);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) S.Y[tid][ch * 32 + c] = v[c] + (ch * 32 + c < kOut ? A.b2[ch * 32 + c] : 0.f);
+            for (int c = 0; c < 32; ++c) S.Y[tid][ch * 32 + c] = v[c] + S.b2[ch * 32 + c];
         }
         tmem_ld16(row + 128, v);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) S.Y[tid][128 + c] = v[c] + (128 + c < kOut ? A.b2[128 + c] : 0.f);
+        for (int c = 0; c < 16; ++c) S.Y[tid][128 + c] = v[c] + S.b2[128 + c];
     }
     __syncthreads();
     {
@@ -358,7 +401,7 @@ struct BwdSmem {
     float dhf[kTileA][kHid + 1];         // dL/dh after the ReLU mask, rounded to bf16, as float
     float x[kTileA][kIn + 1];            // x (bf16 values) as float
     float xyz[kTileA][3], ls[kTileA][6], dls[kTileA][6];
-    float db1[kHid];
+    float db1[kHid], b2[kOutPad];
     uint64_t mbar;
     uint32_t tmem;
     int fail;
@@ -385,16 +428,24 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
         anchor_input(A, a, valid, x);
 #pragma unroll
         for (int k = 0; k < kIn; ++k) S.x[tid][k] = x[k];
+        const uint4 *src = reinterpret_cast<const uint4 *>(A.h_store + a * kHid);
 #pragma unroll
-        for (int c = 0; c < kHid; ++c) {
-            const __nv_bfloat16 hb = valid ? A.h_store[a * kHid + c] : __float2bfloat16_rn(0.0f);
-            S.H[canon(tid, c, kHid)] = hb;
-            S.hf[tid][c] = __bfloat162float(hb);
+        for (int q = 0; q < kHid / 8; ++q) {
+            const uint4 w = valid ? src[q] : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = 8 * q + 2 * e;
+                *reinterpret_cast<uint32_t *>(&S.H[canon(tid, c, kHid)]) = u[e];
+                S.hf[tid][c] = __uint_as_float(u[e] << 16);
+                S.hf[tid][c + 1] = __uint_as_float(u[e] & 0xffff0000u);
+            }
         }
     }
-    for (int i = tid; i < kOutPad * kHid; i += kThreads) S.W2[canon(i / kHid, i % kHid, kHid)] = A.w2b[i];
-    for (int i = tid; i < kHid * kOutPad; i += kThreads) S.W2T[canon(i / kOutPad, i % kOutPad, kOutPad)] = A.w2tb[i];
-    for (int i = tid; i < kInPad * kHid; i += kThreads) S.W1T[canon(i / kHid, i % kHid, kHid)] = A.w1tb[i];
+    copy16(S.W2, A.w2b, kOutPad * kHid * 2, tid);
+    copy16(S.W2T, A.w2tb, kHid * kOutPad * 2, tid);
+    copy16(S.W1T, A.w1tb, kInPad * kHid * 2, tid);
+    for (int i = tid; i < kOutPad; i += kThreads) S.b2[i] = i < kOut ? A.b2[i] : 0.0f;
     for (int j = 0; j < 3; ++j) S.xyz[tid][j] = valid ? A.xyz[3 * a + j] : 0.0f;
     for (int j = 0; j < 6; ++j) {
         S.ls[tid][j] = valid ? A.ls[6 * a + j] : 0.0f;
@@ -425,11 +476,11 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
         for (int ch = 0; ch < 4; ++ch) {
             tmem_ld32(my_lanes + ch * 32, v);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) S.Y[tid][ch * 32 + c] = v[c] + (ch * 32 + c < kOut ? A.b2[ch * 32 + c] : 0.f);
+            for (int c = 0; c < 32; ++c) S.Y[tid][ch * 32 + c] = v[c] + S.b2[ch * 32 + c];
         }
         tmem_ld16(my_lanes + 128, v);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) S.Y[tid][128 + c] = v[c] + (128 + c < kOut ? A.b2[128 + c] : 0.f);
+        for (int c = 0; c < 16; ++c) S.Y[tid][128 + c] = v[c] + S.b2[128 + c];
     }
     tc_fence_before();
     __syncthreads();
@@ -438,24 +489,51 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
         // depends on its own y only); anchor log-scale gradients in shared memory
         const int nch = na * kChild;
         const int64_t c0 = a0 * kChild;
-        for (int i = tid; i < nch * 3; i += kThreads) {
-            const int ch = i / 3, j = i - 3 * ch, r = ch / kChild, c = ch - r * kChild;
-            float &y0 = S.Y[r][c * kPer + j];
-            const float th = tanhf(y0), so = expf(S.ls[r][j]);
-            const float gm = A.g_means[3 * c0 + i];
-            atomicAdd(&S.dls[r][j], gm * th * so);
-            y0 = gm * so * (1.0f - th * th);
-            float &y4 = S.Y[r][c * kPer + 4 + j];
-            const float rgb = sigmoidf_(y4);
-            y4 = A.g_sh[3 * c0 + i] * kDcScale * rgb * (1.0f - rgb);
-            float &y7 = S.Y[r][c * kPer + 7 + j];
-            const float gl = A.g_ls[3 * c0 + i];
-            atomicAdd(&S.dls[r][3 + j], gl);
-            y7 = gl * sigmoidf_(-y7);
+        // the children's gradients are read four strides ahead of their use
+        // so that the loads overlap
+        constexpr int kU = 4;
+        for (int i0 = tid; i0 < nch * 3; i0 += kU * kThreads) {
+            float gm[kU], gs[kU], gl[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int i = i0 + u * kThreads;
+                const bool in = i < nch * 3;
+                gm[u] = in ? A.g_means[3 * c0 + i] : 0.0f;
+                gs[u] = in ? A.g_sh[3 * c0 + i] : 0.0f;
+                gl[u] = in ? A.g_ls[3 * c0 + i] : 0.0f;
+            }
+            if (A.zero_g) {
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int i = i0 + u * kThreads;
+                    if (i < nch * 3) {
+                        A.g_means[3 * c0 + i] = 0.0f;
+                        A.g_sh[3 * c0 + i] = 0.0f;
+                        A.g_ls[3 * c0 + i] = 0.0f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int i = i0 + u * kThreads;
+                if (i >= nch * 3) break;
+                const int ch = i / 3, j = i - 3 * ch, r = ch / kChild, c = ch - r * kChild;
+                float &y0 = S.Y[r][c * kPer + j];
+                const float th = tanhf(y0), so = expf(S.ls[r][j]);
+                atomicAdd(&S.dls[r][j], gm[u] * th * so);
+                y0 = gm[u] * so * (1.0f - th * th);
+                float &y4 = S.Y[r][c * kPer + 4 + j];
+                const float rgb = sigmoidf_(y4);
+                y4 = gs[u] * kDcScale * rgb * (1.0f - rgb);
+                float &y7 = S.Y[r][c * kPer + 7 + j];
+                atomicAdd(&S.dls[r][3 + j], gl[u]);
+                y7 = gl[u] * sigmoidf_(-y7);
+            }
         }
         for (int i = tid; i < nch * 4; i += kThreads) {
             const int ch = i >> 2, j = i & 3, r = ch / kChild, c = ch - r * kChild;
             S.Y[r][c * kPer + 10 + j] = A.g_quats[4 * c0 + i];
+            if (A.zero_g) A.g_quats[4 * c0 + i] = 0.0f;
         }
         for (int ch = tid; ch < nch; ch += kThreads) {
             const int r = ch / kChild, c = ch - r * kChild;
@@ -463,6 +541,7 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
             const float o = tanhf(y3);
             const float oc = fminf(o, kOpacityCeil);
             y3 = (o > 0.0f && o < kOpacityCeil) ? A.g_logits[c0 + ch] / (oc * (1.0f - oc)) * (1.0f - o * o) : 0.0f;
+            if (A.zero_g) A.g_logits[c0 + ch] = 0.0f;
         }
         // rows of absent anchors and the padding columns carry no gradient
         for (int i = tid; i < kTileA * kOutPad; i += kThreads) {
@@ -503,7 +582,8 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
 #pragma unroll
         for (int c = 0; c < kHid; ++c) {
             const float dh = S.hf[tid][c] > 0.0f ? v[c] : 0.0f;
-            atomicAdd(&S.db1[c], dh);
+            const float ws = warp_sum(dh);
+            if ((tid & 31) == 0) atomicAdd(&S.db1[c], ws);
             const __nv_bfloat16 db = __float2bfloat16_rn(dh);
             S.DH[canon(tid, c, kHid)] = db;
             S.dhf[tid][c] = __bfloat162float(db);
@@ -529,24 +609,55 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
         float v[32];
         tmem_ld32(my_lanes + 32, v);
         if (valid) {
+            if (A.feat_vec) {
+                float4 *df = reinterpret_cast<float4 *>(A.d_feat + a * kFeat);
 #pragma unroll
-            for (int c = 0; c < kFeat; ++c) A.d_feat[a * kFeat + c] += v[c];
+                for (int q = 0; q < kFeat / 4; ++q) {
+                    float4 d = df[q];
+                    d.x += v[4 * q];
+                    d.y += v[4 * q + 1];
+                    d.z += v[4 * q + 2];
+                    d.w += v[4 * q + 3];
+                    df[q] = d;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < kFeat; ++c) A.d_feat[a * kFeat + c] += v[c];
+            }
 #pragma unroll
             for (int j = 0; j < 6; ++j) A.d_ls[6 * a + j] += S.dls[tid][j];
         }
     }
-    // weight gradients of the tile: dW2 = dy_bf^T h, dW1 = dh_bf^T x
-    for (int i = tid; i < kOut * kHid; i += kThreads) {
-        const int o = i / kHid, k = i - o * kHid;
-        float s = 0.0f;
-        for (int r = 0; r < kTileA; ++r) s += bf16r(S.Y[r][o]) * S.hf[r][k];
-        part[i] = s;
+    // weight gradients of the tile: dW2 = dy_bf^T h, dW1 = dh_bf^T x.  A
+    // thread owns one output row and a block of columns and keeps the block's
+    // sums in registers; per anchor it reads its own y (consecutive threads,
+    // consecutive rows) and the anchor's h or x (the same address across the
+    // warp: a broadcast).
+    for (int i = tid; i < kOut * 2; i += kThreads) {
+        const int o = i >> 1, k0 = (i & 1) * 16;
+        float s[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) s[c] = 0.0f;
+        for (int r = 0; r < kTileA; ++r) {
+            const float y = bf16r(S.Y[r][o]);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) s[c] += y * S.hf[r][k0 + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) part[o * kHid + k0 + c] = s[c];
     }
-    for (int i = tid; i < kHid * kIn; i += kThreads) {
-        const int h = i / kIn, k = i - h * kIn;
-        float s = 0.0f;
-        for (int r = 0; r < kTileA; ++r) s += S.dhf[r][h] * S.x[r][k];
-        part[kOut * kHid + i] = s;
+    for (int i = tid; i < kHid * 5; i += kThreads) {
+        const int h = i / 5, k0 = (i - h * 5) * 7;
+        float s[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) s[c] = 0.0f;
+        for (int r = 0; r < kTileA; ++r) {
+            const float d = S.dhf[r][h];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) s[c] += d * S.x[r][k0 + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 7; ++c) part[kOut * kHid + h * kIn + k0 + c] = s[c];
     }
     if (tid < kHid) part[kOut * kHid + kHid * kIn + kOut + tid] = S.db1[tid];
 cleanup:
@@ -620,6 +731,7 @@ static Args base_args(const gs_ng_params *p, const gs_camera *cam, void *ws) {
     A.n = p->n_anchors;
     A.xyz = p->anchor_xyz;
     A.feat = p->feat;
+    A.feat_vec = ((uintptr_t)p->feat & 15) == 0;
     A.ls = p->anchor_ls;
     A.b1 = p->b1;
     A.b2 = p->b2;
@@ -680,7 +792,7 @@ extern "C" int gs_ng_decode_fwd(const gs_ng_params *p, const gs_camera *cam, gs_
 }
 
 extern "C" int gs_ng_decode_bwd(const gs_ng_params *p, const gs_camera *cam, const gs_params *child_grads,
-                                gs_ng_params *grads, void *ws, void *stream) {
+                                int32_t zero_child_grads, gs_ng_params *grads, void *ws, void *stream) {
     int rc = ng::check_ng(p);
     if (rc) return rc;
     if (!cam || !ws || !child_grads || !grads || child_grads->n != p->n_anchors * ng::kChild ||
@@ -702,7 +814,9 @@ extern "C" int gs_ng_decode_bwd(const gs_ng_params *p, const gs_camera *cam, con
     A.g_quats = child_grads->quats;
     A.g_logits = child_grads->opacity_logits;
     A.g_sh = child_grads->sh;
+    A.zero_g = zero_child_grads != 0;
     A.d_feat = grads->feat;
+    A.feat_vec = A.feat_vec && ((uintptr_t)grads->feat & 15) == 0;
     A.d_ls = grads->anchor_ls;
     const int tiles = (int)((p->n_anchors + ng::kTileA - 1) / ng::kTileA);
     ng::k_ng_bwd<<<tiles, ng::kThreads, smem, s>>>(A);

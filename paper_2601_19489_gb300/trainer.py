@@ -19,7 +19,8 @@ import ctypes
 import torch
 
 from . import _lib as L
-from .api import Gaussians, Plan, adam_groups_array, camera_struct
+from .api import (Gaussians, NgParams, Plan, adam_groups_array, camera_struct, gs_ng_workspace,
+                  ng_children)
 
 
 def default_lrs(extent: float = 1.0) -> dict:
@@ -63,8 +64,6 @@ class Trainer:
         self.params = params
         self.tuning = dict(tuning or {})
         self.grads = params.zeros_like()
-        self.m = params.zeros_like()
-        self.v = params.zeros_like()
         self.lam = float(lam)
         self.disp_weight = float(disp_weight)
         self.bg = tuple(float(b) for b in bg)
@@ -103,6 +102,9 @@ class Trainer:
         return self._slot(tuple((int(c.width), int(c.height)) for c in _as_list(cams)))
 
     def _build_adam(self) -> None:
+        if not hasattr(self, "m"):
+            self.m = self.params.zeros_like()
+            self.v = self.params.zeros_like()
         K = (self.params.sh_degree + 1) ** 2
         p, g, m, v = self.params, self.grads, self.m, self.v
         groups = []
@@ -176,38 +178,43 @@ class Trainer:
 
         events: optional list of len(STAGES) + 1 CUDA events recorded on the
         stream around the stages, for per-stage timing."""
-        lib = L.lib()
         st = stream if stream is not None else torch.cuda.current_stream()
-        s = st.cuda_stream
+        ev = (lambda i: events[i].record(st)) if events is not None else (lambda i: None)
+        ev(0)
+        self._splat_stages(cams, target, target_disp, st.cuda_stream, ev, 1)
+        self.step_count += 1
+        L.check(L.lib().gs_adam_step_multi_dev(self._adam, len(self._adam), 0.9, 0.999, 1e-15,
+                                               self.d_step.data_ptr(), st.cuda_stream), "gs_adam_step_multi_dev")
+        ev(7)
+
+    def _splat_stages(self, cams, target, target_disp, s, ev, e0: int) -> None:
+        """preprocess .. preprocess backward of self.params on `cams`; the
+        parameter gradients accumulate into self.grads.  Records events
+        e0 .. e0 + 5 after each stage."""
+        lib = L.lib()
         sl = self.slot_for(cams)
         h, ws = sl.plan.handle, sl.plan.ws.data_ptr()
         c = self._cam(cams)
-        ev = (lambda i: events[i].record(st)) if events is not None else (lambda i: None)
         use_disp = target_disp is not None and self.disp_weight > 0.0
-        ev(0)
         L.check(lib.gs_preprocess(h, ws, ctypes.byref(self._pstruct), c, s), "gs_preprocess")
-        ev(1)
+        ev(e0)
         L.check(lib.gs_bin_sort(h, ws, int(self.load_balanced), s), "gs_bin_sort")
-        ev(2)
+        ev(e0 + 1)
         L.check(lib.gs_render_fwd(h, ws, self._bg, sl.rgb.data_ptr(), sl.disp.data_ptr(), sl.T.data_ptr(), s),
                 "gs_render_fwd")
-        ev(3)
+        ev(e0 + 2)
         L.check(lib.gs_loss(h, sl.rgb.data_ptr(), target.data_ptr(), self.lam,
                             sl.disp.data_ptr() if use_disp else None,
                             target_disp.data_ptr() if use_disp else None, self.disp_weight if use_disp else 0.0,
                             sl.dL_drgb.data_ptr(), sl.dL_ddisp.data_ptr() if use_disp else None,
                             self.loss.data_ptr(), sl.scratch.data_ptr(), s), "gs_loss")
-        ev(4)
+        ev(e0 + 3)
         L.check(lib.gs_render_bwd_blend(h, ws, sl.rgb.data_ptr(), sl.disp.data_ptr(), sl.dL_drgb.data_ptr(),
                                         sl.dL_ddisp.data_ptr() if use_disp else None, s), "gs_render_bwd_blend")
-        ev(5)
+        ev(e0 + 4)
         L.check(lib.gs_preprocess_bwd(h, ws, ctypes.byref(self._pstruct), c, ctypes.byref(self._gstruct), s),
                 "gs_preprocess_bwd")
-        ev(6)
-        self.step_count += 1
-        L.check(lib.gs_adam_step_multi_dev(self._adam, len(self._adam), 0.9, 0.999, 1e-15,
-                                           self.d_step.data_ptr(), s), "gs_adam_step_multi_dev")
-        ev(7)
+        ev(e0 + 5)
 
     def capture(self, cams, target: torch.Tensor, target_disp: torch.Tensor | None = None) -> "StepGraph":
         """Capture one training step on `cams` into a CUDA graph.  The graph
@@ -238,3 +245,89 @@ class StepGraph:
     def replay(self) -> None:
         self.graph.replay()
         self.trainer.step_count += 1
+
+
+def default_ng_lrs() -> dict:
+    """Scaffold-GS style rates for the decoder (the paper gives none)."""
+    return {"feat": 7.5e-3, "anchor_ls": 7e-3, "mlp": 4e-3}
+
+
+class NgTrainer(Trainer):
+    """Neural-Gaussian training step (Sec. 2.3) on one view: the decoder
+    infers the anchors' child Gaussians for the view, the children go
+    through the same splatting kernels as explicit 3DGS, and their gradients
+    flow back through the decoder into the anchor features, the anchors'
+    log-scales and the MLP, which one Adam update then trains.  The anchor
+    positions stay fixed."""
+
+    STAGES = ("decode", "preprocess", "bin_sort", "render_fwd", "loss", "render_bwd_blend", "preprocess_bwd",
+              "decode_bwd", "adam")
+
+    def __init__(self, ng: NgParams, width: int | None = None, height: int | None = None, *,
+                 ng_lrs: dict | None = None, **kw):
+        self.ng = ng
+        self.ng_grads = ng.zeros_like()
+        self.ng_m = ng.zeros_like()
+        self.ng_v = ng.zeros_like()
+        self.ng_lrs = dict(ng_lrs or default_ng_lrs())
+        self.ng_ws = gs_ng_workspace(ng.n, device=kw.get("device", "cuda"))
+        children = ng_children(ng.n, device=kw.get("device", "cuda"))
+        kw.setdefault("inst_capacity", max(1 << 20, 16 * children.n))
+        super().__init__(children, width, height, **kw)
+        self._ngp = ng.struct()
+        self._ngg = self.ng_grads.struct()
+
+    @property
+    def children(self) -> Gaussians:
+        return self.params
+
+    def _build_adam(self) -> None:
+        groups = []
+        for name, lr in (("feat", self.ng_lrs["feat"]), ("anchor_ls", self.ng_lrs["anchor_ls"]),
+                         ("w1", self.ng_lrs["mlp"]), ("b1", self.ng_lrs["mlp"]), ("w2", self.ng_lrs["mlp"]),
+                         ("b2", self.ng_lrs["mlp"])):
+            groups.append({"p": getattr(self.ng, name), "g": getattr(self.ng_grads, name),
+                           "m": getattr(self.ng_m, name), "v": getattr(self.ng_v, name), "lr": lr})
+        self._adam = adam_groups_array(groups)
+        self._pstruct = self.params.struct()
+        self._gstruct = self.grads.struct()
+
+    def _decode(self, cam, s) -> None:
+        c = self._cam([cam])
+        L.check(L.lib().gs_ng_decode_fwd(ctypes.byref(self._ngp), c, ctypes.byref(self._pstruct),
+                                         self.ng_ws.data_ptr(), s), "gs_ng_decode_fwd")
+
+    def forward(self, cams, stream=None):
+        cam = _as_list(cams)
+        if len(cam) != 1:
+            raise ValueError("the neural-Gaussian step decodes for one view at a time")
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        self._decode(cam[0], s)
+        return super().forward(cams, stream)
+
+    def step(self, cams, target: torch.Tensor, target_disp: torch.Tensor | None = None, stream=None,
+             events=None) -> None:
+        cam = _as_list(cams)
+        if len(cam) != 1:
+            raise ValueError("the neural-Gaussian step decodes for one view at a time")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        s = st.cuda_stream
+        ev = (lambda i: events[i].record(st)) if events is not None else (lambda i: None)
+        ev(0)
+        self._decode(cam[0], s)
+        ev(1)
+        self._splat_stages(cam, target, target_disp, s, ev, 2)
+        c = self._cam(cam)
+        L.check(L.lib().gs_ng_decode_bwd(ctypes.byref(self._ngp), c, ctypes.byref(self._gstruct), 1,
+                                         ctypes.byref(self._ngg), self.ng_ws.data_ptr(), s), "gs_ng_decode_bwd")
+        ev(8)
+        self.step_count += 1
+        L.check(L.lib().gs_adam_step_multi_dev(self._adam, len(self._adam), 0.9, 0.999, 1e-15,
+                                               self.d_step.data_ptr(), s), "gs_adam_step_multi_dev")
+        ev(9)
+
+    def status(self) -> int:
+        """Synchronise and return the decoder's device status (0 = ok)."""
+        e = ctypes.c_int32(0)
+        return int(L.lib().gs_ng_read_status(self.ng_ws.data_ptr(), ctypes.byref(e),
+                                             torch.cuda.current_stream().cuda_stream))

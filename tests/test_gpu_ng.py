@@ -129,3 +129,86 @@ def test_ng_decode_backward_matches_oracle(gs, n_anchors):
         bad = np.abs(g - r) > tol
         assert bad.sum() == 0, (k, bad.sum(), np.abs(g - r).max(), np.abs(r).max())
         assert np.linalg.norm(g - r) <= 1e-3 * np.linalg.norm(r), (k, np.linalg.norm(g - r), np.linalg.norm(r))
+
+
+def _tiny_chain(seed=3, W=48, H=48):
+    """Six anchors in front of a 48 x 48 camera, children a few pixels wide;
+    seed 3: no decoder value near a bfloat16 midpoint and no pixel near a
+    float32 blend threshold."""
+    cam = synth.camera_tiny(W, H)
+    pts = synth.scene_tiny(6, seed=seed, sh_degree=0, width=W, height=H).means
+    d = synth.ng_anchors(pts, 6, seed=seed)
+    d["anchor_ls"][:, 0:3] = np.log(0.15)
+    d["anchor_ls"][:, 3:6] = np.log(0.25)
+    target = np.random.default_rng(seed).uniform(2.0, 2.5, size=(3, H, W))
+    return cam, d, target
+
+
+def test_ng_training_step_chain_matches_oracle(gs):
+    """decode -> splat -> loss -> splat backward -> decode backward, the
+    decoder gradients against the oracle's chain.  The children's gradients
+    reaching the decoder carry the splatting backward's float32 error
+    (within 1e-3 relative, the splatting parity bar), which the bfloat16
+    rounding of dL/dy may turn into one bfloat16 step (2^-8 relative) per
+    element; the decoder gradients are compared at 1e-2 of their scale."""
+    from oracle import step as ostep
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import NgTrainer
+
+    cam, d, target = _tiny_chain()
+    out, cache = ong.decode_forward(d["anchor_xyz"], d["feat"], d["anchor_ls"], d["w1"], d["b1"], d["w2"],
+                                    d["b2"], np.zeros(3))
+    sc = synth.Scene(out["means"].numpy(), out["log_scales"].numpy(), out["quats"].numpy(),
+                     out["opacity_logits"].numpy(), out["sh"].numpy(), 0)
+    ref_L, g, _ = ostep.forward_backward(sc, cam, target, lam=0.2)
+    ref = ong.decode_backward(cache, g)
+
+    ng = api.NgParams.from_dict(d)
+    tr = NgTrainer(ng, cam.width, cam.height, lam=0.2, inst_capacity=1 << 16)
+    tgt = torch.from_numpy(target.reshape(-1).astype(np.float32)).cuda()
+    # the stages of NgTrainer.step up to (not including) its Adam update
+    s = torch.cuda.current_stream().cuda_stream
+    tr._decode(cam, s)
+    tr._splat_stages([cam], tgt, None, s, lambda i: None, 0)
+    import ctypes
+    from paper_2601_19489_gb300 import _lib as L
+    L.check(L.lib().gs_ng_decode_bwd(ctypes.byref(tr._ngp), tr._cam([cam]), ctypes.byref(tr._gstruct), 1,
+                                     ctypes.byref(tr._ngg), tr.ng_ws.data_ptr(), s), "gs_ng_decode_bwd")
+    assert tr.status() == 0 and tr.plan.status()["rc"] == 0
+    np.testing.assert_allclose(tr.loss.item(), ref_L, rtol=1e-5)
+    for t in tr.grads.tensors():  # consumed by the decoder backward
+        assert float(t.abs().max()) == 0.0
+    for k in ("feat", "anchor_ls", "w1", "b1", "w2", "b2"):
+        got = to_np(getattr(tr.ng_grads, k)).astype(np.float64).reshape(ref[k].shape)
+        r = ref[k]
+        assert np.linalg.norm(got - r) <= 1e-2 * np.linalg.norm(r), (k, np.linalg.norm(got - r), np.linalg.norm(r))
+        assert np.abs(got - r).max() <= 1e-2 * np.abs(r).max(), (k, np.abs(got - r).max(), np.abs(r).max())
+
+
+def test_ng_trainer_learns_and_replays_as_a_graph(gs):
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import NgTrainer
+
+    cam, d, target = _tiny_chain()
+    target = np.clip(target - 1.8, 0.0, 1.0)  # reachable colours
+    tgt = torch.from_numpy(target.reshape(-1).astype(np.float32)).cuda()
+    runs = []
+    for graphed in (False, True):
+        ng = api.NgParams.from_dict(d)
+        xyz0 = ng.anchor_xyz.clone()
+        tr = NgTrainer(ng, cam.width, cam.height, lam=0.2, inst_capacity=1 << 16)
+        tr.ensure_capacity([cam])
+        losses = []
+        tr.step(cam, tgt)
+        losses.append(tr.loss.item())
+        g = tr.capture(cam, tgt) if graphed else None
+        for _ in range(29):
+            g.replay() if graphed else tr.step(cam, tgt)
+            losses.append(tr.loss.item())
+        torch.cuda.synchronize()
+        assert tr.status() == 0 and tr.plan.status()["rc"] == 0
+        assert int(tr.d_step.item()) == 30
+        assert torch.equal(ng.anchor_xyz, xyz0)  # anchors stay where they are
+        runs.append(losses)
+    assert runs[0][-1] < 0.9 * runs[0][0], runs[0]
+    np.testing.assert_allclose(runs[1], runs[0], rtol=1e-3)
