@@ -11,6 +11,8 @@ from .scenes import (  # noqa: F401
     camera_c1,
     ring_cameras,
     mixed_ring_cameras,
+    orbit_cameras,
+    recon_init,
     ng_anchors,
     scene_c1,
     scene_clustered,

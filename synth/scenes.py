@@ -190,6 +190,47 @@ def mixed_ring_cameras(n_views: int = 8, seed: int = 0) -> list[Camera]:
     return cams
 
 
+def orbit_cameras(n_views: int = 200, width: int = 1600, height: int = 1060, fov_x_deg: float = 60.0,
+                  radius: float = 4.0, elev_min: float = -1.2, elev_max: float = 1.8) -> list[Camera]:
+    """Views on a ring around the origin whose height swings between
+    elev_min and elev_max three times per revolution (ring and elevation
+    views of one object-centred capture)."""
+    cams = []
+    fx = 0.5 * width / np.tan(np.deg2rad(fov_x_deg) * 0.5)
+    for v in range(n_views):
+        th = 2.0 * np.pi * v / n_views
+        y = elev_min + (elev_max - elev_min) * 0.5 * (1.0 - np.cos(3.0 * th))
+        eye = np.array([radius * np.sin(th), y, radius * np.cos(th)])
+        R, t = _look_at(eye, np.zeros(3))
+        cams.append(Camera(fx, fx, 0.5 * width, 0.5 * height, R, t, width, height))
+    return cams
+
+
+def recon_init(gt: Scene, n_init: int, seed: int = 0, pos_noise: float = 0.02, rgb_noise: float = 0.05,
+               sh_degree: int = 3) -> Scene:
+    """Starting point of a reconstruction from a sparse point cloud: n_init
+    ground-truth centres with N(0, pos_noise) jitter, their DC colour with
+    N(0, rgb_noise) noise, no higher SH, isotropic log-scale from the mean
+    distance to the three nearest starting points, opacity 0.1, identity
+    rotation (the usual 3DGS initialisation)."""
+    from scipy.spatial import cKDTree
+
+    rng = _rng(seed)
+    idx = rng.choice(gt.n, size=n_init, replace=False)
+    means = gt.means[idx].astype(np.float64) + rng.normal(0.0, pos_noise, size=(n_init, 3))
+    dist, _ = cKDTree(means).query(means, k=4)
+    d = np.maximum(dist[:, 1:].mean(axis=1), 1e-4)
+    log_scales = np.repeat(np.log(d)[:, None], 3, axis=1)
+    quats = np.zeros((n_init, 4), dtype=np.float32)
+    quats[:, 0] = 1.0
+    logits = np.full(n_init, np.log(0.1 / 0.9))
+    K = (sh_degree + 1) ** 2
+    sh = np.zeros((n_init, K, 3), dtype=np.float32)
+    sh[:, 0, :] = gt.sh[idx, 0, :] + rng.normal(0.0, rgb_noise * _DC_SCALE, size=(n_init, 3))
+    return Scene(means.astype(np.float32), log_scales.astype(np.float32), quats, logits.astype(np.float32), sh,
+                 sh_degree, meta={"recipe": "recon_init", "seed": seed, "n": n_init})
+
+
 def scene_tiny(n: int = 6, seed: int = 0, sh_degree: int = 1, width: int = 16,
                height: int = 16) -> Scene:
     """A handful of Gaussians in front of ``camera_tiny`` (finite-difference
