@@ -216,6 +216,43 @@ class Trainer:
                 "gs_preprocess_bwd")
         ev(e0 + 5)
 
+    # ------------------------------------------------------------ checkpoint
+    def _state_tensors(self) -> dict:
+        out = {}
+        for group, g in (("params", self.params), ("m", self.m), ("v", self.v)):
+            for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+                out[f"{group}.{name}"] = getattr(g, name)
+        return out
+
+    def state_dict(self) -> dict:
+        """Everything a resumed run needs: parameters, Adam moments and step
+        count (host copies), learning rates and loss settings."""
+        st = {k: v.detach().cpu().clone() for k, v in self._state_tensors().items()}
+        st["d_step"] = int(self.d_step.item())
+        st["step_count"] = self.step_count
+        st["lrs"] = dict(self.lrs)
+        st["lam"], st["disp_weight"] = self.lam, self.disp_weight
+        return st
+
+    def load_state_dict(self, st: dict) -> None:
+        """Copy a state_dict in place: the device buffers keep their
+        addresses, so captured graphs stay valid."""
+        for k, v in self._state_tensors().items():
+            if st[k].shape != v.shape:
+                raise ValueError(f"{k}: shape {tuple(st[k].shape)} != {tuple(v.shape)}")
+            v.data.copy_(st[k].to(v.device))
+        self.d_step.fill_(int(st["d_step"]))
+        self.step_count = int(st["step_count"])
+        self.lam, self.disp_weight = float(st["lam"]), float(st["disp_weight"])
+        self.lrs = dict(st["lrs"])
+        self._build_adam()
+
+    def save(self, path: str) -> None:
+        torch.save(self.state_dict(), path)
+
+    def load(self, path: str) -> None:
+        self.load_state_dict(torch.load(path, map_location="cpu", weights_only=False))
+
     def capture(self, cams, target: torch.Tensor, target_disp: torch.Tensor | None = None) -> "StepGraph":
         """Capture one training step on `cams` into a CUDA graph.  The graph
         reads the parameters, the optimiser state and `target` (and
@@ -280,6 +317,17 @@ class NgTrainer(Trainer):
     @property
     def children(self) -> Gaussians:
         return self.params
+
+    def _state_tensors(self) -> dict:
+        out = {}
+        for group, g in (("ng", self.ng), ("m", self.ng_m), ("v", self.ng_v)):
+            for name in ("anchor_xyz", "feat", "anchor_ls", "w1", "b1", "w2", "b2"):
+                out[f"{group}.{name}"] = getattr(g, name)
+        return out
+
+    def load_state_dict(self, st: dict) -> None:
+        super().load_state_dict(st)
+        self._ngp = self.ng.struct()
 
     def _build_adam(self) -> None:
         groups = []
