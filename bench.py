@@ -249,7 +249,18 @@ def run_ours(args, rank, world):
     L.load()
     scene, cams = workload(args)
     params = api.Gaussians.from_scene(scene, device=dev)
-    trainer = Trainer(params, args.width, args.height, lam=args.lam, load_balanced=not args.sq, device=dev)
+    tuning, lb, table = {}, not args.sq, None
+    if not args.sq:  # launch shapes from the autotuner, on this workload's own views
+        from paper_2601_19489_gb300.autotune import autotune
+
+        tgt = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1)).to(dev)
+               for v in range(2)]
+        best, table = autotune(params, [[cams[0]], [cams[1]]], tgt, lam=args.lam, device=dev)
+        tuning = {"bucket": best["bucket"], "bwd_warps": best["bwd_warps"]}
+        lb = best["load_balanced"]
+        del tgt
+    trainer = Trainer(params, args.width, args.height, lam=args.lam, load_balanced=lb, tuning=tuning, device=dev)
+    trainer.autotune_table = table
     ntiles = ((args.width + 15) // 16) * ((args.height + 15) // 16)
     trainer.plan_tile_bits = max(1, int(np.ceil(np.log2(ntiles))))
     targets_h = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1))
@@ -349,7 +360,11 @@ def run_ours(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_of(args), "clocks": clocks, "e2e": e2e,
+            "config": {**config_of(args), "binning": "load_balanced" if trainer.load_balanced else "sequential",
+                       "bucket": trainer.slot_for([cams[0]]).plan.tuning["bucket"],
+                       "bwd_warps": trainer.slot_for([cams[0]]).plan.tuning["bwd_warps"],
+                       "autotune_ms_per_step": trainer.autotune_table},
+            "clocks": clocks, "e2e": e2e,
             "gpu_launches": kernels_per_step(trainer) * args.steps,
             "roofline": roof,
             "stages_ms": stage_ms,

@@ -225,13 +225,18 @@ int sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *v
     uint32_t *totals = hist + kHist;
     uint32_t *kin = keys_a, *vin = vals_a, *kout = keys_b, *vout = vals_b;
     int cur = 0;
-    for (int bit = begin_bit; bit < end_bit; bit += kRadixBits) {
-        const int nb = end_bit - bit < kRadixBits ? end_bit - bit : kRadixBits;
+    // as many passes as 8-bit digits need, the bits spread evenly over them
+    // (13 tile bits: 7 + 6 rather than 8 + 5), which lengthens the per-digit
+    // runs each block writes in the pass with the most digits
+    const int passes = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
+    for (int bit = begin_bit, p = 0; bit < end_bit; ++p) {
+        const int nb = (end_bit - bit + (passes - p) - 1) / (passes - p);
         const uint32_t mask = (1u << nb) - 1u;
         k_upsweep<<<kSortBlocks, kSortThreads, 0, s>>>(kin, n_host, n_dev, bit, mask, hist);
         k_scan_digit<<<kRadix, kSortThreads, 0, s>>>(hist, totals);
         k_downsweep<<<kSortBlocks, kSortThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, bit,
                                                          mask, hist, totals);
+        bit += nb;
         uint32_t *tk = kin, *tv = vin;
         kin = kout;
         vin = vout;

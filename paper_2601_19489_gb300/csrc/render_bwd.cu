@@ -35,8 +35,11 @@ struct BwdShared {
     uint32_t next;                            // next unclaimed bucket of the tile
 };
 
+// Per-splat sums over its pixels; the mean's gradient is linear in
+// (dx, dy) with the splat's conic as coefficients, so only sx = sum dpw dx
+// and sy = sum dpw dy are accumulated and the conic is applied once.
 struct SplatGrad {
-    float mx, my, xx, xy, yy, pw, r, g, b, iz;
+    float sx, sy, xx, xy, yy, pw, r, g, b, iz;
 };
 
 // One (splat, pixel) pair of the pipeline: T, S enter as the state in front
@@ -63,12 +66,13 @@ __device__ __forceinline__ void bwd_pair(const float4 *__restrict__ sg, const fl
     if (e.raw <= kAlphaMax) {  // the clamp passes no gradient
         const float dL_da = T * gdot - __fdividef(fin.x - Sv, 1.0f - e.alpha);
         const float dpw = dL_da * e.raw;  // dL/dpower (natural log units)
+        const float sx = dpw * e.dx, sy = dpw * e.dy;
         acc.pw += dpw;
-        acc.mx += dpw * (r0.z * e.dx + r0.w * e.dy);
-        acc.my += dpw * (r0.w * e.dx + r1.x * e.dy);
-        acc.xx += dpw * e.dx * e.dx;
-        acc.xy += dpw * e.dx * e.dy;
-        acc.yy += dpw * e.dy * e.dy;
+        acc.sx += sx;
+        acc.sy += sy;
+        acc.xx += sx * e.dx;
+        acc.xy += sx * e.dy;
+        acc.yy += sy * e.dy;
     }
     T = T * (1.0f - e.alpha);
 }
@@ -210,7 +214,9 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
                     //   d alpha / d o = alpha_raw / o, so dL/do = sum(dL/dpower) / o
                     const float inv_o = fast_exp2(-r1.y);
                     float4 *gp = grad2d + 3 * (size_t)item;
-                    atomicAdd(gp, make_float4(acc.mx * kInvH, acc.my * kInvH, -0.5f * acc.xx, -acc.xy));
+                    const float gmx = (r0.z * acc.sx + r0.w * acc.sy) * kInvH;
+                    const float gmy = (r0.w * acc.sx + r1.x * acc.sy) * kInvH;
+                    atomicAdd(gp, make_float4(gmx, gmy, -0.5f * acc.xx, -acc.xy));
                     atomicAdd(gp + 1, make_float4(-0.5f * acc.yy, acc.pw * inv_o, acc.iz, 0.0f));
                     atomicAdd(gp + 2, make_float4(acc.r, acc.g, acc.b, 0.0f));
                 }
