@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--views", type=int, default=16)
     ap.add_argument("--lam", type=float, default=0.2)
     ap.add_argument("--sq", action="store_true", help="sequential tile-key write instead of load-balanced")
+    ap.add_argument("--tuning", type=str, default="",
+                    help="fixed launch shapes instead of the autotuner, e.g. LB/b32/w2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched CUDA-graph measurement")
     ap.add_argument("--batched-steps", type=int, default=60)
@@ -250,7 +252,10 @@ def run_ours(args, rank, world):
     scene, cams = workload(args)
     params = api.Gaussians.from_scene(scene, device=dev)
     tuning, lb, table = {}, not args.sq, None
-    if not args.sq:  # launch shapes from the autotuner, on this workload's own views
+    if args.tuning:
+        mode, b, w = args.tuning.split("/")
+        lb, tuning = mode == "LB", {"bucket": int(b[1:]), "bwd_warps": int(w[1:])}
+    elif not args.sq:  # launch shapes from the autotuner, on this workload's own views
         from paper_2601_19489_gb300.autotune import autotune
 
         tgt = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1)).to(dev)

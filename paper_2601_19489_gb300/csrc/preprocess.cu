@@ -57,32 +57,47 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, float *Y) {
     }
 }
 
-// Gradient of the basis polynomials w.r.t. (x, y, z); the radial part is
-// removed afterwards by the normalisation's Jacobian.
+// sum_k w[k] * grad Y_k(x, y, z): the gradient of the basis polynomials
+// w.r.t. (x, y, z) contracted with w (the radial part is removed afterwards
+// by the normalisation's Jacobian).
 template <int D>
-__device__ __forceinline__ void sh_grad(float x, float y, float z, float3 *G) {
-    G[0] = make_float3(0.f, 0.f, 0.f);
+__device__ __forceinline__ float3 sh_grad_dot(float x, float y, float z, const float *w) {
+    float gx = 0.f, gy = 0.f, gz = 0.f;
     if (D >= 1) {
-        G[1] = make_float3(0.f, -kSH1, 0.f);
-        G[2] = make_float3(0.f, 0.f, kSH1);
-        G[3] = make_float3(-kSH1, 0.f, 0.f);
+        gy -= kSH1 * w[1];
+        gz += kSH1 * w[2];
+        gx -= kSH1 * w[3];
     }
     if (D >= 2) {
-        G[4] = make_float3(kSH2a * y, kSH2a * x, 0.f);
-        G[5] = make_float3(0.f, -kSH2a * z, -kSH2a * y);
-        G[6] = make_float3(0.f, 0.f, 6.0f * kSH2b * z);
-        G[7] = make_float3(-kSH2a * z, 0.f, -kSH2a * x);
-        G[8] = make_float3(2.0f * kSH2c * x, -2.0f * kSH2c * y, 0.f);
+        gx += kSH2a * y * w[4];
+        gy += kSH2a * x * w[4];
+        gy -= kSH2a * z * w[5];
+        gz -= kSH2a * y * w[5];
+        gz += 6.0f * kSH2b * z * w[6];
+        gx -= kSH2a * z * w[7];
+        gz -= kSH2a * x * w[7];
+        gx += 2.0f * kSH2c * x * w[8];
+        gy -= 2.0f * kSH2c * y * w[8];
     }
     if (D >= 3) {
-        G[9] = make_float3(-6.0f * kSH3a * x * y, -3.0f * kSH3a * (x * x - y * y), 0.f);
-        G[10] = make_float3(kSH3b * y * z, kSH3b * x * z, kSH3b * x * y);
-        G[11] = make_float3(0.f, -kSH3c * (5.0f * z * z - 1.0f), -10.0f * kSH3c * y * z);
-        G[12] = make_float3(0.f, 0.f, kSH3d * (15.0f * z * z - 3.0f));
-        G[13] = make_float3(-kSH3c * (5.0f * z * z - 1.0f), 0.f, -10.0f * kSH3c * x * z);
-        G[14] = make_float3(2.0f * kSH3e * x * z, -2.0f * kSH3e * y * z, kSH3e * (x * x - y * y));
-        G[15] = make_float3(-3.0f * kSH3a * (x * x - y * y), 6.0f * kSH3a * x * y, 0.f);
+        const float xx = x * x, yy = y * y, zz5 = 5.0f * z * z - 1.0f;
+        gx -= 6.0f * kSH3a * x * y * w[9];
+        gy -= 3.0f * kSH3a * (xx - yy) * w[9];
+        gx += kSH3b * y * z * w[10];
+        gy += kSH3b * x * z * w[10];
+        gz += kSH3b * x * y * w[10];
+        gy -= kSH3c * zz5 * w[11];
+        gz -= 10.0f * kSH3c * y * z * w[11];
+        gz += kSH3d * (15.0f * z * z - 3.0f) * w[12];
+        gx -= kSH3c * zz5 * w[13];
+        gz -= 10.0f * kSH3c * x * z * w[13];
+        gx += 2.0f * kSH3e * x * z * w[14];
+        gy -= 2.0f * kSH3e * y * z * w[14];
+        gz += kSH3e * (xx - yy) * w[14];
+        gx -= 3.0f * kSH3a * (xx - yy) * w[15];
+        gy += 6.0f * kSH3a * x * y * w[15];
     }
+    return make_float3(gx, gy, gz);
 }
 
 // Float-float ("double-float") helpers for the few per-Gaussian quantities
@@ -288,8 +303,15 @@ k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
 // a8: one thread per Gaussian, summing over the views where it touched tiles.
 // grad2d per (view, Gaussian): {d mx, d my, d a, d b}, {d c, d o, d(1/z), -},
 // {d r, d g, d b, -} with (a, b, c) the conic of q = a dx^2 + 2 b dx dy + c dy^2.
+// A warp owns 32 consecutive Gaussians: their SH rows (3K floats each) are
+// moved between global and shared memory with coalesced warp-wide accesses
+// (a row per lane would be 3K strided accesses per thread), and each lane
+// reads and accumulates its own row in shared memory (odd row stride: no
+// bank conflicts).
+constexpr int kPbWarps = 2;
+
 template <int D>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kPbWarps * 32, 8)  // <= 128 registers: 8 CTAs (16 warps) per SM
 k_preprocess_bwd(ViewsDev views, int64_t n, const float *__restrict__ means,
                  const float *__restrict__ log_scales, const float4 *__restrict__ quats,
                  const float *__restrict__ logits, const float *__restrict__ sh,
@@ -297,145 +319,173 @@ k_preprocess_bwd(ViewsDev views, int64_t n, const float *__restrict__ means,
                  float *__restrict__ g_means, float *__restrict__ g_log_scales,
                  float *__restrict__ g_quats, float *__restrict__ g_logits, float *__restrict__ g_sh) {
     constexpr int K = (D + 1) * (D + 1);
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
-    const float3 p = make_float3(means[3 * g], means[3 * g + 1], means[3 * g + 2]);
-    const float4 q = quats[g];
-    const float3 ls = make_float3(log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2]);
-    const float o = 1.0f / (1.0f + expf(-logits[g]));
-    float3 dp = make_float3(0.f, 0.f, 0.f);
-    float dRg[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float ds[3] = {0.f, 0.f, 0.f};
-    float dlogit = 0.f;
-    bool any = false;
-    Proj P;
-    for (int v = 0; v < views.V; ++v) {
-        const int64_t item = (int64_t)v * n + g;
-        if (touched[item] == 0) continue;
-        any = true;
-        const ViewDev &cam = views.v[v];
-        project_cov(cam, p, q, ls, P);
-        const float4 ga = grad2d[3 * item + 0];
-        const float4 gb = grad2d[3 * item + 1];
-        const float4 gc = grad2d[3 * item + 2];
-        // ---- opacity
-        dlogit += gb.y * o * (1.0f - o);
-        // ---- colour: SH coefficients and the viewing direction
-        {
-            float3 dv = sub3(p, make_float3(cam.campos[0], cam.campos[1], cam.campos[2]));
-            const float inv_len = rsqrtf(dot3(dv, dv));
-            const float3 dir = mul3(dv, inv_len);
-            float Y[K];
-            float3 G[K];
-            sh_eval<D>(dir.x, dir.y, dir.z, Y);
-            sh_grad<D>(dir.x, dir.y, dir.z, G);
-            const float *shg = sh + g * (K * 3);
-            float *gsh = g_sh + g * (K * 3);
-            float raw[3] = {0.5f, 0.5f, 0.5f};
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) raw[ch] += Y[k] * __ldg(shg + 3 * k + ch);
-            const float gr[3] = {raw[0] > 0.f ? gc.x : 0.f, raw[1] > 0.f ? gc.y : 0.f,
-                                 raw[2] > 0.f ? gc.z : 0.f};
-            float3 ddir = make_float3(0.f, 0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                float wk = 0.f;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    gsh[3 * k + ch] += gr[ch] * Y[k];
-                    wk += gr[ch] * __ldg(shg + 3 * k + ch);
-                }
-                ddir = add3(ddir, mul3(G[k], wk));
-            }
-            // d = dv / |dv|:  d(dv) = (ddir - d (d . ddir)) / |dv|
-            dp = add3(dp, mul3(sub3(ddir, mul3(dir, dot3(dir, ddir))), inv_len));
-        }
-        // ---- conic Q = Sigma'^-1 with Sigma' = U U^T + 0.3 I:
-        //   dL/dSigma' = -Q G Q  (G: gradient w.r.t. the symmetric conic matrix,
-        //   off-diagonal gb / 2), so dL/dU = 2 dL/dSigma' U = -2 Q G (Q U).
-        // Forming W = Q U first keeps a long axis's column small instead of
-        // cancelling large entries of dL/dSigma' against it (needle-like
-        // Gaussians would otherwise lose most float32 digits).
-        const float inv_det = 1.0f / P.det;
-        const float qa = P.Syy * inv_det, qb = -P.Sxy * inv_det, qc = P.Sxx * inv_det;
-        const float3 W0 = add3(mul3(P.U0, qa), mul3(P.U1, qb));
-        const float3 W1 = add3(mul3(P.U0, qb), mul3(P.U1, qc));
-        const float hb = 0.5f * ga.w;
-        const float3 GW0 = add3(mul3(W0, ga.z), mul3(W1, hb));
-        const float3 GW1 = add3(mul3(W0, hb), mul3(W1, gb.x));
-        const float3 dU0 = mul3(add3(mul3(GW0, qa), mul3(GW1, qb)), -2.f);
-        const float3 dU1 = mul3(add3(mul3(GW0, qb), mul3(GW1, qc)), -2.f);
-        // ---- U = T M, M = Rg diag(s):  dT_k = sum_j dU_j Rg[k][j] s_j;  dM[k][j] = T_k dU_j
-        const float du0[3] = {dU0.x, dU0.y, dU0.z}, du1[3] = {dU1.x, dU1.y, dU1.z};
-        const float t0[3] = {P.T0.x, P.T0.y, P.T0.z}, t1[3] = {P.T1.x, P.T1.y, P.T1.z};
-        float dT0[3], dT1[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const float m = P.Rg[3 * k + j] * P.s[j];
-                a0 += du0[j] * m;
-                a1 += du1[j] * m;
-                const float dM = t0[k] * du0[j] + t1[k] * du1[j];
-                dRg[3 * k + j] += dM * P.s[j];
-                ds[j] += dM * P.Rg[3 * k + j];
-            }
-            dT0[k] = a0;
-            dT1[k] = a1;
-        }
-        // ---- T0 = fx iz (W0 - xz W2), T1 = fy iz (W1 - yz W2)
-        const float3 vdT0 = make_float3(dT0[0], dT0[1], dT0[2]);
-        const float3 vdT1 = make_float3(dT1[0], dT1[1], dT1[2]);
-        float d_iz = cam.fx * dot3(vdT0, sub3(P.W0, mul3(P.W2, P.xz))) +
-                     cam.fy * dot3(vdT1, sub3(P.W1, mul3(P.W2, P.yz)));
-        const float d_xz = -cam.fx * P.iz * dot3(vdT0, P.W2);
-        const float d_yz = -cam.fy * P.iz * dot3(vdT1, P.W2);
-        float dx = 0.f, dy = 0.f;
-        if (!P.clx) {  // xz = x * iz
-            dx += d_xz * P.iz;
-            d_iz += d_xz * P.pc.x;
-        }
-        if (!P.cly) {
-            dy += d_yz * P.iz;
-            d_iz += d_yz * P.pc.y;
-        }
-        // ---- mean2d = (fx x iz + cx, fy y iz + cy), disparity 1/z
-        dx += ga.x * cam.fx * P.iz;
-        dy += ga.y * cam.fy * P.iz;
-        d_iz += ga.x * cam.fx * P.pc.x + ga.y * cam.fy * P.pc.y + gb.z;
-        const float dz = -d_iz * P.iz * P.iz;
-        // ---- pc = W p + t
-        dp = add3(dp, add3(add3(mul3(P.W0, dx), mul3(P.W1, dy)), mul3(P.W2, dz)));
+    constexpr int K3 = 3 * K;
+    constexpr int kRow = K3 + 1;
+    __shared__ float s_sh[kPbWarps][32 * kRow];
+    __shared__ float s_dsh[kPbWarps][32 * kRow];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t g0 = (int64_t)blockIdx.x * (kPbWarps * 32) + warp * 32;
+    const int64_t g = g0 + lane;
+    const bool valid = g < n;
+    const int rows = (int)(n - g0 < 32 ? (n - g0 > 0 ? n - g0 : 0) : 32);
+    uint32_t vmask = 0;  // views in which this Gaussian touched tiles
+    if (valid)
+        for (int v = 0; v < views.V; ++v)
+            if (touched[(int64_t)v * n + g] != 0) vmask |= 1u << v;
+    const uint32_t busy = __ballot_sync(0xffffffffu, vmask != 0);
+    if (busy == 0) return;  // uniform over the warp
+    float *row = &s_sh[warp][lane * kRow];
+    float *drow = &s_dsh[warp][lane * kRow];
+    for (int i = lane; i < rows * K3; i += 32) {
+        const int r = i / K3, c = i - r * K3;
+        s_sh[warp][r * kRow + c] = __ldg(sh + g0 * K3 + i);
     }
-    if (!any) return;
-    // ---- scales: s = exp(log_scale)
-    g_log_scales[3 * g + 0] += ds[0] * P.s[0];
-    g_log_scales[3 * g + 1] += ds[1] * P.s[1];
-    g_log_scales[3 * g + 2] += ds[2] * P.s[2];
-    // ---- rotation of the unit quaternion, then its normalisation
-    const float w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
-    const float *R = dRg;
-    float dqn[4];
-    dqn[0] = 2.f * (-z * R[1] + y * R[2] + z * R[3] - x * R[5] - y * R[6] + x * R[7]);
-    dqn[1] = 2.f * (y * R[1] + z * R[2] + y * R[3] - 2.f * x * R[4] - w * R[5] + z * R[6] + w * R[7] -
-                    2.f * x * R[8]);
-    dqn[2] = 2.f * (-2.f * y * R[0] + x * R[1] + w * R[2] + x * R[3] + z * R[5] - w * R[6] + z * R[7] -
-                    2.f * y * R[8]);
-    dqn[3] = 2.f * (-2.f * z * R[0] - w * R[1] + x * R[2] + w * R[3] - 2.f * z * R[4] + y * R[5] + x * R[6] +
-                    y * R[7]);
-    const float proj = dqn[0] * w + dqn[1] * x + dqn[2] * y + dqn[3] * z;
-    const float il = 1.0f / P.qlen;
-    g_quats[4 * g + 0] += (dqn[0] - w * proj) * il;
-    g_quats[4 * g + 1] += (dqn[1] - x * proj) * il;
-    g_quats[4 * g + 2] += (dqn[2] - y * proj) * il;
-    g_quats[4 * g + 3] += (dqn[3] - z * proj) * il;
-    g_means[3 * g + 0] += dp.x;
-    g_means[3 * g + 1] += dp.y;
-    g_means[3 * g + 2] += dp.z;
-    g_logits[g] += dlogit;
+#pragma unroll
+    for (int c = 0; c < K3; ++c) drow[c] = 0.0f;
+    __syncwarp();
+
+    if (vmask) {
+        const float3 p = make_float3(means[3 * g], means[3 * g + 1], means[3 * g + 2]);
+        const float4 q = quats[g];
+        const float3 ls = make_float3(log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2]);
+        const float o = 1.0f / (1.0f + expf(-logits[g]));
+        float3 dp = make_float3(0.f, 0.f, 0.f);
+        float dRg[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float ds[3] = {0.f, 0.f, 0.f};
+        float dlogit = 0.f;
+        Proj P;
+        for (int v = 0; v < views.V; ++v) {
+            if (!((vmask >> v) & 1u)) continue;
+            const int64_t item = (int64_t)v * n + g;
+            const ViewDev &cam = views.v[v];
+            project_cov(cam, p, q, ls, P);
+            const float4 ga = grad2d[3 * item + 0];
+            const float4 gb = grad2d[3 * item + 1];
+            const float4 gc = grad2d[3 * item + 2];
+            // ---- opacity
+            dlogit += gb.y * o * (1.0f - o);
+            // ---- colour: SH coefficients and the viewing direction
+            {
+                float3 dv = sub3(p, make_float3(cam.campos[0], cam.campos[1], cam.campos[2]));
+                const float inv_len = rsqrtf(dot3(dv, dv));
+                const float3 dir = mul3(dv, inv_len);
+                float Y[K];
+                sh_eval<D>(dir.x, dir.y, dir.z, Y);
+                float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) raw[ch] += Y[k] * row[3 * k + ch];
+                const float gr[3] = {raw[0] > 0.f ? gc.x : 0.f, raw[1] > 0.f ? gc.y : 0.f,
+                                     raw[2] > 0.f ? gc.z : 0.f};
+                float wk[K];  // dL/dY_k
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    wk[k] = 0.f;
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        drow[3 * k + ch] += gr[ch] * Y[k];
+                        wk[k] += gr[ch] * row[3 * k + ch];
+                    }
+                }
+                const float3 ddir = sh_grad_dot<D>(dir.x, dir.y, dir.z, wk);
+                // d = dv / |dv|:  d(dv) = (ddir - d (d . ddir)) / |dv|
+                dp = add3(dp, mul3(sub3(ddir, mul3(dir, dot3(dir, ddir))), inv_len));
+            }
+            // ---- conic Q = Sigma'^-1 with Sigma' = U U^T + 0.3 I:
+            //   dL/dSigma' = -Q G Q  (G: gradient w.r.t. the symmetric conic matrix,
+            //   off-diagonal gb / 2), so dL/dU = 2 dL/dSigma' U = -2 Q G (Q U).
+            // Forming W = Q U first keeps a long axis's column small instead of
+            // cancelling large entries of dL/dSigma' against it (needle-like
+            // Gaussians would otherwise lose most float32 digits).
+            const float inv_det = 1.0f / P.det;
+            const float qa = P.Syy * inv_det, qb = -P.Sxy * inv_det, qc = P.Sxx * inv_det;
+            const float3 W0 = add3(mul3(P.U0, qa), mul3(P.U1, qb));
+            const float3 W1 = add3(mul3(P.U0, qb), mul3(P.U1, qc));
+            const float hb = 0.5f * ga.w;
+            const float3 GW0 = add3(mul3(W0, ga.z), mul3(W1, hb));
+            const float3 GW1 = add3(mul3(W0, hb), mul3(W1, gb.x));
+            const float3 dU0 = mul3(add3(mul3(GW0, qa), mul3(GW1, qb)), -2.f);
+            const float3 dU1 = mul3(add3(mul3(GW0, qb), mul3(GW1, qc)), -2.f);
+            // ---- U = T M, M = Rg diag(s):  dT_k = sum_j dU_j Rg[k][j] s_j;  dM[k][j] = T_k dU_j
+            const float du0[3] = {dU0.x, dU0.y, dU0.z}, du1[3] = {dU1.x, dU1.y, dU1.z};
+            const float t0[3] = {P.T0.x, P.T0.y, P.T0.z}, t1[3] = {P.T1.x, P.T1.y, P.T1.z};
+            float dT0[3], dT1[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const float m = P.Rg[3 * k + j] * P.s[j];
+                    a0 += du0[j] * m;
+                    a1 += du1[j] * m;
+                    const float dM = t0[k] * du0[j] + t1[k] * du1[j];
+                    dRg[3 * k + j] += dM * P.s[j];
+                    ds[j] += dM * P.Rg[3 * k + j];
+                }
+                dT0[k] = a0;
+                dT1[k] = a1;
+            }
+            // ---- T0 = fx iz (W0 - xz W2), T1 = fy iz (W1 - yz W2)
+            const float3 vdT0 = make_float3(dT0[0], dT0[1], dT0[2]);
+            const float3 vdT1 = make_float3(dT1[0], dT1[1], dT1[2]);
+            float d_iz = cam.fx * dot3(vdT0, sub3(P.W0, mul3(P.W2, P.xz))) +
+                         cam.fy * dot3(vdT1, sub3(P.W1, mul3(P.W2, P.yz)));
+            const float d_xz = -cam.fx * P.iz * dot3(vdT0, P.W2);
+            const float d_yz = -cam.fy * P.iz * dot3(vdT1, P.W2);
+            float dx = 0.f, dy = 0.f;
+            if (!P.clx) {  // xz = x * iz
+                dx += d_xz * P.iz;
+                d_iz += d_xz * P.pc.x;
+            }
+            if (!P.cly) {
+                dy += d_yz * P.iz;
+                d_iz += d_yz * P.pc.y;
+            }
+            // ---- mean2d = (fx x iz + cx, fy y iz + cy), disparity 1/z
+            dx += ga.x * cam.fx * P.iz;
+            dy += ga.y * cam.fy * P.iz;
+            d_iz += ga.x * cam.fx * P.pc.x + ga.y * cam.fy * P.pc.y + gb.z;
+            const float dz = -d_iz * P.iz * P.iz;
+            // ---- pc = W p + t
+            dp = add3(dp, add3(add3(mul3(P.W0, dx), mul3(P.W1, dy)), mul3(P.W2, dz)));
+        }
+        // ---- scales: s = exp(log_scale)
+        g_log_scales[3 * g + 0] += ds[0] * P.s[0];
+        g_log_scales[3 * g + 1] += ds[1] * P.s[1];
+        g_log_scales[3 * g + 2] += ds[2] * P.s[2];
+        // ---- rotation of the unit quaternion, then its normalisation
+        const float w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
+        const float *R = dRg;
+        float dqn[4];
+        dqn[0] = 2.f * (-z * R[1] + y * R[2] + z * R[3] - x * R[5] - y * R[6] + x * R[7]);
+        dqn[1] = 2.f * (y * R[1] + z * R[2] + y * R[3] - 2.f * x * R[4] - w * R[5] + z * R[6] + w * R[7] -
+                        2.f * x * R[8]);
+        dqn[2] = 2.f * (-2.f * y * R[0] + x * R[1] + w * R[2] + x * R[3] + z * R[5] - w * R[6] + z * R[7] -
+                        2.f * y * R[8]);
+        dqn[3] = 2.f * (-2.f * z * R[0] - w * R[1] + x * R[2] + w * R[3] - 2.f * z * R[4] + y * R[5] +
+                        x * R[6] + y * R[7]);
+        const float proj = dqn[0] * w + dqn[1] * x + dqn[2] * y + dqn[3] * z;
+        const float il = 1.0f / P.qlen;
+        float4 *gq = reinterpret_cast<float4 *>(g_quats) + g;  // quaternion rows are 16-byte aligned
+        float4 dq = *gq;
+        dq.x += (dqn[0] - w * proj) * il;
+        dq.y += (dqn[1] - x * proj) * il;
+        dq.z += (dqn[2] - y * proj) * il;
+        dq.w += (dqn[3] - z * proj) * il;
+        *gq = dq;
+        g_means[3 * g + 0] += dp.x;
+        g_means[3 * g + 1] += dp.y;
+        g_means[3 * g + 2] += dp.z;
+        g_logits[g] += dlogit;
+    }
+    __syncwarp();
+    // the warp's SH gradient rows, accumulated with coalesced accesses (rows
+    // of Gaussians that touched no tile are left alone)
+    for (int i = lane; i < rows * K3; i += 32) {
+        const int r = i / K3, c = i - r * K3;
+        if ((busy >> r) & 1u) g_sh[g0 * K3 + i] += s_dsh[warp][r * kRow + c];
+    }
 }
 
 template <int D>
@@ -452,8 +502,8 @@ static void launch_preprocess(const gs_plan *plan, void *ws, const gs_params *pr
 template <int D>
 static void launch_preprocess_bwd(const gs_plan *plan, void *ws, const gs_params *pr, const ViewsDev &vd,
                                   gs_params *gr, cudaStream_t s) {
-    const unsigned blocks = (unsigned)((plan->n + 127) / 128);
-    k_preprocess_bwd<D><<<blocks, 128, 0, s>>>(
+    const unsigned blocks = (unsigned)((plan->n + kPbWarps * 32 - 1) / (kPbWarps * 32));
+    k_preprocess_bwd<D><<<blocks, kPbWarps * 32, 0, s>>>(
         vd, plan->n, pr->means, pr->log_scales, (const float4 *)pr->quats, pr->opacity_logits, pr->sh,
         ws_at<uint32_t>(ws, plan->o_touched), ws_at<float4>(ws, plan->o_grad2d), gr->means,
         gr->log_scales, gr->quats, gr->opacity_logits, gr->sh);
