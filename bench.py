@@ -232,9 +232,11 @@ def kernels_per_step(trainer) -> int:
     tile_passes = -(-trainer.plan_tile_bits // 8)
     loss_k = 3 if trainer.lam > 0 else 2
     # preprocess 1; depth sort 4 passes x 3; count 2; keys 1; tile sort 3/pass;
-    # ranges 1; buckets 1; forward 1; loss; blend bwd 1; preprocess bwd 1;
-    # adam 2 (step-count tick + update)
-    return 1 + 12 + 2 + 1 + 3 * tile_passes + 2 + 1 + loss_k + 1 + 1 + 2
+    # ranges 1; buckets 1; forward 1; loss; blend bwd 1; then either the
+    # fused preprocess backward + Adam (step-count tick + 1) or preprocess
+    # bwd 1 + adam 2 (tick + update)
+    tail = 2 if trainer.fused_adam else 3
+    return 1 + 12 + 2 + 1 + 3 * tile_passes + 2 + 1 + loss_k + 1 + tail
 
 
 def run_ours(args, rank, world):
@@ -286,7 +288,7 @@ def run_ours(args, rank, world):
     st0 = trainer.plan.status()
     assert st0["rc"] == 0, st0
 
-    n_st = len(Trainer.STAGES)
+    n_st = len(trainer.STAGES)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_st + 1)] for _ in range(args.steps)]
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
@@ -308,7 +310,7 @@ def run_ours(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         elapsed = float(t.item())
     stage_ms = {name: float(np.mean([evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps)]))
-                for i, name in enumerate(Trainer.STAGES)}
+                for i, name in enumerate(trainer.STAGES)}
 
     # algorithmic work of the blend kernels: evaluated pairs up to each
     # pixel's last contributor, summed over the views of the timed steps
@@ -492,7 +494,7 @@ def run_ng(args, dev, n_anchors: int, steps: int, warmup: int = 5) -> dict:
     tr.ensure_capacity(cams)
     for s in range(warmup):
         tr.step(cams[s % len(cams)], targets[s % len(cams)])
-    n_st = len(NgTrainer.STAGES)
+    n_st = len(tr.STAGES)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_st + 1)] for _ in range(steps)]
     torch.cuda.synchronize()
     for s in range(steps):
@@ -503,7 +505,7 @@ def run_ng(args, dev, n_anchors: int, steps: int, warmup: int = 5) -> dict:
         raise RuntimeError("device status after the neural-Gaussian steps")
     total = sum(evs[s][0].elapsed_time(evs[s][n_st]) for s in range(steps)) / steps
     stage_ms = {name: float(np.mean([evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(steps)]))
-                for i, name in enumerate(NgTrainer.STAGES)}
+                for i, name in enumerate(tr.STAGES)}
     return {"anchors": n_anchors, "children": 10 * n_anchors, "steps_per_s": 1e3 / total, "ms_per_step": total,
             "stages_ms": stage_ms, "loss_last": tr.loss.item(),
             "decoder": "x = [feature 32, view dir 3] -> 32 ReLU -> 140 = 10 children x 14; bf16 tcgen05 MMAs"}

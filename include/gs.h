@@ -214,6 +214,29 @@ GS_API int gs_render_bwd_blend(const gs_plan *plan, void *ws, const float *d_rgb
 GS_API int gs_preprocess_bwd(const gs_plan *plan, void *ws, const gs_params *params,
                              const gs_camera *h_cams, gs_params *grads, void *stream);
 
+/* a8 + a9 fused, for a step whose gradient is complete after the blend
+ * backward (every view of the step is in this plan): the preprocess backward
+ * of every Gaussian, summed over the plan's views, followed at once by the
+ * Adam update of gs_adam_step_multi_dev on that Gaussian's parameters, in
+ * place.  The gradient is never stored, which saves writing it here and
+ * reading it back in Adam.  Gaussians that touched no tile are updated with
+ * a zero gradient, as an unfused step would.
+ * params: parameters (device, read and written).  adam_m, adam_v: first and
+ * second moments with the layout of params (device, read and written).
+ * d_step: device int32 step count, incremented on the stream first; the
+ * incremented value is the t of the bias corrections.  Rates per parameter
+ * group; the SH DC coefficients (the first 3 floats of a Gaussian's SH row)
+ * take lr_sh_dc, the rest lr_sh_rest.  b1, b2 in [0.5, 1).  Every array of
+ * params, adam_m and adam_v must start 16-byte aligned (GS_ERR_ARG
+ * otherwise). */
+typedef struct {
+    float lr_means, lr_log_scales, lr_quats, lr_opacity, lr_sh_dc, lr_sh_rest;
+    float b1, b2, eps;
+} gs_adam_hparams;
+GS_API int gs_preprocess_bwd_adam(const gs_plan *plan, void *ws, gs_params *params, const gs_camera *h_cams,
+                                  const gs_params *adam_m, const gs_params *adam_v, const gs_adam_hparams *hp,
+                                  int32_t *d_step, void *stream);
+
 /* ------------------------------------------------------------ a6: loss
  * Eq. 5: loss = (1 - lambda) L1 + lambda (1 - SSIM) over all views' colour
  * pixels, SSIM with an 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2,

@@ -19,6 +19,7 @@ from .api import (  # noqa: F401
     gs_loss,
     gs_loss_scratch,
     gs_preprocess,
+    gs_preprocess_bwd_adam,
     gs_render_bwd,
     gs_render_fwd,
     gs_sort_pairs_u32,

@@ -31,7 +31,7 @@ EXPORTS = (
     "gs_workspace_view", "gs_read_status", "gs_error_string", "gs_preprocess", "gs_bin_sort",
     "gs_render_fwd", "gs_render_bwd", "gs_render_bwd_blend", "gs_preprocess_bwd",
     "gs_loss_scratch_floats", "gs_loss", "gs_adam_step",
-    "gs_adam_step_multi", "gs_adam_step_multi_dev", "gs_sort_scratch_bytes", "gs_sort_pairs_u32", "gs_sort_pairs_u32_noalloc",
+    "gs_adam_step_multi", "gs_adam_step_multi_dev", "gs_preprocess_bwd_adam", "gs_sort_scratch_bytes", "gs_sort_pairs_u32", "gs_sort_pairs_u32_noalloc",
     "gs_ng_workspace_bytes", "gs_ng_decode_fwd", "gs_ng_decode_bwd", "gs_ng_read_status",
 )
 
@@ -51,6 +51,12 @@ class GsParams(ctypes.Structure):
 
 class GsTuning(ctypes.Structure):
     _fields_ = [("bucket", ctypes.c_int32), ("bwd_warps", ctypes.c_int32)]
+
+
+class GsAdamHparams(ctypes.Structure):
+    _fields_ = [("lr_means", ctypes.c_float), ("lr_log_scales", ctypes.c_float), ("lr_quats", ctypes.c_float),
+                ("lr_opacity", ctypes.c_float), ("lr_sh_dc", ctypes.c_float), ("lr_sh_rest", ctypes.c_float),
+                ("b1", ctypes.c_float), ("b2", ctypes.c_float), ("eps", ctypes.c_float)]
 
 
 class GsStatus(ctypes.Structure):
@@ -108,6 +114,8 @@ _SIGS = {
                                           ctypes.c_float, ctypes.c_float, ctypes.c_int32, P]),
     "gs_adam_step_multi_dev": (ctypes.c_int, [ctypes.POINTER(GsAdamGroup), ctypes.c_int32, ctypes.c_float,
                                               ctypes.c_float, ctypes.c_float, P, P]),
+    "gs_preprocess_bwd_adam": (ctypes.c_int, [P, P, ctypes.POINTER(GsParams), P, ctypes.POINTER(GsParams),
+                                              ctypes.POINTER(GsParams), ctypes.POINTER(GsAdamHparams), P, P]),
     "gs_sort_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "gs_sort_pairs_u32": (ctypes.c_int, [P, P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          P, P]),

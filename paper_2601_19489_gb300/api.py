@@ -218,6 +218,27 @@ def gs_adam_step_multi_dev(groups, d_step: torch.Tensor, b1=0.9, b2=0.999, eps=1
                                            _stream(stream)), "gs_adam_step_multi_dev")
 
 
+def adam_hparams(lrs: dict, b1=0.9, b2=0.999, eps=1e-15) -> L.GsAdamHparams:
+    """lrs with keys means, log_scales, quats, opacity_logits, sh_dc, sh_rest."""
+    return L.GsAdamHparams(float(lrs["means"]), float(lrs["log_scales"]), float(lrs["quats"]),
+                           float(lrs["opacity_logits"]), float(lrs["sh_dc"]), float(lrs["sh_rest"]), float(b1),
+                           float(b2), float(eps))
+
+
+def gs_preprocess_bwd_adam(plan: Plan, params: Gaussians, cams, m: Gaussians, v: Gaussians, lrs: dict,
+                           d_step: torch.Tensor, b1=0.9, b2=0.999, eps=1e-15, stream=None) -> None:
+    """Preprocess backward fused with the Adam update (parameters, m and v
+    updated in place; d_step incremented)."""
+    if d_step.dtype != torch.int32 or not d_step.is_cuda:
+        raise TypeError("d_step must be a CUDA int32 tensor")
+    ca = cameras_array(cams)
+    p, ms, vs = params.struct(), m.struct(), v.struct()
+    hp = adam_hparams(lrs, b1, b2, eps)
+    L.check(L.lib().gs_preprocess_bwd_adam(plan.handle, plan.ws.data_ptr(), ctypes.byref(p), ca, ctypes.byref(ms),
+                                           ctypes.byref(vs), ctypes.byref(hp), _ptr(d_step, None),
+                                           _stream(stream)), "gs_preprocess_bwd_adam")
+
+
 def gs_sort_pairs_u32(keys_in, vals_in, keys_out, vals_out, begin_bit: int, end_bit: int, scratch=None,
                       stream=None) -> None:
     n = keys_in.numel()

@@ -94,6 +94,11 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam(AdamGroups G) {
     }
 }
 
+int adam_tick(int32_t *d_step, cudaStream_t s) {
+    k_adam_tick<<<1, 1, 0, s>>>(d_step);
+    return launch_error();
+}
+
 static int adam_launch(const gs_adam_group *groups, int n_groups, float b1, float b2, float eps,
                        int step, int32_t *d_step, cudaStream_t s) {
     if (!groups || n_groups < 1 || n_groups > kMaxGroups || (!d_step && step < 1) ||
@@ -130,8 +135,7 @@ static int adam_launch(const gs_adam_group *groups, int n_groups, float b1, floa
         G.slot_off[i + 1] = G.slot_off[i] + (gr.n + 3) / 4;
     }
     if (d_step) {
-        k_adam_tick<<<1, 1, 0, s>>>(d_step);
-        const int rc = launch_error();
+        const int rc = adam_tick(d_step, s);
         if (rc) return rc;
     }
     const int64_t total = G.slot_off[n_groups];

@@ -100,6 +100,9 @@ ViewsDev make_views(const gs_plan *plan, const gs_camera *cams);
 int check_cuda(cudaError_t e);
 int launch_error();
 
+// One-thread launch that increments the device step count of Adam (adam.cu).
+int adam_tick(int32_t *d_step, cudaStream_t s);
+
 // Radix sort internals (radix_sort.cu), usable with a device-resident count.
 size_t sort_scratch_bytes();
 int sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b,

@@ -15,6 +15,8 @@
 // 1/z, mx_lo), r2 = (r, g, b, my_lo) with (A, B, C) = kH * conic and the
 // projected mean as the float-float (mx + mx_lo, my + my_lo); binning also
 // reads (tb, detc) with tb = kH * t_bin and detc = A C - B^2 = kH^2 / det(Sigma').
+#include <string.h>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -308,16 +310,44 @@ k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
 // (a row per lane would be 3K strided accesses per thread), and each lane
 // reads and accumulates its own row in shared memory (odd row stride: no
 // bank conflicts).
+// With kAdam the gradient is not stored: the thread that completes it (all
+// views of the plan are summed inside the kernel) applies the Adam update to
+// the parameter in place, so the gradient never travels through memory.
+// Every Gaussian is updated, a Gaussian that touched no tile with a zero
+// gradient (its moments still decay and it keeps moving).
 constexpr int kPbWarps = 2;
+constexpr int kSmallRow = 11;  // a lane's gradients: mean 3, log-scale 3, quaternion 4, logit 1
 
-template <int D>
+struct PbArgs {
+    int64_t n;
+    float *means, *log_scales, *quats, *logits, *sh;  // parameters (written only with Adam)
+    const uint32_t *touched;
+    const float4 *grad2d;
+    float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;  // gradient accumulators
+    float *m[5], *v[5];          // Adam moments: means, log_scales, quats, logits, sh
+    float lr[6];                 // means, log_scales, quats, opacity, SH DC, SH rest
+    float b1, b2, eps;
+    const int32_t *d_step;       // step count, already incremented for this update
+};
+
+__device__ __forceinline__ void adam_el(float &p, float g, float &m, float &v, float b1, float b2, float eps,
+                                        float step, float ibc2) {
+    m = b1 * m + (1.0f - b1) * g;
+    v = b2 * v + (1.0f - b2) * g * g;
+    p -= step * m / (sqrtf(v) * ibc2 + eps);
+}
+
+template <int D, bool kAdam>
 __global__ void __launch_bounds__(kPbWarps * 32, 8)  // <= 128 registers: 8 CTAs (16 warps) per SM
-k_preprocess_bwd(ViewsDev views, int64_t n, const float *__restrict__ means,
-                 const float *__restrict__ log_scales, const float4 *__restrict__ quats,
-                 const float *__restrict__ logits, const float *__restrict__ sh,
-                 const uint32_t *__restrict__ touched, const float4 *__restrict__ grad2d,
-                 float *__restrict__ g_means, float *__restrict__ g_log_scales,
-                 float *__restrict__ g_quats, float *__restrict__ g_logits, float *__restrict__ g_sh) {
+k_preprocess_bwd(ViewsDev views, PbArgs A) {
+    const int64_t n = A.n;
+    const float *__restrict__ means = A.means;
+    const float *__restrict__ log_scales = A.log_scales;
+    const float4 *__restrict__ quats = reinterpret_cast<const float4 *>(A.quats);
+    const float *__restrict__ logits = A.logits;
+    const float *__restrict__ sh = A.sh;
+    const uint32_t *__restrict__ touched = A.touched;
+    const float4 *__restrict__ grad2d = A.grad2d;
     constexpr int K = (D + 1) * (D + 1);
     constexpr int K3 = 3 * K;
     constexpr int kRow = K3 + 1;
@@ -333,7 +363,7 @@ k_preprocess_bwd(ViewsDev views, int64_t n, const float *__restrict__ means,
         for (int v = 0; v < views.V; ++v)
             if (touched[(int64_t)v * n + g] != 0) vmask |= 1u << v;
     const uint32_t busy = __ballot_sync(0xffffffffu, vmask != 0);
-    if (busy == 0) return;  // uniform over the warp
+    if (!kAdam && busy == 0) return;  // uniform over the warp
     float *row = &s_sh[warp][lane * kRow];
     float *drow = &s_dsh[warp][lane * kRow];
     for (int i = lane; i < rows * K3; i += 32) {
@@ -344,15 +374,16 @@ k_preprocess_bwd(ViewsDev views, int64_t n, const float *__restrict__ means,
     for (int c = 0; c < K3; ++c) drow[c] = 0.0f;
     __syncwarp();
 
+    float3 dp = make_float3(0.f, 0.f, 0.f);
+    float g_ls[3] = {0.f, 0.f, 0.f}, g_q[4] = {0.f, 0.f, 0.f, 0.f};
+    float dlogit = 0.f;
     if (vmask) {
         const float3 p = make_float3(means[3 * g], means[3 * g + 1], means[3 * g + 2]);
         const float4 q = quats[g];
         const float3 ls = make_float3(log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2]);
         const float o = 1.0f / (1.0f + expf(-logits[g]));
-        float3 dp = make_float3(0.f, 0.f, 0.f);
         float dRg[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float ds[3] = {0.f, 0.f, 0.f};
-        float dlogit = 0.f;
         Proj P;
         for (int v = 0; v < views.V; ++v) {
             if (!((vmask >> v) & 1u)) continue;
@@ -451,9 +482,9 @@ k_preprocess_bwd(ViewsDev views, int64_t n, const float *__restrict__ means,
             dp = add3(dp, add3(add3(mul3(P.W0, dx), mul3(P.W1, dy)), mul3(P.W2, dz)));
         }
         // ---- scales: s = exp(log_scale)
-        g_log_scales[3 * g + 0] += ds[0] * P.s[0];
-        g_log_scales[3 * g + 1] += ds[1] * P.s[1];
-        g_log_scales[3 * g + 2] += ds[2] * P.s[2];
+        g_ls[0] = ds[0] * P.s[0];
+        g_ls[1] = ds[1] * P.s[1];
+        g_ls[2] = ds[2] * P.s[2];
         // ---- rotation of the unit quaternion, then its normalisation
         const float w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
         const float *R = dRg;
@@ -467,24 +498,146 @@ k_preprocess_bwd(ViewsDev views, int64_t n, const float *__restrict__ means,
                         x * R[6] + y * R[7]);
         const float proj = dqn[0] * w + dqn[1] * x + dqn[2] * y + dqn[3] * z;
         const float il = 1.0f / P.qlen;
-        float4 *gq = reinterpret_cast<float4 *>(g_quats) + g;  // quaternion rows are 16-byte aligned
-        float4 dq = *gq;
-        dq.x += (dqn[0] - w * proj) * il;
-        dq.y += (dqn[1] - x * proj) * il;
-        dq.z += (dqn[2] - y * proj) * il;
-        dq.w += (dqn[3] - z * proj) * il;
-        *gq = dq;
-        g_means[3 * g + 0] += dp.x;
-        g_means[3 * g + 1] += dp.y;
-        g_means[3 * g + 2] += dp.z;
-        g_logits[g] += dlogit;
+        g_q[0] = (dqn[0] - w * proj) * il;
+        g_q[1] = (dqn[1] - x * proj) * il;
+        g_q[2] = (dqn[2] - y * proj) * il;
+        g_q[3] = (dqn[3] - z * proj) * il;
+    }
+    if (!kAdam) {
+        if (vmask) {
+            A.g_log_scales[3 * g + 0] += g_ls[0];
+            A.g_log_scales[3 * g + 1] += g_ls[1];
+            A.g_log_scales[3 * g + 2] += g_ls[2];
+            float4 *gq = reinterpret_cast<float4 *>(A.g_quats) + g;  // quaternion rows are 16-byte aligned
+            float4 dq = *gq;
+            dq.x += g_q[0];
+            dq.y += g_q[1];
+            dq.z += g_q[2];
+            dq.w += g_q[3];
+            *gq = dq;
+            A.g_means[3 * g + 0] += dp.x;
+            A.g_means[3 * g + 1] += dp.y;
+            A.g_means[3 * g + 2] += dp.z;
+            A.g_logits[g] += dlogit;
+        }
+        __syncwarp();
+        // the warp's SH gradient rows, accumulated with coalesced accesses
+        // (rows of Gaussians that touched no tile are left alone)
+        for (int i = lane; i < rows * K3; i += 32) {
+            const int r = i / K3, c = i - r * K3;
+            if ((busy >> r) & 1u) A.g_sh[g0 * K3 + i] += s_dsh[warp][r * kRow + c];
+        }
+        return;
+    }
+    // ---- Adam (bias corrections from the device step count, as in k_adam).
+    // Each lane parks its small-attribute gradients in shared memory; then the
+    // warp updates every attribute array of its 32 Gaussians with coalesced
+    // accesses (consecutive lanes, consecutive floats).
+    const float tstep = (float)*A.d_step;
+    const float ibc1 = -1.0f / expm1f(tstep * log1pf(A.b1 - 1.0f));
+    const float ibc2 = 1.0f / sqrtf(-expm1f(tstep * log1pf(A.b2 - 1.0f)));
+    __shared__ float s_g[kPbWarps][32 * kSmallRow];
+    {
+        float *gr = &s_g[warp][lane * kSmallRow];
+        gr[0] = dp.x;
+        gr[1] = dp.y;
+        gr[2] = dp.z;
+        gr[3] = g_ls[0];
+        gr[4] = g_ls[1];
+        gr[5] = g_ls[2];
+        gr[6] = g_q[0];
+        gr[7] = g_q[1];
+        gr[8] = g_q[2];
+        gr[9] = g_q[3];
+        gr[10] = dlogit;
     }
     __syncwarp();
-    // the warp's SH gradient rows, accumulated with coalesced accesses (rows
-    // of Gaussians that touched no tile are left alone)
-    for (int i = lane; i < rows * K3; i += 32) {
+    // The moments stream with float4 accesses, several per lane in flight
+    // (a warp's block of an attribute array starts 16-byte aligned: 32
+    // Gaussians of 4 or 12 bytes, or SH rows).
+    // (attribute array, floats per Gaussian, offset of its gradient in a lane's row)
+    float *const pa[4] = {A.means, A.log_scales, A.quats, A.logits};
+    const int width[4] = {3, 3, 4, 1}, goff[4] = {0, 3, 6, 10};
+    float4 sp[4], sm[4], sv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int nq = (rows * width[a]) >> 2;
+        if (lane < nq) {
+            sp[a] = reinterpret_cast<const float4 *>(pa[a] + g0 * width[a])[lane];
+            sm[a] = reinterpret_cast<const float4 *>(A.m[a] + g0 * width[a])[lane];
+            sv[a] = reinterpret_cast<const float4 *>(A.v[a] + g0 * width[a])[lane];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int w = width[a];
+        const int nq = (rows * w) >> 2;
+        const float st = A.lr[a] * ibc1;
+        if (lane < nq) {
+            float pv[4] = {sp[a].x, sp[a].y, sp[a].z, sp[a].w}, mv[4] = {sm[a].x, sm[a].y, sm[a].z, sm[a].w},
+                  vv[4] = {sv[a].x, sv[a].y, sv[a].z, sv[a].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = 4 * lane + e, r = i / w, c = i - r * w;
+                adam_el(pv[e], s_g[warp][r * kSmallRow + goff[a] + c], mv[e], vv[e], A.b1, A.b2, A.eps, st, ibc2);
+            }
+            reinterpret_cast<float4 *>(pa[a] + g0 * w)[lane] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+            reinterpret_cast<float4 *>(A.m[a] + g0 * w)[lane] = make_float4(mv[0], mv[1], mv[2], mv[3]);
+            reinterpret_cast<float4 *>(A.v[a] + g0 * w)[lane] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+        }
+        for (int i = 4 * nq + lane; i < rows * w; i += 32) {  // ragged end of the last warp
+            const int r = i / w, c = i - r * w;
+            float *pp = pa[a] + g0 * w, *mm = A.m[a] + g0 * w, *vvp = A.v[a] + g0 * w;
+            float pv = pp[i], mv = mm[i], v2 = vvp[i];
+            adam_el(pv, s_g[warp][r * kSmallRow + goff[a] + c], mv, v2, A.b1, A.b2, A.eps, st, ibc2);
+            pp[i] = pv;
+            mm[i] = mv;
+            vvp[i] = v2;
+        }
+    }
+    // SH rows: parameters from shared memory, gradients from the shared
+    // accumulators, moments in float4, three quads per lane in flight
+    const float s_dc = A.lr[4] * ibc1, s_rest = A.lr[5] * ibc1;
+    const int F = rows * K3, FQ = F >> 2;
+    float4 *p4 = reinterpret_cast<float4 *>(A.sh + g0 * K3);
+    float4 *m4 = reinterpret_cast<float4 *>(A.m[4] + g0 * K3);
+    float4 *v4 = reinterpret_cast<float4 *>(A.v[4] + g0 * K3);
+    constexpr int kU = 3;
+    for (int j0 = lane; j0 < FQ; j0 += 32 * kU) {
+        float4 mq[kU], vq[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int j = j0 + 32 * u;
+            if (j < FQ) {
+                mq[u] = m4[j];
+                vq[u] = v4[j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int j = j0 + 32 * u;
+            if (j >= FQ) break;
+            float pv[4], mv[4] = {mq[u].x, mq[u].y, mq[u].z, mq[u].w}, vv[4] = {vq[u].x, vq[u].y, vq[u].z, vq[u].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = 4 * j + e, r = i / K3, c = i - r * K3;
+                pv[e] = s_sh[warp][r * kRow + c];
+                adam_el(pv[e], s_dsh[warp][r * kRow + c], mv[e], vv[e], A.b1, A.b2, A.eps, c < 3 ? s_dc : s_rest,
+                        ibc2);
+            }
+            p4[j] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+            m4[j] = make_float4(mv[0], mv[1], mv[2], mv[3]);
+            v4[j] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+        }
+    }
+    for (int i = 4 * FQ + lane; i < F; i += 32) {  // ragged end of the last warp
         const int r = i / K3, c = i - r * K3;
-        if ((busy >> r) & 1u) g_sh[g0 * K3 + i] += s_dsh[warp][r * kRow + c];
+        float pv = s_sh[warp][r * kRow + c];
+        float mv = A.m[4][g0 * K3 + i], vv = A.v[4][g0 * K3 + i];
+        adam_el(pv, s_dsh[warp][r * kRow + c], mv, vv, A.b1, A.b2, A.eps, c < 3 ? s_dc : s_rest, ibc2);
+        A.sh[g0 * K3 + i] = pv;
+        A.m[4][g0 * K3 + i] = mv;
+        A.v[4][g0 * K3 + i] = vv;
     }
 }
 
@@ -499,14 +652,34 @@ static void launch_preprocess(const gs_plan *plan, void *ws, const gs_params *pr
         ws_at<uint2>(ws, plan->o_rect), ws_at<uint32_t>(ws, plan->o_dkey[0]), ws_at<uint32_t>(ws, plan->o_dval[0]));
 }
 
-template <int D>
-static void launch_preprocess_bwd(const gs_plan *plan, void *ws, const gs_params *pr, const ViewsDev &vd,
-                                  gs_params *gr, cudaStream_t s) {
-    const unsigned blocks = (unsigned)((plan->n + kPbWarps * 32 - 1) / (kPbWarps * 32));
-    k_preprocess_bwd<D><<<blocks, kPbWarps * 32, 0, s>>>(
-        vd, plan->n, pr->means, pr->log_scales, (const float4 *)pr->quats, pr->opacity_logits, pr->sh,
-        ws_at<uint32_t>(ws, plan->o_touched), ws_at<float4>(ws, plan->o_grad2d), gr->means,
-        gr->log_scales, gr->quats, gr->opacity_logits, gr->sh);
+template <int D, bool kAdam>
+static void launch_preprocess_bwd(const ViewsDev &vd, const PbArgs &A, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((A.n + kPbWarps * 32 - 1) / (kPbWarps * 32));
+    k_preprocess_bwd<D, kAdam><<<blocks, kPbWarps * 32, 0, s>>>(vd, A);
+}
+
+static PbArgs pb_args(const gs_plan *plan, void *ws, const gs_params *pr) {
+    PbArgs A;
+    memset(&A, 0, sizeof(A));
+    A.n = plan->n;
+    A.means = pr->means;
+    A.log_scales = pr->log_scales;
+    A.quats = pr->quats;
+    A.logits = pr->opacity_logits;
+    A.sh = pr->sh;
+    A.touched = ws_at<uint32_t>(ws, plan->o_touched);
+    A.grad2d = ws_at<float4>(ws, plan->o_grad2d);
+    return A;
+}
+
+template <bool kAdam>
+static void dispatch_preprocess_bwd(int sh_degree, const ViewsDev &vd, const PbArgs &A, cudaStream_t s) {
+    switch (sh_degree) {
+        case 0: launch_preprocess_bwd<0, kAdam>(vd, A, s); break;
+        case 1: launch_preprocess_bwd<1, kAdam>(vd, A, s); break;
+        case 2: launch_preprocess_bwd<2, kAdam>(vd, A, s); break;
+        default: launch_preprocess_bwd<3, kAdam>(vd, A, s); break;
+    }
 }
 
 int check_params(const gs_plan *plan, const gs_params *p) {
@@ -529,12 +702,40 @@ int check_cams(const gs_plan *plan, const gs_camera *cams) {
 int preprocess_bwd(const gs_plan *plan, void *ws, const gs_params *params, const gs_camera *cams,
                    gs_params *grads, cudaStream_t s) {
     const ViewsDev vd = make_views(plan, cams);
-    switch (plan->sh_degree) {
-        case 0: launch_preprocess_bwd<0>(plan, ws, params, vd, grads, s); break;
-        case 1: launch_preprocess_bwd<1>(plan, ws, params, vd, grads, s); break;
-        case 2: launch_preprocess_bwd<2>(plan, ws, params, vd, grads, s); break;
-        default: launch_preprocess_bwd<3>(plan, ws, params, vd, grads, s); break;
+    PbArgs A = pb_args(plan, ws, params);
+    A.g_means = grads->means;
+    A.g_log_scales = grads->log_scales;
+    A.g_quats = grads->quats;
+    A.g_logits = grads->opacity_logits;
+    A.g_sh = grads->sh;
+    dispatch_preprocess_bwd<false>(plan->sh_degree, vd, A, s);
+    return launch_error();
+}
+
+int preprocess_bwd_adam(const gs_plan *plan, void *ws, gs_params *params, const gs_camera *cams,
+                        const gs_params *m, const gs_params *v, const gs_adam_hparams *hp, int32_t *d_step,
+                        cudaStream_t s) {
+    const ViewsDev vd = make_views(plan, cams);
+    PbArgs A = pb_args(plan, ws, params);
+    const gs_params *mv[2] = {m, v};
+    for (int k = 0; k < 2; ++k) {
+        float **dst = k == 0 ? A.m : A.v;
+        dst[0] = mv[k]->means;
+        dst[1] = mv[k]->log_scales;
+        dst[2] = mv[k]->quats;
+        dst[3] = mv[k]->opacity_logits;
+        dst[4] = mv[k]->sh;
     }
+    const float lr[6] = {hp->lr_means, hp->lr_log_scales, hp->lr_quats, hp->lr_opacity, hp->lr_sh_dc,
+                         hp->lr_sh_rest};
+    for (int k = 0; k < 6; ++k) A.lr[k] = lr[k];
+    A.b1 = hp->b1;
+    A.b2 = hp->b2;
+    A.eps = hp->eps;
+    A.d_step = d_step;
+    int rc = adam_tick(d_step, s);
+    if (rc) return rc;
+    dispatch_preprocess_bwd<true>(plan->sh_degree, vd, A, s);
     return launch_error();
 }
 
@@ -558,4 +759,24 @@ extern "C" int gs_preprocess(const gs_plan *plan, void *ws, const gs_params *par
         default: launch_preprocess<3>(plan, ws, params, vd, s); break;
     }
     return launch_error();
+}
+
+extern "C" int gs_preprocess_bwd_adam(const gs_plan *plan, void *ws, gs_params *params, const gs_camera *cams,
+                                      const gs_params *adam_m, const gs_params *adam_v,
+                                      const gs_adam_hparams *hp, int32_t *d_step, void *stream) {
+    if (!plan || !ws || !hp || !d_step) return GS_ERR_ARG;
+    int rc = check_params(plan, params);
+    if (!rc) rc = check_params(plan, adam_m);
+    if (!rc) rc = check_params(plan, adam_v);
+    if (!rc) rc = check_cams(plan, cams);
+    if (rc) return rc;
+    if (!(hp->b1 >= 0.5f && hp->b1 < 1.0f) || !(hp->b2 >= 0.5f && hp->b2 < 1.0f) || !(hp->eps >= 0.0f))
+        return GS_ERR_ARG;
+    // every attribute array is streamed with float4 accesses
+    const gs_params *all[3] = {params, adam_m, adam_v};
+    for (const gs_params *q : all)
+        if ((((uintptr_t)q->means) | ((uintptr_t)q->log_scales) | ((uintptr_t)q->quats) |
+             ((uintptr_t)q->opacity_logits) | ((uintptr_t)q->sh)) & 15)
+            return GS_ERR_ARG;
+    return preprocess_bwd_adam(plan, ws, params, cams, adam_m, adam_v, hp, d_step, (cudaStream_t)stream);
 }

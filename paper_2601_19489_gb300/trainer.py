@@ -19,7 +19,7 @@ import ctypes
 import torch
 
 from . import _lib as L
-from .api import (Gaussians, NgParams, Plan, adam_groups_array, camera_struct, gs_ng_workspace,
+from .api import (Gaussians, NgParams, Plan, adam_groups_array, adam_hparams, camera_struct, gs_ng_workspace,
                   ng_children)
 
 
@@ -53,15 +53,22 @@ class Trainer:
     ``ensure_capacity``, which should see every batch before timing or
     capture)."""
 
-    STAGES = ("preprocess", "bin_sort", "render_fwd", "loss", "render_bwd_blend", "preprocess_bwd", "adam")
+    STAGES_UNFUSED = ("preprocess", "bin_sort", "render_fwd", "loss", "render_bwd_blend", "preprocess_bwd",
+                      "adam")
+    STAGES_FUSED = ("preprocess", "bin_sort", "render_fwd", "loss", "render_bwd_blend", "preprocess_bwd_adam")
 
     def __init__(self, params: Gaussians, width: int | None = None, height: int | None = None, *,
                  lam: float = 0.2, bg=(0.0, 0.0, 0.0), lrs: dict | None = None,
                  inst_capacity: int | None = None, load_balanced: bool = True, disp_weight: float = 0.0,
-                 tuning: dict | None = None, device="cuda"):
+                 tuning: dict | None = None, fused_adam: bool = True, device="cuda"):
         """tuning: launch shapes of the plans ({"bucket": 32 | 64,
-        "bwd_warps": 2 | 4 | 8}), e.g. from autotune.autotune."""
+        "bwd_warps": 2 | 4 | 8}), e.g. from autotune.autotune.
+        fused_adam: apply Adam inside the preprocess backward
+        (gs_preprocess_bwd_adam) instead of storing the gradient and running
+        a separate Adam pass; self.grads then stays zero."""
         self.params = params
+        self.fused_adam = bool(fused_adam)
+        self.STAGES = self.STAGES_FUSED if self.fused_adam else self.STAGES_UNFUSED
         self.tuning = dict(tuning or {})
         self.grads = params.zeros_like()
         self.lam = float(lam)
@@ -114,8 +121,11 @@ class Trainer:
         groups.append({"p": p.sh, "g": g.sh, "m": m.sh, "v": v.sh, "lr": self.lrs["sh_rest"],
                        "period": 3 * K, "head": 3, "lr_head": self.lrs["sh_dc"]})
         self._adam = adam_groups_array(groups)
+        self._hp = adam_hparams(self.lrs)
         self._pstruct = p.struct()
         self._gstruct = g.struct()
+        self._mstruct = m.struct()
+        self._vstruct = v.struct()
 
     def set_lr(self, name: str, lr: float) -> None:
         """Change one learning rate (takes effect for eager steps; a captured
@@ -179,18 +189,29 @@ class Trainer:
         events: optional list of len(STAGES) + 1 CUDA events recorded on the
         stream around the stages, for per-stage timing."""
         st = stream if stream is not None else torch.cuda.current_stream()
+        s = st.cuda_stream
         ev = (lambda i: events[i].record(st)) if events is not None else (lambda i: None)
         ev(0)
-        self._splat_stages(cams, target, target_disp, st.cuda_stream, ev, 1)
         self.step_count += 1
+        if self.fused_adam:
+            self._splat_stages(cams, target, target_disp, s, ev, 1, with_pbwd=False)
+            sl = self.slot_for(cams)
+            L.check(L.lib().gs_preprocess_bwd_adam(sl.plan.handle, sl.plan.ws.data_ptr(), ctypes.byref(self._pstruct),
+                                                   self._cam(cams), ctypes.byref(self._mstruct),
+                                                   ctypes.byref(self._vstruct), ctypes.byref(self._hp),
+                                                   self.d_step.data_ptr(), s), "gs_preprocess_bwd_adam")
+            ev(6)
+            return
+        self._splat_stages(cams, target, target_disp, s, ev, 1)
         L.check(L.lib().gs_adam_step_multi_dev(self._adam, len(self._adam), 0.9, 0.999, 1e-15,
-                                               self.d_step.data_ptr(), st.cuda_stream), "gs_adam_step_multi_dev")
+                                               self.d_step.data_ptr(), s), "gs_adam_step_multi_dev")
         ev(7)
 
-    def _splat_stages(self, cams, target, target_disp, s, ev, e0: int) -> None:
+    def _splat_stages(self, cams, target, target_disp, s, ev, e0: int, with_pbwd: bool = True) -> None:
         """preprocess .. preprocess backward of self.params on `cams`; the
         parameter gradients accumulate into self.grads.  Records events
-        e0 .. e0 + 5 after each stage."""
+        e0 .. e0 + 5 after each stage (without the preprocess backward:
+        stops after the blend backward, e0 + 4)."""
         lib = L.lib()
         sl = self.slot_for(cams)
         h, ws = sl.plan.handle, sl.plan.ws.data_ptr()
@@ -212,6 +233,8 @@ class Trainer:
         L.check(lib.gs_render_bwd_blend(h, ws, sl.rgb.data_ptr(), sl.disp.data_ptr(), sl.dL_drgb.data_ptr(),
                                         sl.dL_ddisp.data_ptr() if use_disp else None, s), "gs_render_bwd_blend")
         ev(e0 + 4)
+        if not with_pbwd:
+            return
         L.check(lib.gs_preprocess_bwd(h, ws, ctypes.byref(self._pstruct), c, ctypes.byref(self._gstruct), s),
                 "gs_preprocess_bwd")
         ev(e0 + 5)
@@ -297,8 +320,8 @@ class NgTrainer(Trainer):
     log-scales and the MLP, which one Adam update then trains.  The anchor
     positions stay fixed."""
 
-    STAGES = ("decode", "preprocess", "bin_sort", "render_fwd", "loss", "render_bwd_blend", "preprocess_bwd",
-              "decode_bwd", "adam")
+    NG_STAGES = ("decode", "preprocess", "bin_sort", "render_fwd", "loss", "render_bwd_blend", "preprocess_bwd",
+                 "decode_bwd", "adam")
 
     def __init__(self, ng: NgParams, width: int | None = None, height: int | None = None, *,
                  ng_lrs: dict | None = None, **kw):
@@ -310,7 +333,9 @@ class NgTrainer(Trainer):
         self.ng_ws = gs_ng_workspace(ng.n, device=kw.get("device", "cuda"))
         children = ng_children(ng.n, device=kw.get("device", "cuda"))
         kw.setdefault("inst_capacity", max(1 << 20, 16 * children.n))
+        kw["fused_adam"] = False  # the children are decoded, not optimised
         super().__init__(children, width, height, **kw)
+        self.STAGES = NgTrainer.NG_STAGES
         self._ngp = ng.struct()
         self._ngg = self.ng_grads.struct()
 

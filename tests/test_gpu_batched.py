@@ -124,3 +124,61 @@ def test_graph_replay_matches_eager_steps(gs):
         off = np.abs(a - b) > 1e-6 * np.maximum(1.0, np.abs(a))
         assert off.mean() < 0.01, (k, off.mean())
     assert graphed.slot_for(cams).plan.status()["rc"] == 0
+
+
+def test_fused_preprocess_backward_adam_equals_unfused(gs):
+    """The fused preprocess backward + Adam against the separate kernels on
+    the same blend gradients, over three updates (moments evolving)."""
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import Trainer, default_lrs
+
+    scene, cams, targets, dts = _batch()
+    tr = Trainer(api.Gaussians.from_scene(scene), lam=0.2, disp_weight=0.1, inst_capacity=1 << 20)
+    tr.ensure_capacity([cams])
+    sl = tr.slot_for(cams)
+    lrs = default_lrs()
+    # parameters, first and second moments of each side
+    fused = [api.Gaussians(*(t.clone() for t in tr.params.tensors()), scene.sh_degree)]
+    fused += [tr.params.zeros_like(), tr.params.zeros_like()]
+    unf = [api.Gaussians(*(t.clone() for t in tr.params.tensors()), scene.sh_degree)]
+    unf += [tr.params.zeros_like(), tr.params.zeros_like()]
+    step_f = torch.zeros(1, dtype=torch.int32, device="cuda")
+    step_u = torch.zeros(1, dtype=torch.int32, device="cuda")
+    grads = tr.params.zeros_like()
+    tgt, tdisp = _flat(targets), _flat(dts)
+    for it in range(3):
+        # blend gradients of the current (fused) parameters, shared by both
+        tr.params = fused[0]
+        tr._build_adam()
+        tr._splat_stages(cams, tgt, tdisp, torch.cuda.current_stream().cuda_stream, lambda i: None, 0,
+                         with_pbwd=False)
+        api.gs_preprocess_bwd_adam(sl.plan, fused[0], cams, fused[1], fused[2], lrs, step_f)
+        for t in grads.tensors():
+            t.zero_()
+        from paper_2601_19489_gb300 import _lib as L
+        import ctypes
+        p, g = unf[0].struct(), grads.struct()
+        L.check(L.lib().gs_preprocess_bwd(sl.plan.handle, sl.plan.ws.data_ptr(), ctypes.byref(p),
+                                          api.cameras_array(cams), ctypes.byref(g),
+                                          torch.cuda.current_stream().cuda_stream), "gs_preprocess_bwd")
+        groups = []
+        for name in ("means", "log_scales", "quats", "opacity_logits"):
+            groups.append({"p": getattr(unf[0], name), "g": getattr(grads, name), "m": getattr(unf[1], name),
+                           "v": getattr(unf[2], name), "lr": lrs[name]})
+        K = (scene.sh_degree + 1) ** 2
+        groups.append({"p": unf[0].sh, "g": grads.sh, "m": unf[1].sh, "v": unf[2].sh, "lr": lrs["sh_rest"],
+                       "period": 3 * K, "head": 3, "lr_head": lrs["sh_dc"]})
+        api.gs_adam_step_multi_dev(groups, step_u)
+        torch.cuda.synchronize()
+        assert int(step_f.item()) == int(step_u.item()) == it + 1
+        for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+            a, b = to_np(getattr(fused[0], name)), to_np(getattr(unf[0], name))
+            off = np.abs(a - b) > 1e-6 * np.maximum(1.0, np.abs(b))
+            # a gradient that cancels to a few ulps may take either sign
+            assert off.mean() < 1e-3, (name, it, off.mean())
+            assert np.abs(a - b).max() <= 2.5 * max(lrs.values()) * (it + 1), (name, it)
+            # and both copies stay in step from here on
+            getattr(unf[0], name).copy_(getattr(fused[0], name))
+        for k in range(1, 3):
+            for t_u, t_f in zip(unf[k].tensors(), fused[k].tensors()):
+                t_u.copy_(t_f)
