@@ -57,7 +57,7 @@ def parse_args():
     ap.add_argument("--lam", type=float, default=0.2)
     ap.add_argument("--sq", action="store_true", help="sequential tile-key write instead of load-balanced")
     ap.add_argument("--tuning", type=str, default="",
-                    help="fixed launch shapes instead of the autotuner, e.g. LB/b32/w2")
+                    help="fixed launch shapes instead of the autotuner, e.g. LB/b32/w2/c0")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched CUDA-graph measurement")
     ap.add_argument("--batched-steps", type=int, default=60)
@@ -255,15 +255,16 @@ def run_ours(args, rank, world):
     params = api.Gaussians.from_scene(scene, device=dev)
     tuning, lb, table = {}, not args.sq, None
     if args.tuning:
-        mode, b, w = args.tuning.split("/")
-        lb, tuning = mode == "LB", {"bucket": int(b[1:]), "bwd_warps": int(w[1:])}
+        parts = args.tuning.split("/")
+        lb, tuning = parts[0] == "LB", {"bucket": int(parts[1][1:]), "bwd_warps": int(parts[2][1:])}
+        tuning["bwd_chains"] = int(parts[3][1:]) if len(parts) > 3 else 0
     elif not args.sq:  # launch shapes from the autotuner, on this workload's own views
         from paper_2601_19489_gb300.autotune import autotune
 
         tgt = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1)).to(dev)
                for v in range(2)]
         best, table = autotune(params, [[cams[0]], [cams[1]]], tgt, lam=args.lam, device=dev)
-        tuning = {"bucket": best["bucket"], "bwd_warps": best["bwd_warps"]}
+        tuning = {k: best[k] for k in ("bucket", "bwd_warps", "bwd_chains")}
         lb = best["load_balanced"]
         del tgt
     trainer = Trainer(params, args.width, args.height, lam=args.lam, load_balanced=lb, tuning=tuning, device=dev)
@@ -370,6 +371,7 @@ def run_ours(args, rank, world):
             "config": {**config_of(args), "binning": "load_balanced" if trainer.load_balanced else "sequential",
                        "bucket": trainer.slot_for([cams[0]]).plan.tuning["bucket"],
                        "bwd_warps": trainer.slot_for([cams[0]]).plan.tuning["bwd_warps"],
+                       "bwd_chains": trainer.slot_for([cams[0]]).plan.tuning["bwd_chains"],
                        "autotune_ms_per_step": trainer.autotune_table},
             "clocks": clocks, "e2e": e2e,
             "gpu_launches": kernels_per_step(trainer) * args.steps,
@@ -423,7 +425,7 @@ def run_batched(args, dev, n: int, steps: int, warmup: int = 3) -> dict:
     params = api.Gaussians.from_scene(scene, device=dev)
     best, table = autotune(params, batches, targets, lam=args.lam, device=dev)
     tr = Trainer(params, lam=args.lam, load_balanced=best["load_balanced"],
-                 tuning={"bucket": best["bucket"], "bwd_warps": best["bwd_warps"]}, device=dev)
+                 tuning={k: best[k] for k in ("bucket", "bwd_warps", "bwd_chains")}, device=dev)
     tr.ensure_capacity(batches)
     # eager batched steps (also the warm-up before capture)
     stream = torch.cuda.current_stream()
@@ -452,7 +454,7 @@ def run_batched(args, dev, n: int, steps: int, warmup: int = 3) -> dict:
     # the same views one at a time (single-view plans, eager)
     singles = [[c] for cams in batches for c in cams]
     seq = Trainer(params, lam=args.lam, load_balanced=best["load_balanced"],
-                  tuning={"bucket": best["bucket"], "bwd_warps": best["bwd_warps"]}, device=dev)
+                  tuning={k: best[k] for k in ("bucket", "bwd_warps", "bwd_chains")}, device=dev)
     seq.ensure_capacity(singles)
     offs = []
     for b, cams in enumerate(batches):

@@ -115,12 +115,19 @@ GS_API gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views, co
  *              checkpoint memory and traffic halve.
  *   bwd_warps  warps per CTA of the per-Gaussian backward (the warps of a CTA
  *              share one tile's staged pixel data): 2, 4 or 8.
- * A zero field takes the default (32, 4).  gs_plan_create uses the defaults.
+ *   bwd_chains pixel chains a lane of the backward pipeline walks: 2 (two
+ *              interleaved halves of the bucket's live pixels: more
+ *              independent work per step), 1 (one chain: fewer idle steps
+ *              while the pipeline fills and drains), or 0: two when the
+ *              bucket has at least 128 live pixels, else one.
+ * A zero field takes the default (32, 4, 0).  gs_plan_create uses the
+ * defaults.
  * Returns NULL on the same conditions as gs_plan_create or an unsupported
  * choice. */
 typedef struct {
     int32_t bucket;
     int32_t bwd_warps;
+    int32_t bwd_chains;
 } gs_tuning;
 GS_API gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n_views, const int32_t *h_widths,
                                      const int32_t *h_heights, int64_t inst_capacity, const gs_tuning *tuning);

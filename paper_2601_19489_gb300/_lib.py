@@ -31,7 +31,8 @@ EXPORTS = (
     "gs_workspace_view", "gs_read_status", "gs_error_string", "gs_preprocess", "gs_bin_sort",
     "gs_render_fwd", "gs_render_bwd", "gs_render_bwd_blend", "gs_preprocess_bwd",
     "gs_loss_scratch_floats", "gs_loss", "gs_adam_step",
-    "gs_adam_step_multi", "gs_adam_step_multi_dev", "gs_preprocess_bwd_adam", "gs_sort_scratch_bytes", "gs_sort_pairs_u32", "gs_sort_pairs_u32_noalloc",
+    "gs_adam_step_multi", "gs_adam_step_multi_dev", "gs_preprocess_bwd_adam", "gs_sort_scratch_bytes",
+    "gs_sort_pairs_u32", "gs_sort_pairs_u32_noalloc",
     "gs_ng_workspace_bytes", "gs_ng_decode_fwd", "gs_ng_decode_bwd", "gs_ng_read_status",
 )
 
@@ -50,7 +51,7 @@ class GsParams(ctypes.Structure):
 
 
 class GsTuning(ctypes.Structure):
-    _fields_ = [("bucket", ctypes.c_int32), ("bwd_warps", ctypes.c_int32)]
+    _fields_ = [("bucket", ctypes.c_int32), ("bwd_warps", ctypes.c_int32), ("bwd_chains", ctypes.c_int32)]
 
 
 class GsAdamHparams(ctypes.Structure):

@@ -16,6 +16,7 @@ namespace gs {
 constexpr int kTile = GS_TILE;             // 16 x 16 pixel tiles
 constexpr int kTilePix = kTile * kTile;    // 256 pixels
 constexpr int kBucket = GS_BUCKET;         // default splats per checkpoint
+constexpr int kTwoChainAuto = 128;         // automatic chain choice: two chains from 128 live pixels
 constexpr int kCkptCh = 5;                 // T, C.r, C.g, C.b, D
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
@@ -79,6 +80,7 @@ struct gs_plan {
     int64_t bucket_cap;
     int32_t bucket, bucket_shift;  // splats per checkpoint bucket (32 or 64) and its log2
     int32_t bwd_warps;             // warps per CTA of the per-Gaussian backward
+    int32_t two_chain_min;         // live pixels from which a backward bucket walks two chains
     // offsets
     size_t o_status, o_rec, o_touched, o_rect, o_dkey[2], o_dval[2];
     size_t o_ikey[2], o_ival[2], o_ranges, o_tile_maxc, o_bucket_off, o_ncontrib;

@@ -59,7 +59,10 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
                                          int64_t inst_capacity, const gs_tuning *tuning) {
     const int32_t bucket = tuning && tuning->bucket ? tuning->bucket : kBucket;
     const int32_t bwd_warps = tuning && tuning->bwd_warps ? tuning->bwd_warps : 4;
-    if ((bucket != 32 && bucket != 64) || (bwd_warps != 2 && bwd_warps != 4 && bwd_warps != 8)) return nullptr;
+    const int32_t chains = tuning ? tuning->bwd_chains : 0;
+    if ((bucket != 32 && bucket != 64) || (bwd_warps != 2 && bwd_warps != 4 && bwd_warps != 8) || chains < 0 ||
+        chains > 2)
+        return nullptr;
     if (n <= 0 || n >= (1ll << 31) || sh_degree < 0 || sh_degree > 3 || n_views < 1 ||
         n_views > GS_MAX_VIEWS || !widths || !heights || inst_capacity <= 0 ||
         inst_capacity >= (1ll << 31))
@@ -101,6 +104,7 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     p->bucket = bucket;
     p->bucket_shift = bucket == 64 ? 6 : 5;
     p->bwd_warps = bwd_warps;
+    p->two_chain_min = chains == 2 ? 0 : chains == 1 ? (1 << 30) : kTwoChainAuto;
     p->bucket_cap = inst_capacity / bucket + tiles + 1;
     p->sort_scratch_bytes = sort_scratch_bytes();
 

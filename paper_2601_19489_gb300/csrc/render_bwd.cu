@@ -84,7 +84,7 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
              const uint32_t *__restrict__ tile_maxc, const float *__restrict__ ckpt,
              const uint32_t *__restrict__ n_contrib, const float *__restrict__ img_rgb,
              const float *__restrict__ img_disp, const float *__restrict__ dL_drgb,
-             const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d) {
+             const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d, int two_chain_min) {
     constexpr int kThreads = kWarps * 32;
     constexpr int kBucketSplats = 32 * kSub;
     __shared__ BwdShared<kWarps, kSub> S;
@@ -173,39 +173,62 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
                 }
                 const uint32_t k = js + (uint32_t)lane;
                 SplatGrad acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                // two independent pixel chains (first and second half of the
-                // compacted list) interleave to hide the shuffle latency
-                float TA = 0.f, SA = 0.f, TB = 0.f, SB = 0.f;
-                for (int s = 0; s < h + 31; ++s) {
-                    float tA = __shfl_up_sync(0xffffffffu, TA, 1);
-                    float sA = __shfl_up_sync(0xffffffffu, SA, 1);
-                    float tB = __shfl_up_sync(0xffffffffu, TB, 1);
-                    float sB = __shfl_up_sync(0xffffffffu, SB, 1);
-                    const int mA = s - lane, mB = h + s - lane;
-                    if (lane == 0) {
-                        if (mA < h) {
+                if (m_total >= two_chain_min) {
+                    // two independent pixel chains (first and second half of
+                    // the compacted list) interleave to hide the shuffle
+                    // latency; the pipeline fills and drains over 31 steps
+                    float TA = 0.f, SA = 0.f, TB = 0.f, SB = 0.f;
+                    for (int s = 0; s < h + 31; ++s) {
+                        float tA = __shfl_up_sync(0xffffffffu, TA, 1);
+                        float sA = __shfl_up_sync(0xffffffffu, SA, 1);
+                        float tB = __shfl_up_sync(0xffffffffu, TB, 1);
+                        float sB = __shfl_up_sync(0xffffffffu, SB, 1);
+                        const int mA = s - lane, mB = h + s - lane;
+                        if (lane == 0) {
+                            if (mA < h) {
+                                const float2 c = ck_in[mA];
+                                tA = c.x;
+                                sA = c.y;
+                            }
+                            if (mB < m_total) {
+                                const float2 c = ck_in[mB];
+                                tB = c.x;
+                                sB = c.y;
+                            }
+                        }
+                        TA = tA;
+                        SA = sA;
+                        TB = tB;
+                        SB = sB;
+                        if (valid && mA >= 0) {
+                            if (mA < h) bwd_pair(S.g, S.fin, spix, mA, k, r0, r1, r2, TA, SA, acc);
+                            if (mB < m_total) bwd_pair(S.g, S.fin, spix, mB, k, r0, r1, r2, TB, SB, acc);
+                        }
+                        // the state behind the pass's last splat seeds the next pass
+                        if (carry && mA >= 0) {
+                            if (mA < h) ck_out[mA] = make_float2(TA, SA);
+                            if (mB < m_total) ck_out[mB] = make_float2(TB, SB);
+                        }
+                    }
+                } else {
+                    // one chain over the whole list: fewer idle lane-steps
+                    // while the pipeline fills and drains, which pays when
+                    // few pixels are still running
+                    float TA = 0.f, SA = 0.f;
+                    for (int s = 0; s < m_total + 31; ++s) {
+                        float tA = __shfl_up_sync(0xffffffffu, TA, 1);
+                        float sA = __shfl_up_sync(0xffffffffu, SA, 1);
+                        const int mA = s - lane;
+                        if (lane == 0 && mA < m_total) {
                             const float2 c = ck_in[mA];
                             tA = c.x;
                             sA = c.y;
                         }
-                        if (mB < m_total) {
-                            const float2 c = ck_in[mB];
-                            tB = c.x;
-                            sB = c.y;
-                        }
-                    }
-                    TA = tA;
-                    SA = sA;
-                    TB = tB;
-                    SB = sB;
-                    if (valid && mA >= 0) {
-                        if (mA < h) bwd_pair(S.g, S.fin, spix, mA, k, r0, r1, r2, TA, SA, acc);
-                        if (mB < m_total) bwd_pair(S.g, S.fin, spix, mB, k, r0, r1, r2, TB, SB, acc);
-                    }
-                    // the state behind the pass's last splat seeds the next pass
-                    if (carry && mA >= 0) {
-                        if (mA < h) ck_out[mA] = make_float2(TA, SA);
-                        if (mB < m_total) ck_out[mB] = make_float2(TB, SB);
+                        TA = tA;
+                        SA = sA;
+                        const bool live = mA >= 0 && mA < m_total;
+                        if (valid && live) bwd_pair(S.g, S.fin, spix, mA, k, r0, r1, r2, TA, SA, acc);
+                        if (carry && live) ck_out[mA] = make_float2(TA, SA);
                     }
                 }
                 if (valid) {
@@ -246,7 +269,7 @@ static int launch_bwd(const gs_plan *plan, void *ws, const float *d_rgb, const f
         vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
         ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off),
         ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt),
-        ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d);
+        ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, plan->two_chain_min);
     return launch_error();
 }
 

@@ -85,7 +85,7 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
             b_disp = [torch.cat([train_disp[i] for i in ix]) for ix in batches]
             b_cams = [[train_cams[i] for i in ix] for ix in batches]
             best, _ = autotune(params, b_cams[:2], b_rgb[:2], lam=lam, device=device)
-            tuning = {"bucket": best["bucket"], "bwd_warps": best["bwd_warps"]}
+            tuning = {k: best[k] for k in ("bucket", "bwd_warps", "bwd_chains")}
             lb = best["load_balanced"]
         elif method != "plain":
             raise ValueError(method)

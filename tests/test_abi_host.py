@@ -59,8 +59,9 @@ def test_tuned_plan_choices(lib):
 
     w = (ctypes.c_int32 * 1)(1920)
     h = (ctypes.c_int32 * 1)(1080)
-    for bucket, warps in ((16, 4), (128, 4), (32, 3), (64, 16)):
-        assert lib.gs_plan_create_tuned(1000, 0, 1, w, h, 1 << 20, ctypes.byref(L.GsTuning(bucket, warps))) is None
+    for bucket, warps, chains in ((16, 4, 0), (128, 4, 0), (32, 3, 0), (64, 16, 0), (32, 4, 3), (32, 4, -1)):
+        tu = L.GsTuning(bucket, warps, chains)
+        assert lib.gs_plan_create_tuned(1000, 0, 1, w, h, 1 << 20, ctypes.byref(tu)) is None
     sizes = {}
     for bucket in (0, 32, 64):
         p = lib.gs_plan_create_tuned(1000, 0, 1, w, h, 1 << 22, ctypes.byref(L.GsTuning(bucket, 0)))

@@ -148,7 +148,8 @@ def test_binning_lists_match_oracle_and_lb_equals_sq(gs):
 
 # --------------------------------------------------------------- forward
 
-TUNINGS = [None, {"bucket": 64, "bwd_warps": 2}, {"bucket": 64, "bwd_warps": 8}, {"bucket": 32, "bwd_warps": 8}]
+TUNINGS = [None, {"bucket": 64, "bwd_warps": 2, "bwd_chains": 2}, {"bucket": 64, "bwd_warps": 8, "bwd_chains": 1},
+           {"bucket": 32, "bwd_warps": 8, "bwd_chains": 2}, {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1}]
 
 
 @pytest.mark.parametrize("which", ["c1", "clustered_ragged"])
