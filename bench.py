@@ -327,17 +327,22 @@ def run_ours(args, rank, world):
     st2 = trainer.plan.status()
 
     # e2e: through the public API with host buffers, the target copied in and
-    # the loss read back every step
+    # the loss read back every step (the next step's target is copied on a
+    # side stream while the current step runs)
     e2e = None
     if not args.no_e2e:
+        from paper_2601_19489_gb300.trainer import HostFeeder
+
         loss_h = torch.empty(1, pin_memory=True)
+        feeder = HostFeeder(targets_d[0])
         barrier()
         t0 = time.perf_counter()
         for s in range(args.steps):
             v = s % len(cams)
-            tgt = targets_d[v]
-            tgt.copy_(targets_h[v], non_blocking=True)
+            nxt = targets_h[(s + 1) % len(cams)] if s + 1 < args.steps else None
+            tgt = feeder.get(targets_h[v], nxt)
             trainer.step(cams[v], tgt)
+            feeder.done()
             loss_h.copy_(trainer.loss, non_blocking=True)
         barrier()
         t_e2e = time.perf_counter() - t0

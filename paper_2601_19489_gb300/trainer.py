@@ -285,6 +285,52 @@ class Trainer:
         return StepGraph(self, cams, target, target_disp)
 
 
+class HostFeeder:
+    """Per-step inputs that live in pinned host memory, fed to the device
+    with the copy of step i+1's input running on a side stream while step i
+    computes (two device buffers, events between the streams).
+
+        feeder = HostFeeder(like=device_tensor_of_the_input_shape)
+        for i in ...:
+            x = feeder.get(host[i], host[i + 1] if more else None)
+            trainer.step(cams[i], x)
+            feeder.done()
+    """
+
+    def __init__(self, like: torch.Tensor):
+        self.buf = [torch.empty_like(like), torch.empty_like(like)]
+        self.stream = torch.cuda.Stream(like.device)
+        self.ready = [torch.cuda.Event(), torch.cuda.Event()]
+        self.free = [torch.cuda.Event(), torch.cuda.Event()]
+        self.slot = 0
+        self.primed = False
+
+    def _copy(self, slot: int, host: torch.Tensor) -> None:
+        self.stream.wait_event(self.free[slot])  # the buffer's previous step is done with it
+        with torch.cuda.stream(self.stream):
+            self.buf[slot].copy_(host, non_blocking=True)
+            self.ready[slot].record(self.stream)
+
+    def get(self, host_now: torch.Tensor, host_next: torch.Tensor | None = None) -> torch.Tensor:
+        """The device copy of host_now for this step (prefetched by the
+        previous call when it was given as host_next); starts copying
+        host_next."""
+        slot = self.slot
+        if not self.primed:
+            self._copy(slot, host_now)
+        torch.cuda.current_stream().wait_event(self.ready[slot])
+        self.primed = host_next is not None
+        if self.primed:
+            self._copy(1 - slot, host_next)
+        self.slot = 1 - slot
+        return self.buf[slot]
+
+    def done(self) -> None:
+        """Mark the buffer of the last get() free once the work enqueued so
+        far on the current stream (the step that read it) has run."""
+        self.free[1 - self.slot].record(torch.cuda.current_stream())
+
+
 class StepGraph:
     """A captured training step; ``replay()`` enqueues the whole step (every
     launch of it) as one graph launch on the current stream."""
