@@ -38,7 +38,7 @@ __device__ __forceinline__ void adam1(float &p, float &g, float &m, float &v, fl
                                       float eps, float step, float ibc2) {
     m = b1 * m + (1.0f - b1) * g;
     v = b2 * v + (1.0f - b2) * g * g;
-    p -= step * m / (sqrtf(v) * ibc2 + eps);
+    p -= __fdividef(step * m, sqrtf(v) * ibc2 + eps);  // divisor >= eps > 0: fast division, ~2 ulp
     g = 0.0f;
 }
 

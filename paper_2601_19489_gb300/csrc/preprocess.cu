@@ -330,11 +330,79 @@ struct PbArgs {
     const int32_t *d_step;       // step count, already incremented for this update
 };
 
+// The same update as k_adam's (same operations, same order): the quotient
+// with the fast division (about 2 ulp; the divisor is at least eps > 0).
 __device__ __forceinline__ void adam_el(float &p, float g, float &m, float &v, float b1, float b2, float eps,
                                         float step, float ibc2) {
     m = b1 * m + (1.0f - b1) * g;
     v = b2 * v + (1.0f - b2) * g * g;
-    p -= step * m / (sqrtf(v) * ibc2 + eps);
+    p -= __fdividef(step * m, sqrtf(v) * ibc2 + eps);
+}
+
+// (row, column) of element i of a warp's block of rows of kW floats; a quad
+// starting at a multiple of 4 stays in one row when kW is a multiple of 4.
+template <int kW>
+__device__ __forceinline__ void quad_rc(int j, int e, int &r, int &c) {
+    if constexpr (kW % 4 == 0) {
+        r = (4 * j) / kW;
+        c = 4 * j - r * kW + e;
+    } else {
+        const int i = 4 * j + e;
+        r = i / kW;
+        c = i - r * kW;
+    }
+}
+
+// Adam over a warp's SH block: parameters from shared memory (row stride
+// kRowS), gradients from the shared accumulators, moments streamed in
+// float4s, half of a lane's quads in flight per batch.  kFull: all 32 rows
+// present (no bounds checks).
+template <int K3, int kRowS, bool kFull>
+__device__ __forceinline__ void adam_sh_block(const float *s_p, const float *s_g, float *sh, float *m, float *v,
+                                              int rows, int lane, float s_dc, float s_rest, float b1, float b2,
+                                              float eps, float ibc2) {
+    const int F = kFull ? 32 * K3 : rows * K3, FQ = F >> 2;
+    float4 *p4 = reinterpret_cast<float4 *>(sh), *m4 = reinterpret_cast<float4 *>(m);
+    float4 *v4 = reinterpret_cast<float4 *>(v);
+    constexpr int kQL = (32 * K3 / 4 + 31) / 32;  // quads per lane, full block
+    constexpr int kU = (kQL + 1) / 2;
+#pragma unroll
+    for (int b = 0; b < kQL; b += kU) {
+        float4 mq[kU], vq[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int j = lane + 32 * (b + u);
+            if (b + u < kQL && (kFull ? j < 8 * K3 : j < FQ)) {
+                mq[u] = m4[j];
+                vq[u] = v4[j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int j = lane + 32 * (b + u);
+            if (b + u < kQL && (kFull ? j < 8 * K3 : j < FQ)) {
+                float pv[4], mv[4] = {mq[u].x, mq[u].y, mq[u].z, mq[u].w},
+                             vv[4] = {vq[u].x, vq[u].y, vq[u].z, vq[u].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    int r, c;
+                    quad_rc<K3>(j, e, r, c);
+                    pv[e] = s_p[r * kRowS + c];
+                    adam_el(pv[e], s_g[r * kRowS + c], mv[e], vv[e], b1, b2, eps, c < 3 ? s_dc : s_rest, ibc2);
+                }
+                p4[j] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+                m4[j] = make_float4(mv[0], mv[1], mv[2], mv[3]);
+                v4[j] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+            }
+        }
+    }
+    if (!kFull)
+        for (int i = 4 * FQ + lane; i < F; i += 32) {  // ragged end of the last warp
+            const int r = i / K3, c = i - r * K3;
+            float pv = s_p[r * kRowS + c];
+            adam_el(pv, s_g[r * kRowS + c], m[i], v[i], b1, b2, eps, c < 3 ? s_dc : s_rest, ibc2);
+            sh[i] = pv;
+        }
 }
 
 template <int D, bool kAdam>
@@ -364,11 +432,53 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
             if (touched[(int64_t)v * n + g] != 0) vmask |= 1u << v;
     const uint32_t busy = __ballot_sync(0xffffffffu, vmask != 0);
     if (!kAdam && busy == 0) return;  // uniform over the warp
+    if (kAdam && rows > 0) {
+        // ask L2 for the warp's blocks of every array the Adam phase streams
+        // (bulk prefetches, one range per lane, rounded down to whole 16-byte
+        // units inside the arrays), so that they arrive while the gradient
+        // is being computed
+        const int widths[5] = {3, 3, 4, 1, K3};
+        const int a = lane % 5, kind = lane / 5;  // lanes 0..14: (array, p / m / v)
+        if (lane < 15) {
+            const float *base = kind == 0 ? (a == 0 ? A.means : a == 1 ? A.log_scales : a == 2 ? A.quats
+                                                     : a == 3 ? A.logits : A.sh)
+                                          : (kind == 1 ? A.m[a] : A.v[a]);
+            const uint32_t bytes = (uint32_t)(rows * widths[a] * 4) & ~15u;
+            if (bytes > 0)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + g0 * widths[a]), "r"(bytes)
+                             : "memory");
+        }
+    }
     float *row = &s_sh[warp][lane * kRow];
     float *drow = &s_dsh[warp][lane * kRow];
-    for (int i = lane; i < rows * K3; i += 32) {
-        const int r = i / K3, c = i - r * K3;
-        s_sh[warp][r * kRow + c] = __ldg(sh + g0 * K3 + i);
+    {
+        // the warp's SH block (16-byte aligned: 32 rows of 3K floats) moves
+        // in float4s, all of a lane's loads issued before any is used
+        const int F = rows * K3, FQ = F >> 2;
+        const float4 *src = reinterpret_cast<const float4 *>(sh + g0 * K3);
+        constexpr int kQ = (32 * K3 / 4 + 31) / 32;  // float4s per lane for a full warp
+        float4 q[kQ];
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) {
+            const int j = lane + 32 * u;
+            if (j < FQ) q[u] = __ldg(src + j);
+        }
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) {
+            const int j = lane + 32 * u;
+            if (j < FQ) {
+                const float e[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = 4 * j + k, r = i / K3, c = i - r * K3;
+                    s_sh[warp][r * kRow + c] = e[k];
+                }
+            }
+        }
+        for (int i = 4 * FQ + lane; i < F; i += 32) {  // ragged end of the last warp
+            const int r = i / K3, c = i - r * K3;
+            s_sh[warp][r * kRow + c] = __ldg(sh + g0 * K3 + i);
+        }
     }
 #pragma unroll
     for (int c = 0; c < K3; ++c) drow[c] = 0.0f;
@@ -521,11 +631,34 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
             A.g_logits[g] += dlogit;
         }
         __syncwarp();
-        // the warp's SH gradient rows, accumulated with coalesced accesses
-        // (rows of Gaussians that touched no tile are left alone)
-        for (int i = lane; i < rows * K3; i += 32) {
+        // the warp's SH gradient rows, accumulated with coalesced float4
+        // accesses, all loads of a lane in flight together (rows of Gaussians
+        // that touched no tile get + 0)
+        const int F = rows * K3, FQ = F >> 2;
+        float4 *dst = reinterpret_cast<float4 *>(A.g_sh + g0 * K3);
+        constexpr int kQ = (32 * K3 / 4 + 31) / 32;
+        float4 q[kQ];
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) {
+            const int j = lane + 32 * u;
+            if (j < FQ) q[u] = dst[j];
+        }
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) {
+            const int j = lane + 32 * u;
+            if (j < FQ) {
+                float e[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = 4 * j + k, r = i / K3, c = i - r * K3;
+                    e[k] += s_dsh[warp][r * kRow + c];
+                }
+                dst[j] = make_float4(e[0], e[1], e[2], e[3]);
+            }
+        }
+        for (int i = 4 * FQ + lane; i < F; i += 32) {  // ragged end of the last warp
             const int r = i / K3, c = i - r * K3;
-            if ((busy >> r) & 1u) A.g_sh[g0 * K3 + i] += s_dsh[warp][r * kRow + c];
+            A.g_sh[g0 * K3 + i] += s_dsh[warp][r * kRow + c];
         }
         return;
     }
@@ -595,50 +728,14 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
             vvp[i] = v2;
         }
     }
-    // SH rows: parameters from shared memory, gradients from the shared
-    // accumulators, moments in float4, three quads per lane in flight
+    // SH rows
     const float s_dc = A.lr[4] * ibc1, s_rest = A.lr[5] * ibc1;
-    const int F = rows * K3, FQ = F >> 2;
-    float4 *p4 = reinterpret_cast<float4 *>(A.sh + g0 * K3);
-    float4 *m4 = reinterpret_cast<float4 *>(A.m[4] + g0 * K3);
-    float4 *v4 = reinterpret_cast<float4 *>(A.v[4] + g0 * K3);
-    constexpr int kU = 3;
-    for (int j0 = lane; j0 < FQ; j0 += 32 * kU) {
-        float4 mq[kU], vq[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int j = j0 + 32 * u;
-            if (j < FQ) {
-                mq[u] = m4[j];
-                vq[u] = v4[j];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int j = j0 + 32 * u;
-            if (j >= FQ) break;
-            float pv[4], mv[4] = {mq[u].x, mq[u].y, mq[u].z, mq[u].w}, vv[4] = {vq[u].x, vq[u].y, vq[u].z, vq[u].w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int i = 4 * j + e, r = i / K3, c = i - r * K3;
-                pv[e] = s_sh[warp][r * kRow + c];
-                adam_el(pv[e], s_dsh[warp][r * kRow + c], mv[e], vv[e], A.b1, A.b2, A.eps, c < 3 ? s_dc : s_rest,
-                        ibc2);
-            }
-            p4[j] = make_float4(pv[0], pv[1], pv[2], pv[3]);
-            m4[j] = make_float4(mv[0], mv[1], mv[2], mv[3]);
-            v4[j] = make_float4(vv[0], vv[1], vv[2], vv[3]);
-        }
-    }
-    for (int i = 4 * FQ + lane; i < F; i += 32) {  // ragged end of the last warp
-        const int r = i / K3, c = i - r * K3;
-        float pv = s_sh[warp][r * kRow + c];
-        float mv = A.m[4][g0 * K3 + i], vv = A.v[4][g0 * K3 + i];
-        adam_el(pv, s_dsh[warp][r * kRow + c], mv, vv, A.b1, A.b2, A.eps, c < 3 ? s_dc : s_rest, ibc2);
-        A.sh[g0 * K3 + i] = pv;
-        A.m[4][g0 * K3 + i] = mv;
-        A.v[4][g0 * K3 + i] = vv;
-    }
+    if (rows == 32)
+        adam_sh_block<K3, kRow, true>(s_sh[warp], s_dsh[warp], A.sh + g0 * K3, A.m[4] + g0 * K3,
+                                      A.v[4] + g0 * K3, rows, lane, s_dc, s_rest, A.b1, A.b2, A.eps, ibc2);
+    else
+        adam_sh_block<K3, kRow, false>(s_sh[warp], s_dsh[warp], A.sh + g0 * K3, A.m[4] + g0 * K3,
+                                       A.v[4] + g0 * K3, rows, lane, s_dc, s_rest, A.b1, A.b2, A.eps, ibc2);
 }
 
 template <int D>
