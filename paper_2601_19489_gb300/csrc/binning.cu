@@ -14,8 +14,7 @@
 //     evaluates a per-column ellipse test whatever the Gaussians' sizes, and
 //     a segmented warp scan places each column's tiles;
 //     sequential ("Sq"): one thread walks its Gaussian's columns.
-//     Each round of Gaussians assembles its (contiguous) run of instances in
-//     shared memory and writes it out coalesced.
+//     Each round of Gaussians writes its (contiguous) run of instances.
 //  4. stable radix sort of the instances by tile id: every tile's list keeps
 //     the depth order of step 1, ties in depth by ascending Gaussian index.
 //  5. tile ranges by binary search in the sorted ids and the 32-splat bucket
@@ -50,7 +49,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *w
 }
 
 __device__ __forceinline__ void chunk_of(int64_t n, int64_t *beg, int64_t *end) {
-    const int64_t chunk = (n + kSortBlocks - 1) / kSortBlocks;
+    const int64_t chunk = (n + kBinBlocks - 1) / kBinBlocks;
     *beg = (int64_t)blockIdx.x * chunk;
     *end = *beg + chunk < n ? *beg + chunk : n;
 }
@@ -70,12 +69,22 @@ k_count_reduce(const uint32_t *__restrict__ order, const uint32_t *__restrict__ 
 
 // One block: exclusive scan (64-bit) of the block sums into block_offs;
 // publishes the instance count (saturated to 32 bits) and the overflow flag.
+// Thread t owns the kCountPer consecutive sums from t * kCountPer.
+constexpr int kCountPer = (kBinBlocks + 1023) / 1024;
+
 __global__ void __launch_bounds__(1024)
 k_count_top(const uint32_t *__restrict__ block_sums, unsigned long long *__restrict__ block_offs,
             StatusDev *st, int64_t capacity) {
     __shared__ unsigned long long tmp[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned long long x = tid < kSortBlocks ? block_sums[tid] : 0ull;
+    unsigned long long own[kCountPer];
+    unsigned long long x = 0;
+#pragma unroll
+    for (int k = 0; k < kCountPer; ++k) {
+        const int b = tid * kCountPer + k;
+        own[k] = b < kBinBlocks ? block_sums[b] : 0ull;
+        x += own[k];
+    }
     unsigned long long inc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -89,7 +98,13 @@ k_count_top(const uint32_t *__restrict__ block_sums, unsigned long long *__restr
         before += w < warp ? tmp[w] : 0ull;
         all += tmp[w];
     }
-    if (tid < kSortBlocks) block_offs[tid] = inc - x + before;
+    unsigned long long run = inc - x + before;
+#pragma unroll
+    for (int k = 0; k < kCountPer; ++k) {
+        const int b = tid * kCountPer + k;
+        if (b < kBinBlocks) block_offs[b] = run;
+        run += own[k];
+    }
     if (tid == 0) {
         st->n_inst = all > 0xffffffffull ? 0xffffffffu : (uint32_t)all;
         st->overflow = all > (unsigned long long)capacity ? 1u : 0u;
@@ -98,12 +113,11 @@ k_count_top(const uint32_t *__restrict__ block_sums, unsigned long long *__restr
 
 // Instance key write.  Block b takes the chunk of depth ranks whose count it
 // summed, in rounds of kWriteRound ranks: a block scan of their tile counts
-// gives each Gaussian its slot range, the round's instances are assembled in
-// shared memory (they form one contiguous run of the output) and written out
-// coalesced.  A round with more instances than the staging holds writes
-// straight to global memory instead.
+// gives each Gaussian its slot range, and the round's instances (one
+// contiguous run of the output) are written straight to global memory, where
+// L2 merges the lanes' neighbouring writes.  (Assembling each run in shared
+// memory first was measured slower: it limited the blocks per SM.)
 constexpr int kWriteRound = 128;
-constexpr int kStageCap = 5504;  // instances staged per round (43 KB)
 
 __device__ __forceinline__ uint32_t block_exclusive_scan128(uint32_t x, uint32_t *warp_tmp, uint32_t *total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -128,21 +142,14 @@ __device__ __forceinline__ uint32_t block_exclusive_scan128(uint32_t x, uint32_t
 }
 
 struct WriteSink {
-    uint32_t *s_tile, *s_item;       // staging (shared)
     uint32_t *g_tile, *g_item;       // output (global)
     unsigned long long round_base;   // global position of the round's first instance
     unsigned long long capacity;
-    bool staged;
     __device__ __forceinline__ void put(uint32_t local, uint32_t tile, uint32_t item) const {
-        if (staged) {
-            s_tile[local] = tile;
-            s_item[local] = item;
-        } else {
-            const unsigned long long pos = round_base + local;
-            if (pos < capacity) {
-                g_tile[pos] = tile;
-                g_item[pos] = item;
-            }
+        const unsigned long long pos = round_base + local;
+        if (pos < capacity) {
+            g_tile[pos] = tile;
+            g_item[pos] = item;
         }
     }
 };
@@ -155,7 +162,6 @@ k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ or
              const unsigned long long *__restrict__ block_offs, int64_t n, int64_t capacity,
              uint32_t *__restrict__ inst_tile, uint32_t *__restrict__ inst_item, StatusDev *st) {
     __shared__ uint32_t tmp[kWriteRound / 32];
-    __shared__ uint32_t s_tile_out[kStageCap], s_item_out[kStageCap];
     int64_t beg, end;
     chunk_of(n, &beg, &end);
     unsigned long long base = block_offs[blockIdx.x];
@@ -169,8 +175,7 @@ k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ or
         }
         uint32_t total;
         const uint32_t off = block_exclusive_scan128(cnt, tmp, &total);
-        WriteSink sink{s_tile_out, s_item_out, inst_tile, inst_item, base, (unsigned long long)capacity,
-                       total <= (uint32_t)kStageCap};
+        WriteSink sink{inst_tile, inst_item, base, (unsigned long long)capacity};
         if (!kLB) {
             // one thread per Gaussian walks its columns
             if (cnt) {
@@ -298,17 +303,6 @@ k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ or
                     sink.put(off + w, (uint32_t)(mtoff + mty0 * mtiles_x + mtx0), item);
             }
         }
-        __syncthreads();
-        if (sink.staged) {
-            for (uint32_t i = threadIdx.x; i < total; i += kWriteRound) {
-                const unsigned long long pos = base + i;
-                if (pos < (unsigned long long)capacity) {
-                    inst_tile[pos] = s_tile_out[i];
-                    inst_item[pos] = s_item_out[i];
-                }
-            }
-            __syncthreads();
-        }
         base += total;
     }
 }
@@ -399,9 +393,9 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
 
     // 2. scan of tile counts in depth order
     uint32_t *block_sums = ws_at<uint32_t>(ws, plan->o_block_sums);
-    unsigned long long *block_offs = reinterpret_cast<unsigned long long *>(block_sums + kSortBlocks + 32);
+    unsigned long long *block_offs = reinterpret_cast<unsigned long long *>(block_sums + kBinBlocks + 32);
     const uint32_t *touched = ws_at<uint32_t>(ws, plan->o_touched);
-    k_count_reduce<<<kSortBlocks, kScanThreads, 0, s>>>(order, touched, VN, block_sums);
+    k_count_reduce<<<kBinBlocks, kScanThreads, 0, s>>>(order, touched, VN, block_sums);
     k_count_top<<<1, 1024, 0, s>>>(block_sums, block_offs, st, plan->inst_cap);
 
     // 3. instance keys
@@ -409,12 +403,12 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
     uint32_t *ik0 = ws_at<uint32_t>(ws, plan->o_ikey[0]), *iv0 = ws_at<uint32_t>(ws, plan->o_ival[0]);
     uint32_t *ik1 = ws_at<uint32_t>(ws, plan->o_ikey[1]), *iv1 = ws_at<uint32_t>(ws, plan->o_ival[1]);
     if (load_balanced)
-        k_write_keys<true><<<kSortBlocks, kWriteRound, 0, s>>>(
+        k_write_keys<true><<<kBinBlocks, kWriteRound, 0, s>>>(
             vd, plan->n, order, touched, ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin),
             ws_at<uint2>(ws, plan->o_rect),
             block_offs, VN, plan->inst_cap, ik0, iv0, st);
     else
-        k_write_keys<false><<<kSortBlocks, kWriteRound, 0, s>>>(
+        k_write_keys<false><<<kBinBlocks, kWriteRound, 0, s>>>(
             vd, plan->n, order, touched, ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin),
             ws_at<uint2>(ws, plan->o_rect),
             block_offs, VN, plan->inst_cap, ik0, iv0, st);

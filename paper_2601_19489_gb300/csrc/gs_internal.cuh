@@ -31,6 +31,7 @@ constexpr float kInvH = 1.0f / kH;
 constexpr float kLevelRel = 1.0f + 1.0f / 1024.0f;
 constexpr float kLevelAbs = 1.0f / 4096.0f;
 constexpr int kSortBlocks = 608;           // 4 x 152 SMs: fixed grid of the sort/scan passes
+constexpr int kBinBlocks = 2432;           // 16 x 152 SMs: fixed grid of the tile-count scan and key write
 constexpr int kSortThreads = 256;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;

@@ -136,7 +136,7 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     p->o_grad2d = take(VN * 3 * sizeof(float4));
     p->o_sort_scratch = take(p->sort_scratch_bytes);
     // uint32 block sums, then (8-byte aligned) uint64 block offsets
-    p->o_block_sums = take((kSortBlocks + 32) * sizeof(uint32_t) + kSortBlocks * sizeof(uint64_t));
+    p->o_block_sums = take((kBinBlocks + 32) * sizeof(uint32_t) + kBinBlocks * sizeof(uint64_t));
     p->bytes = o;
     // the radix sort ping-pongs: after P passes the data is in buffer P % 2
     p->depth_final = (32 / kRadixBits) % 2;
