@@ -75,56 +75,81 @@ k_ssim_fwd(Planes pl, Window win, const float *__restrict__ x, const float *__re
         Yv[r][c] = b;
     }
     __syncthreads();
-    for (int i = tid; i < kSsimIn * kSsimT; i += 256) {
-        const int r = i / kSsimT, c = i - r * kSsimT;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+    // horizontal pass: a thread blurs 4 adjacent outputs of a row from 14
+    // loaded inputs (register blocking: each input and its products are
+    // read once for 4 outputs)
+    for (int i = tid; i < kSsimIn * (kSsimT / 4); i += 256) {
+        const int r = i / (kSsimT / 4), c0 = 4 * (i - r * (kSsimT / 4));
+        float s[5][4];
 #pragma unroll
-        for (int u = 0; u < 11; ++u) {
-            const float a = X[r][c + u], b = Yv[r][c + u], w = win.w[u];
-            s0 += w * a;
-            s1 += w * b;
-            s2 += w * a * a;
-            s3 += w * b * b;
-            s4 += w * a * b;
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) s[q][o] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 14; ++k) {
+            const float a = X[r][c0 + k], b = Yv[r][c0 + k];
+            const float v[5] = {a, b, a * a, b * b, a * b};
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const int u = k - o;  // tap of output c0 + o
+                if (u >= 0 && u < 11) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) s[q][o] += win.w[u] * v[q];
+                }
+            }
         }
-        Hs[0][r][c] = s0;
-        Hs[1][r][c] = s1;
-        Hs[2][r][c] = s2;
-        Hs[3][r][c] = s3;
-        Hs[4][r][c] = s4;
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) Hs[q][r][c0 + o] = s[q][o];
     }
     __syncthreads();
     float acc_s = 0.f, acc_l1 = 0.f;
     const int64_t npl = (int64_t)W * H;
-    for (int i = tid; i < kSsimT * kSsimT; i += 256) {
-        const int r = i / kSsimT, c = i - r * kSsimT;
-        const int gx = blockIdx.x * kSsimT + c, gy = blockIdx.y * kSsimT + r;
-        if (gx >= W || gy >= H) continue;
-        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+    // vertical pass: a thread blurs 4 outputs of a column from 14 rows
+    for (int i = tid; i < (kSsimT / 4) * kSsimT; i += 256) {
+        const int r0 = 4 * (i / kSsimT), c = i - (i / kSsimT) * kSsimT;
+        float s[5][4];
 #pragma unroll
-        for (int u = 0; u < 11; ++u) {
-            const float w = win.w[u];
-            mx += w * Hs[0][r + u][c];
-            my += w * Hs[1][r + u][c];
-            exx += w * Hs[2][r + u][c];
-            eyy += w * Hs[3][r + u][c];
-            exy += w * Hs[4][r + u][c];
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) s[q][o] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 14; ++k) {
+            float v[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) v[q] = Hs[q][r0 + k][c];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const int u = k - o;
+                if (u >= 0 && u < 11) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) s[q][o] += win.w[u] * v[q];
+                }
+            }
         }
-        const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
-        const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
-        const float inv = 1.0f / (B1 * B2);
-        const float S = A1 * A2 * inv;
-        // partials w.r.t. mu_x, E_xx, E_xy (sxx = E_xx - mu_x^2, sxy = E_xy - mu_x mu_y)
-        const float d_mu = 2.f * my * (A2 - A1) * inv - 2.f * mx * S * (1.0f / B1 - 1.0f / B2);
-        const float d_exx = -S / B2;
-        const float d_exy = 2.f * A1 * inv;
-        const int64_t p = base + (int64_t)gy * W + gx;
-        maps[p] = d_mu;
-        maps[plane_stride + p] = d_exx;
-        maps[2 * plane_stride + p] = d_exy;
-        acc_s += S;
-        acc_l1 += fabsf(X[r + kHalo][c + kHalo] - Yv[r + kHalo][c + kHalo]);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const int r = r0 + o;
+            const int gx = blockIdx.x * kSsimT + c, gy = blockIdx.y * kSsimT + r;
+            if (gx >= W || gy >= H) continue;
+            const float mx = s[0][o], my = s[1][o], exx = s[2][o], eyy = s[3][o], exy = s[4][o];
+            const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
+            const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
+            const float inv = 1.0f / (B1 * B2);
+            const float S = A1 * A2 * inv;
+            // partials w.r.t. mu_x, E_xx, E_xy (sxx = E_xx - mu_x^2, sxy = E_xy - mu_x mu_y)
+            const float d_mu = 2.f * my * (A2 - A1) * inv - 2.f * mx * S * (1.0f / B1 - 1.0f / B2);
+            const float d_exx = -S / B2;
+            const float d_exy = 2.f * A1 * inv;
+            const int64_t p = base + (int64_t)gy * W + gx;
+            maps[p] = d_mu;
+            maps[plane_stride + p] = d_exx;
+            maps[2 * plane_stride + p] = d_exy;
+            acc_s += S;
+            acc_l1 += fabsf(X[r + kHalo][c + kHalo] - Yv[r + kHalo][c + kHalo]);
+        }
     }
     (void)npl;
 #pragma unroll
@@ -174,36 +199,59 @@ k_ssim_bwd(Planes pl, Window win, const float *__restrict__ x, const float *__re
         M[2][r][c] = d;
     }
     __syncthreads();
-    for (int i = tid; i < kSsimIn * kSsimT; i += 256) {
-        const int r = i / kSsimT, c = i - r * kSsimT;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    // the same two register-blocked passes as the forward, over 3 maps
+    for (int i = tid; i < kSsimIn * (kSsimT / 4); i += 256) {
+        const int r = i / (kSsimT / 4), c0 = 4 * (i - r * (kSsimT / 4));
+        float s[3][4];
 #pragma unroll
-        for (int u = 0; u < 11; ++u) {
-            const float w = win.w[u];
-            s0 += w * M[0][r][c + u];
-            s1 += w * M[1][r][c + u];
-            s2 += w * M[2][r][c + u];
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) s[q][o] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 14; ++k) {
+            const float v[3] = {M[0][r][c0 + k], M[1][r][c0 + k], M[2][r][c0 + k]};
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const int u = k - o;
+                if (u >= 0 && u < 11) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) s[q][o] += win.w[u] * v[q];
+                }
+            }
         }
-        Hs[0][r][c] = s0;
-        Hs[1][r][c] = s1;
-        Hs[2][r][c] = s2;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) Hs[q][r][c0 + o] = s[q][o];
     }
     __syncthreads();
-    for (int i = tid; i < kSsimT * kSsimT; i += 256) {
-        const int r = i / kSsimT, c = i - r * kSsimT;
-        const int gx = blockIdx.x * kSsimT + c, gy = blockIdx.y * kSsimT + r;
-        if (gx >= W || gy >= H) continue;
-        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+    for (int i = tid; i < (kSsimT / 4) * kSsimT; i += 256) {
+        const int r0 = 4 * (i / kSsimT), c = i - (i / kSsimT) * kSsimT;
+        float s[3][4];
 #pragma unroll
-        for (int u = 0; u < 11; ++u) {
-            const float w = win.w[u];
-            b0 += w * Hs[0][r + u][c];
-            b1 += w * Hs[1][r + u][c];
-            b2 += w * Hs[2][r + u][c];
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) s[q][o] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 14; ++k) {
+            const float v[3] = {Hs[0][r0 + k][c], Hs[1][r0 + k][c], Hs[2][r0 + k][c]};
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const int u = k - o;
+                if (u >= 0 && u < 11) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) s[q][o] += win.w[u] * v[q];
+                }
+            }
         }
-        const int64_t p = base + (int64_t)gy * W + gx;
-        const float xv = x[p], yv = y[p];
-        grad[p] = c_l1 * sgn(xv - yv) + c_ssim * (b0 + 2.f * xv * b1 + yv * b2);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const int gx = blockIdx.x * kSsimT + c, gy = blockIdx.y * kSsimT + r0 + o;
+            if (gx >= W || gy >= H) continue;
+            const int64_t p = base + (int64_t)gy * W + gx;
+            const float xv = x[p], yv = y[p];
+            grad[p] = c_l1 * sgn(xv - yv) + c_ssim * (s[0][o] + 2.f * xv * s[1][o] + yv * s[2][o]);
+        }
     }
 }
 
