@@ -39,9 +39,14 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # Algorithmic floating-point work per evaluated pixel-splat pair, counted
 # from the kernels' arithmetic (FMA = 2): forward blend 25, backward 62.
 FLOP_PER_PAIR = {"render_fwd": 25.0, "render_bwd_blend": 62.0}
-# DRAM bytes per launch from one ncu capture, valid only for the kernel
-# source they were taken on (sha256 of the .cu file, first 16 hex digits).
-NCU_TRAFFIC: dict = {}
+# DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, 1 pass, on this workload at full size: 1M Gaussians,
+# one 1920x1080 view), valid only for the kernel source they were taken on
+# (sha256 of the .cu file, first 16 hex digits) and the same launch shape.
+NCU_TRAFFIC: dict = {
+    "k_render_bwd": {"bytes_per_launch": 2.415e8, "src_sha": "61f4d54018853a4b", "tuning": "LB/b32/w2/c1",
+                     "read": 2.393e8, "write": 2.3e6},
+}
 
 
 def parse_args():
@@ -269,6 +274,8 @@ def run_ours(args, rank, world):
         del tgt
     trainer = Trainer(params, args.width, args.height, lam=args.lam, load_balanced=lb, tuning=tuning, device=dev)
     trainer.autotune_table = table
+    tu = trainer.slot_for([cams[0]]).plan.tuning
+    trainer_tuning_key = (f"{'LB' if lb else 'Sq'}/b{tu['bucket']}/w{tu['bwd_warps']}/c{tu['bwd_chains']}")
     ntiles = ((args.width + 15) // 16) * ((args.height + 15) // 16)
     trainer.plan_tile_bits = max(1, int(np.ceil(np.log2(ntiles))))
     targets_h = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1))
@@ -364,7 +371,9 @@ def run_ours(args, rank, world):
         ach = FLOP_PER_PAIR[dominant] * mean_pairs / (stage_ms[dominant] / 1e3) / 1e12
         tr = NCU_TRAFFIC.get(kname)
         src = {"k_render_bwd": "render_bwd.cu", "k_render_fwd": "render_fwd.cu"}[kname]
-        traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == src_sha(src) else None
+        tun = trainer_tuning_key
+        traffic = (tr["bytes_per_launch"] if tr and tr.get("src_sha") == src_sha(src) and tr.get("tuning") == tun
+                   else None)
         roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": kname,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
