@@ -409,5 +409,37 @@ void orc_render_bwd(int64_t n, const double *proj, const double *bg,
     orc_free_lists(&L);
 }
 
+/*
+ * Contributor-weighted sums for score-guided densification (Sec. 3.3, Eq. 4
+ * and Eq. 6): for every pixel of the window and every Gaussian the forward
+ * blends there (the same rules as orc_render_fwd: alpha >= 1/255, before the
+ * transmittance stop), ADD the pixel's weight weight[p] (h x w) to
+ * out_score[id].  Serial over pixels, in pixel order.
+ */
+void orc_contrib_score(int64_t n, const double *proj, int x0, int y0, int x1, int y1,
+                       const double *weight, double *out_score) {
+    orc_lists L;
+    orc_build_lists(n, proj, x0, y0, x1, y1, &L);
+    int w = x1 - x0, h = y1 - y0;
+    int64_t npix = (int64_t)w * h;
+    for (int64_t p = 0; p < npix; ++p) {
+        if (weight[p] == 0.0) continue;
+        double px = (double)(x0 + p % w) + 0.5, py = (double)(y0 + p / w) + 0.5;
+        double T = 1.0;
+        for (int64_t k = L.start[p]; k < L.start[p + 1]; ++k) {
+            const double *g = proj + L.ids[k] * ORC_STRIDE;
+            orc_pair e;
+            orc_eval(g, px, py, &e);
+            if (e.power > 0.0 || e.alpha < ORC_ALPHA_MIN) continue;
+            double test_T = T * (1.0 - e.alpha);
+            if (test_T < ORC_T_STOP) break;
+            out_score[L.ids[k]] += weight[p];
+            T = test_T;
+        }
+    }
+    (void)h;
+    orc_free_lists(&L);
+}
+
 int orc_stride(void) { return ORC_STRIDE; }
 int orc_g2d(void) { return ORC_G2D; }

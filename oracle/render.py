@@ -73,6 +73,9 @@ def _load():
             lib.orc_render_bwd.restype = None
             lib.orc_render_bwd.argtypes = [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_int]
+            lib.orc_contrib_score.restype = None
+            lib.orc_contrib_score.argtypes = [ctypes.c_int64, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, P, P]
             assert lib.orc_stride() == STRIDE and lib.orc_g2d() == G2D
             _lib = lib
     return _lib
@@ -123,4 +126,19 @@ def render_bwd(proj: np.ndarray, bg, window, g_rgb: np.ndarray, g_disp: np.ndarr
     out = np.zeros((proj.shape[0], G2D))
     lib.orc_render_bwd(proj.shape[0], _ptr(proj), _ptr(bg), x0, y0, x1, y1, _ptr(g_rgb),
                        _ptr(g_disp), _ptr(out), int(n_threads))
+    return out
+
+
+def contrib_score(proj: np.ndarray, window, weight: np.ndarray, out: np.ndarray | None = None) -> np.ndarray:
+    """Add, for every pixel of the window and every Gaussian blended there,
+    the pixel's weight (h, w) to that Gaussian's entry of the (N,) score."""
+    lib = _load()
+    proj = np.ascontiguousarray(proj, dtype=np.float64)
+    x0, y0, x1, y1 = (int(v) for v in window)
+    weight = np.ascontiguousarray(weight, dtype=np.float64)
+    assert weight.shape == (y1 - y0, x1 - x0)
+    if out is None:
+        out = np.zeros(proj.shape[0])
+    assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape == (proj.shape[0],)
+    lib.orc_contrib_score(proj.shape[0], _ptr(proj), x0, y0, x1, y1, _ptr(weight), _ptr(out))
     return out
