@@ -354,6 +354,56 @@ GS_API int gs_ng_decode_bwd(const gs_ng_params *ng, const gs_camera *h_cam, cons
  * if a bounded wait for the tensor cores gave up). */
 GS_API int gs_ng_read_status(void *d_ws, int32_t *out_error, void *stream);
 
+/* ------------------------------ densification and pruning (Sec. 3.3)
+ * Multi-view score-guided densification and pruning, in three calls:
+ *
+ * gs_densify_score: after gs_render_fwd on a plan (one or more views), add
+ *   each view's terms to the per-Gaussian scores.  Eq. 3: the view's error
+ *   E(u,v) = sum_c |rgb_c - target_c| divided by its maximum over the view;
+ *   mask M = [E / max E > tau].  Eq. 4: d_s_plus[i] += number of masked
+ *   pixels of the view that Gaussian i is blended into (same alpha, cut-off
+ *   and stop decisions as the forward).  Eq. 6: d_r_minus[i] += that number
+ *   times d_photo[v], the view's photometric loss (device float per view of
+ *   the plan, e.g. gs_loss of that view alone).  d_rgb, d_target: planar
+ *   colour of the plan's views (device).  Scores accumulate (+=).
+ *   d_scratch: device bytes of gs_densify_scratch_bytes(n).
+ *
+ * gs_densify_plan: from the accumulated scores over K views, every
+ *   Gaussian's action (d_action[i], one of GS_DENSIFY_*) and its first
+ *   output slot (d_offsets[i], int64): s+ = d_s_plus / K; s- = d_r_minus /
+ *   max d_r_minus; prune if s- > tau_minus or sigmoid(opacity logit) <
+ *   min_opacity; else clone (largest scale <= percent_dense * extent) or
+ *   split (larger) if s+ > tau_plus; else keep.  Writes the new Gaussian
+ *   count to *out_new_n (host) and synchronises the stream.
+ *
+ * gs_densify_apply: write the new Gaussian set (parameters and both Adam
+ *   moments) into dst, dst_m, dst_v (device arrays with room for the new
+ *   count; same SH degree): kept Gaussians are copied with their moments;
+ *   a clone adds a copy with zero moments; a split replaces the Gaussian by
+ *   two at mean + R diag(s) z_k (z_k: d_normals[6 i + 3 k .. + 3], standard
+ *   normal samples supplied by the caller) with scales s / 1.6, the same
+ *   rotation, opacity and SH, and zero moments.  Output order follows the
+ *   sources.  The paper gives no thresholds or split rule; these are the 3DGS
+ *   rules the method builds on. */
+enum { GS_DENSIFY_PRUNE = 0, GS_DENSIFY_KEEP = 1, GS_DENSIFY_CLONE = 2, GS_DENSIFY_SPLIT = 3 };
+typedef struct {
+    float tau_plus;       /* threshold on s+ (masked pixels per view) */
+    float tau_minus;      /* threshold on the normalised s- */
+    float min_opacity;    /* opacity below which a Gaussian is pruned */
+    float percent_dense;  /* clone/split boundary as a fraction of extent */
+    float extent;         /* scene extent */
+    int32_t k_views;      /* K, the number of views scored */
+} gs_densify_rules;
+GS_API size_t gs_densify_scratch_bytes(int64_t n);
+GS_API int gs_densify_score(const gs_plan *plan, void *ws, const float *d_rgb, const float *d_target, float tau,
+                            const float *d_photo, float *d_s_plus, float *d_r_minus, void *d_scratch, void *stream);
+GS_API int gs_densify_plan(int64_t n, const gs_params *params, const float *d_s_plus, const float *d_r_minus,
+                           const gs_densify_rules *rules, int32_t *d_action, int64_t *d_offsets, void *d_scratch,
+                           int64_t *out_new_n, void *stream);
+GS_API int gs_densify_apply(int64_t n, const gs_params *src, const gs_params *src_m, const gs_params *src_v,
+                            const int32_t *d_action, const int64_t *d_offsets, const float *d_normals,
+                            gs_params *dst, gs_params *dst_m, gs_params *dst_v, void *stream);
+
 /* The same sort for callers that cannot allocate device memory, such as code
  * running inside a CUDA graph capture in global mode (where cudaMalloc is
  * refused), plug-ins whose host framework owns all device memory through its

@@ -34,7 +34,10 @@ EXPORTS = (
     "gs_adam_step_multi", "gs_adam_step_multi_dev", "gs_preprocess_bwd_adam", "gs_sort_scratch_bytes",
     "gs_sort_pairs_u32", "gs_sort_pairs_u32_noalloc",
     "gs_ng_workspace_bytes", "gs_ng_decode_fwd", "gs_ng_decode_bwd", "gs_ng_read_status",
+    "gs_densify_scratch_bytes", "gs_densify_score", "gs_densify_plan", "gs_densify_apply",
 )
+
+GS_DENSIFY_PRUNE, GS_DENSIFY_KEEP, GS_DENSIFY_CLONE, GS_DENSIFY_SPLIT = 0, 1, 2, 3
 
 
 class GsCamera(ctypes.Structure):
@@ -58,6 +61,11 @@ class GsAdamHparams(ctypes.Structure):
     _fields_ = [("lr_means", ctypes.c_float), ("lr_log_scales", ctypes.c_float), ("lr_quats", ctypes.c_float),
                 ("lr_opacity", ctypes.c_float), ("lr_sh_dc", ctypes.c_float), ("lr_sh_rest", ctypes.c_float),
                 ("b1", ctypes.c_float), ("b2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+class GsDensifyRules(ctypes.Structure):
+    _fields_ = [("tau_plus", ctypes.c_float), ("tau_minus", ctypes.c_float), ("min_opacity", ctypes.c_float),
+                ("percent_dense", ctypes.c_float), ("extent", ctypes.c_float), ("k_views", ctypes.c_int32)]
 
 
 class GsStatus(ctypes.Structure):
@@ -117,6 +125,13 @@ _SIGS = {
                                               ctypes.c_float, ctypes.c_float, P, P]),
     "gs_preprocess_bwd_adam": (ctypes.c_int, [P, P, ctypes.POINTER(GsParams), P, ctypes.POINTER(GsParams),
                                               ctypes.POINTER(GsParams), ctypes.POINTER(GsAdamHparams), P, P]),
+    "gs_densify_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
+    "gs_densify_score": (ctypes.c_int, [P, P, P, P, ctypes.c_float, P, P, P, P, P]),
+    "gs_densify_plan": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(GsParams), P, P,
+                                       ctypes.POINTER(GsDensifyRules), P, P, P, ctypes.POINTER(ctypes.c_int64), P]),
+    "gs_densify_apply": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(GsParams), ctypes.POINTER(GsParams),
+                                        ctypes.POINTER(GsParams), P, P, P, ctypes.POINTER(GsParams),
+                                        ctypes.POINTER(GsParams), ctypes.POINTER(GsParams), P]),
     "gs_sort_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "gs_sort_pairs_u32": (ctypes.c_int, [P, P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          P, P]),

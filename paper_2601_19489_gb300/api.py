@@ -240,6 +240,46 @@ def gs_preprocess_bwd_adam(plan: Plan, params: Gaussians, cams, m: Gaussians, v:
                                            _stream(stream)), "gs_preprocess_bwd_adam")
 
 
+# ------------------------------------------------- densification (Sec. 3.3)
+
+def gs_densify_scratch(n: int, device="cuda") -> torch.Tensor:
+    return torch.zeros(int(L.lib().gs_densify_scratch_bytes(int(n))), dtype=torch.uint8, device=device)
+
+
+def gs_densify_score(plan: Plan, rgb, target, tau: float, photo, s_plus, r_minus, scratch, stream=None) -> None:
+    """Add the views' Eq. 4 / Eq. 6 terms to s_plus and r_minus (float32, N);
+    photo: float32 device tensor with one photometric loss per view."""
+    L.check(L.lib().gs_densify_score(plan.handle, plan.ws.data_ptr(), _ptr(rgb), _ptr(target), float(tau),
+                                     _ptr(photo), _ptr(s_plus), _ptr(r_minus), _ptr(scratch, None),
+                                     _stream(stream)), "gs_densify_score")
+
+
+def gs_densify_plan(params: "Gaussians", s_plus, r_minus, rules: dict, action, offsets, scratch,
+                    stream=None) -> int:
+    """Actions (int32, N) and first output slots (int64, N); returns the new
+    Gaussian count (synchronises)."""
+    if action.dtype != torch.int32 or offsets.dtype != torch.int64:
+        raise TypeError("action must be int32 and offsets int64")
+    r = L.GsDensifyRules(float(rules["tau_plus"]), float(rules["tau_minus"]), float(rules["min_opacity"]),
+                         float(rules["percent_dense"]), float(rules["extent"]), int(rules["k_views"]))
+    p = params.struct()
+    out = ctypes.c_int64(0)
+    L.check(L.lib().gs_densify_plan(params.n, ctypes.byref(p), _ptr(s_plus), _ptr(r_minus), ctypes.byref(r),
+                                    _ptr(action, None), _ptr(offsets, None), _ptr(scratch, None), ctypes.byref(out),
+                                    _stream(stream)), "gs_densify_plan")
+    return int(out.value)
+
+
+def gs_densify_apply(src: "Gaussians", src_m: "Gaussians", src_v: "Gaussians", action, offsets, normals,
+                     dst: "Gaussians", dst_m: "Gaussians", dst_v: "Gaussians", stream=None) -> None:
+    """normals: float32 (N, 2, 3) standard normal samples (used by splits)."""
+    a, b, c = src.struct(), src_m.struct(), src_v.struct()
+    d, e, f = dst.struct(), dst_m.struct(), dst_v.struct()
+    L.check(L.lib().gs_densify_apply(src.n, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _ptr(action, None),
+                                     _ptr(offsets, None), _ptr(normals), ctypes.byref(d), ctypes.byref(e),
+                                     ctypes.byref(f), _stream(stream)), "gs_densify_apply")
+
+
 def gs_sort_pairs_u32(keys_in, vals_in, keys_out, vals_out, begin_bit: int, end_bit: int, scratch=None,
                       stream=None) -> None:
     n = keys_in.numel()

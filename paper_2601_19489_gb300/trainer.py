@@ -19,8 +19,8 @@ import ctypes
 import torch
 
 from . import _lib as L
-from .api import (Gaussians, NgParams, Plan, adam_groups_array, adam_hparams, camera_struct, gs_ng_workspace,
-                  ng_children)
+from .api import (Gaussians, NgParams, Plan, adam_groups_array, adam_hparams, camera_struct, gs_densify_apply,
+                  gs_densify_plan, gs_densify_score, gs_densify_scratch, gs_ng_workspace, ng_children)
 
 
 def default_lrs(extent: float = 1.0) -> dict:
@@ -238,6 +238,64 @@ class Trainer:
         L.check(lib.gs_preprocess_bwd(h, ws, ctypes.byref(self._pstruct), c, ctypes.byref(self._gstruct), s),
                 "gs_preprocess_bwd")
         ev(e0 + 5)
+
+    # ------------------------------------------------------------ densify
+    def densify(self, cams, targets, tau: float = 0.3, rules: dict | None = None, seed: int = 0,
+                max_gaussians: int | None = None) -> dict:
+        """One densify-and-prune stage (Sec. 3.3): score every Gaussian on the
+        given views (single-view forwards against their targets, flat planar
+        colour on the device), then clone, split or prune it by the rules and
+        rebuild the parameter set with its Adam moments.  Plans are rebuilt
+        for the new count; captured graphs must be captured again.
+        rules: tau_plus, tau_minus, min_opacity, percent_dense, extent.
+        max_gaussians: if the result would exceed it, no Gaussian is added
+        (pruning still happens).  Returns before / after counts and actions."""
+        import numpy as np
+
+        lib = L.lib()
+        r = {"tau_plus": 5.0, "tau_minus": 0.95, "min_opacity": 0.005, "percent_dense": 0.01, "extent": 4.4}
+        r.update(rules or {})
+        r["k_views"] = len(cams)
+        n = self.params.n
+        dev = self.params.means.device
+        s_plus = torch.zeros(n, device=dev)
+        r_minus = torch.zeros(n, device=dev)
+        scratch = gs_densify_scratch(n, device=dev)
+        photo = torch.zeros(1, device=dev)
+        for cam, tgt in zip(cams, targets):
+            sl = self.forward([cam])
+            s = torch.cuda.current_stream().cuda_stream
+            L.check(lib.gs_loss(sl.plan.handle, sl.rgb.data_ptr(), tgt.data_ptr(), self.lam, None, None, 0.0,
+                                sl.dL_drgb.data_ptr(), None, photo.data_ptr(), sl.scratch.data_ptr(), s), "gs_loss")
+            gs_densify_score(sl.plan, sl.rgb, tgt, tau, photo, s_plus, r_minus, scratch)
+        action = torch.empty(n, dtype=torch.int32, device=dev)
+        offsets = torch.empty(n, dtype=torch.int64, device=dev)
+        new_n = gs_densify_plan(self.params, s_plus, r_minus, r, action, offsets, scratch)
+        if max_gaussians is not None and new_n > max_gaussians:
+            r_capped = dict(r, tau_plus=float("inf"))
+            new_n = gs_densify_plan(self.params, s_plus, r_minus, r_capped, action, offsets, scratch)
+        counts = torch.bincount(action.long(), minlength=4).tolist()
+        if new_n == n and counts[L.GS_DENSIFY_KEEP] == n:
+            return {"n_before": n, "n_after": n, "prune": 0, "clone": 0, "split": 0}
+        rng = np.random.default_rng(seed)
+        normals = torch.from_numpy(rng.standard_normal((n, 2, 3)).astype(np.float32)).to(dev)
+        like = lambda: Gaussians(*(torch.empty((new_n,) + tuple(x.shape[1:]), device=dev)
+                                   for x in self.params.tensors()), self.params.sh_degree)
+        dst, dm, dv = like(), like(), like()
+        gs_densify_apply(self.params, self.m, self.v, action, offsets, normals, dst, dm, dv)
+        self.params, self.m, self.v = dst, dm, dv
+        self.grads = dst.zeros_like()
+        self.cap = max(self.cap, 16 * new_n)
+        sizes = list(self._slots)
+        default = self._default.sizes if self._default is not None else None
+        self._slots = {}
+        for sz in sizes:
+            self._slot(sz)
+        if default is not None:
+            self._default = self._slots[default]
+        self._build_adam()
+        return {"n_before": n, "n_after": new_n, "prune": counts[L.GS_DENSIFY_PRUNE],
+                "clone": counts[L.GS_DENSIFY_CLONE], "split": counts[L.GS_DENSIFY_SPLIT]}
 
     # ------------------------------------------------------------ checkpoint
     def _state_tensors(self) -> dict:
