@@ -71,7 +71,8 @@ def parse_args():
                     help="batched: only the 8-view CUDA-graph step, one line per --batched-n; "
                          "recon60: held-out PSNR after a timed reconstruction")
     ap.add_argument("--recon-budget", type=float, default=60.0, help="seconds of training per method")
-    ap.add_argument("--recon-methods", type=str, default="plain,batched_graph,ng")
+    ap.add_argument("--recon-methods", type=str, default="plain,densify,batched_graph,ng")
+    ap.add_argument("--densify-tau-plus", type=float, default=5.0)
     ap.add_argument("--batched-n", type=str, default="",
                     help="comma-separated Gaussian counts for --workload batched (default: --n)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -582,7 +583,9 @@ def run_recon(args):
         for m in [x for x in args.recon_methods.split(",") if x]:
             results[m] = reconstruct(m, init, [cams[i] for i in tr_ix], [views[i][0] for i in tr_ix],
                                      [views[i][1] for i in tr_ix], [cams[i] for i in ev], [views[i][0] for i in ev],
-                                     budget_s=args.recon_budget, lam=args.lam, device=dev)
+                                     budget_s=args.recon_budget, lam=args.lam,
+                                     densify_rules={"tau_plus": args.densify_tau_plus}, max_gaussians=600000,
+                                     device=dev)
             torch.cuda.empty_cache()
     head = results.get("plain") or next(iter(results.values()))
     line = {"metric": f"held-out PSNR after {args.recon_budget:g} s of training", "value": head["psnr_final"],

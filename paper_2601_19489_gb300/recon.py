@@ -2,8 +2,12 @@
 views for a wall-clock budget and follow the held-out PSNR (the 1-minute
 reconstruction setting of the paper's Sec. 4, without its densification).
 
-Three ways to spend the budget share one schedule:
+Ways to spend the budget, all on one schedule:
   plain          one view per step, eager launches;
+  densify        plain, plus a multi-view score-guided densify-and-prune
+                 stage (Sec. 3.3) after each of the first half of the
+                 evaluation segments (K = 10 random training views; its time
+                 counts as training time);
   batched_graph  8 views per step through the batched plan, launch shapes from
                  the autotuner, every step replayed from a CUDA graph;
   ng             one view per step of the neural-Gaussian model (Sec. 2.3):
@@ -65,7 +69,9 @@ def _ng_start(init, seed: int) -> dict:
 
 def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams, eval_rgb, *,
                 budget_s: float = 60.0, eval_every_s: float = 5.0, lam: float = 0.2, disp_weight: float = 0.1,
-                extent: float = 4.4, batch: int = 8, seed: int = 0, device="cuda") -> dict:
+                extent: float = 4.4, batch: int = 8, seed: int = 0, densify_rules: dict | None = None,
+                densify_tau: float = 0.3, densify_k: int = 10, max_gaussians: int | None = None,
+                device="cuda") -> dict:
     """Run one method for budget_s seconds of training; returns its held-out
     PSNR curve [(seconds trained, PSNR)], steps and views trained."""
     W, H = train_cams[0].width, train_cams[0].height
@@ -87,7 +93,7 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
             best, _ = autotune(params, b_cams[:2], b_rgb[:2], lam=lam, device=device)
             tuning = {k: best[k] for k in ("bucket", "bwd_warps", "bwd_chains")}
             lb = best["load_balanced"]
-        elif method != "plain":
+        elif method not in ("plain", "densify"):
             raise ValueError(method)
         tr = Trainer(params, W, H, lam=lam, disp_weight=disp_weight, lrs=lrs, load_balanced=lb, tuning=tuning,
                      device=device)
@@ -99,6 +105,7 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
     steps = 0
     trained = 0.0
     order = []
+    densify_log = []
     for seg in range(n_seg):
         frac = seg / n_seg
         tr.disp_weight = disp_weight * (1.0 - frac)
@@ -121,6 +128,14 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
                     tr.step(views[i], train_rgb[i], train_disp[i])
                 steps += 1
             torch.cuda.synchronize()
+        if method == "densify" and seg < n_seg // 2:
+            pick = rng.choice(nv, size=min(densify_k, nv), replace=False)
+            rules = dict({"extent": extent}, **(densify_rules or {}))
+            info = tr.densify([train_cams[i] for i in pick], [train_rgb[i] for i in pick], tau=densify_tau,
+                              rules=rules, seed=seed + seg, max_gaussians=max_gaussians)
+            tr.ensure_capacity(views, slack=2.0)
+            densify_log.append(info)
+            torch.cuda.synchronize()
         trained += time.perf_counter() - t0
         st = tr.slot_for(views[0]).plan.status()
         if st["error"]:
@@ -132,4 +147,5 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
     per_step = batch if method == "batched_graph" else 1
     return {"method": method, "curve": curve, "psnr_final": curve[-1][1], "psnr_start": curve[0][1],
             "steps": steps, "views": steps * per_step, "seconds": trained,
-            "views_per_s": steps * per_step / trained}
+            "views_per_s": steps * per_step / trained, "gaussians_final": tr.params.n,
+            "densify": densify_log}

@@ -8,7 +8,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("method", ["plain", "batched_graph", "ng"])
+@pytest.mark.parametrize("method", ["plain", "densify", "batched_graph", "ng"])
 def test_short_reconstruction_improves_heldout_psnr(gs, method):
     from paper_2601_19489_gb300 import api
     from paper_2601_19489_gb300.recon import reconstruct, render_views
