@@ -67,7 +67,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched CUDA-graph measurement")
     ap.add_argument("--batched-steps", type=int, default=60)
     ap.add_argument("--no-ng", action="store_true", help="skip the neural-Gaussian step measurement")
-    ap.add_argument("--workload", choices=("explicit", "batched", "recon60"), default="explicit",
+    ap.add_argument("--workload", choices=("explicit", "batched", "recon60", "ablation"), default="explicit",
                     help="batched: only the 8-view CUDA-graph step, one line per --batched-n; "
                          "recon60: held-out PSNR after a timed reconstruction")
     ap.add_argument("--recon-budget", type=float, default=60.0, help="seconds of training per method")
@@ -598,8 +598,74 @@ def run_recon(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ Tab. 1 ablation
+
+def run_ablation(args, steps: int = 200, warmup: int = 10):
+    """The paper's speed ablation (Tab. 1) on the headline workload: per-pixel
+    backward + 3-sigma tile box + sequential key write (the classic step),
+    then the per-Gaussian backward (B), then the SnugBox (F) with the
+    sequential (Sq) and the load-balanced (LB) key write.  Train steps/s and
+    the time 30,000 iterations would take."""
+    import torch
+
+    import synth
+    from paper_2601_19489_gb300 import _lib as L
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import Trainer
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    L.load()
+    scene, cams = workload(args)
+    targets = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1)).to(dev)
+               for v in range(len(cams))]
+    shape = {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1}
+    configs = [("3DGS (per-pixel backward, 3-sigma box, Sq)", False, {"bwd_per_pixel": 1, "bbox_3sigma": 1}),
+               ("w/ B", False, {**shape, "bbox_3sigma": 1}),
+               ("w/ B & F & Sq", False, dict(shape)),
+               ("w/ B & F & LB", True, dict(shape)),
+               ("w/ F & LB, per-pixel backward (not in Tab. 1)", True, {"bwd_per_pixel": 1})]
+    rows = []
+    with ClockSampler(0) as clk:
+        for name, lb, tuning in configs:
+            tr = Trainer(api.Gaussians.from_scene(scene, device=dev), args.width, args.height, lam=args.lam,
+                         load_balanced=lb, tuning=tuning, device=dev)
+            tr.ensure_capacity(cams)
+            for s in range(warmup):
+                tr.step(cams[s % len(cams)], targets[s % len(cams)])
+            n_st = len(tr.STAGES)
+            evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_st + 1)] for _ in range(steps)]
+            torch.cuda.synchronize()
+            for s in range(steps):
+                v = (warmup + s) % len(cams)
+                tr.step(cams[v], targets[v], events=evs[s])
+            torch.cuda.synchronize()
+            st = tr.plan.status()
+            if st["rc"] != 0:
+                raise RuntimeError(f"device status in {name}: {st}")
+            ms = float(np.mean([evs[s][0].elapsed_time(evs[s][n_st]) for s in range(steps)]))
+            stage = {k: float(np.mean([evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(steps)]))
+                     for i, k in enumerate(tr.STAGES)}
+            rows.append({"config": name, "steps_per_s": 1e3 / ms, "ms_per_step": ms,
+                         "seconds_per_30k_iterations": 30.0 * ms, "instances": st["n_instances"],
+                         "stages_ms": stage})
+            del tr
+            torch.cuda.empty_cache()
+    base = rows[0]["ms_per_step"]
+    for r in rows:
+        r["speedup_vs_3dgs"] = base / r["ms_per_step"]
+    line = {"metric": "train steps/s, Tab. 1 ablation", "value": rows[3]["steps_per_s"], "unit": "steps/s",
+            "n_gpus": 1, "steps": steps, "warmup": warmup, "higher_is_better": True, "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": config_of(args), "clocks": clk.summary(),
+            "ablation": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == "ablation":
+        run_ablation(args)
+        return
     if args.workload == "batched":
         run_batched_only(args)
         return

@@ -128,6 +128,19 @@ typedef struct {
     int32_t bucket;
     int32_t bwd_warps;
     int32_t bwd_chains;
+    /* Ablation switches (Sec. 4, Tab. 1), both 0 by default:
+     *   bbox_3sigma    bin each Gaussian into the tiles holding the pixel
+     *                  centres of the classic square of half-width
+     *                  ceil(3 sqrt(largest eigenvalue of Sigma')) instead of
+     *                  the SnugBox with its per-column test (Sec. 2.1, "F").
+     *                  Not result-exact: a Gaussian with opacity above ~0.35 can
+     *                  reach alpha >= 1/255 outside that box.
+     *   bwd_per_pixel  the classic per-pixel backward (a thread per pixel walks
+     *                  its list back to front; warp sums of each splat's
+     *                  gradient, then atomics) instead of the per-Gaussian
+     *                  backward of Sec. 2.2 ("B"); no checkpoints are written. */
+    int32_t bbox_3sigma;
+    int32_t bwd_per_pixel;
 } gs_tuning;
 GS_API gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n_views, const int32_t *h_widths,
                                      const int32_t *h_heights, int64_t inst_capacity, const gs_tuning *tuning);

@@ -93,14 +93,17 @@ class Plan:
     def __init__(self, n: int, sh_degree: int, sizes, inst_capacity: int, device="cuda",
                  tuning: dict | None = None):
         """tuning: optional {"bucket": 32 | 64, "bwd_warps": 2 | 4 | 8,
-        "bwd_chains": 0 | 1 | 2}."""
+        "bwd_chains": 0 | 1 | 2, "bbox_3sigma": 0 | 1, "bwd_per_pixel": 0 | 1}
+        (the last two are the Tab. 1 ablation switches)."""
         lib = L.lib()
         self.sizes = [(int(w), int(h)) for (w, h) in sizes]
         V = len(self.sizes)
         ws_ = (ctypes.c_int32 * V)(*[w for w, _ in self.sizes])
         hs_ = (ctypes.c_int32 * V)(*[h for _, h in self.sizes])
-        self.tuning = {"bucket": 32, "bwd_warps": 4, "bwd_chains": 0, **(tuning or {})}
-        tu = L.GsTuning(int(self.tuning["bucket"]), int(self.tuning["bwd_warps"]), int(self.tuning["bwd_chains"]))
+        self.tuning = {"bucket": 32, "bwd_warps": 4, "bwd_chains": 0, "bbox_3sigma": 0, "bwd_per_pixel": 0,
+                       **(tuning or {})}
+        tu = L.GsTuning(*(int(self.tuning[k]) for k in ("bucket", "bwd_warps", "bwd_chains", "bbox_3sigma",
+                                                        "bwd_per_pixel")))
         self.handle = lib.gs_plan_create_tuned(int(n), int(sh_degree), V, ws_, hs_, int(inst_capacity),
                                                ctypes.byref(tu))
         if not self.handle:

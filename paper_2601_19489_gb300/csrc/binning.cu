@@ -160,7 +160,7 @@ k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ or
              const uint32_t *__restrict__ touched, const float4 *__restrict__ rec,
              const float2 *__restrict__ bin, const uint2 *__restrict__ rects,
              const unsigned long long *__restrict__ block_offs, int64_t n, int64_t capacity,
-             uint32_t *__restrict__ inst_tile, uint32_t *__restrict__ inst_item, StatusDev *st) {
+             uint32_t *__restrict__ inst_tile, uint32_t *__restrict__ inst_item, StatusDev *st, int box3) {
     __shared__ uint32_t tmp[kWriteRound / 32];
     int64_t beg, end;
     chunk_of(n, &beg, &end);
@@ -183,16 +183,16 @@ k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ or
                 const ViewDev &cam = views.v[v];
                 const float4 r0v = rec[3 * (size_t)item];
                 const float2 bv = bin[item];
-                BinGeom bg;
-                bin_geom(r0v.x, r0v.y, r0v.z, r0v.w, rec[3 * (size_t)item + 1].x, bv.y, bv.x, bg);
+                BinGeom bg{};
+                if (!box3) bin_geom(r0v.x, r0v.y, r0v.z, r0v.w, rec[3 * (size_t)item + 1].x, bv.y, bv.x, bg);
                 int tx0, ty0, tx1, ty1;
                 unpack_rect(rects[item], &tx0, &ty0, &tx1, &ty1);
                 uint32_t w = 0;
                 for (int tx = tx0; tx < tx1; ++tx) {
                     float xa, xb;
                     column_span(tx, (float)cam.W, &xa, &xb);
-                    int lo, hi;
-                    if (!column_rows(bg, xa, xb, (float)cam.H, ty0, ty1, &lo, &hi)) continue;
+                    int lo = ty0, hi = ty1 - 1;  // the whole box column (3-sigma box)
+                    if (!box3 && !column_rows(bg, xa, xb, (float)cam.H, ty0, ty1, &lo, &hi)) continue;
                     for (int ty = lo; ty <= hi; ++ty, ++w)
                         if (w < cnt) sink.put(off + w, (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx), item);
                 }
@@ -216,7 +216,7 @@ k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ or
                 const ViewDev &cam = views.v[v];
                 const float4 r0v = rec[3 * (size_t)item];
                 const float2 bv = bin[item];
-                bin_geom(r0v.x, r0v.y, r0v.z, r0v.w, rec[3 * (size_t)item + 1].x, bv.y, bv.x, my);
+                if (!box3) bin_geom(r0v.x, r0v.y, r0v.z, r0v.w, rec[3 * (size_t)item + 1].x, bv.y, bv.x, my);
                 unpack_rect(rects[item], &mtx0, &mty0, &mtx1, &mty1);
                 mtoff = cam.tile_off;
                 mtiles_x = cam.tiles_x;
@@ -267,9 +267,15 @@ k_write_keys(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ or
                 const int tx = tx0 + (int)(f - cp_j);
                 int lo = 0, hi = -1, rows = 0;
                 if (has) {
-                    float xa, xb;
-                    column_span(tx, fW, &xa, &xb);
-                    rows = column_rows(bg, xa, xb, fH, ty0, ty1, &lo, &hi);
+                    if (box3) {  // the whole box column (3-sigma box)
+                        lo = ty0;
+                        hi = ty1 - 1;
+                        rows = ty1 - ty0;
+                    } else {
+                        float xa, xb;
+                        column_span(tx, fW, &xa, &xb);
+                        rows = column_rows(bg, xa, xb, fH, ty0, ty1, &lo, &hi);
+                    }
                 }
                 // segmented exclusive scan of rows over the chunk (segments =
                 // runs of equal owner)
@@ -406,12 +412,12 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
         k_write_keys<true><<<kBinBlocks, kWriteRound, 0, s>>>(
             vd, plan->n, order, touched, ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin),
             ws_at<uint2>(ws, plan->o_rect),
-            block_offs, VN, plan->inst_cap, ik0, iv0, st);
+            block_offs, VN, plan->inst_cap, ik0, iv0, st, plan->bbox_3sigma);
     else
         k_write_keys<false><<<kBinBlocks, kWriteRound, 0, s>>>(
             vd, plan->n, order, touched, ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin),
             ws_at<uint2>(ws, plan->o_rect),
-            block_offs, VN, plan->inst_cap, ik0, iv0, st);
+            block_offs, VN, plan->inst_cap, ik0, iv0, st, plan->bbox_3sigma);
     rc = launch_error();
     if (rc) return rc;
 

@@ -82,10 +82,13 @@ struct gs_plan {
     int32_t bucket, bucket_shift;  // splats per checkpoint bucket (32 or 64) and its log2
     int32_t bwd_warps;             // warps per CTA of the per-Gaussian backward
     int32_t two_chain_min;         // live pixels from which a backward bucket walks two chains
+    int32_t bbox_3sigma;           // ablation: classic 3-sigma tile box
+    int32_t bwd_per_pixel;         // ablation: classic per-pixel backward
     // offsets
     size_t o_status, o_rec, o_touched, o_rect, o_dkey[2], o_dval[2];
     size_t o_ikey[2], o_ival[2], o_ranges, o_tile_maxc, o_bucket_off, o_ncontrib;
     size_t o_ckpt, o_grad2d, o_sort_scratch, o_block_sums, o_bin;
+    size_t o_final;  // per-pixel final T, then the background (per-pixel backward only)
     size_t sort_scratch_bytes;
     size_t bytes;
     int inst_final;   // which ping-pong buffer holds the sorted instances

@@ -105,6 +105,8 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     p->bucket_shift = bucket == 64 ? 6 : 5;
     p->bwd_warps = bwd_warps;
     p->two_chain_min = chains == 2 ? 0 : chains == 1 ? (1 << 30) : kTwoChainAuto;
+    p->bbox_3sigma = tuning && tuning->bbox_3sigma ? 1 : 0;
+    p->bwd_per_pixel = tuning && tuning->bwd_per_pixel ? 1 : 0;
     p->bucket_cap = inst_capacity / bucket + tiles + 1;
     p->sort_scratch_bytes = sort_scratch_bytes();
 
@@ -132,6 +134,7 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     p->o_tile_maxc = take(T * sizeof(uint32_t));
     p->o_bucket_off = take((T + 1) * sizeof(uint32_t));
     p->o_ncontrib = take((size_t)pix * sizeof(uint32_t));
+    p->o_final = take(p->bwd_per_pixel ? ((size_t)pix + 4) * sizeof(float) : 16);
     p->o_ckpt = take((size_t)p->bucket_cap * kCkptCh * kTilePix * sizeof(float));
     p->o_grad2d = take(VN * 3 * sizeof(float4));
     p->o_sort_scratch = take(p->sort_scratch_bytes);

@@ -224,7 +224,7 @@ k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
              const float *__restrict__ log_scales, const float4 *__restrict__ quats,
              const float *__restrict__ logits, const float *__restrict__ sh, float4 *__restrict__ rec,
              float2 *__restrict__ bin, uint32_t *__restrict__ touched, uint2 *__restrict__ rects,
-             uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval) {
+             uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval, int box3) {
     constexpr int K = (D + 1) * (D + 1);
     const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= (int64_t)views.V * n) return;
@@ -284,7 +284,16 @@ k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
 
     uint32_t count = 0;
     int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
-    if (t > 0.0f) {
+    if (box3) {
+        // classic tile box: square of radius ceil(3 sqrt(largest eigenvalue))
+        const float mid = 0.5f * (P.Sxx + P.Syy);
+        const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - (P.Sxx * P.Syy - P.Sxy * P.Sxy)));
+        const float rad = ceilf(3.0f * sqrtf(lam));
+        // the tiles holding the pixel centres of the square (the same
+        // pixel-centre rule as the SnugBox's rectangle)
+        if (snug_rect(mx, my, rad, rad, (float)cam.W, (float)cam.H, &tx0, &ty0, &tx1, &ty1))
+            count = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
+    } else if (t > 0.0f) {
         BinGeom bg;
         bin_geom(mx, my, A, B, C, detc, tb, bg);
         if (snug_rect(mx, my, bg.rx, bg.ry, (float)cam.W, (float)cam.H, &tx0, &ty0, &tx1, &ty1)) {
@@ -746,7 +755,8 @@ static void launch_preprocess(const gs_plan *plan, void *ws, const gs_params *pr
     k_preprocess<D><<<blocks, 256, 0, s>>>(
         vd, plan->n, pr->means, pr->log_scales, (const float4 *)pr->quats, pr->opacity_logits, pr->sh,
         ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin), ws_at<uint32_t>(ws, plan->o_touched),
-        ws_at<uint2>(ws, plan->o_rect), ws_at<uint32_t>(ws, plan->o_dkey[0]), ws_at<uint32_t>(ws, plan->o_dval[0]));
+        ws_at<uint2>(ws, plan->o_rect), ws_at<uint32_t>(ws, plan->o_dkey[0]), ws_at<uint32_t>(ws, plan->o_dval[0]),
+        plan->bbox_3sigma);
 }
 
 template <int D, bool kAdam>

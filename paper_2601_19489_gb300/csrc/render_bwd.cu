@@ -253,6 +253,120 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
     }
 }
 
+// ------------------------------------------------ per-pixel backward (ablation)
+// The classic formulation the per-Gaussian backward replaces (Sec. 2.2): a CTA
+// per tile, a thread per pixel walking its blended list back to front from
+// its last contributor.  With T_final and R = T_final (g . bg) (the part of
+// the pixel's value behind every splat), each blended splat k gives
+//   T_k = T_{k+1} / (1 - alpha_k),  dL/dalpha_k = T_k gdot_k - R / (1 - alpha_k),
+// then R += alpha_k T_k gdot_k.  The lanes of a warp visit the same splat at
+// the same time, so its 10 sums are reduced over the warp before one lane's
+// atomics.
+__device__ __forceinline__ float warp_sum10(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kTilePix)
+k_render_bwd_pixel(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ inst_item,
+                   const float4 *__restrict__ rec, const uint32_t *__restrict__ tile_maxc,
+                   const uint32_t *__restrict__ n_contrib, const float *__restrict__ final_T,
+                   const float *__restrict__ dL_drgb, const float *__restrict__ dL_ddisp,
+                   float4 *__restrict__ grad2d) {
+    __shared__ float4 s_r0[kTilePix], s_r1[kTilePix], s_r2[kTilePix];
+    __shared__ uint32_t s_it[kTilePix];
+    const int t = blockIdx.x;
+    int v = 0;
+    while (v + 1 < views.V && t >= views.v[v + 1].tile_off) ++v;
+    const ViewDev &cam = views.v[v];
+    const int lt = t - cam.tile_off;
+    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int ix = tx * kTile + (tid & (kTile - 1)), iy = ty * kTile + (tid >> 4);
+    const bool inside = ix < cam.W && iy < cam.H;
+    const float px = (float)(tid & (kTile - 1)) + 0.5f, py = (float)(tid >> 4) + 0.5f;
+    const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
+    const uint2 range = ranges[t];
+    const uint32_t maxc = min(tile_maxc[t], range.y - range.x);
+    if (maxc == 0) return;  // uniform
+    const ViewDev &lv = views.v[views.V - 1];
+    const float *bg = final_T + lv.pix_off + (int64_t)lv.W * lv.H;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t last = 0;
+    float T = 1.0f, R = 0.0f;
+    if (inside) {
+        const size_t npix = (size_t)cam.W * cam.H, base = (size_t)cam.pix_off, pix = (size_t)iy * cam.W + ix;
+        g = make_float4(dL_drgb[3 * base + pix], dL_drgb[3 * base + npix + pix], dL_drgb[3 * base + 2 * npix + pix],
+                        dL_ddisp ? dL_ddisp[base + pix] : 0.0f);
+        last = n_contrib[base + pix];
+        T = final_T[base + pix];
+        R = T * (g.x * bg[0] + g.y * bg[1] + g.z * bg[2]);
+    }
+    for (int b0 = (int)((maxc - 1) / kTilePix) * kTilePix; b0 >= 0; b0 -= kTilePix) {
+        __syncthreads();  // the previous batch is no longer read
+        if (b0 + tid < (int)maxc) {
+            const uint32_t it = inst_item[range.x + b0 + tid];
+            float4 r0 = rec[3 * (size_t)it];
+            const float4 r1 = rec[3 * (size_t)it + 1], r2 = rec[3 * (size_t)it + 2];
+            const float2 mm = tile_local_mean(r0, r1.w, r2.w, x0, y0);
+            r0.x = mm.x;
+            r0.y = mm.y;
+            s_r0[tid] = r0;
+            s_r1[tid] = r1;
+            s_r2[tid] = r2;
+            s_it[tid] = it;
+        }
+        __syncthreads();
+        for (int j = min(kTilePix, (int)maxc - b0) - 1; j >= 0; --j) {
+            const uint32_t k = (uint32_t)(b0 + j);
+            SplatGrad acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool hit = false;
+            const float4 r0 = s_r0[j], r1 = s_r1[j];
+            if (k < last) {
+                PairEval e;
+                eval_pair(r0, r1, px, py, e);
+                if (!(e.power2 > 0.0f) && !(e.alpha < kAlphaMin)) {
+                    hit = true;
+                    const float4 r2 = s_r2[j];
+                    T = __fdividef(T, 1.0f - e.alpha);  // transmittance in front of splat k
+                    const float w = e.alpha * T;
+                    const float gdot = g.x * r2.x + g.y * r2.y + g.z * r2.z + g.w * r1.z;
+                    acc.r = w * g.x;
+                    acc.g = w * g.y;
+                    acc.b = w * g.z;
+                    acc.iz = w * g.w;
+                    if (e.raw <= kAlphaMax) {
+                        const float dL_da = T * gdot - __fdividef(R, 1.0f - e.alpha);
+                        const float dpw = dL_da * e.raw;
+                        acc.pw = dpw;
+                        acc.sx = dpw * e.dx;
+                        acc.sy = dpw * e.dy;
+                        acc.xx = acc.sx * e.dx;
+                        acc.xy = acc.sx * e.dy;
+                        acc.yy = acc.sy * e.dy;
+                    }
+                    R += w * gdot;
+                }
+            }
+            if (__ballot_sync(0xffffffffu, hit) == 0u) continue;  // uniform over the warp
+            const float sx = warp_sum10(acc.sx), sy = warp_sum10(acc.sy), xx = warp_sum10(acc.xx);
+            const float xy = warp_sum10(acc.xy), yy = warp_sum10(acc.yy), pw = warp_sum10(acc.pw);
+            const float cr = warp_sum10(acc.r), cg = warp_sum10(acc.g), cb = warp_sum10(acc.b);
+            const float iz = warp_sum10(acc.iz);
+            if (lane == 0) {
+                const float inv_o = fast_exp2(-r1.y);
+                float4 *gp = grad2d + 3 * (size_t)s_it[j];
+                const float gmx = (r0.z * sx + r0.w * sy) * kInvH;
+                const float gmy = (r0.w * sx + r1.x * sy) * kInvH;
+                atomicAdd(gp, make_float4(gmx, gmy, -0.5f * xx, -xy));
+                atomicAdd(gp + 1, make_float4(-0.5f * yy, pw * inv_o, iz, 0.0f));
+                atomicAdd(gp + 2, make_float4(cr, cg, cb, 0.0f));
+            }
+        }
+    }
+}
+
 template <int kWarps, int kSub>
 static int launch_bwd(const gs_plan *plan, void *ws, const float *d_rgb, const float *d_disp,
                       const float *d_dL_drgb, const float *d_dL_ddisp, float4 *g2d, cudaStream_t s) {
@@ -289,6 +403,14 @@ extern "C" int gs_render_bwd_blend(const gs_plan *plan, void *ws, const float *d
     float4 *g2d = ws_at<float4>(ws, plan->o_grad2d);
     int rc = check_cuda(cudaMemsetAsync(g2d, 0, (size_t)plan->VN * 3 * sizeof(float4), s));
     if (rc) return rc;
+    if (plan->bwd_per_pixel) {
+        const ViewsDev vd = make_views(plan, nullptr);
+        k_render_bwd_pixel<<<plan->total_tiles, kTilePix, 0, s>>>(
+            vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
+            ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_tile_maxc),
+            ws_at<uint32_t>(ws, plan->o_ncontrib), ws_at<float>(ws, plan->o_final), d_dL_drgb, d_dL_ddisp, g2d);
+        return launch_error();
+    }
     const bool two = plan->bucket == 64;
     switch (plan->bwd_warps) {
         case 2: return two ? launch_bwd<2, 2>(plan, ws, d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, s)

@@ -27,7 +27,7 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
              const float4 *__restrict__ rec, const uint32_t *__restrict__ bucket_off, int bucket_shift, float bg_r,
              float bg_g, float bg_b, float *__restrict__ out_rgb, float *__restrict__ out_disp,
              float *__restrict__ out_T, uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ tile_maxc,
-             float *__restrict__ ckpt) {
+             float *__restrict__ ckpt, float *__restrict__ final_T) {
     __shared__ float4 s_r0[kTilePix];
     __shared__ float4 s_r1[kTilePix];
     __shared__ float4 s_r2[kTilePix];
@@ -46,7 +46,11 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
     const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
     const uint2 range = ranges[t];
     const int n = (int)(range.y - range.x);
-    float *ck = ckpt + (size_t)bucket_off[t] * (kCkptCh * kTilePix) + tid;
+    float *ck = ckpt ? ckpt + (size_t)bucket_off[t] * (kCkptCh * kTilePix) + tid : nullptr;
+    if (final_T && t == 0 && tid < 3) {  // the background, after the last pixel
+        const ViewDev &lv = views.v[views.V - 1];
+        final_T[lv.pix_off + (int64_t)lv.W * lv.H + tid] = tid == 0 ? bg_r : (tid == 1 ? bg_g : bg_b);
+    }
     if (tid == 0) s_maxc = 0;
 
     float T = 1.0f, Cr = 0.f, Cg = 0.f, Cb = 0.f, D = 0.f;
@@ -70,7 +74,7 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
         const int bucket = 1 << bucket_shift;
         for (int j0 = 0; j0 < cnt; j0 += bucket) {
             if (__all_sync(0xffffffffu, done)) break;
-            if (!done) {  // checkpoint before list position b0 + j0
+            if (ckpt && !done) {  // checkpoint before list position b0 + j0
                 float *c = ck + (size_t)((b0 + j0) >> bucket_shift) * (kCkptCh * kTilePix);
                 c[0] = T;
                 c[kTilePix] = Cr;
@@ -110,6 +114,7 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
         out_disp[base + pix] = D;
         out_T[base + pix] = T;
         n_contrib[base + pix] = last;
+        if (final_T) final_T[base + pix] = T;
     }
     // tile maximum of n_contrib: buckets at or beyond it have no work
     uint32_t m = last;
@@ -135,6 +140,7 @@ extern "C" int gs_render_fwd(const gs_plan *plan, void *ws, const float *bg, flo
         ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off), plan->bucket_shift, bg[0],
         bg[1], bg[2],
         out_rgb, out_disp, out_T, ws_at<uint32_t>(ws, plan->o_ncontrib),
-        ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt));
+        ws_at<uint32_t>(ws, plan->o_tile_maxc), plan->bwd_per_pixel ? nullptr : ws_at<float>(ws, plan->o_ckpt),
+        plan->bwd_per_pixel ? ws_at<float>(ws, plan->o_final) : nullptr);
     return launch_error();
 }

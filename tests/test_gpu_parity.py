@@ -149,7 +149,8 @@ def test_binning_lists_match_oracle_and_lb_equals_sq(gs):
 # --------------------------------------------------------------- forward
 
 TUNINGS = [None, {"bucket": 64, "bwd_warps": 2, "bwd_chains": 2}, {"bucket": 64, "bwd_warps": 8, "bwd_chains": 1},
-           {"bucket": 32, "bwd_warps": 8, "bwd_chains": 2}, {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1}]
+           {"bucket": 32, "bwd_warps": 8, "bwd_chains": 2}, {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1},
+           {"bwd_per_pixel": 1}]
 
 
 @pytest.mark.parametrize("which", ["c1", "clustered_ragged"])
@@ -389,3 +390,26 @@ def test_single_gaussian_and_nan_parameters_do_not_hang(gs):
     scene2.log_scales[7] = np.nan
     plan2, params2, rgb2, disp2, T2 = _run_forward(gs, scene2, [cam])
     assert plan2.status()["rc"] == 0
+
+
+def test_three_sigma_box_renders_like_the_snugbox_when_it_covers_the_level_set(gs):
+    """The Tab. 1 ablation's classic 3-sigma tile box: with every opacity
+    below e^4.5 / 255 (0.353) the box covers the alpha >= 1/255 level set, so
+    the blended sequence of every pixel, hence the image, is the SnugBox's
+    (bit for bit); the box touches more tiles."""
+    from paper_2601_19489_gb300 import api
+
+    base = synth.scene_clustered(20000, seed=13, sh_degree=1)
+    rng = np.random.default_rng(13)
+    o = rng.uniform(0.02, 0.34, base.n)
+    scene = synth.Scene(base.means, base.log_scales, base.quats, np.log(o / (1 - o)).astype(np.float32),
+                        base.sh, 1)
+    cam = synth.ring_cameras(4, 250, 140)[3]
+    outs = []
+    for tuning in (None, {"bbox_3sigma": 1}):
+        plan, params, rgb, disp, T = _run_forward(gs, scene, [cam], tuning=tuning)
+        outs.append((to_np(rgb), to_np(disp), to_np(T), plan.status()["n_instances"]))
+    np.testing.assert_array_equal(outs[1][0], outs[0][0])
+    np.testing.assert_array_equal(outs[1][1], outs[0][1])
+    np.testing.assert_array_equal(outs[1][2], outs[0][2])
+    assert outs[1][3] > outs[0][3]
