@@ -108,15 +108,26 @@ def params_from_scene(scene, requires_grad: bool = False) -> dict:
     return p
 
 
-def project(params: dict, cam, sh_degree: int) -> dict:
+def project(params: dict, cam, sh_degree: int, R: torch.Tensor | None = None,
+            t: torch.Tensor | None = None) -> dict:
     """Per-Gaussian projected quantities in float64 (differentiable).
+
+    R, t: the world->camera transform to use instead of the camera's own,
+    either one (3, 3) / (3,) for all Gaussians or one per Gaussian (N, 3, 3) /
+    (N, 3) (the pose gradient of Sec. 2.5 differentiates through these).
 
     Returns a dict with mean2d (N, 2), conic (N, 3) = (a, b, c), cov2d (N, 3)
     = (Sxx, Sxy, Syy) after dilation, opacity (N,), rgb (N, 3), depth (N,),
     level t (N,), valid (N,) bool, rgb_clamped (N, 3) bool, J (N, 2, 3)."""
-    R, tr = camera_tensors(cam)
+    if R is None:
+        R, tr = camera_tensors(cam)
+    else:
+        tr = t
     means = params["means"]
-    pc = means @ R.T + tr
+    if R.dim() == 3:
+        pc = torch.einsum("nij,nj->ni", R, means) + tr
+    else:
+        pc = means @ R.T + tr
     x, y, z = pc.unbind(-1)
     near = getattr(cam, "near", NEAR_DEFAULT)
     valid = z > near
@@ -149,7 +160,10 @@ def project(params: dict, cam, sh_degree: int) -> dict:
     opacity = torch.sigmoid(params["opacity_logits"])
     level = 2.0 * torch.log(255.0 * opacity)
 
-    cam_centre = -(R.T @ tr)
+    if R.dim() == 3:
+        cam_centre = -torch.einsum("nji,nj->ni", R, tr)
+    else:
+        cam_centre = -(R.T @ tr)
     dvec = means - cam_centre
     dirs = dvec / torch.linalg.norm(dvec, dim=-1, keepdim=True)
     basis = sh_basis(sh_degree, dirs)  # (N, K)

@@ -73,6 +73,7 @@ def forward_backward(scene, cam, target, bg=(0.0, 0.0, 0.0), lam: float = 0.2,
     g2d = render.render_bwd(rec, bg, win, g_rgb, g_disp, n_threads=n_threads)
     t3 = time.perf_counter()
     grads = preprocess.preprocess_backward(scene, cam, g2d)
+    f["grad2d"] = g2d
     t4 = time.perf_counter()
     if timings is not None:
         timings.update(preprocess=t1 - t0, render_fwd_loss=t2 - t1, render_bwd=t3 - t2,
