@@ -417,6 +417,53 @@ GS_API int gs_densify_apply(int64_t n, const gs_params *src, const gs_params *sr
                             const int32_t *d_action, const int64_t *d_offsets, const float *d_normals,
                             gs_params *dst, gs_params *dst_m, gs_params *dst_v, void *stream);
 
+/* ------------------------------ global pose refinement (Sec. 2.5)
+ * One learnable correction (Delta_R, Delta_t) shared by every camera of every
+ * plan it is attached to (training and evaluation views alike), applied on
+ * the camera side: a camera with world -> camera transform [W | t] is used as
+ * [Delta_R W | Delta_R t + Delta_t].  The loss gradient with respect to a
+ * left increment xi = (omega, tau) of the correction (the camera then seeing
+ * exp([omega]_x) (Delta_R (W p + t) + Delta_t) + tau: omega an axis-angle
+ * rotation about the camera centre, tau a translation, both in the camera
+ * frame) accumulates over every step; gs_pose_step turns the accumulated sum
+ * into one Adam increment and folds it into the correction (the paper does
+ * this every 300 iterations).
+ *
+ * The whole state is one device buffer of GS_POSE_STATE_DOUBLES doubles,
+ * owned by the caller, 16-byte aligned:
+ *   [0..8]    Delta_R, row-major          [9..11]   Delta_t
+ *   [12..17]  Adam first moments of xi    [18..23]  Adam second moments
+ *   [24]      Adam step count             [25..31]  unused
+ *   [32 + 8 s + k], s < GS_POSE_SLOTS, k < 6: partial sums of dL/d(omega,
+ *             tau); the gradient is their sum over s (spread over slots so
+ *             that concurrent atomic adds do not queue on one address).
+ *
+ * gs_pose_init: the identity correction, zero moments, step and sums.
+ * gs_plan_set_pose: attach a state to a plan (NULL detaches).  While
+ *   attached, gs_preprocess composes the correction with each camera (in
+ *   double precision, the corrected transform rounded once to float32, the
+ *   camera centre -R^T t computed from the rounded values) into the
+ *   workspace, and the preprocess backward (gs_preprocess_bwd,
+ *   gs_preprocess_bwd_adam, gs_render_bwd) uses those cameras and adds its
+ *   views' dL/d(omega, tau) into the state's sums.  The backward therefore
+ *   uses the correction of the step's gs_preprocess.  The plan keeps the
+ *   pointer only; the state must outlive its use.  GS_ERR_ARG for a
+ *   misaligned state.
+ * gs_pose_step: sum the slots into g, then in double precision: t += 1;
+ *   m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2;
+ *   xi = -lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps) with lr = lr_rot
+ *   for omega and lr_trans for tau; Delta_R <- exp([omega]_x) Delta_R,
+ *   Delta_t <- exp([omega]_x) Delta_t + tau; the sums restart from zero. */
+#define GS_POSE_SLOTS 256
+#define GS_POSE_STATE_DOUBLES (32 + 8 * GS_POSE_SLOTS)
+typedef struct {
+    double lr_rot, lr_trans; /* Adam rates of omega (radians) and tau (scene units) */
+    double b1, b2, eps;      /* b1, b2 in [0.5, 1), eps >= 0 */
+} gs_pose_hparams;
+GS_API int gs_pose_init(double *d_state, void *stream);
+GS_API int gs_plan_set_pose(gs_plan *plan, double *d_state);
+GS_API int gs_pose_step(double *d_state, const gs_pose_hparams *hp, void *stream);
+
 /* The same sort for callers that cannot allocate device memory, such as code
  * running inside a CUDA graph capture in global mode (where cudaMalloc is
  * refused), plug-ins whose host framework owns all device memory through its

@@ -35,9 +35,13 @@ EXPORTS = (
     "gs_sort_pairs_u32", "gs_sort_pairs_u32_noalloc",
     "gs_ng_workspace_bytes", "gs_ng_decode_fwd", "gs_ng_decode_bwd", "gs_ng_read_status",
     "gs_densify_scratch_bytes", "gs_densify_score", "gs_densify_plan", "gs_densify_apply",
+    "gs_pose_init", "gs_plan_set_pose", "gs_pose_step",
 )
 
 GS_DENSIFY_PRUNE, GS_DENSIFY_KEEP, GS_DENSIFY_CLONE, GS_DENSIFY_SPLIT = 0, 1, 2, 3
+
+GS_POSE_SLOTS = 256
+GS_POSE_STATE_DOUBLES = 32 + 8 * GS_POSE_SLOTS
 
 
 class GsCamera(ctypes.Structure):
@@ -67,6 +71,11 @@ class GsAdamHparams(ctypes.Structure):
 class GsDensifyRules(ctypes.Structure):
     _fields_ = [("tau_plus", ctypes.c_float), ("tau_minus", ctypes.c_float), ("min_opacity", ctypes.c_float),
                 ("percent_dense", ctypes.c_float), ("extent", ctypes.c_float), ("k_views", ctypes.c_int32)]
+
+
+class GsPoseHparams(ctypes.Structure):
+    _fields_ = [("lr_rot", ctypes.c_double), ("lr_trans", ctypes.c_double), ("b1", ctypes.c_double),
+                ("b2", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
 class GsStatus(ctypes.Structure):
@@ -143,6 +152,9 @@ _SIGS = {
     "gs_ng_decode_bwd": (ctypes.c_int, [ctypes.POINTER(GsNgParams), P, ctypes.POINTER(GsParams), ctypes.c_int32,
                                          ctypes.POINTER(GsNgParams), P, P]),
     "gs_ng_read_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), P]),
+    "gs_pose_init": (ctypes.c_int, [P, P]),
+    "gs_plan_set_pose": (ctypes.c_int, [P, P]),
+    "gs_pose_step": (ctypes.c_int, [P, ctypes.POINTER(GsPoseHparams), P]),
 }
 
 

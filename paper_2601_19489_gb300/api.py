@@ -137,6 +137,12 @@ class Plan:
         off = ptr.value - self.ws.data_ptr()
         return self.ws[off:off + nb.value].view(dtype)
 
+    def set_pose(self, state: "PoseState | None") -> None:
+        """Attach a pose-refinement state (gs_plan_set_pose); None detaches."""
+        L.check(L.lib().gs_plan_set_pose(self.handle, state.buf.data_ptr() if state is not None else None),
+                "gs_plan_set_pose")
+        self.pose = state  # keeps the buffer alive while attached
+
     def status(self, stream=None) -> dict:
         st = L.GsStatus()
         rc = L.lib().gs_read_status(self.handle, self.ws.data_ptr(), ctypes.byref(st), _stream(stream))
@@ -366,3 +372,47 @@ def gs_ng_decode_bwd(ng: NgParams, cam, child_grads: "Gaussians", grads: NgParam
 def gs_ng_status(ws: torch.Tensor, stream=None) -> int:
     e = ctypes.c_int32(0)
     return int(L.lib().gs_ng_read_status(ws.data_ptr(), ctypes.byref(e), _stream(stream)))
+
+
+# ---------------------------------------------------------------- pose refinement (Sec. 2.5)
+
+class PoseState:
+    """The device state of the global pose correction (gs.h's pose-state
+    layout): correction (Delta_R, Delta_t), Adam moments and step, and the
+    slots the preprocess backward adds dL/d(omega, tau) into."""
+
+    R, T, M, V, STEP, ACC = slice(0, 9), slice(9, 12), slice(12, 18), slice(18, 24), 24, 32
+
+    def __init__(self, device="cuda"):
+        self.buf = torch.empty(L.GS_POSE_STATE_DOUBLES, dtype=torch.float64, device=device)
+        self.reset()
+
+    def reset(self, stream=None) -> None:
+        L.check(L.lib().gs_pose_init(self.buf.data_ptr(), _stream(stream)), "gs_pose_init")
+
+    def correction(self):
+        """(Delta_R (3, 3), Delta_t (3,)) as float64 host arrays (synchronises)."""
+        h = self.buf[:12].cpu().numpy()
+        return h[:9].reshape(3, 3).copy(), h[9:12].copy()
+
+    def set_correction(self, R, t) -> None:
+        self.buf[:9].copy_(torch.as_tensor(R, dtype=torch.float64).reshape(9))
+        self.buf[9:12].copy_(torch.as_tensor(t, dtype=torch.float64).reshape(3))
+
+    def slots(self) -> torch.Tensor:
+        """(GS_POSE_SLOTS, 6) view of the gradient partial sums."""
+        return self.buf[self.ACC:].view(L.GS_POSE_SLOTS, 8)[:, :6]
+
+    def grad(self):
+        """The accumulated dL/d(omega, tau) (host float64, synchronises)."""
+        return self.slots().sum(0).cpu().numpy()
+
+
+def pose_hparams(lr_rot: float, lr_trans: float, b1=0.9, b2=0.999, eps=1e-15) -> L.GsPoseHparams:
+    return L.GsPoseHparams(float(lr_rot), float(lr_trans), float(b1), float(b2), float(eps))
+
+
+def gs_pose_step(state: PoseState, lr_rot: float, lr_trans: float, b1=0.9, b2=0.999, eps=1e-15,
+                 stream=None, _hp=None) -> None:
+    hp = _hp if _hp is not None else pose_hparams(lr_rot, lr_trans, b1, b2, eps)
+    L.check(L.lib().gs_pose_step(state.buf.data_ptr(), ctypes.byref(hp), _stream(stream)), "gs_pose_step")

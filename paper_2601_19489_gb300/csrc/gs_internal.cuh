@@ -84,11 +84,13 @@ struct gs_plan {
     int32_t two_chain_min;         // live pixels from which a backward bucket walks two chains
     int32_t bbox_3sigma;           // ablation: classic 3-sigma tile box
     int32_t bwd_per_pixel;         // ablation: classic per-pixel backward
+    double *pose;                  // attached pose-refinement state (gs_plan_set_pose) or nullptr
     // offsets
     size_t o_status, o_rec, o_touched, o_rect, o_dkey[2], o_dval[2];
     size_t o_ikey[2], o_ival[2], o_ranges, o_tile_maxc, o_bucket_off, o_ncontrib;
     size_t o_ckpt, o_grad2d, o_sort_scratch, o_block_sums, o_bin;
     size_t o_final;  // per-pixel final T, then the background (per-pixel backward only)
+    size_t o_posed;  // GS_MAX_VIEWS ViewDev: the cameras with the pose correction applied
     size_t sort_scratch_bytes;
     size_t bytes;
     int inst_final;   // which ping-pong buffer holds the sorted instances
@@ -108,6 +110,10 @@ int launch_error();
 
 // One-thread launch that increments the device step count of Adam (adam.cu).
 int adam_tick(int32_t *d_step, cudaStream_t s);
+
+// Pose refinement (pose.cu): write the plan's cameras with the attached
+// correction applied into the workspace (ViewDev array at o_posed).
+int pose_compose(const gs_plan *plan, void *ws, const ViewsDev &vd, cudaStream_t s);
 
 // Radix sort internals (radix_sort.cu), usable with a device-resident count.
 size_t sort_scratch_bytes();

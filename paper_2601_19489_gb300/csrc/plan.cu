@@ -137,6 +137,7 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     p->o_final = take(p->bwd_per_pixel ? ((size_t)pix + 4) * sizeof(float) : 16);
     p->o_ckpt = take((size_t)p->bucket_cap * kCkptCh * kTilePix * sizeof(float));
     p->o_grad2d = take(VN * 3 * sizeof(float4));
+    p->o_posed = take(GS_MAX_VIEWS * sizeof(ViewDev));
     p->o_sort_scratch = take(p->sort_scratch_bytes);
     // uint32 block sums, then (8-byte aligned) uint64 block offsets
     p->o_block_sums = take((kBinBlocks + 32) * sizeof(uint32_t) + kBinBlocks * sizeof(uint64_t));

@@ -218,9 +218,11 @@ __device__ __forceinline__ void project_cov(const ViewDev &cam, float3 p, float4
     P.det = dot3(cr, cr) + 0.3f * (aa + cc) + 0.09f;
 }
 
-template <int D>
+// kPose: the cameras come from `posed` (the pose-corrected copies written by
+// pose_compose) instead of the kernel parameter.
+template <int D, bool kPose>
 __global__ void __launch_bounds__(256)
-k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
+k_preprocess(ViewsDev views, const ViewDev *__restrict__ posed, int64_t n, const float *__restrict__ means,
              const float *__restrict__ log_scales, const float4 *__restrict__ quats,
              const float *__restrict__ logits, const float *__restrict__ sh, float4 *__restrict__ rec,
              float2 *__restrict__ bin, uint32_t *__restrict__ touched, uint2 *__restrict__ rects,
@@ -230,7 +232,7 @@ k_preprocess(ViewsDev views, int64_t n, const float *__restrict__ means,
     if (item >= (int64_t)views.V * n) return;
     const int v = (int)(item / n);
     const int64_t g = item - (int64_t)v * n;
-    const ViewDev &cam = views.v[v];
+    const ViewDev &cam = kPose ? posed[v] : views.v[v];
     dval[item] = (uint32_t)item;
 
     const float3 p = make_float3(means[3 * g], means[3 * g + 1], means[3 * g + 2]);
@@ -337,6 +339,8 @@ struct PbArgs {
     float lr[6];                 // means, log_scales, quats, opacity, SH DC, SH rest
     float b1, b2, eps;
     const int32_t *d_step;       // step count, already incremented for this update
+    const ViewDev *posed;        // pose-corrected cameras (kPose)
+    double *pose_acc;            // pose-gradient slots: GS_POSE_SLOTS x 8 doubles (kPose)
 };
 
 // The same update as k_adam's (same operations, same order): the quotient
@@ -414,7 +418,7 @@ __device__ __forceinline__ void adam_sh_block(const float *s_p, const float *s_g
         }
 }
 
-template <int D, bool kAdam>
+template <int D, bool kAdam, bool kPose>
 __global__ void __launch_bounds__(kPbWarps * 32, 8)  // <= 128 registers: 8 CTAs (16 warps) per SM
 k_preprocess_bwd(ViewsDev views, PbArgs A) {
     const int64_t n = A.n;
@@ -496,6 +500,9 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
     float3 dp = make_float3(0.f, 0.f, 0.f);
     float g_ls[3] = {0.f, 0.f, 0.f}, g_q[4] = {0.f, 0.f, 0.f, 0.f};
     float dlogit = 0.f;
+    // kPose: this Gaussian's share of dL/d(omega, tau), the camera-frame
+    // increment of the global pose correction (Sec. 2.5), summed over views
+    float3 pw = make_float3(0.f, 0.f, 0.f), pt = make_float3(0.f, 0.f, 0.f);
     if (vmask) {
         const float3 p = make_float3(means[3 * g], means[3 * g + 1], means[3 * g + 2]);
         const float4 q = quats[g];
@@ -507,7 +514,7 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
         for (int v = 0; v < views.V; ++v) {
             if (!((vmask >> v) & 1u)) continue;
             const int64_t item = (int64_t)v * n + g;
-            const ViewDev &cam = views.v[v];
+            const ViewDev &cam = kPose ? A.posed[v] : views.v[v];
             project_cov(cam, p, q, ls, P);
             const float4 ga = grad2d[3 * item + 0];
             const float4 gb = grad2d[3 * item + 1];
@@ -540,7 +547,11 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
                 }
                 const float3 ddir = sh_grad_dot<D>(dir.x, dir.y, dir.z, wk);
                 // d = dv / |dv|:  d(dv) = (ddir - d (d . ddir)) / |dv|
-                dp = add3(dp, mul3(sub3(ddir, mul3(dir, dot3(dir, ddir))), inv_len));
+                const float3 gdv = mul3(sub3(ddir, mul3(dir, dot3(dir, ddir))), inv_len);
+                dp = add3(dp, gdv);
+                // the camera centre moves by -W^T tau under tau and stays put
+                // under omega: dL/dtau = W dL/d(dv)
+                if (kPose) pt = add3(pt, make_float3(dot3(P.W0, gdv), dot3(P.W1, gdv), dot3(P.W2, gdv)));
             }
             // ---- conic Q = Sigma'^-1 with Sigma' = U U^T + 0.3 I:
             //   dL/dSigma' = -Q G Q  (G: gradient w.r.t. the symmetric conic matrix,
@@ -599,6 +610,19 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
             const float dz = -d_iz * P.iz * P.iz;
             // ---- pc = W p + t
             dp = add3(dp, add3(add3(mul3(P.W0, dx), mul3(P.W1, dy)), mul3(P.W2, dz)));
+            if (kPose) {
+                // pc -> exp([omega]_x) pc + tau: dL/dtau = dL/dpc, and
+                // dL/domega = pc x dL/dpc plus, through T = J W with W ->
+                // exp([omega]_x) W at fixed J, sum_a (W dT_a) x J_a over the rows
+                // J_0 = fx iz (1, 0, -xz), J_1 = fy iz (0, 1, -yz)
+                const float3 gpc = make_float3(dx, dy, dz);
+                pt = add3(pt, gpc);
+                const float3 wt0 = make_float3(dot3(P.W0, vdT0), dot3(P.W1, vdT0), dot3(P.W2, vdT0));
+                const float3 wt1 = make_float3(dot3(P.W0, vdT1), dot3(P.W1, vdT1), dot3(P.W2, vdT1));
+                const float3 j0 = make_float3(cam.fx * P.iz, 0.f, -cam.fx * P.iz * P.xz);
+                const float3 j1 = make_float3(0.f, cam.fy * P.iz, -cam.fy * P.iz * P.yz);
+                pw = add3(pw, add3(cross3(P.pc, gpc), add3(cross3(wt0, j0), cross3(wt1, j1))));
+            }
         }
         // ---- scales: s = exp(log_scale)
         g_ls[0] = ds[0] * P.s[0];
@@ -621,6 +645,20 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
         g_q[1] = (dqn[1] - x * proj) * il;
         g_q[2] = (dqn[2] - y * proj) * il;
         g_q[3] = (dqn[3] - z * proj) * il;
+    }
+    if (kPose) {
+        // warp sum, then one lane adds it into the warp's slot (the slots
+        // spread the atomic adds over GS_POSE_SLOTS addresses)
+        float acc[6] = {pw.x, pw.y, pw.z, pt.x, pt.y, pt.z};
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+        if (lane == 0) {
+            double *slot = A.pose_acc + 8 * (int)((g0 >> 5) % GS_POSE_SLOTS);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) atomicAdd(slot + k, (double)acc[k]);
+        }
     }
     if (!kAdam) {
         if (vmask) {
@@ -747,13 +785,13 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
                                        A.v[4] + g0 * K3, rows, lane, s_dc, s_rest, A.b1, A.b2, A.eps, ibc2);
 }
 
-template <int D>
+template <int D, bool kPose>
 static void launch_preprocess(const gs_plan *plan, void *ws, const gs_params *pr, const ViewsDev &vd,
                               cudaStream_t s) {
     const int64_t total = plan->VN;
     const unsigned blocks = (unsigned)((total + 255) / 256);
-    k_preprocess<D><<<blocks, 256, 0, s>>>(
-        vd, plan->n, pr->means, pr->log_scales, (const float4 *)pr->quats, pr->opacity_logits, pr->sh,
+    k_preprocess<D, kPose><<<blocks, 256, 0, s>>>(
+        vd, ws_at<ViewDev>(ws, plan->o_posed), plan->n, pr->means, pr->log_scales, (const float4 *)pr->quats, pr->opacity_logits, pr->sh,
         ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin), ws_at<uint32_t>(ws, plan->o_touched),
         ws_at<uint2>(ws, plan->o_rect), ws_at<uint32_t>(ws, plan->o_dkey[0]), ws_at<uint32_t>(ws, plan->o_dval[0]),
         plan->bbox_3sigma);
@@ -762,7 +800,10 @@ static void launch_preprocess(const gs_plan *plan, void *ws, const gs_params *pr
 template <int D, bool kAdam>
 static void launch_preprocess_bwd(const ViewsDev &vd, const PbArgs &A, cudaStream_t s) {
     const unsigned blocks = (unsigned)((A.n + kPbWarps * 32 - 1) / (kPbWarps * 32));
-    k_preprocess_bwd<D, kAdam><<<blocks, kPbWarps * 32, 0, s>>>(vd, A);
+    if (A.pose_acc)
+        k_preprocess_bwd<D, kAdam, true><<<blocks, kPbWarps * 32, 0, s>>>(vd, A);
+    else
+        k_preprocess_bwd<D, kAdam, false><<<blocks, kPbWarps * 32, 0, s>>>(vd, A);
 }
 
 static PbArgs pb_args(const gs_plan *plan, void *ws, const gs_params *pr) {
@@ -776,6 +817,10 @@ static PbArgs pb_args(const gs_plan *plan, void *ws, const gs_params *pr) {
     A.sh = pr->sh;
     A.touched = ws_at<uint32_t>(ws, plan->o_touched);
     A.grad2d = ws_at<float4>(ws, plan->o_grad2d);
+    if (plan->pose) {
+        A.posed = ws_at<ViewDev>(ws, plan->o_posed);
+        A.pose_acc = plan->pose + 32;
+    }
     return A;
 }
 
@@ -859,11 +904,22 @@ extern "C" int gs_preprocess(const gs_plan *plan, void *ws, const gs_params *par
     if (rc) return rc;
     const ViewsDev vd = make_views(plan, cams);
     cudaStream_t s = (cudaStream_t)stream;
+    if (plan->pose) {
+        rc = pose_compose(plan, ws, vd, s);
+        if (rc) return rc;
+        switch (plan->sh_degree) {
+            case 0: launch_preprocess<0, true>(plan, ws, params, vd, s); break;
+            case 1: launch_preprocess<1, true>(plan, ws, params, vd, s); break;
+            case 2: launch_preprocess<2, true>(plan, ws, params, vd, s); break;
+            default: launch_preprocess<3, true>(plan, ws, params, vd, s); break;
+        }
+        return launch_error();
+    }
     switch (plan->sh_degree) {
-        case 0: launch_preprocess<0>(plan, ws, params, vd, s); break;
-        case 1: launch_preprocess<1>(plan, ws, params, vd, s); break;
-        case 2: launch_preprocess<2>(plan, ws, params, vd, s); break;
-        default: launch_preprocess<3>(plan, ws, params, vd, s); break;
+        case 0: launch_preprocess<0, false>(plan, ws, params, vd, s); break;
+        case 1: launch_preprocess<1, false>(plan, ws, params, vd, s); break;
+        case 2: launch_preprocess<2, false>(plan, ws, params, vd, s); break;
+        default: launch_preprocess<3, false>(plan, ws, params, vd, s); break;
     }
     return launch_error();
 }

@@ -1,6 +1,6 @@
 """Timed reconstruction: train from a sparse start against a set of posed
 views for a wall-clock budget and follow the held-out PSNR (the 1-minute
-reconstruction setting of the paper's Sec. 4, without its densification).
+reconstruction setting of the paper's Sec. 4).
 
 Ways to spend the budget, all on one schedule:
   plain          one view per step, eager launches;
@@ -11,10 +11,14 @@ Ways to spend the budget, all on one schedule:
   batched_graph  8 views per step through the batched plan, launch shapes from
                  the autotuner, every step replayed from a CUDA graph;
   ng             one view per step of the neural-Gaussian model (Sec. 2.3):
-                 anchors at the starting points, 10 decoded children each.
+                 anchors at the starting points, 10 decoded children each;
+  pose           plain, plus the global pose refinement of Sec. 2.5 (one
+                 camera-side correction for all views, updated every 300
+                 steps, applied to the held-out views too).
 The schedule is piecewise constant over the evaluation segments: the mean
 positions' learning rate decays exponentially from lr0 to lr0 / 100 (the
-3DGS schedule) and the disparity weight linearly to zero (Sec. 3.1).
+3DGS schedule), the pose rates the same way, and the disparity weight
+linearly to zero (Sec. 3.1).
 Evaluation time is not counted in the budget.
 """
 from __future__ import annotations
@@ -27,7 +31,7 @@ import torch
 
 from .api import Gaussians, NgParams
 from .autotune import autotune
-from .trainer import NgTrainer, Trainer, default_lrs
+from .trainer import NgTrainer, Trainer, default_lrs, default_pose
 
 
 def psnr(img: torch.Tensor, ref: torch.Tensor) -> float:
@@ -71,9 +75,10 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
                 budget_s: float = 60.0, eval_every_s: float = 5.0, lam: float = 0.2, disp_weight: float = 0.1,
                 extent: float = 4.4, batch: int = 8, seed: int = 0, densify_rules: dict | None = None,
                 densify_tau: float = 0.3, densify_k: int = 10, max_gaussians: int | None = None,
-                device="cuda") -> dict:
+                pose: dict | None = None, device="cuda") -> dict:
     """Run one method for budget_s seconds of training; returns its held-out
-    PSNR curve [(seconds trained, PSNR)], steps and views trained."""
+    PSNR curve [(seconds trained, PSNR)], steps and views trained.
+    pose: settings of the `pose` method (default_pose(extent) by default)."""
     W, H = train_cams[0].width, train_cams[0].height
     lrs = default_lrs(extent)
     lr0 = lrs["means"]
@@ -93,10 +98,11 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
             best, _ = autotune(params, b_cams[:2], b_rgb[:2], lam=lam, device=device)
             tuning = {k: best[k] for k in ("bucket", "bwd_warps", "bwd_chains")}
             lb = best["load_balanced"]
-        elif method not in ("plain", "densify"):
+        elif method not in ("plain", "densify", "pose"):
             raise ValueError(method)
+        pose_cfg = {**default_pose(extent), **(pose or {})} if method == "pose" else None
         tr = Trainer(params, W, H, lam=lam, disp_weight=disp_weight, lrs=lrs, load_balanced=lb, tuning=tuning,
-                     device=device)
+                     pose=pose_cfg, device=device)
     views = b_cams if method == "batched_graph" else [[c] for c in train_cams]
     tr.ensure_capacity(views, slack=2.0)
     n_seg = max(1, int(round(budget_s / eval_every_s)))
@@ -111,6 +117,8 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
         tr.disp_weight = disp_weight * (1.0 - frac)
         if method != "ng":
             tr.set_lr("means", lr0 * 0.01 ** frac)
+        if method == "pose":
+            tr.set_pose_lr(pose_cfg["lr_rot"] * 0.01 ** frac, pose_cfg["lr_trans"] * 0.01 ** frac)
         graphs = None
         if method == "batched_graph":
             graphs = [tr.capture(b_cams[b], b_rgb[b], b_disp[b]) for b in range(len(b_cams))]
@@ -145,7 +153,11 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
         del graphs
         curve.append((trained, eval_psnr(tr, eval_cams, eval_rgb)))
     per_step = batch if method == "batched_graph" else 1
-    return {"method": method, "curve": curve, "psnr_final": curve[-1][1], "psnr_start": curve[0][1],
+    extra = {}
+    if method == "pose":
+        R, t = tr.pose.correction()
+        extra["pose_correction"] = {"R": R.tolist(), "t": t.tolist(), "updates": int(tr.pose.buf[24].item())}
+    return {**extra, "method": method, "curve": curve, "psnr_final": curve[-1][1], "psnr_start": curve[0][1],
             "steps": steps, "views": steps * per_step, "seconds": trained,
             "views_per_s": steps * per_step / trained, "gaussians_final": tr.params.n,
             "densify": densify_log}

@@ -8,6 +8,11 @@ end to end), its gradients sum over the views, and one Adam update follows.
 The Adam step count lives on the device, so a step can be captured once in a
 CUDA graph (``Trainer.capture``) and replayed.
 
+With ``pose`` set, the global pose refinement of Sec. 2.5 runs alongside: one
+camera-side correction shared by every view (training and evaluation), its
+gradient accumulated by every step's preprocess backward and applied by an
+Adam step every ``every`` steps (300 in the paper).
+
 Learning rates default to the 3DGS values the paper trains with (its Sec. 4
 builds on 3DGS and names no optimiser settings); SH DC coefficients and the
 higher SH coefficients get different rates inside one Adam group.
@@ -19,13 +24,21 @@ import ctypes
 import torch
 
 from . import _lib as L
-from .api import (Gaussians, NgParams, Plan, adam_groups_array, adam_hparams, camera_struct, gs_densify_apply,
-                  gs_densify_plan, gs_densify_score, gs_densify_scratch, gs_ng_workspace, ng_children)
+from .api import (Gaussians, NgParams, Plan, PoseState, adam_groups_array, adam_hparams, camera_struct,
+                  gs_densify_apply, gs_densify_plan, gs_densify_score, gs_densify_scratch, gs_ng_workspace,
+                  gs_pose_step, ng_children, pose_hparams)
 
 
 def default_lrs(extent: float = 1.0) -> dict:
     return {"means": 1.6e-4 * extent, "log_scales": 5e-3, "quats": 1e-3, "opacity_logits": 0.05,
             "sh_dc": 2.5e-3, "sh_rest": 2.5e-3 / 20.0}
+
+
+def default_pose(extent: float = 1.0) -> dict:
+    """Pose-refinement settings: an update every 300 steps (Sec. 2.5); the
+    paper gives no rates, these move the correction by at most about 1 mrad
+    and 0.1 % of the scene extent per update."""
+    return {"every": 300, "lr_rot": 1e-3, "lr_trans": 1e-3 * extent}
 
 
 def _as_list(cams):
@@ -60,12 +73,16 @@ class Trainer:
     def __init__(self, params: Gaussians, width: int | None = None, height: int | None = None, *,
                  lam: float = 0.2, bg=(0.0, 0.0, 0.0), lrs: dict | None = None,
                  inst_capacity: int | None = None, load_balanced: bool = True, disp_weight: float = 0.0,
-                 tuning: dict | None = None, fused_adam: bool = True, device="cuda"):
+                 tuning: dict | None = None, fused_adam: bool = True, pose: dict | None = None, device="cuda"):
         """tuning: launch shapes of the plans ({"bucket": 32 | 64,
         "bwd_warps": 2 | 4 | 8}), e.g. from autotune.autotune.
         fused_adam: apply Adam inside the preprocess backward
         (gs_preprocess_bwd_adam) instead of storing the gradient and running
-        a separate Adam pass; self.grads then stays zero."""
+        a separate Adam pass; self.grads then stays zero.
+        pose: enable the global pose refinement ({"every", "lr_rot",
+        "lr_trans"}, missing keys from default_pose()); the correction is in
+        self.pose (a PoseState) and applies to every view this trainer
+        renders."""
         self.params = params
         self.fused_adam = bool(fused_adam)
         self.STAGES = self.STAGES_FUSED if self.fused_adam else self.STAGES_UNFUSED
@@ -81,11 +98,18 @@ class Trainer:
         self.d_step = torch.zeros(1, dtype=torch.int32, device=device)
         self.loss = torch.zeros(1, device=device)
         self.cap = int(inst_capacity) if inst_capacity is not None else max(1 << 20, 16 * params.n)
+        self._bg = (ctypes.c_float * 3)(*self.bg)
+        self.pose_cfg = None
+        self.pose = None
+        self._capturing = False
+        if pose is not None:
+            self.pose_cfg = {**default_pose(), **pose}
+            self.pose = PoseState(device)
+            self._pose_hp = pose_hparams(self.pose_cfg["lr_rot"], self.pose_cfg["lr_trans"])
         self._slots: dict = {}
         self._default = None
         if width is not None:
             self._default = self._slot(((int(width), int(height)),))
-        self._bg = (ctypes.c_float * 3)(*self.bg)
         self._build_adam()
         self._cam_cache = {}
 
@@ -94,6 +118,8 @@ class Trainer:
         s = self._slots.get(sizes)
         if s is None:
             s = _Slot(self.params, sizes, self.cap, self.device, self.tuning)
+            if self.pose is not None:
+                s.plan.set_pose(self.pose)
             self._slots[sizes] = s
         return s
 
@@ -132,6 +158,18 @@ class Trainer:
         graph keeps the rates it was captured with)."""
         self.lrs[name] = float(lr)
         self._build_adam()
+
+    def set_pose_lr(self, lr_rot: float, lr_trans: float) -> None:
+        """Change the pose-refinement rates (for the following updates)."""
+        self.pose_cfg.update(lr_rot=float(lr_rot), lr_trans=float(lr_trans))
+        self._pose_hp = pose_hparams(self.pose_cfg["lr_rot"], self.pose_cfg["lr_trans"])
+
+    def _pose_tick(self, s) -> None:
+        """After a step: every `every` steps, fold the accumulated pose
+        gradient into the correction (one launch, on the step's stream)."""
+        if self.pose is not None and not self._capturing and self.step_count % self.pose_cfg["every"] == 0:
+            L.check(L.lib().gs_pose_step(self.pose.buf.data_ptr(), ctypes.byref(self._pose_hp), s),
+                    "gs_pose_step")
 
     def _cam(self, cams):
         cams = _as_list(cams)
@@ -201,11 +239,13 @@ class Trainer:
                                                    ctypes.byref(self._vstruct), ctypes.byref(self._hp),
                                                    self.d_step.data_ptr(), s), "gs_preprocess_bwd_adam")
             ev(6)
+            self._pose_tick(s)
             return
         self._splat_stages(cams, target, target_disp, s, ev, 1)
         L.check(L.lib().gs_adam_step_multi_dev(self._adam, len(self._adam), 0.9, 0.999, 1e-15,
                                                self.d_step.data_ptr(), s), "gs_adam_step_multi_dev")
         ev(7)
+        self._pose_tick(s)
 
     def _splat_stages(self, cams, target, target_disp, s, ev, e0: int, with_pbwd: bool = True) -> None:
         """preprocess .. preprocess backward of self.params on `cams`; the
@@ -313,6 +353,9 @@ class Trainer:
         st["step_count"] = self.step_count
         st["lrs"] = dict(self.lrs)
         st["lam"], st["disp_weight"] = self.lam, self.disp_weight
+        if self.pose is not None:
+            st["pose"] = self.pose.buf.detach().cpu().clone()
+            st["pose_cfg"] = dict(self.pose_cfg)
         return st
 
     def load_state_dict(self, st: dict) -> None:
@@ -326,6 +369,10 @@ class Trainer:
         self.step_count = int(st["step_count"])
         self.lam, self.disp_weight = float(st["lam"]), float(st["disp_weight"])
         self.lrs = dict(st["lrs"])
+        if self.pose is not None and "pose" in st:
+            self.pose.buf.copy_(st["pose"].to(self.pose.buf.device))
+            self.set_pose_lr(st["pose_cfg"]["lr_rot"], st["pose_cfg"]["lr_trans"])
+            self.pose_cfg["every"] = int(st["pose_cfg"]["every"])
         self._build_adam()
 
     def save(self, path: str) -> None:
@@ -401,14 +448,19 @@ class StepGraph:
         self.graph = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.graph(self.graph, stream=side):
-            trainer.step(self.cams, target, target_disp)
+        trainer._capturing = True  # the periodic pose update stays out of the graph
+        try:
+            with torch.cuda.graph(self.graph, stream=side):
+                trainer.step(self.cams, target, target_disp)
+        finally:
+            trainer._capturing = False
         trainer.step_count -= 1  # capture does not run the step
         torch.cuda.current_stream().wait_stream(side)
 
     def replay(self) -> None:
         self.graph.replay()
         self.trainer.step_count += 1
+        self.trainer._pose_tick(torch.cuda.current_stream().cuda_stream)
 
 
 def default_ng_lrs() -> dict:
@@ -438,6 +490,8 @@ class NgTrainer(Trainer):
         children = ng_children(ng.n, device=kw.get("device", "cuda"))
         kw.setdefault("inst_capacity", max(1 << 20, 16 * children.n))
         kw["fused_adam"] = False  # the children are decoded, not optimised
+        if kw.get("pose") is not None:
+            raise ValueError("pose refinement is not wired into the neural-Gaussian decoder's view direction")
         super().__init__(children, width, height, **kw)
         self.STAGES = NgTrainer.NG_STAGES
         self._ngp = ng.struct()

@@ -9,6 +9,8 @@ from .scenes import (  # noqa: F401
     Camera,
     Scene,
     camera_c1,
+    camera_pose_error,
+    with_pose_error,
     ring_cameras,
     mixed_ring_cameras,
     orbit_cameras,

@@ -19,6 +19,9 @@ Recipes (sizes and distributions of the paper's workloads, Sec. 4):
   coefficients N(0, 0.1)).
 * ``ring_cameras``: cameras on a y = 0 ring of radius 4 looking at the origin,
   OpenCV axes (x right, y down, z forward), horizontal field of view 60 deg.
+* ``camera_pose_error`` / ``with_pose_error``: one systematic camera-side
+  pose error shared by every camera of a capture (the inaccurate poses that
+  Sec. 2.5's global correction is for).
 """
 from __future__ import annotations
 
@@ -204,6 +207,28 @@ def orbit_cameras(n_views: int = 200, width: int = 1600, height: int = 1060, fov
         R, t = _look_at(eye, np.zeros(3))
         cams.append(Camera(fx, fx, 0.5 * width, 0.5 * height, R, t, width, height))
     return cams
+
+
+def camera_pose_error(rot: float, trans: float, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """One seeded camera-side pose error: a rotation of `rot` radians about a
+    uniformly random axis and a translation of length `trans` in a uniformly
+    random direction, (R, t) in float64 (scipy builds the rotation)."""
+    from scipy.spatial.transform import Rotation
+
+    rng = _rng(seed)
+    axis = rng.standard_normal(3)
+    d = rng.standard_normal(3)
+    R = Rotation.from_rotvec(rot * axis / np.linalg.norm(axis)).as_matrix()
+    return R, trans * d / np.linalg.norm(d)
+
+
+def with_pose_error(cams, R_err: np.ndarray, t_err: np.ndarray) -> list:
+    """The cameras as a capture with a systematic pose error reports them:
+    every camera's world -> camera transform [R | t] becomes
+    [R_err R | R_err t + t_err] (the same error in each camera's own frame)."""
+    from dataclasses import replace
+
+    return [replace(c, R=R_err @ c.R, t=R_err @ c.t + t_err) for c in cams]
 
 
 def recon_init(gt: Scene, n_init: int, seed: int = 0, pos_noise: float = 0.02, rgb_noise: float = 0.05,

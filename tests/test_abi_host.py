@@ -120,3 +120,32 @@ def test_argument_errors_are_caught_on_the_host(lib):
     assert lib.gs_adam_step_multi(None, 0, 0.9, 0.999, 1e-15, 1, None) == -1
     g = (_lib.GsAdamGroup * 1)()
     assert lib.gs_adam_step_multi(g, 1, 0.9, 0.999, 1e-15, 0, None) == -1  # step < 1
+
+
+def test_pose_entry_points_check_arguments_on_the_host(lib):
+    """Argument errors are reported before anything is enqueued (no GPU is
+    touched: the pointers below are never dereferenced)."""
+    from paper_2601_19489_gb300 import _lib as L
+
+    w = (ctypes.c_int32 * 1)(64)
+    h = (ctypes.c_int32 * 1)(48)
+    plan = lib.gs_plan_create(10, 0, 1, w, h, 100)
+    assert plan
+    try:
+        assert lib.gs_plan_set_pose(plan, None) == L.GS_OK  # detach
+        assert lib.gs_plan_set_pose(plan, ctypes.c_void_p(8)) == L.GS_ERR_ARG  # misaligned
+        assert lib.gs_plan_set_pose(None, ctypes.c_void_p(16)) == L.GS_ERR_ARG
+    finally:
+        lib.gs_plan_destroy(plan)
+    ok = L.GsPoseHparams(1e-3, 1e-3, 0.9, 0.999, 1e-15)
+    assert lib.gs_pose_step(None, ctypes.byref(ok), None) == L.GS_ERR_ARG
+    assert lib.gs_pose_step(ctypes.c_void_p(24), ctypes.byref(ok), None) == L.GS_ERR_ARG
+    assert lib.gs_pose_step(ctypes.c_void_p(16), None, None) == L.GS_ERR_ARG
+    for bad in (L.GsPoseHparams(1e-3, 1e-3, 1.0, 0.999, 1e-15), L.GsPoseHparams(1e-3, 1e-3, 0.9, 0.2, 1e-15),
+                L.GsPoseHparams(-1.0, 1e-3, 0.9, 0.999, 1e-15), L.GsPoseHparams(1e-3, 1e-3, 0.9, 0.999, -1.0)):
+        assert lib.gs_pose_step(ctypes.c_void_p(16), ctypes.byref(bad), None) == L.GS_ERR_ARG
+    assert lib.gs_pose_init(None, None) == L.GS_ERR_ARG
+    assert lib.gs_pose_init(ctypes.c_void_p(40), None) == L.GS_ERR_ARG
+    assert L.GS_POSE_STATE_DOUBLES == 32 + 8 * L.GS_POSE_SLOTS
+    hdr = open(os.path.join(ROOT, "include", "gs.h")).read()
+    assert re.search(r"#define GS_POSE_SLOTS %d\b" % L.GS_POSE_SLOTS, hdr)

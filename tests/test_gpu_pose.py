@@ -1,0 +1,246 @@
+"""Global pose refinement (Sec. 2.5) on the GPU: the pose-corrected cameras
+and the accumulated dL/d(omega, tau) against the oracle, the update against
+the oracle's, a rigid-motion identity at the full 1M-Gaussian 1080p size, and
+the trainer recovering a known camera-side error."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import pose as opose
+from oracle import step as ostep
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(96, 54), (128, 72), (160, 90)]
+BG = (0.0, 0.0, 0.0)
+
+
+def _batch():
+    scene = synth.scene_clustered(400, seed=1, sh_degree=1)
+    cams = [synth.ring_cameras(5, w, h)[i] for i, (w, h) in enumerate(SIZES)]
+    rng = np.random.default_rng(7)
+    targets = [rng.uniform(2.0, 2.5, size=(3, h, w)) for (w, h) in SIZES]
+    dts = [rng.uniform(-0.1, -0.05, size=(h, w)) for (w, h) in SIZES]
+    return scene, cams, targets, dts
+
+
+def _corr():
+    return opose.so3_exp([0.012, -0.02, 0.008]), np.array([0.03, -0.02, 0.05])
+
+
+def _flat(arrs):
+    return torch.from_numpy(np.concatenate([a.reshape(-1) for a in arrs]).astype(np.float32)).cuda()
+
+
+def _step_through_abi(api, plan, params, cams, targets, dts, fused):
+    P = plan.pixels
+    rgb, disp, T = (torch.empty(k * P, device="cuda") for k in (3, 1, 1))
+    dL, dLd = torch.empty(3 * P, device="cuda"), torch.empty(P, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    api.gs_preprocess(plan, params, cams)
+    api.gs_bin_sort(plan, True)
+    api.gs_render_fwd(plan, BG, rgb, disp, T)
+    api.gs_loss(plan, rgb, _flat(targets), 0.2, dL, loss, api.gs_loss_scratch(plan), disp=disp,
+                target_disp=_flat(dts), disp_weight=0.1, dL_ddisp=dLd)
+    if fused:
+        from paper_2601_19489_gb300 import _lib as L
+        import ctypes
+
+        L.check(L.lib().gs_render_bwd_blend(plan.handle, plan.ws.data_ptr(), rgb.data_ptr(), disp.data_ptr(),
+                                            dL.data_ptr(), dLd.data_ptr(), torch.cuda.current_stream().cuda_stream),
+                "gs_render_bwd_blend")
+        m, v = params.zeros_like(), params.zeros_like()
+        api.gs_preprocess_bwd_adam(plan, params, cams, m, v, {"means": 0.0, "log_scales": 0.0, "quats": 0.0,
+                                                              "opacity_logits": 0.0, "sh_dc": 0.0, "sh_rest": 0.0},
+                                   torch.zeros(1, dtype=torch.int32, device="cuda"))
+        grads = None
+    else:
+        grads = params.zeros_like()
+        api.gs_render_bwd(plan, params, cams, BG, rgb, disp, dL, dLd, grads)
+    assert plan.status()["rc"] == 0
+    return loss.item(), grads
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_pose_gradient_matches_oracle(gs, fused):
+    from paper_2601_19489_gb300 import api
+
+    scene, cams, targets, dts = _batch()
+    plan = api.Plan(scene.n, scene.sh_degree, SIZES, 1 << 20)
+    params = api.Gaussians.from_scene(scene)
+    state = api.PoseState()
+    Rc, tc = _corr()
+    state.set_correction(Rc, tc)
+    plan.set_pose(state)
+    L_gpu, _ = _step_through_abi(api, plan, params, cams, targets, dts, fused)
+    g_gpu = state.grad()
+    # oracle: the same cameras corrected on the host side from the state's
+    # values, each view weighted by its share of the batch's pixels
+    sc64 = synth.Scene(*(a.astype(np.float64) for a in scene.arrays()), sh_degree=scene.sh_degree)
+    ccams = [opose.corrected_camera(c, Rc, tc) for c in cams]
+    Ptot = float(sum(w * h for (w, h) in SIZES))
+    L_ref, g_ref, scale = 0.0, np.zeros(6), np.zeros(6)
+    for c, tgt, dt in zip(ccams, targets, dts):
+        wv = c.width * c.height / Ptot
+        Lv, _, f = ostep.forward_backward(sc64, c, tgt, bg=BG, lam=0.2, disp_target=dt, disp_weight=0.1)
+        L_ref += wv * Lv
+        gv, av = opose.pose_gradient(sc64, [c], [wv * f["grad2d"]])
+        g_ref += gv
+        scale += av
+    np.testing.assert_allclose(L_gpu, L_ref, rtol=1e-5)
+    # per-Gaussian float32 terms (each within about 1e-5 of its own size),
+    # summed in float32 within a warp and in double across warps: the error
+    # is bounded by a small multiple of the sum of |terms|
+    assert np.all(np.abs(g_gpu - g_ref) <= 2e-4 * scale), (g_gpu, g_ref, scale)
+    # and not vacuous: every component is at least ten times that bound
+    # (the terms cancel down to about 0.5 % of their absolute sum here)
+    assert np.all(np.abs(g_ref) > 2e-3 * scale)
+
+
+def test_detached_plan_matches_the_host_corrected_cameras(gs):
+    """A plan with a correction attached renders exactly what a plan without
+    one renders from cameras corrected on the host (double precision,
+    rounded once to float32), and after detaching it renders the plain
+    cameras again."""
+    from paper_2601_19489_gb300 import api
+
+    scene, cams, _, _ = _batch()
+    params = api.Gaussians.from_scene(scene)
+    Rc, tc = _corr()
+
+    def render(plan, cs):
+        P = plan.pixels
+        rgb, disp, T = (torch.empty(k * P, device="cuda") for k in (3, 1, 1))
+        api.gs_preprocess(plan, params, cs)
+        api.gs_bin_sort(plan, True)
+        api.gs_render_fwd(plan, BG, rgb, disp, T)
+        return rgb.cpu().numpy(), disp.cpu().numpy()
+
+    plan = api.Plan(scene.n, scene.sh_degree, SIZES, 1 << 20)
+    state = api.PoseState()
+    state.set_correction(Rc, tc)
+    plan.set_pose(state)
+    a = render(plan, cams)
+    plain = api.Plan(scene.n, scene.sh_degree, SIZES, 1 << 20)
+    b = render(plain, [opose.corrected_camera(c, Rc, tc) for c in cams])
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    plan.set_pose(None)
+    c0 = render(plan, cams)
+    d0 = render(plain, cams)
+    np.testing.assert_array_equal(c0[0], d0[0])
+    assert np.abs(c0[0] - a[0]).max() > 1e-3  # the correction did change the image
+
+
+def test_pose_step_matches_oracle(gs):
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300 import _lib as L
+
+    rng = np.random.default_rng(5)
+    state = api.PoseState()
+    Rc, tc = _corr()
+    state.set_correction(Rc, tc)
+    ref = opose.identity_state()
+    ref["R"], ref["t"] = Rc.copy(), tc.copy()
+    for it, (lr_r, lr_t) in enumerate([(1e-3, 4e-3), (2e-3, 1e-3), (5e-4, 5e-4)]):
+        acc = rng.standard_normal((L.GS_POSE_SLOTS, 6)) * rng.uniform(0.1, 10.0, size=6)
+        state.slots().copy_(torch.from_numpy(acc))
+        api.gs_pose_step(state, lr_r, lr_t)
+        ref = opose.pose_step(ref, acc.sum(0), lr_r, lr_t)
+        R, t = state.correction()
+        np.testing.assert_allclose(R, ref["R"], rtol=0, atol=1e-13)
+        np.testing.assert_allclose(t, ref["t"], rtol=0, atol=1e-13)
+        h = state.buf.cpu().numpy()
+        np.testing.assert_allclose(h[12:18], ref["m"], rtol=1e-13)
+        np.testing.assert_allclose(h[18:24], ref["v"], rtol=1e-13)
+        assert h[24] == it + 1
+        assert np.all(state.slots().cpu().numpy() == 0.0)  # the sums restart
+
+
+@pytest.mark.slow
+def test_translation_gradient_identity_at_1m_1080p(gs):
+    """At the full size (1M clustered Gaussians, 1080p, one view), the
+    camera-frame translation gradient equals W' sum_i dL/dmean_i (moving the
+    camera by tau moves every Gaussian by W'^T tau relative to it), W' the
+    corrected camera rotation: a property of any size, checked between the
+    pose accumulation and the means gradient of the same step."""
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import Trainer
+
+    scene = synth.scene_clustered(1 << 20, seed=0, sh_degree=3)
+    cam = synth.ring_cameras(16, 1920, 1080)[3]
+    tgt = torch.from_numpy(synth.target_uniform(11, 1920, 1080).reshape(-1)).cuda()
+    tr = Trainer(api.Gaussians.from_scene(scene), 1920, 1080, fused_adam=False, pose={"every": 10 ** 9})
+    Rc, tc = _corr()
+    tr.pose.set_correction(Rc, tc)
+    tr.ensure_capacity([[cam]])
+    tr.pose.slots().zero_()  # ensure_capacity's forward passes add nothing, but start clean
+    # the step's stages up to the preprocess backward (the Adam pass would
+    # consume the means gradient)
+    tr._splat_stages([cam], tgt, None, torch.cuda.current_stream().cuda_stream, lambda i: None, 0)
+    torch.cuda.synchronize()
+    assert tr.slot_for([cam]).plan.status()["rc"] == 0
+    g = tr.pose.grad()
+    gm = tr.grads.means.double()
+    W = torch.from_numpy(opose.corrected_camera(cam, Rc, tc).w2c().astype(np.float64)[:, :3]).cuda()
+    want = (W @ gm.sum(0)).cpu().numpy()
+    scale = (gm @ W.T).abs().sum(0).cpu().numpy()
+    assert np.all(np.abs(g[3:] - want) <= 1e-4 * scale + 1e-9), (g[3:], want, scale)
+    assert np.all(np.abs(want) > 1e-3 * scale)
+
+
+def _reprojection_px(means, base, train, R, t):
+    """Mean image distance of the Gaussian centres between the true cameras
+    and the corrected training cameras."""
+    out = []
+    for c0, ct in zip(base, train):
+        c1 = opose.corrected_camera(ct, R, t)
+        uv = []
+        for c in (c0, c1):
+            w = c.w2c().astype(np.float64)
+            pc = means @ w[:, :3].T + w[:, 3]
+            keep = pc[:, 2] > 0.5
+            uv.append((c.fx * pc[keep, 0] / pc[keep, 2], c.fy * pc[keep, 1] / pc[keep, 2]))
+        out.append(np.hypot(uv[0][0] - uv[1][0], uv[0][1] - uv[1][1]).mean())
+    return float(np.mean(out))
+
+
+@pytest.mark.parametrize("graphed", [False, True])
+def test_trainer_recovers_a_camera_side_error(gs, graphed):
+    """Targets rendered from the true cameras; training cameras carry one
+    camera-side error; the Gaussians are held fixed (zero rates) so that only
+    the correction can reduce the loss.  Updates every 10 steps."""
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import Trainer
+
+    scene = synth.scene_clustered(20000, seed=2, sh_degree=1)
+    W, H = 320, 180
+    base = synth.ring_cameras(8, W, H)
+    truth = Trainer(api.Gaussians.from_scene(scene), W, H)
+    targets = [truth.forward([c]).rgb.clone() for c in base]
+    err_R, err_t = opose.so3_exp([0.006, -0.008, 0.004]), np.array([0.02, -0.015, 0.01])
+    train = [opose.corrected_camera(c, err_R, err_t) for c in base]
+    zero = {k: 0.0 for k in ("means", "log_scales", "quats", "opacity_logits", "sh_dc", "sh_rest")}
+    tr = Trainer(api.Gaussians.from_scene(scene), W, H, lrs=zero, lam=0.0,
+                 pose={"every": 10, "lr_rot": 1e-3, "lr_trans": 2e-3})
+    means = np.asarray(scene.means, dtype=np.float64)
+    e0 = _reprojection_px(means, base, train, np.eye(3), np.zeros(3))
+    graphs = None
+    if graphed:
+        tr.step([train[0]], targets[0])  # one eager step loads every kernel before capture
+        graphs = [tr.capture([c], tgt) for c, tgt in zip(train, targets)]
+    for it in range(400):
+        i = it % len(train)
+        if it == 200:
+            tr.set_pose_lr(3e-4, 6e-4)
+        if graphs is not None:
+            graphs[i].replay()
+        else:
+            tr.step([train[i]], targets[i])
+    torch.cuda.synchronize()
+    assert tr.pose.buf[24].item() == tr.step_count // 10
+    R, t = tr.pose.correction()
+    e1 = _reprojection_px(means, base, train, R, t)
+    assert e1 < 0.2 * e0, (e0, e1)
+    np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-12)
