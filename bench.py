@@ -77,6 +77,7 @@ def parse_args():
                     help="comma-separated Gaussian counts for --workload batched (default: --n)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-pose", action="store_true", help="skip the pose-refinement overhead measurement")
+    ap.add_argument("--no-visible-adam", action="store_true", help="skip the visible-only Adam measurement")
     ap.add_argument("--recon-pose-error", type=str, default="",
                     help="'rot_rad,trans': give every recon view one seeded camera-side pose error "
                          "(methods suffixed @true keep the true poses)")
@@ -411,6 +412,9 @@ def run_ours(args, rank, world):
         torch.cuda.empty_cache()
     if world == 1 and not args.no_pose:
         line["pose_refinement"] = run_pose_overhead(args, dev, scene, cams, lb, tuning, max(60, args.steps // 3))
+        torch.cuda.empty_cache()
+    if world == 1 and not args.no_visible_adam:
+        line["visible_adam"] = run_visible_adam(args, dev, scene, lb, tuning, max(60, args.steps // 3))
     if world == 1 and not args.no_cpu_baseline:
         scene_h = scene
         cam = cams[0]
@@ -573,6 +577,52 @@ def run_pose_overhead(args, dev, scene, cams, lb, tuning, steps: int, warmup: in
     out["overhead_pct"] = 100.0 * (out["on"]["ms_per_step"] / out["off"]["ms_per_step"] - 1.0)
     out["note"] = ("pose on: camera composition kernel + pose-gradient terms and warp sums in the fused "
                    "preprocess backward + Adam; the 1-block pose update every 300 steps")
+    return out
+
+
+def run_visible_adam(args, dev, scene, lb, tuning, steps: int, warmup: int = 5, radius: float = 2.2) -> dict:
+    """Dense against visible-only (sparse) Adam in the fused preprocess
+    backward, on the headline scene seen from a closer ring (radius 2.2
+    instead of 4), where part of the scene is outside each view."""
+    import torch
+
+    import synth
+    from paper_2601_19489_gb300 import _lib as L
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import Trainer
+
+    cams = synth.ring_cameras(args.views, args.width, args.height, radius=radius)
+    targets = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1)).to(dev)
+               for v in range(len(cams))]
+    out = {"ring_radius": radius}
+    for name, vis in (("dense", False), ("visible_only", True)):
+        tr = Trainer(api.Gaussians.from_scene(scene, device=dev), args.width, args.height, lam=args.lam,
+                     load_balanced=lb, tuning=tuning, visible_adam=vis, device=dev)
+        tr.ensure_capacity(cams)
+        if not vis:
+            frac = []
+            for c in cams:
+                tr.forward([c])
+                frac.append(float((tr.plan.view(L.GS_WS_TILES_TOUCHED, torch.int32) > 0).float().mean().item()))
+            out["visible_fraction"] = float(np.mean(frac))
+        for s in range(warmup):
+            tr.step(cams[s % len(cams)], targets[s % len(cams)])
+        n_st = len(tr.STAGES)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_st + 1)] for _ in range(steps)]
+        torch.cuda.synchronize()
+        for s in range(steps):
+            v = (warmup + s) % len(cams)
+            tr.step(cams[v], targets[v], events=evs[s])
+        torch.cuda.synchronize()
+        if tr.plan.status()["rc"] != 0:
+            raise RuntimeError(f"device status after the {name} steps")
+        ms = float(np.mean([evs[s][0].elapsed_time(evs[s][n_st]) for s in range(steps)]))
+        out[name] = {"steps_per_s": 1e3 / ms, "ms_per_step": ms,
+                     "preprocess_bwd_adam_ms": float(np.mean([evs[s][n_st - 1].elapsed_time(evs[s][n_st])
+                                                              for s in range(steps)]))}
+        del tr
+        torch.cuda.empty_cache()
+    out["adam_stage_speedup"] = out["dense"]["preprocess_bwd_adam_ms"] / out["visible_only"]["preprocess_bwd_adam_ms"]
     return out
 
 

@@ -248,10 +248,16 @@ GS_API int gs_preprocess_bwd(const gs_plan *plan, void *ws, const gs_params *par
  * group; the SH DC coefficients (the first 3 floats of a Gaussian's SH row)
  * take lr_sh_dc, the rest lr_sh_rest.  b1, b2 in [0.5, 1).  Every array of
  * params, adam_m and adam_v must start 16-byte aligned (GS_ERR_ARG
- * otherwise). */
+ * otherwise).
+ * visible_only != 0 selects the sparse (visible-only) Adam of the Taming-3DGS
+ * line the paper builds on (Sec. 2.2): a Gaussian that touched no tile in any
+ * view of the plan keeps its parameters and both moments unchanged (its
+ * moments do not decay); the others get the update above with the global
+ * step count t. */
 typedef struct {
     float lr_means, lr_log_scales, lr_quats, lr_opacity, lr_sh_dc, lr_sh_rest;
     float b1, b2, eps;
+    int32_t visible_only;
 } gs_adam_hparams;
 GS_API int gs_preprocess_bwd_adam(const gs_plan *plan, void *ws, gs_params *params, const gs_camera *h_cams,
                                   const gs_params *adam_m, const gs_params *adam_v, const gs_adam_hparams *hp,

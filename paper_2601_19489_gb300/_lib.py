@@ -65,7 +65,8 @@ class GsTuning(ctypes.Structure):
 class GsAdamHparams(ctypes.Structure):
     _fields_ = [("lr_means", ctypes.c_float), ("lr_log_scales", ctypes.c_float), ("lr_quats", ctypes.c_float),
                 ("lr_opacity", ctypes.c_float), ("lr_sh_dc", ctypes.c_float), ("lr_sh_rest", ctypes.c_float),
-                ("b1", ctypes.c_float), ("b2", ctypes.c_float), ("eps", ctypes.c_float)]
+                ("b1", ctypes.c_float), ("b2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("visible_only", ctypes.c_int32)]
 
 
 class GsDensifyRules(ctypes.Structure):

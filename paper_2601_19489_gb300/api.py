@@ -228,22 +228,24 @@ def gs_adam_step_multi_dev(groups, d_step: torch.Tensor, b1=0.9, b2=0.999, eps=1
                                            _stream(stream)), "gs_adam_step_multi_dev")
 
 
-def adam_hparams(lrs: dict, b1=0.9, b2=0.999, eps=1e-15) -> L.GsAdamHparams:
+def adam_hparams(lrs: dict, b1=0.9, b2=0.999, eps=1e-15, visible_only: bool = False) -> L.GsAdamHparams:
     """lrs with keys means, log_scales, quats, opacity_logits, sh_dc, sh_rest."""
     return L.GsAdamHparams(float(lrs["means"]), float(lrs["log_scales"]), float(lrs["quats"]),
                            float(lrs["opacity_logits"]), float(lrs["sh_dc"]), float(lrs["sh_rest"]), float(b1),
-                           float(b2), float(eps))
+                           float(b2), float(eps), int(bool(visible_only)))
 
 
 def gs_preprocess_bwd_adam(plan: Plan, params: Gaussians, cams, m: Gaussians, v: Gaussians, lrs: dict,
-                           d_step: torch.Tensor, b1=0.9, b2=0.999, eps=1e-15, stream=None) -> None:
+                           d_step: torch.Tensor, b1=0.9, b2=0.999, eps=1e-15, visible_only: bool = False,
+                           stream=None) -> None:
     """Preprocess backward fused with the Adam update (parameters, m and v
-    updated in place; d_step incremented)."""
+    updated in place; d_step incremented).  visible_only: the sparse Adam
+    that leaves Gaussians which touched no tile as they are."""
     if d_step.dtype != torch.int32 or not d_step.is_cuda:
         raise TypeError("d_step must be a CUDA int32 tensor")
     ca = cameras_array(cams)
     p, ms, vs = params.struct(), m.struct(), v.struct()
-    hp = adam_hparams(lrs, b1, b2, eps)
+    hp = adam_hparams(lrs, b1, b2, eps, visible_only)
     L.check(L.lib().gs_preprocess_bwd_adam(plan.handle, plan.ws.data_ptr(), ctypes.byref(p), ca, ctypes.byref(ms),
                                            ctypes.byref(vs), ctypes.byref(hp), _ptr(d_step, None),
                                            _stream(stream)), "gs_preprocess_bwd_adam")

@@ -17,8 +17,9 @@
 // no-swizzle K-major layout (8 x 16-byte core matrices).  One thread issues
 // the MMAs; tcgen05.commit arrives on an mbarrier that the CTA waits on with
 // a bounded spin.  The weight gradients (sums over anchors) are formed per CTA
-// on the CUDA cores and reduced over CTAs in a fixed order.
+// and reduced over CTAs in a fixed order.
 #include <cuda_bf16.h>
+#include <stddef.h>
 
 #include "gs_internal.cuh"
 
@@ -389,45 +390,82 @@ cleanup:
 }
 
 // --------------------------------------------------------------- backward
+// Per CTA of 128 anchors, every contraction on the tensor cores:
+//   y  = H W2^T          (recompute, M = 128 anchors, N = 144, K = 32)
+//   dh = dY W2           (M = 128 anchors, N = 32, K = 144)
+//   dW2 = dY^T H         (outputs 0..127 and 128..143 as two M = 128 tiles,
+//                         N = 32, K = 128 anchors)
+//   dx = dH W1           (M = 128 anchors, N = 48, K = 32)
+//   dW1^T = x^T dH       (M = 128 input rows of which 48 exist, N = 32,
+//                         K = 128 anchors)
+// An M = 128 operand with fewer real rows (dW2's last 16 outputs, dW1's 48
+// inputs) is followed in shared memory by other operand buffers: the MMA reads
+// them as its remaining rows, whose results land in TMEM lanes nobody reads.
+// TMEM columns: y 0..143, then dh 0..31, dx 32..79, dW2 128..159 and
+// 160..191, dW1^T 192..223.
 struct BwdSmem {
-    __nv_bfloat16 H[kTileA * kHid];      // GEMM 2 A (recompute of y)
-    __nv_bfloat16 W2[kOutPad * kHid];    // GEMM 2 B
-    __nv_bfloat16 DY[kTileA * kOutPad];  // dh GEMM A (M = 128, K = 144)
-    __nv_bfloat16 W2T[kHid * kOutPad];   // dh GEMM B (N = 32, K = 144)
-    __nv_bfloat16 DH[kTileA * kHid];     // dx GEMM A (M = 128, K = 32)
-    __nv_bfloat16 W1T[kInPad * kHid];    // dx GEMM B (N = 48, K = 32)
-    float Y[kTileA][kOutPad + 1];        // y, then dL/dy (fp32)
-    float hf[kTileA][kHid + 1];          // h (bf16 values) as float
-    float dhf[kTileA][kHid + 1];         // dL/dh after the ReLU mask, rounded to bf16, as float
-    float x[kTileA][kIn + 1];            // x (bf16 values) as float
+    __nv_bfloat16 W2T[kHid * kOutPad];   // dh B (N = 32, K = 144)
+    __nv_bfloat16 W1T[kInPad * kHid];    // dx B (N = 48, K = 32)
+    __nv_bfloat16 DY[kTileA * kOutPad];  // dh A (M = 128 anchors, K = 144)
+    // the next three are read as 128-row A operands of K = 128 anchors
+    __nv_bfloat16 DYT2[16 * kTileA];     // dW2 A, outputs 128..143 (+112 rows read past the end)
+    __nv_bfloat16 XT[kInPad * kTileA];   // dW1^T A, inputs 0..47 (+80 rows read past the end)
+    __nv_bfloat16 DYT[kTileA * kTileA];  // dW2 A, outputs 0..127
+    __nv_bfloat16 HT[kHid * kTileA];     // dW2 B (N = 32 hidden, K = 128 anchors)
+    union {
+        struct {
+            __nv_bfloat16 H[kTileA * kHid];    // y A (M = 128, K = 32)
+            __nv_bfloat16 W2[kOutPad * kHid];  // y B (N = 144, K = 32)
+        } p1;
+        struct {
+            __nv_bfloat16 DH[kTileA * kHid];   // dx A (M = 128, K = 32)
+            __nv_bfloat16 DHT[kHid * kTileA];  // dW1^T B (N = 32 hidden, K = 128 anchors)
+        } p2;
+    } u;
+    float Y[kTileA][kOutPad + 1];  // y, then dL/dy (fp32)
     float xyz[kTileA][3], ls[kTileA][6], dls[kTileA][6];
-    float db1[kHid], b2[kOutPad];
+    float db1w[kThreads / 32][kHid];  // per-warp sums of db1
+    float b2[kOutPad];
     uint64_t mbar;
     uint32_t tmem;
     int fail;
 };
 
+static_assert(sizeof(BwdSmem::DYT) >= sizeof(float) * kTileA * kChild * 6, "log-scale terms fit the dW2 operand");
+static_assert(offsetof(BwdSmem, DYT2) + 2 * kTileA * kTileA <= offsetof(BwdSmem, u), "dW2 tail operand rows");
+static_assert(offsetof(BwdSmem, XT) + 2 * kTileA * kTileA <= offsetof(BwdSmem, u), "dW1 operand rows");
+
+__device__ __forceinline__ float bf16f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
 __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     extern __shared__ uint8_t smem_raw[];
     BwdSmem &S = *reinterpret_cast<BwdSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t a0 = (int64_t)blockIdx.x * kTileA;
     const int64_t a = a0 + tid;
     const bool valid = a < A.n;
     const int na = (int)min((int64_t)kTileA, A.n - a0);
     float *part = A.partial + (size_t)blockIdx.x * kPartial;
 
+    if (warp == 1 && lane < 5) {
+        // ask L2 for this tile's children's gradients (five contiguous
+        // ranges, read only after the y recompute) while the operands load
+        const int nch = na * kChild;
+        const float *base = lane == 0 ? A.g_means + 3 * a0 * kChild : lane == 1 ? A.g_sh + 3 * a0 * kChild
+                          : lane == 2 ? A.g_ls + 3 * a0 * kChild : lane == 3 ? A.g_quats + 4 * a0 * kChild
+                                                                               : A.g_logits + a0 * kChild;
+        const uint32_t bytes = (uint32_t)(nch * (lane == 3 ? 16 : lane == 4 ? 4 : 12)) & ~15u;
+        if (bytes > 0 && ((uintptr_t)base & 15) == 0)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base), "r"(bytes) : "memory");
+    }
     if (warp == 0) tmem_alloc(&S.tmem, kTmemCols);
     if (tid == 0) {
         mbar_init(&S.mbar, 1);
         S.fail = 0;
     }
-    if (tid < kHid) S.db1[tid] = 0.0f;
     {
-        float x[kInPad];
-        anchor_input(A, a, valid, x);
-#pragma unroll
-        for (int k = 0; k < kIn; ++k) S.x[tid][k] = x[k];
+        // h of this anchor into the y GEMM's A (row = anchor) and the dW2
+        // GEMM's B (row = hidden unit, K = anchors)
         const uint4 *src = reinterpret_cast<const uint4 *>(A.h_store + a * kHid);
 #pragma unroll
         for (int q = 0; q < kHid / 8; ++q) {
@@ -436,21 +474,23 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int c = 8 * q + 2 * e;
-                *reinterpret_cast<uint32_t *>(&S.H[canon(tid, c, kHid)]) = u[e];
-                S.hf[tid][c] = __uint_as_float(u[e] << 16);
-                S.hf[tid][c + 1] = __uint_as_float(u[e] & 0xffff0000u);
+                *reinterpret_cast<uint32_t *>(&S.u.p1.H[canon(tid, c, kHid)]) = u[e];
+                S.HT[canon(c, tid, kTileA)] = __ushort_as_bfloat16((unsigned short)(u[e] & 0xffffu));
+                S.HT[canon(c + 1, tid, kTileA)] = __ushort_as_bfloat16((unsigned short)(u[e] >> 16));
             }
         }
+        // x of this anchor as the dW1^T GEMM's A (row = input, K = anchors)
+        float x[kInPad];
+        anchor_input(A, a, valid, x);
+#pragma unroll
+        for (int k = 0; k < kInPad; ++k) S.XT[canon(k, tid, kTileA)] = __float2bfloat16_rn(x[k]);
     }
-    copy16(S.W2, A.w2b, kOutPad * kHid * 2, tid);
+    copy16(S.u.p1.W2, A.w2b, kOutPad * kHid * 2, tid);
     copy16(S.W2T, A.w2tb, kHid * kOutPad * 2, tid);
     copy16(S.W1T, A.w1tb, kInPad * kHid * 2, tid);
     for (int i = tid; i < kOutPad; i += kThreads) S.b2[i] = i < kOut ? A.b2[i] : 0.0f;
     for (int j = 0; j < 3; ++j) S.xyz[tid][j] = valid ? A.xyz[3 * a + j] : 0.0f;
-    for (int j = 0; j < 6; ++j) {
-        S.ls[tid][j] = valid ? A.ls[6 * a + j] : 0.0f;
-        S.dls[tid][j] = 0.0f;
-    }
+    for (int j = 0; j < 6; ++j) S.ls[tid][j] = valid ? A.ls[6 * a + j] : 0.0f;
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -462,8 +502,8 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     if (tid == 0) {
 #pragma unroll
         for (int kk = 0; kk < kHid / 16; ++kk)
-            mma_bf16(tmem, smem_desc(S.H + kk * 128, 128, kHid * 16), smem_desc(S.W2 + kk * 128, 128, kHid * 16),
-                     idesc_bf16(kTileA, kOutPad), kk > 0);
+            mma_bf16(tmem, smem_desc(S.u.p1.H + kk * 128, 128, kHid * 16),
+                     smem_desc(S.u.p1.W2 + kk * 128, 128, kHid * 16), idesc_bf16(kTileA, kOutPad), kk > 0);
         mma_commit(&S.mbar);
     }
     if (!mbar_wait(&S.mbar, 0)) S.fail = 1;
@@ -486,7 +526,10 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     __syncthreads();
     {
         // dL/dy from the children's gradients, in place of y (every element
-        // depends on its own y only); anchor log-scale gradients in shared memory
+        // depends on its own y only).  Each child's six terms of its anchor's
+        // log-scale gradients are parked in the (not yet used) dW2 operand
+        // buffer and summed per anchor afterwards, children in order.
+        float *lsterm = reinterpret_cast<float *>(S.DYT);  // [child][6]
         const int nch = na * kChild;
         const int64_t c0 = a0 * kChild;
         // the children's gradients are read four strides ahead of their use
@@ -520,13 +563,13 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
                 const int ch = i / 3, j = i - 3 * ch, r = ch / kChild, c = ch - r * kChild;
                 float &y0 = S.Y[r][c * kPer + j];
                 const float th = tanhf(y0), so = expf(S.ls[r][j]);
-                atomicAdd(&S.dls[r][j], gm[u] * th * so);
+                lsterm[6 * ch + j] = gm[u] * th * so;
                 y0 = gm[u] * so * (1.0f - th * th);
                 float &y4 = S.Y[r][c * kPer + 4 + j];
                 const float rgb = sigmoidf_(y4);
                 y4 = gs[u] * kDcScale * rgb * (1.0f - rgb);
                 float &y7 = S.Y[r][c * kPer + 7 + j];
-                atomicAdd(&S.dls[r][3 + j], gl[u]);
+                lsterm[6 * ch + 3 + j] = gl[u];
                 y7 = gl[u] * sigmoidf_(-y7);
             }
         }
@@ -543,33 +586,64 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
             y3 = (o > 0.0f && o < kOpacityCeil) ? A.g_logits[c0 + ch] / (oc * (1.0f - oc)) * (1.0f - o * o) : 0.0f;
             if (A.zero_g) A.g_logits[c0 + ch] = 0.0f;
         }
-        // rows of absent anchors and the padding columns carry no gradient
-        for (int i = tid; i < kTileA * kOutPad; i += kThreads) {
-            const int r = i / kOutPad, o = i - r * kOutPad;
-            if (r >= na || o >= kOut) S.Y[r][o] = 0.0f;
-        }
     }
     __syncthreads();
-    // db2 (unrounded dy) and the rounded dy as the dh GEMM operand
+    if (tid < na) {
+        const float *t = reinterpret_cast<const float *>(S.DYT) + 6 * kChild * tid;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float sum = 0.0f;
+#pragma unroll
+            for (int c = 0; c < kChild; ++c) sum += t[6 * c + k];
+            S.dls[tid][k] = sum;
+        }
+    }
+    // db2 (unrounded dy of the present anchors)
     for (int o = tid; o < kOut; o += kThreads) {
         float s = 0.0f;
-        for (int r = 0; r < kTileA; ++r) s += S.Y[r][o];
+        for (int r = 0; r < na; ++r) s += S.Y[r][o];
         part[kOut * kHid + kHid * kIn + o] = s;
     }
-    for (int i = tid; i < kTileA * kOutPad; i += kThreads) {
-        const int r = i / kOutPad, o = i - r * kOutPad;
-        S.DY[canon(r, o, kOutPad)] = __float2bfloat16_rn(S.Y[r][o]);
+    __syncthreads();
+    {
+        // this anchor's rounded dy (zero for an absent anchor and the padding
+        // outputs) as its row of the dh GEMM's A and its column (K index) of
+        // the dW2 GEMMs' A operands
+        const bool live = tid < na;
+#pragma unroll 4
+        for (int o = 0; o < kOutPad; o += 2) {
+            const float v0 = live && o < kOut ? S.Y[tid][o] : 0.0f;
+            const float v1 = live && o + 1 < kOut ? S.Y[tid][o + 1] : 0.0f;
+            const uint32_t pk = pack_bf16x2(v0, v1);
+            *reinterpret_cast<uint32_t *>(&S.DY[canon(tid, o, kOutPad)]) = pk;
+            const __nv_bfloat16 b0 = __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
+            const __nv_bfloat16 b1 = __ushort_as_bfloat16((unsigned short)(pk >> 16));
+            if (o < kTileA) {
+                S.DYT[canon(o, tid, kTileA)] = b0;
+                S.DYT[canon(o + 1, tid, kTileA)] = b1;
+            } else {
+                S.DYT2[canon(o - kTileA, tid, kTileA)] = b0;
+                S.DYT2[canon(o + 1 - kTileA, tid, kTileA)] = b1;
+            }
+        }
     }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    // dh = dy W2 (contraction over the 144 outputs)
+    // dh = dy W2 (contraction over the 144 outputs), dW2 = dy^T h (over the
+    // 128 anchors) for outputs 0..127 and 128..143
     if (tid == 0) {
 #pragma unroll
         for (int kk = 0; kk < kOutPad / 16; ++kk)
             mma_bf16(tmem, smem_desc(S.DY + kk * 128, 128, kOutPad * 16), smem_desc(S.W2T + kk * 128, 128, kOutPad * 16),
                      idesc_bf16(kTileA, kHid), kk > 0);
+#pragma unroll
+        for (int kk = 0; kk < kTileA / 16; ++kk) {
+            const uint64_t hb = smem_desc(S.HT + kk * 128, 128, kTileA * 16);
+            mma_bf16(tmem + 128, smem_desc(S.DYT + kk * 128, 128, kTileA * 16), hb, idesc_bf16(kTileA, kHid), kk > 0);
+            mma_bf16(tmem + 160, smem_desc(S.DYT2 + kk * 128, 128, kTileA * 16), hb, idesc_bf16(kTileA, kHid), kk > 0);
+        }
         mma_commit(&S.mbar);
     }
     if (!mbar_wait(&S.mbar, 1)) S.fail = 1;
@@ -577,29 +651,61 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     __syncthreads();
     if (S.fail) goto cleanup;
     {
+        // dh after the ReLU mask, rounded, as the dx GEMM's A (row = anchor)
+        // and the dW1^T GEMM's B (row = hidden unit, K = anchors); the
+        // y-recompute operands it overwrites are no longer read
         float v[32];
         tmem_ld32(my_lanes, v);
 #pragma unroll
-        for (int c = 0; c < kHid; ++c) {
-            const float dh = S.hf[tid][c] > 0.0f ? v[c] : 0.0f;
-            const float ws = warp_sum(dh);
-            if ((tid & 31) == 0) atomicAdd(&S.db1[c], ws);
-            const __nv_bfloat16 db = __float2bfloat16_rn(dh);
-            S.DH[canon(tid, c, kHid)] = db;
-            S.dhf[tid][c] = __bfloat162float(db);
+        for (int c = 0; c < kHid; c += 2) {
+            const float d0 = bf16f(S.HT[canon(c, tid, kTileA)]) > 0.0f ? v[c] : 0.0f;
+            const float d1 = bf16f(S.HT[canon(c + 1, tid, kTileA)]) > 0.0f ? v[c + 1] : 0.0f;
+            const float w0 = warp_sum(d0), w1 = warp_sum(d1);
+            if (lane == 0) {
+                S.db1w[warp][c] = w0;
+                S.db1w[warp][c + 1] = w1;
+            }
+            const uint32_t pk = pack_bf16x2(d0, d1);
+            *reinterpret_cast<uint32_t *>(&S.u.p2.DH[canon(tid, c, kHid)]) = pk;
+            S.u.p2.DHT[canon(c, tid, kTileA)] = __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
+            S.u.p2.DHT[canon(c + 1, tid, kTileA)] = __ushort_as_bfloat16((unsigned short)(pk >> 16));
+        }
+        // this thread's row (output tid) of dW2
+        tmem_ld32(my_lanes + 128, v);
+        float4 *dst = reinterpret_cast<float4 *>(part + tid * kHid);
+#pragma unroll
+        for (int q = 0; q < kHid / 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        if (warp == 0) {  // outputs 128..139
+            tmem_ld32(my_lanes + 160, v);
+            if (lane < kOut - kTileA) {
+                float4 *d2 = reinterpret_cast<float4 *>(part + (kTileA + lane) * kHid);
+#pragma unroll
+                for (int q = 0; q < kHid / 4; ++q)
+                    d2[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
         }
     }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    // dx = dh W1 (contraction over the 32 hidden units)
+    // dx = dh W1 (over the 32 hidden units); dW1^T = x^T dh (over the anchors)
     if (tid == 0) {
 #pragma unroll
         for (int kk = 0; kk < kHid / 16; ++kk)
-            mma_bf16(tmem + 32, smem_desc(S.DH + kk * 128, 128, kHid * 16), smem_desc(S.W1T + kk * 128, 128, kHid * 16),
-                     idesc_bf16(kTileA, kInPad), kk > 0);
+            mma_bf16(tmem + 32, smem_desc(S.u.p2.DH + kk * 128, 128, kHid * 16),
+                     smem_desc(S.W1T + kk * 128, 128, kHid * 16), idesc_bf16(kTileA, kInPad), kk > 0);
+#pragma unroll
+        for (int kk = 0; kk < kTileA / 16; ++kk)
+            mma_bf16(tmem + 192, smem_desc(S.XT + kk * 128, 128, kTileA * 16),
+                     smem_desc(S.u.p2.DHT + kk * 128, 128, kTileA * 16), idesc_bf16(kTileA, kHid), kk > 0);
         mma_commit(&S.mbar);
+    }
+    if (tid < kHid) {  // db1, warps in order
+        float sum = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) sum += S.db1w[w][tid];
+        part[kOut * kHid + kHid * kIn + kOut + tid] = sum;
     }
     if (!mbar_wait(&S.mbar, 0)) S.fail = 1;
     tc_fence_after();
@@ -627,39 +733,13 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
 #pragma unroll
             for (int j = 0; j < 6; ++j) A.d_ls[6 * a + j] += S.dls[tid][j];
         }
-    }
-    // weight gradients of the tile: dW2 = dy_bf^T h, dW1 = dh_bf^T x.  A
-    // thread owns one output row and a block of columns and keeps the block's
-    // sums in registers; per anchor it reads its own y (consecutive threads,
-    // consecutive rows) and the anchor's h or x (the same address across the
-    // warp: a broadcast).
-    for (int i = tid; i < kOut * 2; i += kThreads) {
-        const int o = i >> 1, k0 = (i & 1) * 16;
-        float s[16];
+        if (warp < 2) {  // dW1[h][i] = (dW1^T)[i][h] for the 35 inputs
+            tmem_ld32(my_lanes + 192, v);
+            if (tid < kIn)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) s[c] = 0.0f;
-        for (int r = 0; r < kTileA; ++r) {
-            const float y = bf16r(S.Y[r][o]);
-#pragma unroll
-            for (int c = 0; c < 16; ++c) s[c] += y * S.hf[r][k0 + c];
+                for (int h = 0; h < kHid; ++h) part[kOut * kHid + h * kIn + tid] = v[h];
         }
-#pragma unroll
-        for (int c = 0; c < 16; ++c) part[o * kHid + k0 + c] = s[c];
     }
-    for (int i = tid; i < kHid * 5; i += kThreads) {
-        const int h = i / 5, k0 = (i - h * 5) * 7;
-        float s[7];
-#pragma unroll
-        for (int c = 0; c < 7; ++c) s[c] = 0.0f;
-        for (int r = 0; r < kTileA; ++r) {
-            const float d = S.dhf[r][h];
-#pragma unroll
-            for (int c = 0; c < 7; ++c) s[c] += d * S.x[r][k0 + c];
-        }
-#pragma unroll
-        for (int c = 0; c < 7; ++c) part[kOut * kHid + h * kIn + k0 + c] = s[c];
-    }
-    if (tid < kHid) part[kOut * kHid + kHid * kIn + kOut + tid] = S.db1[tid];
 cleanup:
     if (S.fail) {
         // give the tensor cores one more bounded wait before the memory goes
@@ -672,17 +752,34 @@ cleanup:
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// Sum of the per-CTA partials in CTA order (deterministic), added to the grads.
-__global__ void __launch_bounds__(256) k_ng_reduce(const float *__restrict__ partial, int n_tiles, float *dw2,
-                                                   float *dw1, float *db2, float *db1) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kPartial) return;
-    float s = 0.0f;
-    for (int t = 0; t < n_tiles; ++t) s += partial[(size_t)t * kPartial + i];
-    if (i < kOut * kHid) dw2[i] += s;
-    else if (i < kOut * kHid + kHid * kIn) dw1[i - kOut * kHid] += s;
-    else if (i < kOut * kHid + kHid * kIn + kOut) db2[i - kOut * kHid - kHid * kIn] += s;
-    else db1[i - kOut * kHid - kHid * kIn - kOut] += s;
+// Sum of the per-CTA partials, added to the grads.  A block owns 32
+// consecutive partial entries (a warp reads them as one 128-byte row); its 32
+// warps take the CTAs t = warp, warp + 32, ... (four running sums each, for
+// independent loads in flight), then one warp adds the 32 warp sums in warp
+// order.  The order is fixed, so the result is deterministic.
+constexpr int kRedCols = 32, kRedRows = 32;
+__global__ void __launch_bounds__(kRedCols * kRedRows) k_ng_reduce(const float *__restrict__ partial, int n_tiles,
+                                                                   float *dw2, float *dw1, float *db2, float *db1) {
+    __shared__ float red[kRedRows][kRedCols + 1];
+    const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int i = blockIdx.x * kRedCols + c;
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (i < kPartial) {
+        int t = g;
+        for (; t + 3 * kRedRows < n_tiles; t += 4 * kRedRows)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s[u] += partial[(size_t)(t + u * kRedRows) * kPartial + i];
+        for (int u = 0; t < n_tiles; t += kRedRows, ++u) s[u & 3] += partial[(size_t)t * kPartial + i];
+    }
+    red[g][c] = (s[0] + s[1]) + (s[2] + s[3]);
+    __syncthreads();
+    if (g != 0 || i >= kPartial) return;
+    float tot = 0.0f;
+    for (int r = 0; r < kRedRows; ++r) tot += red[r][c];
+    if (i < kOut * kHid) dw2[i] += tot;
+    else if (i < kOut * kHid + kHid * kIn) dw1[i - kOut * kHid] += tot;
+    else if (i < kOut * kHid + kHid * kIn + kOut) db2[i - kOut * kHid - kHid * kIn] += tot;
+    else db1[i - kOut * kHid - kHid * kIn - kOut] += tot;
 }
 
 // ---------------------------------------------------------------- workspace
@@ -820,8 +917,8 @@ extern "C" int gs_ng_decode_bwd(const gs_ng_params *p, const gs_camera *cam, con
     A.d_ls = grads->anchor_ls;
     const int tiles = (int)((p->n_anchors + ng::kTileA - 1) / ng::kTileA);
     ng::k_ng_bwd<<<tiles, ng::kThreads, smem, s>>>(A);
-    ng::k_ng_reduce<<<(ng::kPartial + 255) / 256, 256, 0, s>>>(A.partial, tiles, grads->w2, grads->w1, grads->b2,
-                                                              grads->b1);
+    ng::k_ng_reduce<<<(ng::kPartial + ng::kRedCols - 1) / ng::kRedCols, ng::kRedCols * ng::kRedRows, 0, s>>>(
+        A.partial, tiles, grads->w2, grads->w1, grads->b2, grads->b1);
     return launch_error();
 }
 

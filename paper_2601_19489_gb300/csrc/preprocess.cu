@@ -325,7 +325,9 @@ k_preprocess(ViewsDev views, const ViewDev *__restrict__ posed, int64_t n, const
 // views of the plan are summed inside the kernel) applies the Adam update to
 // the parameter in place, so the gradient never travels through memory.
 // Every Gaussian is updated, a Gaussian that touched no tile with a zero
-// gradient (its moments still decay and it keeps moving).
+// gradient (its moments still decay and it keeps moving), unless the update
+// is visible-only: then such a Gaussian's parameters and moments are left as
+// they are, and a warp of 32 of them reads and writes nothing.
 constexpr int kPbWarps = 2;
 constexpr int kSmallRow = 11;  // a lane's gradients: mean 3, log-scale 3, quaternion 4, logit 1
 
@@ -339,6 +341,7 @@ struct PbArgs {
     float lr[6];                 // means, log_scales, quats, opacity, SH DC, SH rest
     float b1, b2, eps;
     const int32_t *d_step;       // step count, already incremented for this update
+    int visible_only;            // Adam: leave Gaussians that touched no tile untouched
     const ViewDev *posed;        // pose-corrected cameras (kPose)
     double *pose_acc;            // pose-gradient slots: GS_POSE_SLOTS x 8 doubles (kPose)
 };
@@ -370,22 +373,26 @@ __device__ __forceinline__ void quad_rc(int j, int e, int &r, int &c) {
 // kRowS), gradients from the shared accumulators, moments streamed in
 // float4s, half of a lane's quads in flight per batch.  kFull: all 32 rows
 // present (no bounds checks).
+// upd: bit r set = row r is updated (a row left out keeps its values).
 template <int K3, int kRowS, bool kFull>
 __device__ __forceinline__ void adam_sh_block(const float *s_p, const float *s_g, float *sh, float *m, float *v,
                                               int rows, int lane, float s_dc, float s_rest, float b1, float b2,
-                                              float eps, float ibc2) {
+                                              float eps, float ibc2, uint32_t upd) {
     const int F = kFull ? 32 * K3 : rows * K3, FQ = F >> 2;
     float4 *p4 = reinterpret_cast<float4 *>(sh), *m4 = reinterpret_cast<float4 *>(m);
     float4 *v4 = reinterpret_cast<float4 *>(v);
     constexpr int kQL = (32 * K3 / 4 + 31) / 32;  // quads per lane, full block
     constexpr int kU = (kQL + 1) / 2;
+    // a quad of a row left out is neither read nor written (rows of 3K
+    // floats hold whole quads when 3K is a multiple of 4)
+    auto quad_live = [&](int j) { return K3 % 4 != 0 || ((upd >> ((4 * j) / K3)) & 1u); };
 #pragma unroll
     for (int b = 0; b < kQL; b += kU) {
         float4 mq[kU], vq[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int j = lane + 32 * (b + u);
-            if (b + u < kQL && (kFull ? j < 8 * K3 : j < FQ)) {
+            if (b + u < kQL && (kFull ? j < 8 * K3 : j < FQ) && quad_live(j)) {
                 mq[u] = m4[j];
                 vq[u] = v4[j];
             }
@@ -393,7 +400,7 @@ __device__ __forceinline__ void adam_sh_block(const float *s_p, const float *s_g
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int j = lane + 32 * (b + u);
-            if (b + u < kQL && (kFull ? j < 8 * K3 : j < FQ)) {
+            if (b + u < kQL && (kFull ? j < 8 * K3 : j < FQ) && quad_live(j)) {
                 float pv[4], mv[4] = {mq[u].x, mq[u].y, mq[u].z, mq[u].w},
                              vv[4] = {vq[u].x, vq[u].y, vq[u].z, vq[u].w};
 #pragma unroll
@@ -401,7 +408,8 @@ __device__ __forceinline__ void adam_sh_block(const float *s_p, const float *s_g
                     int r, c;
                     quad_rc<K3>(j, e, r, c);
                     pv[e] = s_p[r * kRowS + c];
-                    adam_el(pv[e], s_g[r * kRowS + c], mv[e], vv[e], b1, b2, eps, c < 3 ? s_dc : s_rest, ibc2);
+                    if ((upd >> r) & 1u)
+                        adam_el(pv[e], s_g[r * kRowS + c], mv[e], vv[e], b1, b2, eps, c < 3 ? s_dc : s_rest, ibc2);
                 }
                 p4[j] = make_float4(pv[0], pv[1], pv[2], pv[3]);
                 m4[j] = make_float4(mv[0], mv[1], mv[2], mv[3]);
@@ -412,13 +420,14 @@ __device__ __forceinline__ void adam_sh_block(const float *s_p, const float *s_g
     if (!kFull)
         for (int i = 4 * FQ + lane; i < F; i += 32) {  // ragged end of the last warp
             const int r = i / K3, c = i - r * K3;
+            if (!((upd >> r) & 1u)) continue;
             float pv = s_p[r * kRowS + c];
             adam_el(pv, s_g[r * kRowS + c], m[i], v[i], b1, b2, eps, c < 3 ? s_dc : s_rest, ibc2);
             sh[i] = pv;
         }
 }
 
-template <int D, bool kAdam, bool kPose>
+template <int D, bool kAdam, bool kPose, bool kVisible>
 __global__ void __launch_bounds__(kPbWarps * 32, 8)  // <= 128 registers: 8 CTAs (16 warps) per SM
 k_preprocess_bwd(ViewsDev views, PbArgs A) {
     const int64_t n = A.n;
@@ -444,9 +453,13 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
         for (int v = 0; v < views.V; ++v)
             if (touched[(int64_t)v * n + g] != 0) vmask |= 1u << v;
     const uint32_t busy = __ballot_sync(0xffffffffu, vmask != 0);
-    if (!kAdam && busy == 0) return;  // uniform over the warp
-    if (kAdam && rows > 0) {
+    if ((!kAdam || kVisible) && busy == 0) return;  // uniform over the warp
+    // rows the Adam phase updates: all, or (visible-only Adam) the Gaussians
+    // that touched a tile in some view of the step
+    const uint32_t upd = kVisible ? busy : 0xffffffffu;
+    if (kAdam && rows > 0 && (!kVisible || busy == 0xffffffffu)) {
         // ask L2 for the warp's blocks of every array the Adam phase streams
+        // (visible-only: when the whole warp is updated)
         // (bulk prefetches, one range per lane, rounded down to whole 16-byte
         // units inside the arrays), so that they arrive while the gradient
         // is being computed
@@ -759,7 +772,9 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int i = 4 * lane + e, r = i / w, c = i - r * w;
-                adam_el(pv[e], s_g[warp][r * kSmallRow + goff[a] + c], mv[e], vv[e], A.b1, A.b2, A.eps, st, ibc2);
+                if ((upd >> r) & 1u)
+                    adam_el(pv[e], s_g[warp][r * kSmallRow + goff[a] + c], mv[e], vv[e], A.b1, A.b2, A.eps, st,
+                            ibc2);
             }
             reinterpret_cast<float4 *>(pa[a] + g0 * w)[lane] = make_float4(pv[0], pv[1], pv[2], pv[3]);
             reinterpret_cast<float4 *>(A.m[a] + g0 * w)[lane] = make_float4(mv[0], mv[1], mv[2], mv[3]);
@@ -767,6 +782,7 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
         }
         for (int i = 4 * nq + lane; i < rows * w; i += 32) {  // ragged end of the last warp
             const int r = i / w, c = i - r * w;
+            if (!((upd >> r) & 1u)) continue;
             float *pp = pa[a] + g0 * w, *mm = A.m[a] + g0 * w, *vvp = A.v[a] + g0 * w;
             float pv = pp[i], mv = mm[i], v2 = vvp[i];
             adam_el(pv, s_g[warp][r * kSmallRow + goff[a] + c], mv, v2, A.b1, A.b2, A.eps, st, ibc2);
@@ -779,10 +795,10 @@ k_preprocess_bwd(ViewsDev views, PbArgs A) {
     const float s_dc = A.lr[4] * ibc1, s_rest = A.lr[5] * ibc1;
     if (rows == 32)
         adam_sh_block<K3, kRow, true>(s_sh[warp], s_dsh[warp], A.sh + g0 * K3, A.m[4] + g0 * K3,
-                                      A.v[4] + g0 * K3, rows, lane, s_dc, s_rest, A.b1, A.b2, A.eps, ibc2);
+                                      A.v[4] + g0 * K3, rows, lane, s_dc, s_rest, A.b1, A.b2, A.eps, ibc2, upd);
     else
         adam_sh_block<K3, kRow, false>(s_sh[warp], s_dsh[warp], A.sh + g0 * K3, A.m[4] + g0 * K3,
-                                       A.v[4] + g0 * K3, rows, lane, s_dc, s_rest, A.b1, A.b2, A.eps, ibc2);
+                                       A.v[4] + g0 * K3, rows, lane, s_dc, s_rest, A.b1, A.b2, A.eps, ibc2, upd);
 }
 
 template <int D, bool kPose>
@@ -800,10 +816,18 @@ static void launch_preprocess(const gs_plan *plan, void *ws, const gs_params *pr
 template <int D, bool kAdam>
 static void launch_preprocess_bwd(const ViewsDev &vd, const PbArgs &A, cudaStream_t s) {
     const unsigned blocks = (unsigned)((A.n + kPbWarps * 32 - 1) / (kPbWarps * 32));
-    if (A.pose_acc)
-        k_preprocess_bwd<D, kAdam, true><<<blocks, kPbWarps * 32, 0, s>>>(vd, A);
-    else
-        k_preprocess_bwd<D, kAdam, false><<<blocks, kPbWarps * 32, 0, s>>>(vd, A);
+    const bool vis = kAdam && A.visible_only;
+    if (A.pose_acc) {
+        if (vis)
+            k_preprocess_bwd<D, kAdam, true, kAdam><<<blocks, kPbWarps * 32, 0, s>>>(vd, A);
+        else
+            k_preprocess_bwd<D, kAdam, true, false><<<blocks, kPbWarps * 32, 0, s>>>(vd, A);
+    } else {
+        if (vis)
+            k_preprocess_bwd<D, kAdam, false, kAdam><<<blocks, kPbWarps * 32, 0, s>>>(vd, A);
+        else
+            k_preprocess_bwd<D, kAdam, false, false><<<blocks, kPbWarps * 32, 0, s>>>(vd, A);
+    }
 }
 
 static PbArgs pb_args(const gs_plan *plan, void *ws, const gs_params *pr) {
@@ -885,6 +909,7 @@ int preprocess_bwd_adam(const gs_plan *plan, void *ws, gs_params *params, const 
     A.b2 = hp->b2;
     A.eps = hp->eps;
     A.d_step = d_step;
+    A.visible_only = hp->visible_only != 0;
     int rc = adam_tick(d_step, s);
     if (rc) return rc;
     dispatch_preprocess_bwd<true>(plan->sh_degree, vd, A, s);

@@ -73,18 +73,25 @@ class Trainer:
     def __init__(self, params: Gaussians, width: int | None = None, height: int | None = None, *,
                  lam: float = 0.2, bg=(0.0, 0.0, 0.0), lrs: dict | None = None,
                  inst_capacity: int | None = None, load_balanced: bool = True, disp_weight: float = 0.0,
-                 tuning: dict | None = None, fused_adam: bool = True, pose: dict | None = None, device="cuda"):
+                 tuning: dict | None = None, fused_adam: bool = True, pose: dict | None = None,
+                 visible_adam: bool = False, device="cuda"):
         """tuning: launch shapes of the plans ({"bucket": 32 | 64,
         "bwd_warps": 2 | 4 | 8}), e.g. from autotune.autotune.
         fused_adam: apply Adam inside the preprocess backward
         (gs_preprocess_bwd_adam) instead of storing the gradient and running
         a separate Adam pass; self.grads then stays zero.
+        visible_adam: with fused_adam, the sparse Adam that updates only the
+        Gaussians that touched a tile in the step's views (the others keep
+        their parameters and moments).
         pose: enable the global pose refinement ({"every", "lr_rot",
         "lr_trans"}, missing keys from default_pose()); the correction is in
         self.pose (a PoseState) and applies to every view this trainer
         renders."""
         self.params = params
         self.fused_adam = bool(fused_adam)
+        self.visible_adam = bool(visible_adam)
+        if self.visible_adam and not self.fused_adam:
+            raise ValueError("visible-only Adam runs inside the fused preprocess backward")
         self.STAGES = self.STAGES_FUSED if self.fused_adam else self.STAGES_UNFUSED
         self.tuning = dict(tuning or {})
         self.grads = params.zeros_like()
@@ -147,7 +154,7 @@ class Trainer:
         groups.append({"p": p.sh, "g": g.sh, "m": m.sh, "v": v.sh, "lr": self.lrs["sh_rest"],
                        "period": 3 * K, "head": 3, "lr_head": self.lrs["sh_dc"]})
         self._adam = adam_groups_array(groups)
-        self._hp = adam_hparams(self.lrs)
+        self._hp = adam_hparams(self.lrs, visible_only=getattr(self, "visible_adam", False))
         self._pstruct = p.struct()
         self._gstruct = g.struct()
         self._mstruct = m.struct()

@@ -182,3 +182,64 @@ def test_fused_preprocess_backward_adam_equals_unfused(gs):
         for k in range(1, 3):
             for t_u, t_f in zip(unf[k].tensors(), fused[k].tensors()):
                 t_u.copy_(t_f)
+
+
+def test_visible_only_adam_matches_oracle(gs):
+    """The fused update in its visible-only form against the oracle's sparse
+    Adam over two steps: a third of the Gaussians sit far above the ring of
+    views, so they touch no tile and must keep their parameters and moments
+    bit for bit; the others follow the oracle's Adam."""
+    from oracle import binning as obin
+    from oracle import preprocess as opre
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import Trainer, default_lrs
+
+    scene, cams, targets, dts = _batch()
+    scene = scene.copy()
+    scene.means[::3] += np.array([0.0, -60.0, 0.0], dtype=np.float32)
+    tgt, tdisp = _flat(targets), _flat(dts)
+    lrs = default_lrs()
+    tr = Trainer(api.Gaussians.from_scene(scene), lam=0.2, disp_weight=0.1, lrs=lrs, inst_capacity=1 << 20,
+                 visible_adam=True)
+    tr.ensure_capacity([cams])
+    names = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    p0 = {k: to_np(getattr(tr.params, k)).copy() for k in names}
+    st = ostep.new_state(synth.Scene(*(a.astype(np.float64) for a in scene.arrays()), sh_degree=scene.sh_degree))
+    for it in range(2):
+        sc = ostep.scene_from_state(st, scene)
+        # visibility as the binning defines it: some tile of some view within
+        # the level set; Gaussians within the binning's widening of it are
+        # ambiguous and compared loosely
+        vis, amb = np.zeros(scene.n, bool), np.zeros(scene.n, bool)
+        for cam in cams:
+            rec = opre.pack_for_render(opre.project(opre.params_from_scene(sc), cam, sc.sh_degree))
+            for gid, (ids, mq, t) in obin.tile_min_q(rec, cam.width, cam.height).items():
+                vis[gid] |= bool(np.any(mq <= t))
+                amb[gid] |= bool(np.any(mq <= t * (1 + 2.0 ** -9) + 2.0 ** -11)) and not np.any(mq <= t)
+        _, g = ostep.forward_backward_batch(sc, cams, targets, bg=BG, lam=0.2, disp_targets=dts, disp_weight=0.1)
+        st["step"] += 1
+        gsplit = ostep._split(g)
+        for k in ostep.GROUPS:
+            st["params"][k], st["m"][k], st["v"][k] = oadam.adam_step_visible(
+                st["params"][k], gsplit[k], st["m"][k], st["v"][k], st["step"], lrs[k], vis)
+        tr.step(cams, tgt, tdisp)
+    torch.cuda.synchronize()
+    assert tr.slot_for(cams).plan.status()["rc"] == 0
+    hidden = ~vis & ~amb
+    assert hidden.sum() >= scene.n // 3 - 2
+    ref = {"means": st["params"]["means"], "log_scales": st["params"]["log_scales"], "quats": st["params"]["quats"],
+           "opacity_logits": st["params"]["opacity_logits"],
+           "sh": np.concatenate([st["params"]["sh_dc"], st["params"]["sh_rest"]], axis=1)}
+    for k in names:
+        got = to_np(getattr(tr.params, k)).reshape(ref[k].shape)
+        base = p0[k].reshape(ref[k].shape)
+        # never-visible Gaussians: untouched, bit for bit, moments still zero
+        np.testing.assert_array_equal(got[hidden], base[hidden], err_msg=k)
+        for mom in (tr.m, tr.v):
+            assert not np.any(to_np(getattr(mom, k)).reshape(ref[k].shape)[hidden]), k
+        # the others follow the oracle (a gradient that cancels to a few ulps
+        # may take either sign in Adam's first steps)
+        live = vis & ~amb
+        off = np.abs(got[live] - ref[k][live]) > 1e-5 * np.maximum(1.0, np.abs(ref[k][live]))
+        assert off.mean() < 0.01, (k, off.mean())
+        assert np.abs(got[live] - ref[k][live]).max() <= 2.5 * max(lrs.values()) * 2, k

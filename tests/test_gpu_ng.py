@@ -92,8 +92,14 @@ def test_ng_decode_backward_matches_oracle(gs, n_anchors):
     cg = api.Gaussians(*(torch.from_numpy(cg_np[k]).cuda() for k in
                          ("means", "log_scales", "quats", "opacity_logits", "sh")), 0)
     grads = ng.zeros_like()
+    cg2 = api.Gaussians(*(t.clone() for t in cg.tensors()), 0)
     api.gs_ng_decode_bwd(ng, cam, cg, grads, ws)
     assert api.gs_ng_status(ws) == 0
+    # the sums over anchors run in a fixed order: a second run is bit-identical
+    grads2 = ng.zeros_like()
+    api.gs_ng_decode_bwd(ng, cam, cg2, grads2, ws)
+    for k in ("feat", "anchor_ls", "w1", "b1", "w2", "b2"):
+        assert torch.equal(getattr(grads, k), getattr(grads2, k)), k
     ref = ong.decode_backward(cache, {k: v.astype(np.float64) for k, v in cg_np.items()})
     # backward roundings: a dL/dy element within the float32 error of a
     # bfloat16 midpoint may round one step differently; that step moves dL/dh

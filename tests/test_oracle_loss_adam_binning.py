@@ -109,6 +109,38 @@ def test_adam_matches_torch_optim():
     np.testing.assert_allclose(p, pt.detach().numpy(), rtol=1e-12, atol=1e-15)
 
 
+def test_visible_adam_matches_torch_sparse_adam():
+    """torch.optim.SparseAdam updates only the rows present in a sparse
+    gradient, with the global step count: the same rule, up to where eps
+    enters the denominator (negligible at eps = 1e-30, where both coincide)."""
+    rng = np.random.default_rng(4)
+    n, d = 40, 3
+    p0 = rng.standard_normal((n, d))
+    pt = torch.nn.Parameter(torch.as_tensor(p0.copy()))
+    opt = torch.optim.SparseAdam([pt], lr=2e-3, betas=(0.9, 0.999), eps=1e-30)
+    p, m, v = p0.copy(), np.zeros((n, d)), np.zeros((n, d))
+    for k in range(1, 6):
+        vis = rng.uniform(size=n) < 0.6
+        g = rng.standard_normal((n, d)) * vis[:, None]
+        rows = np.nonzero(vis)[0]
+        pt.grad = torch.sparse_coo_tensor(torch.as_tensor(rows[None]), torch.as_tensor(g[rows]), (n, d))
+        opt.step()
+        p, m, v = adam.adam_step_visible(p, g, m, v, k, lr=2e-3, visible=vis, eps=1e-30)
+    np.testing.assert_allclose(p, pt.detach().numpy(), rtol=1e-12, atol=1e-15)
+
+
+def test_visible_adam_special_cases():
+    rng = np.random.default_rng(5)
+    p0, g = rng.standard_normal((9, 4)), rng.standard_normal((9, 4))
+    m0, v0 = rng.standard_normal((9, 4)), rng.uniform(0.1, 1.0, (9, 4))
+    everyone = adam.adam_step_visible(p0, g, m0, v0, 3, 1e-2, np.ones(9, bool))
+    for a, b in zip(everyone, adam.adam_step(p0, g, m0, v0, 3, 1e-2)):
+        np.testing.assert_array_equal(a, b)
+    nobody = adam.adam_step_visible(p0, g, m0, v0, 3, 1e-2, np.zeros(9, bool))
+    for a, b in zip(nobody, (p0, m0, v0)):
+        np.testing.assert_array_equal(a, b)
+
+
 # ------------------------------------------------------------------ binning
 
 def test_min_q_over_rectangle_matches_dense_sampling():
