@@ -109,6 +109,21 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// Expect `bytes` of bulk-copy transactions on the mbarrier (one arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to this CTA's shared memory, completing on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -171,6 +186,7 @@ struct Args {
     // backward inputs (children's gradients) and outputs
     float *g_means, *g_ls, *g_quats, *g_logits, *g_sh;
     int zero_g;  // zero the children's gradients after reading them
+    int grads_bulk;  // the children's gradient arrays start 16-byte aligned (bulk copies)
     int feat_vec;  // feat and d_feat are 16-byte aligned (float4 rows)
     float *d_feat, *d_ls, *partial;
     int *err;
@@ -406,11 +422,13 @@ cleanup:
 struct BwdSmem {
     __nv_bfloat16 W2T[kHid * kOutPad];   // dh B (N = 32, K = 144)
     __nv_bfloat16 W1T[kInPad * kHid];    // dx B (N = 48, K = 32)
+    // DY, DYT2 and DYT first hold the tile's children's gradients (copied
+    // in while y is recomputed); the A operands with fewer than 128 rows
+    // (DYT2, XT) read their missing rows from the buffers after them
     __nv_bfloat16 DY[kTileA * kOutPad];  // dh A (M = 128 anchors, K = 144)
-    // the next three are read as 128-row A operands of K = 128 anchors
     __nv_bfloat16 DYT2[16 * kTileA];     // dW2 A, outputs 128..143 (+112 rows read past the end)
-    __nv_bfloat16 XT[kInPad * kTileA];   // dW1^T A, inputs 0..47 (+80 rows read past the end)
     __nv_bfloat16 DYT[kTileA * kTileA];  // dW2 A, outputs 0..127
+    __nv_bfloat16 XT[kInPad * kTileA];   // dW1^T A, inputs 0..47 (+80 rows read past the end)
     __nv_bfloat16 HT[kHid * kTileA];     // dW2 B (N = 32 hidden, K = 128 anchors)
     union {
         struct {
@@ -426,14 +444,18 @@ struct BwdSmem {
     float xyz[kTileA][3], ls[kTileA][6], dls[kTileA][6];
     float db1w[kThreads / 32][kHid];  // per-warp sums of db1
     float b2[kOutPad];
-    uint64_t mbar;
+    uint64_t mbar, gbar;  // MMA completion; children's gradients copied in
     uint32_t tmem;
     int fail;
 };
 
-static_assert(sizeof(BwdSmem::DYT) >= sizeof(float) * kTileA * kChild * 6, "log-scale terms fit the dW2 operand");
-static_assert(offsetof(BwdSmem, DYT2) + 2 * kTileA * kTileA <= offsetof(BwdSmem, u), "dW2 tail operand rows");
-static_assert(offsetof(BwdSmem, XT) + 2 * kTileA * kTileA <= offsetof(BwdSmem, u), "dW1 operand rows");
+// staged children's gradients (floats from the start of DY): means, SH DC,
+// log-scales (3 per child), quaternions (4), opacity logits (1)
+constexpr int kStM = 0, kStS = kTileA * kChild * 3, kStL = 2 * kStS, kStQ = 3 * kStS;
+constexpr int kStO = kStQ + kTileA * kChild * 4, kStEnd = kStO + kTileA * kChild;
+static_assert(offsetof(BwdSmem, DY) + 4 * kStEnd <= offsetof(BwdSmem, XT), "children's gradients fit the staging");
+static_assert(offsetof(BwdSmem, DYT2) + 2 * kTileA * kTileA <= sizeof(BwdSmem), "dW2 tail operand rows");
+static_assert(offsetof(BwdSmem, XT) + 2 * kTileA * kTileA <= sizeof(BwdSmem), "dW1 operand rows");
 
 __device__ __forceinline__ float bf16f(__nv_bfloat16 v) { return __bfloat162float(v); }
 
@@ -447,21 +469,36 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     const int na = (int)min((int64_t)kTileA, A.n - a0);
     float *part = A.partial + (size_t)blockIdx.x * kPartial;
 
-    if (warp == 1 && lane < 5) {
-        // ask L2 for this tile's children's gradients (five contiguous
-        // ranges, read only after the y recompute) while the operands load
-        const int nch = na * kChild;
-        const float *base = lane == 0 ? A.g_means + 3 * a0 * kChild : lane == 1 ? A.g_sh + 3 * a0 * kChild
-                          : lane == 2 ? A.g_ls + 3 * a0 * kChild : lane == 3 ? A.g_quats + 4 * a0 * kChild
-                                                                               : A.g_logits + a0 * kChild;
-        const uint32_t bytes = (uint32_t)(nch * (lane == 3 ? 16 : lane == 4 ? 4 : 12)) & ~15u;
-        if (bytes > 0 && ((uintptr_t)base & 15) == 0)
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base), "r"(bytes) : "memory");
-    }
     if (warp == 0) tmem_alloc(&S.tmem, kTmemCols);
+    // the tile's children's gradients into shared memory: five bulk copies
+    // that run while the operands load and y is recomputed (a partial last
+    // tile or unaligned arrays take plain loads instead)
+    float *stg = reinterpret_cast<float *>(S.DY);
+    const int nch = na * kChild;
+    const int64_t c0 = a0 * kChild;
+    const bool bulk = A.grads_bulk && na == kTileA;
     if (tid == 0) {
         mbar_init(&S.mbar, 1);
+        mbar_init(&S.gbar, 1);
         S.fail = 0;
+        if (bulk) {
+            constexpr uint32_t b3 = kTileA * kChild * 3 * 4, b4 = kTileA * kChild * 4 * 4, b1 = kTileA * kChild * 4;
+            mbar_expect_tx(&S.gbar, 3 * b3 + b4 + b1);
+            bulk_g2s(stg + kStM, A.g_means + 3 * c0, b3, &S.gbar);
+            bulk_g2s(stg + kStS, A.g_sh + 3 * c0, b3, &S.gbar);
+            bulk_g2s(stg + kStL, A.g_ls + 3 * c0, b3, &S.gbar);
+            bulk_g2s(stg + kStQ, A.g_quats + 4 * c0, b4, &S.gbar);
+            bulk_g2s(stg + kStO, A.g_logits + c0, b1, &S.gbar);
+        }
+    }
+    if (!bulk) {
+        for (int i = tid; i < nch * 3; i += kThreads) {
+            stg[kStM + i] = A.g_means[3 * c0 + i];
+            stg[kStS + i] = A.g_sh[3 * c0 + i];
+            stg[kStL + i] = A.g_ls[3 * c0 + i];
+        }
+        for (int i = tid; i < nch * 4; i += kThreads) stg[kStQ + i] = A.g_quats[4 * c0 + i];
+        for (int i = tid; i < nch; i += kThreads) stg[kStO + i] = A.g_logits[c0 + i];
     }
     {
         // h of this anchor into the y GEMM's A (row = anchor) and the dW2
@@ -524,80 +561,63 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     }
     tc_fence_before();
     __syncthreads();
-    {
-        // dL/dy from the children's gradients, in place of y (every element
-        // depends on its own y only).  Each child's six terms of its anchor's
-        // log-scale gradients are parked in the (not yet used) dW2 operand
-        // buffer and summed per anchor afterwards, children in order.
-        float *lsterm = reinterpret_cast<float *>(S.DYT);  // [child][6]
-        const int nch = na * kChild;
-        const int64_t c0 = a0 * kChild;
-        // the children's gradients are read four strides ahead of their use
-        // so that the loads overlap
-        constexpr int kU = 4;
-        for (int i0 = tid; i0 < nch * 3; i0 += kU * kThreads) {
-            float gm[kU], gs[kU], gl[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int i = i0 + u * kThreads;
-                const bool in = i < nch * 3;
-                gm[u] = in ? A.g_means[3 * c0 + i] : 0.0f;
-                gs[u] = in ? A.g_sh[3 * c0 + i] : 0.0f;
-                gl[u] = in ? A.g_ls[3 * c0 + i] : 0.0f;
+    if (bulk && !mbar_wait(&S.gbar, 0)) S.fail = 1;
+    __syncthreads();
+    if (S.fail) goto cleanup;
+    if (A.zero_g) {
+        // the children's gradients are consumed: clear them (coalesced)
+        if (bulk) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = tid; i < nch * 3 / 4; i += kThreads) {
+                reinterpret_cast<float4 *>(A.g_means + 3 * c0)[i] = z;
+                reinterpret_cast<float4 *>(A.g_sh + 3 * c0)[i] = z;
+                reinterpret_cast<float4 *>(A.g_ls + 3 * c0)[i] = z;
             }
-            if (A.zero_g) {
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const int i = i0 + u * kThreads;
-                    if (i < nch * 3) {
-                        A.g_means[3 * c0 + i] = 0.0f;
-                        A.g_sh[3 * c0 + i] = 0.0f;
-                        A.g_ls[3 * c0 + i] = 0.0f;
-                    }
-                }
+            for (int i = tid; i < nch; i += kThreads) reinterpret_cast<float4 *>(A.g_quats + 4 * c0)[i] = z;
+            for (int i = tid; i < nch / 4; i += kThreads) reinterpret_cast<float4 *>(A.g_logits + c0)[i] = z;
+        } else {
+            for (int i = tid; i < nch * 3; i += kThreads) {
+                A.g_means[3 * c0 + i] = 0.0f;
+                A.g_sh[3 * c0 + i] = 0.0f;
+                A.g_ls[3 * c0 + i] = 0.0f;
             }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int i = i0 + u * kThreads;
-                if (i >= nch * 3) break;
-                const int ch = i / 3, j = i - 3 * ch, r = ch / kChild, c = ch - r * kChild;
-                float &y0 = S.Y[r][c * kPer + j];
-                const float th = tanhf(y0), so = expf(S.ls[r][j]);
-                lsterm[6 * ch + j] = gm[u] * th * so;
-                y0 = gm[u] * so * (1.0f - th * th);
-                float &y4 = S.Y[r][c * kPer + 4 + j];
-                const float rgb = sigmoidf_(y4);
-                y4 = gs[u] * kDcScale * rgb * (1.0f - rgb);
-                float &y7 = S.Y[r][c * kPer + 7 + j];
-                lsterm[6 * ch + 3 + j] = gl[u];
-                y7 = gl[u] * sigmoidf_(-y7);
-            }
+            for (int i = tid; i < nch * 4; i += kThreads) A.g_quats[4 * c0 + i] = 0.0f;
+            for (int i = tid; i < nch; i += kThreads) A.g_logits[c0 + i] = 0.0f;
         }
-        for (int i = tid; i < nch * 4; i += kThreads) {
-            const int ch = i >> 2, j = i & 3, r = ch / kChild, c = ch - r * kChild;
-            S.Y[r][c * kPer + 10 + j] = A.g_quats[4 * c0 + i];
-            if (A.zero_g) A.g_quats[4 * c0 + i] = 0.0f;
-        }
-        for (int ch = tid; ch < nch; ch += kThreads) {
-            const int r = ch / kChild, c = ch - r * kChild;
-            float &y3 = S.Y[r][c * kPer + 3];
-            const float o = tanhf(y3);
+    }
+    if (tid < na) {
+        // dL/dy of this anchor's children in place of y (every element
+        // depends on its own y only), and the anchor's log-scale gradients,
+        // children in order
+        float *yr = S.Y[tid];
+        float so[3], dl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) so[j] = expf(S.ls[tid][j]);
+#pragma unroll 2
+        for (int c = 0; c < kChild; ++c) {
+            const int ch = tid * kChild + c;
+            float *u = yr + c * kPer;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float gm = stg[kStM + 3 * ch + j], gs = stg[kStS + 3 * ch + j], gl = stg[kStL + 3 * ch + j];
+                const float th = tanhf(u[j]);
+                dl[j] += gm * th * so[j];
+                u[j] = gm * so[j] * (1.0f - th * th);
+                const float rgb = sigmoidf_(u[4 + j]);
+                u[4 + j] = gs * kDcScale * rgb * (1.0f - rgb);
+                dl[3 + j] += gl;
+                u[7 + j] = gl * sigmoidf_(-u[7 + j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) u[10 + j] = stg[kStQ + 4 * ch + j];
+            const float o = tanhf(u[3]);
             const float oc = fminf(o, kOpacityCeil);
-            y3 = (o > 0.0f && o < kOpacityCeil) ? A.g_logits[c0 + ch] / (oc * (1.0f - oc)) * (1.0f - o * o) : 0.0f;
-            if (A.zero_g) A.g_logits[c0 + ch] = 0.0f;
+            u[3] = (o > 0.0f && o < kOpacityCeil) ? stg[kStO + ch] / (oc * (1.0f - oc)) * (1.0f - o * o) : 0.0f;
         }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) S.dls[tid][k] = dl[k];
     }
     __syncthreads();
-    if (tid < na) {
-        const float *t = reinterpret_cast<const float *>(S.DYT) + 6 * kChild * tid;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            float sum = 0.0f;
-#pragma unroll
-            for (int c = 0; c < kChild; ++c) sum += t[6 * c + k];
-            S.dls[tid][k] = sum;
-        }
-    }
     // db2 (unrounded dy of the present anchors)
     for (int o = tid; o < kOut; o += kThreads) {
         float s = 0.0f;
@@ -742,10 +762,12 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     }
 cleanup:
     if (S.fail) {
-        // give the tensor cores one more bounded wait before the memory goes
+        // give the tensor cores and the copies one more bounded wait before
+        // the memory goes
         if (tid == 0) atomicCAS(A.err, 0, GS_ERR_TIMEOUT);
         mbar_wait(&S.mbar, 0);
         mbar_wait(&S.mbar, 1);
+        if (bulk) mbar_wait(&S.gbar, 0);
     }
     tc_fence_before();
     __syncthreads();
@@ -912,6 +934,8 @@ extern "C" int gs_ng_decode_bwd(const gs_ng_params *p, const gs_camera *cam, con
     A.g_logits = child_grads->opacity_logits;
     A.g_sh = child_grads->sh;
     A.zero_g = zero_child_grads != 0;
+    A.grads_bulk = ((((uintptr_t)A.g_means) | ((uintptr_t)A.g_ls) | ((uintptr_t)A.g_quats) |
+                     ((uintptr_t)A.g_logits) | ((uintptr_t)A.g_sh)) & 15) == 0;
     A.d_feat = grads->feat;
     A.feat_vec = A.feat_vec && ((uintptr_t)grads->feat & 15) == 0;
     A.d_ls = grads->anchor_ls;
