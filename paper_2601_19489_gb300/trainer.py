@@ -138,6 +138,10 @@ class Trainer:
     def rgb(self):
         return self._default.rgb
 
+    @property
+    def disp(self):
+        return self._default.disp
+
     def slot_for(self, cams) -> _Slot:
         return self._slot(tuple((int(c.width), int(c.height)) for c in _as_list(cams)))
 

@@ -149,3 +149,12 @@ def test_pose_entry_points_check_arguments_on_the_host(lib):
     assert L.GS_POSE_STATE_DOUBLES == 32 + 8 * L.GS_POSE_SLOTS
     hdr = open(os.path.join(ROOT, "include", "gs.h")).read()
     assert re.search(r"#define GS_POSE_SLOTS %d\b" % L.GS_POSE_SLOTS, hdr)
+
+
+def test_trainer_exposes_the_default_views_buffers():
+    """The default view's image buffers are reachable from the trainer (the
+    smoke check and the tests read them)."""
+    from paper_2601_19489_gb300.trainer import Trainer
+
+    for name in ("plan", "rgb", "disp"):
+        assert isinstance(getattr(Trainer, name), property), name
