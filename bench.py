@@ -239,6 +239,37 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------ GPU arm
 
+def stage_roofline(stage_ms: dict, n: int, sh_degree: int, pixels: int, instances: float, pairs: float,
+                   hbm_gbs: float) -> dict:
+    """Each stage's achieved rate against its bound, from the algorithmic
+    work per unit (parameters of P = 4 (11 + 3 K) bytes per Gaussian):
+      preprocess    P read + 76 B of records written per Gaussian      (HBM)
+      bin_sort      depth sort 4 x 20 B and counts 72 B per Gaussian;
+                    key write 8 B, tile sort 2 x 20 B and ranges 8 B
+                    per instance                                       (HBM)
+      render_fwd    25 FLOP per pixel-splat pair                       (FP32)
+      loss          48 B per pixel                                     (HBM)
+      render_bwd    62 FLOP per pixel-splat pair                       (FP32)
+      fused bwd     2 P parameters + 4 P moments per Gaussian          (HBM)
+    Pairs are counted up to each pixel's last contributor."""
+    P = 4 * (11 + 3 * (sh_degree + 1) ** 2)
+    work = {"preprocess": ("hbm", (P + 76) * n), "bin_sort": ("hbm", 152 * n + 56 * instances),
+            "render_fwd": ("alu", 25 * pairs), "loss": ("hbm", 48 * pixels),
+            "render_bwd_blend": ("alu", 62 * pairs), "preprocess_bwd_adam": ("hbm", 6 * P * n)}
+    out = {}
+    for name, (bound, w) in work.items():
+        if name not in stage_ms or stage_ms[name] <= 0:
+            continue
+        sec = stage_ms[name] / 1e3
+        if bound == "hbm":
+            ach = w / sec / 1e9
+            out[name] = {"bound": "hbm", "achieved": ach, "unit": "GB/s", "frac": ach / hbm_gbs}
+        else:
+            ach = w / sec / 1e12
+            out[name] = {"bound": "alu", "achieved": ach, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS}
+    return out
+
+
 def kernels_per_step(trainer) -> int:
     tile_passes = -(-trainer.plan_tile_bits // 8)
     loss_k = 3 if trainer.lam > 0 else 2
@@ -397,6 +428,8 @@ def run_ours(args, rank, world):
             "gpu_launches": kernels_per_step(trainer) * args.steps,
             "roofline": roof,
             "stages_ms": stage_ms,
+            "stages_roofline": stage_roofline(stage_ms, args.n, 3, args.width * args.height, st2["n_instances"],
+                                              mean_pairs, hbm or FALLBACK_HBM_GBS),
             "work": {"instances_max": worst, "instances_last": st2["n_instances"],
                      "buckets_last": st2["n_buckets"], "pairs_per_view": mean_pairs},
             "peaks": {"hbm_gbs": hbm or FALLBACK_HBM_GBS, "hbm_source": "measured" if hbm else "fallback",

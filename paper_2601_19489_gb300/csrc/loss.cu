@@ -19,6 +19,9 @@ namespace gs {
 constexpr int kSsimT = 32;              // output tile edge
 constexpr int kHalo = 5;                // window radius
 constexpr int kSsimIn = kSsimT + 2 * kHalo;  // 42
+// 11 warps: the horizontal pass (42 rows x 8 groups of 4 outputs = 336
+// items) and the vertical pass (256 items) each take one round
+constexpr int kSsimThreads = 352;
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
@@ -43,14 +46,14 @@ __device__ __forceinline__ bool plane_geom(const Planes &pl, int z, int *W, int 
     return (int)blockIdx.x * kSsimT < *W && (int)blockIdx.y * kSsimT < *H;
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSsimThreads)
 k_ssim_fwd(Planes pl, Window win, const float *__restrict__ x, const float *__restrict__ y,
            float *__restrict__ maps, int64_t plane_stride, float *__restrict__ part_s,
            float *__restrict__ part_l1) {
     __shared__ float X[kSsimIn][kSsimIn + 1];
     __shared__ float Yv[kSsimIn][kSsimIn + 1];
     __shared__ float Hs[5][kSsimIn][kSsimT + 1];
-    __shared__ float red[2][8];
+    __shared__ float red[2][kSsimThreads / 32];
     int W, H;
     int64_t base;
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -63,7 +66,7 @@ k_ssim_fwd(Planes pl, Window win, const float *__restrict__ x, const float *__re
         return;
     }
     const int ox = blockIdx.x * kSsimT - kHalo, oy = blockIdx.y * kSsimT - kHalo;
-    for (int i = tid; i < kSsimIn * kSsimIn; i += 256) {
+    for (int i = tid; i < kSsimIn * kSsimIn; i += kSsimThreads) {
         const int r = i / kSsimIn, c = i - r * kSsimIn;
         const int gx = ox + c, gy = oy + r;
         float a = 0.f, b = 0.f;
@@ -78,7 +81,7 @@ k_ssim_fwd(Planes pl, Window win, const float *__restrict__ x, const float *__re
     // horizontal pass: a thread blurs 4 adjacent outputs of a row from 14
     // loaded inputs (register blocking: each input and its products are
     // read once for 4 outputs)
-    for (int i = tid; i < kSsimIn * (kSsimT / 4); i += 256) {
+    for (int i = tid; i < kSsimIn * (kSsimT / 4); i += kSsimThreads) {
         const int r = i / (kSsimT / 4), c0 = 4 * (i - r * (kSsimT / 4));
         float s[5][4];
 #pragma unroll
@@ -107,7 +110,7 @@ k_ssim_fwd(Planes pl, Window win, const float *__restrict__ x, const float *__re
     float acc_s = 0.f, acc_l1 = 0.f;
     const int64_t npl = (int64_t)W * H;
     // vertical pass: a thread blurs 4 outputs of a column from 14 rows
-    for (int i = tid; i < (kSsimT / 4) * kSsimT; i += 256) {
+    for (int i = tid; i < (kSsimT / 4) * kSsimT; i += kSsimThreads) {
         const int r0 = 4 * (i / kSsimT), c = i - (i / kSsimT) * kSsimT;
         float s[5][4];
 #pragma unroll
@@ -164,7 +167,7 @@ k_ssim_fwd(Planes pl, Window win, const float *__restrict__ x, const float *__re
     __syncthreads();
     if (tid == 0) {
         float a = 0.f, b = 0.f;
-        for (int w = 0; w < 8; ++w) {
+        for (int w = 0; w < kSsimThreads / 32; ++w) {
             a += red[0][w];
             b += red[1][w];
         }
@@ -173,7 +176,7 @@ k_ssim_fwd(Planes pl, Window win, const float *__restrict__ x, const float *__re
     }
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSsimThreads)
 k_ssim_bwd(Planes pl, Window win, const float *__restrict__ x, const float *__restrict__ y,
            const float *__restrict__ maps, int64_t plane_stride, float c_l1, float c_ssim,
            float *__restrict__ grad) {
@@ -184,7 +187,7 @@ k_ssim_bwd(Planes pl, Window win, const float *__restrict__ x, const float *__re
     if (!plane_geom(pl, blockIdx.z, &W, &H, &base)) return;
     const int tid = threadIdx.x;
     const int ox = blockIdx.x * kSsimT - kHalo, oy = blockIdx.y * kSsimT - kHalo;
-    for (int i = tid; i < kSsimIn * kSsimIn; i += 256) {
+    for (int i = tid; i < kSsimIn * kSsimIn; i += kSsimThreads) {
         const int r = i / kSsimIn, c = i - r * kSsimIn;
         const int gx = ox + c, gy = oy + r;
         float a = 0.f, b = 0.f, d = 0.f;
@@ -200,7 +203,7 @@ k_ssim_bwd(Planes pl, Window win, const float *__restrict__ x, const float *__re
     }
     __syncthreads();
     // the same two register-blocked passes as the forward, over 3 maps
-    for (int i = tid; i < kSsimIn * (kSsimT / 4); i += 256) {
+    for (int i = tid; i < kSsimIn * (kSsimT / 4); i += kSsimThreads) {
         const int r = i / (kSsimT / 4), c0 = 4 * (i - r * (kSsimT / 4));
         float s[3][4];
 #pragma unroll
@@ -225,7 +228,7 @@ k_ssim_bwd(Planes pl, Window win, const float *__restrict__ x, const float *__re
             for (int o = 0; o < 4; ++o) Hs[q][r][c0 + o] = s[q][o];
     }
     __syncthreads();
-    for (int i = tid; i < (kSsimT / 4) * kSsimT; i += 256) {
+    for (int i = tid; i < (kSsimT / 4) * kSsimT; i += kSsimThreads) {
         const int r0 = 4 * (i / kSsimT), c = i - (i / kSsimT) * kSsimT;
         float s[3][4];
 #pragma unroll
@@ -374,8 +377,8 @@ extern "C" int gs_loss(const gs_plan *plan, const float *rgb, const float *targe
             pl.off[v] = plan->pix_off[v];
         }
         const Window win = make_window();
-        k_ssim_fwd<<<grid, 256, 0, s>>>(pl, win, rgb, target, maps, n3, part_s, part_l1);
-        k_ssim_bwd<<<grid, 256, 0, s>>>(pl, win, rgb, target, maps, n3, (float)((1.0 - lambda) * inv3p),
+        k_ssim_fwd<<<grid, kSsimThreads, 0, s>>>(pl, win, rgb, target, maps, n3, part_s, part_l1);
+        k_ssim_bwd<<<grid, kSsimThreads, 0, s>>>(pl, win, rgb, target, maps, n3, (float)((1.0 - lambda) * inv3p),
                                         (float)(-lambda * inv3p), dL_drgb);
         n_s = nblk;
         n_l1 = nblk;

@@ -244,3 +244,46 @@ def test_trainer_recovers_a_camera_side_error(gs, graphed):
     e1 = _reprojection_px(means, base, train, R, t)
     assert e1 < 0.2 * e0, (e0, e1)
     np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-12)
+
+
+def test_pose_state_survives_checkpoint_and_densification(gs, tmp_path):
+    """The pose state is part of a checkpoint (a resumed run continues with
+    the same correction and losses), and densification, which rebuilds the
+    plans, keeps the correction attached to the new plans."""
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import Trainer
+
+    scene = synth.scene_clustered(5000, seed=3, sh_degree=1)
+    cams = synth.ring_cameras(4, 128, 96)
+    tgts = [torch.from_numpy(synth.target_uniform(50 + i, 128, 96).reshape(-1)).cuda() for i in range(4)]
+    cfg = {"every": 2, "lr_rot": 2e-3, "lr_trans": 2e-3}
+    a = Trainer(api.Gaussians.from_scene(scene), 128, 96, inst_capacity=1 << 20, pose=cfg)
+    for i in range(5):
+        a.step(cams[i % 4], tgts[i % 4])
+    a.save(str(tmp_path / "ckpt.pt"))
+    la = []
+    for i in range(5, 9):
+        a.step(cams[i % 4], tgts[i % 4])
+        la.append(a.loss.item())
+    Ra, ta = a.pose.correction()
+    b = Trainer(api.Gaussians.from_scene(synth.scene_clustered(5000, seed=4, sh_degree=1)), 128, 96,
+                inst_capacity=1 << 20, pose={"every": 7})
+    b.load(str(tmp_path / "ckpt.pt"))
+    assert b.pose_cfg["every"] == 2 and b.step_count == 5
+    lb = []
+    for i in range(5, 9):
+        b.step(cams[i % 4], tgts[i % 4])
+        lb.append(b.loss.item())
+    np.testing.assert_allclose(lb, la, rtol=1e-4)
+    Rb, tb = b.pose.correction()
+    np.testing.assert_allclose(Rb, Ra, atol=1e-6)
+    np.testing.assert_allclose(tb, ta, atol=1e-6)
+    assert np.abs(Ra - np.eye(3)).max() > 0  # the correction did move
+    # densification rebuilds every plan; the correction stays attached
+    b.densify(cams[:2], tgts[:2], rules={"tau_plus": 0.5, "extent": 4.0})
+    sl = b.slot_for([cams[0]])
+    assert sl.plan.pose is b.pose
+    b.step(cams[0], tgts[0])  # step 10: its gradient is folded in by the update every 2 steps
+    torch.cuda.synchronize()
+    assert b.slot_for([cams[0]]).plan.status()["rc"] == 0
+    assert b.pose.buf[24].item() == b.step_count // 2
