@@ -113,6 +113,7 @@ class Plan:
         self.pixels = int(lib.gs_plan_pixels(self.handle))
         self.ws = torch.empty(self.bytes, dtype=torch.uint8, device=device)
         self.ws.zero_()
+        self.pose = None  # attached pose-refinement state (set_pose)
 
     def __del__(self):
         h = getattr(self, "handle", None)
