@@ -30,7 +30,9 @@
  *  - Gaussian parameters are float32 arrays of n rows: means n x 3,
  *    log_scales n x 3, quats n x 4 as (w, x, y, z), opacity_logits n,
  *    sh n x K x 3 with K = (sh_degree + 1)^2 (coefficient-major per Gaussian,
- *    real spherical harmonics with the Condon-Shortley phase).
+ *    real spherical harmonics with the Condon-Shortley phase).  quats and sh
+ *    (of parameters and of gradients) must start 16-byte aligned: they are
+ *    moved in float4s (GS_ERR_ARG otherwise).
  *  - Gradients are ACCUMULATED (+=) into the caller's gradient arrays, so
  *    several views or calls sum.
  */

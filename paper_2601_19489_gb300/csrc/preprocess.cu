@@ -220,18 +220,62 @@ __device__ __forceinline__ void project_cov(const ViewDev &cam, float3 p, float4
 
 // kPose: the cameras come from `posed` (the pose-corrected copies written by
 // pose_compose) instead of the kernel parameter.
+// A warp whose 32 items are 32 consecutive Gaussians of one view (the rule
+// for one view; every warp when the Gaussian count is a multiple of 32)
+// first moves their SH rows into shared memory with coalesced float4 loads
+// (a row per lane would be 3K strided loads per thread, each touching 32
+// different rows); the others read their rows directly.
+constexpr int kPreThreads = 128;
 template <int D, bool kPose>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kPreThreads)
 k_preprocess(ViewsDev views, const ViewDev *__restrict__ posed, int64_t n, const float *__restrict__ means,
              const float *__restrict__ log_scales, const float4 *__restrict__ quats,
              const float *__restrict__ logits, const float *__restrict__ sh, float4 *__restrict__ rec,
              float2 *__restrict__ bin, uint32_t *__restrict__ touched, uint2 *__restrict__ rects,
              uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval, int box3) {
     constexpr int K = (D + 1) * (D + 1);
+    constexpr int K3 = 3 * K;
+    constexpr int kRow = K3 + 1;  // odd row stride: the lanes' rows fall in different banks
+    constexpr bool kStage = D >= 1;
+    __shared__ float s_sh[kStage ? kPreThreads / 32 : 1][kStage ? 32 * kRow : 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (item >= (int64_t)views.V * n) return;
+    const int64_t total = (int64_t)views.V * n;
+    const float *shrow = nullptr;  // this item's SH row (shared or global memory)
+    if (kStage) {
+        const int64_t item0 = item - lane;
+        const int64_t g0 = item0 % n;
+        // uniform over the warp: whole warp in range, one view, 16-byte aligned block
+        const bool coop = item0 + 31 < total && g0 + 31 < n && ((g0 * K3) & 3) == 0;
+        if (coop) {
+            const float4 *src = reinterpret_cast<const float4 *>(sh + g0 * K3);
+            constexpr int kQ = (32 * K3 / 4 + 31) / 32;  // float4s per lane
+            float4 q[kQ];
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) {
+                const int j = lane + 32 * u;
+                if (j < 8 * K3) q[u] = __ldg(src + j);
+            }
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) {
+                const int j = lane + 32 * u;
+                if (j < 8 * K3) {
+                    const float e[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int i = 4 * j + k, r = i / K3, c = i - r * K3;
+                        s_sh[warp][r * kRow + c] = e[k];
+                    }
+                }
+            }
+            __syncwarp();
+            shrow = &s_sh[warp][lane * kRow];
+        }
+    }
+    if (item >= total) return;
     const int v = (int)(item / n);
     const int64_t g = item - (int64_t)v * n;
+    if (!shrow) shrow = sh + g * K3;
     const ViewDev &cam = kPose ? posed[v] : views.v[v];
     dval[item] = (uint32_t)item;
 
@@ -267,13 +311,12 @@ k_preprocess(ViewsDev views, const ViewDev *__restrict__ posed, int64_t n, const
     dir = mul3(dir, rsqrtf(dot3(dir, dir)));
     float Y[K];
     sh_eval<D>(dir.x, dir.y, dir.z, Y);
-    const float *shg = sh + g * (K * 3);
     float r = 0.5f, gg = 0.5f, bb = 0.5f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        r += Y[k] * __ldg(shg + 3 * k);
-        gg += Y[k] * __ldg(shg + 3 * k + 1);
-        bb += Y[k] * __ldg(shg + 3 * k + 2);
+        r += Y[k] * shrow[3 * k];
+        gg += Y[k] * shrow[3 * k + 1];
+        bb += Y[k] * shrow[3 * k + 2];
     }
     r = fmaxf(r, 0.f);
     gg = fmaxf(gg, 0.f);
@@ -805,8 +848,8 @@ template <int D, bool kPose>
 static void launch_preprocess(const gs_plan *plan, void *ws, const gs_params *pr, const ViewsDev &vd,
                               cudaStream_t s) {
     const int64_t total = plan->VN;
-    const unsigned blocks = (unsigned)((total + 255) / 256);
-    k_preprocess<D, kPose><<<blocks, 256, 0, s>>>(
+    const unsigned blocks = (unsigned)((total + kPreThreads - 1) / kPreThreads);
+    k_preprocess<D, kPose><<<blocks, kPreThreads, 0, s>>>(
         vd, ws_at<ViewDev>(ws, plan->o_posed), plan->n, pr->means, pr->log_scales, (const float4 *)pr->quats, pr->opacity_logits, pr->sh,
         ws_at<float4>(ws, plan->o_rec), ws_at<float2>(ws, plan->o_bin), ws_at<uint32_t>(ws, plan->o_touched),
         ws_at<uint2>(ws, plan->o_rect), ws_at<uint32_t>(ws, plan->o_dkey[0]), ws_at<uint32_t>(ws, plan->o_dval[0]),
@@ -862,7 +905,7 @@ int check_params(const gs_plan *plan, const gs_params *p) {
     if (!p || p->n != plan->n || p->sh_degree != plan->sh_degree || !p->means || !p->log_scales ||
         !p->quats || !p->opacity_logits || !p->sh)
         return GS_ERR_ARG;
-    if (((uintptr_t)p->quats) & 15) return GS_ERR_ARG;  // read as float4
+    if ((((uintptr_t)p->quats) | ((uintptr_t)p->sh)) & 15) return GS_ERR_ARG;  // read as float4 rows / blocks
     return GS_OK;
 }
 

@@ -158,3 +158,27 @@ def test_trainer_exposes_the_default_views_buffers():
 
     for name in ("plan", "rgb", "disp"):
         assert isinstance(getattr(Trainer, name), property), name
+
+
+def test_misaligned_parameter_rows_are_refused_on_the_host(lib):
+    """quats and sh move in float4s: a pointer off a 16-byte boundary is an
+    argument error, reported before anything is enqueued."""
+    from paper_2601_19489_gb300 import _lib as L
+
+    w = (ctypes.c_int32 * 1)(64)
+    h = (ctypes.c_int32 * 1)(48)
+    plan = lib.gs_plan_create(10, 1, 1, w, h, 100)
+    assert plan
+    try:
+        cam = L.GsCamera()
+        cam.fx = cam.fy = 64.0
+        cam.cx, cam.cy, cam.width, cam.height, cam.near_z = 32.0, 24.0, 64, 48, 0.2
+        for bad in ("quats", "sh"):
+            p = L.GsParams()
+            p.n, p.sh_degree = 10, 1
+            p.means, p.log_scales, p.quats, p.opacity_logits, p.sh = 256, 512, 768, 1024, 1280
+            setattr(p, bad, getattr(p, bad) + 4)
+            rc = lib.gs_preprocess(plan, ctypes.c_void_p(4096), ctypes.byref(p), ctypes.byref(cam), None)
+            assert rc == L.GS_ERR_ARG, bad
+    finally:
+        lib.gs_plan_destroy(plan)
