@@ -107,8 +107,8 @@ k_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ v
     __shared__ uint32_t wcnt[kWarps][kRadix];   // per-warp digit counts of the tile
     __shared__ uint32_t tile_start[kRadix];     // tile-local start of each digit
     __shared__ uint32_t gbase[kRadix];          // global start of each digit for this block
-    __shared__ uint32_t sk[kTileItems];
-    __shared__ uint32_t sv[kTileItems];
+    __shared__ uint32_t gshift[kRadix];         // gbase - tile_start: output position - tile slot
+    __shared__ uint2 skv[kTileItems];           // the tile reordered by digit: (key, value)
     __shared__ uint32_t scan_tmp[kWarps];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -194,23 +194,26 @@ k_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ v
             if (tid < kWarps) scan_tmp[tid] = s;
         }
         __syncthreads();
-        if (tid < kRadix) tile_start[tid] = x - total + (warp > 0 ? scan_tmp[warp - 1] : 0u);
+        if (tid < kRadix) {
+            const uint32_t ts = x - total + (warp > 0 ? scan_tmp[warp - 1] : 0u);
+            tile_start[tid] = ts;
+            gshift[tid] = gbase[tid] - ts;
+        }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kItems; ++r) {
             if (dig[r] < kRadix) {
                 const uint32_t pos = tile_start[dig[r]] + wcnt[warp][dig[r]] + rank[r];
-                sk[pos] = k[r];
-                sv[pos] = v[r];
+                skv[pos] = make_uint2(k[r], v[r]);
             }
         }
         __syncthreads();
         for (int i = tid; i < tile_n; i += kSortThreads) {
-            const uint32_t kk = sk[i];
-            const int d = (int)((kk >> shift) & mask);
-            const uint32_t g = gbase[d] + (uint32_t)i - tile_start[d];
-            keys_out[g] = kk;
-            vals_out[g] = sv[i];
+            const uint2 kv = skv[i];
+            const int d = (int)((kv.x >> shift) & mask);
+            const uint32_t g = gshift[d] + (uint32_t)i;  // (unsigned wrap-around is exact)
+            keys_out[g] = kv.x;
+            vals_out[g] = kv.y;
         }
         __syncthreads();
         if (tid < kRadix) gbase[tid] += total;
