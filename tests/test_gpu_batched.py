@@ -243,3 +243,53 @@ def test_visible_only_adam_matches_oracle(gs):
         off = np.abs(got[live] - ref[k][live]) > 1e-5 * np.maximum(1.0, np.abs(ref[k][live]))
         assert off.mean() < 0.01, (k, off.mean())
         assert np.abs(got[live] - ref[k][live]).max() <= 2.5 * max(lrs.values()) * 2, k
+
+
+@pytest.mark.slow
+def test_visible_only_adam_at_1m_1080p(gs):
+    """At the full size (1M clustered Gaussians, 1080p views from a ring of
+    radius 2.2 that leaves about half of them outside each view), two steps
+    on two views, visible-only against dense Adam: a Gaussian outside the
+    second view keeps its first-step state bit for bit under the visible-only
+    update while the dense update keeps moving it (momentum); Gaussians inside
+    the second view get the same update from both."""
+    from paper_2601_19489_gb300 import _lib as L
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import Trainer
+
+    scene = synth.scene_clustered(1 << 20, seed=0, sh_degree=3)
+    ring = synth.ring_cameras(16, 1920, 1080, radius=2.2)
+    views = [ring[2], ring[6]]  # a quarter turn apart: each sees Gaussians the other does not
+    tgt = [torch.from_numpy(synth.target_uniform(12 + i, 1920, 1080).reshape(-1)).cuda() for i in range(2)]
+    names = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    tr = {}
+    for vis in (False, True):
+        t = Trainer(api.Gaussians.from_scene(scene), 1920, 1080, visible_adam=vis)
+        t.ensure_capacity([[c] for c in views])
+        t.step([views[0]], tgt[0])
+        tr[vis] = t
+    s1 = {k: (getattr(tr[True].params, k).clone(), getattr(tr[True].m, k).clone(), getattr(tr[True].v, k).clone())
+          for k in names}
+    d1 = {k: getattr(tr[False].params, k).clone() for k in names}
+    for t in tr.values():
+        t.step([views[1]], tgt[1])
+    torch.cuda.synchronize()
+    sl = tr[True].slot_for([views[1]])
+    assert sl.plan.status()["rc"] == 0
+    seen = sl.plan.view(L.GS_WS_TILES_TOUCHED, torch.int32)[: scene.n] > 0
+    assert 0.2 < float(seen.float().mean()) < 0.9
+    hidden = ~seen
+    for k in names:
+        p, m, v = (getattr(g, k) for g in (tr[True].params, tr[True].m, tr[True].v))
+        assert torch.equal(p[hidden], s1[k][0][hidden]), k
+        assert torch.equal(m[hidden], s1[k][1][hidden]) and torch.equal(v[hidden], s1[k][2][hidden]), k
+        # the dense update moves the hidden Gaussians that carry momentum
+        mom = (s1[k][1][hidden] != 0).reshape(int(hidden.sum()), -1).any(1)
+        assert int(mom.sum()) > 1000, k
+        dense_moved = (getattr(tr[False].params, k)[hidden] != d1[k][hidden]).reshape(int(hidden.sum()), -1).any(1)
+        assert float(dense_moved[mom].float().mean()) > 0.9, k
+        # inside the second view both take the same update (up to the order
+        # of the gradient's atomic sums)
+        a, b = p[seen], getattr(tr[False].params, k)[seen]
+        off = (a - b).abs() > 1e-6 * torch.clamp(b.abs(), min=1.0)
+        assert float(off.float().mean()) < 0.01, k
