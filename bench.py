@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--n", "--gaussians", dest="n", type=int, default=1 << 20)
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--views", type=int, default=16)
@@ -270,6 +270,24 @@ def stage_roofline(stage_ms: dict, n: int, sh_degree: int, pixels: int, instance
     return out
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of every rank's x (each rank's timed region; the job
+    takes as long as its slowest rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank runs `steps` steps of its own views
+    (replicas, weak scaling) in at most `seconds`."""
+    return world * steps / seconds
+
+
 def kernels_per_step(trainer) -> int:
     tile_passes = -(-trainer.plan_tile_bits // 8)
     loss_k = 3 if trainer.lam > 0 else 2
@@ -350,10 +368,7 @@ def run_ours(args, rank, world):
     st1 = trainer.plan.status()
     if st1["rc"] != 0:
         raise RuntimeError(f"device status after the timed region: {st1}")
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, world, dev)
     stage_ms = {name: float(np.mean([evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps)]))
                 for i, name in enumerate(trainer.STAGES)}
 
@@ -389,12 +404,8 @@ def run_ours(args, rank, world):
             feeder.done()
             loss_h.copy_(trainer.loss, non_blocking=True)
         barrier()
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * args.steps / t_e2e, "unit": UNIT,
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_rate(world, args.steps, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": int(targets_h[0].numel() * 4), "d2h_bytes_per_step": 4}
 
     if rank != 0:
@@ -415,7 +426,7 @@ def run_ours(args, rank, world):
                 "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": kname,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                 "work": f"{FLOP_PER_PAIR[dominant]:.0f} FLOP x {mean_pairs:.4g} pixel-splat pairs per launch"}
-    value = world * args.steps / elapsed
+    value = job_rate(world, args.steps, elapsed)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
