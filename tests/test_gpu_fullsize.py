@@ -1,0 +1,91 @@
+"""Parity at the benchmark's full size and launch configuration (1M
+clustered Gaussians with SH degree 3, one 1920 x 1080 ring view, LB binning,
+32-splat buckets, 2-warp backward CTAs, one pixel chain: the shape the
+autotuner picks and bench.py times), on outputs the oracle can compute one
+window at a time: the forward's pixels in twelve 16 x 16 windows, and the
+blend backward of an upstream gradient that is non-zero only inside those
+windows (so every Gaussian's full 2D gradient is the sum over the windows,
+which the oracle computes exactly)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import preprocess as opre
+from oracle import render as oren
+from tests.parity import grad_mismatch, pixel_mismatch, to_np, view_image
+
+pytestmark = pytest.mark.gpu
+
+BG = (0.0, 0.0, 0.0)
+W, H = 1920, 1080
+TUNING = {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1}
+
+
+def _windows(seed, k=12, size=16):
+    """k non-overlapping windows at seeded positions (one per distinct cell of
+    a 240 x 216 grid, anywhere inside the cell)."""
+    rng = np.random.default_rng(seed)
+    cells = rng.choice((W // 240) * (H // 216), size=k, replace=False)
+    out = []
+    for c in cells:
+        cx, cy = (c % (W // 240)) * 240, (c // (W // 240)) * 216
+        x0 = cx + int(rng.integers(0, 240 - size))
+        y0 = cy + int(rng.integers(0, 216 - size))
+        out.append((int(x0), int(y0), int(x0) + size, int(y0) + size))
+    return out
+
+
+@pytest.mark.slow
+def test_forward_and_blend_backward_at_1m_1080p_on_sampled_windows(gs):
+    from paper_2601_19489_gb300 import _lib as L
+    from paper_2601_19489_gb300 import api
+
+    scene = synth.scene_clustered(1 << 20, seed=0, sh_degree=3)
+    cam = synth.ring_cameras(16, W, H)[3]
+    plan = api.Plan(scene.n, 3, [(W, H)], 1 << 25, tuning=TUNING)
+    params = api.Gaussians.from_scene(scene)
+    rgb, disp, T = (torch.empty(k * W * H, device="cuda") for k in (3, 1, 1))
+    api.gs_preprocess(plan, params, [cam])
+    api.gs_bin_sort(plan, True)
+    api.gs_render_fwd(plan, BG, rgb, disp, T)
+    st = plan.status()
+    assert st["rc"] == 0 and st["n_instances"] > 10_000_000, st
+    orec = opre.pack_for_render(opre.project(opre.params_from_scene(scene), cam, 3))
+    g_rgb = view_image(rgb, W, H)
+    g_disp, g_T = view_image(disp, W, H, channels=1)[0], view_image(T, W, H, channels=1)[0]
+    rng = np.random.default_rng(21)
+    up = np.zeros((3, H, W))
+    up_d = np.zeros((H, W))
+    wins = _windows(4)
+    n_amb = 0
+    for (x0, y0, x1, y1) in wins:
+        ref = oren.render_fwd(orec, BG, (x0, y0, x1, y1), amb=oren.float32_bands(W, H))
+        ok = ~ref["amb"]
+        n_amb += int(ref["amb"].sum())
+        for ch in range(3):
+            bad = pixel_mismatch(g_rgb[ch, y0:y1, x0:x1], ref["rgb"][ch], ok)
+            assert bad.sum() == 0, ((x0, y0), ch, int(bad.sum()))
+        assert pixel_mismatch(g_disp[y0:y1, x0:x1], ref["disp"], ok).sum() == 0
+        assert pixel_mismatch(g_T[y0:y1, x0:x1], ref["T"], ok).sum() == 0
+        up[:, y0:y1, x0:x1] = rng.standard_normal((3, y1 - y0, x1 - x0)) * ok
+        up_d[y0:y1, x0:x1] = rng.standard_normal((y1 - y0, x1 - x0)) * ok
+    assert n_amb < 0.02 * len(wins) * 256
+    dL = torch.from_numpy(up.astype(np.float32).reshape(-1)).cuda()
+    dLd = torch.from_numpy(up_d.astype(np.float32).reshape(-1)).cuda()
+    L.check(L.lib().gs_render_bwd_blend(plan.handle, plan.ws.data_ptr(), rgb.data_ptr(), disp.data_ptr(),
+                                        dL.data_ptr(), dLd.data_ptr(), torch.cuda.current_stream().cuda_stream),
+            "gs_render_bwd_blend")
+    assert plan.status()["rc"] == 0
+    g2d = to_np(plan.view(L.GS_WS_GRAD2D, torch.float32)).reshape(-1, 12)
+    gpu10 = g2d[:, [0, 1, 2, 3, 4, 5, 8, 9, 10, 6]]
+    ref2d = np.zeros((scene.n, 10))
+    for (x0, y0, x1, y1) in wins:
+        ref2d += oren.render_bwd(orec, BG, (x0, y0, x1, y1), up[:, y0:y1, x0:x1].copy(), up_d[y0:y1, x0:x1].copy())
+    touched = np.abs(ref2d).sum(1) > 0
+    assert touched.sum() > 500  # the windows reach many Gaussians
+    names = ["mx", "my", "a", "b", "c", "o", "r", "g", "b", "invz"]
+    for k in range(10):
+        bad = grad_mismatch(gpu10[:, k], ref2d[:, k])
+        idx = np.nonzero(bad)[0][:5]
+        assert bad.sum() == 0, (names[k], int(bad.sum()), idx, gpu10[idx, k], ref2d[idx, k])
