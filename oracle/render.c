@@ -35,7 +35,9 @@
  * depths within a relative band (their order could flip).  The alpha and
  * clamp bands are a relative part plus the change of ln(alpha) that a shift
  * of the projected mean by pos_abs pixels causes (|d power / d mean| pos_abs);
- * the stop band adds the same shifts, propagated through T.  A pixel is also
+ * the stop band adds the same shifts and the relative alpha error cond_eps,
+ * both propagated through T (a long chain of high-alpha splats widens it
+ * through the factors alpha / (1 - alpha)).  A pixel is also
  * flagged when its value is ill-conditioned: when relative errors of cond_eps
  * in every blended alpha could move a colour channel, D or T by more than half
  * of the per-pixel tolerance 1e-4 |v| + 1e-7 (first-order bound
@@ -220,7 +222,10 @@ int64_t orc_render_fwd(int64_t n, const double *proj, const double *bg,
             if (e.alpha < ORC_ALPHA_MIN) continue;
             double test_T = T * (1.0 - e.alpha);
             if (amb) {
-                double s_here = t_sens + (e.clamped ? 0.0 : e.alpha / (1.0 - e.alpha) * shift);
+                /* ln T moves by alpha / (1 - alpha) times the relative change of
+                 * alpha: from a mean2d shift, and from the relative float32 error
+                 * cond_eps that every alpha carries (a clamped alpha is exact) */
+                double s_here = t_sens + (e.clamped ? 0.0 : e.alpha / (1.0 - e.alpha) * (shift + amb->cond_eps));
                 if (fabs(log(test_T / ORC_T_STOP)) < amb->tstop_rel + s_here) flag = 1;
                 t_sens = s_here;
             }

@@ -89,3 +89,77 @@ def test_forward_and_blend_backward_at_1m_1080p_on_sampled_windows(gs):
         bad = grad_mismatch(gpu10[:, k], ref2d[:, k])
         idx = np.nonzero(bad)[0][:5]
         assert bad.sum() == 0, (names[k], int(bad.sum()), idx, gpu10[idx, k], ref2d[idx, k])
+
+
+@pytest.mark.slow
+def test_batched_plan_at_1m_on_sampled_windows(gs):
+    """The 8-view batched configuration at full size (1M Gaussians; 3 x
+    960x540, 3 x 1280x720, 2 x 1920x1080 ring views in one plan, one launch
+    per stage): two sampled windows per view, forward pixels and the blend
+    backward's per-(view, Gaussian) 2D gradients against the oracle."""
+    from paper_2601_19489_gb300 import _lib as L
+    from paper_2601_19489_gb300 import api
+
+    scene = synth.scene_clustered(1 << 20, seed=0, sh_degree=3)
+    cams = synth.mixed_ring_cameras(8, seed=0)
+    sizes = [(c.width, c.height) for c in cams]
+    plan = api.Plan(scene.n, 3, sizes, 1 << 27, tuning=TUNING)
+    params = api.Gaussians.from_scene(scene)
+    P = plan.pixels
+    rgb, disp, T = (torch.empty(k * P, device="cuda") for k in (3, 1, 1))
+    api.gs_preprocess(plan, params, cams)
+    api.gs_bin_sort(plan, True)
+    api.gs_render_fwd(plan, BG, rgb, disp, T)
+    assert plan.status()["rc"] == 0
+    rng = np.random.default_rng(33)
+    up, up_d = np.zeros(3 * P, np.float32), np.zeros(P, np.float32)
+    refs = []
+    off = 0
+    n_amb = 0
+    for v, cam in enumerate(cams):
+        w, h = cam.width, cam.height
+        orec = opre.pack_for_render(opre.project(opre.params_from_scene(scene), cam, 3))
+        g_rgb = view_image(rgb, w, h, offset=off)
+        img = up[3 * off: 3 * (off + w * h)].reshape(3, h, w)
+        img_d = up_d[off: off + w * h].reshape(h, w)
+        for (x0, y0, x1, y1) in [((w // 4) + 37 * v, (h // 3) + 11 * v, (w // 4) + 37 * v + 16, (h // 3) + 11 * v + 16),
+                                 ((w // 2) + 23 * v, (h // 2) - 9 * v, (w // 2) + 23 * v + 16, (h // 2) - 9 * v + 16)]:
+            ref = oren.render_fwd(orec, BG, (x0, y0, x1, y1), amb=oren.float32_bands(w, h))
+            ok = ~ref["amb"]
+            n_amb += int(ref["amb"].sum())
+            for ch in range(3):
+                assert pixel_mismatch(g_rgb[ch, y0:y1, x0:x1], ref["rgb"][ch], ok).sum() == 0, (v, ch)
+            img[:, y0:y1, x0:x1] = rng.standard_normal((3, 16, 16)) * ok
+            img_d[y0:y1, x0:x1] = rng.standard_normal((16, 16)) * ok
+            refs.append((v, orec, (x0, y0, x1, y1)))
+        off += w * h
+    assert n_amb < 0.05 * len(refs) * 256, n_amb
+    dL, dLd = torch.from_numpy(up).cuda(), torch.from_numpy(up_d).cuda()
+    L.check(L.lib().gs_render_bwd_blend(plan.handle, plan.ws.data_ptr(), rgb.data_ptr(), disp.data_ptr(),
+                                        dL.data_ptr(), dLd.data_ptr(), torch.cuda.current_stream().cuda_stream),
+            "gs_render_bwd_blend")
+    g2d = to_np(plan.view(L.GS_WS_GRAD2D, torch.float32)).reshape(len(cams), scene.n, 12)
+    off = 0
+    starts = np.cumsum([0] + [w * h for (w, h) in sizes])
+    for v, cam in enumerate(cams):
+        w, h = cam.width, cam.height
+        img = up[3 * starts[v]: 3 * starts[v + 1]].reshape(3, h, w).astype(np.float64)
+        img_d = up_d[starts[v]: starts[v + 1]].reshape(h, w).astype(np.float64)
+        ref2d = np.zeros((scene.n, 10))
+        for (vv, orec, (x0, y0, x1, y1)) in refs:
+            if vv == v:
+                ref2d += oren.render_bwd(orec, BG, (x0, y0, x1, y1), img[:, y0:y1, x0:x1].copy(),
+                                         img_d[y0:y1, x0:x1].copy())
+        gpu10 = g2d[v][:, [0, 1, 2, 3, 4, 5, 8, 9, 10, 6]]
+        for k in range(10):
+            # A Gaussian's 2D gradient sums its terms over the few hundred
+            # window pixels it covers, and with a random upstream gradient
+            # those terms cancel (the mean's gradient by the symmetry about
+            # the mean, the opacity's to 1e-3 of the terms in these dense
+            # views); the float32 sum then carries an absolute error up to
+            # about 1e-5 of the column's largest entry, so the absolute floor
+            # is 1e-5 of it (the single-view test holds the 1e-6 floor).
+            scale = np.abs(ref2d[:, k]).max()
+            bad = np.abs(gpu10[:, k] - ref2d[:, k]) > 1e-3 * np.abs(ref2d[:, k]) + 1e-5 * scale
+            idx = np.nonzero(bad)[0][:3]
+            assert bad.sum() == 0, (v, k, idx, gpu10[idx, k], ref2d[idx, k], scale)

@@ -218,3 +218,38 @@ def test_ng_trainer_learns_and_replays_as_a_graph(gs):
         runs.append(losses)
     assert runs[0][-1] < 0.9 * runs[0][0], runs[0]
     np.testing.assert_allclose(runs[1], runs[0], rtol=1e-3)
+
+
+@pytest.mark.slow
+def test_ng_decode_forward_at_full_size_on_sampled_anchors(gs):
+    """The decoder at the benchmark's size (104,857 anchors -> 1,048,570
+    children, a 1080p ring view): the children of 512 sampled anchors,
+    spread over every CTA tile, against the oracle (each anchor's decode
+    depends only on its own inputs and the shared MLP)."""
+    from paper_2601_19489_gb300 import api
+
+    n = (1 << 20) // 10
+    pts = synth.scene_clustered(1 << 20, seed=0, sh_degree=0).means
+    d = synth.ng_anchors(pts, n, seed=0)
+    cam = synth.ring_cameras(16, 1920, 1080)[0]
+    ng = api.NgParams.from_dict(d)
+    ws = api.gs_ng_workspace(n)
+    ch = api.ng_children(n)
+    api.gs_ng_decode_fwd(ng, cam, ch, ws)
+    assert api.gs_ng_status(ws) == 0
+    pick = np.sort(np.random.default_rng(8).choice(n, size=512, replace=False))
+    pick[-1] = n - 1  # the ragged last tile
+    sub = {k: (v[pick] if k in ("anchor_xyz", "feat", "anchor_ls") else v) for k, v in d.items()}
+    out, cache, risky = _oracle(sub, cam)
+    assert risky.mean() < 0.5
+    rows = (pick[:, None] * 10 + np.arange(10)[None]).reshape(-1)
+    ok = np.repeat(~risky, 10)
+    got = {"means": ch.means, "log_scales": ch.log_scales, "quats": ch.quats, "opacity_logits": ch.opacity_logits,
+           "sh": ch.sh}
+    for k, t in got.items():
+        g = to_np(t).reshape(n * 10, -1)[rows].astype(np.float64)
+        r = out[k].numpy().reshape(ok.size, -1)
+        err = np.abs(g - r)
+        tol = 1e-4 * np.abs(r) + 2e-5
+        assert np.all(err[ok] <= tol[ok]), (k, err[ok].max())
+        assert np.all(err <= 0.05 * np.abs(r) + 0.05), (k, err.max())
