@@ -350,6 +350,12 @@ def run_ours(args, rank, world):
     barrier()
     st0 = trainer.plan.status()
     assert st0["rc"] == 0, st0
+    # the training state after the warm-up: the e2e measurement restarts from
+    # it, so that both measurements time the same stretch of the same run
+    # (the scene changes as it trains, and with it the work per step)
+    snapshot = None
+    if not args.no_e2e:
+        snapshot = [t.clone() for t in trainer._state_tensors().values()] + [trainer.d_step.clone()]
 
     n_st = len(trainer.STAGES)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_st + 1)] for _ in range(args.steps)]
@@ -392,13 +398,16 @@ def run_ours(args, rank, world):
     if not args.no_e2e:
         from paper_2601_19489_gb300.trainer import HostFeeder
 
+        for dst, src in zip(list(trainer._state_tensors().values()) + [trainer.d_step], snapshot):
+            dst.copy_(src)
+        del snapshot
         loss_h = torch.empty(1, pin_memory=True)
         feeder = HostFeeder(targets_d[0])
         barrier()
         t0 = time.perf_counter()
         for s in range(args.steps):
-            v = s % len(cams)
-            nxt = targets_h[(s + 1) % len(cams)] if s + 1 < args.steps else None
+            v = (args.warmup + s) % len(cams)
+            nxt = targets_h[(args.warmup + s + 1) % len(cams)] if s + 1 < args.steps else None
             tgt = feeder.get(targets_h[v], nxt)
             trainer.step(cams[v], tgt)
             feeder.done()
