@@ -6,7 +6,11 @@
  * (arXiv 2601.19489).  The step follows Sec. 2.1 (preprocessCUDA: projection,
  * compact SnugBox, per-column tile test, load-balanced tile-key write, depth
  * sort; renderCUDA: front-to-back alpha blending) and Sec. 2.2 (checkpoints
- * every 32 splats, per-Gaussian parallel backward), followed by Adam.
+ * every 32 splats, per-Gaussian parallel backward), followed by Adam (also
+ * fused into the preprocess backward, dense or visible-only).  Around it:
+ * the neural-Gaussian decoder of Sec. 2.3 (gs_ng_*), the global pose
+ * refinement of Sec. 2.5 (gs_pose_*, gs_plan_set_pose) and the score-guided
+ * densification and pruning of Sec. 3.3 (gs_densify_*).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
