@@ -182,3 +182,52 @@ def test_misaligned_parameter_rows_are_refused_on_the_host(lib):
             assert rc == L.GS_ERR_ARG, bad
     finally:
         lib.gs_plan_destroy(plan)
+
+
+def test_more_argument_errors_are_caught_on_the_host(lib):
+    """Each call below carries one invalid argument that the host check
+    reports before any launch (the device pointers are never touched)."""
+    from paper_2601_19489_gb300 import _lib as L
+
+    ARG = L.GS_ERR_ARG
+    w = (ctypes.c_int32 * 1)(64)
+    h = (ctypes.c_int32 * 1)(48)
+    plan = lib.gs_plan_create(10, 1, 1, w, h, 100)
+    assert plan
+    fake = ctypes.c_void_p(4096)
+    try:
+        # loss: lambda outside [0, 1]; disparity without its target
+        assert lib.gs_loss(plan, fake, fake, ctypes.c_float(1.5), None, None, ctypes.c_float(0.0), fake, None,
+                           fake, fake, None) == ARG
+        assert lib.gs_loss(plan, fake, fake, ctypes.c_float(0.2), fake, None, ctypes.c_float(0.1), fake, fake,
+                           fake, fake, None) == ARG
+        # densification: negative mask threshold; K < 1; empty set
+        assert lib.gs_densify_score(plan, fake, fake, fake, ctypes.c_float(-0.1), fake, fake, fake, fake,
+                                    None) == ARG
+        p = L.GsParams()
+        p.n, p.sh_degree = 10, 1
+        p.means, p.log_scales, p.quats, p.opacity_logits, p.sh = 256, 512, 768, 1024, 1280
+        rules = L.GsDensifyRules(5.0, 0.95, 0.005, 0.01, 4.0, 0)
+        out_n = ctypes.c_int64(0)
+        assert lib.gs_densify_plan(10, ctypes.byref(p), fake, fake, ctypes.byref(rules), fake, fake, fake,
+                                   ctypes.byref(out_n), None) == ARG
+        assert lib.gs_densify_apply(0, ctypes.byref(p), ctypes.byref(p), ctypes.byref(p), fake, fake, fake,
+                                    ctypes.byref(p), ctypes.byref(p), ctypes.byref(p), None) == ARG
+        # fused Adam: b1 outside [0.5, 1)
+        cam = L.GsCamera()
+        cam.fx = cam.fy = 64.0
+        cam.cx, cam.cy, cam.width, cam.height, cam.near_z = 32.0, 24.0, 64, 48, 0.2
+        hp = L.GsAdamHparams(1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 1.0, 0.999, 1e-15, 0)
+        assert lib.gs_preprocess_bwd_adam(plan, fake, ctypes.byref(p), ctypes.byref(cam), ctypes.byref(p),
+                                          ctypes.byref(p), ctypes.byref(hp), fake, None) == ARG
+    finally:
+        lib.gs_plan_destroy(plan)
+    # decoder: no anchors; a child set of the wrong size
+    ng = L.GsNgParams(0, 256, 512, 768, 1024, 1280, 1536, 1792)
+    kids = L.GsParams()
+    kids.n, kids.sh_degree = 10, 0
+    assert lib.gs_ng_decode_fwd(ctypes.byref(ng), ctypes.byref(L.GsCamera()), ctypes.byref(kids), fake,
+                                None) == ARG
+    ng.n_anchors = 4
+    assert lib.gs_ng_decode_fwd(ctypes.byref(ng), ctypes.byref(L.GsCamera()), ctypes.byref(kids), fake,
+                                None) == ARG
