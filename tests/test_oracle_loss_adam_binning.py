@@ -1,6 +1,7 @@
 """Pins of the oracle's loss (Eq. 5), Adam, binning definition (Eq. 1, the
 per-column test) and the end-to-end chain of gradients."""
 import math
+from pathlib import Path
 
 import numpy as np
 import pytest
@@ -199,6 +200,53 @@ def test_tile_min_q_on_config1_covers_every_blended_pixel():
         ys, xs = np.nonzero(f["count"])
         blended_tiles = set((ys // 16 * 16 + xs // 16).tolist())
         assert blended_tiles <= touched
+
+
+GOLDEN = Path(__file__).parent / "golden"
+
+
+def _golden_snugbox_cases():
+    cases = []
+    for line in (GOLDEN / "snugbox_tiles.txt").read_text().splitlines():
+        if not line.strip() or line.startswith("#"):
+            continue
+        lhs, rhs = line.split(":")
+        w, h, mx, my, a, b, c, t = (float(x) for x in lhs.split())
+        want = set() if rhs.strip() == "-" else {int(x) for x in rhs.split()}
+        cases.append((int(w), int(h), mx, my, a, b, c, t, want))
+    return cases
+
+
+def test_golden_snugbox_tiles_worked_by_hand():
+    """Sec. 2.1, Eq. 1-2: the tile sets of tests/golden/snugbox_tiles.txt,
+    derived by hand there, from the oracle's tile test and from dense sampling
+    of every tile rectangle (which shares nothing with the oracle's
+    edge-minimum search)."""
+    cases = _golden_snugbox_cases()
+    assert len(cases) == 4
+    for w, h, mx, my, a, b, c, t, want in cases:
+        rec = np.zeros((1, 12))
+        rec[0, 0:5] = (mx, my, a, b, c)
+        rec[0, 5] = math.exp(t / 2.0) / 255.0  # Eq. 1 solved for o
+        rec[0, 10] = t
+        rec[0, 11] = 1.0
+        tiles = binning.tile_min_q(rec, w, h)
+        got = set()
+        if 0 in tiles:
+            ids, mq, tt = tiles[0]
+            got = set(ids[mq <= tt].tolist())
+        assert got == want, (w, h, mx, my, got, want)
+        # dense sampling of each tile's pixel-centre rectangle
+        tw, th = -(-w // 16), -(-h // 16)
+        dense = set()
+        for ty in range(th):
+            for tx in range(tw):
+                xs = np.linspace(tx * 16 + 0.5, min(tx * 16 + 15, w - 1) + 0.5, 241)
+                ys = np.linspace(ty * 16 + 0.5, min(ty * 16 + 15, h - 1) + 0.5, 241)
+                dx, dy = np.meshgrid(xs - mx, ys - my)
+                if t > 0 and (a * dx * dx + 2 * b * dx * dy + c * dy * dy).min() <= t:
+                    dense.add(ty * tw + tx)
+        assert dense == want, (w, h, mx, my, dense, want)
 
 
 def test_stable_sort_definition():
