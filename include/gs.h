@@ -10,7 +10,7 @@
  * fused into the preprocess backward, dense or visible-only).  Around it:
  * the neural-Gaussian decoder of Sec. 2.3 (gs_ng_*), the global pose
  * refinement of Sec. 2.5 (gs_pose_*, gs_plan_set_pose) and the score-guided
- * densification and pruning of Sec. 3.3 (gs_densify_*).
+ * densification and pruning of Sec. 3.2 (gs_densify_*).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -379,7 +379,7 @@ GS_API int gs_ng_decode_bwd(const gs_ng_params *ng, const gs_camera *h_cam, cons
  * if a bounded wait for the tensor cores gave up). */
 GS_API int gs_ng_read_status(void *d_ws, int32_t *out_error, void *stream);
 
-/* ------------------------------ densification and pruning (Sec. 3.3)
+/* ------------------------------ densification and pruning (Sec. 3.2)
  * Multi-view score-guided densification and pruning, in three calls:
  *
  * gs_densify_score: after gs_render_fwd on a plan (one or more views), add

@@ -12,7 +12,7 @@ Modules:
   adam        Adam update
   binning     brute-force tile sets and stable sort definitions
   step        one whole training step composed from the above
-  densify     score-guided densification and pruning (Sec. 3.3)
+  densify     score-guided densification and pruning (Sec. 3.2)
   ng          neural-Gaussian decoder (Sec. 2.3)
   pose        global pose correction: its gradient and update (Sec. 2.5)
 """

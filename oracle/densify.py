@@ -1,5 +1,5 @@
 """Oracle for the multi-view score-guided densification and pruning of
-Sec. 3.3, float64 numpy on the CPU.
+Sec. 3.2, float64 numpy on the CPU.
 
 TEST INFRASTRUCTURE: only the test suite, the smoke check and the benchmark's
 CPU-baseline leg may import this module.

@@ -415,7 +415,7 @@ void orc_render_bwd(int64_t n, const double *proj, const double *bg,
 }
 
 /*
- * Contributor-weighted sums for score-guided densification (Sec. 3.3, Eq. 4
+ * Contributor-weighted sums for score-guided densification (Sec. 3.2, Eq. 4
  * and Eq. 6): for every pixel of the window and every Gaussian the forward
  * blends there (the same rules as orc_render_fwd: alpha >= 1/255, before the
  * transmittance stop), ADD the pixel's weight weight[p] (h x w) to

@@ -252,7 +252,7 @@ def gs_preprocess_bwd_adam(plan: Plan, params: Gaussians, cams, m: Gaussians, v:
                                            _stream(stream)), "gs_preprocess_bwd_adam")
 
 
-# ------------------------------------------------- densification (Sec. 3.3)
+# ------------------------------------------------- densification (Sec. 3.2)
 
 def gs_densify_scratch(n: int, device="cuda") -> torch.Tensor:
     return torch.zeros(int(L.lib().gs_densify_scratch_bytes(int(n))), dtype=torch.uint8, device=device)

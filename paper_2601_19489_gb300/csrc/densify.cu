@@ -1,4 +1,4 @@
-// Multi-view score-guided densification and pruning (Sec. 3.3, Eq. 3-6).
+// Multi-view score-guided densification and pruning (Sec. 3.2, Eq. 3-6).
 //
 // Scores (per view, after that view's forward): the view's error image
 // E(u, v) = sum_c |R_c - G_c| is normalised by its maximum (one atomic max

@@ -5,7 +5,7 @@ reconstruction setting of the paper's Sec. 4).
 Ways to spend the budget, all on one schedule:
   plain          one view per step, eager launches;
   densify        plain, plus a multi-view score-guided densify-and-prune
-                 stage (Sec. 3.3) after each of the first half of the
+                 stage (Sec. 3.2) after each of the first half of the
                  evaluation segments (K = 10 random training views; its time
                  counts as training time);
   batched_graph  8 views per step through the batched plan, launch shapes from

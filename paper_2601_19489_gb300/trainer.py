@@ -293,7 +293,7 @@ class Trainer:
     # ------------------------------------------------------------ densify
     def densify(self, cams, targets, tau: float = 0.3, rules: dict | None = None, seed: int = 0,
                 max_gaussians: int | None = None) -> dict:
-        """One densify-and-prune stage (Sec. 3.3): score every Gaussian on the
+        """One densify-and-prune stage (Sec. 3.2): score every Gaussian on the
         given views (single-view forwards against their targets, flat planar
         colour on the device), then clone, split or prune it by the rules and
         rebuild the parameter set with its Adam moments.  Plans are rebuilt

@@ -1,4 +1,4 @@
-"""Score-guided densification and pruning (Sec. 3.3) on the GPU against the
+"""Score-guided densification and pruning (Sec. 3.2) on the GPU against the
 oracle: the per-Gaussian scores, the actions and slots, and the rebuilt
 parameter set; and a training run that densifies."""
 import numpy as np

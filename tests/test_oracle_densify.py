@@ -1,4 +1,4 @@
-"""Pins of the densification oracle (Sec. 3.3, Eq. 3-6): the contributor
+"""Pins of the densification oracle (Sec. 3.2, Eq. 3-6): the contributor
 scores against closed forms, the blend's stop rule and additivity; the
 actions against their rules; clone and split against their definitions
 with an independent rotation (scipy)."""

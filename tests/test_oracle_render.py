@@ -81,6 +81,31 @@ def test_transmittance_stop_blends_exactly_three_of_four():
     np.testing.assert_allclose(f["rgb"][2, 4, 4], 1 - 0.05 ** 3, rtol=1e-12)
 
 
+def test_golden_one_pixel_blend_worked_by_hand():
+    """tests/golden/blend_one_pixel.txt: five splats on one pixel, given out of
+    depth order, exercising the sort by depth, the 1/255 skip, the 0.99
+    clamp, the transmittance stop without blending, the background and the
+    disparity channel; the expected values are derived by hand in the file."""
+    from pathlib import Path
+
+    rows, want = [], {}
+    for line in (Path(__file__).parent / "golden" / "blend_one_pixel.txt").read_text().splitlines():
+        if not line.strip() or line.startswith("#"):
+            continue
+        key, *vals = line.split()
+        if key == "splat":
+            z, o, r, g, b = (float(v) for v in vals)
+            rows.append(rec(0.5, 0.5, 1.0, 0.0, 1.0, o, (r, g, b), z))
+        else:
+            want[key] = [float(v) for v in vals]
+    assert len(rows) == 5
+    f = render.render_fwd(records(rows), tuple(want["bg"]), (0, 0, 1, 1))
+    np.testing.assert_allclose(f["rgb"][:, 0, 0], want["rgb"], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(f["disp"][0, 0], want["disp"][0], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(f["T"][0, 0], want["T"][0], rtol=0, atol=1e-15)
+    assert f["count"][0, 0] == int(want["blended"][0])
+
+
 def test_alpha_cutoff_either_side_of_one_over_255():
     o = 0.5
     for sign, blended in ((+1, 1), (-1, 0)):
