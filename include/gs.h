@@ -199,7 +199,7 @@ GS_API int gs_preprocess(const gs_plan *plan, void *ws, const gs_params *params,
  * Sec. 2.1: order the visible Gaussians of every view by depth (on-device
  * radix sort), scan their tile counts, write one (tile, Gaussian) instance
  * per touched tile — load_balanced = 1: a warp tests one Gaussian's candidate
- * tiles lane-parallel and compacts with ballot/popc (Fig. "LB"); 0: one
+ * tiles lane-parallel and compacts with ballot/popc (Fig. 2); 0: one
  * thread walks its columns sequentially ("Sq") — then stably radix-sort the
  * instances by tile so each tile's list is in (depth, id) order, and record
  * each tile's [start, end) range and 32-splat bucket count. */

@@ -9,7 +9,7 @@
 //     and the capacity overflow flag), and the key-write pass that rescans
 //     inside each block.
 //  3. key write, one (global tile id, item) instance per touched tile:
-//     load-balanced (Fig. "LB"): the SnugBox columns of a warp's 32 Gaussians
+//     load-balanced (Fig. 2): the SnugBox columns of a warp's 32 Gaussians
 //     form one flat list that the lanes walk one column each, so every lane
 //     evaluates a per-column ellipse test whatever the Gaussians' sizes, and
 //     a segmented warp scan places each column's tiles;
