@@ -485,7 +485,9 @@ class NgTrainer(Trainer):
     through the same splatting kernels as explicit 3DGS, and their gradients
     flow back through the decoder into the anchor features, the anchors'
     log-scales and the MLP, which one Adam update then trains.  The anchor
-    positions stay fixed."""
+    positions stay fixed.  ng_lrs overrides the rates of default_ng_lrs()
+    by name; {"anchor_ls": 0.0} trains only the features and the MLP, as
+    Sec. 2.3 states."""
 
     NG_STAGES = ("decode", "preprocess", "bin_sort", "render_fwd", "loss", "render_bwd_blend", "preprocess_bwd",
                  "decode_bwd", "adam")
@@ -496,7 +498,7 @@ class NgTrainer(Trainer):
         self.ng_grads = ng.zeros_like()
         self.ng_m = ng.zeros_like()
         self.ng_v = ng.zeros_like()
-        self.ng_lrs = dict(ng_lrs or default_ng_lrs())
+        self.ng_lrs = {**default_ng_lrs(), **(ng_lrs or {})}
         self.ng_ws = gs_ng_workspace(ng.n, device=kw.get("device", "cuda"))
         children = ng_children(ng.n, device=kw.get("device", "cuda"))
         kw.setdefault("inst_capacity", max(1 << 20, 16 * children.n))
