@@ -83,8 +83,8 @@ def forward_backward(scene, cam, target, bg=(0.0, 0.0, 0.0), lam: float = 0.2,
 
 def forward_backward_batch(scene, cams, targets, bg=(0.0, 0.0, 0.0), lam: float = 0.2,
                            disp_targets=None, disp_weight: float = 0.0, n_threads: int = 0):
-    """Loss and parameter gradients of a batch of views (Sec. 2.2 trains on
-    several views per step; the paper gives no weighting).  Reading: the
+    """Loss and parameter gradients of a batch of views (the paper says
+    nothing about batching views, so it gives no weighting).  Reading: the
     batch loss is the mean over all the batch's pixels, i.e. each view's own
     loss weighted by its share of the pixels,
         L = sum_v (P_v / P) L_v,   P = sum_v P_v,
