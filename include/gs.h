@@ -198,9 +198,13 @@ GS_API int gs_preprocess(const gs_plan *plan, void *ws, const gs_params *params,
 /* ---------------------------------------------- a2-a4: bin, sort, ranges
  * Sec. 2.1: order the visible Gaussians of every view by depth (on-device
  * radix sort), scan their tile counts, write one (tile, Gaussian) instance
- * per touched tile — load_balanced = 1: a warp tests one Gaussian's candidate
- * tiles lane-parallel and compacts with ballot/popc (Fig. 2); 0: one
- * thread walks its columns sequentially ("Sq") — then stably radix-sort the
+ * per touched tile — load_balanced = 1 (the load-balanced write of Fig. 2):
+ * a warp takes 32 Gaussians, lays their SnugBox tile columns out as one flat
+ * list and gives each lane one column at a time, so every lane runs a
+ * per-column ellipse test whatever the Gaussians' sizes; a segmented warp
+ * scan of the columns' row counts places each column's tiles; 0: one thread
+ * walks its own Gaussian's columns sequentially ("Sq") — then stably
+ * radix-sort the
  * instances by tile so each tile's list is in (depth, id) order, and record
  * each tile's [start, end) range and 32-splat bucket count. */
 GS_API int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, void *stream);
@@ -476,27 +480,28 @@ GS_API int gs_pose_init(double *d_state, void *stream);
 GS_API int gs_plan_set_pose(gs_plan *plan, double *d_state);
 GS_API int gs_pose_step(double *d_state, const gs_pose_hparams *hp, void *stream);
 
-/* The same sort for callers that cannot allocate device memory, such as code
- * running inside a CUDA graph capture in global mode (where cudaMalloc is
- * refused), plug-ins whose host framework owns all device memory through its
- * own pool, or loops that cannot take cudaMalloc's implicit device
- * synchronisation.  The paper has no counterpart to this entry point; it is a
- * convenience of this library.
+/* The same sort for callers that cannot allocate device memory: plug-ins
+ * whose host framework owns every byte of device memory through its own
+ * pool, code that runs under a fixed device-memory budget, and loops that
+ * cannot take cudaMalloc's implicit device synchronisation.  The paper has
+ * no counterpart to this entry point; it is a convenience of this library.
  *
  * The caller passes only the key and value buffers (same rules as
  * gs_sort_pairs_u32).  The scratch lives in a static device array inside the
  * library, 609 KiB per GPU that loads the library, held until the process
- * exits.  n may not exceed GS_SORT_NOALLOC_MAX_N (2^31 - 1, the reach of the
- * sort's 32-bit counters); larger n returns GS_ERR_ARG before any work is
- * enqueued.  The call makes no allocation: no cudaMalloc, no cudaFree, no
- * allocating library routine.
+ * exits.  n may not exceed GS_SORT_NOALLOC_MAX_N (2^31 - 1, the limit of
+ * gs_sort_pairs_u32, which this call wraps); larger n returns GS_ERR_ARG
+ * before any work is enqueued.  The call makes no allocation: no cudaMalloc,
+ * no cudaFree, no allocating library routine.
  *
  * The first call on each device looks up the array's device address with
  * that device current (cudaGetSymbolAddress) and caches it; make that first
- * call before any stream capture.  All calls on a device share the one
- * array, which keeps the previous call's contents (every pass rewrites it in
- * full, so nothing needs clearing): calls that may overlap on the GPU — on
- * different streams without ordering between them — race on it and must be
+ * call before any stream capture.  The cached address does not survive
+ * cudaDeviceReset: a process that resets a device must not call this entry
+ * point on it again.  All calls on a device share the one array, which
+ * keeps the previous call's contents (every pass rewrites it in full, so
+ * nothing needs clearing): calls that may overlap on the GPU — on different
+ * streams without ordering between them — race on it and must be
  * serialised by the caller. */
 #define GS_SORT_NOALLOC_MAX_N 2147483647LL
 GS_API int gs_sort_pairs_u32_noalloc(uint32_t *d_keys_in, uint32_t *d_vals_in, uint32_t *d_keys_out,

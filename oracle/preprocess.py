@@ -46,6 +46,12 @@ def camera_tensors(cam):
     return w2c[:, :3], w2c[:, 3]
 
 
+def intrinsics(cam):
+    """fx, fy, cx, cy rounded to float32 (the values the GPU receives) and
+    widened to float64."""
+    return tuple(float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+
+
 def quat_to_rotmat(q: torch.Tensor) -> torch.Tensor:
     """Rotation matrix of the unit quaternion q / |q|, q = (w, x, y, z)."""
     q = q / torch.linalg.norm(q, dim=-1, keepdim=True)
@@ -138,16 +144,17 @@ def project(params: dict, cam, sh_degree: int, R: torch.Tensor | None = None,
     M = rot * s[:, None, :]  # R diag(s)
     sigma = M @ M.transpose(-1, -2)
 
-    tan_fovx = cam.width / (2.0 * cam.fx)
-    tan_fovy = cam.height / (2.0 * cam.fy)
+    fx, fy, cx, cy = intrinsics(cam)
+    tan_fovx = cam.width / (2.0 * fx)
+    tan_fovy = cam.height / (2.0 * fy)
     limx = FRUSTUM_SLACK * tan_fovx
     limy = FRUSTUM_SLACK * tan_fovy
     txz = torch.clamp(x / zs, -limx, limx) * zs
     tyz = torch.clamp(y / zs, -limy, limy) * zs
     zero = torch.zeros_like(zs)
     J = torch.stack([
-        torch.stack([cam.fx / zs, zero, -cam.fx * txz / (zs * zs)], -1),
-        torch.stack([zero, cam.fy / zs, -cam.fy * tyz / (zs * zs)], -1),
+        torch.stack([fx / zs, zero, -fx * txz / (zs * zs)], -1),
+        torch.stack([zero, fy / zs, -fy * tyz / (zs * zs)], -1),
     ], -2)
     T = J @ R
     cov = T @ sigma @ T.transpose(-1, -2)
@@ -156,7 +163,7 @@ def project(params: dict, cam, sh_degree: int, R: torch.Tensor | None = None,
     det = sxx * syy - sxy * sxy
     conic = torch.stack([syy / det, -sxy / det, sxx / det], -1)
 
-    mean2d = torch.stack([cam.fx * x / zs + cam.cx, cam.fy * y / zs + cam.cy], -1)
+    mean2d = torch.stack([fx * x / zs + cx, fy * y / zs + cy], -1)
     opacity = torch.sigmoid(params["opacity_logits"])
     level = 2.0 * torch.log(255.0 * opacity)
 
@@ -213,3 +220,30 @@ def preprocess_backward(scene, cam, grad2d: np.ndarray) -> dict:
     )
     (total * valid).sum().backward()
     return {k: v.grad.detach().numpy().copy() for k, v in params.items()}
+
+
+def preprocess_backward_abs(scene, cam, slack2d: np.ndarray) -> dict:
+    """Bound on how far the parameter gradients move when each Gaussian's 2D
+    gradients (N, 10) move by at most slack2d (elementwise, >= 0): for every
+    Gaussian, sum over the ten 2D quantities of |d quantity / d parameter|
+    times that quantity's slack.  The Jacobian of a Gaussian's 2D quantities
+    depends only on its own parameters, so one autograd pass per quantity
+    gives every Gaussian's column at once."""
+    slack2d = np.asarray(slack2d, dtype=np.float64)
+    out = None
+    rows = np.nonzero(np.any(slack2d > 0, axis=1))[0]
+    for c in range(slack2d.shape[1]):
+        if not np.any(slack2d[:, c] > 0):
+            continue
+        e = np.zeros_like(slack2d)
+        e[rows, c] = 1.0
+        jc = preprocess_backward(scene, cam, e)
+        if out is None:
+            out = {k: np.zeros_like(v) for k, v in jc.items()}
+        for k, v in jc.items():
+            w = slack2d[:, c].reshape((-1,) + (1,) * (v.ndim - 1))
+            out[k] += np.abs(v) * w
+    if out is None:
+        params = params_from_scene(scene)
+        out = {k: np.zeros(tuple(v.shape)) for k, v in params.items()}
+    return out

@@ -288,15 +288,15 @@ extern "C" int gs_sort_pairs_u32(uint32_t *keys_in, uint32_t *vals_in, uint32_t 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of gs_sort_pairs_u32.
 //
-// Some callers cannot hand the sort a scratch buffer: code that runs while a
-// CUDA graph is captured in global mode (where cudaMalloc is not allowed),
-// plug-ins living inside a framework whose memory pool owns all device
-// memory, and latency-critical loops that cannot afford cudaMalloc's implicit
-// device synchronisation.  This entry point keeps its scratch in a file-scope
-// __device__ array instead.  The array holds the per-pass digit histogram of
-// the fixed-grid sort, kRadix * kSortBlocks + kRadix 32-bit counters
-// (609 KiB); it does not grow with n, and every GPU that loads the library
-// keeps it until the process exits.
+// Some callers cannot hand the sort a scratch buffer: plug-ins living
+// inside a framework whose memory pool owns all device memory, code that
+// runs under a fixed device-memory budget, and latency-critical loops that
+// cannot afford cudaMalloc's implicit device synchronisation.  This entry
+// point keeps its scratch in a file-scope __device__ array instead.  The
+// array holds the per-pass digit histogram of the fixed-grid sort,
+// kRadix * kSortBlocks + kRadix 32-bit counters (609 KiB); it does not grow
+// with n, and every GPU that loads the library keeps it until the process
+// exits.
 #include <mutex>
 
 namespace gs {
@@ -308,7 +308,8 @@ static uint32_t *g_noalloc_ptr[kNoallocMaxDevices];
 static std::mutex g_noalloc_mutex;
 
 // Device address of the scratch array for the current device, looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached for the life of the
+// process (a cudaDeviceReset invalidates it; the header says so).
 static int noalloc_scratch(uint32_t **out) {
     int dev = 0;
     int rc = check_cuda(cudaGetDevice(&dev));

@@ -142,6 +142,10 @@ class Trainer:
     def disp(self):
         return self._default.disp
 
+    @property
+    def T(self):
+        return self._default.T
+
     def slot_for(self, cams) -> _Slot:
         return self._slot(tuple((int(c.width), int(c.height)) for c in _as_list(cams)))
 

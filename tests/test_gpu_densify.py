@@ -48,8 +48,7 @@ def test_scores_match_oracle(gs):
         api.gs_densify_score(plan, rgb, t_d, TAU, photo, s_plus, r_minus, scratch)
         # oracle
         rec = opre.pack_for_render(opre.project(opre.params_from_scene(scene), cam, scene.sh_degree))
-        f = oren.render_fwd(rec, (0.0, 0.0, 0.0), (0, 0, cam.width, cam.height),
-                            amb=oren.float32_bands(cam.width, cam.height))
+        f = oren.render_fwd(rec, (0.0, 0.0, 0.0), (0, 0, cam.width, cam.height), amb=oren.float32_bands())
         E = np.abs(f["rgb"] - tgt.astype(np.float64)).sum(axis=0)
         e = E / E.max()
         mask = e > TAU

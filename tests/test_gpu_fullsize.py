@@ -2,7 +2,8 @@
 clustered Gaussians with SH degree 3, one 1920 x 1080 ring view, LB binning,
 32-splat buckets, 2-warp backward CTAs, one pixel chain: the shape the
 autotuner picks and bench.py times), on outputs the oracle can compute one
-window at a time: the forward's pixels in twelve 16 x 16 windows, and the
+window at a time: the forward's pixels in 24 seeded 16 x 16 windows (every
+pixel: values, and the id of the last blended Gaussian bit-exact), and the
 blend backward of an upstream gradient that is non-zero only inside those
 windows (so every Gaussian's full 2D gradient is the sum over the windows,
 which the oracle computes exactly)."""
@@ -13,13 +14,17 @@ import torch
 import synth
 from oracle import preprocess as opre
 from oracle import render as oren
-from tests.parity import grad_mismatch, pixel_mismatch, to_np, view_image
+from tests.parity import assert_forward, check_forward, format_stats, gpu_last_ids, grad_mismatch, to_np, view_image
 
 pytestmark = pytest.mark.gpu
 
 BG = (0.0, 0.0, 0.0)
 W, H = 1920, 1080
 TUNING = {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1}
+AMB = oren.float32_bands()
+# these 1080p views carry 200-400 candidate splats per pixel, so more pixels
+# have a decision within the float32 error of the blend than the small scenes
+MAX_BRANCH_FRAC = 1e-2
 
 
 def _windows(seed, k=12, size=16):
@@ -34,6 +39,29 @@ def _windows(seed, k=12, size=16):
         y0 = cy + int(rng.integers(0, 216 - size))
         out.append((int(x0), int(y0), int(x0) + size, int(y0) + size))
     return out
+
+
+def _nonoverlapping(ws):
+    out = []
+    for w in ws:
+        if all(w[2] <= o[0] or o[2] <= w[0] or w[3] <= o[1] or o[3] <= w[1] for o in out):
+            out.append(w)
+    return out
+
+
+def _merge(total, st):
+    for k, v in st.items():
+        if isinstance(v, int):
+            total[k] = total.get(k, 0) + v
+    for k, v in st["fractions"].items():
+        total.setdefault("fractions", {})
+        total["fractions"][k] = total["fractions"].get(k, 0.0) + v * st["pixels"]
+    return total
+
+
+def _finish(total):
+    total["fractions"] = {k: v / total["pixels"] for k, v in total["fractions"].items()}
+    return total
 
 
 @pytest.mark.slow
@@ -54,23 +82,23 @@ def test_forward_and_blend_backward_at_1m_1080p_on_sampled_windows(gs):
     orec = opre.pack_for_render(opre.project(opre.params_from_scene(scene), cam, 3))
     g_rgb = view_image(rgb, W, H)
     g_disp, g_T = view_image(disp, W, H, channels=1)[0], view_image(T, W, H, channels=1)[0]
+    last = gpu_last_ids(plan, [(W, H)], scene.n)[0]
     rng = np.random.default_rng(21)
     up = np.zeros((3, H, W))
     up_d = np.zeros((H, W))
-    wins = _windows(4)
-    n_amb = 0
+    wins = _nonoverlapping(_windows(4) + _windows(5))
+    total = {}
     for (x0, y0, x1, y1) in wins:
-        ref = oren.render_fwd(orec, BG, (x0, y0, x1, y1), amb=oren.float32_bands(W, H))
-        ok = ~ref["amb"]
-        n_amb += int(ref["amb"].sum())
-        for ch in range(3):
-            bad = pixel_mismatch(g_rgb[ch, y0:y1, x0:x1], ref["rgb"][ch], ok)
-            assert bad.sum() == 0, ((x0, y0), ch, int(bad.sum()))
-        assert pixel_mismatch(g_disp[y0:y1, x0:x1], ref["disp"], ok).sum() == 0
-        assert pixel_mismatch(g_T[y0:y1, x0:x1], ref["T"], ok).sum() == 0
-        up[:, y0:y1, x0:x1] = rng.standard_normal((3, y1 - y0, x1 - x0)) * ok
-        up_d[y0:y1, x0:x1] = rng.standard_normal((y1 - y0, x1 - x0)) * ok
-    assert n_amb < 0.02 * len(wins) * 256
+        ref = oren.render_fwd(orec, BG, (x0, y0, x1, y1), amb=AMB)
+        sl = (slice(y0, y1), slice(x0, x1))
+        st = check_forward(g_rgb[:, sl[0], sl[1]], g_disp[sl], g_T[sl], last[sl], ref)
+        assert st["bad_value"] == 0 and st["bad_last"] == 0 and st["bad_branch"] == 0, ((x0, y0), st)
+        _merge(total, st)
+        up[:, y0:y1, x0:x1] = rng.standard_normal((3, y1 - y0, x1 - x0))
+        up_d[y0:y1, x0:x1] = rng.standard_normal((y1 - y0, x1 - x0))
+    total = _finish(total)
+    print("1M 1080p windows:", format_stats(total))
+    assert_forward(total, MAX_BRANCH_FRAC)
     dL = torch.from_numpy(up.astype(np.float32).reshape(-1)).cuda()
     dLd = torch.from_numpy(up_d.astype(np.float32).reshape(-1)).cuda()
     L.check(L.lib().gs_render_bwd_blend(plan.handle, plan.ws.data_ptr(), rgb.data_ptr(), disp.data_ptr(),
@@ -80,13 +108,18 @@ def test_forward_and_blend_backward_at_1m_1080p_on_sampled_windows(gs):
     g2d = to_np(plan.view(L.GS_WS_GRAD2D, torch.float32)).reshape(-1, 12)
     gpu10 = g2d[:, [0, 1, 2, 3, 4, 5, 8, 9, 10, 6]]
     ref2d = np.zeros((scene.n, 10))
+    slack = np.zeros((scene.n, 10))
     for (x0, y0, x1, y1) in wins:
-        ref2d += oren.render_bwd(orec, BG, (x0, y0, x1, y1), up[:, y0:y1, x0:x1].copy(), up_d[y0:y1, x0:x1].copy())
+        gw, sw = oren.render_bwd(orec, BG, (x0, y0, x1, y1), up[:, y0:y1, x0:x1].copy(), up_d[y0:y1, x0:x1].copy(),
+                                 amb=AMB, with_slack=True)
+        ref2d += gw
+        slack += sw
+    assert np.isfinite(slack).all()
     touched = np.abs(ref2d).sum(1) > 0
     assert touched.sum() > 500  # the windows reach many Gaussians
     names = ["mx", "my", "a", "b", "c", "o", "r", "g", "b", "invz"]
     for k in range(10):
-        bad = grad_mismatch(gpu10[:, k], ref2d[:, k])
+        bad = grad_mismatch(gpu10[:, k], ref2d[:, k], slack=slack[:, k])
         idx = np.nonzero(bad)[0][:5]
         assert bad.sum() == 0, (names[k], int(bad.sum()), idx, gpu10[idx, k], ref2d[idx, k])
 
@@ -115,25 +148,30 @@ def test_batched_plan_at_1m_on_sampled_windows(gs):
     up, up_d = np.zeros(3 * P, np.float32), np.zeros(P, np.float32)
     refs = []
     off = 0
-    n_amb = 0
+    total = {}
+    lasts = gpu_last_ids(plan, sizes, scene.n)
     for v, cam in enumerate(cams):
         w, h = cam.width, cam.height
         orec = opre.pack_for_render(opre.project(opre.params_from_scene(scene), cam, 3))
         g_rgb = view_image(rgb, w, h, offset=off)
+        g_disp = view_image(disp, w, h, offset=off, channels=1)[0]
+        g_T = view_image(T, w, h, offset=off, channels=1)[0]
         img = up[3 * off: 3 * (off + w * h)].reshape(3, h, w)
         img_d = up_d[off: off + w * h].reshape(h, w)
         for (x0, y0, x1, y1) in [((w // 4) + 37 * v, (h // 3) + 11 * v, (w // 4) + 37 * v + 16, (h // 3) + 11 * v + 16),
                                  ((w // 2) + 23 * v, (h // 2) - 9 * v, (w // 2) + 23 * v + 16, (h // 2) - 9 * v + 16)]:
-            ref = oren.render_fwd(orec, BG, (x0, y0, x1, y1), amb=oren.float32_bands(w, h))
-            ok = ~ref["amb"]
-            n_amb += int(ref["amb"].sum())
-            for ch in range(3):
-                assert pixel_mismatch(g_rgb[ch, y0:y1, x0:x1], ref["rgb"][ch], ok).sum() == 0, (v, ch)
-            img[:, y0:y1, x0:x1] = rng.standard_normal((3, 16, 16)) * ok
-            img_d[y0:y1, x0:x1] = rng.standard_normal((16, 16)) * ok
+            ref = oren.render_fwd(orec, BG, (x0, y0, x1, y1), amb=AMB)
+            st = check_forward(g_rgb[:, y0:y1, x0:x1], g_disp[y0:y1, x0:x1], g_T[y0:y1, x0:x1],
+                               lasts[v][y0:y1, x0:x1], ref)
+            assert st["bad_value"] == 0 and st["bad_last"] == 0 and st["bad_branch"] == 0, (v, st)
+            _merge(total, st)
+            img[:, y0:y1, x0:x1] = rng.standard_normal((3, 16, 16))
+            img_d[y0:y1, x0:x1] = rng.standard_normal((16, 16))
             refs.append((v, orec, (x0, y0, x1, y1)))
         off += w * h
-    assert n_amb < 0.05 * len(refs) * 256, n_amb
+    total = _finish(total)
+    print("8-view plan windows:", format_stats(total))
+    assert_forward(total, MAX_BRANCH_FRAC)
     dL, dLd = torch.from_numpy(up).cuda(), torch.from_numpy(up_d).cuda()
     L.check(L.lib().gs_render_bwd_blend(plan.handle, plan.ws.data_ptr(), rgb.data_ptr(), disp.data_ptr(),
                                         dL.data_ptr(), dLd.data_ptr(), torch.cuda.current_stream().cuda_stream),
@@ -146,10 +184,14 @@ def test_batched_plan_at_1m_on_sampled_windows(gs):
         img = up[3 * starts[v]: 3 * starts[v + 1]].reshape(3, h, w).astype(np.float64)
         img_d = up_d[starts[v]: starts[v + 1]].reshape(h, w).astype(np.float64)
         ref2d = np.zeros((scene.n, 10))
+        slack = np.zeros((scene.n, 10))
         for (vv, orec, (x0, y0, x1, y1)) in refs:
             if vv == v:
-                ref2d += oren.render_bwd(orec, BG, (x0, y0, x1, y1), img[:, y0:y1, x0:x1].copy(),
-                                         img_d[y0:y1, x0:x1].copy())
+                gw, sw = oren.render_bwd(orec, BG, (x0, y0, x1, y1), img[:, y0:y1, x0:x1].copy(),
+                                         img_d[y0:y1, x0:x1].copy(), amb=AMB, with_slack=True)
+                ref2d += gw
+                slack += sw
+        assert np.isfinite(slack).all()
         gpu10 = g2d[v][:, [0, 1, 2, 3, 4, 5, 8, 9, 10, 6]]
         for k in range(10):
             # A Gaussian's 2D gradient sums its terms over the few hundred
@@ -160,6 +202,6 @@ def test_batched_plan_at_1m_on_sampled_windows(gs):
             # about 1e-5 of the column's largest entry, so the absolute floor
             # is 1e-5 of it (the single-view test holds the 1e-6 floor).
             scale = np.abs(ref2d[:, k]).max()
-            bad = np.abs(gpu10[:, k] - ref2d[:, k]) > 1e-3 * np.abs(ref2d[:, k]) + 1e-5 * scale
+            bad = np.abs(gpu10[:, k] - ref2d[:, k]) > 1e-3 * (np.abs(ref2d[:, k]) + slack[:, k]) + 1e-5 * scale + slack[:, k]
             idx = np.nonzero(bad)[0][:3]
             assert bad.sum() == 0, (v, k, idx, gpu10[idx, k], ref2d[idx, k], scale)

@@ -12,13 +12,18 @@ from oracle import binning as obin
 from oracle import loss as oloss
 from oracle import preprocess as opre
 from oracle import render as oren
-from tests.parity import block_mismatch, grad_mismatch, pixel_mismatch, to_np, view_image
+from tests.parity import (assert_forward, block_mismatch, check_forward, format_stats, gpu_last_ids, grad_mismatch,
+                          to_np, view_image)
 
 pytestmark = pytest.mark.gpu
 
 BG = (0.3, 0.1, 0.6)
-def AMB_FOR(cam):
-    return oren.float32_bands(cam.width, cam.height)
+AMB = oren.float32_bands()
+# Largest fraction of pixels the oracle may flag as branch-ambiguous on these
+# scenes (cut, clamp, stop or depth decided within the float32 error of the
+# blend).  Flagged pixels are still compared: against the canonical branch or
+# one of the oracle's alternatives.
+MAX_BRANCH_FRAC = 2.5e-3
 
 
 def _run_forward(gs, scene, cams, cap=1 << 22, lb=True, tuning=None):
@@ -85,20 +90,34 @@ def test_preprocess_matches_oracle(gs, which):
     kH = 0.5 * math.log2(math.e)
     ok = (orec[:, 11] > 0) & (orec[:, 10] > 0) & (touched > 0)
     assert ok.sum() > 0.3 * scene.n
-    np.testing.assert_allclose(rec[ok, 0:2], orec[ok, 0:2], rtol=1e-5, atol=2e-4)
-    scale = np.maximum(np.abs(orec[ok, 2]), np.abs(orec[ok, 4]))[:, None]
-    conic = np.stack([rec[ok, 2], rec[ok, 3], rec[ok, 4]], 1) / kH
-    assert np.all(np.abs(conic - orec[ok, 2:5]) <= 2e-4 * scale)
-    np.testing.assert_allclose(2.0 ** rec[ok, 5], orec[ok, 5], rtol=2e-6)
-    np.testing.assert_allclose(rec[ok, 6], 1.0 / orec[ok, 9], rtol=2e-6)
-    np.testing.assert_allclose(rec[ok, 8:11], orec[ok, 6:9], atol=2e-5)
-    # exact tile count: every tile the level set reaches, none beyond the
-    # widened level set used for binning
+    # the compensated projected mean (high + low word) is the float64
+    # projection of the same float32 inputs to far below a float32 ulp
+    np.testing.assert_allclose(rec[ok, 0] + rec[ok, 7], orec[ok, 0], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(rec[ok, 1] + rec[ok, 11], orec[ok, 1], rtol=0, atol=1e-9)
+    # the conic within the float32 error model of the oracle's bands
+    # (oracle/render.py float32_bands): relative error of the quadratic form
+    # in its worst direction <= (32 + 24 kappa) u
+    a, b, c = orec[ok, 2], orec[ok, 3], orec[ok, 4]
+    M = np.stack([np.stack([a, b], -1), np.stack([b, c], -1)], -2)
+    G = np.stack([np.stack([rec[ok, 2], rec[ok, 3]], -1), np.stack([rec[ok, 3], rec[ok, 4]], -1)], -2) / kH
+    w, V = np.linalg.eigh(M)
+    E = np.einsum("nji,njk,nkl->nil", V, G - M, V) / np.sqrt(w[:, :, None] * w[:, None, :])
+    rel = np.abs(np.linalg.eigvalsh(E)).max(-1)
+    kappa = w[:, 1] / w[:, 0]
+    u = 2.0 ** -24
+    assert np.all(rel <= (32 + 24 * kappa) * u), float(np.max(rel / ((32 + 24 * kappa) * u)))
+    np.testing.assert_allclose(2.0 ** rec[ok, 5], orec[ok, 5], rtol=1e-6)
+    np.testing.assert_allclose(rec[ok, 6], 1.0 / orec[ok, 9], rtol=2e-7)
+    np.testing.assert_allclose(rec[ok, 8:11], orec[ok, 6:9], atol=2e-6)
+    # exact tile count: the tiles that meet the widened level set
+    # t (1 + 2^-10) + 2^-12 (pinned outside a relative band of 1e-4, which
+    # float32 may decide either way)
     tiles = obin.tile_min_q(orec, cam.width, cam.height)
     for gid in np.nonzero(orec[:, 11] > 0)[0][:: max(1, scene.n // 1500)]:
         ids, mq, t = tiles.get(gid, (np.zeros(0, int), np.zeros(0), 0.0))
-        required = int((mq <= t).sum())
-        allowed = int((mq <= (t * (1 + 2 ** -10) + 2 ** -12) * (1 + 1e-4)).sum())
+        tw = t * (1 + 2 ** -10) + 2 ** -12
+        required = int((mq <= tw * (1 - 1e-4)).sum())
+        allowed = int((mq <= tw * (1 + 1e-4)).sum())
         assert required <= touched[gid] <= allowed, (gid, required, touched[gid], allowed)
 
 
@@ -124,14 +143,21 @@ def test_binning_lists_match_oracle_and_lb_equals_sq(gs):
     assert np.all(np.diff(tile) >= 0)
     _, orec = _oracle_records(scene, cam)
     tiles = obin.tile_min_q(orec, cam.width, cam.height)
-    req = {}
-    allow = {}
+    # The kernel bins against the level set widened to t (1 + 2^-10) + 2^-12
+    # (so every pixel a float32 blend can reach is in a touched tile).  Its
+    # tile set is pinned to the oracle's widened set, tile by tile, except
+    # where the tile's minimum of the quadratic form is within 1e-4 (relative)
+    # of the widened level, which float32 may decide either way.
+    req, allow, band_tiles = {}, {}, 0
     for gid, (ids, mq, t) in tiles.items():
+        tw = t * (1 + 2 ** -10) + 2 ** -12
         for tid, q in zip(ids.tolist(), mq.tolist()):
-            if q <= t:
+            if q <= tw * (1 - 1e-4):
                 req.setdefault(tid, set()).add(gid)
-            if q <= (t * (1 + 2 ** -10) + 2 ** -12) * (1 + 1e-4):
+            if q <= tw * (1 + 1e-4):
                 allow.setdefault(tid, set()).add(gid)
+            band_tiles += int(tw * (1 - 1e-4) < q <= tw * (1 + 1e-4))
+    assert band_tiles <= 1e-3 * n_inst, band_tiles
     z = orec[:, 9]
     for tid in range(ranges.shape[0]):
         s, e = ranges[tid]
@@ -140,10 +166,10 @@ def test_binning_lists_match_oracle_and_lb_equals_sq(gs):
         gs_set = set(got)
         assert len(gs_set) == len(got)
         assert req.get(tid, set()) <= gs_set <= allow.get(tid, set()), tid
-        # depth order, ties by index (float32 near-ties may swap)
+        # depth order: the float32 depth, ties by index
+        zf = z.astype(np.float32)
         for a, b in zip(got[:-1], got[1:]):
-            if abs(z[a] - z[b]) > 2.4e-7 * z[a]:
-                assert (z[a], a) < (z[b], b), (tid, a, b)
+            assert (zf[a], a) < (zf[b], b), (tid, a, b)
 
 
 # --------------------------------------------------------------- forward
@@ -154,7 +180,11 @@ TUNINGS = [None, {"bucket": 64, "bwd_warps": 2, "bwd_chains": 2}, {"bucket": 64,
 
 
 @pytest.mark.parametrize("which", ["c1", "clustered_ragged"])
-def test_render_fwd_matches_oracle(gs, which):
+def test_render_fwd_matches_oracle(gs, which, record_property):
+    """Every pixel against the oracle: colour, disparity and T within the
+    per-pixel tolerance (plus the oracle's float32 bound), and the id of the
+    last blended Gaussian bit-exact; at branch-flagged pixels the canonical
+    branch or one of the oracle's alternatives."""
     if which == "c1":
         scene, cam = synth.scene_c1(0), synth.camera_c1()
     else:
@@ -162,18 +192,14 @@ def test_render_fwd_matches_oracle(gs, which):
         cam = synth.ring_cameras(4, 333, 187)[2]  # ragged: partial tiles on both edges
     plan, params, rgb, disp, T = _run_forward(gs, scene, [cam])
     _, orec = _oracle_records(scene, cam)
-    ref = oren.render_fwd(orec, BG, (0, 0, cam.width, cam.height), amb=AMB_FOR(cam))
-    ok = ~ref["amb"]
-    assert ref["amb"].mean() < 5e-3, ref["amb"].mean()
     W, H = cam.width, cam.height
-    g_rgb = view_image(rgb, W, H)
-    g_disp = view_image(disp, W, H, channels=1)[0]
-    g_T = view_image(T, W, H, channels=1)[0]
-    for ch in range(3):
-        bad = pixel_mismatch(g_rgb[ch], ref["rgb"][ch], ok)
-        assert bad.sum() == 0, (ch, bad.sum(), np.abs(g_rgb[ch] - ref["rgb"][ch])[bad].max())
-    assert pixel_mismatch(g_disp, ref["disp"], ok).sum() == 0
-    assert pixel_mismatch(g_T, ref["T"], ok).sum() == 0
+    ref = oren.render_fwd(orec, BG, (0, 0, W, H), amb=AMB)
+    last = gpu_last_ids(plan, [(W, H)], scene.n)[0]
+    st = check_forward(view_image(rgb, W, H), view_image(disp, W, H, channels=1)[0],
+                       view_image(T, W, H, channels=1)[0], last, ref)
+    print(which, format_stats(st))
+    record_property("parity", format_stats(st))
+    assert_forward(st, MAX_BRANCH_FRAC)
 
 
 # -------------------------------------------------------------- backward
@@ -194,10 +220,8 @@ def test_render_bwd_matches_oracle(gs, which, tuning):
     W, H = cam.width, cam.height
     plan, params, rgb, disp, T = _run_forward(gs, scene, [cam], tuning=tuning)
     _, orec = _oracle_records(scene, cam)
-    ref = oren.render_fwd(orec, BG, (0, 0, W, H), amb=AMB_FOR(cam))
+    # the upstream gradient covers every pixel, flagged ones included
     g, gd = synth.upstream_grads(11, W, H)
-    g[:, ref["amb"]] = 0.0
-    gd[ref["amb"]] = 0.0
     grads = params.zeros_like()
     api.gs_render_bwd(plan, params, [cam], BG, rgb, disp, torch.from_numpy(g.reshape(-1)).cuda(),
                       torch.from_numpy(gd.reshape(-1)).cuda(), grads)
@@ -205,20 +229,26 @@ def test_render_bwd_matches_oracle(gs, which, tuning):
     g2d = to_np(plan.view(L.GS_WS_GRAD2D, torch.float32)).reshape(-1, 12)
     gpu10 = np.stack([g2d[:, 0], g2d[:, 1], g2d[:, 2], g2d[:, 3], g2d[:, 4], g2d[:, 5], g2d[:, 8],
                       g2d[:, 9], g2d[:, 10], g2d[:, 6]], 1)
-    ref2d = oren.render_bwd(orec, BG, (0, 0, W, H), g.astype(np.float64), gd.astype(np.float64))
+    ref2d, slack = oren.render_bwd(orec, BG, (0, 0, W, H), g.astype(np.float64), gd.astype(np.float64),
+                                   amb=AMB, with_slack=True)
+    assert np.isfinite(slack).all()  # no unresolved pixel
+    n_slack = int((slack.sum(1) > 0).sum())
     names = ["mx", "my", "a", "b", "c", "o", "r", "g", "b", "invz"]
     for k in range(10):
-        bad = grad_mismatch(gpu10[:, k], ref2d[:, k])
+        bad = grad_mismatch(gpu10[:, k], ref2d[:, k], slack=slack[:, k])
         idx = np.nonzero(bad)[0][:5]
-        assert bad.sum() == 0, (names[k], bad.sum(), idx, gpu10[idx, k], ref2d[idx, k],
+        assert bad.sum() == 0, (names[k], bad.sum(), idx, gpu10[idx, k], ref2d[idx, k], slack[idx, k],
                                 np.abs(ref2d[:, k]).max())
-    # parameters: oracle preprocess backward of the oracle's 2D gradients
+    # parameters: oracle preprocess backward of the oracle's 2D gradients, the
+    # slack carried through the absolute Jacobian
     ref_p = opre.preprocess_backward(scene, cam, ref2d)
+    slack_p = opre.preprocess_backward_abs(scene, cam, slack)
     for name, t in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), grads.tensors()):
         got = to_np(t)
-        bad = grad_mismatch(got, ref_p[name])
+        bad = grad_mismatch(got, ref_p[name], slack=slack_p[name])
         idx = np.nonzero(bad.reshape(bad.shape[0], -1).any(axis=1))[0][:3]
         assert bad.sum() == 0, (name, bad.sum(), idx, got[idx], ref_p[name][idx])
+    print(which, tuning, f"Gaussians reaching a flagged pixel: {n_slack} of {scene.n}")
 
 
 # ------------------------------------------------------------------ loss

@@ -53,7 +53,9 @@ def test_quaternion_rotation_matches_scipy():
 
 
 def _pinhole(cam, pc):
-    return np.array([cam.fx * pc[0] / pc[2] + cam.cx, cam.fy * pc[1] / pc[2] + cam.cy])
+    # the intrinsics as the GPU receives them: rounded to float32
+    fx, fy, cx, cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+    return np.array([fx * pc[0] / pc[2] + cx, fy * pc[1] / pc[2] + cy])
 
 
 def _num_jac(cam, pc, h=1e-6):
@@ -78,8 +80,8 @@ def test_jacobian_and_covariance_against_numerical_projection():
             pc = R @ scene.means[i].astype(np.float64) + t
             if pc[2] <= 0.2:
                 continue
-            limx = 1.3 * cam.width / (2 * cam.fx)
-            limy = 1.3 * cam.height / (2 * cam.fy)
+            limx = 1.3 * cam.width / (2 * float(np.float32(cam.fx)))
+            limy = 1.3 * cam.height / (2 * float(np.float32(cam.fy)))
             pcl = pc.copy()
             pcl[0] = np.clip(pc[0] / pc[2], -limx, limx) * pc[2]
             pcl[1] = np.clip(pc[1] / pc[2], -limy, limy) * pc[2]

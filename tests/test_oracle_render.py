@@ -104,6 +104,7 @@ def test_golden_one_pixel_blend_worked_by_hand():
     np.testing.assert_allclose(f["disp"][0, 0], want["disp"][0], rtol=0, atol=1e-14)
     np.testing.assert_allclose(f["T"][0, 0], want["T"][0], rtol=0, atol=1e-15)
     assert f["count"][0, 0] == int(want["blended"][0])
+    assert f["last"][0, 0] == int(want["last"][0])
 
 
 def test_alpha_cutoff_either_side_of_one_over_255():
@@ -273,3 +274,122 @@ def test_threads_do_not_change_results():
     a = render.render_bwd(r, BLACK, (0, 0, 256, 256), g, gd, n_threads=1)
     b = render.render_bwd(r, BLACK, (0, 0, 256, 256), g, gd, n_threads=4)
     np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Where float32 may decide a branch: flags, alternatives and slack.
+
+F32 = render.float32_bands()
+
+
+def _stack_rows(alphas, z0=1.0):
+    """Splats centred on pixel (0, 0) with the given alphas (power = 0), at
+    increasing depths, colours distinct per splat."""
+    return [rec(0.5, 0.5, 1.0, 0.0, 1.0, a, (0.1 * (k + 1), 1.0 - 0.1 * k, 0.5), z0 + k) for k, a in enumerate(alphas)]
+
+
+def _blend_by_hand(alphas, bg, rows):
+    T, C, D = 1.0, np.zeros(3), 0.0
+    for a, r in zip(alphas, rows):
+        C += np.array(r[6:9]) * a * T
+        D += a * T / r[9]
+        T *= 1.0 - a
+    return C + T * np.array(bg), D, T
+
+
+def test_alternatives_at_the_cut_the_clamp_and_the_stop():
+    """A splat whose alpha sits just above 1/255, one just above the 0.99
+    clamp, and a stop whose T (1 - alpha) lies just above 1e-4: each decision
+    is flagged, and each alternative (the decision taken the other way) is the
+    hand-computed blend of that branch."""
+    bg = (0.2, 0.3, 0.4)
+    # the cut: alpha = (1/255)(1 + 1e-9)
+    a_cut = (1 / 255) * (1 + 1e-9)
+    rows = _stack_rows([0.3, a_cut, 0.5])
+    f = render.render_fwd(records(rows), bg, (0, 0, 1, 1), amb=F32)
+    assert f["flags"][0, 0] & render.F_CUT
+    C, D, T = _blend_by_hand([0.3, a_cut, 0.5], bg, rows)
+    np.testing.assert_allclose(f["rgb"][:, 0, 0], C, rtol=1e-13)
+    assert len(f["alts"]["pix"]) == 1
+    C2, D2, T2 = _blend_by_hand([0.3, 0.5], bg, [rows[0], rows[2]])
+    np.testing.assert_allclose(f["alts"]["val"][0], [*C2, D2, T2], rtol=1e-13)
+    assert f["alts"]["last"][0] == 2
+    # the clamp: o = 0.99 (1 + 1e-9) blends 0.99 (no gradient); the
+    # alternative blends o itself
+    o = 0.99 * (1 + 1e-9)
+    rows = _stack_rows([0.4, o])
+    f = render.render_fwd(records(rows), bg, (0, 0, 1, 1), amb=F32)
+    assert f["flags"][0, 0] & render.F_CLAMP
+    C, D, T = _blend_by_hand([0.4, 0.99], bg, rows)
+    np.testing.assert_allclose(f["T"][0, 0], T, rtol=1e-13)
+    C2, D2, T2 = _blend_by_hand([0.4, o], bg, rows)
+    np.testing.assert_allclose(f["alts"]["val"][0], [*C2, D2, T2], rtol=1e-12)
+    # the stop: after three splats of alpha 0.9 (T = 1e-3), a fourth with
+    # T (1 - alpha) = 1e-4 (1 + 1e-9) is blended; the alternative stops
+    # there (three splats blended, last id 2)
+    a4 = 1.0 - 0.1 * (1 + 1e-9)
+    rows = _stack_rows([0.9, 0.9, 0.9, a4, 0.3])
+    f = render.render_fwd(records(rows), bg, (0, 0, 1, 1), amb=F32)
+    assert f["flags"][0, 0] & render.F_STOP
+    assert f["count"][0, 0] == 4 and f["last"][0, 0] == 3  # the fifth would stop
+    C2, D2, T2 = _blend_by_hand([0.9, 0.9, 0.9], bg, rows[:3])
+    alt = [k for k in range(len(f["alts"]["pix"])) if f["alts"]["last"][k] == 2]
+    assert len(alt) == 1
+    np.testing.assert_allclose(f["alts"]["val"][alt[0]], [*C2, D2, T2], rtol=1e-12)
+    # far from every threshold: nothing flagged, no alternative
+    rows = _stack_rows([0.3, 0.2, 0.5])
+    f = render.render_fwd(records(rows), bg, (0, 0, 1, 1), amb=F32)
+    assert f["flags"][0, 0] == 0 and len(f["alts"]["pix"]) == 0
+
+
+def test_slack_is_the_change_of_each_gaussians_gradient_under_the_other_branch():
+    """At a flagged cut, the slack of every Gaussian is the largest change of
+    its 2D gradient between the two branches, which equals the difference of
+    the oracle's own backward on records nudged to either side of the cut."""
+    bg = (0.2, 0.3, 0.4)
+    a_cut = (1 / 255) * (1 + 1e-9)
+    base = _stack_rows([0.3, a_cut, 0.5])
+    g = np.array([0.7, -0.4, 0.9]).reshape(3, 1, 1)
+    gd = np.array([[0.3]])
+    grad, slack = render.render_bwd(records(base), bg, (0, 0, 1, 1), g, gd, amb=F32, with_slack=True)
+    below = [list(r) for r in base]
+    below[1][5] = (1 / 255) * (1 - 1e-9)
+    below[1][10] = 2 * math.log(255 * below[1][5])
+    g_below = render.render_bwd(records(below), bg, (0, 0, 1, 1), g, gd)
+    np.testing.assert_allclose(slack, np.abs(g_below - grad), rtol=1e-6, atol=1e-12)
+    assert slack[1].max() > 0 and slack[2].max() > 0 and slack[0].max() > 0
+
+
+def test_depth_order_is_the_float32_depth_ties_by_index():
+    """Two splats whose depths differ by less than half a float32 ulp round
+    to the same float32 depth: they blend in index order, although the
+    float64 depths would put the second one first."""
+    z = 3.0
+    rows = [rec(0.5, 0.5, 1.0, 0.0, 1.0, 0.6, (1, 0, 0), z + 1e-9),
+            rec(0.5, 0.5, 1.0, 0.0, 1.0, 0.5, (0, 1, 0), z)]
+    assert np.float32(z + 1e-9) == np.float32(z)
+    f = render.render_fwd(records(rows), BLACK, (0, 0, 1, 1))
+    want = 0.6 * np.array([1, 0, 0]) + 0.5 * 0.4 * np.array([0, 1, 0])
+    np.testing.assert_allclose(f["rgb"][:, 0, 0], want, rtol=1e-13)
+    assert f["last"][0, 0] == 1
+    # one float32 ulp apart: depth order
+    rows[0][9] = float(np.nextafter(np.float32(z), np.float32(np.inf)))
+    f = render.render_fwd(records(rows), BLACK, (0, 0, 1, 1))
+    want = 0.5 * np.array([0, 1, 0]) + 0.6 * 0.5 * np.array([1, 0, 0])
+    np.testing.assert_allclose(f["rgb"][:, 0, 0], want, rtol=1e-13)
+    assert f["last"][0, 0] == 0
+
+
+def test_value_bound_of_one_splat():
+    """With only the fixed band eps of ln alpha and the rounding t of T, a
+    pixel under one splat (alpha, colour c, background b) has the bounds
+    alpha |c - b| eps + b (1 - alpha) t for a colour channel,
+    alpha eps / z for the disparity and alpha eps + (1 - alpha) t for T."""
+    eps, t = 1e-6, 2e-7
+    amb = (eps, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, t, 0.0)
+    a, z = 0.6, 2.0
+    bg = (0.2, 0.3, 0.4)
+    col = (0.9, 0.1, 0.5)
+    f = render.render_fwd(records([rec(0.5, 0.5, 1.0, 0.0, 1.0, a, col, z)]), bg, (0, 0, 1, 1), amb=amb)
+    want = [a * abs(c - b) * eps + b * (1 - a) * t for c, b in zip(col, bg)] + [a * eps / z, a * eps + (1 - a) * t]
+    np.testing.assert_allclose(f["bound"][:, 0, 0], want, rtol=1e-12)

@@ -1,9 +1,9 @@
 """The allocation-free sort entry point (gs_sort_pairs_u32_noalloc).
 
-It exists for callers that cannot allocate device memory: code inside a CUDA
-graph capture in global mode, plug-ins whose host framework owns every byte
-of device memory, and loops that cannot afford cudaMalloc's implicit device
-synchronisation.  These tests call it through the C ABI and check that it
+It exists for callers that cannot allocate device memory: plug-ins whose
+host framework owns every byte of device memory, code under a fixed
+device-memory budget, and loops that cannot afford cudaMalloc's implicit
+device synchronisation.  These tests call it through the C ABI and check that it
 returns exactly what the scratch-taking gs_sort_pairs_u32 returns, on two
 calls in a row (the second call reuses the static scratch the first one left
 behind), and that it refuses sizes beyond its stated maximum.
