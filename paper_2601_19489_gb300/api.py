@@ -92,7 +92,7 @@ class Plan:
 
     def __init__(self, n: int, sh_degree: int, sizes, inst_capacity: int, device="cuda",
                  tuning: dict | None = None):
-        """tuning: optional {"bucket": 32 | 64, "bwd_warps": 2 | 4 | 8,
+        """tuning: optional {"bucket": 32 | 64, "bwd_warps": 1 | 2 | 4 | 8,
         "bwd_chains": 0 | 1 | 2, "bbox_3sigma": 0 | 1, "bwd_per_pixel": 0 | 1}
         (the last two are the Tab. 1 ablation switches)."""
         lib = L.lib()

@@ -4,10 +4,11 @@ The choices change speed, not results (beyond float32 summation order):
   load_balanced  warp-cooperative (LB) or one-thread-per-Gaussian (Sq) tile-key
                  write of the binning (Sec. 2.1 compares the two);
   bucket         splats per checkpoint bucket and per backward work unit
-                 (Sec. 2.2 uses 32; 64 halves the checkpoint traffic);
+                 (Sec. 2.2 uses 32; 64 halves the checkpoint traffic and runs
+                 the backward with two splats per lane in packed pairs);
   bwd_warps      warps per CTA of the per-Gaussian backward;
-  bwd_chains     pixel chains per lane of the backward pipeline (1, 2, or
-                 0: chosen per bucket by its live pixel count).
+  bwd_chains     pixel chains per lane of the 32-splat backward pipeline (1,
+                 2, or 0: chosen per bucket by its live pixel count).
 Tile size stays at the paper's 16 x 16 (Sec. 2.2).
 
 ``autotune`` times a few real training steps of candidates on the caller's
@@ -28,8 +29,12 @@ from .trainer import Trainer
 
 BINNING = ({"load_balanced": True, "bucket": 32, "bwd_warps": 4, "bwd_chains": 0},
            {"load_balanced": False, "bucket": 32, "bwd_warps": 4, "bwd_chains": 0})
-SHAPES = tuple({"bucket": b, "bwd_warps": w, "bwd_chains": c}
-               for b, w, c in itertools.product((32, 64), (2, 4, 8), (0, 1, 2)))
+# 32-splat buckets: one splat per lane, CTA width and pixel chains searched;
+# 64-splat buckets: two splats per lane in packed pairs (one chain), CTA
+# width searched
+SHAPES = (tuple({"bucket": 32, "bwd_warps": w, "bwd_chains": c}
+                for w, c in itertools.product((2, 4, 8), (0, 1, 2)))
+          + tuple({"bucket": 64, "bwd_warps": w, "bwd_chains": 0} for w in (1, 2, 4)))
 
 
 def _key(c: dict) -> str:

@@ -17,8 +17,7 @@
 //     Each round of Gaussians writes its (contiguous) run of instances.
 //  4. stable radix sort of the instances by tile id: every tile's list keeps
 //     the depth order of step 1, ties in depth by ascending Gaussian index.
-//  5. tile ranges by binary search in the sorted ids and the 32-splat bucket
-//     offsets.
+//  5. tile ranges by binary search in the sorted ids and the bucket offsets.
 #include "gs_internal.cuh"
 
 namespace gs {

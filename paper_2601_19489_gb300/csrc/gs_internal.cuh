@@ -117,6 +117,35 @@ int pose_compose(const gs_plan *plan, void *ws, const ViewsDev &vd, cudaStream_t
 
 // Radix sort internals (radix_sort.cu), usable with a device-resident count.
 size_t sort_scratch_bytes();
+
+// Element count of a fixed-grid pass: the host bound, or the device count
+// (the tile-instance count is only known on the device) capped by it.
+__device__ __forceinline__ int64_t sort_count(int64_t n_host, const uint32_t *n_dev) {
+    if (!n_dev) return n_host;
+    int64_t n = (int64_t)(*n_dev);
+    return n < n_host ? n : n_host;
+}
+// The lanes of the warp whose digit equals this lane's (digits of nbits
+// bits; a lane may pass 1 << nbits as "no digit", which matches only other
+// such lanes): one ballot per bit of the digit.
+#ifndef GS_RANK_BALLOT
+#define GS_RANK_BALLOT 1
+#endif
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d, int nbits) {
+#if GS_RANK_BALLOT
+    uint32_t peers = 0xffffffffu;
+    for (int b = 0; b <= nbits; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
+#else
+    (void)nbits;
+    return __match_any_sync(0xffffffffu, d);
+#endif
+}
+
 int sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b,
                int64_t n_host, const uint32_t *n_dev, int begin_bit, int end_bit, void *scratch,
                cudaStream_t s, int *final_buf);
@@ -238,6 +267,39 @@ __device__ __forceinline__ float2 tile_local_mean(const float4 &r0, float mx_lo,
     return make_float2(__fadd_rn(__fsub_rn(r0.x, x0), mx_lo), __fadd_rn(__fsub_rn(r0.y, y0), my_lo));
 }
 
+// Packed float32 pairs: two values side by side in one 64-bit register pair,
+// so one f32x2 instruction (round to nearest, element by element: the same
+// results as the scalar operations) serves both.
+typedef unsigned long long f2x;
+
+__device__ __forceinline__ f2x pk2(float a, float b) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f2x r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+    f2x d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+    f2x d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+    f2x d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+    f2x d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 struct PairEval {
     float dx, dy, power2, raw, alpha;
 };

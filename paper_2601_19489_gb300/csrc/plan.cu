@@ -60,7 +60,8 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     const int32_t bucket = tuning && tuning->bucket ? tuning->bucket : kBucket;
     const int32_t bwd_warps = tuning && tuning->bwd_warps ? tuning->bwd_warps : 4;
     const int32_t chains = tuning ? tuning->bwd_chains : 0;
-    if ((bucket != 32 && bucket != 64) || (bwd_warps != 2 && bwd_warps != 4 && bwd_warps != 8) || chains < 0 ||
+    if ((bucket != 32 && bucket != 64) || (bwd_warps != 1 && bwd_warps != 2 && bwd_warps != 4 && bwd_warps != 8) ||
+        chains < 0 ||
         chains > 2)
         return nullptr;
     if (n <= 0 || n >= (1ll << 31) || sh_degree < 0 || sh_degree > 3 || n_views < 1 ||

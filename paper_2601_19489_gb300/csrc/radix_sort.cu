@@ -8,7 +8,7 @@
 //   scan:      one block per digit scans that digit's block counts and
 //              writes the digit total; the downsweep adds the prefix of
 //              the lower digits' totals
-//   downsweep: block b ranks its chunk tile by tile (warp match_any ranking,
+//   downsweep: block b ranks its chunk tile by tile (warp ranking by ballots,
 //              stable), reorders each tile by digit in shared memory and
 //              writes it out with coalesced runs per digit.
 #include "gs_internal.cuh"
@@ -22,12 +22,6 @@ constexpr int kHist = kRadix * kSortBlocks;
 static_assert(kRadix == kSortThreads, "one thread per digit");
 
 size_t sort_scratch_bytes() { return (size_t)(kHist + kRadix) * sizeof(uint32_t); }
-
-__device__ __forceinline__ int64_t sort_count(int64_t n_host, const uint32_t *n_dev) {
-    if (!n_dev) return n_host;
-    int64_t n = (int64_t)(*n_dev);
-    return n < n_host ? n : n_host;
-}
 
 __global__ void __launch_bounds__(kSortThreads)
 k_upsweep(const uint32_t *__restrict__ keys, int64_t n_host, const uint32_t *n_dev, int shift,
@@ -113,6 +107,7 @@ k_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ v
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
+    const int nbits = 32 - __clz(mask);  // digit width; the value 1 << nbits marks "no item"
     const int64_t n = sort_count(n_host, n_dev);
     const int64_t chunk = (n + kSortBlocks - 1) / kSortBlocks;
     const int64_t beg = (int64_t)blockIdx.x * chunk;
@@ -149,18 +144,19 @@ k_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ v
                 v[r] = __ldg(vals_in + t0 + li);
                 dig[r] = (int)((k[r] >> shift) & mask);
             } else {
-                dig[r] = kRadix;  // sentinel: matches only other invalid lanes
+                dig[r] = 1 << nbits;  // no digit: matches only other lanes past the end
             }
         }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kItems; ++r) {
-            const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+            const bool has = dig[r] < (1 << nbits);
+            const uint32_t peers = warp_peers((uint32_t)dig[r], nbits);
             const int leader = __ffs(peers) - 1;
             uint32_t base = 0;
-            if (dig[r] < kRadix) base = wcnt[warp][dig[r]];
+            if (has) base = wcnt[warp][dig[r]];
             __syncwarp();
-            if (lane == leader && dig[r] < kRadix) wcnt[warp][dig[r]] = base + __popc(peers);
+            if (lane == leader && has) wcnt[warp][dig[r]] = base + __popc(peers);
             __syncwarp();
             rank[r] = base + __popc(peers & lt_mask);
         }
@@ -202,7 +198,7 @@ k_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ v
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kItems; ++r) {
-            if (dig[r] < kRadix) {
+            if (dig[r] < (1 << nbits)) {
                 const uint32_t pos = tile_start[dig[r]] + wcnt[warp][dig[r]] + rank[r];
                 skv[pos] = make_uint2(k[r], v[r]);
             }

@@ -132,15 +132,16 @@ def test_binning_lists_match_oracle_and_lb_equals_sq(gs):
     plan_sq, *_ = _run_forward(gs, scene, [cam], lb=False)
     n_inst = plan_lb.status()["n_instances"]
     assert n_inst == plan_sq.status()["n_instances"] > 0
-    for which in (L.GS_WS_INST_TILE, L.GS_WS_INST_GID, L.GS_WS_TILE_RANGES):
+    for which in (L.GS_WS_INST_GID, L.GS_WS_TILE_RANGES):
         a = to_np(plan_lb.view(which, torch.int32))
         b = to_np(plan_sq.view(which, torch.int32))
         n = n_inst if which != L.GS_WS_TILE_RANGES else a.size
         np.testing.assert_array_equal(a[:n], b[:n])
-    tile = to_np(plan_lb.view(L.GS_WS_INST_TILE, torch.int32))[:n_inst]
     item = to_np(plan_lb.view(L.GS_WS_INST_GID, torch.int32))[:n_inst]
     ranges = to_np(plan_lb.view(L.GS_WS_TILE_RANGES, torch.int32)).reshape(-1, 2)
-    assert np.all(np.diff(tile) >= 0)
+    # the ranges tile the instance list in tile order
+    assert ranges[0, 0] == 0 and ranges[-1, 1] == n_inst and np.all(ranges[1:, 0] == ranges[:-1, 1])
+    tile = np.repeat(np.arange(ranges.shape[0]), ranges[:, 1] - ranges[:, 0])
     _, orec = _oracle_records(scene, cam)
     tiles = obin.tile_min_q(orec, cam.width, cam.height)
     # The kernel bins against the level set widened to t (1 + 2^-10) + 2^-12
