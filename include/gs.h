@@ -116,16 +116,16 @@ GS_API gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views, co
  * summation order), for an autotuner to pick per workload:
  *   bucket     splats per checkpoint bucket of the forward and per unit of
  *              work of the per-Gaussian backward (Sec. 2.2 uses 32): 32 or
- *              64.  At 64 one warp walks a bucket as two 32-splat passes,
- *              carrying the per-pixel state between them in shared memory;
+ *              64.  At 64 each lane of the backward owns two adjacent splats
+ *              and evaluates both in packed float32 pairs, branch-free;
  *              checkpoint memory and traffic halve.
  *   bwd_warps  warps per CTA of the per-Gaussian backward (the warps of a CTA
- *              share one tile's staged pixel data): 2, 4 or 8.
- *   bwd_chains pixel chains a lane of the backward pipeline walks: 2 (two
- *              interleaved halves of the bucket's live pixels: more
+ *              share one tile's staged pixel data): 1, 2, 4 or 8.
+ *   bwd_chains pixel chains a lane of the 32-splat backward pipeline walks:
+ *              2 (two interleaved halves of the bucket's live pixels: more
  *              independent work per step), 1 (one chain: fewer idle steps
  *              while the pipeline fills and drains), or 0: two when the
- *              bucket has at least 128 live pixels, else one.
+ *              bucket has at least 128 live pixels, else one.  Ignored at 64.
  * A zero field takes the default (32, 4, 0).  gs_plan_create uses the
  * defaults.
  * Returns NULL on the same conditions as gs_plan_create or an unsupported
@@ -281,7 +281,8 @@ GS_API int gs_preprocess_bwd_adam(const gs_plan *plan, void *ws, gs_params *para
  * disp_weight * mean |disp - target_disp| (d_disp may be NULL to skip).
  * Writes dL/d(rgb) to d_dL_drgb and, if d_disp is given, dL/d(disp) to
  * d_dL_ddisp (both overwritten), and the scalar loss to d_loss (device, one
- * float).  d_scratch: device float scratch of gs_loss_scratch_floats(plan).
+ * float).  d_scratch: device float scratch of gs_loss_scratch_floats(plan),
+ * 8-byte aligned (GS_ERR_ARG otherwise).
  * lambda = 0 gives plain L1 and skips the SSIM passes. */
 GS_API int64_t gs_loss_scratch_floats(const gs_plan *plan);
 GS_API int gs_loss(const gs_plan *plan, const float *d_rgb, const float *d_target, float lambda,
@@ -382,6 +383,17 @@ GS_API int gs_ng_decode_bwd(const gs_ng_params *ng, const gs_camera *h_cam, cons
 /* Synchronise `stream` and read the decoder's device status (GS_ERR_TIMEOUT
  * if a bounded wait for the tensor cores gave up). */
 GS_API int gs_ng_read_status(void *d_ws, int32_t *out_error, void *stream);
+/* Failure detection of the decoder's bounded waits, checked without a fault:
+ * one thread of a one-block launch initialises an mbarrier for one arrival
+ * and waits for its first phase with the same bounded wait the tensor-core
+ * kernels use, giving up after `limit` tries (1 .. 2^22).  With arrive = 0
+ * nothing arrives (no copy and no MMA is in flight), the wait runs out and
+ * GS_ERR_TIMEOUT is written to *d_err (device int32, left alone if already
+ * non-zero); with arrive = 1 the thread arrives first and *d_err is not
+ * touched.  The paper has no counterpart; the kernels it checks are the
+ * decoder's (Sec. 2.3).  Returns GS_ERR_ARG for a NULL d_err, a limit
+ * outside the range or arrive not 0 or 1. */
+GS_API int gs_ng_wait_probe(int32_t *d_err, int64_t limit, int32_t arrive, void *stream);
 
 /* ------------------------------ densification and pruning (Sec. 3.2)
  * Multi-view score-guided densification and pruning, in three calls:

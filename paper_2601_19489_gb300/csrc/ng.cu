@@ -67,10 +67,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Wait for the mbarrier phase with the given parity; false after kWaitLimit tries.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for the mbarrier phase with the given parity; false after `limit`
+// tries (kWaitLimit in every kernel of the decoder).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = kWaitLimit) {
     const uint32_t a = smem_u32(bar);
-    for (long long i = 0; i < kWaitLimit; ++i) {
+    for (long long i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -943,6 +944,35 @@ extern "C" int gs_ng_decode_bwd(const gs_ng_params *p, const gs_camera *cam, con
     ng::k_ng_bwd<<<tiles, ng::kThreads, smem, s>>>(A);
     ng::k_ng_reduce<<<(ng::kPartial + ng::kRedCols - 1) / ng::kRedCols, ng::kRedCols * ng::kRedRows, 0, s>>>(
         A.partial, tiles, grads->w2, grads->w1, grads->b2, grads->b1);
+    return launch_error();
+}
+
+namespace gs {
+namespace ng {
+
+// The bounded wait on its own: one thread initialises an mbarrier for one
+// arrival and waits for its first phase.  With arrive = 0 nothing ever
+// arrives (no thread, no copy, no MMA is in flight), so the wait must give
+// up after `limit` tries and record GS_ERR_TIMEOUT; with arrive = 1 the
+// thread arrives first and the wait must succeed.
+__global__ void k_wait_probe(int32_t *err, long long limit, int arrive) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    if (arrive) {
+        uint64_t state;
+        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(&bar)) : "memory");
+        (void)state;
+    }
+    if (!mbar_wait(&bar, 0, limit)) atomicCAS(err, 0, GS_ERR_TIMEOUT);
+}
+
+}  // namespace ng
+}  // namespace gs
+
+extern "C" int gs_ng_wait_probe(int32_t *d_err, int64_t limit, int32_t arrive, void *stream) {
+    if (!d_err || limit < 1 || limit > ng::kWaitLimit || (arrive != 0 && arrive != 1)) return GS_ERR_ARG;
+    ng::k_wait_probe<<<1, 32, 0, (cudaStream_t)stream>>>(d_err, (long long)limit, arrive);
     return launch_error();
 }
 

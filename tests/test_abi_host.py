@@ -231,3 +231,13 @@ def test_more_argument_errors_are_caught_on_the_host(lib):
     ng.n_anchors = 4
     assert lib.gs_ng_decode_fwd(ctypes.byref(ng), ctypes.byref(L.GsCamera()), ctypes.byref(kids), fake,
                                 None) == ARG
+
+
+def test_wait_probe_arguments_are_checked_on_the_host(lib):
+    from paper_2601_19489_gb300 import _lib as L
+
+    fake = ctypes.c_void_p(4096)
+    assert lib.gs_ng_wait_probe(None, 10, 0, None) == L.GS_ERR_ARG
+    assert lib.gs_ng_wait_probe(fake, 0, 0, None) == L.GS_ERR_ARG
+    assert lib.gs_ng_wait_probe(fake, (1 << 22) + 1, 0, None) == L.GS_ERR_ARG
+    assert lib.gs_ng_wait_probe(fake, 10, 2, None) == L.GS_ERR_ARG

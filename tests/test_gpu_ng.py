@@ -253,3 +253,34 @@ def test_ng_decode_forward_at_full_size_on_sampled_anchors(gs):
         tol = 1e-4 * np.abs(r) + 2e-5
         assert np.all(err[ok] <= tol[ok]), (k, err[ok].max())
         assert np.all(err <= 0.05 * np.abs(r) + 0.05), (k, err.max())
+
+
+def test_bounded_wait_runs_out_and_reports_a_timeout(gs):
+    """Failure detection without a GPU fault: the decoder's bounded mbarrier
+    wait, on a barrier nothing arrives on (no copy and no MMA in flight),
+    gives up after its try limit and records GS_ERR_TIMEOUT; the launch
+    returns and the context stays usable.  With an arrival first, the same
+    wait succeeds and records nothing."""
+    import time
+
+    from paper_2601_19489_gb300 import _lib as L
+
+    lib = L.load()
+    s = torch.cuda.current_stream().cuda_stream
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    assert lib.gs_ng_wait_probe(err.data_ptr(), 1000, 0, s) == 0
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 5.0
+    assert int(err.item()) == L.GS_ERR_TIMEOUT
+    err.zero_()
+    assert lib.gs_ng_wait_probe(err.data_ptr(), 1000, 1, s) == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    # the context is still usable after the timed-out wait
+    x = torch.arange(1000, device="cuda", dtype=torch.float32)
+    assert float(x.sum().item()) == 499500.0
+    # arguments outside the stated range are refused before any launch
+    assert lib.gs_ng_wait_probe(err.data_ptr(), 0, 0, s) == L.GS_ERR_ARG
+    assert lib.gs_ng_wait_probe(err.data_ptr(), (1 << 22) + 1, 0, s) == L.GS_ERR_ARG
+    assert lib.gs_ng_wait_probe(None, 10, 0, s) == L.GS_ERR_ARG
