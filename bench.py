@@ -39,13 +39,17 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # Algorithmic floating-point work per evaluated pixel-splat pair, counted
 # from the kernels' arithmetic (FMA = 2): forward blend 25, backward 62.
 FLOP_PER_PAIR = {"render_fwd": 25.0, "render_bwd_blend": 62.0}
+# CPU oracle samples: 16 x 16 windows per reference-arm step and in the
+# cpu_baseline leg
+REF_WINDOWS = 12
+BASELINE_WINDOWS = 24
 # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, 1 pass, on this workload at full size: 1M Gaussians,
 # one 1920x1080 view), valid only for the kernel source they were taken on
 # (sha256 of the .cu file, first 16 hex digits) and the same launch shape.
 NCU_TRAFFIC: dict = {
-    "k_render_bwd": {"bytes_per_launch": 2.432e8, "src_sha": "569e52752364865d", "tuning": "LB/b32/w2/c1",
-                     "read": 2.394e8, "write": 3.83e6},
+    "k_render_bwd_pk": {"bytes_per_launch": 1.7251e8, "src_sha": "e05c8d2d9f574e78", "tuning": "LB/b64/w1/c0",
+                        "read": 1.6838e8, "write": 4.13e6},
 }
 
 
@@ -71,7 +75,7 @@ def parse_args():
                     help="batched: only the 8-view CUDA-graph step, one line per --batched-n; "
                          "recon60: held-out PSNR after a timed reconstruction")
     ap.add_argument("--recon-budget", type=float, default=60.0, help="seconds of training per method")
-    ap.add_argument("--recon-methods", type=str, default="plain,densify,batched_graph,ng")
+    ap.add_argument("--recon-methods", type=str, default="plain,densify,batched_graph,ng,ng_frozen")
     ap.add_argument("--densify-tau-plus", type=float, default=5.0)
     ap.add_argument("--batched-n", type=str, default="",
                     help="comma-separated Gaussian counts for --workload batched (default: --n)")
@@ -92,10 +96,36 @@ def workload(args):
     return scene, cams
 
 
+def render_targets(n: int, cams, dev, seed: int = 1, bg=(0.0, 0.0, 0.0)):
+    """Training targets: a second seeded clustered scene of the same kind (n
+    Gaussians, SH degree 3) rendered through the same cameras by the CUDA
+    forward, one flat planar colour image per camera (device tensors).  A
+    workload to fit, not a parity reference: the oracle would take hours per
+    1080p view of a 1M-Gaussian scene."""
+    import torch
+
+    import synth
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import Trainer
+
+    tgt_scene = synth.scene_clustered(n, seed=seed, sh_degree=3)
+    tr = Trainer(api.Gaussians.from_scene(tgt_scene, device=dev), lam=0.2, bg=bg, device=dev)
+    tr.ensure_capacity([[c] for c in cams])
+    out = []
+    for c in cams:
+        sl = tr.forward([c])
+        out.append(sl.rgb[: 3 * c.width * c.height].clone())
+    torch.cuda.synchronize()
+    del tr
+    torch.cuda.empty_cache()
+    return out
+
+
 def config_of(args):
     return {"workload": f"clustered {args.n} Gaussians SH3, {args.views} ring views {args.width}x{args.height}, "
                         f"16x16 tiles, loss {1 - args.lam:.1f} L1 + {args.lam:.1f} D-SSIM, one view per step",
             "gaussians": args.n, "views": args.views, "width": args.width, "height": args.height,
+            "targets": "a second seeded clustered scene (seed 1, same size) rendered through the same cameras",
             "tile": 16, "bucket": 32, "sh_degree": 3, "binning": "sequential" if args.sq else "load_balanced",
             "l2": "working set > L2 (params + Adam state ~1 GB, instances, checkpoints); no flush"}
 
@@ -160,13 +190,31 @@ def src_sha(name: str) -> str:
 
 # ------------------------------------------------------------ CPU oracle
 
-def oracle_sample(scene, cam, target, window_px: int, pre_sample: int, n_threads: int, seed: int = 0):
+def sample_windows(W: int, H: int, k: int, seed: int, size: int = 16):
+    """k non-overlapping size x size windows at seeded positions, one per
+    distinct cell of a grid of 240 x 216-pixel cells (anywhere inside the
+    cell), so the sample covers the whole image rather than its centre."""
+    rng = np.random.default_rng(seed)
+    nx, ny = max(1, W // 240), max(1, H // 216)
+    cw, ch = W // nx, H // ny
+    cells = rng.choice(nx * ny, size=min(k, nx * ny), replace=False)
+    out = []
+    for c in cells:
+        x0 = (c % nx) * cw + int(rng.integers(0, max(1, cw - size)))
+        y0 = (c // nx) * ch + int(rng.integers(0, max(1, ch - size)))
+        out.append((int(x0), int(y0), int(x0) + size, int(y0) + size))
+    return out
+
+
+def oracle_sample(scene, target_scene, cam, n_windows: int, pre_sample: int, n_threads: int, seed: int = 0):
     """Time the float64 oracle on a bounded sample of one training step and
     extrapolate to the whole step.  Returns (seconds per full step, detail).
 
     preprocess fwd+bwd and Adam: a random subset of `pre_sample` Gaussians,
-    scaled by N / pre_sample; blend fwd + loss + per-pixel bwd: a window of
-    window_px^2 pixels at the image centre, scaled by H*W / window_px^2."""
+    scaled by N / pre_sample; blend fwd + loss + per-pixel bwd: n_windows
+    16 x 16 windows spread over the image (sample_windows), scaled by
+    H * W / (n_windows * 256).  The target inside each window is the
+    oracle's own render of target_scene there (setup, untimed)."""
     import torch
 
     from oracle import preprocess as opre
@@ -180,33 +228,37 @@ def oracle_sample(scene, cam, target, window_px: int, pre_sample: int, n_threads
     N = scene.n
     sub = np.sort(rng.choice(N, size=min(pre_sample, N), replace=False))
     sub_scene = synth.Scene(*(a[sub] for a in scene.arrays()), sh_degree=scene.sh_degree)
-    # full records for the window render (setup, untimed: the subset's time
-    # below stands for the preprocess of every Gaussian)
+    W, H = cam.width, cam.height
+    wins = sample_windows(W, H, n_windows, seed)
+    # full records for the window renders and the windows' targets (setup,
+    # untimed: the subset's time below stands for the preprocess of every
+    # Gaussian)
     with torch.no_grad():
         rec = opre.pack_for_render(opre.project(opre.params_from_scene(scene), cam, scene.sh_degree))
-    W, H = cam.width, cam.height
-    x0 = W // 2 - window_px // 2
-    y0 = H // 2 - window_px // 2
-    win = (x0, y0, x0 + window_px, y0 + window_px)
+        trec = opre.pack_for_render(opre.project(opre.params_from_scene(target_scene), cam,
+                                                 target_scene.sh_degree))
+    tgts = [oren.render_fwd(trec, (0.0, 0.0, 0.0), w, amb=None, n_threads=n_threads)["rgb"] for w in wins]
     t0 = time.perf_counter()
     with torch.no_grad():
         opre.project(opre.params_from_scene(sub_scene), cam, scene.sh_degree)
     g2d = rng.standard_normal((sub.size, 10))
     grads = opre.preprocess_backward(sub_scene, cam, g2d)
     t1 = time.perf_counter()
-    f = oren.render_fwd(rec, (0.0, 0.0, 0.0), win, amb=None, n_threads=n_threads)
-    tgt = np.asarray(target, dtype=np.float64).reshape(3, H, W)[:, win[1]:win[3], win[0]:win[2]]
-    _, g_rgb = oloss.photometric(f["rgb"], tgt, 0.2)
-    oren.render_bwd(rec, (0.0, 0.0, 0.0), win, g_rgb, np.zeros_like(f["disp"]), n_threads=n_threads)
+    pairs = 0
+    for w, tgt in zip(wins, tgts):
+        f = oren.render_fwd(rec, (0.0, 0.0, 0.0), w, amb=None, n_threads=n_threads)
+        _, g_rgb = oloss.photometric(f["rgb"], tgt, 0.2)
+        oren.render_bwd(rec, (0.0, 0.0, 0.0), w, g_rgb, np.zeros_like(f["disp"]), n_threads=n_threads)
+        pairs += f["pairs"]
     t2 = time.perf_counter()
     for k, v in grads.items():
         oadam.adam_step(getattr(sub_scene, k), v, np.zeros_like(v), np.zeros_like(v), 1, 1e-3)
     t3 = time.perf_counter()
     scale_g = N / sub.size
-    scale_p = (W * H) / float(window_px * window_px)
+    scale_p = (W * H) / float(sum((w[2] - w[0]) * (w[3] - w[1]) for w in wins))
     est = (t1 - t0) * scale_g + (t2 - t1) * scale_p + (t3 - t2) * scale_g
     detail = {"preprocess_s": (t1 - t0) * scale_g, "render_s": (t2 - t1) * scale_p,
-              "adam_s": (t3 - t2) * scale_g, "measured_s": t3 - t0, "pairs": f["pairs"]}
+              "adam_s": (t3 - t2) * scale_g, "measured_s": t3 - t0, "pairs": pairs, "windows": len(wins)}
     return est, detail
 
 
@@ -217,12 +269,13 @@ def run_reference(args, rank, world):
     scene, cams = workload(args)
     import synth
 
+    target_scene = synth.scene_clustered(args.n, seed=1, sh_degree=3)
     n_threads = os.cpu_count() or 1
     times = []
     for s in range(args.warmup + args.steps):
         cam = cams[s % len(cams)]
-        target = synth.target_uniform(1000 + s % len(cams), cam.width, cam.height)
-        est, _ = oracle_sample(scene, cam, target, window_px=24, pre_sample=1 << 14, n_threads=n_threads, seed=s)
+        est, _ = oracle_sample(scene, target_scene, cam, n_windows=REF_WINDOWS, pre_sample=1 << 14,
+                               n_threads=n_threads, seed=s)
         if s >= args.warmup:
             times.append(est)
     value = 1.0 / float(np.mean(times))
@@ -231,8 +284,9 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(args), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_threads, "kind": "oracle",
-                             "sample": "per step: preprocess fwd+bwd and Adam on 16384 random Gaussians "
-                                       "(x N/16384), blend fwd+loss+bwd on a 24x24 centre window (x H*W/576)"},
+                             "sample": f"per step (view s mod 16, seed s): preprocess fwd+bwd and Adam on 16384 "
+                                       f"random Gaussians (x N/16384), blend fwd+loss+bwd on {REF_WINDOWS} seeded "
+                                       f"16x16 windows spread over the image (x H*W/({REF_WINDOWS}*256))"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -240,7 +294,7 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------ GPU arm
 
 def stage_roofline(stage_ms: dict, n: int, sh_degree: int, pixels: int, instances: float, pairs: float,
-                   hbm_gbs: float) -> dict:
+                   hbm_gbs: float, ssim: bool = True) -> dict:
     """Each stage's achieved rate against its bound, from the algorithmic
     work per unit (parameters of P = 4 (11 + 3 K) bytes per Gaussian):
       preprocess    P read + 76 B of records written per Gaussian      (HBM)
@@ -248,13 +302,17 @@ def stage_roofline(stage_ms: dict, n: int, sh_degree: int, pixels: int, instance
                     key write 8 B, tile sort 2 x 20 B and ranges 8 B
                     per instance                                       (HBM)
       render_fwd    25 FLOP per pixel-splat pair                       (FP32)
-      loss          48 B per pixel                                     (HBM)
+      loss          with SSIM: 1215 FLOP per pixel (per channel: x^2,
+                    y^2, x y 3; five 11-tap separable window sums 220;
+                    SSIM and its three partials 40; L1 2; three 11-tap
+                    separable sums of the maps 132; the gradient 8)    (FP32)
+                    plain L1: 36 B per pixel                           (HBM)
       render_bwd    62 FLOP per pixel-splat pair                       (FP32)
       fused bwd     2 P parameters + 4 P moments per Gaussian          (HBM)
     Pairs are counted up to each pixel's last contributor."""
     P = 4 * (11 + 3 * (sh_degree + 1) ** 2)
     work = {"preprocess": ("hbm", (P + 76) * n), "bin_sort": ("hbm", 152 * n + 56 * instances),
-            "render_fwd": ("alu", 25 * pairs), "loss": ("hbm", 48 * pixels),
+            "render_fwd": ("alu", 25 * pairs), "loss": ("alu", 1215 * pixels) if ssim else ("hbm", 36 * pixels),
             "render_bwd_blend": ("alu", 62 * pairs), "preprocess_bwd_adam": ("hbm", 6 * P * n)}
     out = {}
     for name, (bound, w) in work.items():
@@ -313,6 +371,7 @@ def run_ours(args, rank, world):
     L.load()
     scene, cams = workload(args)
     params = api.Gaussians.from_scene(scene, device=dev)
+    targets_d = render_targets(args.n, cams, dev)
     tuning, lb, table = {}, not args.sq, None
     if args.tuning:
         parts = args.tuning.split("/")
@@ -321,21 +380,16 @@ def run_ours(args, rank, world):
     elif not args.sq:  # launch shapes from the autotuner, on this workload's own views
         from paper_2601_19489_gb300.autotune import autotune
 
-        tgt = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1)).to(dev)
-               for v in range(2)]
-        best, table = autotune(params, [[cams[0]], [cams[1]]], tgt, lam=args.lam, device=dev)
+        best, table = autotune(params, [[cams[0]], [cams[1]]], targets_d[:2], lam=args.lam, device=dev)
         tuning = {k: best[k] for k in ("bucket", "bwd_warps", "bwd_chains")}
         lb = best["load_balanced"]
-        del tgt
     trainer = Trainer(params, args.width, args.height, lam=args.lam, load_balanced=lb, tuning=tuning, device=dev)
     trainer.autotune_table = table
     tu = trainer.slot_for([cams[0]]).plan.tuning
     trainer_tuning_key = (f"{'LB' if lb else 'Sq'}/b{tu['bucket']}/w{tu['bwd_warps']}/c{tu['bwd_chains']}")
     ntiles = ((args.width + 15) // 16) * ((args.height + 15) // 16)
     trainer.plan_tile_bits = max(1, int(np.ceil(np.log2(ntiles))))
-    targets_h = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1))
-                 .pin_memory() for v in range(len(cams))]
-    targets_d = [t.to(dev) for t in targets_h]
+    targets_h = [t.cpu().pin_memory() for t in targets_d]
     torch.cuda.synchronize()
     worst = trainer.ensure_capacity(cams)
     stream = torch.cuda.current_stream()
@@ -422,19 +476,29 @@ def run_ours(args, rank, world):
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     dominant = max(stage_ms, key=stage_ms.get)
-    roof = None
-    kname = {"render_bwd_blend": "k_render_bwd", "render_fwd": "k_render_fwd"}.get(dominant, dominant)
-    if dominant in FLOP_PER_PAIR:
-        ach = FLOP_PER_PAIR[dominant] * mean_pairs / (stage_ms[dominant] / 1e3) / 1e12
-        tr = NCU_TRAFFIC.get(kname)
-        src = {"k_render_bwd": "render_bwd.cu", "k_render_fwd": "render_fwd.cu"}[kname]
-        tun = trainer_tuning_key
-        traffic = (tr["bytes_per_launch"] if tr and tr.get("src_sha") == src_sha(src) and tr.get("tuning") == tun
-                   else None)
-        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": kname,
+    stages_roof = stage_roofline(stage_ms, args.n, 3, args.width * args.height, st2["n_instances"], mean_pairs,
+                                 hbm or FALLBACK_HBM_GBS, ssim=args.lam > 0)
+    bucket = trainer.slot_for([cams[0]]).plan.tuning["bucket"]
+    kname = {"render_bwd_blend": "k_render_bwd_pk" if bucket == 64 else "k_render_bwd",
+             "render_fwd": "k_render_fwd", "preprocess": "k_preprocess",
+             "preprocess_bwd_adam": "k_preprocess_bwd (Adam fused)", "loss": "k_ssim_fwd + k_ssim_bwd",
+             "bin_sort": "bin_sort (depth sort, key write, tile sort)"}.get(dominant, dominant)
+    sr = stages_roof[dominant]
+    tr = NCU_TRAFFIC.get(kname)
+    src = {"k_render_bwd": "render_bwd.cu", "k_render_bwd_pk": "render_bwd.cu",
+           "k_render_fwd": "render_fwd.cu"}.get(kname)
+    traffic = (tr["bytes_per_launch"] if tr and src and tr.get("src_sha") == src_sha(src)
+               and tr.get("tuning") == trainer_tuning_key else None)
+    if sr["bound"] == "alu":
+        roof = {"bound": "alu", "achieved": sr["achieved"], "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": sr["frac"], "traffic": traffic, "kernel": kname,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                "work": f"{FLOP_PER_PAIR[dominant]:.0f} FLOP x {mean_pairs:.4g} pixel-splat pairs per launch"}
+                "work": (f"{FLOP_PER_PAIR[dominant]:.0f} FLOP x {mean_pairs:.4g} pixel-splat pairs per launch"
+                         if dominant in FLOP_PER_PAIR else "algorithmic FLOP of the stage")}
+    else:
+        roof = {"bound": "hbm", "achieved": sr["achieved"], "peak": hbm or FALLBACK_HBM_GBS, "unit": "GB/s",
+                "frac": sr["frac"], "traffic": traffic, "kernel": kname,
+                "peak_source": "measured" if hbm else "fallback", "work": "algorithmic bytes of the stage"}
     value = job_rate(world, args.steps, elapsed)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -448,8 +512,7 @@ def run_ours(args, rank, world):
             "gpu_launches": kernels_per_step(trainer) * args.steps,
             "roofline": roof,
             "stages_ms": stage_ms,
-            "stages_roofline": stage_roofline(stage_ms, args.n, 3, args.width * args.height, st2["n_instances"],
-                                              mean_pairs, hbm or FALLBACK_HBM_GBS),
+            "stages_roofline": stages_roof,
             "work": {"instances_max": worst, "instances_last": st2["n_instances"],
                      "buckets_last": st2["n_buckets"], "pairs_per_view": mean_pairs},
             "peaks": {"hbm_gbs": hbm or FALLBACK_HBM_GBS, "hbm_source": "measured" if hbm else "fallback",
@@ -461,23 +524,30 @@ def run_ours(args, rank, world):
         line["batched_graph"] = run_batched(args, dev, args.n, args.batched_steps)
         torch.cuda.empty_cache()
     if world == 1 and not args.no_ng:
-        line["neural_gaussians"] = run_ng(args, dev, max(1, args.n // 10), max(20, args.steps // 3))
+        ng = run_ng(args, dev, max(1, args.n // 10), cams, targets_d, args.warmup, args.steps)
+        ng["vs_explicit_same_protocol"] = {
+            "explicit_steps_per_s": line["value"], "neural_steps_per_s": ng["steps_per_s"],
+            "explicit_instances_per_view": st2["n_instances"], "explicit_pairs_per_view": mean_pairs,
+            "note": "both from their own initial state, the same warm-up and timed steps on the same views and "
+                    "targets; per-step work differs (children whose decoded opacity is <= 0 reach no tile)"}
+        line["neural_gaussians"] = ng
         torch.cuda.empty_cache()
     if world == 1 and not args.no_pose:
-        line["pose_refinement"] = run_pose_overhead(args, dev, scene, cams, lb, tuning, max(60, args.steps // 3))
+        line["pose_refinement"] = run_pose_overhead(args, dev, scene, cams, targets_d, lb, tuning,
+                                                      max(60, args.steps // 3))
         torch.cuda.empty_cache()
     if world == 1 and not args.no_visible_adam:
         line["visible_adam"] = run_visible_adam(args, dev, scene, lb, tuning, max(60, args.steps // 3))
     if world == 1 and not args.no_cpu_baseline:
-        scene_h = scene
         cam = cams[0]
         n_threads = os.cpu_count() or 1
-        target = synth.target_uniform(1000, cam.width, cam.height)
-        est, detail = oracle_sample(scene_h, cam, target, window_px=128, pre_sample=1 << 18, n_threads=n_threads)
+        est, detail = oracle_sample(scene, synth.scene_clustered(args.n, seed=1, sh_degree=3), cam,
+                                    n_windows=BASELINE_WINDOWS, pre_sample=1 << 18, n_threads=n_threads)
         line["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": n_threads, "kind": "oracle",
-                                "sample": "preprocess fwd+bwd and Adam on 262144 random Gaussians (x N/262144), "
-                                          "blend fwd + loss + per-pixel bwd on a 128x128 centre window "
-                                          "(x H*W/16384); float64",
+                                "sample": f"view 0: preprocess fwd+bwd and Adam on 262144 random Gaussians "
+                                          f"(x N/262144), blend fwd + loss + per-pixel bwd on {BASELINE_WINDOWS} "
+                                          f"seeded 16x16 windows spread over the image "
+                                          f"(x H*W/({BASELINE_WINDOWS}*256)); float64",
                                 "detail": detail}
     print(json.dumps(line), flush=True)
 
@@ -499,8 +569,7 @@ def run_batched(args, dev, n: int, steps: int, warmup: int = 3) -> dict:
 
     scene = synth.scene_clustered(n, seed=0, sh_degree=3)
     batches = [synth.mixed_ring_cameras(8, seed=s) for s in (0, 1)]
-    targets = [torch.cat([torch.from_numpy(synth.target_uniform(2000 + 8 * b + i, c.width, c.height).reshape(-1))
-                          for i, c in enumerate(cams)]).to(dev) for b, cams in enumerate(batches)]
+    targets = [torch.cat(render_targets(n, cams, dev)) for cams in batches]
     params = api.Gaussians.from_scene(scene, device=dev)
     best, table = autotune(params, batches, targets, lam=args.lam, device=dev)
     tr = Trainer(params, lam=args.lam, load_balanced=best["load_balanced"],
@@ -546,31 +615,75 @@ def run_batched(args, dev, n: int, steps: int, warmup: int = 3) -> dict:
         seq.step(singles[i], single_t[i])
     t_seq = timed(lambda i: seq.step(singles[i % 16], single_t[i % 16]), 8 * steps)
     views = 8 * steps
+    small = graph_vs_eager_small(args, dev, steps)
     return {"gaussians": n, "views_per_step": 8,
             "views": "3 x 960x540, 3 x 1280x720, 2 x 1920x1080 ring views; two batches alternate",
             "graph_steps_per_s": steps / t_graph, "graph_views_per_s": views / t_graph,
             "eager_batched_views_per_s": views / t_eager, "sequential_views_per_s": views / t_seq,
             "graph_ms_per_step": 1e3 * t_graph / steps, "sequential_ms_per_8_views": 1e3 * t_seq / steps,
             "tuning": best, "autotune_ms_per_step": table, "clocks": clk.summary(),
-            "instances_last": st["n_instances"]}
+            "instances_last": st["n_instances"], "launch_bound_case": small}
 
 
-def run_ng(args, dev, n_anchors: int, steps: int, warmup: int = 5) -> dict:
-    """Neural-Gaussian step: n_anchors anchors subsampled from the clustered
-    scene's points, 10 children each, the same 16 ring views at full size,
-    one view per step (decode, splat, loss, backward, decoder backward, Adam
-    on features, anchor scales and MLP)."""
+def graph_vs_eager_small(args, dev, steps: int) -> dict:
+    """Where a CUDA graph pays: a launch-bound step (8 views of 320x180, 20k
+    Gaussians; about 40 launches of a few microseconds each), the same batch
+    eager and replayed from a graph."""
     import torch
 
     import synth
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import Trainer
+
+    n = 20000
+    cams = synth.ring_cameras(8, 320, 180)
+    tgt = torch.cat(render_targets(n, cams, dev))
+    tr = Trainer(api.Gaussians.from_scene(synth.scene_clustered(n, seed=0, sh_degree=3), device=dev),
+                 lam=args.lam, device=dev)
+    tr.ensure_capacity([cams])
+    for _ in range(3):
+        tr.step(cams, tgt)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    k = max(50, 4 * steps)
+    t_eager = timed(lambda: tr.step(cams, tgt), k)
+    g = tr.capture(cams, tgt)
+    for _ in range(3):
+        g.replay()
+    t_graph = timed(g.replay, k)
+    return {"gaussians": n, "views": "8 ring views 320x180", "eager_ms_per_step": 1e3 * t_eager / k,
+            "graph_ms_per_step": 1e3 * t_graph / k, "graph_speedup": t_eager / t_graph}
+
+
+def run_ng(args, dev, n_anchors: int, cams, targets, warmup: int, steps: int) -> dict:
+    """Neural-Gaussian step: n_anchors anchors subsampled from the clustered
+    scene's points, 10 children each, the same ring views and targets as the
+    headline, one view per step (decode, splat, loss, backward, decoder
+    backward, Adam on features, anchor scales and MLP).  Timed over the
+    headline's own protocol (the same warm-up and timed step counts from the
+    method's initial state, the same view order), with the work per step
+    (tile instances, pixel-splat pairs up to each pixel's last contributor)
+    reported beside the time, since a decoder in training changes how many of
+    its children reach the blend."""
+    import torch
+
+    import synth
+    from paper_2601_19489_gb300 import _lib as L
     from paper_2601_19489_gb300 import api
     from paper_2601_19489_gb300.trainer import NgTrainer
 
     pts = synth.scene_clustered(args.n, seed=0, sh_degree=0).means
     d = synth.ng_anchors(pts, n_anchors, seed=0)
-    cams = synth.ring_cameras(args.views, args.width, args.height)
-    targets = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1)).to(dev)
-               for v in range(len(cams))]
     tr = NgTrainer(api.NgParams.from_dict(d, device=dev), args.width, args.height, lam=args.lam, device=dev)
     tr.ensure_capacity(cams)
     for s in range(warmup):
@@ -578,8 +691,9 @@ def run_ng(args, dev, n_anchors: int, steps: int, warmup: int = 5) -> dict:
     n_st = len(tr.STAGES)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_st + 1)] for _ in range(steps)]
     torch.cuda.synchronize()
+    inst = []
     for s in range(steps):
-        v = s % len(cams)
+        v = (warmup + s) % len(cams)
         tr.step(cams[v], targets[v], events=evs[s])
     torch.cuda.synchronize()
     if tr.status() != 0 or tr.plan.status()["rc"] != 0:
@@ -587,12 +701,21 @@ def run_ng(args, dev, n_anchors: int, steps: int, warmup: int = 5) -> dict:
     total = sum(evs[s][0].elapsed_time(evs[s][n_st]) for s in range(steps)) / steps
     stage_ms = {name: float(np.mean([evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(steps)]))
                 for i, name in enumerate(tr.STAGES)}
+    # the work of the trained state, on the views of the timed steps
+    pairs = []
+    for s in range(min(steps, len(cams))):
+        v = (warmup + s) % len(cams)
+        tr.forward(cams[v])
+        inst.append(tr.plan.status()["n_instances"])
+        nc = tr.plan.view(L.GS_WS_N_CONTRIB, torch.int32)[: args.width * args.height]
+        pairs.append(float(nc.double().sum().item()))
     return {"anchors": n_anchors, "children": 10 * n_anchors, "steps_per_s": 1e3 / total, "ms_per_step": total,
-            "stages_ms": stage_ms, "loss_last": tr.loss.item(),
+            "warmup": warmup, "steps": steps, "stages_ms": stage_ms, "loss_last": tr.loss.item(),
+            "instances_per_view": float(np.mean(inst)), "pairs_per_view": float(np.mean(pairs)),
             "decoder": "x = [feature 32, view dir 3] -> 32 ReLU -> 140 = 10 children x 14; bf16 tcgen05 MMAs"}
 
 
-def run_pose_overhead(args, dev, scene, cams, lb, tuning, steps: int, warmup: int = 5) -> dict:
+def run_pose_overhead(args, dev, scene, cams, targets, lb, tuning, steps: int, warmup: int = 5) -> dict:
     """The headline step with and without the global pose refinement of
     Sec. 2.5 (gradient accumulated by every step's preprocess backward, the
     correction updated every 300 steps), same launch shapes, eager."""
@@ -602,8 +725,6 @@ def run_pose_overhead(args, dev, scene, cams, lb, tuning, steps: int, warmup: in
     from paper_2601_19489_gb300 import api
     from paper_2601_19489_gb300.trainer import Trainer
 
-    targets = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1)).to(dev)
-               for v in range(len(cams))]
     out = {}
     for name, pose in (("off", None), ("on", {"every": 300})):
         tr = Trainer(api.Gaussians.from_scene(scene, device=dev), args.width, args.height, lam=args.lam,
@@ -645,8 +766,7 @@ def run_visible_adam(args, dev, scene, lb, tuning, steps: int, warmup: int = 5, 
     from paper_2601_19489_gb300.trainer import Trainer
 
     cams = synth.ring_cameras(args.views, args.width, args.height, radius=radius)
-    targets = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1)).to(dev)
-               for v in range(len(cams))]
+    targets = render_targets(scene.n, cams, dev)
     out = {"ring_radius": radius}
     for name, vis in (("dense", False), ("visible_only", True)):
         tr = Trainer(api.Gaussians.from_scene(scene, device=dev), args.width, args.height, lam=args.lam,
@@ -748,11 +868,16 @@ def run_recon(args):
             if err is not None and not true_poses:
                 results[m]["pose_error"] = pose_error_report(gt.means, cams, given, results[m].get("pose_correction"))
             torch.cuda.empty_cache()
+    from paper_2601_19489_gb300.recon import time_to_psnr
+
     head = results.get("plain") or next(iter(results.values()))
     line = {"metric": f"held-out PSNR after {args.recon_budget:g} s of training", "value": head["psnr_final"],
             "unit": "dB", "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "method": head["method"],
             "vs_plain_db": {m: r["psnr_final"] - head["psnr_final"] for m, r in results.items()},
+            # wall time (training seconds) each method takes to reach the
+            # head method's final held-out PSNR (None: not within the budget)
+            "time_to_plain_psnr_s": {m: time_to_psnr(r["curve"], head["psnr_final"]) for m, r in results.items()},
             "config": {"workload": "300k clustered Gaussians SH3 ground truth, 200 orbit views 1600x1060 "
                                    "(20 held out), start from 50k noisy points",
                        "camera_pose_error": args.recon_pose_error or None},
@@ -802,8 +927,7 @@ def run_ablation(args, steps: int = 200, warmup: int = 10):
     dev = torch.device("cuda", 0)
     L.load()
     scene, cams = workload(args)
-    targets = [torch.from_numpy(synth.target_uniform(1000 + v, args.width, args.height).reshape(-1)).to(dev)
-               for v in range(len(cams))]
+    targets = render_targets(args.n, cams, dev)
     shape = {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1}
     configs = [("3DGS (per-pixel backward, 3-sigma box, Sq)", False, {"bwd_per_pixel": 1, "bbox_3sigma": 1}),
                ("w/ B", False, {**shape, "bbox_3sigma": 1}),

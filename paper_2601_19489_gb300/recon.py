@@ -9,9 +9,18 @@ Ways to spend the budget, all on one schedule:
                  evaluation segments (K = 10 random training views; its time
                  counts as training time);
   batched_graph  8 views per step through the batched plan, launch shapes from
-                 the autotuner, every step replayed from a CUDA graph;
+                 the autotuner, every step replayed from a CUDA graph; every
+                 learning rate scaled by batch_lr_scale (default sqrt(8)):
+                 a batch of 8 takes 8x fewer Adam steps, each of which moves
+                 a parameter by about its rate whatever the gradient's scale,
+                 while the batch's averaged gradient is less noisy, so the
+                 rate grows with the square root of the batch (the usual
+                 rule for Adam); the decay schedule is unchanged;
   ng             one view per step of the neural-Gaussian model (Sec. 2.3):
                  anchors at the starting points, 10 decoded children each;
+  ng_frozen      the same anchors and children with the decoder's MLP kept at
+                 its initialisation (features and anchor scales still
+                 train): what the trained network adds;
   pose           plain, plus the global pose refinement of Sec. 2.5 (one
                  camera-side correction for all views, updated every 300
                  steps, applied to the held-out views too).
@@ -75,18 +84,25 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
                 budget_s: float = 60.0, eval_every_s: float = 5.0, lam: float = 0.2, disp_weight: float = 0.1,
                 extent: float = 4.4, batch: int = 8, seed: int = 0, densify_rules: dict | None = None,
                 densify_tau: float = 0.3, densify_k: int = 10, max_gaussians: int | None = None,
-                pose: dict | None = None, device="cuda") -> dict:
+                pose: dict | None = None, batch_lr_scale: float | None = None, ng_lrs: dict | None = None,
+                device="cuda") -> dict:
     """Run one method for budget_s seconds of training; returns its held-out
     PSNR curve [(seconds trained, PSNR)], steps and views trained.
-    pose: settings of the `pose` method (default_pose(extent) by default)."""
+    pose: settings of the `pose` method (default_pose(extent) by default).
+    ng_lrs: decoder learning rates of the ng methods (default_ng_lrs()
+    overridden by name)."""
     W, H = train_cams[0].width, train_cams[0].height
     lrs = default_lrs(extent)
+    if method == "batched_graph":
+        scale = math.sqrt(batch) if batch_lr_scale is None else float(batch_lr_scale)
+        lrs = {k: v * scale for k, v in lrs.items()}
     lr0 = lrs["means"]
     rng = np.random.default_rng(seed)
     nv = len(train_cams)
-    if method == "ng":
+    if method in ("ng", "ng_frozen"):
         tr = NgTrainer(NgParams.from_dict(_ng_start(init, seed), device=device), W, H, lam=lam,
-                       disp_weight=disp_weight, lrs=lrs, device=device)
+                       disp_weight=disp_weight, lrs=lrs,
+                       ng_lrs={**(ng_lrs or {}), "mlp": 0.0} if method == "ng_frozen" else ng_lrs, device=device)
     else:
         params = Gaussians.from_scene(init, device=device)
         tuning, lb = None, True
@@ -115,7 +131,7 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
     for seg in range(n_seg):
         frac = seg / n_seg
         tr.disp_weight = disp_weight * (1.0 - frac)
-        if method != "ng":
+        if method not in ("ng", "ng_frozen"):
             tr.set_lr("means", lr0 * 0.01 ** frac)
         if method == "pose":
             tr.set_pose_lr(pose_cfg["lr_rot"] * 0.01 ** frac, pose_cfg["lr_trans"] * 0.01 ** frac)
@@ -157,7 +173,21 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
     if method == "pose":
         R, t = tr.pose.correction()
         extra["pose_correction"] = {"R": R.tolist(), "t": t.tolist(), "updates": int(tr.pose.buf[24].item())}
+    if method == "batched_graph":
+        extra["lr_scale"] = lrs["log_scales"] / default_lrs(extent)["log_scales"]
     return {**extra, "method": method, "curve": curve, "psnr_final": curve[-1][1], "psnr_start": curve[0][1],
             "steps": steps, "views": steps * per_step, "seconds": trained,
             "views_per_s": steps * per_step / trained, "gaussians_final": tr.params.n,
             "densify": densify_log}
+
+
+def time_to_psnr(curve, target: float) -> float | None:
+    """Training seconds at which a held-out PSNR curve [(seconds, PSNR)]
+    first reaches `target`, interpolated linearly between evaluations; None
+    if it never does."""
+    for (t0, p0), (t1, p1) in zip(curve[:-1], curve[1:]):
+        if p0 >= target:
+            return float(t0)
+        if p1 >= target:
+            return float(t0 + (t1 - t0) * (target - p0) / (p1 - p0))
+    return float(curve[0][0]) if curve and curve[0][1] >= target else None

@@ -48,3 +48,13 @@ def test_camera_pose_error_has_the_stated_size_and_acts_on_the_camera_side():
     R2, t2 = synth.camera_pose_error(0.03, 0.12, seed=7)
     np.testing.assert_array_equal(R, R2)
     np.testing.assert_array_equal(t, t2)
+
+
+def test_time_to_psnr_interpolates_the_curve():
+    from paper_2601_19489_gb300.recon import time_to_psnr
+
+    curve = [(0.0, 15.0), (5.0, 20.0), (10.0, 24.0), (15.0, 25.0)]
+    assert time_to_psnr(curve, 22.0) == 7.5
+    assert time_to_psnr(curve, 15.0) == 0.0
+    assert time_to_psnr(curve, 25.0) == 15.0
+    assert time_to_psnr(curve, 26.0) is None
