@@ -39,10 +39,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # Algorithmic floating-point work per evaluated pixel-splat pair, counted
 # from the kernels' arithmetic (FMA = 2): forward blend 25, backward 62.
 FLOP_PER_PAIR = {"render_fwd": 25.0, "render_bwd_blend": 62.0}
-# CPU oracle samples: 16 x 16 windows per reference-arm step and in the
-# cpu_baseline leg
-REF_WINDOWS = 12
-BASELINE_WINDOWS = 24
+# CPU oracle samples: WINDOW x WINDOW pixel windows, one per cell of an
+# 8 x 5 grid over the image in the cpu_baseline leg, one per step (cells in
+# rotation) in the reference arm; preprocess and Adam on a random subset
+WINDOW = 16
+REF_PRE_SAMPLE = 1 << 12
+BASELINE_PRE_SAMPLE = 1 << 18
 # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, 1 pass, on this workload at full size: 1M Gaussians,
 # one 1920x1080 view), valid only for the kernel source they were taken on
@@ -76,6 +78,8 @@ def parse_args():
                          "recon60: held-out PSNR after a timed reconstruction")
     ap.add_argument("--recon-budget", type=float, default=60.0, help="seconds of training per method")
     ap.add_argument("--recon-methods", type=str, default="plain,densify,batched_graph,ng,ng_frozen")
+    ap.add_argument("--recon-batch-lr-scale", type=float, default=None,
+                    help="learning-rate scale of the batched method (default sqrt(8))")
     ap.add_argument("--densify-tau-plus", type=float, default=5.0)
     ap.add_argument("--batched-n", type=str, default="",
                     help="comma-separated Gaussian counts for --workload batched (default: --n)")
@@ -126,7 +130,7 @@ def config_of(args):
                         f"16x16 tiles, loss {1 - args.lam:.1f} L1 + {args.lam:.1f} D-SSIM, one view per step",
             "gaussians": args.n, "views": args.views, "width": args.width, "height": args.height,
             "targets": "a second seeded clustered scene (seed 1, same size) rendered through the same cameras",
-            "tile": 16, "bucket": 32, "sh_degree": 3, "binning": "sequential" if args.sq else "load_balanced",
+            "tile": 16, "bucket": 64, "sh_degree": 3, "binning": "sequential" if args.sq else "load_balanced",
             "l2": "working set > L2 (params + Adam state ~1 GB, instances, checkpoints); no flush"}
 
 
@@ -190,14 +194,19 @@ def src_sha(name: str) -> str:
 
 # ------------------------------------------------------------ CPU oracle
 
-def sample_windows(W: int, H: int, k: int, seed: int, size: int = 16):
-    """k non-overlapping size x size windows at seeded positions, one per
-    distinct cell of a grid of 240 x 216-pixel cells (anywhere inside the
-    cell), so the sample covers the whole image rather than its centre."""
-    rng = np.random.default_rng(seed)
+def window_cells(W: int, H: int):
+    """The grid of cells the CPU samples stratify over: 240 x 216 pixels at
+    1920 x 1080 (8 x 5 = 40 cells)."""
     nx, ny = max(1, W // 240), max(1, H // 216)
-    cw, ch = W // nx, H // ny
-    cells = rng.choice(nx * ny, size=min(k, nx * ny), replace=False)
+    return nx, ny, W // nx, H // ny
+
+
+def sample_windows(W: int, H: int, cells, seed: int, size: int = WINDOW):
+    """One size x size window per listed cell of window_cells's grid, at a
+    seeded position anywhere inside the cell.  Listing every cell gives a
+    stratified sample of the whole image; the positions differ per seed."""
+    rng = np.random.default_rng(seed)
+    nx, ny, cw, ch = window_cells(W, H)
     out = []
     for c in cells:
         x0 = (c % nx) * cw + int(rng.integers(0, max(1, cw - size)))
@@ -206,15 +215,46 @@ def sample_windows(W: int, H: int, k: int, seed: int, size: int = 16):
     return out
 
 
-def oracle_sample(scene, target_scene, cam, n_windows: int, pre_sample: int, n_threads: int, seed: int = 0):
+def near_windows(rec: np.ndarray, wins) -> np.ndarray:
+    """The render records of the Gaussians whose level-set box (Eq. 1 level
+    set, widened by one pixel) reaches one of the windows (in input order).  The oracle builds its per-pixel candidate lists from
+    every Gaussian on each call, so without this each small window would also
+    pay a pass over all N Gaussians, a cost that does not scale with the
+    window's area; outside its box a Gaussian reaches no pixel, so the
+    windows' results are unchanged."""
+    a, b, c, t = rec[:, 2], rec[:, 3], rec[:, 4], rec[:, 10]
+    det = a * c - b * b
+    ok = (rec[:, 11] > 0) & (t > 0) & (det > 0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rx = np.sqrt(np.where(ok, t * c / det, 0.0)) + 1.0
+        ry = np.sqrt(np.where(ok, t * a / det, 0.0)) + 1.0
+    hit = np.zeros(rec.shape[0], bool)
+    for (x0, y0, x1, y1) in wins:
+        hit |= (rec[:, 0] + rx >= x0) & (rec[:, 0] - rx <= x1) & (rec[:, 1] + ry >= y0) & (rec[:, 1] - ry <= y1)
+    return rec[ok & hit]
+
+
+def oracle_records(scene, cam):
+    """The oracle's render records of every Gaussian for one view (setup of
+    the CPU samples, untimed)."""
+    import torch
+
+    from oracle import preprocess as opre
+
+    with torch.no_grad():
+        return opre.pack_for_render(opre.project(opre.params_from_scene(scene), cam, scene.sh_degree))
+
+
+def oracle_sample(scene, cam, rec_full, trec_full, wins, pre_sample: int, n_threads: int, seed: int = 0):
     """Time the float64 oracle on a bounded sample of one training step and
     extrapolate to the whole step.  Returns (seconds per full step, detail).
 
     preprocess fwd+bwd and Adam: a random subset of `pre_sample` Gaussians,
-    scaled by N / pre_sample; blend fwd + loss + per-pixel bwd: n_windows
-    16 x 16 windows spread over the image (sample_windows), scaled by
-    H * W / (n_windows * 256).  The target inside each window is the
-    oracle's own render of target_scene there (setup, untimed)."""
+    scaled by N / pre_sample; blend fwd + loss + per-pixel bwd: the windows
+    `wins`, scaled by H * W / (their pixels).  rec_full / trec_full are the
+    view's records of the trained and of the target scene (oracle_records);
+    the target inside each window is the oracle's own render of the target
+    scene there (setup, untimed)."""
     import torch
 
     from oracle import preprocess as opre
@@ -229,14 +269,8 @@ def oracle_sample(scene, target_scene, cam, n_windows: int, pre_sample: int, n_t
     sub = np.sort(rng.choice(N, size=min(pre_sample, N), replace=False))
     sub_scene = synth.Scene(*(a[sub] for a in scene.arrays()), sh_degree=scene.sh_degree)
     W, H = cam.width, cam.height
-    wins = sample_windows(W, H, n_windows, seed)
-    # full records for the window renders and the windows' targets (setup,
-    # untimed: the subset's time below stands for the preprocess of every
-    # Gaussian)
-    with torch.no_grad():
-        rec = opre.pack_for_render(opre.project(opre.params_from_scene(scene), cam, scene.sh_degree))
-        trec = opre.pack_for_render(opre.project(opre.params_from_scene(target_scene), cam,
-                                                 target_scene.sh_degree))
+    rec = near_windows(rec_full, wins)
+    trec = near_windows(trec_full, wins)
     tgts = [oren.render_fwd(trec, (0.0, 0.0, 0.0), w, amb=None, n_threads=n_threads)["rgb"] for w in wins]
     t0 = time.perf_counter()
     with torch.no_grad():
@@ -255,15 +289,20 @@ def oracle_sample(scene, target_scene, cam, n_windows: int, pre_sample: int, n_t
         oadam.adam_step(getattr(sub_scene, k), v, np.zeros_like(v), np.zeros_like(v), 1, 1e-3)
     t3 = time.perf_counter()
     scale_g = N / sub.size
-    scale_p = (W * H) / float(sum((w[2] - w[0]) * (w[3] - w[1]) for w in wins))
+    px = float(sum((w[2] - w[0]) * (w[3] - w[1]) for w in wins))
+    scale_p = (W * H) / px
     est = (t1 - t0) * scale_g + (t2 - t1) * scale_p + (t3 - t2) * scale_g
     detail = {"preprocess_s": (t1 - t0) * scale_g, "render_s": (t2 - t1) * scale_p,
-              "adam_s": (t3 - t2) * scale_g, "measured_s": t3 - t0, "pairs": pairs, "windows": len(wins)}
+              "adam_s": (t3 - t2) * scale_g, "measured_s": t3 - t0, "pairs": pairs,
+              "pairs_per_px": pairs / px, "windows": len(wins)}
     return est, detail
 
 
 def run_reference(args, rank, world):
-    """The reference arm: the float64 oracle as it stands, on the host cores."""
+    """The reference arm: the float64 oracle as it stands, on the host cores.
+    Step s renders one window in cell (7 s mod 40) of view s mod 16, so every
+    40 steps cover all cells of the image once; the per-view records are
+    computed once beforehand (untimed)."""
     if rank != 0:
         return
     scene, cams = workload(args)
@@ -271,11 +310,19 @@ def run_reference(args, rank, world):
 
     target_scene = synth.scene_clustered(args.n, seed=1, sh_degree=3)
     n_threads = os.cpu_count() or 1
+    nx, ny, _, _ = window_cells(args.width, args.height)
+    n_cells = nx * ny
+    stride = next(k for k in (7, 3, 1) if n_cells % k or k == 1)
+    records = {}
     times = []
     for s in range(args.warmup + args.steps):
-        cam = cams[s % len(cams)]
-        est, _ = oracle_sample(scene, target_scene, cam, n_windows=REF_WINDOWS, pre_sample=1 << 14,
-                               n_threads=n_threads, seed=s)
+        v = s % len(cams)
+        cam = cams[v]
+        if v not in records:
+            records[v] = (oracle_records(scene, cam), oracle_records(target_scene, cam))
+        wins = sample_windows(cam.width, cam.height, [(stride * s) % n_cells], seed=s)
+        est, _ = oracle_sample(scene, cam, *records[v], wins, pre_sample=REF_PRE_SAMPLE, n_threads=n_threads,
+                               seed=s)
         if s >= args.warmup:
             times.append(est)
     value = 1.0 / float(np.mean(times))
@@ -284,9 +331,11 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(args), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_threads, "kind": "oracle",
-                             "sample": f"per step (view s mod 16, seed s): preprocess fwd+bwd and Adam on 16384 "
-                                       f"random Gaussians (x N/16384), blend fwd+loss+bwd on {REF_WINDOWS} seeded "
-                                       f"16x16 windows spread over the image (x H*W/({REF_WINDOWS}*256))"},
+                             "sample": f"per step s (view s mod {len(cams)}): preprocess fwd+bwd and Adam on "
+                                       f"{REF_PRE_SAMPLE} random Gaussians (x N/{REF_PRE_SAMPLE}), blend "
+                                       f"fwd+loss+bwd on one seeded {WINDOW}x{WINDOW} window in cell "
+                                       f"({stride} s mod {n_cells}) of a {nx}x{ny} grid over the image "
+                                       f"(x H*W/{WINDOW * WINDOW}); the mean over steps covers every cell"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -524,7 +573,7 @@ def run_ours(args, rank, world):
         line["batched_graph"] = run_batched(args, dev, args.n, args.batched_steps)
         torch.cuda.empty_cache()
     if world == 1 and not args.no_ng:
-        ng = run_ng(args, dev, max(1, args.n // 10), cams, targets_d, args.warmup, args.steps)
+        ng = run_ng(args, dev, max(1, args.n // 10), cams, targets_d, args.warmup, args.steps, lb, tuning)
         ng["vs_explicit_same_protocol"] = {
             "explicit_steps_per_s": line["value"], "neural_steps_per_s": ng["steps_per_s"],
             "explicit_instances_per_view": st2["n_instances"], "explicit_pairs_per_view": mean_pairs,
@@ -541,13 +590,17 @@ def run_ours(args, rank, world):
     if world == 1 and not args.no_cpu_baseline:
         cam = cams[0]
         n_threads = os.cpu_count() or 1
-        est, detail = oracle_sample(scene, synth.scene_clustered(args.n, seed=1, sh_degree=3), cam,
-                                    n_windows=BASELINE_WINDOWS, pre_sample=1 << 18, n_threads=n_threads)
+        nx, ny, _, _ = window_cells(cam.width, cam.height)
+        wins = sample_windows(cam.width, cam.height, range(nx * ny), seed=0)
+        tscene = synth.scene_clustered(args.n, seed=1, sh_degree=3)
+        est, detail = oracle_sample(scene, cam, oracle_records(scene, cam), oracle_records(tscene, cam), wins,
+                                    pre_sample=BASELINE_PRE_SAMPLE, n_threads=n_threads)
         line["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": n_threads, "kind": "oracle",
-                                "sample": f"view 0: preprocess fwd+bwd and Adam on 262144 random Gaussians "
-                                          f"(x N/262144), blend fwd + loss + per-pixel bwd on {BASELINE_WINDOWS} "
-                                          f"seeded 16x16 windows spread over the image "
-                                          f"(x H*W/({BASELINE_WINDOWS}*256)); float64",
+                                "sample": f"view 0: preprocess fwd+bwd and Adam on {BASELINE_PRE_SAMPLE} random "
+                                          f"Gaussians (x N/{BASELINE_PRE_SAMPLE}), blend fwd + loss + per-pixel "
+                                          f"bwd on one seeded {WINDOW}x{WINDOW} window in each cell of a "
+                                          f"{nx}x{ny} grid over the image (x H*W/({nx * ny}*{WINDOW * WINDOW})); "
+                                          f"float64",
                                 "detail": detail}
     print(json.dumps(line), flush=True)
 
@@ -665,7 +718,8 @@ def graph_vs_eager_small(args, dev, steps: int) -> dict:
             "graph_ms_per_step": 1e3 * t_graph / k, "graph_speedup": t_eager / t_graph}
 
 
-def run_ng(args, dev, n_anchors: int, cams, targets, warmup: int, steps: int) -> dict:
+def run_ng(args, dev, n_anchors: int, cams, targets, warmup: int, steps: int, lb: bool = True,
+           tuning: dict | None = None) -> dict:
     """Neural-Gaussian step: n_anchors anchors subsampled from the clustered
     scene's points, 10 children each, the same ring views and targets as the
     headline, one view per step (decode, splat, loss, backward, decoder
@@ -674,7 +728,8 @@ def run_ng(args, dev, n_anchors: int, cams, targets, warmup: int, steps: int) ->
     method's initial state, the same view order), with the work per step
     (tile instances, pixel-splat pairs up to each pixel's last contributor)
     reported beside the time, since a decoder in training changes how many of
-    its children reach the blend."""
+    its children reach the blend.  Binning and launch shapes are the
+    headline's (lb, tuning)."""
     import torch
 
     import synth
@@ -684,7 +739,8 @@ def run_ng(args, dev, n_anchors: int, cams, targets, warmup: int, steps: int) ->
 
     pts = synth.scene_clustered(args.n, seed=0, sh_degree=0).means
     d = synth.ng_anchors(pts, n_anchors, seed=0)
-    tr = NgTrainer(api.NgParams.from_dict(d, device=dev), args.width, args.height, lam=args.lam, device=dev)
+    tr = NgTrainer(api.NgParams.from_dict(d, device=dev), args.width, args.height, lam=args.lam,
+                   load_balanced=lb, tuning=tuning, device=dev)
     tr.ensure_capacity(cams)
     for s in range(warmup):
         tr.step(cams[s % len(cams)], targets[s % len(cams)])
@@ -864,7 +920,7 @@ def run_recon(args):
                                      [views[i][1] for i in tr_ix], [cs[i] for i in ev], [views[i][0] for i in ev],
                                      budget_s=args.recon_budget, lam=args.lam,
                                      densify_rules={"tau_plus": args.densify_tau_plus}, max_gaussians=600000,
-                                     device=dev)
+                                     batch_lr_scale=args.recon_batch_lr_scale, device=dev)
             if err is not None and not true_poses:
                 results[m]["pose_error"] = pose_error_report(gt.means, cams, given, results[m].get("pose_correction"))
             torch.cuda.empty_cache()

@@ -204,16 +204,17 @@ GS_API int gs_preprocess(const gs_plan *plan, void *ws, const gs_params *params,
  * per-column ellipse test whatever the Gaussians' sizes; a segmented warp
  * scan of the columns' row counts places each column's tiles; 0: one thread
  * walks its own Gaussian's columns sequentially ("Sq") — then stably
- * radix-sort the
- * instances by tile so each tile's list is in (depth, id) order, and record
- * each tile's [start, end) range and 32-splat bucket count. */
+ * radix-sort the instances by tile so each tile's list is in (depth, id)
+ * order, and record each tile's [start, end) range. */
 GS_API int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, void *stream);
 
 /* --------------------------------------------------------- a5: forward
  * Sec. 2.1 (renderCUDA) and Sec. 2.2: per pixel, front-to-back blending of
  * its tile's depth-sorted splats with alpha = min(0.99, o e^power), skipping
- * alpha < 1/255 and stopping before T (1 - alpha) < 1e-4; every 32 splats the
- * per-pixel T, C and D are checkpointed in ws for the backward.
+ * alpha < 1/255 and stopping before T (1 - alpha) < 1e-4; every 32 (or 64,
+ * the plan's bucket) splats the per-pixel T, C and D are checkpointed in ws
+ * for the backward (each tile takes its buckets from a counter the call
+ * restarts, so the checkpoints belong to the last forward).
  * h_bg: 3 floats (host) background colour.  Outputs (device, may not alias):
  * d_out_rgb  colour C + T bg, planar per view;  d_out_disp  blended
  * disparity sum(alpha T / z);  d_out_T  final transmittance. */

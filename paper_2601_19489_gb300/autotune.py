@@ -27,8 +27,8 @@ import torch
 from .api import Gaussians
 from .trainer import Trainer
 
-BINNING = ({"load_balanced": True, "bucket": 32, "bwd_warps": 4, "bwd_chains": 0},
-           {"load_balanced": False, "bucket": 32, "bwd_warps": 4, "bwd_chains": 0})
+BINNING = ({"load_balanced": True, "bucket": 64, "bwd_warps": 1, "bwd_chains": 0},
+           {"load_balanced": False, "bucket": 64, "bwd_warps": 1, "bwd_chains": 0})
 # 32-splat buckets: one splat per lane, CTA width and pixel chains searched;
 # 64-splat buckets: two splats per lane in packed pairs (one chain), CTA
 # width searched

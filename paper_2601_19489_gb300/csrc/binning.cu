@@ -5,9 +5,9 @@
 //     largest key).  Items of different views interleave, which is harmless:
 //     an item only ever writes tiles of its own view.
 //  2. scan of the tile counts in depth order (fixed grid, no host sync): the
-//     block sums, one block scanning them (also publishing the instance count
-//     and the capacity overflow flag), and the key-write pass that rescans
-//     inside each block.
+//     block sums, scanned by the block that finishes last (which also
+//     publishes the instance count and the capacity overflow flag), and the
+//     key-write pass that rescans inside each block.
 //  3. key write, one (global tile id, item) instance per touched tile:
 //     load-balanced (Fig. 2): the SnugBox columns of a warp's 32 Gaussians
 //     form one flat list that the lanes walk one column each, so every lane
@@ -17,7 +17,8 @@
 //     Each round of Gaussians writes its (contiguous) run of instances.
 //  4. stable radix sort of the instances by tile id: every tile's list keeps
 //     the depth order of step 1, ties in depth by ascending Gaussian index.
-//  5. tile ranges by binary search in the sorted ids and the bucket offsets.
+//  5. tile ranges by binary search in the sorted ids.  (Each tile's first
+//     checkpoint bucket is taken by the forward, one atomic per tile.)
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -53,35 +54,42 @@ __device__ __forceinline__ void chunk_of(int64_t n, int64_t *beg, int64_t *end) 
     *end = *beg + chunk < n ? *beg + chunk : n;
 }
 
+// Block b sums the tile counts of its chunk of depth ranks into
+// block_sums[b]; the block that finishes last (a counter in the status
+// words, cleared by gs_bin_sort) then scans the block sums (64-bit) into
+// block_offs and publishes the instance count (saturated to 32 bits) and the
+// overflow flag.  Thread t of that block owns the kCountPer consecutive sums
+// from t * kCountPer.
+constexpr int kCountPer = (kBinBlocks + kScanThreads - 1) / kScanThreads;
+
 __global__ void __launch_bounds__(kScanThreads)
-k_count_reduce(const uint32_t *__restrict__ order, const uint32_t *__restrict__ touched, int64_t n,
-               uint32_t *__restrict__ block_sums) {
+k_count(const uint32_t *__restrict__ order, const uint32_t *__restrict__ touched, int64_t n,
+        uint32_t *__restrict__ block_sums, unsigned long long *__restrict__ block_offs, StatusDev *st,
+        int64_t capacity) {
     __shared__ uint32_t tmp[kScanThreads / 32];
+    __shared__ unsigned long long tmp64[kScanThreads / 32];
+    __shared__ bool s_last;
     int64_t beg, end;
     chunk_of(n, &beg, &end);
     uint32_t s = 0;
     for (int64_t r = beg + threadIdx.x; r < end; r += kScanThreads) s += touched[order[r]];
     uint32_t total;
     block_exclusive_scan(s, tmp, &total);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
-}
-
-// One block: exclusive scan (64-bit) of the block sums into block_offs;
-// publishes the instance count (saturated to 32 bits) and the overflow flag.
-// Thread t owns the kCountPer consecutive sums from t * kCountPer.
-constexpr int kCountPer = (kBinBlocks + 1023) / 1024;
-
-__global__ void __launch_bounds__(1024)
-k_count_top(const uint32_t *__restrict__ block_sums, unsigned long long *__restrict__ block_offs,
-            StatusDev *st, int64_t capacity) {
-    __shared__ unsigned long long tmp[32];
+    if (threadIdx.x == 0) {
+        block_sums[blockIdx.x] = total;
+        __threadfence();  // the sum is visible before this block counts as done
+        s_last = atomicAdd(&st->done_blocks, 1u) == (uint32_t)kBinBlocks - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long own[kCountPer];
     unsigned long long x = 0;
 #pragma unroll
     for (int k = 0; k < kCountPer; ++k) {
         const int b = tid * kCountPer + k;
-        own[k] = b < kBinBlocks ? block_sums[b] : 0ull;
+        own[k] = b < kBinBlocks ? __ldcg(block_sums + b) : 0ull;
         x += own[k];
     }
     unsigned long long inc = x;
@@ -90,12 +98,12 @@ k_count_top(const uint32_t *__restrict__ block_sums, unsigned long long *__restr
         unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
     }
-    if (lane == 31) tmp[warp] = inc;
+    if (lane == 31) tmp64[warp] = inc;
     __syncthreads();
     unsigned long long before = 0, all = 0;
-    for (int w = 0; w < 32; ++w) {
-        before += w < warp ? tmp[w] : 0ull;
-        all += tmp[w];
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        before += w < warp ? tmp64[w] : 0ull;
+        all += tmp64[w];
     }
     unsigned long long run = inc - x + before;
 #pragma unroll
@@ -107,6 +115,7 @@ k_count_top(const uint32_t *__restrict__ block_sums, unsigned long long *__restr
     if (tid == 0) {
         st->n_inst = all > 0xffffffffull ? 0xffffffffu : (uint32_t)all;
         st->overflow = all > (unsigned long long)capacity ? 1u : 0u;
+        st->done_blocks = 0;
     }
 }
 
@@ -335,46 +344,6 @@ k_tile_ranges(const uint32_t *__restrict__ keys, const StatusDev *st, int64_t ca
     ranges[t] = make_uint2(lower_bound_u32(keys, n, t), lower_bound_u32(keys, n, t + 1));
 }
 
-// One block: bucket_off[t] = sum over tiles before t of ceil(len / bucket).
-__global__ void __launch_bounds__(1024)
-k_bucket_offsets(const uint2 *__restrict__ ranges, int total_tiles, int bucket_shift,
-                 uint32_t *__restrict__ bucket_off, StatusDev *st) {
-    __shared__ uint32_t tmp[32];
-    __shared__ uint32_t carry;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry = 0;
-    __syncthreads();
-    for (int t0 = 0; t0 < total_tiles; t0 += 1024) {
-        const int t = t0 + tid;
-        uint32_t nb = 0;
-        if (t < total_tiles) {
-            const uint2 r = ranges[t];
-            nb = (r.y - r.x + (1u << bucket_shift) - 1) >> bucket_shift;
-        }
-        uint32_t inc = nb;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) tmp[warp] = inc;
-        __syncthreads();
-        uint32_t before = 0, all = 0;
-        for (int w = 0; w < 32; ++w) {
-            before += w < warp ? tmp[w] : 0u;
-            all += tmp[w];
-        }
-        if (t < total_tiles) bucket_off[t] = carry + inc - nb + before;
-        __syncthreads();
-        if (tid == 0) carry += all;
-        __syncthreads();
-    }
-    if (tid == 0) {
-        bucket_off[total_tiles] = carry;
-        st->n_buckets = carry;
-    }
-}
-
 }  // namespace gs
 
 using namespace gs;
@@ -385,7 +354,8 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
     const int64_t VN = plan->VN;
     StatusDev *st = ws_at<StatusDev>(ws, plan->o_status);
     uint32_t *scratch = ws_at<uint32_t>(ws, plan->o_sort_scratch);
-    int rc = check_cuda(cudaMemsetAsync(&st->error, 0, sizeof(int32_t), s));
+    // the error word and the finished-block counter of k_count (adjacent)
+    int rc = check_cuda(cudaMemsetAsync(&st->error, 0, 2 * sizeof(int32_t), s));
     if (rc) return rc;
 
     // 1. depth order of the items (keys were written by gs_preprocess)
@@ -400,8 +370,7 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
     uint32_t *block_sums = ws_at<uint32_t>(ws, plan->o_block_sums);
     unsigned long long *block_offs = reinterpret_cast<unsigned long long *>(block_sums + kBinBlocks + 32);
     const uint32_t *touched = ws_at<uint32_t>(ws, plan->o_touched);
-    k_count_reduce<<<kBinBlocks, kScanThreads, 0, s>>>(order, touched, VN, block_sums);
-    k_count_top<<<1, 1024, 0, s>>>(block_sums, block_offs, st, plan->inst_cap);
+    k_count<<<kBinBlocks, kScanThreads, 0, s>>>(order, touched, VN, block_sums, block_offs, st, plan->inst_cap);
 
     // 3. instance keys
     const ViewsDev vd = make_views(plan, nullptr);
@@ -430,7 +399,5 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
     uint2 *ranges = ws_at<uint2>(ws, plan->o_ranges);
     k_tile_ranges<<<(plan->total_tiles + 255) / 256, 256, 0, s>>>(
         ws_at<uint32_t>(ws, plan->o_ikey[ifinal]), st, plan->inst_cap, (uint32_t)plan->total_tiles, ranges);
-    k_bucket_offsets<<<1, 1024, 0, s>>>(ranges, plan->total_tiles, plan->bucket_shift,
-                                        ws_at<uint32_t>(ws, plan->o_bucket_off), st);
     return launch_error();
 }

@@ -83,6 +83,7 @@ k_densify_score(ViewsDev views, int64_t n, const uint2 *__restrict__ ranges,
             const float2 mm = tile_local_mean(r0, r1.w, r2.w, x0, y0);
             r0.x = mm.x;
             r0.y = mm.y;
+            r0.w = __fmul_rn(2.0f, r0.w);  // staged as 2B (exact)
             s_r0[tid] = r0;
             s_r1[tid] = r1;
             s_g[tid] = (uint32_t)(it % (uint32_t)n);
@@ -94,7 +95,7 @@ k_densify_score(ViewsDev views, int64_t n, const uint2 *__restrict__ ranges,
             bool hit = false;
             if (!done) {
                 PairEval e;
-                eval_pair(s_r0[j], s_r1[j], px, py, e);
+                eval_pair_b2(s_r0[j], s_r1[j], px, py, e);
                 if (!(e.power2 > 0.0f) && !(e.alpha < kAlphaMin)) {
                     const float test_T = T * (1.0f - e.alpha);
                     if (test_T < kTStop) {

@@ -59,7 +59,8 @@ struct StatusDev {
     uint32_t n_buckets;   // buckets of the last bin/sort
     uint32_t overflow;    // 1 if n_inst > capacity
     int32_t error;        // first device-side error code
-    uint32_t pad[60];
+    uint32_t done_blocks;  // k_count: blocks finished (cleared with error by gs_bin_sort)
+    uint32_t pad[59];
 };
 
 }  // namespace gs
@@ -304,15 +305,24 @@ struct PairEval {
     float dx, dy, power2, raw, alpha;
 };
 
-__device__ __forceinline__ void eval_pair(const float4 &r0, const float4 &r1, float px, float py,
-                                          PairEval &e) {
+// The same evaluation with r0.w already doubled (2B, exact): for records
+// staged once and evaluated against many pixels.
+__device__ __forceinline__ void eval_pair_b2(const float4 &r0, const float4 &r1, float px, float py,
+                                             PairEval &e) {
     e.dx = __fsub_rn(px, r0.x);
     e.dy = __fsub_rn(py, r0.y);
-    float u = __fmaf_rn(r0.z, e.dx, __fmul_rn(__fmul_rn(2.0f, r0.w), e.dy));  // A dx + 2B dy
-    float w = __fmul_rn(__fmul_rn(r1.x, e.dy), e.dy);                         // C dy^2
+    float u = __fmaf_rn(r0.z, e.dx, __fmul_rn(r0.w, e.dy));  // A dx + 2B dy
+    float w = __fmul_rn(__fmul_rn(r1.x, e.dy), e.dy);        // C dy^2
     e.power2 = -__fmaf_rn(u, e.dx, w);
     e.raw = fast_exp2(__fadd_rn(e.power2, r1.y));
     e.alpha = fminf(kAlphaMax, e.raw);
+}
+
+__device__ __forceinline__ void eval_pair(const float4 &r0, const float4 &r1, float px, float py,
+                                          PairEval &e) {
+    float4 q = r0;
+    q.w = __fmul_rn(2.0f, r0.w);
+    eval_pair_b2(q, r1, px, py, e);
 }
 
 }  // namespace gs

@@ -11,7 +11,8 @@
 // done skips the rest of the batch and the CTA leaves when all 256 are done.
 // Before list positions 0, B, 2B, ... (B = 32 or 64 splats per bucket) every
 // pixel still running stores its (T, C, D) in bucket-major, channel-planar
-// layout [bucket][5][256] so the backward's warps read them coalesced.
+// layout [bucket][5][256] so the backward's warps read them coalesced; a
+// tile's ceil(n / B) buckets are taken from a shared counter by its CTA.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -24,14 +25,15 @@ __device__ __forceinline__ int view_of_tile(const ViewsDev &vd, int t) {
 
 __global__ void __launch_bounds__(kTilePix)
 k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ inst_item,
-             const float4 *__restrict__ rec, const uint32_t *__restrict__ bucket_off, int bucket_shift, float bg_r,
+             const float4 *__restrict__ rec, int bucket_shift, float bg_r,
              float bg_g, float bg_b, float *__restrict__ out_rgb, float *__restrict__ out_disp,
              float *__restrict__ out_T, uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ tile_maxc,
-             float *__restrict__ ckpt, float *__restrict__ final_T) {
+             float *__restrict__ ckpt, float *__restrict__ final_T, uint32_t *__restrict__ bucket_off,
+             StatusDev *st) {
     __shared__ float4 s_r0[kTilePix];
     __shared__ float4 s_r1[kTilePix];
     __shared__ float4 s_r2[kTilePix];
-    __shared__ uint32_t s_maxc;
+    __shared__ uint32_t s_maxc, s_boff;
 
     const int t = blockIdx.x;
     const int v = view_of_tile(views, t);
@@ -46,12 +48,23 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
     const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
     const uint2 range = ranges[t];
     const int n = (int)(range.y - range.x);
-    float *ck = ckpt ? ckpt + (size_t)bucket_off[t] * (kCkptCh * kTilePix) + tid : nullptr;
     if (final_T && t == 0 && tid < 3) {  // the background, after the last pixel
         const ViewDev &lv = views.v[views.V - 1];
         final_T[lv.pix_off + (int64_t)lv.W * lv.H + tid] = tid == 0 ? bg_r : (tid == 1 ? bg_g : bg_b);
     }
-    if (tid == 0) s_maxc = 0;
+    if (tid == 0) {
+        s_maxc = 0;
+        // this tile's checkpoint buckets: ceil(n / bucket) consecutive ones,
+        // taken from the shared counter (the order of the tiles' ranges does
+        // not matter; the backward reads bucket_off)
+        if (ckpt) {
+            const uint32_t nb = ((uint32_t)n + (1u << bucket_shift) - 1u) >> bucket_shift;
+            s_boff = nb ? atomicAdd(&st->n_buckets, nb) : 0u;
+            bucket_off[t] = s_boff;
+        }
+    }
+    __syncthreads();
+    float *ck = ckpt ? ckpt + (size_t)s_boff * (kCkptCh * kTilePix) + tid : nullptr;
 
     float T = 1.0f, Cr = 0.f, Cg = 0.f, Cb = 0.f, D = 0.f;
     uint32_t last = 0;
@@ -65,6 +78,7 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
             const float2 m = tile_local_mean(r0, r1.w, r2.w, x0, y0);
             r0.x = m.x;
             r0.y = m.y;
+            r0.w = __fmul_rn(2.0f, r0.w);  // staged as 2B (exact)
             s_r0[tid] = r0;
             s_r1[tid] = r1;
             s_r2[tid] = r2;
@@ -86,7 +100,7 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
             for (int j = j0; j < j1 && !done; ++j) {
                 const float4 r0 = s_r0[j], r1 = s_r1[j];
                 PairEval e;
-                eval_pair(r0, r1, px, py, e);
+                eval_pair_b2(r0, r1, px, py, e);
                 if (e.power2 > 0.0f || e.alpha < kAlphaMin) continue;
                 const float test_T = T * (1.0f - e.alpha);
                 if (test_T < kTStop) {
@@ -135,12 +149,16 @@ extern "C" int gs_render_fwd(const gs_plan *plan, void *ws, const float *bg, flo
     if (!plan || !ws || !bg || !out_rgb || !out_disp || !out_T) return GS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const ViewsDev vd = make_views(plan, nullptr);
+    StatusDev *st = ws_at<StatusDev>(ws, plan->o_status);
+    // the bucket counter restarts with every forward
+    int rc = check_cuda(cudaMemsetAsync(&st->n_buckets, 0, sizeof(uint32_t), s));
+    if (rc) return rc;
     k_render_fwd<<<plan->total_tiles, kTilePix, 0, s>>>(
         vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
-        ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off), plan->bucket_shift, bg[0],
-        bg[1], bg[2],
-        out_rgb, out_disp, out_T, ws_at<uint32_t>(ws, plan->o_ncontrib),
-        ws_at<uint32_t>(ws, plan->o_tile_maxc), plan->bwd_per_pixel ? nullptr : ws_at<float>(ws, plan->o_ckpt),
-        plan->bwd_per_pixel ? ws_at<float>(ws, plan->o_final) : nullptr);
+        ws_at<float4>(ws, plan->o_rec), plan->bucket_shift, bg[0], bg[1], bg[2], out_rgb, out_disp, out_T,
+        ws_at<uint32_t>(ws, plan->o_ncontrib), ws_at<uint32_t>(ws, plan->o_tile_maxc),
+        plan->bwd_per_pixel ? nullptr : ws_at<float>(ws, plan->o_ckpt),
+        plan->bwd_per_pixel ? ws_at<float>(ws, plan->o_final) : nullptr, ws_at<uint32_t>(ws, plan->o_bucket_off),
+        st);
     return launch_error();
 }
