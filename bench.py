@@ -342,14 +342,33 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------ GPU arm
 
-def stage_roofline(stage_ms: dict, n: int, sh_degree: int, pixels: int, instances: float, pairs: float,
+def bin_bytes(n: int, instances: float, entries: float = 0.0, chunks: float = 0.0, tiles: int = 0,
+              counting: bool = True) -> float:
+    """Algorithmic bytes of the binning stage.
+      both paths    depth sort 4 passes x 20 B per Gaussian (keys and
+                    values read, written; the upsweep's key read)
+      counting      per Gaussian: entry count and entry write read its
+                    order, count and rectangle twice (2 x 16 B); per
+                    (Gaussian, block) entry: 8 B written, one sort pass
+                    20 B, two column walks reading the entry and its
+                    record, level set and rectangle (2 x 40 B); per
+                    instance the 4 B id written once; per chunk its 64
+                    tile counts written, rescanned and read (3 x 256 B);
+                    per tile its range (8 B)
+      radix         counts 72 B per Gaussian; per instance the 8 B key
+                    write, two tile-sort passes 2 x 20 B and the range
+                    search 8 B"""
+    if counting:
+        return 80 * n + 32 * n + 108 * entries + 4 * instances + 768 * chunks + 8 * tiles
+    return 152 * n + 56 * instances
+
+
+def stage_roofline(stage_ms: dict, n: int, sh_degree: int, pixels: int, bin_b: float, pairs: float,
                    hbm_gbs: float, ssim: bool = True) -> dict:
     """Each stage's achieved rate against its bound, from the algorithmic
     work per unit (parameters of P = 4 (11 + 3 K) bytes per Gaussian):
       preprocess    P read + 76 B of records written per Gaussian      (HBM)
-      bin_sort      depth sort 4 x 20 B and counts 72 B per Gaussian;
-                    key write 8 B, tile sort 2 x 20 B and ranges 8 B
-                    per instance                                       (HBM)
+      bin_sort      bin_bytes                                          (HBM)
       render_fwd    25 FLOP per pixel-splat pair                       (FP32)
       loss          with SSIM: 1215 FLOP per pixel (per channel: x^2,
                     y^2, x y 3; five 11-tap separable window sums 220;
@@ -360,7 +379,7 @@ def stage_roofline(stage_ms: dict, n: int, sh_degree: int, pixels: int, instance
       fused bwd     2 P parameters + 4 P moments per Gaussian          (HBM)
     Pairs are counted up to each pixel's last contributor."""
     P = 4 * (11 + 3 * (sh_degree + 1) ** 2)
-    work = {"preprocess": ("hbm", (P + 76) * n), "bin_sort": ("hbm", 152 * n + 56 * instances),
+    work = {"preprocess": ("hbm", (P + 76) * n), "bin_sort": ("hbm", bin_b),
             "render_fwd": ("alu", 25 * pairs), "loss": ("alu", 1215 * pixels) if ssim else ("hbm", 36 * pixels),
             "render_bwd_blend": ("alu", 62 * pairs), "preprocess_bwd_adam": ("hbm", 6 * P * n)}
     out = {}
@@ -395,15 +414,26 @@ def job_rate(world: int, steps: int, seconds: float) -> float:
     return world * steps / seconds
 
 
-def kernels_per_step(trainer) -> int:
-    tile_passes = -(-trainer.plan_tile_bits // 8)
+def block_bits(sizes) -> int:
+    """Bits of the block ids of the counting binning (8 x 8-tile blocks)."""
+    blocks = sum(-(-(-(-w // 16)) // 8) * -(-(-(-h // 16)) // 8) for (w, h) in sizes)
+    return max(1, int(np.ceil(np.log2(blocks))) if blocks > 1 else 1)
+
+
+def kernels_per_step(trainer, sizes) -> int:
     loss_k = 3 if trainer.lam > 0 else 2
-    # preprocess 1; depth sort 4 passes x 3; count 2; keys 1; tile sort 3/pass;
-    # ranges 1; buckets 1; forward 1; loss; blend bwd 1; then either the
+    # preprocess 1; depth sort 4 passes x 3; then the binning: counting
+    # (entry count 1, entry write 1, entry sort 3/pass, block bounds 1, chunk
+    # scan 1, count / offsets / scatter 3) or radix (count 1, keys 1, tile
+    # sort 3/pass, ranges 1); forward 1; loss; blend bwd 1; then either the
     # fused preprocess backward + Adam (step-count tick + 1) or preprocess
     # bwd 1 + adam 2 (tick + update)
     tail = 2 if trainer.fused_adam else 3
-    return 1 + 12 + 2 + 1 + 3 * tile_passes + 2 + 1 + loss_k + 1 + tail
+    if trainer.load_balanced and not trainer.tuning.get("bin_radix", 0):
+        binning = 2 + 3 * -(-block_bits(sizes) // 8) + 2 + 3
+    else:
+        binning = 2 + 3 * -(-trainer.plan_tile_bits // 8) + 1
+    return 1 + 12 + binning + 1 + loss_k + 1 + tail
 
 
 def run_ours(args, rank, world):
@@ -493,6 +523,11 @@ def run_ours(args, rank, world):
         pairs.append(float(nc.double().sum().item()))
     mean_pairs = float(np.mean(pairs))
     st2 = trainer.plan.status()
+    words = trainer.plan.view(L.GS_WS_STATUS, torch.int32)
+    counting = trainer.load_balanced and not trainer.tuning.get("bin_radix", 0)
+    tiles = -(-args.width // 16) * -(-args.height // 16)
+    bin_b = bin_bytes(args.n, st2["n_instances"], float(words[5].item()), float(words[6].item()), tiles,
+                      counting=counting)
 
     # e2e: through the public API with host buffers, the target copied in and
     # the loss read back every step (the next step's target is copied on a
@@ -525,13 +560,14 @@ def run_ours(args, rank, world):
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     dominant = max(stage_ms, key=stage_ms.get)
-    stages_roof = stage_roofline(stage_ms, args.n, 3, args.width * args.height, st2["n_instances"], mean_pairs,
+    stages_roof = stage_roofline(stage_ms, args.n, 3, args.width * args.height, bin_b, mean_pairs,
                                  hbm or FALLBACK_HBM_GBS, ssim=args.lam > 0)
     bucket = trainer.slot_for([cams[0]]).plan.tuning["bucket"]
     kname = {"render_bwd_blend": "k_render_bwd_pk" if bucket == 64 else "k_render_bwd",
              "render_fwd": "k_render_fwd", "preprocess": "k_preprocess",
              "preprocess_bwd_adam": "k_preprocess_bwd (Adam fused)", "loss": "k_ssim_fwd + k_ssim_bwd",
-             "bin_sort": "bin_sort (depth sort, key write, tile sort)"}.get(dominant, dominant)
+             "bin_sort": ("bin_sort (depth sort, counting binning)" if counting else
+                          "bin_sort (depth sort, key write, tile sort)")}.get(dominant, dominant)
     sr = stages_roof[dominant]
     tr = NCU_TRAFFIC.get(kname)
     src = {"k_render_bwd": "render_bwd.cu", "k_render_bwd_pk": "render_bwd.cu",
@@ -552,13 +588,15 @@ def run_ours(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {**config_of(args), "binning": "load_balanced" if trainer.load_balanced else "sequential",
+            "config": {**config_of(args), "binning": ("counting, load-balanced column walk" if counting else
+                                                      "radix, load-balanced key write" if trainer.load_balanced
+                                                      else "radix, sequential key write"),
                        "bucket": trainer.slot_for([cams[0]]).plan.tuning["bucket"],
                        "bwd_warps": trainer.slot_for([cams[0]]).plan.tuning["bwd_warps"],
                        "bwd_chains": trainer.slot_for([cams[0]]).plan.tuning["bwd_chains"],
                        "autotune_ms_per_step": trainer.autotune_table},
             "clocks": clocks, "e2e": e2e,
-            "gpu_launches": kernels_per_step(trainer) * args.steps,
+            "gpu_launches": kernels_per_step(trainer, [(args.width, args.height)]) * args.steps,
             "roofline": roof,
             "stages_ms": stage_ms,
             "stages_roofline": stages_roof,

@@ -127,7 +127,8 @@ GS_API gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views, co
  *              while the pipeline fills and drains), or 0: two when the
  *              bucket has at least 128 live pixels, else one.  Ignored at 64.
  * A zero field takes the default (32, 4, 0).  gs_plan_create uses the
- * defaults.
+ * defaults (the Python layer's default plan takes 64, 1, 0: the
+ * autotuner's pick at 1M Gaussians and 1080p).
  * Returns NULL on the same conditions as gs_plan_create or an unsupported
  * choice. */
 typedef struct {
@@ -147,6 +148,11 @@ typedef struct {
      *                  backward of Sec. 2.2 ("B"); no checkpoints are written. */
     int32_t bbox_3sigma;
     int32_t bwd_per_pixel;
+    /* bin_radix  1: gs_bin_sort with load_balanced = 1 takes the key-write +
+     *            radix-sort path (the only path of load_balanced = 0) instead
+     *            of the counting binning; both give the same per-tile lists.
+     *            0 by default. */
+    int32_t bin_radix;
 } gs_tuning;
 GS_API gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n_views, const int32_t *h_widths,
                                      const int32_t *h_heights, int64_t inst_capacity, const gs_tuning *tuning);
@@ -166,7 +172,8 @@ enum {
     GS_WS_TILES_TOUCHED,  /* uint32 per (view, Gaussian) */
     GS_WS_RECTS,          /* uint16 x 4 per (view, Gaussian): candidate tile box */
     GS_WS_DEPTH_ORDER,    /* uint32 per rank: item id v*n + g in ascending depth */
-    GS_WS_INST_TILE,      /* uint32 per instance, sorted global tile id */
+    GS_WS_INST_TILE,      /* uint32 per instance, sorted global tile id (radix
+                             binning path only; not written by the counting path) */
     GS_WS_INST_GID,       /* uint32 per instance, item id v*n + g */
     GS_WS_TILE_RANGES,    /* uint32 x 2 per global tile: [start, end) */
     GS_WS_N_CONTRIB,      /* uint32 per pixel: list position of last blended splat + 1 */
@@ -197,15 +204,26 @@ GS_API int gs_preprocess(const gs_plan *plan, void *ws, const gs_params *params,
 
 /* ---------------------------------------------- a2-a4: bin, sort, ranges
  * Sec. 2.1: order the visible Gaussians of every view by depth (on-device
- * radix sort), scan their tile counts, write one (tile, Gaussian) instance
- * per touched tile — load_balanced = 1 (the load-balanced write of Fig. 2):
- * a warp takes 32 Gaussians, lays their SnugBox tile columns out as one flat
- * list and gives each lane one column at a time, so every lane runs a
- * per-column ellipse test whatever the Gaussians' sizes; a segmented warp
- * scan of the columns' row counts places each column's tiles; 0: one thread
- * walks its own Gaussian's columns sequentially ("Sq") — then stably
- * radix-sort the instances by tile so each tile's list is in (depth, id)
- * order, and record each tile's [start, end) range. */
+ * radix sort), then build every tile's list of the Gaussians that touch it
+ * (the SnugBox tile columns with the exact per-column ellipse test), each
+ * list in (depth, id) order, and record each tile's [start, end) range in
+ * the instance list.
+ * load_balanced = 1 (default path, "counting binning"): tiles are grouped
+ * in blocks of 8 x 8; one (block, Gaussian) entry per block the Gaussian's
+ * SnugBox meets is written in depth order and stably sorted by block
+ * (a radix sort over these few entries); each block's entries are cut into
+ * chunks of 128, and a warp per chunk lays the chunk's in-block tile
+ * columns out as one flat list, one column per lane (the load-balanced
+ * column walk of Fig. 2), counts the chunk's instances per tile, and after
+ * a scan of the counts (tiles of a block, chunks of a tile, blocks) walks
+ * the columns again and writes each Gaussian id straight to its final
+ * position, the rank among the warp's lanes that share a tile taken by
+ * ballots.  Tile lists lie block by block in the instance list.
+ * load_balanced = 0 ("Sq", and load_balanced = 1 with the plan's bin_radix):
+ * one (tile, Gaussian) key per touched tile is written in depth order — by
+ * one thread walking its Gaussian's columns (Sq), or by the load-balanced
+ * column walk — and the keys are stably radix-sorted by tile; tile lists lie
+ * in tile order.  Every path gives the same list for every tile. */
 GS_API int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, void *stream);
 
 /* --------------------------------------------------------- a5: forward

@@ -400,6 +400,52 @@ static void orc_bound(const double *proj, const int64_t *ids, const orc_scratch 
     for (int c = 0; c < 5; ++c) bound[c] = b[c];
 }
 
+/* Magnitudes of one pixel's gradient terms, ADDED into mag at each blended
+ * splat's candidate position: every term of orc_pixel_backward with each
+ * factor replaced by its absolute value and the colour behind a splat by
+ * the pixel's whole absolute composited colour (a float32 backward that
+ * recovers what lies behind a splat from the pixel's totals carries an
+ * absolute error of the order of those totals).  A float32 evaluation of
+ * the terms, summed in any order, is within a small multiple of the unit
+ * roundoff times these magnitudes of the exact sums. */
+static void orc_pixel_magnitude(const double *proj, const int64_t *ids, const orc_scratch *s,
+                                const orc_result *r, const double *bg, const double *gC, double gD,
+                                double *mag) {
+    double Cabs[3] = {r->T * fabs(bg[0]), r->T * fabs(bg[1]), r->T * fabs(bg[2])};
+    double Dabs = 0.0;
+    for (int64_t j = 0; j < r->nblend; ++j) {
+        const double *g = proj + ids[s->pos[j]] * ORC_STRIDE;
+        double w = s->alpha[j] * s->Tb[j];
+        Cabs[0] += fabs(g[ORC_R]) * w;
+        Cabs[1] += fabs(g[ORC_G]) * w;
+        Cabs[2] += fabs(g[ORC_BL]) * w;
+        Dabs += fabs(1.0 / g[ORC_Z]) * w;
+    }
+    for (int64_t j = 0; j < r->nblend; ++j) {
+        const double *g = proj + ids[s->pos[j]] * ORC_STRIDE;
+        const orc_pair *e = &s->pair[j];
+        double Tk = s->Tb[j], a = s->alpha[j];
+        double rgb[3] = {g[ORC_R], g[ORC_G], g[ORC_BL]};
+        double *out = mag + (size_t)s->pos[j] * ORC_G2D;
+        double m_alpha = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+            out[6 + ch] += a * Tk * fabs(gC[ch]);
+            m_alpha += fabs(gC[ch]) * (fabs(rgb[ch]) * Tk + Cabs[ch] / (1.0 - a));
+        }
+        out[9] += a * Tk * fabs(gD);
+        m_alpha += fabs(gD) * (fabs(1.0 / g[ORC_Z]) * Tk + Dabs / (1.0 - a));
+        if (s->clamped[j]) continue;
+        out[5] += m_alpha * e->G;
+        double m_power = m_alpha * e->raw;
+        double dx = fabs(e->dx), dy = fabs(e->dy);
+        out[0] += m_power * (fabs(g[ORC_A]) * dx + fabs(g[ORC_B]) * dy);
+        out[1] += m_power * (fabs(g[ORC_B]) * dx + fabs(g[ORC_C]) * dy);
+        out[2] += m_power * 0.5 * dx * dx;
+        out[3] += m_power * dx * dy;
+        out[4] += m_power * 0.5 * dy * dy;
+    }
+}
+
 /* Backward of one pixel for the blended splats in s: ADD the ORC_G2D
  * gradient values of each into s->contrib at its candidate position. */
 static void orc_pixel_backward(const double *proj, const int64_t *ids, const orc_scratch *s,
@@ -547,12 +593,14 @@ int64_t orc_render_fwd2(int64_t n, const double *proj, const double *bg,
  * every pixel.  With amb and slack, for every flagged pixel the largest
  * change of each Gaussian's ORC_G2D values over the pixel's alternatives is
  * ADDED to slack (N x ORC_G2D); a Gaussian that is a candidate of an
- * unresolved pixel gets slack = +inf.
+ * unresolved pixel gets slack = +inf.  With mag, the magnitudes of the
+ * canonical branch's terms (orc_pixel_magnitude) are ADDED to mag
+ * (N x ORC_G2D).
  */
 void orc_render_bwd2(int64_t n, const double *proj, const double *bg,
                      int x0, int y0, int x1, int y1,
                      const double *g_rgb, const double *g_disp, const orc_amb *amb,
-                     double *grad2d, double *slack, int n_threads) {
+                     double *grad2d, double *slack, double *mag, int n_threads) {
     orc_lists L;
     orc_build_lists(n, proj, x0, y0, x1, y1, &L);
     int w = x1 - x0, h = y1 - y0;
@@ -574,6 +622,7 @@ void orc_render_bwd2(int64_t n, const double *proj, const double *bg,
     size_t per = (size_t)(n_local > 0 ? n_local : 1) * ORC_G2D;
     double *acc = (double *)calloc((size_t)nt * per, sizeof(double));
     double *sacc = (amb && slack) ? (double *)calloc((size_t)nt * per, sizeof(double)) : NULL;
+    double *macc = mag ? (double *)calloc((size_t)nt * per, sizeof(double)) : NULL;
 #ifdef _OPENMP
 #pragma omp parallel
 #endif
@@ -584,6 +633,7 @@ void orc_render_bwd2(int64_t n, const double *proj, const double *bg,
 #endif
         double *my = acc + (size_t)tid * per;
         double *mys = sacc ? sacc + (size_t)tid * per : NULL;
+        double *mym = macc ? macc + (size_t)tid * per : NULL;
         orc_scratch s = {0};
         orc_scratch s2 = {0};
         double *canon = NULL;
@@ -610,6 +660,14 @@ void orc_render_bwd2(int64_t n, const double *proj, const double *bg,
             for (int64_t k = 0; k < ncand; ++k) {
                 double *out = my + (size_t)local[ids[k]] * ORC_G2D;
                 for (int c = 0; c < ORC_G2D; ++c) out[c] += canon[k * ORC_G2D + c];
+            }
+            if (mym) {
+                memset(canon, 0, sizeof(double) * ORC_G2D * (size_t)(ncand > 0 ? ncand : 0));
+                orc_pixel_magnitude(proj, ids, &s, &r, bg, gC, gD, canon);
+                for (int64_t k = 0; k < ncand; ++k) {
+                    double *out = mym + (size_t)local[ids[k]] * ORC_G2D;
+                    for (int c = 0; c < ORC_G2D; ++c) out[c] += canon[k * ORC_G2D + c];
+                }
             }
             if (!mys || (r.nd == 0 && !(r.flags & ORC_F_UNRESOLVED))) continue;
             if (r.flags & ORC_F_UNRESOLVED) {
@@ -647,9 +705,11 @@ void orc_render_bwd2(int64_t n, const double *proj, const double *bg,
             for (int c = 0; c < ORC_G2D; ++c) {
                 grad2d[global_of[li] * ORC_G2D + c] += acc[((size_t)t * n_local + li) * ORC_G2D + c];
                 if (sacc) slack[global_of[li] * ORC_G2D + c] += sacc[((size_t)t * n_local + li) * ORC_G2D + c];
+                if (macc) mag[global_of[li] * ORC_G2D + c] += macc[((size_t)t * n_local + li) * ORC_G2D + c];
             }
     free(acc);
     free(sacc);
+    free(macc);
     free(global_of);
     free(local);
     orc_free_lists(&L);

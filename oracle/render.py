@@ -110,7 +110,7 @@ def _load():
                                             ctypes.c_int64, P, P, P, P, ctypes.c_int]
             lib.orc_render_bwd2.restype = None
             lib.orc_render_bwd2.argtypes = [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int,
-                                            ctypes.c_int, ctypes.c_int, P, P, P, P, P, ctypes.c_int]
+                                            ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, ctypes.c_int]
             lib.orc_contrib_score.restype = None
             lib.orc_contrib_score.argtypes = [ctypes.c_int64, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, P, P]
@@ -185,13 +185,18 @@ def flag_fractions(flags: np.ndarray) -> dict:
 
 
 def render_bwd(proj: np.ndarray, bg, window, g_rgb: np.ndarray, g_disp: np.ndarray,
-               n_threads: int = 0, amb=None, with_slack: bool = False):
+               n_threads: int = 0, amb=None, with_slack: bool = False, with_mag: bool = False):
     """Per-Gaussian 2D gradients (N, 10) of sum(g_rgb * rgb) + sum(g_disp * disp)
     over the window; see render.c for the column order.  Every pixel takes the
     canonical branch.  With amb and with_slack, also returns the slack
     (N, 10): for every Gaussian, the sum over the flagged pixels of the
     largest change of its values over the pixel's alternatives (+inf for a
-    candidate of an unresolved pixel); returns (grad, slack) then."""
+    candidate of an unresolved pixel); returns (grad, slack) then.  With
+    with_mag, also returns the magnitudes (N, 10) of the summed terms (each
+    factor of each pixel's term by its absolute value, the colour behind a
+    splat by the pixel's absolute composited colour): the scale of the
+    float32 error of an order-free sum of those terms; returns
+    (grad, slack, mag) then (slack None without with_slack)."""
     lib = _load()
     proj = np.ascontiguousarray(proj, dtype=np.float64)
     x0, y0, x1, y1 = (int(v) for v in window)
@@ -201,9 +206,12 @@ def render_bwd(proj: np.ndarray, bg, window, g_rgb: np.ndarray, g_disp: np.ndarr
     assert g_rgb.shape == (3, y1 - y0, x1 - x0) and g_disp.shape == (y1 - y0, x1 - x0)
     out = np.zeros((proj.shape[0], G2D))
     slack = np.zeros((proj.shape[0], G2D)) if with_slack else None
+    mag = np.zeros((proj.shape[0], G2D)) if with_mag else None
     a = _amb(amb) if with_slack else None
     lib.orc_render_bwd2(proj.shape[0], _ptr(proj), _ptr(bg), x0, y0, x1, y1, _ptr(g_rgb),
-                        _ptr(g_disp), _ref(a), _ptr(out), _ptr(slack), int(n_threads))
+                        _ptr(g_disp), _ref(a), _ptr(out), _ptr(slack), _ptr(mag), int(n_threads))
+    if with_mag:
+        return out, slack, mag
     return (out, slack) if with_slack else out
 
 

@@ -19,6 +19,10 @@
 //     the depth order of step 1, ties in depth by ascending Gaussian index.
 //  5. tile ranges by binary search in the sorted ids.  (Each tile's first
 //     checkpoint bucket is taken by the forward, one atomic per tile.)
+// Steps 2-5 are the radix path (load_balanced = 0, or the plan's bin_radix);
+// the default path replaces them with the counting binning further below,
+// which writes every instance once, straight to its place in its tile's
+// list, with no key array and no sort of the instances.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -62,22 +66,49 @@ __device__ __forceinline__ void chunk_of(int64_t n, int64_t *beg, int64_t *end) 
 // from t * kCountPer.
 constexpr int kCountPer = (kBinBlocks + kScanThreads - 1) / kScanThreads;
 
+// The (Gaussian, block) entries of the counting binning: the 8 x 8-tile
+// blocks its tile rectangle meets (none for a culled Gaussian).
+__device__ __forceinline__ uint32_t coarse_blocks(const uint32_t *__restrict__ touched,
+                                                  const uint2 *__restrict__ rects, uint32_t item) {
+    if (!touched[item]) return 0u;
+    int tx0, ty0, tx1, ty1;
+    unpack_rect(rects[item], &tx0, &ty0, &tx1, &ty1);
+    return (uint32_t)((((tx1 - 1) / kBlk) - tx0 / kBlk + 1) * (((ty1 - 1) / kBlk) - ty0 / kBlk + 1));
+}
+
+// kCoarse = false: scans the tile instances (touched) and publishes n_inst
+// (and the overflow flag against capacity).  kCoarse = true: scans the
+// (Gaussian, block) entries into block_offs and publishes n_coarse; the
+// tile instances are only summed (their block sums in inst_sums) and
+// published as n_inst, so the instance count is exact even when the entries
+// overflow; the overflow flag covers both (capacity holds both).
+template <bool kCoarse>
 __global__ void __launch_bounds__(kScanThreads)
-k_count(const uint32_t *__restrict__ order, const uint32_t *__restrict__ touched, int64_t n,
-        uint32_t *__restrict__ block_sums, unsigned long long *__restrict__ block_offs, StatusDev *st,
-        int64_t capacity) {
+k_count(const uint32_t *__restrict__ order, const uint32_t *__restrict__ touched, const uint2 *__restrict__ rects,
+        int64_t n, uint32_t *__restrict__ block_sums, unsigned long long *__restrict__ block_offs, StatusDev *st,
+        int64_t capacity, uint32_t *__restrict__ inst_sums) {
     __shared__ uint32_t tmp[kScanThreads / 32];
     __shared__ unsigned long long tmp64[kScanThreads / 32];
     __shared__ bool s_last;
     int64_t beg, end;
     chunk_of(n, &beg, &end);
-    uint32_t s = 0;
-    for (int64_t r = beg + threadIdx.x; r < end; r += kScanThreads) s += touched[order[r]];
-    uint32_t total;
+    uint32_t s = 0, si = 0;
+    for (int64_t r = beg + threadIdx.x; r < end; r += kScanThreads) {
+        const uint32_t item = order[r];
+        if (kCoarse) {
+            s += coarse_blocks(touched, rects, item);
+            si += touched[item];
+        } else {
+            s += touched[item];
+        }
+    }
+    uint32_t total, total_i = 0;
     block_exclusive_scan(s, tmp, &total);
+    if (kCoarse) block_exclusive_scan(si, tmp, &total_i);
     if (threadIdx.x == 0) {
         block_sums[blockIdx.x] = total;
-        __threadfence();  // the sum is visible before this block counts as done
+        if (kCoarse) inst_sums[blockIdx.x] = total_i;
+        __threadfence();  // the sums are visible before this block counts as done
         s_last = atomicAdd(&st->done_blocks, 1u) == (uint32_t)kBinBlocks - 1;
     }
     __syncthreads();
@@ -112,9 +143,28 @@ k_count(const uint32_t *__restrict__ order, const uint32_t *__restrict__ touched
         if (b < kBinBlocks) block_offs[b] = run;
         run += own[k];
     }
+    unsigned long long all_i = all;
+    if (kCoarse) {
+        // the instance total: the block sums of touched, summed
+        unsigned long long xi = 0;
+#pragma unroll
+        for (int k = 0; k < kCountPer; ++k) {
+            const int b = tid * kCountPer + k;
+            xi += b < kBinBlocks ? __ldcg(inst_sums + b) : 0ull;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) xi += __shfl_xor_sync(0xffffffffu, xi, o);
+        __syncthreads();
+        if (lane == 0) tmp64[warp] = xi;
+        __syncthreads();
+        all_i = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) all_i += tmp64[w];
+    }
     if (tid == 0) {
-        st->n_inst = all > 0xffffffffull ? 0xffffffffu : (uint32_t)all;
-        st->overflow = all > (unsigned long long)capacity ? 1u : 0u;
+        const auto sat = [](unsigned long long v) { return v > 0xffffffffull ? 0xffffffffu : (uint32_t)v; };
+        if (kCoarse) st->n_coarse = sat(all);
+        st->n_inst = sat(all_i);
+        st->overflow = (all > (unsigned long long)capacity || all_i > (unsigned long long)capacity) ? 1u : 0u;
         st->done_blocks = 0;
     }
 }
@@ -344,6 +394,449 @@ k_tile_ranges(const uint32_t *__restrict__ keys, const StatusDev *st, int64_t ca
     ranges[t] = make_uint2(lower_bound_u32(keys, n, t), lower_bound_u32(keys, n, t + 1));
 }
 
+// ============================================================================
+// Counting binning (the default path of gs_bin_sort).
+//
+// The tiles are grouped in blocks of kBlk x kBlk.  After the depth sort:
+//  1. k_count<true>: each visible Gaussian's number of blocks its tile
+//     rectangle meets, scanned in depth order (n_coarse);
+//  2. k_coarse_write: one (block id, item) entry per such block, in depth
+//     order;
+//  3. a stable radix sort of the entries by block id (block_bits bits): every
+//     block's entries stay in depth order;
+//  4. k_block_bounds: each block's [start, end) among the sorted entries;
+//  5. k_chunk_scan: each block's entries cut into chunks of kChunk, the
+//     chunks of all blocks numbered by a scan;
+//  6. k_fine<0>: a warp per chunk counts the chunk's instances per tile of
+//     the block;
+//  7. k_fine_offsets: a CTA per block turns the counts into each chunk's
+//     first position per tile (the block's tiles in row order, each tile's
+//     chunks in order); the CTA that finishes last scans the block totals
+//     into block bases and publishes the instance count;
+//  8. k_fine<1>: the warps walk the chunks again and write every item to its
+//     position; the tile ranges come from the block bases.
+// Within a chunk the instances of one tile keep the entries' order, so each
+// tile's list is in depth order as after the radix path.
+
+__device__ __forceinline__ int view_of_block(const ViewsDev &vd, int b) {
+    int v = 0;
+    while (v + 1 < vd.V && b >= vd.v[v + 1].block_off) ++v;
+    return v;
+}
+
+__global__ void __launch_bounds__(kWriteRound)
+k_coarse_write(ViewsDev views, int64_t n_per_view, const uint32_t *__restrict__ order,
+               const uint32_t *__restrict__ touched, const uint2 *__restrict__ rects,
+               const unsigned long long *__restrict__ block_offs, int64_t n, int64_t capacity,
+               uint32_t *__restrict__ ckey, uint32_t *__restrict__ cval) {
+    __shared__ uint32_t tmp[kWriteRound / 32];
+    int64_t beg, end;
+    chunk_of(n, &beg, &end);
+    unsigned long long base = block_offs[blockIdx.x];
+    for (int64_t r0 = beg; r0 < end; r0 += kWriteRound) {
+        const int64_t r = r0 + threadIdx.x;
+        uint32_t item = 0, cnt = 0;
+        if (r < end) {
+            item = order[r];
+            cnt = coarse_blocks(touched, rects, item);
+        }
+        uint32_t total;
+        const uint32_t off = block_exclusive_scan128(cnt, tmp, &total);
+        if (cnt) {
+            const ViewDev &cam = views.v[item / (uint32_t)n_per_view];
+            int tx0, ty0, tx1, ty1;
+            unpack_rect(rects[item], &tx0, &ty0, &tx1, &ty1);
+            uint32_t w = 0;
+            for (int by = ty0 / kBlk; by <= (ty1 - 1) / kBlk; ++by)
+                for (int bx = tx0 / kBlk; bx <= (tx1 - 1) / kBlk; ++bx, ++w) {
+                    const unsigned long long pos = base + off + w;
+                    if (pos < (unsigned long long)capacity) {
+                        ckey[pos] = (uint32_t)(cam.block_off + by * cam.blocks_x + bx);
+                        cval[pos] = item;
+                    }
+                }
+        }
+        base += total;
+    }
+}
+
+// [start, end) of every block that has entries (the caller zeroes brange).
+__global__ void __launch_bounds__(256)
+k_block_bounds(const uint32_t *__restrict__ ckey, const StatusDev *st, int64_t capacity, uint2 *__restrict__ brange) {
+    int64_t n = st->n_coarse;
+    if (n > capacity) n = capacity;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        const uint32_t k = ckey[i];
+        if (i == 0 || ckey[i - 1] != k) brange[k].x = (uint32_t)i;
+        if (i + 1 == n || ckey[i + 1] != k) brange[k].y = (uint32_t)(i + 1);
+    }
+}
+
+// One CTA: bchunk[b] = chunks of the blocks before b, bchunk[nblocks] = all
+// chunks (also published as n_chunks).  Thread t owns a contiguous range of
+// blocks.
+constexpr int kChunkScanThreads = 1024;
+
+__global__ void __launch_bounds__(kChunkScanThreads)
+k_chunk_scan(const uint2 *__restrict__ brange, int nblocks, uint32_t *__restrict__ bchunk, StatusDev *st) {
+    __shared__ uint32_t warp_tot[kChunkScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (nblocks + kChunkScanThreads - 1) / kChunkScanThreads;
+    const int b0 = min(tid * per, nblocks), b1 = min(b0 + per, nblocks);
+    uint32_t local = 0;
+    for (int b = b0; b < b1; ++b) {
+        const uint2 r = brange[b];
+        local += (r.y - r.x + kChunk - 1) / kChunk;
+    }
+    uint32_t inc = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t x = warp_tot[lane], xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        warp_tot[lane] = xi - x;
+    }
+    __syncthreads();
+    uint32_t run = inc - local + warp_tot[warp];
+    for (int b = b0; b < b1; ++b) {
+        bchunk[b] = run;
+        const uint2 r = brange[b];
+        run += (r.y - r.x + kChunk - 1) / kChunk;
+    }
+    if (tid == kChunkScanThreads - 1) {
+        bchunk[nblocks] = run;
+        st->n_chunks = run;
+    }
+}
+
+constexpr int kFineWarps = 4;
+constexpr int kFineCtas = 152 * 16;
+
+// kPass 0: per chunk, its instance count per tile of the block into
+// ccnt[chunk][64].  kPass 1: ccnt holds each chunk's first position per tile
+// (block-local) and bbase the blocks' bases; write every item to its
+// position and the tile ranges.  A warp takes a chunk at a time; its
+// entries go 32 at a time, their in-block tile columns laid out as one flat
+// list (one column per lane, as the load-balanced key write), and each
+// column's rows come from the same exact column test as the tile count.
+template <int kPass>
+__global__ void __launch_bounds__(kFineWarps * 32)
+k_fine(ViewsDev views, const uint32_t *__restrict__ cval, const uint2 *__restrict__ brange,
+       const uint32_t *__restrict__ bchunk, const float4 *__restrict__ rec, const float2 *__restrict__ bin,
+       const uint2 *__restrict__ rects, uint32_t *__restrict__ ccnt, const uint32_t *__restrict__ bbase,
+       const uint2 *__restrict__ btile, const StatusDev *st, int64_t capacity, uint32_t *__restrict__ inst_item,
+       uint2 *__restrict__ ranges, int box3) {
+    __shared__ uint32_t s_ctr[kFineWarps][kBlkTiles];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int gw = blockIdx.x * kFineWarps + warp, nw = gridDim.x * kFineWarps;
+    const int nblocks = views.total_blocks;
+    const uint32_t cap = (uint32_t)capacity;
+    if (kPass == 1) {
+        // the tile ranges, a block per warp (tiles past the view's edge have none)
+        for (int b = gw; b < nblocks; b += nw) {
+            const ViewDev &cam = views.v[view_of_block(views, b)];
+            const int lb = b - cam.block_off;
+            const int bx = lb % cam.blocks_x, by = lb / cam.blocks_x;
+            const uint32_t base = bbase[b];
+            for (int lt = lane; lt < kBlkTiles; lt += 32) {
+                const int tx = bx * kBlk + (lt % kBlk), ty = by * kBlk + lt / kBlk;
+                if (tx < cam.tiles_x && ty < cam.tiles_y) {
+                    const uint2 bt = btile[(size_t)b * kBlkTiles + lt];
+                    const uint32_t s = min(base + bt.x, cap), e = min(base + bt.x + bt.y, cap);
+                    ranges[cam.tile_off + ty * cam.tiles_x + tx] = make_uint2(s, e);
+                }
+            }
+        }
+    }
+    const uint32_t n_chunks = st->n_chunks;
+    for (uint32_t c = (uint32_t)gw; c < n_chunks; c += (uint32_t)nw) {
+        // the chunk's block: bchunk[b] <= c < bchunk[b + 1]
+        int lo = 0, hi = nblocks;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (bchunk[mid] <= c) lo = mid;
+            else hi = mid;
+        }
+        const int b = lo;
+        const uint2 br = brange[b];
+        const uint32_t e0 = br.x + (c - bchunk[b]) * (uint32_t)kChunk;
+        const uint32_t e1 = min(e0 + (uint32_t)kChunk, br.y);
+        const ViewDev &cam = views.v[view_of_block(views, b)];
+        const int lb = b - cam.block_off;
+        const int btx0 = (lb % cam.blocks_x) * kBlk, bty0 = (lb / cam.blocks_x) * kBlk;
+        const float fW = (float)cam.W, fH = (float)cam.H;
+        uint32_t *ctr = s_ctr[warp];
+        if (kPass == 0) {
+            ctr[lane] = 0u;
+            ctr[lane + 32] = 0u;
+        } else {
+            const uint32_t base = bbase[b];
+            ctr[lane] = min(base + ccnt[(size_t)c * kBlkTiles + lane], cap);
+            ctr[lane + 32] = min(base + ccnt[(size_t)c * kBlkTiles + lane + 32], cap);
+        }
+        __syncwarp();
+        for (uint32_t s0 = e0; s0 < e1; s0 += 32) {
+            const uint32_t e = s0 + (uint32_t)lane;
+            uint32_t item = 0;
+            BinGeom my{};
+            int cx0 = 0, ry0 = 0, ry1 = 0;
+            uint32_t ncols = 0;
+            if (e < e1) {
+                item = cval[e];
+                const float4 r0v = rec[3 * (size_t)item];
+                const float2 bv = bin[item];
+                if (!box3) bin_geom(r0v.x, r0v.y, r0v.z, r0v.w, rec[3 * (size_t)item + 1].x, bv.y, bv.x, my);
+                int tx0, ty0, tx1, ty1;
+                unpack_rect(rects[item], &tx0, &ty0, &tx1, &ty1);
+                cx0 = max(tx0, btx0);
+                const int cx1 = min(tx1, btx0 + kBlk);
+                ry0 = max(ty0, bty0);
+                ry1 = min(ty1, bty0 + kBlk);
+                ncols = (cx1 > cx0 && ry1 > ry0) ? (uint32_t)(cx1 - cx0) : 0u;
+            }
+            uint32_t colpref = ncols;  // inclusive, then exclusive scan of column counts
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, colpref, o);
+                if (lane >= o) colpref += y;
+            }
+            const uint32_t n_cols = __shfl_sync(0xffffffffu, colpref, 31);
+            colpref -= ncols;
+            for (uint32_t f0 = 0; f0 < n_cols; f0 += 32) {
+                const uint32_t f = f0 + (uint32_t)lane;
+                const bool has = f < n_cols;
+                // owner: the last lane j with colpref_j <= f
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t cp = __shfl_sync(0xffffffffu, colpref, j + step);
+                    if (cp <= f) j += step;
+                }
+                BinGeom bg;
+                bg.mx = __shfl_sync(0xffffffffu, my.mx, j);
+                bg.my = __shfl_sync(0xffffffffu, my.my, j);
+                bg.B = __shfl_sync(0xffffffffu, my.B, j);
+                bg.detc = __shfl_sync(0xffffffffu, my.detc, j);
+                bg.tC = __shfl_sync(0xffffffffu, my.tC, j);
+                bg.invC = __shfl_sync(0xffffffffu, my.invC, j);
+                bg.dx_top = __shfl_sync(0xffffffffu, my.dx_top, j);
+                bg.rx = __shfl_sync(0xffffffffu, my.rx, j);
+                bg.ry = __shfl_sync(0xffffffffu, my.ry, j);
+                const int jcx0 = __shfl_sync(0xffffffffu, cx0, j);
+                const int jry0 = __shfl_sync(0xffffffffu, ry0, j), jry1 = __shfl_sync(0xffffffffu, ry1, j);
+                const uint32_t cp_j = __shfl_sync(0xffffffffu, colpref, j);
+                const uint32_t it = __shfl_sync(0xffffffffu, item, j);
+                const int tx = jcx0 + (int)(f - cp_j);
+                int rlo = 0, rhi = -1;
+                if (has) {
+                    if (box3) {
+                        rlo = jry0;
+                        rhi = jry1 - 1;
+                    } else {
+                        float xa, xb;
+                        column_span(tx, fW, &xa, &xb);
+                        if (!column_rows(bg, xa, xb, fH, jry0, jry1, &rlo, &rhi)) {
+                            rlo = 0;
+                            rhi = -1;
+                        }
+                    }
+                }
+                const int cx = tx - btx0;  // in-block column (any value when the lane has no rows)
+                const uint32_t rows = rhi >= rlo ? (((2u << (rhi - rlo)) - 1u) << (rlo - bty0)) : 0u;
+                if (kPass == 0) {
+                    for (int y = rlo; y <= rhi; ++y) atomicAdd(&ctr[cx + kBlk * (y - bty0)], 1u);
+                } else {
+                    // the lanes holding the same tile, in lane (= entry) order
+                    const uint32_t q0 = __ballot_sync(0xffffffffu, cx & 1), q1 = __ballot_sync(0xffffffffu, cx & 2);
+                    const uint32_t q2 = __ballot_sync(0xffffffffu, cx & 4);
+                    const uint32_t cpeers = ((cx & 1) ? q0 : ~q0) & ((cx & 2) ? q1 : ~q1) & ((cx & 4) ? q2 : ~q2);
+                    uint32_t rowb[kBlk];
+#pragma unroll
+                    for (int y = 0; y < kBlk; ++y) rowb[y] = __ballot_sync(0xffffffffu, (rows >> y) & 1u);
+#pragma unroll
+                    for (int y = 0; y < kBlk; ++y) {
+                        if ((rows >> y) & 1u) {
+                            const uint32_t P = cpeers & rowb[y];
+                            const uint32_t pos = ctr[cx + kBlk * y] + __popc(P & lt_mask);
+                            if (pos < cap) inst_item[pos] = it;
+                        }
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int y = 0; y < kBlk; ++y) {
+                        if ((rows >> y) & 1u) {
+                            const uint32_t P = cpeers & rowb[y];
+                            if (lane == __ffs(P) - 1) ctr[cx + kBlk * y] += __popc(P);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (kPass == 0) {
+            ccnt[(size_t)c * kBlkTiles + lane] = ctr[lane];
+            ccnt[(size_t)c * kBlkTiles + lane + 32] = ctr[lane + 32];
+        }
+        __syncwarp();
+    }
+}
+
+// A CTA per block: group g (of kOffGroups) of threads owns a contiguous run
+// of the block's chunks, thread (g, t) tile t.  ccnt[chunk][t] becomes the
+// chunk's first block-local position for tile t; btile[b][t] = (tile start
+// in the block, tile total); bbase[b] is written by the CTA that finishes
+// last, which scans the block totals (64-bit) and publishes n_inst.
+constexpr int kOffThreads = 512;
+constexpr int kOffGroups = kOffThreads / kBlkTiles;
+
+__global__ void __launch_bounds__(kOffThreads)
+k_fine_offsets(const uint32_t *__restrict__ bchunk, uint32_t *__restrict__ ccnt, uint2 *__restrict__ btile,
+               uint32_t *__restrict__ btot, uint32_t *__restrict__ bbase, StatusDev *st, int nblocks,
+               int64_t capacity) {
+    __shared__ uint32_t s_part[kOffGroups][kBlkTiles];
+    __shared__ uint32_t s_tstart[kBlkTiles];
+    __shared__ uint32_t s_w0;
+    __shared__ bool s_last;
+    __shared__ unsigned long long s_scan[kOffThreads / 32];
+    const int tid = threadIdx.x, t = tid % kBlkTiles, g = tid / kBlkTiles;
+    const int b = blockIdx.x;
+    const uint32_t c0 = bchunk[b], nch = bchunk[b + 1] - c0;
+    const uint32_t per = (nch + kOffGroups - 1) / kOffGroups;
+    const uint32_t ga = c0 + min((uint32_t)g * per, nch), gb = c0 + min((uint32_t)(g + 1) * per, nch);
+    uint32_t sum = 0;
+    for (uint32_t c = ga; c < gb; ++c) sum += ccnt[(size_t)c * kBlkTiles + t];
+    s_part[g][t] = sum;
+    __syncthreads();
+    uint32_t tot = 0, inc = 0;
+    if (tid < kBlkTiles) {
+        // exclusive prefix over the groups, per tile
+        for (int gg = 0; gg < kOffGroups; ++gg) {
+            const uint32_t x = s_part[gg][t];
+            s_part[gg][t] = tot;
+            tot += x;
+        }
+        inc = tot;  // inclusive scan over the 64 tiles (two warps)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if ((tid & 31) >= o) inc += y;
+        }
+        if (tid == 31) s_w0 = inc;
+    }
+    __syncthreads();
+    if (tid < kBlkTiles) {
+        if (tid >= 32) inc += s_w0;
+        s_tstart[t] = inc - tot;
+        btile[(size_t)b * kBlkTiles + t] = make_uint2(inc - tot, tot);
+        if (tid == kBlkTiles - 1) btot[b] = inc;
+    }
+    __syncthreads();
+    uint32_t run = s_tstart[t] + s_part[g][t];
+    for (uint32_t c = ga; c < gb; ++c) {
+        const uint32_t x = ccnt[(size_t)c * kBlkTiles + t];
+        ccnt[(size_t)c * kBlkTiles + t] = run;
+        run += x;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();  // btot[b] is visible before this CTA counts as done
+        s_last = atomicAdd(&st->done_offsets, 1u) == (uint32_t)nblocks - 1u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the last CTA: exclusive scan of the block totals, thread tid owning a
+    // contiguous run of blocks
+    const int lane = tid & 31, warp = tid >> 5;
+    const int bper = (nblocks + kOffThreads - 1) / kOffThreads;
+    const int b0 = min(tid * bper, nblocks), b1 = min(b0 + bper, nblocks);
+    unsigned long long local = 0;
+    for (int k = b0; k < b1; ++k) local += __ldcg(btot + k);
+    unsigned long long x = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_scan[warp] = x;
+    __syncthreads();
+    unsigned long long before = 0, all = 0;
+    for (int w = 0; w < kOffThreads / 32; ++w) {
+        before += w < warp ? s_scan[w] : 0ull;
+        all += s_scan[w];
+    }
+    unsigned long long runb = x - local + before;
+    for (int k = b0; k < b1; ++k) {
+        // a base at or past the capacity parks the whole block there (every
+        // position is then rejected by the writes)
+        bbase[k] = runb < (unsigned long long)capacity ? (uint32_t)runb : (uint32_t)capacity;
+        runb += __ldcg(btot + k);
+    }
+    if (tid == 0) {
+        // without an overflow, the walks placed exactly the instances the
+        // tile counts of the preprocess promised
+        if (!st->overflow && all != (unsigned long long)st->n_inst) atomicCAS(&st->error, 0, GS_ERR_INTERNAL);
+        st->done_offsets = 0;
+    }
+}
+
+// Steps 2-8 of the counting binning (after the depth sort).
+static int bin_counting(const gs_plan *plan, void *ws, const uint32_t *order, uint32_t *block_sums,
+                        unsigned long long *block_offs, cudaStream_t s) {
+    StatusDev *st = ws_at<StatusDev>(ws, plan->o_status);
+    const ViewsDev vd = make_views(plan, nullptr);
+    const uint32_t *touched = ws_at<uint32_t>(ws, plan->o_touched);
+    const uint2 *rects = ws_at<uint2>(ws, plan->o_rect);
+    const int64_t ccap = plan->coarse_cap;
+    const int nblocks = plan->total_blocks;
+    // the entries ping-pong through the instance buffers the radix path
+    // uses and one more of the same size, never through the output buffer
+    uint32_t *ckA = ws_at<uint32_t>(ws, plan->o_ikey[0]), *cvA = ws_at<uint32_t>(ws, plan->o_ikey[1]);
+    uint32_t *ckB = ws_at<uint32_t>(ws, plan->o_ival[1 - plan->inst_final]), *cvB = ws_at<uint32_t>(ws, plan->o_cval);
+    uint32_t *out = ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]);
+    uint32_t *inst_sums = reinterpret_cast<uint32_t *>(block_offs + kBinBlocks);
+    k_count<true><<<kBinBlocks, kScanThreads, 0, s>>>(order, touched, rects, plan->VN, block_sums, block_offs, st,
+                                                      ccap, inst_sums);
+    k_coarse_write<<<kBinBlocks, kWriteRound, 0, s>>>(vd, plan->n, order, touched, rects, block_offs, plan->VN, ccap,
+                                                      ckA, cvA);
+    int rc = launch_error();
+    if (rc) return rc;
+    int cfinal = 0;
+    rc = sort_pairs(ckA, cvA, ckB, cvB, ccap, &st->n_coarse, 0, plan->block_bits,
+                    ws_at<uint32_t>(ws, plan->o_sort_scratch), s, &cfinal);
+    if (rc) return rc;
+    const uint32_t *ckey = cfinal ? ckB : ckA, *cval = cfinal ? cvB : cvA;
+    uint2 *brange = ws_at<uint2>(ws, plan->o_brange);
+    uint32_t *bchunk = ws_at<uint32_t>(ws, plan->o_bchunk);
+    rc = check_cuda(cudaMemsetAsync(brange, 0, (size_t)nblocks * sizeof(uint2), s));
+    if (rc) return rc;
+    k_block_bounds<<<kSortBlocks, 256, 0, s>>>(ckey, st, ccap, brange);
+    k_chunk_scan<<<1, kChunkScanThreads, 0, s>>>(brange, nblocks, bchunk, st);
+    uint32_t *ccnt = ws_at<uint32_t>(ws, plan->o_ccnt);
+    uint2 *btile = ws_at<uint2>(ws, plan->o_btile);
+    uint32_t *bbase = ws_at<uint32_t>(ws, plan->o_bbase);
+    uint32_t *btot = bbase + nblocks;  // block totals
+    const float4 *rec = ws_at<float4>(ws, plan->o_rec);
+    const float2 *bin = ws_at<float2>(ws, plan->o_bin);
+    uint2 *ranges = ws_at<uint2>(ws, plan->o_ranges);
+    k_fine<0><<<kFineCtas, kFineWarps * 32, 0, s>>>(vd, cval, brange, bchunk, rec, bin, rects, ccnt, bbase, btile,
+                                                    st, plan->inst_cap, out, ranges, plan->bbox_3sigma);
+    k_fine_offsets<<<nblocks, kOffThreads, 0, s>>>(bchunk, ccnt, btile, btot, bbase, st, nblocks, plan->inst_cap);
+    k_fine<1><<<kFineCtas, kFineWarps * 32, 0, s>>>(vd, cval, brange, bchunk, rec, bin, rects, ccnt, bbase, btile,
+                                                    st, plan->inst_cap, out, ranges, plan->bbox_3sigma);
+    return launch_error();
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -354,8 +847,9 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
     const int64_t VN = plan->VN;
     StatusDev *st = ws_at<StatusDev>(ws, plan->o_status);
     uint32_t *scratch = ws_at<uint32_t>(ws, plan->o_sort_scratch);
-    // the error word and the finished-block counter of k_count (adjacent)
-    int rc = check_cuda(cudaMemsetAsync(&st->error, 0, 2 * sizeof(int32_t), s));
+    // the error word, the finished-block counter of k_count, the entry and
+    // chunk counts and the finished-CTA counter of k_fine_offsets (adjacent)
+    int rc = check_cuda(cudaMemsetAsync(&st->error, 0, 5 * sizeof(int32_t), s));
     if (rc) return rc;
 
     // 1. depth order of the items (keys were written by gs_preprocess)
@@ -366,11 +860,14 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
     if (rc) return rc;
     const uint32_t *order = ws_at<uint32_t>(ws, plan->o_dval[dfinal]);
 
-    // 2. scan of tile counts in depth order
     uint32_t *block_sums = ws_at<uint32_t>(ws, plan->o_block_sums);
     unsigned long long *block_offs = reinterpret_cast<unsigned long long *>(block_sums + kBinBlocks + 32);
     const uint32_t *touched = ws_at<uint32_t>(ws, plan->o_touched);
-    k_count<<<kBinBlocks, kScanThreads, 0, s>>>(order, touched, VN, block_sums, block_offs, st, plan->inst_cap);
+    if (load_balanced && !plan->bin_radix) return bin_counting(plan, ws, order, block_sums, block_offs, s);
+
+    // 2. scan of tile counts in depth order
+    k_count<false><<<kBinBlocks, kScanThreads, 0, s>>>(order, touched, nullptr, VN, block_sums, block_offs, st,
+                                                       plan->inst_cap, nullptr);
 
     // 3. instance keys
     const ViewsDev vd = make_views(plan, nullptr);

@@ -33,6 +33,9 @@ constexpr float kLevelAbs = 1.0f / 4096.0f;
 constexpr int kSortBlocks = 608;           // 4 x 152 SMs: fixed grid of the sort/scan passes
 constexpr int kBinBlocks = 2432;           // 16 x 152 SMs: fixed grid of the tile-count scan and key write
 constexpr int kSortThreads = 256;
+constexpr int kBlk = 8;                    // counting binning: blocks of kBlk x kBlk tiles
+constexpr int kBlkTiles = kBlk * kBlk;
+constexpr int kChunk = 128;                // coarse entries per chunk (one warp)
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 
@@ -45,11 +48,13 @@ struct ViewDev {
     float limx, limy, near_z;
     int W, H, tiles_x, tiles_y;
     int tile_off, pix_off;
+    int blocks_x, block_off;  // 8 x 8-tile blocks of the counting binning
 };
 
 struct ViewsDev {
     int V;
     int total_tiles;
+    int total_blocks;
     ViewDev v[GS_MAX_VIEWS];
 };
 
@@ -60,7 +65,10 @@ struct StatusDev {
     uint32_t overflow;    // 1 if n_inst > capacity
     int32_t error;        // first device-side error code
     uint32_t done_blocks;  // k_count: blocks finished (cleared with error by gs_bin_sort)
-    uint32_t pad[59];
+    uint32_t n_coarse;     // (Gaussian, tile block) entries of the counting binning
+    uint32_t n_chunks;     // their chunks
+    uint32_t done_offsets;  // k_fine_offsets: CTAs finished (cleared by gs_bin_sort)
+    uint32_t pad[56];
 };
 
 }  // namespace gs
@@ -85,11 +93,16 @@ struct gs_plan {
     int32_t two_chain_min;         // live pixels from which a backward bucket walks two chains
     int32_t bbox_3sigma;           // ablation: classic 3-sigma tile box
     int32_t bwd_per_pixel;         // ablation: classic per-pixel backward
+    int32_t bin_radix;             // binning by key write + radix sort of the instances
+    int32_t blocks_x[GS_MAX_VIEWS], block_off[GS_MAX_VIEWS + 1];
+    int32_t total_blocks, block_bits;
+    int64_t coarse_cap, chunk_cap;
     double *pose;                  // attached pose-refinement state (gs_plan_set_pose) or nullptr
     // offsets
     size_t o_status, o_rec, o_touched, o_rect, o_dkey[2], o_dval[2];
     size_t o_ikey[2], o_ival[2], o_ranges, o_tile_maxc, o_bucket_off, o_ncontrib;
     size_t o_ckpt, o_grad2d, o_sort_scratch, o_block_sums, o_bin;
+    size_t o_brange, o_bchunk, o_btile, o_bbase, o_ccnt, o_cval;  // counting binning
     size_t o_final;  // per-pixel final T, then the background (per-pixel backward only)
     size_t o_posed;  // GS_MAX_VIEWS ViewDev: the cameras with the pose correction applied
     size_t sort_scratch_bytes;

@@ -17,6 +17,7 @@ ViewsDev make_views(const gs_plan *plan, const gs_camera *cams) {
     memset(&vd, 0, sizeof(vd));
     vd.V = plan->V;
     vd.total_tiles = plan->total_tiles;
+    vd.total_blocks = plan->total_blocks;
     for (int v = 0; v < plan->V; ++v) {
         ViewDev &d = vd.v[v];
         d.W = plan->W[v];
@@ -25,6 +26,8 @@ ViewsDev make_views(const gs_plan *plan, const gs_camera *cams) {
         d.tiles_y = plan->tiles_y[v];
         d.tile_off = plan->tile_off[v];
         d.pix_off = (int)plan->pix_off[v];
+        d.blocks_x = plan->blocks_x[v];
+        d.block_off = plan->block_off[v];
         if (!cams) continue;  // image geometry only
         const gs_camera &c = cams[v];
         d.fx = c.fx;
@@ -92,6 +95,13 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     }
     p->tile_off[n_views] = (int32_t)tiles;
     p->pix_off[n_views] = pix;
+    int64_t blocks = 0;
+    for (int v = 0; v < n_views; ++v) {
+        p->blocks_x[v] = (p->tiles_x[v] + kBlk - 1) / kBlk;
+        p->block_off[v] = (int32_t)blocks;
+        blocks += (int64_t)p->blocks_x[v] * ((p->tiles_y[v] + kBlk - 1) / kBlk);
+    }
+    p->block_off[n_views] = (int32_t)blocks;
     if (p->VN >= (1ll << 31) || tiles >= (1ll << 24)) {
         free(p);
         return nullptr;
@@ -101,6 +111,10 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     int bits = 1;
     while ((1ll << bits) < tiles) ++bits;
     p->tile_bits = bits;
+    p->total_blocks = (int32_t)blocks;
+    bits = 1;
+    while ((1ll << bits) < blocks) ++bits;
+    p->block_bits = bits;
     p->inst_cap = inst_capacity;
     p->bucket = bucket;
     p->bucket_shift = bucket == 64 ? 6 : 5;
@@ -108,6 +122,12 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     p->two_chain_min = chains == 2 ? 0 : chains == 1 ? (1 << 30) : kTwoChainAuto;
     p->bbox_3sigma = tuning && tuning->bbox_3sigma ? 1 : 0;
     p->bwd_per_pixel = tuning && tuning->bwd_per_pixel ? 1 : 0;
+    p->bin_radix = tuning && tuning->bin_radix ? 1 : 0;
+    // the counting binning's (Gaussian, block) entries: at most one per
+    // instance of capacity (an entry whose block holds no tile of its
+    // Gaussian is rare), in the radix path's instance buffers and o_cval
+    p->coarse_cap = inst_capacity;
+    p->chunk_cap = p->coarse_cap / kChunk + blocks + 1;
     p->bucket_cap = inst_capacity / bucket + tiles + 1;
     p->sort_scratch_bytes = sort_scratch_bytes();
 
@@ -140,8 +160,17 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     p->o_grad2d = take(VN * 3 * sizeof(float4));
     p->o_posed = take(GS_MAX_VIEWS * sizeof(ViewDev));
     p->o_sort_scratch = take(p->sort_scratch_bytes);
-    // uint32 block sums, then (8-byte aligned) uint64 block offsets
-    p->o_block_sums = take((kBinBlocks + 32) * sizeof(uint32_t) + kBinBlocks * sizeof(uint64_t));
+    // uint32 block sums, then (8-byte aligned) uint64 block offsets, then the
+    // uint32 instance block sums of the counting binning's count
+    p->o_block_sums = take((kBinBlocks + 32) * sizeof(uint32_t) + kBinBlocks * sizeof(uint64_t) +
+                           kBinBlocks * sizeof(uint32_t));
+    const size_t NB = (size_t)blocks;
+    p->o_brange = take(NB * sizeof(uint2));
+    p->o_bchunk = take((NB + 1) * sizeof(uint32_t));
+    p->o_btile = take(NB * kBlkTiles * sizeof(uint2));
+    p->o_bbase = take(2 * NB * sizeof(uint32_t));  // block bases, then block totals
+    p->o_ccnt = take((size_t)p->chunk_cap * kBlkTiles * sizeof(uint32_t));
+    p->o_cval = take(I * sizeof(uint32_t));
     p->bytes = o;
     // the radix sort ping-pongs: after P passes the data is in buffer P % 2
     p->depth_final = (32 / kRadixBits) % 2;

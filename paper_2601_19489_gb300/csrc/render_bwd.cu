@@ -73,7 +73,9 @@ __device__ __forceinline__ void stage_tile_pixels(const ViewDev &cam, int tx, in
 
 // The pixels still running at list position j0 (n_contrib > j0), compacted
 // into the warp's list in pixel order, each seeded with the checkpoint of
-// its bucket: (T, g . C + g_D D) in front of j0.  Returns their number.
+// its bucket: T in front of j0 and X = S(j0) = g . C + g_D D in front of j0
+// for the first bucket, X = S(j0) - S_fin for the others (see bwd_pair).
+// Returns their number.
 __device__ __forceinline__ int compact_live(const float4 *sg, const float2 *sfin, const float *__restrict__ ckb,
                                            uint32_t j0, float2 *ck, uint8_t *pix) {
     const int lane = threadIdx.x & 31;
@@ -88,7 +90,7 @@ __device__ __forceinline__ int compact_live(const float4 *sg, const float2 *sfin
             const float4 g = sg[p];
             const float sck = g.x * ckb[kTilePix + p] + g.y * ckb[2 * kTilePix + p] + g.z * ckb[3 * kTilePix + p] +
                               g.w * ckb[4 * kTilePix + p];
-            ck[m] = make_float2(ckb[p], sck);
+            ck[m] = make_float2(ckb[p], j0 == 0 ? sck : sck - sfin[p].x);
             pix[m] = (uint8_t)p;
         }
         m_total += __popc(bal);
@@ -104,11 +106,16 @@ struct SplatGrad {
     float sx, sy, xx, xy, yy, pw, r, g, b, iz;
 };
 
-// One (splat, pixel) pair of the pipeline: T, S enter as the state in front
-// of the splat and leave as the state behind it.
+// One (splat, pixel) pair of the pipeline: T, X enter as the state in front
+// of the splat and leave as the state behind it.  X runs as S + const: in
+// the first bucket X = S and the value behind the splat is S_fin - X; in
+// later buckets X = S - S_fin (seeded from the checkpoint) and the value
+// behind is -X.  Both are the same quantity; the second keeps the running
+// sum at the size of what is still behind, so its float32 rounding shrinks
+// as the pixel saturates instead of growing with everything in front.
 __device__ __forceinline__ void bwd_pair(const float4 *__restrict__ sg, const float2 *__restrict__ sfin,
                                          const uint8_t *__restrict__ spix, int m, uint32_t k, const float4 &r0,
-                                         const float4 &r1, const float4 &r2, float &T, float &Sv,
+                                         const float4 &r1, const float4 &r2, bool first, float &T, float &Sv,
                                          SplatGrad &acc) {
     const int p = spix[m];
     const float2 fin = sfin[p];
@@ -126,7 +133,7 @@ __device__ __forceinline__ void bwd_pair(const float4 *__restrict__ sg, const fl
     const float S_in = Sv;
     Sv = S_in + w * gdot;
     if (e.raw <= kAlphaMax) {  // the clamp passes no gradient
-        const float dL_da = T * gdot - __fdividef(fin.x - Sv, 1.0f - e.alpha);
+        const float dL_da = T * gdot - __fdividef((first ? fin.x : 0.0f) - Sv, 1.0f - e.alpha);
         const float dpw = dL_da * e.raw;  // dL/dpower (natural log units)
         const float sx = dpw * e.dx, sy = dpw * e.dy;
         acc.pw += dpw;
@@ -219,8 +226,8 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
                     TB = tB;
                     SB = sB;
                     if (valid && mA >= 0) {
-                        if (mA < h) bwd_pair(S.g, S.fin, spix, mA, k, r0, r1, r2, TA, SA, acc);
-                        if (mB < m_total) bwd_pair(S.g, S.fin, spix, mB, k, r0, r1, r2, TB, SB, acc);
+                        if (mA < h) bwd_pair(S.g, S.fin, spix, mA, k, r0, r1, r2, j0 == 0, TA, SA, acc);
+                        if (mB < m_total) bwd_pair(S.g, S.fin, spix, mB, k, r0, r1, r2, j0 == 0, TB, SB, acc);
                     }
                 }
             } else {
@@ -239,7 +246,7 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
                     }
                     TA = tA;
                     SA = sA;
-                    if (valid && mA >= 0 && mA < m_total) bwd_pair(S.g, S.fin, spix, mA, k, r0, r1, r2, TA, SA, acc);
+                    if (valid && mA >= 0 && mA < m_total) bwd_pair(S.g, S.fin, spix, mA, k, r0, r1, r2, j0 == 0, TA, SA, acc);
                 }
             }
             if (valid) {
@@ -287,7 +294,7 @@ __device__ __forceinline__ int compact_live_grouped(const float4 *sg, const floa
                 const float4 g = sg[p];
                 const float sck = g.x * ckb[kTilePix + p] + g.y * ckb[2 * kTilePix + p] +
                                   g.z * ckb[3 * kTilePix + p] + g.w * ckb[4 * kTilePix + p];
-                ck[m] = make_float2(ckb[p], sck);
+                ck[m] = make_float2(ckb[p], j0 == 0 ? sck : sck - sfin[p].x);
                 pix[m] = (uint8_t)p;
                 need = max(need, m + (int)min(31u, (nc - j0 - 1u) >> 1) + 1);
             }
@@ -394,6 +401,7 @@ k_render_bwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
                     const float2 fin = S.fin[p];
                     const float4 g = S.g[p];
                     const uint32_t nc = __float_as_uint(fin.y);
+                    const float fsel = j0 == 0 ? fin.x : 0.0f;  // X = S or S - S_fin (bwd_pair)
                     const float px = (float)(p & (kTile - 1)) + 0.5f, py = (float)(p >> 4) + 0.5f;
                     const f2x dx = sub2(pk2(px, px), MX), dy = sub2(pk2(py, py), MY);
                     // q = A dx^2 + 2B dx dy + C dy^2 (base 2), e = log2 o - q
@@ -413,13 +421,16 @@ k_render_bwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
                     const f2x gx = pk2(g.x, g.x), gy = pk2(g.y, g.y), gz = pk2(g.z, g.z), gw = pk2(g.w, g.w);
                     float gdA, gdB;
                     upk2(fma2(gx, CR, fma2(gy, CG, fma2(gz, CBL, mul2(gw, IZ)))), gdA, gdB);
-                    // the chain through the two splats
+                    // the chain through the two splats; T advances as
+                    // T (1 - alpha), the forward's own float32 operation, so
+                    // the backward walks the forward's transmittances
+                    const float omA = 1.0f - aA, omB = 1.0f - aB;
                     const float wA = aA * t_in;
                     const float SA = fmaf(wA, gdA, s_in);
-                    const float TA = t_in - wA;
+                    const float TA = t_in * omA;
                     const float wB = aB * TA;
                     const float SB = fmaf(wB, gdB, SA);
-                    T = TA - wB;
+                    T = TA * omB;
                     Sv = SB;
                     const f2x W = pk2(wA, wB);
                     acc_r = fma2(W, gx, acc_r);
@@ -428,15 +439,15 @@ k_render_bwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
                     acc_iz = fma2(W, gw, acc_iz);
                     // dL/dpower = dL/dalpha alpha_raw; zero where the clamp is
                     // active or the pair was not blended
-                    const float dA = fmaf(t_in, gdA, -(fin.x - SA) * fast_rcp(1.0f - aA));
-                    const float dB = fmaf(TA, gdB, -(fin.x - SB) * fast_rcp(1.0f - aB));
+                    const float dA = fmaf(t_in, gdA, (SA - fsel) * fast_rcp(omA));
+                    const float dB = fmaf(TA, gdB, (SB - fsel) * fast_rcp(omB));
                     const float pA = (okA && rawA <= kAlphaMax) ? dA * rawA : 0.0f;
                     const float pB = (okB && rawB <= kAlphaMax) ? dB * rawB : 0.0f;
                     const f2x dpw = pk2(pA, pB);
                     const f2x sx = mul2(dpw, dx), sy = mul2(dpw, dy);
                     acc_pw = add2(acc_pw, dpw);
-                    acc_sx = add2(acc_sx, sx);
-                    acc_sy = add2(acc_sy, sy);
+                    acc_sx = fma2(dpw, dx, acc_sx);  // the mean's sums without the rounding of sx, sy
+                    acc_sy = fma2(dpw, dy, acc_sy);
                     acc_xx = fma2(sx, dx, acc_xx);
                     acc_xy = fma2(sx, dy, acc_xy);
                     acc_yy = fma2(sy, dy, acc_yy);

@@ -123,25 +123,49 @@ def test_preprocess_matches_oracle(gs, which):
 
 # --------------------------------------------------------------- binning
 
-def test_binning_lists_match_oracle_and_lb_equals_sq(gs):
+def _tile_lists(plan):
+    """(n_instances, items, ranges) of the last binning, each tile's list
+    checked to be one piece of a partition of the instance list."""
     from paper_2601_19489_gb300 import _lib as L
 
+    n_inst = plan.status()["n_instances"]
+    item = to_np(plan.view(L.GS_WS_INST_GID, torch.int32))[:n_inst].astype(np.int64)
+    ranges = to_np(plan.view(L.GS_WS_TILE_RANGES, torch.int32)).reshape(-1, 2).astype(np.int64)
+    # the ranges partition [0, n_instances)
+    assert np.all(ranges[:, 1] >= ranges[:, 0])
+    r = ranges[np.argsort(ranges[:, 0], kind="stable")]
+    r = r[r[:, 1] > r[:, 0]]
+    if r.size:
+        assert r[0, 0] == 0 and r[-1, 1] == n_inst and np.all(r[1:, 0] == r[:-1, 1])
+    else:
+        assert n_inst == 0
+    return n_inst, item, ranges
+
+
+def _same_lists(pa, pb):
+    na, ia, ra = _tile_lists(pa)
+    nb, ib, rb = _tile_lists(pb)
+    assert na == nb
+    assert ra.shape == rb.shape
+    for t in range(ra.shape[0]):
+        np.testing.assert_array_equal(ia[ra[t, 0]:ra[t, 1]], ib[rb[t, 0]:rb[t, 1]], err_msg=f"tile {t}")
+    return na
+
+
+def test_binning_lists_match_oracle_and_lb_equals_sq(gs):
     scene = synth.scene_clustered(30000, seed=5, sh_degree=0)
     cam = synth.ring_cameras(8, 400, 248)[3]
     plan_lb, *_ = _run_forward(gs, scene, [cam], lb=True)
     plan_sq, *_ = _run_forward(gs, scene, [cam], lb=False)
-    n_inst = plan_lb.status()["n_instances"]
-    assert n_inst == plan_sq.status()["n_instances"] > 0
-    for which in (L.GS_WS_INST_GID, L.GS_WS_TILE_RANGES):
-        a = to_np(plan_lb.view(which, torch.int32))
-        b = to_np(plan_sq.view(which, torch.int32))
-        n = n_inst if which != L.GS_WS_TILE_RANGES else a.size
-        np.testing.assert_array_equal(a[:n], b[:n])
-    item = to_np(plan_lb.view(L.GS_WS_INST_GID, torch.int32))[:n_inst]
-    ranges = to_np(plan_lb.view(L.GS_WS_TILE_RANGES, torch.int32)).reshape(-1, 2)
-    # the ranges tile the instance list in tile order
-    assert ranges[0, 0] == 0 and ranges[-1, 1] == n_inst and np.all(ranges[1:, 0] == ranges[:-1, 1])
-    tile = np.repeat(np.arange(ranges.shape[0]), ranges[:, 1] - ranges[:, 0])
+    plan_lr, *_ = _run_forward(gs, scene, [cam], lb=True, tuning={"bin_radix": 1})
+    # the counting binning (default), the radix path with the load-balanced
+    # key write and with the sequential one give the same list for every tile
+    n_inst = _same_lists(plan_lb, plan_sq)
+    assert n_inst > 0 and _same_lists(plan_lb, plan_lr) == n_inst
+    _, item, ranges = _tile_lists(plan_lb)
+    tile = np.zeros(n_inst, np.int64)
+    for t in range(ranges.shape[0]):
+        tile[ranges[t, 0]:ranges[t, 1]] = t
     _, orec = _oracle_records(scene, cam)
     tiles = obin.tile_min_q(orec, cam.width, cam.height)
     # The kernel bins against the level set widened to t (1 + 2^-10) + 2^-12
@@ -173,11 +197,70 @@ def test_binning_lists_match_oracle_and_lb_equals_sq(gs):
             assert (zf[a], a) < (zf[b], b), (tid, a, b)
 
 
+@pytest.mark.parametrize("case", ["multiview_ragged", "box3", "large_splats", "nothing_visible"])
+def test_counting_binning_equals_radix_binning(gs, case):
+    """The counting binning and the radix path give the same per-tile lists
+    on several views of uneven, ragged sizes (block grids with partial
+    blocks), with the 3-sigma box, with Gaussians that span many blocks, and
+    when no Gaussian is visible (every list empty)."""
+    tuning = {"bbox_3sigma": 1} if case == "box3" else {}
+    if case == "multiview_ragged" or case == "box3":
+        scene = synth.scene_clustered(20000, seed=13, sh_degree=0)
+        ring = synth.ring_cameras(6, 333, 187)
+        cams = [ring[0], synth.ring_cameras(6, 129, 300)[2], synth.ring_cameras(6, 17, 9)[4],
+                synth.ring_cameras(6, 640, 360)[5]]
+    elif case == "large_splats":
+        scene = synth.scene_clustered(3000, seed=14, sh_degree=0)
+        scene.log_scales[:] += 3.0  # screen radii of tens to hundreds of pixels
+        cams = [synth.ring_cameras(4, 500, 420)[1]]
+    else:
+        scene = synth.scene_clustered(2000, seed=15, sh_degree=0)
+        scene.opacity_logits[:] = -20.0  # opacity below 1/255: no level set, nothing binned
+        cams = [synth.ring_cameras(4, 96, 64)[0]]
+    pc, *_ = _run_forward(gs, scene, cams, lb=True, tuning=tuning)
+    pr, *_ = _run_forward(gs, scene, cams, lb=True, tuning={**tuning, "bin_radix": 1})
+    ps, *_ = _run_forward(gs, scene, cams, lb=False, tuning=tuning)
+    n = _same_lists(pc, pr)
+    assert _same_lists(pc, ps) == n
+    if case == "nothing_visible":
+        assert n == 0
+    else:
+        assert n > 0
+
+
+@pytest.mark.parametrize("cap", [4096, 40000])
+def test_counting_binning_reports_overflow(gs, cap):
+    """A capacity below the instance count: the counting binning flags the
+    overflow and reports the exact count a large plan finds (at 4096 the
+    (Gaussian, block) entries overflow too); every write stays inside the
+    buffers and every tile range inside the capacity."""
+    from paper_2601_19489_gb300 import api
+
+    scene = synth.scene_clustered(20000, seed=16, sh_degree=0)
+    cam = synth.ring_cameras(4, 400, 300)[1]
+    big, *_ = _run_forward(gs, scene, [cam])
+    need = big.status()["n_instances"]
+    assert need > cap
+    plan = api.Plan(scene.n, 0, [(cam.width, cam.height)], cap)
+    params = api.Gaussians.from_scene(scene)
+    api.gs_preprocess(plan, params, [cam])
+    api.gs_bin_sort(plan, True)
+    torch.cuda.synchronize()
+    st = plan.status()
+    assert st["overflow"] == 1 and st["n_instances"] == need, (st, need)
+    from paper_2601_19489_gb300 import _lib as L
+
+    ranges = to_np(plan.view(L.GS_WS_TILE_RANGES, torch.int32)).reshape(-1, 2).astype(np.int64)
+    assert ranges.max() <= cap and np.all(ranges[:, 1] >= ranges[:, 0])
+
+
 # --------------------------------------------------------------- forward
 
-TUNINGS = [None, {"bucket": 64, "bwd_warps": 2, "bwd_chains": 2}, {"bucket": 64, "bwd_warps": 8, "bwd_chains": 1},
-           {"bucket": 32, "bwd_warps": 8, "bwd_chains": 2}, {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1},
-           {"bwd_per_pixel": 1}]
+# None: the plan's default (64-splat buckets, packed two-splat backward, one
+# warp per CTA)
+TUNINGS = [None, {"bucket": 64, "bwd_warps": 2, "bwd_chains": 0}, {"bucket": 64, "bwd_warps": 8, "bwd_chains": 0},
+           {"bucket": 32, "bwd_warps": 4, "bwd_chains": 0}, {"bucket": 32, "bwd_warps": 8, "bwd_chains": 2},
+           {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1}, {"bwd_per_pixel": 1}]
 
 
 @pytest.mark.parametrize("which", ["c1", "clustered_ragged"])
