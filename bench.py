@@ -423,14 +423,16 @@ def block_bits(sizes) -> int:
 def kernels_per_step(trainer, sizes) -> int:
     loss_k = 3 if trainer.lam > 0 else 2
     # preprocess 1; depth sort 4 passes x 3; then the binning: counting
-    # (entry count 1, entry write 1, entry sort 3/pass, block bounds 1, chunk
-    # scan 1, count / offsets / scatter 3) or radix (count 1, keys 1, tile
-    # sort 3/pass, ranges 1); forward 1; loss; blend bwd 1; then either the
-    # fused preprocess backward + Adam (step-count tick + 1) or preprocess
-    # bwd 1 + adam 2 (tick + update)
+    # (entry count 1, entry write 1, entry sort 3/pass, block bounds 1 when
+    # the sort takes more than one pass, chunk scan 1, mask / offsets /
+    # scatter 3) or radix (count 1, keys 1, tile sort 3/pass, ranges 1);
+    # forward 1; loss; blend bwd 1; then either the fused preprocess backward
+    # + Adam (step-count tick + 1) or preprocess bwd 1 + adam 2 (tick +
+    # update)
     tail = 2 if trainer.fused_adam else 3
     if trainer.load_balanced and not trainer.tuning.get("bin_radix", 0):
-        binning = 2 + 3 * -(-block_bits(sizes) // 8) + 2 + 3
+        passes = -(-block_bits(sizes) // 8)
+        binning = 2 + 3 * passes + (1 if passes > 1 else 0) + 1 + 3
     else:
         binning = 2 + 3 * -(-trainer.plan_tile_bits // 8) + 1
     return 1 + 12 + binning + 1 + loss_k + 1 + tail

@@ -407,16 +407,19 @@ k_tile_ranges(const uint32_t *__restrict__ keys, const StatusDev *st, int64_t ca
 //  4. k_block_bounds: each block's [start, end) among the sorted entries;
 //  5. k_chunk_scan: each block's entries cut into chunks of kChunk, the
 //     chunks of all blocks numbered by a scan;
-//  6. k_fine<0>: a warp per chunk counts the chunk's instances per tile of
-//     the block;
+//  6. k_fine_mask: a warp per chunk computes every entry's 64-bit mask of
+//     the block's tiles its Gaussian touches (exact column test), stores it
+//     and counts the chunk's instances per tile;
 //  7. k_fine_offsets: a CTA per block turns the counts into each chunk's
-//     first position per tile (the block's tiles in row order, each tile's
-//     chunks in order); the CTA that finishes last scans the block totals
-//     into block bases and publishes the instance count;
-//  8. k_fine<1>: the warps walk the chunks again and write every item to its
-//     position; the tile ranges come from the block bases.
-// Within a chunk the instances of one tile keep the entries' order, so each
-// tile's list is in depth order as after the radix path.
+//     first position per tile (the block's tiles in column-major order, each
+//     tile's chunks in order); the CTA that finishes last scans the block
+//     totals into block bases and checks their sum against the instance
+//     count;
+//  8. k_fine_scatter: a warp per chunk, a lane per tile, walks the chunk's
+//     entries in order and writes each item at the next position of every
+//     tile in its mask; the tile ranges come from the block bases.
+// Each tile's list therefore keeps the entries' order, which is the depth
+// order: the same lists as the radix path's.
 
 __device__ __forceinline__ int view_of_block(const ViewsDev &vd, int b) {
     int v = 0;
@@ -477,18 +480,10 @@ k_block_bounds(const uint32_t *__restrict__ ckey, const StatusDev *st, int64_t c
 // blocks.
 constexpr int kChunkScanThreads = 1024;
 
-__global__ void __launch_bounds__(kChunkScanThreads)
-k_chunk_scan(const uint2 *__restrict__ brange, int nblocks, uint32_t *__restrict__ bchunk, StatusDev *st) {
-    __shared__ uint32_t warp_tot[kChunkScanThreads / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (nblocks + kChunkScanThreads - 1) / kChunkScanThreads;
-    const int b0 = min(tid * per, nblocks), b1 = min(b0 + per, nblocks);
-    uint32_t local = 0;
-    for (int b = b0; b < b1; ++b) {
-        const uint2 r = brange[b];
-        local += (r.y - r.x + kChunk - 1) / kChunk;
-    }
-    uint32_t inc = local;
+// Exclusive scan of x over the CTA (kChunkScanThreads threads).
+__device__ __forceinline__ uint32_t cta_exclusive_scan1024(uint32_t x, uint32_t *warp_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
@@ -497,16 +492,46 @@ k_chunk_scan(const uint2 *__restrict__ brange, int nblocks, uint32_t *__restrict
     if (lane == 31) warp_tot[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        uint32_t x = warp_tot[lane], xi = x;
+        uint32_t w = warp_tot[lane], wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o);
-            if (lane >= o) xi += y;
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
         }
-        warp_tot[lane] = xi - x;
+        warp_tot[lane] = wi - w;
     }
     __syncthreads();
-    uint32_t run = inc - local + warp_tot[warp];
+    const uint32_t r = inc - x + warp_tot[warp];
+    __syncthreads();  // warp_tot is free again
+    return r;
+}
+
+// With totals (the entries per block, when the entries were sorted in one
+// pass whose digit is the block id: the sort's digit totals), brange is
+// written here from their scan; otherwise k_block_bounds wrote it.
+__global__ void __launch_bounds__(kChunkScanThreads)
+k_chunk_scan(uint2 *__restrict__ brange, const uint32_t *__restrict__ totals, int nblocks,
+             uint32_t *__restrict__ bchunk, StatusDev *st) {
+    __shared__ uint32_t warp_tot[kChunkScanThreads / 32];
+    const int tid = threadIdx.x;
+    const int per = (nblocks + kChunkScanThreads - 1) / kChunkScanThreads;
+    const int b0 = min(tid * per, nblocks), b1 = min(b0 + per, nblocks);
+    if (totals) {
+        uint32_t sum = 0;
+        for (int b = b0; b < b1; ++b) sum += totals[b];
+        uint32_t run = cta_exclusive_scan1024(sum, warp_tot);
+        for (int b = b0; b < b1; ++b) {
+            brange[b] = make_uint2(run, run + totals[b]);
+            run += totals[b];
+        }
+        __syncthreads();  // brange is read back below by other threads
+    }
+    uint32_t local = 0;
+    for (int b = b0; b < b1; ++b) {
+        const uint2 r = brange[b];
+        local += (r.y - r.x + kChunk - 1) / kChunk;
+    }
+    uint32_t run = cta_exclusive_scan1024(local, warp_tot);
     for (int b = b0; b < b1; ++b) {
         bchunk[b] = run;
         const uint2 r = brange[b];
@@ -521,53 +546,55 @@ k_chunk_scan(const uint2 *__restrict__ brange, int nblocks, uint32_t *__restrict
 constexpr int kFineWarps = 4;
 constexpr int kFineCtas = 152 * 16;
 
-// kPass 0: per chunk, its instance count per tile of the block into
-// ccnt[chunk][64].  kPass 1: ccnt holds each chunk's first position per tile
-// (block-local) and bbase the blocks' bases; write every item to its
-// position and the tile ranges.  A warp takes a chunk at a time; its
-// entries go 32 at a time, their in-block tile columns laid out as one flat
-// list (one column per lane, as the load-balanced key write), and each
-// column's rows come from the same exact column test as the tile count.
-template <int kPass>
+// The chunk c of a warp: its block b (bchunk[b] <= c < bchunk[b + 1]) and
+// its entries [e0, e1).
+__device__ __forceinline__ int chunk_block(const uint32_t *__restrict__ bchunk, int nblocks, uint32_t c) {
+    int lo = 0, hi = nblocks;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bchunk[mid] <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Tiles of a block are numbered column-major, t = 8 cx + cy, so an entry's
+// tile set is a 64-bit mask whose byte cx holds the rows of column cx; it is
+// kept as two words (columns 0-3, columns 4-7).
+
+// 32 x 32 bit-matrix transpose across a warp: lane i holds row i (bit j =
+// element (i, j)); afterwards lane j holds column j (bit i = element (i, j)).
+// Five butterfly stages: at stage s, lanes i and i ^ s exchange the s x s
+// blocks whose row and column bit s differ.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+    uint32_t m = 0x0000ffffu;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+        x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+        m ^= m << (s >> 1);
+    }
+    return x;
+}
+
+// Pass 1: a warp per chunk; its entries go 32 at a time, one per lane.  A
+// lane computes its entry's mask — for every in-block column of the
+// entry's tile rectangle, the rows of the exact column test (the same test
+// as the tile count) — and stores it; then the warp counts the chunk's
+// instances per tile (lane l: tiles l and l + 32) into ccnt[chunk][64].
+// The columns are visited in lockstep over the union of the lanes'
+// column ranges, so the lanes share one loop.
 __global__ void __launch_bounds__(kFineWarps * 32)
-k_fine(ViewsDev views, const uint32_t *__restrict__ cval, const uint2 *__restrict__ brange,
-       const uint32_t *__restrict__ bchunk, const float4 *__restrict__ rec, const float2 *__restrict__ bin,
-       const uint2 *__restrict__ rects, uint32_t *__restrict__ ccnt, const uint32_t *__restrict__ bbase,
-       const uint2 *__restrict__ btile, const StatusDev *st, int64_t capacity, uint32_t *__restrict__ inst_item,
-       uint2 *__restrict__ ranges, int box3) {
-    __shared__ uint32_t s_ctr[kFineWarps][kBlkTiles];
+k_fine_mask(ViewsDev views, const uint32_t *__restrict__ cval, const uint2 *__restrict__ brange,
+            const uint32_t *__restrict__ bchunk, const float4 *__restrict__ rec, const float2 *__restrict__ bin,
+            const uint2 *__restrict__ rects, uint32_t *__restrict__ mlo, uint32_t *__restrict__ mhi,
+            uint32_t *__restrict__ ccnt, const StatusDev *st, int box3) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
     const int gw = blockIdx.x * kFineWarps + warp, nw = gridDim.x * kFineWarps;
     const int nblocks = views.total_blocks;
-    const uint32_t cap = (uint32_t)capacity;
-    if (kPass == 1) {
-        // the tile ranges, a block per warp (tiles past the view's edge have none)
-        for (int b = gw; b < nblocks; b += nw) {
-            const ViewDev &cam = views.v[view_of_block(views, b)];
-            const int lb = b - cam.block_off;
-            const int bx = lb % cam.blocks_x, by = lb / cam.blocks_x;
-            const uint32_t base = bbase[b];
-            for (int lt = lane; lt < kBlkTiles; lt += 32) {
-                const int tx = bx * kBlk + (lt % kBlk), ty = by * kBlk + lt / kBlk;
-                if (tx < cam.tiles_x && ty < cam.tiles_y) {
-                    const uint2 bt = btile[(size_t)b * kBlkTiles + lt];
-                    const uint32_t s = min(base + bt.x, cap), e = min(base + bt.x + bt.y, cap);
-                    ranges[cam.tile_off + ty * cam.tiles_x + tx] = make_uint2(s, e);
-                }
-            }
-        }
-    }
     const uint32_t n_chunks = st->n_chunks;
     for (uint32_t c = (uint32_t)gw; c < n_chunks; c += (uint32_t)nw) {
-        // the chunk's block: bchunk[b] <= c < bchunk[b + 1]
-        int lo = 0, hi = nblocks;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (bchunk[mid] <= c) lo = mid;
-            else hi = mid;
-        }
-        const int b = lo;
+        const int b = chunk_block(bchunk, nblocks, c);
         const uint2 br = brange[b];
         const uint32_t e0 = br.x + (c - bchunk[b]) * (uint32_t)kChunk;
         const uint32_t e1 = min(e0 + (uint32_t)kChunk, br.y);
@@ -575,119 +602,171 @@ k_fine(ViewsDev views, const uint32_t *__restrict__ cval, const uint2 *__restric
         const int lb = b - cam.block_off;
         const int btx0 = (lb % cam.blocks_x) * kBlk, bty0 = (lb / cam.blocks_x) * kBlk;
         const float fW = (float)cam.W, fH = (float)cam.H;
-        uint32_t *ctr = s_ctr[warp];
-        if (kPass == 0) {
-            ctr[lane] = 0u;
-            ctr[lane + 32] = 0u;
-        } else {
-            const uint32_t base = bbase[b];
-            ctr[lane] = min(base + ccnt[(size_t)c * kBlkTiles + lane], cap);
-            ctr[lane + 32] = min(base + ccnt[(size_t)c * kBlkTiles + lane + 32], cap);
-        }
-        __syncwarp();
+        uint32_t cnt0 = 0, cnt1 = 0;
         for (uint32_t s0 = e0; s0 < e1; s0 += 32) {
             const uint32_t e = s0 + (uint32_t)lane;
-            uint32_t item = 0;
-            BinGeom my{};
-            int cx0 = 0, ry0 = 0, ry1 = 0;
-            uint32_t ncols = 0;
+            BinGeom g{};
+            int xa = kBlk, xb = 0, ry0 = 0, ry1 = 0;  // in-block column range [xa, xb)
             if (e < e1) {
-                item = cval[e];
+                const uint32_t item = cval[e];
                 const float4 r0v = rec[3 * (size_t)item];
                 const float2 bv = bin[item];
-                if (!box3) bin_geom(r0v.x, r0v.y, r0v.z, r0v.w, rec[3 * (size_t)item + 1].x, bv.y, bv.x, my);
+                if (!box3) bin_geom(r0v.x, r0v.y, r0v.z, r0v.w, rec[3 * (size_t)item + 1].x, bv.y, bv.x, g);
                 int tx0, ty0, tx1, ty1;
                 unpack_rect(rects[item], &tx0, &ty0, &tx1, &ty1);
-                cx0 = max(tx0, btx0);
-                const int cx1 = min(tx1, btx0 + kBlk);
                 ry0 = max(ty0, bty0);
                 ry1 = min(ty1, bty0 + kBlk);
-                ncols = (cx1 > cx0 && ry1 > ry0) ? (uint32_t)(cx1 - cx0) : 0u;
+                if (ry1 > ry0) {
+                    xa = max(tx0, btx0) - btx0;
+                    xb = min(tx1, btx0 + kBlk) - btx0;
+                }
             }
-            uint32_t colpref = ncols;  // inclusive, then exclusive scan of column counts
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, colpref, o);
-                if (lane >= o) colpref += y;
+            const int xmin = (int)__reduce_min_sync(0xffffffffu, (unsigned)xa);
+            const int xmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)xb);
+            uint32_t lo32 = 0, hi32 = 0;
+            for (int X = xmin; X < xmax; ++X) {
+                if (X >= xa && X < xb) {
+                    int rlo = ry0, rhi = ry1 - 1;
+                    bool any = true;
+                    if (!box3) {
+                        float pa, pb;
+                        column_span(btx0 + X, fW, &pa, &pb);
+                        any = column_rows(g, pa, pb, fH, ry0, ry1, &rlo, &rhi) > 0;
+                    }
+                    if (any) {
+                        const uint32_t rowbits = ((2u << (rhi - rlo)) - 1u) << (rlo - bty0);
+                        if (X < 4) lo32 |= rowbits << (8 * X);
+                        else hi32 |= rowbits << (8 * (X - 4));
+                    }
+                }
             }
-            const uint32_t n_cols = __shfl_sync(0xffffffffu, colpref, 31);
-            colpref -= ncols;
-            for (uint32_t f0 = 0; f0 < n_cols; f0 += 32) {
-                const uint32_t f = f0 + (uint32_t)lane;
-                const bool has = f < n_cols;
-                // owner: the last lane j with colpref_j <= f
-                int j = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const uint32_t cp = __shfl_sync(0xffffffffu, colpref, j + step);
-                    if (cp <= f) j += step;
-                }
-                BinGeom bg;
-                bg.mx = __shfl_sync(0xffffffffu, my.mx, j);
-                bg.my = __shfl_sync(0xffffffffu, my.my, j);
-                bg.B = __shfl_sync(0xffffffffu, my.B, j);
-                bg.detc = __shfl_sync(0xffffffffu, my.detc, j);
-                bg.tC = __shfl_sync(0xffffffffu, my.tC, j);
-                bg.invC = __shfl_sync(0xffffffffu, my.invC, j);
-                bg.dx_top = __shfl_sync(0xffffffffu, my.dx_top, j);
-                bg.rx = __shfl_sync(0xffffffffu, my.rx, j);
-                bg.ry = __shfl_sync(0xffffffffu, my.ry, j);
-                const int jcx0 = __shfl_sync(0xffffffffu, cx0, j);
-                const int jry0 = __shfl_sync(0xffffffffu, ry0, j), jry1 = __shfl_sync(0xffffffffu, ry1, j);
-                const uint32_t cp_j = __shfl_sync(0xffffffffu, colpref, j);
-                const uint32_t it = __shfl_sync(0xffffffffu, item, j);
-                const int tx = jcx0 + (int)(f - cp_j);
-                int rlo = 0, rhi = -1;
-                if (has) {
-                    if (box3) {
-                        rlo = jry0;
-                        rhi = jry1 - 1;
-                    } else {
-                        float xa, xb;
-                        column_span(tx, fW, &xa, &xb);
-                        if (!column_rows(bg, xa, xb, fH, jry0, jry1, &rlo, &rhi)) {
-                            rlo = 0;
-                            rhi = -1;
-                        }
-                    }
-                }
-                const int cx = tx - btx0;  // in-block column (any value when the lane has no rows)
-                const uint32_t rows = rhi >= rlo ? (((2u << (rhi - rlo)) - 1u) << (rlo - bty0)) : 0u;
-                if (kPass == 0) {
-                    for (int y = rlo; y <= rhi; ++y) atomicAdd(&ctr[cx + kBlk * (y - bty0)], 1u);
-                } else {
-                    // the lanes holding the same tile, in lane (= entry) order
-                    const uint32_t q0 = __ballot_sync(0xffffffffu, cx & 1), q1 = __ballot_sync(0xffffffffu, cx & 2);
-                    const uint32_t q2 = __ballot_sync(0xffffffffu, cx & 4);
-                    const uint32_t cpeers = ((cx & 1) ? q0 : ~q0) & ((cx & 2) ? q1 : ~q1) & ((cx & 4) ? q2 : ~q2);
-                    uint32_t rowb[kBlk];
-#pragma unroll
-                    for (int y = 0; y < kBlk; ++y) rowb[y] = __ballot_sync(0xffffffffu, (rows >> y) & 1u);
-#pragma unroll
-                    for (int y = 0; y < kBlk; ++y) {
-                        if ((rows >> y) & 1u) {
-                            const uint32_t P = cpeers & rowb[y];
-                            const uint32_t pos = ctr[cx + kBlk * y] + __popc(P & lt_mask);
-                            if (pos < cap) inst_item[pos] = it;
-                        }
-                    }
-                    __syncwarp();
-#pragma unroll
-                    for (int y = 0; y < kBlk; ++y) {
-                        if ((rows >> y) & 1u) {
-                            const uint32_t P = cpeers & rowb[y];
-                            if (lane == __ffs(P) - 1) ctr[cx + kBlk * y] += __popc(P);
-                        }
-                    }
-                }
-                __syncwarp();
+            if (e < e1) {
+                mlo[e] = lo32;
+                mhi[e] = hi32;
+            }
+            // lane l: the step's entries that touch tiles l and l + 32
+            cnt0 += __popc(warp_transpose32(lo32, lane));
+            cnt1 += __popc(warp_transpose32(hi32, lane));
+        }
+        ccnt[(size_t)c * kBlkTiles + lane] = cnt0;
+        ccnt[(size_t)c * kBlkTiles + 32 + lane] = cnt1;
+    }
+}
+
+// Pass 2: ccnt holds each chunk's first block-local position per tile and
+// bbase the block bases.  A warp per chunk, lane l owning tiles l and
+// l + 32: 32 entries at a time, the warp transposes their masks so that lane
+// l holds, as bits, which of the entries touch its tiles, and appends those
+// entries' items to its runs in entry order, so each run keeps the entries'
+// (depth) order by construction.  The runs are
+// staged in shared memory a 32-byte sector at a time: a lane writes a
+// sector once it is full (two 16-byte stores), and only the sectors its run
+// shares with a neighbour's (its first and last) word by word, so the
+// instance list is written in whole sectors rather than one scattered word
+// per instance.  The warps also write the tile ranges (a block per warp).
+struct RunStage {
+    uint32_t r;    // next position of the run
+    uint32_t lo;   // first slot of the current sector that belongs to the run
+};
+
+__device__ __forceinline__ void run_flush_partial(const RunStage &rs, const uint32_t *slot, uint32_t cap,
+                                                  uint32_t *__restrict__ out) {
+    const uint32_t sec = rs.r & ~7u;
+    for (uint32_t j = rs.lo; j < (rs.r & 7u); ++j)
+        if (sec + j < cap) out[sec + j] = slot[j];
+}
+
+__device__ __forceinline__ void run_append(RunStage &rs, uint32_t *slot, uint32_t x, uint32_t cap,
+                                           uint32_t *__restrict__ out) {
+    slot[rs.r & 7u] = x;
+    ++rs.r;
+    if ((rs.r & 7u) == 0u) {  // the sector [r - 8, r) is complete
+        const uint32_t sec = rs.r - 8u;
+        if (rs.lo == 0u && rs.r <= cap) {
+            uint4 *o = reinterpret_cast<uint4 *>(out + sec);
+            o[0] = make_uint4(slot[0], slot[1], slot[2], slot[3]);
+            o[1] = make_uint4(slot[4], slot[5], slot[6], slot[7]);
+        } else {
+            for (uint32_t j = rs.lo; j < 8u; ++j)
+                if (sec + j < cap) out[sec + j] = slot[j];
+        }
+        rs.lo = 0u;
+    }
+}
+
+constexpr int kStageStride = 9;  // words per staged sector (8 + 1 against bank conflicts)
+
+__global__ void __launch_bounds__(kFineWarps * 32)
+k_fine_scatter(ViewsDev views, const uint32_t *__restrict__ cval, const uint2 *__restrict__ brange,
+               const uint32_t *__restrict__ bchunk, const uint32_t *__restrict__ mlo,
+               const uint32_t *__restrict__ mhi, const uint32_t *__restrict__ ccnt,
+               const uint32_t *__restrict__ bbase, const uint2 *__restrict__ btile, const StatusDev *st,
+               int64_t capacity, uint32_t *__restrict__ inst_item, uint2 *__restrict__ ranges) {
+    __shared__ uint32_t s_stage[kFineWarps][kBlkTiles * kStageStride];
+    __shared__ uint32_t s_item[kFineWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kFineWarps + warp, nw = gridDim.x * kFineWarps;
+    const int nblocks = views.total_blocks;
+    const uint32_t cap = (uint32_t)capacity;
+    for (int b = gw; b < nblocks; b += nw) {
+        const ViewDev &cam = views.v[view_of_block(views, b)];
+        const int lb = b - cam.block_off;
+        const int bx = lb % cam.blocks_x, by = lb / cam.blocks_x;
+        const uint32_t base = bbase[b];
+        for (int t = lane; t < kBlkTiles; t += 32) {
+            const int tx = bx * kBlk + t / kBlk, ty = by * kBlk + t % kBlk;
+            if (tx < cam.tiles_x && ty < cam.tiles_y) {
+                const uint2 bt = btile[(size_t)b * kBlkTiles + t];
+                const uint32_t s = min(base + bt.x, cap), e = min(base + bt.x + bt.y, cap);
+                ranges[cam.tile_off + ty * cam.tiles_x + tx] = make_uint2(s, e);
             }
         }
-        if (kPass == 0) {
-            ccnt[(size_t)c * kBlkTiles + lane] = ctr[lane];
-            ccnt[(size_t)c * kBlkTiles + lane + 32] = ctr[lane + 32];
+    }
+    uint32_t *slot0 = s_stage[warp] + lane * kStageStride;
+    uint32_t *slot1 = s_stage[warp] + (lane + 32) * kStageStride;
+    const uint32_t n_chunks = st->n_chunks;
+    for (uint32_t c = (uint32_t)gw; c < n_chunks; c += (uint32_t)nw) {
+        const int b = chunk_block(bchunk, nblocks, c);
+        const uint2 br = brange[b];
+        const uint32_t e0 = br.x + (c - bchunk[b]) * (uint32_t)kChunk;
+        const uint32_t e1 = min(e0 + (uint32_t)kChunk, br.y);
+        const uint32_t base = bbase[b];
+        // the runs of tiles lane and lane + 32 (a base parked at the capacity
+        // keeps every position there or beyond: no write)
+        RunStage rs0, rs1;
+        rs0.r = min(base + ccnt[(size_t)c * kBlkTiles + lane], cap);
+        rs1.r = min(base + ccnt[(size_t)c * kBlkTiles + 32 + lane], cap);
+        rs0.lo = rs0.r & 7u;
+        rs1.lo = rs1.r & 7u;
+        uint32_t *items = s_item[warp];
+        for (uint32_t s0 = e0; s0 < e1; s0 += 32) {
+            const uint32_t e = s0 + (uint32_t)lane;
+            uint32_t lo = 0, hi = 0, it = 0;
+            if (e < e1) {
+                lo = mlo[e];
+                hi = mhi[e];
+                it = cval[e];
+            }
+            items[lane] = it;
+            // lane l: bit k set when the step's entry k touches tile l (w0)
+            // or l + 32 (w1); the set bits in order are the run's entries
+            uint32_t w0 = warp_transpose32(lo, lane), w1 = warp_transpose32(hi, lane);
+            __syncwarp();
+            while (w0) {
+                const int k = __ffs(w0) - 1;
+                w0 &= w0 - 1u;
+                run_append(rs0, slot0, items[k], cap, inst_item);
+            }
+            while (w1) {
+                const int k = __ffs(w1) - 1;
+                w1 &= w1 - 1u;
+                run_append(rs1, slot1, items[k], cap, inst_item);
+            }
+            __syncwarp();  // the next step overwrites items
         }
-        __syncwarp();
+        run_flush_partial(rs0, slot0, cap, inst_item);
+        run_flush_partial(rs1, slot1, cap, inst_item);
+        __syncwarp();  // the next chunk reuses the staging
     }
 }
 
@@ -818,10 +897,17 @@ static int bin_counting(const gs_plan *plan, void *ws, const uint32_t *order, ui
     const uint32_t *ckey = cfinal ? ckB : ckA, *cval = cfinal ? cvB : cvA;
     uint2 *brange = ws_at<uint2>(ws, plan->o_brange);
     uint32_t *bchunk = ws_at<uint32_t>(ws, plan->o_bchunk);
-    rc = check_cuda(cudaMemsetAsync(brange, 0, (size_t)nblocks * sizeof(uint2), s));
-    if (rc) return rc;
-    k_block_bounds<<<kSortBlocks, 256, 0, s>>>(ckey, st, ccap, brange);
-    k_chunk_scan<<<1, kChunkScanThreads, 0, s>>>(brange, nblocks, bchunk, st);
+    const uint32_t *totals = nullptr;
+    if (plan->block_bits <= kRadixBits) {
+        // one sort pass with the block id as its digit: its digit totals are
+        // the entries per block
+        totals = ws_at<uint32_t>(ws, plan->o_sort_scratch) + kRadix * kSortBlocks;
+    } else {
+        rc = check_cuda(cudaMemsetAsync(brange, 0, (size_t)nblocks * sizeof(uint2), s));
+        if (rc) return rc;
+        k_block_bounds<<<kSortBlocks, 256, 0, s>>>(ckey, st, ccap, brange);
+    }
+    k_chunk_scan<<<1, kChunkScanThreads, 0, s>>>(brange, totals, nblocks, bchunk, st);
     uint32_t *ccnt = ws_at<uint32_t>(ws, plan->o_ccnt);
     uint2 *btile = ws_at<uint2>(ws, plan->o_btile);
     uint32_t *bbase = ws_at<uint32_t>(ws, plan->o_bbase);
@@ -829,11 +915,13 @@ static int bin_counting(const gs_plan *plan, void *ws, const uint32_t *order, ui
     const float4 *rec = ws_at<float4>(ws, plan->o_rec);
     const float2 *bin = ws_at<float2>(ws, plan->o_bin);
     uint2 *ranges = ws_at<uint2>(ws, plan->o_ranges);
-    k_fine<0><<<kFineCtas, kFineWarps * 32, 0, s>>>(vd, cval, brange, bchunk, rec, bin, rects, ccnt, bbase, btile,
-                                                    st, plan->inst_cap, out, ranges, plan->bbox_3sigma);
+    // the entries' tile masks go to the pair of buffers the sort left free
+    uint32_t *mlo = cfinal ? ckA : ckB, *mhi = cfinal ? cvA : cvB;
+    k_fine_mask<<<kFineCtas, kFineWarps * 32, 0, s>>>(vd, cval, brange, bchunk, rec, bin, rects, mlo, mhi, ccnt, st,
+                                                      plan->bbox_3sigma);
     k_fine_offsets<<<nblocks, kOffThreads, 0, s>>>(bchunk, ccnt, btile, btot, bbase, st, nblocks, plan->inst_cap);
-    k_fine<1><<<kFineCtas, kFineWarps * 32, 0, s>>>(vd, cval, brange, bchunk, rec, bin, rects, ccnt, bbase, btile,
-                                                    st, plan->inst_cap, out, ranges, plan->bbox_3sigma);
+    k_fine_scatter<<<kFineCtas, kFineWarps * 32, 0, s>>>(vd, cval, brange, bchunk, mlo, mhi, ccnt, bbase, btile, st,
+                                                         plan->inst_cap, out, ranges);
     return launch_error();
 }
 
