@@ -775,7 +775,7 @@ k_fine_scatter(ViewsDev views, const uint32_t *__restrict__ cval, const uint2 *_
 // chunk's first block-local position for tile t; btile[b][t] = (tile start
 // in the block, tile total); bbase[b] is written by the CTA that finishes
 // last, which scans the block totals (64-bit) and publishes n_inst.
-constexpr int kOffThreads = 512;
+constexpr int kOffThreads = 1024;
 constexpr int kOffGroups = kOffThreads / kBlkTiles;
 
 __global__ void __launch_bounds__(kOffThreads)
@@ -793,6 +793,7 @@ k_fine_offsets(const uint32_t *__restrict__ bchunk, uint32_t *__restrict__ ccnt,
     const uint32_t per = (nch + kOffGroups - 1) / kOffGroups;
     const uint32_t ga = c0 + min((uint32_t)g * per, nch), gb = c0 + min((uint32_t)(g + 1) * per, nch);
     uint32_t sum = 0;
+#pragma unroll 4
     for (uint32_t c = ga; c < gb; ++c) sum += ccnt[(size_t)c * kBlkTiles + t];
     s_part[g][t] = sum;
     __syncthreads();

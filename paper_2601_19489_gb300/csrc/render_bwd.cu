@@ -37,25 +37,26 @@ namespace gs {
 template <int kWarps>
 struct BwdShared {
     float4 g[kTilePix];                       // (g_r, g_g, g_b, g_D), zero outside the image
-    float2 fin[kTilePix];                     // (S_fin, n_contrib as bits)
+    float4 fin[kTilePix];                     // (S_fin, n_contrib as bits, tile-local px, py)
     float2 ck[kWarps][kTilePix];              // per warp, compacted: (T, S) in front of its bucket
     uint8_t pix[kWarps][kTilePix];            // per warp, compacted: pixel index in the tile
     uint32_t next;                            // next unclaimed bucket of the tile
 };
 
 // Stage the tile's per-pixel data: the upstream gradient and
-// (S_fin, n_contrib) of every pixel, zero outside the image.
+// (S_fin, n_contrib) of every pixel, zero outside the image, with the
+// pixel's tile-local centre.
 template <int kThreads>
 __device__ __forceinline__ void stage_tile_pixels(const ViewDev &cam, int tx, int ty, const float *__restrict__ img_rgb,
                                                   const float *__restrict__ img_disp, const float *__restrict__ dL_drgb,
                                                   const float *__restrict__ dL_ddisp,
-                                                  const uint32_t *__restrict__ n_contrib, float4 *sg, float2 *sfin) {
+                                                  const uint32_t *__restrict__ n_contrib, float4 *sg, float4 *sfin) {
     const size_t npix = (size_t)cam.W * cam.H;
     const size_t base = (size_t)cam.pix_off;
     for (int p = threadIdx.x; p < kTilePix; p += kThreads) {
         const int ix = tx * kTile + (p & (kTile - 1)), iy = ty * kTile + (p >> 4);
         float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 fin = make_float2(0.f, __uint_as_float(0u));
+        float4 fin = make_float4(0.f, __uint_as_float(0u), (float)(p & (kTile - 1)) + 0.5f, (float)(p >> 4) + 0.5f);
         if (ix < cam.W && iy < cam.H) {
             const size_t pix = (size_t)iy * cam.W + ix;
             g.x = dL_drgb[3 * base + pix];
@@ -76,7 +77,7 @@ __device__ __forceinline__ void stage_tile_pixels(const ViewDev &cam, int tx, in
 // its bucket: T in front of j0 and X = S(j0) = g . C + g_D D in front of j0
 // for the first bucket, X = S(j0) - S_fin for the others (see bwd_pair).
 // Returns their number.
-__device__ __forceinline__ int compact_live(const float4 *sg, const float2 *sfin, const float *__restrict__ ckb,
+__device__ __forceinline__ int compact_live(const float4 *sg, const float4 *sfin, const float *__restrict__ ckb,
                                            uint32_t j0, float2 *ck, uint8_t *pix) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -113,12 +114,12 @@ struct SplatGrad {
 // behind is -X.  Both are the same quantity; the second keeps the running
 // sum at the size of what is still behind, so its float32 rounding shrinks
 // as the pixel saturates instead of growing with everything in front.
-__device__ __forceinline__ void bwd_pair(const float4 *__restrict__ sg, const float2 *__restrict__ sfin,
+__device__ __forceinline__ void bwd_pair(const float4 *__restrict__ sg, const float4 *__restrict__ sfin,
                                          const uint8_t *__restrict__ spix, int m, uint32_t k, const float4 &r0,
                                          const float4 &r1, const float4 &r2, bool first, float &T, float &Sv,
                                          SplatGrad &acc) {
     const int p = spix[m];
-    const float2 fin = sfin[p];
+    const float2 fin = make_float2(sfin[p].x, sfin[p].y);
     if (k >= __float_as_uint(fin.y)) return;  // beyond this pixel's last blended splat
     PairEval e;
     eval_pair(r0, r1, (float)(p & (kTile - 1)) + 0.5f, (float)(p >> 4) + 0.5f, e);
@@ -277,7 +278,7 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
 // pixels last the pipeline drains in fewer steps.  Returns the live count and
 // in *steps the number of pipeline steps: max over the list of m + (last
 // lane the pixel needs) + 1.
-__device__ __forceinline__ int compact_live_grouped(const float4 *sg, const float2 *sfin, const float *__restrict__ ckb,
+__device__ __forceinline__ int compact_live_grouped(const float4 *sg, const float4 *sfin, const float *__restrict__ ckb,
                                                    uint32_t j0, float2 *ck, uint8_t *pix, int *steps) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -398,12 +399,11 @@ k_render_bwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
                 }
                 if (m >= 0 && m < m_total) {  // false only while the pipeline fills and drains
                     const int p = spix[m];
-                    const float2 fin = S.fin[p];
+                    const float4 fin = S.fin[p];
                     const float4 g = S.g[p];
                     const uint32_t nc = __float_as_uint(fin.y);
                     const float fsel = j0 == 0 ? fin.x : 0.0f;  // X = S or S - S_fin (bwd_pair)
-                    const float px = (float)(p & (kTile - 1)) + 0.5f, py = (float)(p >> 4) + 0.5f;
-                    const f2x dx = sub2(pk2(px, px), MX), dy = sub2(pk2(py, py), MY);
+                    const f2x dx = sub2(pk2(fin.z, fin.z), MX), dy = sub2(pk2(fin.w, fin.w), MY);
                     // q = A dx^2 + 2B dx dy + C dy^2 (base 2), e = log2 o - q
                     const f2x q = fma2(fma2(CA, dx, mul2(CB2, dy)), dx, mul2(mul2(CC, dy), dy));
                     float eA, eB, qA, qB;
