@@ -130,7 +130,7 @@ def config_of(args):
                         f"16x16 tiles, loss {1 - args.lam:.1f} L1 + {args.lam:.1f} D-SSIM, one view per step",
             "gaussians": args.n, "views": args.views, "width": args.width, "height": args.height,
             "targets": "a second seeded clustered scene (seed 1, same size) rendered through the same cameras",
-            "tile": 16, "bucket": 64, "sh_degree": 3, "binning": "sequential" if args.sq else "load_balanced",
+            "tile": 16, "bucket": 64, "sh_degree": 3, "binning": "radix, sequential key write" if args.sq else "counting",
             "l2": "working set > L2 (params + Adam state ~1 GB, instances, checkpoints); no flush"}
 
 
@@ -245,16 +245,27 @@ def oracle_records(scene, cam):
         return opre.pack_for_render(opre.project(opre.params_from_scene(scene), cam, scene.sh_degree))
 
 
-def oracle_sample(scene, cam, rec_full, trec_full, wins, pre_sample: int, n_threads: int, seed: int = 0):
+def sample_plan(W: int, H: int, n_views: int, steps):
+    """The (view, window) of each CPU sample step s: view s mod n_views, one
+    seeded window (seed s) in cell 7 s mod 40 of the 8 x 5 grid, so 40
+    consecutive steps visit every cell once."""
+    nx, ny, _, _ = window_cells(W, H)
+    n_cells = nx * ny
+    stride = next(k for k in (7, 3, 1) if n_cells % k or k == 1)
+    return [(s % n_views, sample_windows(W, H, [(stride * s) % n_cells], seed=s)[0]) for s in steps]
+
+
+def oracle_sample(scene, groups, pre_cam, pre_sample: int, n_threads: int, seed: int = 0):
     """Time the float64 oracle on a bounded sample of one training step and
     extrapolate to the whole step.  Returns (seconds per full step, detail).
 
-    preprocess fwd+bwd and Adam: a random subset of `pre_sample` Gaussians,
-    scaled by N / pre_sample; blend fwd + loss + per-pixel bwd: the windows
-    `wins`, scaled by H * W / (their pixels).  rec_full / trec_full are the
-    view's records of the trained and of the target scene (oracle_records);
-    the target inside each window is the oracle's own render of the target
-    scene there (setup, untimed)."""
+    preprocess fwd+bwd and Adam: a random subset of `pre_sample` Gaussians on
+    view pre_cam, scaled by N / pre_sample; blend fwd + loss + per-pixel bwd:
+    the windows of `groups`, a list of (cam, rec_full, trec_full, windows)
+    (rec_full / trec_full: that view's records of the trained and of the
+    target scene, oracle_records), scaled by one view's H * W over the
+    windows' pixels.  The target inside each window is the oracle's own
+    render of the target scene there (setup, untimed)."""
     import torch
 
     from oracle import preprocess as opre
@@ -268,18 +279,21 @@ def oracle_sample(scene, cam, rec_full, trec_full, wins, pre_sample: int, n_thre
     N = scene.n
     sub = np.sort(rng.choice(N, size=min(pre_sample, N), replace=False))
     sub_scene = synth.Scene(*(a[sub] for a in scene.arrays()), sh_degree=scene.sh_degree)
-    W, H = cam.width, cam.height
-    rec = near_windows(rec_full, wins)
-    trec = near_windows(trec_full, wins)
-    tgts = [oren.render_fwd(trec, (0.0, 0.0, 0.0), w, amb=None, n_threads=n_threads)["rgb"] for w in wins]
+    W, H = pre_cam.width, pre_cam.height
+    work = []
+    for cam, rec_full, trec_full, wins in groups:
+        rec = near_windows(rec_full, wins)
+        trec = near_windows(trec_full, wins)
+        for w in wins:
+            work.append((rec, w, oren.render_fwd(trec, (0.0, 0.0, 0.0), w, amb=None, n_threads=n_threads)["rgb"]))
     t0 = time.perf_counter()
     with torch.no_grad():
-        opre.project(opre.params_from_scene(sub_scene), cam, scene.sh_degree)
+        opre.project(opre.params_from_scene(sub_scene), pre_cam, scene.sh_degree)
     g2d = rng.standard_normal((sub.size, 10))
-    grads = opre.preprocess_backward(sub_scene, cam, g2d)
+    grads = opre.preprocess_backward(sub_scene, pre_cam, g2d)
     t1 = time.perf_counter()
     pairs = 0
-    for w, tgt in zip(wins, tgts):
+    for rec, w, tgt in work:
         f = oren.render_fwd(rec, (0.0, 0.0, 0.0), w, amb=None, n_threads=n_threads)
         _, g_rgb = oloss.photometric(f["rgb"], tgt, 0.2)
         oren.render_bwd(rec, (0.0, 0.0, 0.0), w, g_rgb, np.zeros_like(f["disp"]), n_threads=n_threads)
@@ -289,12 +303,12 @@ def oracle_sample(scene, cam, rec_full, trec_full, wins, pre_sample: int, n_thre
         oadam.adam_step(getattr(sub_scene, k), v, np.zeros_like(v), np.zeros_like(v), 1, 1e-3)
     t3 = time.perf_counter()
     scale_g = N / sub.size
-    px = float(sum((w[2] - w[0]) * (w[3] - w[1]) for w in wins))
+    px = float(sum((w[2] - w[0]) * (w[3] - w[1]) for _, w, _ in work))
     scale_p = (W * H) / px
     est = (t1 - t0) * scale_g + (t2 - t1) * scale_p + (t3 - t2) * scale_g
     detail = {"preprocess_s": (t1 - t0) * scale_g, "render_s": (t2 - t1) * scale_p,
               "adam_s": (t3 - t2) * scale_g, "measured_s": t3 - t0, "pairs": pairs,
-              "pairs_per_px": pairs / px, "windows": len(wins)}
+              "pairs_per_px": pairs / px, "windows": len(work)}
     return est, detail
 
 
@@ -311,18 +325,15 @@ def run_reference(args, rank, world):
     target_scene = synth.scene_clustered(args.n, seed=1, sh_degree=3)
     n_threads = os.cpu_count() or 1
     nx, ny, _, _ = window_cells(args.width, args.height)
-    n_cells = nx * ny
-    stride = next(k for k in (7, 3, 1) if n_cells % k or k == 1)
     records = {}
     times = []
-    for s in range(args.warmup + args.steps):
-        v = s % len(cams)
+    for s, (v, win) in zip(range(args.warmup + args.steps),
+                           sample_plan(args.width, args.height, len(cams), range(args.warmup + args.steps))):
         cam = cams[v]
         if v not in records:
             records[v] = (oracle_records(scene, cam), oracle_records(target_scene, cam))
-        wins = sample_windows(cam.width, cam.height, [(stride * s) % n_cells], seed=s)
-        est, _ = oracle_sample(scene, cam, *records[v], wins, pre_sample=REF_PRE_SAMPLE, n_threads=n_threads,
-                               seed=s)
+        est, _ = oracle_sample(scene, [(cam, *records[v], [win])], cam, pre_sample=REF_PRE_SAMPLE,
+                               n_threads=n_threads, seed=s)
         if s >= args.warmup:
             times.append(est)
     value = 1.0 / float(np.mean(times))
@@ -334,7 +345,7 @@ def run_reference(args, rank, world):
                              "sample": f"per step s (view s mod {len(cams)}): preprocess fwd+bwd and Adam on "
                                        f"{REF_PRE_SAMPLE} random Gaussians (x N/{REF_PRE_SAMPLE}), blend "
                                        f"fwd+loss+bwd on one seeded {WINDOW}x{WINDOW} window in cell "
-                                       f"({stride} s mod {n_cells}) of a {nx}x{ny} grid over the image "
+                                       f"(7 s mod {nx * ny}) of a {nx}x{ny} grid over the image "
                                        f"(x H*W/{WINDOW * WINDOW}); the mean over steps covers every cell"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -421,7 +432,9 @@ def block_bits(sizes) -> int:
 
 
 def kernels_per_step(trainer, sizes) -> int:
-    loss_k = 3 if trainer.lam > 0 else 2
+    # loss: SSIM forward + backward (or L1 + final reduction), and the
+    # disparity L1 when it is weighted
+    loss_k = 2 + (1 if trainer.disp_weight > 0 else 0)
     # preprocess 1; depth sort 4 passes x 3; then the binning: counting
     # (entry count 1, entry write 1, entry sort 3/pass, block bounds 1 when
     # the sort takes more than one pass, chunk scan 1, mask / offsets /
@@ -628,19 +641,23 @@ def run_ours(args, rank, world):
     if world == 1 and not args.no_visible_adam:
         line["visible_adam"] = run_visible_adam(args, dev, scene, lb, tuning, max(60, args.steps // 3))
     if world == 1 and not args.no_cpu_baseline:
-        cam = cams[0]
         n_threads = os.cpu_count() or 1
-        nx, ny, _, _ = window_cells(cam.width, cam.height)
-        wins = sample_windows(cam.width, cam.height, range(nx * ny), seed=0)
+        nx, ny, _, _ = window_cells(args.width, args.height)
+        # the reference arm's first 40 steps: every cell once, views s mod 16
+        plan = sample_plan(args.width, args.height, len(cams), range(nx * ny))
         tscene = synth.scene_clustered(args.n, seed=1, sh_degree=3)
-        est, detail = oracle_sample(scene, cam, oracle_records(scene, cam), oracle_records(tscene, cam), wins,
-                                    pre_sample=BASELINE_PRE_SAMPLE, n_threads=n_threads)
+        groups = []
+        for v in sorted({v for v, _ in plan}):
+            groups.append((cams[v], oracle_records(scene, cams[v]), oracle_records(tscene, cams[v]),
+                           [w for vv, w in plan if vv == v]))
+        est, detail = oracle_sample(scene, groups, cams[0], pre_sample=BASELINE_PRE_SAMPLE, n_threads=n_threads)
         line["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": n_threads, "kind": "oracle",
-                                "sample": f"view 0: preprocess fwd+bwd and Adam on {BASELINE_PRE_SAMPLE} random "
-                                          f"Gaussians (x N/{BASELINE_PRE_SAMPLE}), blend fwd + loss + per-pixel "
-                                          f"bwd on one seeded {WINDOW}x{WINDOW} window in each cell of a "
-                                          f"{nx}x{ny} grid over the image (x H*W/({nx * ny}*{WINDOW * WINDOW})); "
-                                          f"float64",
+                                "sample": f"preprocess fwd+bwd and Adam on {BASELINE_PRE_SAMPLE} random Gaussians "
+                                          f"(x N/{BASELINE_PRE_SAMPLE}, view 0); blend fwd + loss + per-pixel bwd "
+                                          f"on {nx * ny} seeded {WINDOW}x{WINDOW} windows, window s in cell "
+                                          f"7 s mod {nx * ny} of a {nx}x{ny} grid over view s mod {len(cams)} "
+                                          f"(every cell once; the reference arm's first {nx * ny} steps), "
+                                          f"x H*W/({nx * ny}*{WINDOW * WINDOW}); float64",
                                 "detail": detail}
     print(json.dumps(line), flush=True)
 
@@ -954,13 +971,16 @@ def run_recon(args):
     results = {}
     with ClockSampler(0) as clk:
         for m in [x for x in args.recon_methods.split(",") if x]:
-            method, true_poses = m.split("@")[0], m.endswith("@true")
+            # "<method>@true": on the true poses; "batched_graph~fixed": Adam's
+            # betas unscaled by the batch
+            method, true_poses = m.split("@")[0].split("~")[0], m.endswith("@true")
             cs = cams if true_poses else given
             results[m] = reconstruct(method, init, [cs[i] for i in tr_ix], [views[i][0] for i in tr_ix],
                                      [views[i][1] for i in tr_ix], [cs[i] for i in ev], [views[i][0] for i in ev],
                                      budget_s=args.recon_budget, lam=args.lam,
                                      densify_rules={"tau_plus": args.densify_tau_plus}, max_gaussians=600000,
-                                     batch_lr_scale=args.recon_batch_lr_scale, device=dev)
+                                     batch_lr_scale=args.recon_batch_lr_scale,
+                                     batch_betas="fixed" if "~fixed" in m else "scaled", device=dev)
             if err is not None and not true_poses:
                 results[m]["pose_error"] = pose_error_report(gt.means, cams, given, results[m].get("pose_correction"))
             torch.cuda.empty_cache()

@@ -15,7 +15,11 @@ Ways to spend the budget, all on one schedule:
                  a parameter by about its rate whatever the gradient's scale,
                  while the batch's averaged gradient is less noisy, so the
                  rate grows with the square root of the batch (the usual
-                 rule for Adam); the decay schedule is unchanged;
+                 rule for Adam); with batch_betas "scaled" (the default)
+                 Adam's betas become beta^8, so the moments forget at the
+                 same rate per view as with one view per step (the rule of
+                 Grendel, Zhao et al. 2024, for batched 3DGS); "fixed" keeps
+                 (0.9, 0.999); the decay schedule is unchanged;
   ng             one view per step of the neural-Gaussian model (Sec. 2.3):
                  anchors at the starting points, 10 decoded children each;
   ng_frozen      the same anchors and children with the decoder's MLP kept at
@@ -84,8 +88,8 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
                 budget_s: float = 60.0, eval_every_s: float = 5.0, lam: float = 0.2, disp_weight: float = 0.1,
                 extent: float = 4.4, batch: int = 8, seed: int = 0, densify_rules: dict | None = None,
                 densify_tau: float = 0.3, densify_k: int = 10, max_gaussians: int | None = None,
-                pose: dict | None = None, batch_lr_scale: float | None = None, ng_lrs: dict | None = None,
-                device="cuda") -> dict:
+                pose: dict | None = None, batch_lr_scale: float | None = None, batch_betas: str = "scaled",
+                ng_lrs: dict | None = None, device="cuda") -> dict:
     """Run one method for budget_s seconds of training; returns its held-out
     PSNR curve [(seconds trained, PSNR)], steps and views trained.
     pose: settings of the `pose` method (default_pose(extent) by default).
@@ -117,8 +121,13 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
         elif method not in ("plain", "densify", "pose"):
             raise ValueError(method)
         pose_cfg = {**default_pose(extent), **(pose or {})} if method == "pose" else None
+        betas = (0.9, 0.999)
+        if method == "batched_graph" and batch_betas == "scaled":
+            betas = (0.9 ** batch, 0.999 ** batch)
+        elif batch_betas not in ("scaled", "fixed"):
+            raise ValueError(batch_betas)
         tr = Trainer(params, W, H, lam=lam, disp_weight=disp_weight, lrs=lrs, load_balanced=lb, tuning=tuning,
-                     pose=pose_cfg, device=device)
+                     pose=pose_cfg, betas=betas, device=device)
     views = b_cams if method == "batched_graph" else [[c] for c in train_cams]
     tr.ensure_capacity(views, slack=2.0)
     n_seg = max(1, int(round(budget_s / eval_every_s)))
@@ -175,6 +184,7 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
         extra["pose_correction"] = {"R": R.tolist(), "t": t.tolist(), "updates": int(tr.pose.buf[24].item())}
     if method == "batched_graph":
         extra["lr_scale"] = lrs["log_scales"] / default_lrs(extent)["log_scales"]
+        extra["betas"] = list(tr.betas)
     return {**extra, "method": method, "curve": curve, "psnr_final": curve[-1][1], "psnr_start": curve[0][1],
             "steps": steps, "views": steps * per_step, "seconds": trained,
             "views_per_s": steps * per_step / trained, "gaussians_final": tr.params.n,

@@ -74,7 +74,7 @@ class Trainer:
                  lam: float = 0.2, bg=(0.0, 0.0, 0.0), lrs: dict | None = None,
                  inst_capacity: int | None = None, load_balanced: bool = True, disp_weight: float = 0.0,
                  tuning: dict | None = None, fused_adam: bool = True, pose: dict | None = None,
-                 visible_adam: bool = False, device="cuda"):
+                 visible_adam: bool = False, betas=(0.9, 0.999), device="cuda"):
         """tuning: launch shapes of the plans ({"bucket": 32 | 64,
         "bwd_warps": 2 | 4 | 8}), e.g. from autotune.autotune.
         fused_adam: apply Adam inside the preprocess backward
@@ -86,7 +86,8 @@ class Trainer:
         pose: enable the global pose refinement ({"every", "lr_rot",
         "lr_trans"}, missing keys from default_pose()); the correction is in
         self.pose (a PoseState) and applies to every view this trainer
-        renders."""
+        renders.
+        betas: Adam's (beta1, beta2)."""
         self.params = params
         self.fused_adam = bool(fused_adam)
         self.visible_adam = bool(visible_adam)
@@ -94,6 +95,7 @@ class Trainer:
             raise ValueError("visible-only Adam runs inside the fused preprocess backward")
         self.STAGES = self.STAGES_FUSED if self.fused_adam else self.STAGES_UNFUSED
         self.tuning = dict(tuning or {})
+        self.betas = (float(betas[0]), float(betas[1]))
         self.grads = params.zeros_like()
         self.lam = float(lam)
         self.disp_weight = float(disp_weight)
@@ -162,7 +164,8 @@ class Trainer:
         groups.append({"p": p.sh, "g": g.sh, "m": m.sh, "v": v.sh, "lr": self.lrs["sh_rest"],
                        "period": 3 * K, "head": 3, "lr_head": self.lrs["sh_dc"]})
         self._adam = adam_groups_array(groups)
-        self._hp = adam_hparams(self.lrs, visible_only=getattr(self, "visible_adam", False))
+        self._hp = adam_hparams(self.lrs, b1=self.betas[0], b2=self.betas[1],
+                                visible_only=getattr(self, "visible_adam", False))
         self._pstruct = p.struct()
         self._gstruct = g.struct()
         self._mstruct = m.struct()
@@ -257,7 +260,7 @@ class Trainer:
             self._pose_tick(s)
             return
         self._splat_stages(cams, target, target_disp, s, ev, 1)
-        L.check(L.lib().gs_adam_step_multi_dev(self._adam, len(self._adam), 0.9, 0.999, 1e-15,
+        L.check(L.lib().gs_adam_step_multi_dev(self._adam, len(self._adam), self.betas[0], self.betas[1], 1e-15,
                                                self.d_step.data_ptr(), s), "gs_adam_step_multi_dev")
         ev(7)
         self._pose_tick(s)
@@ -570,7 +573,7 @@ class NgTrainer(Trainer):
                                          ctypes.byref(self._ngg), self.ng_ws.data_ptr(), s), "gs_ng_decode_bwd")
         ev(8)
         self.step_count += 1
-        L.check(L.lib().gs_adam_step_multi_dev(self._adam, len(self._adam), 0.9, 0.999, 1e-15,
+        L.check(L.lib().gs_adam_step_multi_dev(self._adam, len(self._adam), self.betas[0], self.betas[1], 1e-15,
                                                self.d_step.data_ptr(), s), "gs_adam_step_multi_dev")
         ev(9)
 
