@@ -1044,11 +1044,12 @@ def run_ablation(args, steps: int = 200, warmup: int = 10):
     L.load()
     scene, cams = workload(args)
     targets = render_targets(args.n, cams, dev)
-    shape = {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1}
+    shape = {"bucket": 64, "bwd_warps": 1, "bwd_chains": 0}
     configs = [("3DGS (per-pixel backward, 3-sigma box, Sq)", False, {"bwd_per_pixel": 1, "bbox_3sigma": 1}),
                ("w/ B", False, {**shape, "bbox_3sigma": 1}),
                ("w/ B & F & Sq", False, dict(shape)),
-               ("w/ B & F & LB", True, dict(shape)),
+               ("w/ B & F & LB (counting binning)", True, dict(shape)),
+               ("w/ B & F & LB (key write + tile sort; not in Tab. 1)", True, {**shape, "bin_radix": 1}),
                ("w/ F & LB, per-pixel backward (not in Tab. 1)", True, {"bwd_per_pixel": 1})]
     rows = []
     with ClockSampler(0) as clk:

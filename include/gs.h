@@ -275,7 +275,7 @@ GS_API int gs_preprocess_bwd(const gs_plan *plan, void *ws, const gs_params *par
  * d_step: device int32 step count, incremented on the stream first; the
  * incremented value is the t of the bias corrections.  Rates per parameter
  * group; the SH DC coefficients (the first 3 floats of a Gaussian's SH row)
- * take lr_sh_dc, the rest lr_sh_rest.  b1, b2 in [0.5, 1).  Every array of
+ * take lr_sh_dc, the rest lr_sh_rest.  b1, b2 in (0, 1).  Every array of
  * params, adam_m and adam_v must start 16-byte aligned (GS_ERR_ARG
  * otherwise).
  * visible_only != 0 selects the sparse (visible-only) Adam of the Taming-3DGS
@@ -336,7 +336,8 @@ GS_API int gs_adam_step_multi(const gs_adam_group *h_groups, int32_t n_groups, f
  * step captured once in a CUDA graph can be replayed: d_step (device int32,
  * 0 before the first update) is incremented on the stream first, and the
  * incremented value is the t of the bias corrections, evaluated in float32
- * as 1 - b^t = -expm1(t log1p(b - 1)).  b1 and b2 must lie in [0.5, 1).
+ * as 1 - b^t = -expm1(t log1p(b - 1)) (b - 1 is exact for b in [0.5, 1)
+ * and rounds once below).  b1 and b2 must lie in (0, 1).
  * Two launches; the groups are captured by value. */
 GS_API int gs_adam_step_multi_dev(const gs_adam_group *h_groups, int32_t n_groups, float b1, float b2,
                                   float eps, int32_t *d_step, void *stream);

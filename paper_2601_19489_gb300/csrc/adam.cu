@@ -8,8 +8,9 @@
 // double there) or lives in device memory, for a step captured once in a
 // CUDA graph and replayed: a one-thread launch increments it, and every
 // thread of the update derives 1 - b^t = -expm1(t log1p(b - 1)) in float32
-// (b - 1 is exact for b in [0.5, 1), and the two library calls keep the
-// relative error near 1e-7 even at t = 1, where 1 - b^t cancels).
+// (b - 1 is exact for b in [0.5, 1) and rounds once below; the two library
+// calls keep the relative error near 1e-7 even at t = 1, where 1 - b^t
+// cancels).
 #include <math.h>
 
 #include "gs_internal.cuh"
@@ -102,7 +103,7 @@ int adam_tick(int32_t *d_step, cudaStream_t s) {
 static int adam_launch(const gs_adam_group *groups, int n_groups, float b1, float b2, float eps,
                        int step, int32_t *d_step, cudaStream_t s) {
     if (!groups || n_groups < 1 || n_groups > kMaxGroups || (!d_step && step < 1) ||
-        !(b1 >= (d_step ? 0.5f : 0.f) && b1 < 1.f) || !(b2 >= (d_step ? 0.5f : 0.f) && b2 < 1.f) ||
+        !(b1 > 0.f && b1 < 1.f) || !(b2 > 0.f && b2 < 1.f) ||
         !(eps >= 0.f))
         return GS_ERR_ARG;
     AdamGroups G;

@@ -1001,7 +1001,7 @@ extern "C" int gs_preprocess_bwd_adam(const gs_plan *plan, void *ws, gs_params *
     if (!rc) rc = check_params(plan, adam_v);
     if (!rc) rc = check_cams(plan, cams);
     if (rc) return rc;
-    if (!(hp->b1 >= 0.5f && hp->b1 < 1.0f) || !(hp->b2 >= 0.5f && hp->b2 < 1.0f) || !(hp->eps >= 0.0f))
+    if (!(hp->b1 > 0.0f && hp->b1 < 1.0f) || !(hp->b2 > 0.0f && hp->b2 < 1.0f) || !(hp->eps >= 0.0f))
         return GS_ERR_ARG;
     // every attribute array is streamed with float4 accesses
     const gs_params *all[3] = {params, adam_m, adam_v};

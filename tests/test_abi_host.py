@@ -213,7 +213,7 @@ def test_more_argument_errors_are_caught_on_the_host(lib):
                                    ctypes.byref(out_n), None) == ARG
         assert lib.gs_densify_apply(0, ctypes.byref(p), ctypes.byref(p), ctypes.byref(p), fake, fake, fake,
                                     ctypes.byref(p), ctypes.byref(p), ctypes.byref(p), None) == ARG
-        # fused Adam: b1 outside [0.5, 1)
+        # fused Adam: b1 outside (0, 1)
         cam = L.GsCamera()
         cam.fx = cam.fy = 64.0
         cam.cx, cam.cy, cam.width, cam.height, cam.near_z = 32.0, 24.0, 64, 48, 0.2

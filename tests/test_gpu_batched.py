@@ -32,8 +32,13 @@ def _flat(arrs, planar=True):
     return torch.from_numpy(np.concatenate([a.reshape(-1) for a in arrs]).astype(np.float32)).cuda()
 
 
-def test_adam_device_step_matches_oracle(gs):
+@pytest.mark.parametrize("betas", [(0.9, 0.999), (0.9 ** 8, 0.999 ** 8)])
+def test_adam_device_step_matches_oracle(gs, betas):
+    """Default betas and the batch-scaled ones of an 8-view batch (beta^8:
+    beta1 below 0.5, where b - 1 in the bias correction rounds)."""
     from paper_2601_19489_gb300 import api
+
+    b1, b2 = betas
 
     rng = np.random.default_rng(11)
     n = 5003
@@ -50,10 +55,12 @@ def test_adam_device_step_matches_oracle(gs):
         gp, gq = torch.from_numpy(gp0.copy()).cuda(), torch.from_numpy(gq0.copy()).cuda()
         api.gs_adam_step_multi_dev([{"p": p, "g": gp, "m": mp, "v": vp, "lr": 1e-2},
                                     {"p": q, "g": gq, "m": mq, "v": vq, "lr": 3e-3, "period": 48, "head": 3,
-                                     "lr_head": 5e-2}], d_step)
-        ref["p"], ref["mp"], ref["vp"] = oadam.adam_step(ref["p"], gp0, ref["mp"], ref["vp"], step, lr=1e-2)
+                                     "lr_head": 5e-2}], d_step, b1=b1, b2=b2)
+        ref["p"], ref["mp"], ref["vp"] = oadam.adam_step(ref["p"], gp0, ref["mp"], ref["vp"], step, lr=1e-2,
+                                                         b1=b1, b2=b2)
         lr_q = np.where(np.arange(96) % 48 < 3, 5e-2, 3e-3)
-        ref["q"], ref["mq"], ref["vq"] = oadam.adam_step(ref["q"], gq0, ref["mq"], ref["vq"], step, lr=lr_q)
+        ref["q"], ref["mq"], ref["vq"] = oadam.adam_step(ref["q"], gq0, ref["mq"], ref["vq"], step, lr=lr_q,
+                                                         b1=b1, b2=b2)
         assert float(gp.abs().max()) == 0.0 and float(gq.abs().max()) == 0.0
     assert int(d_step.item()) == 4
     np.testing.assert_allclose(to_np(p), ref["p"], rtol=1e-5, atol=1e-6)
