@@ -432,9 +432,9 @@ def block_bits(sizes) -> int:
 
 
 def kernels_per_step(trainer, sizes) -> int:
-    # loss: SSIM forward + backward (or L1 + final reduction), and the
-    # disparity L1 when it is weighted
-    loss_k = 2 + (1 if trainer.disp_weight > 0 else 0)
+    # loss: the fused SSIM pass (or L1 + final reduction), and the disparity
+    # L1 when it is weighted
+    loss_k = (1 if trainer.lam > 0 else 2) + (1 if trainer.disp_weight > 0 else 0)
     # preprocess 1; depth sort 4 passes x 3; then the binning: counting
     # (entry count 1, entry write 1, entry sort 3/pass, block bounds 1 when
     # the sort takes more than one pass, chunk scan 1, mask / offsets /
@@ -460,6 +460,7 @@ def run_ours(args, rank, world):
     from paper_2601_19489_gb300 import api
     from paper_2601_19489_gb300 import _lib as L
     from paper_2601_19489_gb300.trainer import Trainer
+    from paper_2601_19489_gb300.autotune import TUNED, parse_tuning_key, tuning_key
     import synth
 
     L.load()
@@ -468,19 +469,17 @@ def run_ours(args, rank, world):
     targets_d = render_targets(args.n, cams, dev)
     tuning, lb, table = {}, not args.sq, None
     if args.tuning:
-        parts = args.tuning.split("/")
-        lb, tuning = parts[0] == "LB", {"bucket": int(parts[1][1:]), "bwd_warps": int(parts[2][1:])}
-        tuning["bwd_chains"] = int(parts[3][1:]) if len(parts) > 3 else 0
+        lb, tuning = parse_tuning_key(args.tuning)
     elif not args.sq:  # launch shapes from the autotuner, on this workload's own views
-        from paper_2601_19489_gb300.autotune import autotune
+        from paper_2601_19489_gb300.autotune import TUNED, autotune
 
         best, table = autotune(params, [[cams[0]], [cams[1]]], targets_d[:2], lam=args.lam, device=dev)
-        tuning = {k: best[k] for k in ("bucket", "bwd_warps", "bwd_chains")}
+        tuning = {k: best[k] for k in TUNED}
         lb = best["load_balanced"]
     trainer = Trainer(params, args.width, args.height, lam=args.lam, load_balanced=lb, tuning=tuning, device=dev)
     trainer.autotune_table = table
     tu = trainer.slot_for([cams[0]]).plan.tuning
-    trainer_tuning_key = (f"{'LB' if lb else 'Sq'}/b{tu['bucket']}/w{tu['bwd_warps']}/c{tu['bwd_chains']}")
+    trainer_tuning_key = tuning_key(lb, tu)
     ntiles = ((args.width + 15) // 16) * ((args.height + 15) // 16)
     trainer.plan_tile_bits = max(1, int(np.ceil(np.log2(ntiles))))
     targets_h = [t.cpu().pin_memory() for t in targets_d]
@@ -579,14 +578,15 @@ def run_ours(args, rank, world):
                                  hbm or FALLBACK_HBM_GBS, ssim=args.lam > 0)
     bucket = trainer.slot_for([cams[0]]).plan.tuning["bucket"]
     kname = {"render_bwd_blend": "k_render_bwd_pk" if bucket == 64 else "k_render_bwd",
-             "render_fwd": "k_render_fwd", "preprocess": "k_preprocess",
-             "preprocess_bwd_adam": "k_preprocess_bwd (Adam fused)", "loss": "k_ssim_fwd + k_ssim_bwd",
+             "render_fwd": "k_render_fwd_pk" if tu["fwd_pixels"] == 2 else "k_render_fwd",
+             "preprocess": "k_preprocess",
+             "preprocess_bwd_adam": "k_preprocess_bwd (Adam fused)", "loss": "k_ssim_fused",
              "bin_sort": ("bin_sort (depth sort, counting binning)" if counting else
                           "bin_sort (depth sort, key write, tile sort)")}.get(dominant, dominant)
     sr = stages_roof[dominant]
     tr = NCU_TRAFFIC.get(kname)
     src = {"k_render_bwd": "render_bwd.cu", "k_render_bwd_pk": "render_bwd.cu",
-           "k_render_fwd": "render_fwd.cu"}.get(kname)
+           "k_render_fwd": "render_fwd.cu", "k_render_fwd_pk": "render_fwd.cu"}.get(kname)
     traffic = (tr["bytes_per_launch"] if tr and src and tr.get("src_sha") == src_sha(src)
                and tr.get("tuning") == trainer_tuning_key else None)
     if sr["bound"] == "alu":
@@ -609,6 +609,7 @@ def run_ours(args, rank, world):
                        "bucket": trainer.slot_for([cams[0]]).plan.tuning["bucket"],
                        "bwd_warps": trainer.slot_for([cams[0]]).plan.tuning["bwd_warps"],
                        "bwd_chains": trainer.slot_for([cams[0]]).plan.tuning["bwd_chains"],
+                       "fwd_pixels": trainer.slot_for([cams[0]]).plan.tuning["fwd_pixels"],
                        "autotune_ms_per_step": trainer.autotune_table},
             "clocks": clocks, "e2e": e2e,
             "gpu_launches": kernels_per_step(trainer, [(args.width, args.height)]) * args.steps,
@@ -674,7 +675,7 @@ def run_batched(args, dev, n: int, steps: int, warmup: int = 3) -> dict:
 
     import synth
     from paper_2601_19489_gb300 import api
-    from paper_2601_19489_gb300.autotune import autotune
+    from paper_2601_19489_gb300.autotune import TUNED, autotune
     from paper_2601_19489_gb300.trainer import Trainer
 
     scene = synth.scene_clustered(n, seed=0, sh_degree=3)
@@ -683,7 +684,7 @@ def run_batched(args, dev, n: int, steps: int, warmup: int = 3) -> dict:
     params = api.Gaussians.from_scene(scene, device=dev)
     best, table = autotune(params, batches, targets, lam=args.lam, device=dev)
     tr = Trainer(params, lam=args.lam, load_balanced=best["load_balanced"],
-                 tuning={k: best[k] for k in ("bucket", "bwd_warps", "bwd_chains")}, device=dev)
+                 tuning={k: best[k] for k in TUNED}, device=dev)
     tr.ensure_capacity(batches)
     # eager batched steps (also the warm-up before capture)
     stream = torch.cuda.current_stream()
@@ -712,7 +713,7 @@ def run_batched(args, dev, n: int, steps: int, warmup: int = 3) -> dict:
     # the same views one at a time (single-view plans, eager)
     singles = [[c] for cams in batches for c in cams]
     seq = Trainer(params, lam=args.lam, load_balanced=best["load_balanced"],
-                  tuning={k: best[k] for k in ("bucket", "bwd_warps", "bwd_chains")}, device=dev)
+                  tuning={k: best[k] for k in TUNED}, device=dev)
     seq.ensure_capacity(singles)
     offs = []
     for b, cams in enumerate(batches):

@@ -126,9 +126,10 @@ GS_API gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views, co
  *              independent work per step), 1 (one chain: fewer idle steps
  *              while the pipeline fills and drains), or 0: two when the
  *              bucket has at least 128 live pixels, else one.  Ignored at 64.
- * A zero field takes the default (32, 4, 0).  gs_plan_create uses the
- * defaults (the Python layer's default plan takes 64, 1, 0: the
- * autotuner's pick at 1M Gaussians and 1080p).
+ * A zero field takes the default (32, 4, 0; fwd_pixels 1).  gs_plan_create
+ * uses the defaults (the Python layer's default plan takes bucket 64, two
+ * backward warps, chains 0 and fwd_pixels 2: the autotuner's pick at 1M
+ * Gaussians and 1080p).
  * Returns NULL on the same conditions as gs_plan_create or an unsupported
  * choice. */
 typedef struct {
@@ -153,6 +154,12 @@ typedef struct {
      *            of the counting binning; both give the same per-tile lists.
      *            0 by default. */
     int32_t bin_radix;
+    /* fwd_pixels pixels per thread of the forward blend: 1 (a CTA of 256
+     *            threads per tile), or 2 (128 threads, each blending two
+     *            horizontally adjacent pixels in packed float32 pairs,
+     *            branch-free; the same float32 operations per pixel, so the
+     *            blend decisions are identical).  0 takes 1. */
+    int32_t fwd_pixels;
 } gs_tuning;
 GS_API gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n_views, const int32_t *h_widths,
                                      const int32_t *h_heights, int64_t inst_capacity, const gs_tuning *tuning);
@@ -300,9 +307,12 @@ GS_API int gs_preprocess_bwd_adam(const gs_plan *plan, void *ws, gs_params *para
  * disp_weight * mean |disp - target_disp| (d_disp may be NULL to skip).
  * Writes dL/d(rgb) to d_dL_drgb and, if d_disp is given, dL/d(disp) to
  * d_dL_ddisp (both overwritten), and the scalar loss to d_loss (device, one
- * float).  d_scratch: device float scratch of gs_loss_scratch_floats(plan),
- * 8-byte aligned (GS_ERR_ARG otherwise).
- * lambda = 0 gives plain L1 and skips the SSIM passes. */
+ * float).  d_scratch: device float scratch of gs_loss_scratch_floats(plan)
+ * (per-block partial sums and a completion counter; a few KB, independent of
+ * the pixel count), 8-byte aligned (GS_ERR_ARG otherwise).  Calls sharing
+ * one scratch must not overlap on the GPU.  With lambda > 0 the SSIM
+ * statistics, maps and gradient are one launch (the last block to finish
+ * reduces the loss value); lambda = 0 gives plain L1. */
 GS_API int64_t gs_loss_scratch_floats(const gs_plan *plan);
 GS_API int gs_loss(const gs_plan *plan, const float *d_rgb, const float *d_target, float lambda,
                    const float *d_disp, const float *d_target_disp, float disp_weight, float *d_dL_drgb,

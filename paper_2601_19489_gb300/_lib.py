@@ -59,7 +59,8 @@ class GsParams(ctypes.Structure):
 
 class GsTuning(ctypes.Structure):
     _fields_ = [("bucket", ctypes.c_int32), ("bwd_warps", ctypes.c_int32), ("bwd_chains", ctypes.c_int32),
-                ("bbox_3sigma", ctypes.c_int32), ("bwd_per_pixel", ctypes.c_int32), ("bin_radix", ctypes.c_int32)]
+                ("bbox_3sigma", ctypes.c_int32), ("bwd_per_pixel", ctypes.c_int32), ("bin_radix", ctypes.c_int32),
+                ("fwd_pixels", ctypes.c_int32)]
 
 
 class GsAdamHparams(ctypes.Structure):

@@ -94,18 +94,19 @@ class Plan:
                  tuning: dict | None = None):
         """tuning: optional {"bucket": 32 | 64, "bwd_warps": 1 | 2 | 4 | 8,
         "bwd_chains": 0 | 1 | 2, "bbox_3sigma": 0 | 1, "bwd_per_pixel": 0 | 1,
-        "bin_radix": 0 | 1} (bbox_3sigma and bwd_per_pixel are the Tab. 1
-        ablation switches; bin_radix takes the key-write + radix-sort binning
-        instead of the counting binning, same lists)."""
+        "bin_radix": 0 | 1, "fwd_pixels": 1 | 2} (bbox_3sigma and
+        bwd_per_pixel are the Tab. 1 ablation switches; bin_radix takes the
+        key-write + radix-sort binning instead of the counting binning, same
+        lists; fwd_pixels 2 blends two pixels per thread in packed pairs)."""
         lib = L.lib()
         self.sizes = [(int(w), int(h)) for (w, h) in sizes]
         V = len(self.sizes)
         ws_ = (ctypes.c_int32 * V)(*[w for w, _ in self.sizes])
         hs_ = (ctypes.c_int32 * V)(*[h for _, h in self.sizes])
-        self.tuning = {"bucket": 64, "bwd_warps": 1, "bwd_chains": 0, "bbox_3sigma": 0, "bwd_per_pixel": 0,
-                       "bin_radix": 0, **(tuning or {})}
+        self.tuning = {"bucket": 64, "bwd_warps": 2, "bwd_chains": 0, "bbox_3sigma": 0, "bwd_per_pixel": 0,
+                       "bin_radix": 0, "fwd_pixels": 2, **(tuning or {})}
         tu = L.GsTuning(*(int(self.tuning[k]) for k in ("bucket", "bwd_warps", "bwd_chains", "bbox_3sigma",
-                                                        "bwd_per_pixel", "bin_radix")))
+                                                        "bwd_per_pixel", "bin_radix", "fwd_pixels")))
         self.handle = lib.gs_plan_create_tuned(int(n), int(sh_degree), V, ws_, hs_, int(inst_capacity),
                                                ctypes.byref(tu))
         if not self.handle:

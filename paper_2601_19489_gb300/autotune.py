@@ -8,14 +8,17 @@ The choices change speed, not results (beyond float32 summation order):
                  the backward with two splats per lane in packed pairs);
   bwd_warps      warps per CTA of the per-Gaussian backward;
   bwd_chains     pixel chains per lane of the 32-splat backward pipeline (1,
-                 2, or 0: chosen per bucket by its live pixel count).
+                 2, or 0: chosen per bucket by its live pixel count);
+  fwd_pixels     pixels per thread of the forward blend (1, or 2 in packed
+                 float32 pairs).
 Tile size stays at the paper's 16 x 16 (Sec. 2.2).
 
 ``autotune`` times a few real training steps of candidates on the caller's
 own views and targets, using a scratch copy of the parameters so that
 tuning does not train the model, and returns the fastest.  The binning
 mode is settled first (at the default backward shape); the backward shapes
-are then searched with the faster binning.
+are then searched with the faster binning, and last the forward's pixels per
+thread with the best of them.
 """
 from __future__ import annotations
 
@@ -37,9 +40,29 @@ SHAPES = (tuple({"bucket": 32, "bwd_warps": w, "bwd_chains": c}
           + tuple({"bucket": 64, "bwd_warps": w, "bwd_chains": 0} for w in (1, 2, 4)))
 
 
+TUNED = ("bucket", "bwd_warps", "bwd_chains", "fwd_pixels")
+
+
+def tuning_key(load_balanced: bool, t: dict) -> str:
+    """'LB/b64/w1/c0', with '/f2' appended for the two-pixel forward."""
+    return (f"{'LB' if load_balanced else 'Sq'}/b{t['bucket']}/w{t['bwd_warps']}/c{t['bwd_chains']}"
+            + ("/f2" if t.get("fwd_pixels", 1) == 2 else ""))
+
+
+def parse_tuning_key(key: str) -> tuple[bool, dict]:
+    """Inverse of tuning_key: (load_balanced, tuning dict)."""
+    parts = key.split("/")
+    t = {"bucket": int(parts[1][1:]), "bwd_warps": int(parts[2][1:]), "bwd_chains": 0, "fwd_pixels": 1}
+    for p in parts[3:]:
+        if p.startswith("c"):
+            t["bwd_chains"] = int(p[1:])
+        elif p.startswith("f"):
+            t["fwd_pixels"] = int(p[1:])
+    return parts[0] == "LB", t
+
+
 def _key(c: dict) -> str:
-    return (f"{'LB' if c['load_balanced'] else 'Sq'}/b{c['bucket']}/w{c['bwd_warps']}/"
-            f"c{c['bwd_chains']}")
+    return tuning_key(c["load_balanced"], c)
 
 
 def _clone(params: Gaussians) -> Gaussians:
@@ -48,7 +71,7 @@ def _clone(params: Gaussians) -> Gaussians:
 
 def _time(scratch, cand, batches, targets, lam, trials, inst_capacity, device) -> float:
     tr = Trainer(scratch, lam=lam, load_balanced=cand["load_balanced"], inst_capacity=inst_capacity,
-                 tuning={k: cand[k] for k in ("bucket", "bwd_warps", "bwd_chains")}, device=device)
+                 tuning={k: cand.get(k, 1 if k == "fwd_pixels" else 0) for k in TUNED}, device=device)
     tr.ensure_capacity(batches)
     for b, t in zip(batches, targets):  # warm-up: every launch shape once
         tr.step(b, t)
@@ -82,6 +105,11 @@ def autotune(params: Gaussians, batches, targets, *, lam: float = 0.2, trials: i
             table[k] = _time(scratch, cand, batches, targets, lam, trials, inst_capacity, device)
         if table[k] < best_ms:
             best, best_ms = dict(cand), table[k]
+    best["fwd_pixels"] = 1
+    cand = {**best, "fwd_pixels": 2}
+    table[_key(cand)] = _time(scratch, cand, batches, targets, lam, trials, inst_capacity, device)
+    if table[_key(cand)] < best_ms:
+        best = cand
     del scratch
     torch.cuda.empty_cache()
     return best, table

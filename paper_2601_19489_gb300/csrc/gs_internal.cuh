@@ -68,7 +68,8 @@ struct StatusDev {
     uint32_t n_coarse;     // (Gaussian, tile block) entries of the counting binning
     uint32_t n_chunks;     // their chunks
     uint32_t done_offsets;  // k_fine_offsets: CTAs finished (cleared by gs_bin_sort)
-    uint32_t pad[56];
+    uint32_t bwd_next_tile;  // per-Gaussian backward: next unclaimed tile (cleared per launch)
+    uint32_t pad[55];
 };
 
 }  // namespace gs
@@ -94,6 +95,7 @@ struct gs_plan {
     int32_t bbox_3sigma;           // ablation: classic 3-sigma tile box
     int32_t bwd_per_pixel;         // ablation: classic per-pixel backward
     int32_t bin_radix;             // binning by key write + radix sort of the instances
+    int32_t fwd_pixels;            // pixels per thread of the forward blend (1, or 2 packed)
     int32_t blocks_x[GS_MAX_VIEWS], block_off[GS_MAX_VIEWS + 1];
     int32_t total_blocks, block_bits;
     int64_t coarse_cap, chunk_cap;
@@ -271,6 +273,14 @@ __device__ __forceinline__ void column_span(int tx, float img_w, float *xa, floa
 __device__ __forceinline__ float fast_exp2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 1/x with the hardware approximation (PTX rcp.approx.ftz.f32: within one
+// ulp of the rounded reciprocal for normal x).
+__device__ __forceinline__ float fast_rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 

@@ -6,27 +6,60 @@
 // channels and pixels.  With mu_x = w*x, E_xx = w*(x^2), E_xy = w*(x y) the
 // per-pixel SSIM is S(mu_x, E_xx, E_xy); its gradient w.r.t. x is
 //   dS/dx(q) = sum_p w(p - q) [dS/dmu_x(p) + 2 x(q) dS/dE_xx(p) + y(q) dS/dE_xy(p)],
-// i.e. the same symmetric window applied to three per-pixel maps.  Pass 1
-// computes S and the three maps (separable blur of x, y, x^2, y^2, x y in a
-// 42x42 shared-memory tile), pass 2 blurs the maps and forms dL/dx.  The
-// quantities that share a window weight are summed in packed float32 pairs
-// ((mu_x, mu_y), (E_xx, E_yy), (dS/dmu_x, dS/dE_xx)): one f32x2 FMA per tap
-// for two of them.  The partial sums of the blocks are reduced in a fixed
-// order by the first block of pass 2, after its own tile.
+// i.e. the same symmetric window applied to three per-pixel maps.
+//
+// One launch does both (k_ssim_fused).  A CTA owns a strip of 32 output
+// columns and 120 output rows of one plane and walks down it in chunks of 16
+// rows.  Per chunk it loads 16 new input rows, blurs them horizontally (five
+// sums per column, over the 42 statistic columns the strip needs), blurs the
+// horizontal sums vertically into the statistics of 16 map rows five rows
+// behind, forms S and the three maps there, blurs the maps horizontally, and
+// blurs those sums vertically into the gradient of 16 output rows ten rows
+// behind the input.  The horizontal sums of both blurs live in 32-row rings
+// in shared memory, so the rows the window shares with the next chunk are
+// kept, not recomputed: only the strip's 10 halo columns and the first
+// chunk's 20 halo rows are computed twice.  Nothing but the gradient goes to
+// HBM.  Quantities that share a window weight are summed in packed float32
+// pairs ((x, y), (x^2, y^2), (dS/dmu_x, dS/dE_xx)): one f32x2 FMA per tap
+// for two of them.  Each block writes its partial sums; the last block to
+// finish (atomic counter) reduces them in a fixed order.
 #include <math.h>
 
 #include "gs_internal.cuh"
 
 namespace gs {
 
-constexpr int kSsimT = 32;              // output tile edge
-constexpr int kHalo = 5;                // window radius
-constexpr int kSsimIn = kSsimT + 2 * kHalo;  // 42
-// 11 warps: the horizontal pass (42 rows x 8 groups of 4 outputs = 336
-// items) and the vertical pass (256 items) each take one round
-constexpr int kSsimThreads = 352;
+constexpr int kSsimT = 32;                    // output columns of a strip
+constexpr int kHalo = 5;                      // window radius
+constexpr int kSegH = 120;                    // output rows of a CTA
+constexpr int kR = 16;                        // rows per chunk
+constexpr int kRing = 32;                     // rows of the horizontal-sum rings
+constexpr int kStatW = kSsimT + 2 * kHalo;    // 42 statistic / map columns
+constexpr int kHGroups = (kStatW + 3) / 4;    // 11 groups of 4 horizontal outputs (44 columns)
+constexpr int kInW = 4 * kHGroups + 2 * kHalo;  // 54 input columns
+constexpr int kSsimThreads = 256;
+// row strides in elements: odd, so that 16 consecutive rows of one column
+// fall in 16 different banks
+constexpr int kInS = 55, kHS = 45, kMpS = 43, kBhS = 33;
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
+
+struct SsimSmem {
+    union {
+        float2 in[kR][kInS];  // this chunk's input rows (x, y)
+        struct {
+            float2 ab[kR][kMpS];  // this chunk's maps (dS/dmu_x, dS/dE_xx)
+            float c[kR][kMpS];    // dS/dE_xy
+        } mp;
+    } u;
+    float2 h01[kRing][kHS];    // horizontal sums of (x, y)
+    float2 h23[kRing][kHS];    // of (x^2, y^2)
+    float h4[kRing][kHS];      // of x y
+    float2 bh01[kRing][kBhS];  // horizontal sums of the maps (dS/dmu_x, dS/dE_xx)
+    float bh4[kRing][kBhS];    // of dS/dE_xy
+    float red[2][kSsimThreads / 32];
+    int last;
+};
 
 struct Window {
     float w[11];
@@ -46,165 +79,19 @@ __device__ __forceinline__ bool plane_geom(const Planes &pl, int z, int *W, int 
     *W = pl.W[v];
     *H = pl.H[v];
     *base = 3 * pl.off[v] + (int64_t)c * pl.W[v] * pl.H[v];
-    return (int)blockIdx.x * kSsimT < *W && (int)blockIdx.y * kSsimT < *H;
+    return (int)blockIdx.x * kSsimT < *W && (int)blockIdx.y * kSegH < *H;
 }
 
-__device__ __forceinline__ f2x ld2(const float2 &v) { return pk2(v.x, v.y); }
+__device__ __forceinline__ f2x ld2(const float2 &v) { return *reinterpret_cast<const f2x *>(&v); }
 __device__ __forceinline__ float2 st2(f2x v) {
     float2 r;
     upk2(v, r.x, r.y);
     return r;
 }
 
-// Window sums of five quantities per pixel, in packed pairs where the
-// quantities share the window weight: (mu_x, mu_y), (E_xx, E_yy) packed and
-// E_xy alone.  Maps written for the backward: (dS/dmu_x, dS/dE_xx) packed
-// and dS/dE_xy.
-__global__ void __launch_bounds__(kSsimThreads)
-k_ssim_fwd(Planes pl, Window win, const float *__restrict__ x, const float *__restrict__ y,
-           float2 *__restrict__ maps_ab, float *__restrict__ maps_c, float *__restrict__ part_s,
-           float *__restrict__ part_l1) {
-    __shared__ float2 XY[kSsimIn][kSsimIn + 1];
-    __shared__ float2 H2[2][kSsimIn][kSsimT + 1];  // horizontal sums: (mu_x, mu_y), (E_xx, E_yy)
-    __shared__ float H1[kSsimIn][kSsimT + 1];      // horizontal sums: E_xy
-    __shared__ float red[2][kSsimThreads / 32];
-    int W, H;
-    int64_t base;
-    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    const int tid = threadIdx.x;
-    if (!plane_geom(pl, blockIdx.z, &W, &H, &base)) {
-        if (tid == 0) {
-            part_s[blk] = 0.f;
-            part_l1[blk] = 0.f;
-        }
-        return;
-    }
-    f2x w2[11];
-#pragma unroll
-    for (int u = 0; u < 11; ++u) w2[u] = pk2(win.w[u], win.w[u]);
-    const int ox = blockIdx.x * kSsimT - kHalo, oy = blockIdx.y * kSsimT - kHalo;
-    for (int i = tid; i < kSsimIn * kSsimIn; i += kSsimThreads) {
-        const int r = i / kSsimIn, c = i - r * kSsimIn;
-        const int gx = ox + c, gy = oy + r;
-        float a = 0.f, b = 0.f;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-            a = x[base + (int64_t)gy * W + gx];
-            b = y[base + (int64_t)gy * W + gx];
-        }
-        XY[r][c] = make_float2(a, b);
-    }
-    __syncthreads();
-    // horizontal pass: a thread sums 4 adjacent outputs of a row from 14
-    // inputs (register blocking: each input and its products are read once
-    // for 4 outputs)
-    for (int i = tid; i < kSsimIn * (kSsimT / 4); i += kSsimThreads) {
-        const int r = i / (kSsimT / 4), c0 = 4 * (i - r * (kSsimT / 4));
-        f2x s01[4], s23[4];
-        float s4[4];
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            s01[o] = pk2(0.f, 0.f);
-            s23[o] = pk2(0.f, 0.f);
-            s4[o] = 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < 14; ++k) {
-            const float2 v = XY[r][c0 + k];
-            const f2x xy = ld2(v), sq = mul2(xy, xy);
-            const float p = v.x * v.y;
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                const int u = k - o;  // tap of output c0 + o
-                if (u >= 0 && u < 11) {
-                    s01[o] = fma2(w2[u], xy, s01[o]);
-                    s23[o] = fma2(w2[u], sq, s23[o]);
-                    s4[o] = fmaf(win.w[u], p, s4[o]);
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            H2[0][r][c0 + o] = st2(s01[o]);
-            H2[1][r][c0 + o] = st2(s23[o]);
-            H1[r][c0 + o] = s4[o];
-        }
-    }
-    __syncthreads();
-    float acc_s = 0.f, acc_l1 = 0.f;
-    // vertical pass: a thread sums 4 outputs of a column from 14 rows
-    for (int i = tid; i < (kSsimT / 4) * kSsimT; i += kSsimThreads) {
-        const int r0 = 4 * (i / kSsimT), c = i - (i / kSsimT) * kSsimT;
-        f2x s01[4], s23[4];
-        float s4[4];
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            s01[o] = pk2(0.f, 0.f);
-            s23[o] = pk2(0.f, 0.f);
-            s4[o] = 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < 14; ++k) {
-            const f2x a = ld2(H2[0][r0 + k][c]), b = ld2(H2[1][r0 + k][c]);
-            const float e = H1[r0 + k][c];
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                const int u = k - o;
-                if (u >= 0 && u < 11) {
-                    s01[o] = fma2(w2[u], a, s01[o]);
-                    s23[o] = fma2(w2[u], b, s23[o]);
-                    s4[o] = fmaf(win.w[u], e, s4[o]);
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            const int r = r0 + o;
-            const int gx = blockIdx.x * kSsimT + c, gy = blockIdx.y * kSsimT + r;
-            if (gx >= W || gy >= H) continue;
-            float mx, my, exx, eyy;
-            upk2(s01[o], mx, my);
-            upk2(s23[o], exx, eyy);
-            const float exy = s4[o];
-            const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
-            const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
-            const float inv = 1.0f / (B1 * B2);
-            const float S = A1 * A2 * inv;
-            // partials w.r.t. mu_x, E_xx, E_xy (sxx = E_xx - mu_x^2, sxy = E_xy - mu_x mu_y)
-            const float d_mu = 2.f * my * (A2 - A1) * inv - 2.f * mx * S * (1.0f / B1 - 1.0f / B2);
-            const float d_exx = -S / B2;
-            const float d_exy = 2.f * A1 * inv;
-            const int64_t p = base + (int64_t)gy * W + gx;
-            maps_ab[p] = make_float2(d_mu, d_exx);
-            maps_c[p] = d_exy;
-            acc_s += S;
-            const float2 v = XY[r + kHalo][c + kHalo];
-            acc_l1 += fabsf(v.x - v.y);
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        acc_s += __shfl_xor_sync(0xffffffffu, acc_s, o);
-        acc_l1 += __shfl_xor_sync(0xffffffffu, acc_l1, o);
-    }
-    if ((tid & 31) == 0) {
-        red[0][tid >> 5] = acc_s;
-        red[1][tid >> 5] = acc_l1;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        float a = 0.f, b = 0.f;
-        for (int w = 0; w < kSsimThreads / 32; ++w) {
-            a += red[0][w];
-            b += red[1][w];
-        }
-        part_s[blk] = a;
-        part_l1[blk] = b;
-    }
-}
-
 // The loss value: fixed-order reduction of the per-block partial sums in
-// double by one block of threads (part_* fully written before the launch).
+// double by one block of threads (part_* written by earlier launches, or by
+// every other block of this launch before it counted itself done).
 struct LossSums {
     const float *part_s, *part_l1, *part_d;
     int n_s, n_l1, n_d;
@@ -216,9 +103,9 @@ template <int kThreads>
 __device__ __forceinline__ void reduce_loss(const LossSums &L) {
     __shared__ double red[3][kThreads / 32];
     double a = 0.0, b = 0.0, c = 0.0;
-    for (int i = threadIdx.x; i < L.n_s; i += kThreads) a += L.part_s[i];
-    for (int i = threadIdx.x; i < L.n_l1; i += kThreads) b += L.part_l1[i];
-    for (int i = threadIdx.x; i < L.n_d; i += kThreads) c += L.part_d[i];
+    for (int i = threadIdx.x; i < L.n_s; i += kThreads) a += __ldcg(L.part_s + i);
+    for (int i = threadIdx.x; i < L.n_l1; i += kThreads) b += __ldcg(L.part_l1 + i);
+    for (int i = threadIdx.x; i < L.n_d; i += kThreads) c += __ldcg(L.part_d + i);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -242,110 +129,278 @@ __device__ __forceinline__ void reduce_loss(const LossSums &L) {
     }
 }
 
-// Gradient: the window sums of the three maps ((dS/dmu_x, dS/dE_xx) packed,
-// dS/dE_xy alone) around each pixel.  Block (0, 0, 0) also reduces the loss
-// value after its tile (the forward's partial sums and the disparity's are
-// complete before this launch).
-__global__ void __launch_bounds__(kSsimThreads)
-k_ssim_bwd(Planes pl, Window win, const float *__restrict__ x, const float *__restrict__ y,
-           const float2 *__restrict__ maps_ab, const float *__restrict__ maps_c, float c_l1, float c_ssim,
-           float *__restrict__ grad, LossSums sums) {
-    __shared__ float2 M2[kSsimIn][kSsimIn + 1];
-    __shared__ float M1[kSsimIn][kSsimIn + 1];
-    __shared__ float2 H2[kSsimIn][kSsimT + 1];
-    __shared__ float H1[kSsimIn][kSsimT + 1];
+// The whole SSIM pass of one (plane, strip, segment): statistics, maps,
+// gradient and the block's partial sums (see the file's header).  Row
+// bookkeeping for chunk k with a = y0 - 10 + 16 k: input rows [a, a + 16)
+// are loaded and blurred horizontally; map rows [a - 5, a + 11) get their
+// statistics (their windows need horizontal sums of rows [a - 10, a + 16));
+// output rows [a - 10, a + 6) get their gradient (their windows need the
+// maps' horizontal sums of rows [a - 15, a + 11)).
+__global__ void __launch_bounds__(kSsimThreads, 4)
+k_ssim_fused(Planes pl, Window win, const float *__restrict__ x, const float *__restrict__ y, float c_l1,
+             float c_ssim, float *__restrict__ grad, float *__restrict__ part_s, float *__restrict__ part_l1,
+             unsigned int *__restrict__ done_ctr, LossSums sums) {
+    extern __shared__ __align__(16) unsigned char ssim_smem[];
+    SsimSmem &sm = *reinterpret_cast<SsimSmem *>(ssim_smem);
+    const int tid = threadIdx.x;
+    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
     int W, H;
     int64_t base;
-    const bool first = blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+    float acc_s = 0.f, acc_l1 = 0.f;
     if (plane_geom(pl, blockIdx.z, &W, &H, &base)) {
-        const int tid = threadIdx.x;
+        const float *__restrict__ xp = x + base;
+        const float *__restrict__ yp = y + base;
+        float *__restrict__ gp = grad + base;
+        const int c0 = blockIdx.x * kSsimT, y0 = blockIdx.y * kSegH;
+        const int y1 = min(y0 + kSegH, H);
+        const int nchunks = (y1 - y0 + 4 + kR - 1) / kR + 1;
         f2x w2[11];
 #pragma unroll
         for (int u = 0; u < 11; ++u) w2[u] = pk2(win.w[u], win.w[u]);
-        const int ox = blockIdx.x * kSsimT - kHalo, oy = blockIdx.y * kSsimT - kHalo;
-        for (int i = tid; i < kSsimIn * kSsimIn; i += kSsimThreads) {
-            const int r = i / kSsimIn, c = i - r * kSsimIn;
-            const int gx = ox + c, gy = oy + r;
-            float2 ab = make_float2(0.f, 0.f);
-            float d = 0.f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                const int64_t p = base + (int64_t)gy * W + gx;
-                ab = maps_ab[p];
-                d = maps_c[p];
-            }
-            M2[r][c] = ab;
-            M1[r][c] = d;
-        }
-        __syncthreads();
-        // the same two register-blocked passes as the forward, over the maps
-        for (int i = tid; i < kSsimIn * (kSsimT / 4); i += kSsimThreads) {
-            const int r = i / (kSsimT / 4), c0 = 4 * (i - r * (kSsimT / 4));
-            f2x s2[4];
-            float s1[4];
+        // ring row of an image row (rows from y0 - 20 on)
+        auto ring = [y0](int row) { return (row - y0 + 64) & (kRing - 1); };
+        // this thread's place in each phase
+        const int hr = tid & 15, hg = tid >> 4;              // horizontal passes: row, group of 4 columns
+        const int vq = tid / kStatW, vc = tid - vq * kStatW;  // statistics pass: row group, column
+        const int gq = tid >> 5, gc = tid & 31;               // gradient pass: row group, column
+        for (int k = 0; k < nchunks; ++k) {
+            const int a = y0 - 2 * kHalo + kR * k;
+            // (1) x, y of this thread's gradient pixels, fetched early
+            float gx_[4], gy_[4];
+            const int go0 = a - 2 * kHalo + 4 * gq;
+            const bool gcol = c0 + gc < W;
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
-                s2[o] = pk2(0.f, 0.f);
-                s1[o] = 0.f;
+                gx_[o] = 0.f;
+                gy_[o] = 0.f;
+                const int row = go0 + o;
+                if (k > 0 && tid < 4 * kSsimT && gcol && row >= y0 && row < y1) {
+                    const int64_t p = (int64_t)row * W + c0 + gc;
+                    gx_[o] = __ldg(xp + p);
+                    gy_[o] = __ldg(yp + p);
+                }
             }
+            // (2) input rows [a, a + 16), columns [c0 - 10, c0 + 44): warp w
+            // takes rows 2w and 2w + 1, lanes the columns
+            {
+                const int lane = tid & 31, w = tid >> 5;
 #pragma unroll
-            for (int k = 0; k < 14; ++k) {
-                const f2x v = ld2(M2[r][c0 + k]);
-                const float e = M1[r][c0 + k];
+                for (int rr = 0; rr < 2; ++rr) {
+                    const int r = 2 * w + rr, gyy = a + r;
+                    const bool rowin = gyy >= 0 && gyy < H;
+                    const int64_t rb = (int64_t)gyy * W;
 #pragma unroll
-                for (int o = 0; o < 4; ++o) {
-                    const int u = k - o;
-                    if (u >= 0 && u < 11) {
-                        s2[o] = fma2(w2[u], v, s2[o]);
-                        s1[o] = fmaf(win.w[u], e, s1[o]);
+                    for (int cc = lane; cc < kInW; cc += 32) {
+                        const int gxx = c0 - 2 * kHalo + cc;
+                        float2 v = make_float2(0.f, 0.f);
+                        if (rowin && gxx >= 0 && gxx < W) v = make_float2(__ldg(xp + rb + gxx), __ldg(yp + rb + gxx));
+                        sm.u.in[r][cc] = v;
                     }
                 }
             }
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                H2[r][c0 + o] = st2(s2[o]);
-                H1[r][c0 + o] = s1[o];
-            }
-        }
-        __syncthreads();
-        for (int i = tid; i < (kSsimT / 4) * kSsimT; i += kSsimThreads) {
-            const int r0 = 4 * (i / kSsimT), c = i - (i / kSsimT) * kSsimT;
-            f2x s2[4];
-            float s1[4];
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                s2[o] = pk2(0.f, 0.f);
-                s1[o] = 0.f;
-            }
-#pragma unroll
-            for (int k = 0; k < 14; ++k) {
-                const f2x v = ld2(H2[r0 + k][c]);
-                const float e = H1[r0 + k][c];
+            __syncthreads();
+            // (3) horizontal sums of input row a + hr at statistic columns
+            // 4 hg .. 4 hg + 3 (column j is image column c0 - 5 + j), from
+            // input columns 4 hg .. 4 hg + 13: each input read once for 4 outputs
+            if (tid < kR * kHGroups) {
+                f2x s01[4], s23[4];
+                float s4[4];
 #pragma unroll
                 for (int o = 0; o < 4; ++o) {
-                    const int u = k - o;
-                    if (u >= 0 && u < 11) {
-                        s2[o] = fma2(w2[u], v, s2[o]);
-                        s1[o] = fmaf(win.w[u], e, s1[o]);
+                    s01[o] = pk2(0.f, 0.f);
+                    s23[o] = pk2(0.f, 0.f);
+                    s4[o] = 0.f;
+                }
+#pragma unroll
+                for (int kk = 0; kk < 14; ++kk) {
+                    const f2x xy = ld2(sm.u.in[hr][4 * hg + kk]);
+                    float xv, yv;
+                    upk2(xy, xv, yv);
+                    const f2x sq = mul2(xy, xy);
+                    const float p = xv * yv;
+#pragma unroll
+                    for (int o = 0; o < 4; ++o) {
+                        const int u = kk - o;
+                        if (u >= 0 && u < 11) {
+                            s01[o] = fma2(w2[u], xy, s01[o]);
+                            s23[o] = fma2(w2[u], sq, s23[o]);
+                            s4[o] = fmaf(win.w[u], p, s4[o]);
+                        }
+                    }
+                }
+                const int rr = ring(a + hr);
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    sm.h01[rr][4 * hg + o] = st2(s01[o]);
+                    sm.h23[rr][4 * hg + o] = st2(s23[o]);
+                    sm.h4[rr][4 * hg + o] = s4[o];
+                }
+            }
+            __syncthreads();
+            // (4) statistics and maps of map rows m0 .. m0 + 3 at column vc
+            // (vertical sums over horizontal-sum rows m0 - 5 .. m0 + 8); rows
+            // outside the image, or before y0 - 5 (not needed, their rows of
+            // horizontal sums were not computed), get zero maps
+            if (tid < 4 * kStatW) {
+                const int m0 = a - kHalo + 4 * vq;
+                const int gxs = c0 - kHalo + vc;
+                f2x s01[4], s23[4];
+                float s4[4];
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    s01[o] = pk2(0.f, 0.f);
+                    s23[o] = pk2(0.f, 0.f);
+                    s4[o] = 0.f;
+                }
+                if (m0 + 3 >= y0 - kHalo) {
+#pragma unroll
+                    for (int kk = 0; kk < 14; ++kk) {
+                        const int rr = ring(m0 - kHalo + kk);
+                        const f2x h01 = ld2(sm.h01[rr][vc]), h23 = ld2(sm.h23[rr][vc]);
+                        const float h4 = sm.h4[rr][vc];
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) {
+                            const int u = kk - o;
+                            if (u >= 0 && u < 11) {
+                                s01[o] = fma2(w2[u], h01, s01[o]);
+                                s23[o] = fma2(w2[u], h23, s23[o]);
+                                s4[o] = fmaf(win.w[u], h4, s4[o]);
+                            }
+                        }
+                    }
+                }
+                const bool colin = gxs >= 0 && gxs < W;
+                const bool counted = vc >= kHalo && vc < kHalo + kSsimT && colin;
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const int m = m0 + o;
+                    float d_mu = 0.f, d_exx = 0.f, d_exy = 0.f;
+                    if (colin && m >= 0 && m < H && m >= y0 - kHalo) {
+                        float mx, my, exx, eyy;
+                        upk2(s01[o], mx, my);
+                        upk2(s23[o], exx, eyy);
+                        const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = s4[o] - mx * my;
+                        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
+                        const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
+                        const float rB1 = fast_rcp(B1), rB2 = fast_rcp(B2);
+                        const float inv = rB1 * rB2;
+                        const float S = A1 * A2 * inv;
+                        // partials w.r.t. mu_x, E_xx, E_xy (sxx = E_xx - mu_x^2, sxy = E_xy - mu_x mu_y)
+                        d_mu = 2.f * my * (A2 - A1) * inv - 2.f * mx * S * (rB1 - rB2);
+                        d_exx = -S * rB2;
+                        d_exy = 2.f * A1 * inv;
+                        if (counted && m >= y0 && m < y1) acc_s += S;
+                    }
+                    sm.u.mp.ab[4 * vq + o][vc] = make_float2(d_mu, d_exx);
+                    sm.u.mp.c[4 * vq + o][vc] = d_exy;
+                }
+            }
+            __syncthreads();
+            // (5) horizontal sums of the maps of map row a - 5 + hr at output
+            // columns 4 hg .. 4 hg + 3, from map columns 4 hg .. 4 hg + 13
+            if (tid < kR * (kSsimT / 4)) {
+                f2x s2[4];
+                float s1[4];
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    s2[o] = pk2(0.f, 0.f);
+                    s1[o] = 0.f;
+                }
+#pragma unroll
+                for (int kk = 0; kk < 14; ++kk) {
+                    const f2x v = ld2(sm.u.mp.ab[hr][4 * hg + kk]);
+                    const float e = sm.u.mp.c[hr][4 * hg + kk];
+#pragma unroll
+                    for (int o = 0; o < 4; ++o) {
+                        const int u = kk - o;
+                        if (u >= 0 && u < 11) {
+                            s2[o] = fma2(w2[u], v, s2[o]);
+                            s1[o] = fmaf(win.w[u], e, s1[o]);
+                        }
+                    }
+                }
+                const int rr = ring(a - kHalo + hr);
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    sm.bh01[rr][4 * hg + o] = st2(s2[o]);
+                    sm.bh4[rr][4 * hg + o] = s1[o];
+                }
+            }
+            __syncthreads();
+            // (6) gradient of output rows go0 .. go0 + 3 at column gc
+            // (vertical sums over map rows go0 - 5 .. go0 + 8); the first
+            // chunk has no output rows inside the segment
+            if (k > 0 && tid < 4 * kSsimT) {
+                f2x s2[4];
+                float s1[4];
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    s2[o] = pk2(0.f, 0.f);
+                    s1[o] = 0.f;
+                }
+#pragma unroll
+                for (int kk = 0; kk < 14; ++kk) {
+                    const int rr = ring(go0 - kHalo + kk);
+                    const f2x v = ld2(sm.bh01[rr][gc]);
+                    const float e = sm.bh4[rr][gc];
+#pragma unroll
+                    for (int o = 0; o < 4; ++o) {
+                        const int u = kk - o;
+                        if (u >= 0 && u < 11) {
+                            s2[o] = fma2(w2[u], v, s2[o]);
+                            s1[o] = fmaf(win.w[u], e, s1[o]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const int row = go0 + o;
+                    if (gcol && row >= y0 && row < y1) {
+                        float dmu, dxx;
+                        upk2(s2[o], dmu, dxx);
+                        const float xv = gx_[o], yv = gy_[o];
+                        gp[(int64_t)row * W + c0 + gc] =
+                            c_l1 * sgn(xv - yv) + c_ssim * (dmu + 2.f * xv * dxx + yv * s1[o]);
+                        acc_l1 += fabsf(xv - yv);
                     }
                 }
             }
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                const int gx = blockIdx.x * kSsimT + c, gy = blockIdx.y * kSsimT + r0 + o;
-                if (gx >= W || gy >= H) continue;
-                const int64_t p = base + (int64_t)gy * W + gx;
-                const float xv = x[p], yv = y[p];
-                float dmu, dxx;
-                upk2(s2[o], dmu, dxx);
-                grad[p] = c_l1 * sgn(xv - yv) + c_ssim * (dmu + 2.f * xv * dxx + yv * s1[o]);
-            }
+            // the next chunk's first write (input rows, aliasing the maps)
+            // comes after step 5's barrier; its ring writes come after its
+            // own barriers, when this chunk's reads are done
         }
     }
-    if (first) {
-        __syncthreads();
+    // block partial sums, then the last block to finish reduces them all
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_s += __shfl_xor_sync(0xffffffffu, acc_s, o);
+        acc_l1 += __shfl_xor_sync(0xffffffffu, acc_l1, o);
+    }
+    if ((tid & 31) == 0) {
+        sm.red[0][tid >> 5] = acc_s;
+        sm.red[1][tid >> 5] = acc_l1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float s = 0.f, l = 0.f;
+        for (int w = 0; w < kSsimThreads / 32; ++w) {
+            s += sm.red[0][w];
+            l += sm.red[1][w];
+        }
+        part_s[blk] = s;
+        part_l1[blk] = l;
+        __threadfence();
+        sm.last = atomicAdd(done_ctr, 1u) == (unsigned int)(nblk - 1);
+    }
+    __syncthreads();
+    if (sm.last) {
+        __threadfence();
         reduce_loss<kSsimThreads>(sums);
+        if (tid == 0) *done_ctr = 0u;
     }
 }
+
 
 // Plain L1 (lambda = 0): gradient and per-block partial sums.
 __global__ void __launch_bounds__(256)
@@ -390,7 +445,21 @@ static void ssim_grid(const gs_plan *plan, dim3 *grid) {
         mw = plan->W[v] > mw ? plan->W[v] : mw;
         mh = plan->H[v] > mh ? plan->H[v] : mh;
     }
-    *grid = dim3((mw + kSsimT - 1) / kSsimT, (mh + kSsimT - 1) / kSsimT, 3 * plan->V);
+    *grid = dim3((mw + kSsimT - 1) / kSsimT, (mh + kSegH - 1) / kSegH, 3 * plan->V);
+}
+
+// The fused kernel's shared memory exceeds the 48 KB default: raise the
+// limit once per device.
+static int ssim_smem_setup() {
+    static bool done[64] = {};
+    int dev = 0;
+    int rc = check_cuda(cudaGetDevice(&dev));
+    if (rc) return rc;
+    if (dev >= 0 && dev < 64 && done[dev]) return GS_OK;
+    rc = check_cuda(cudaFuncSetAttribute(k_ssim_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(SsimSmem)));
+    if (rc == GS_OK && dev >= 0 && dev < 64) done[dev] = true;
+    return rc;
 }
 
 static constexpr int kL1Blocks = 4 * 152;
@@ -404,7 +473,7 @@ extern "C" int64_t gs_loss_scratch_floats(const gs_plan *plan) {
     dim3 g;
     ssim_grid(plan, &g);
     const int64_t nblk = (int64_t)g.x * g.y * g.z;
-    return 9 * plan->total_pixels + 2 * nblk + 2 * kL1Blocks + 64;
+    return 2 * nblk + 2 * kL1Blocks + 64;
 }
 
 extern "C" int gs_loss(const gs_plan *plan, const float *rgb, const float *target, float lambda,
@@ -413,19 +482,18 @@ extern "C" int gs_loss(const gs_plan *plan, const float *rgb, const float *targe
     if (!plan || !rgb || !target || !dL_drgb || !loss || !scratch || lambda < 0.f || lambda > 1.f)
         return GS_ERR_ARG;
     if (disp && (!target_disp || !dL_ddisp)) return GS_ERR_ARG;
+    if (((uintptr_t)scratch & 7) != 0) return GS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t P = plan->total_pixels;
     const int64_t n3 = 3 * P;
     dim3 grid;
     ssim_grid(plan, &grid);
     const int nblk = (int)(grid.x * grid.y * grid.z);
-    float2 *maps_ab = reinterpret_cast<float2 *>(scratch);  // 3P pairs
-    float *maps_c = scratch + 6 * P;                         // 3P
-    float *part_s = scratch + 9 * P;
+    float *part_s = scratch;
     float *part_l1 = part_s + nblk;
     float *part_d = part_l1 + nblk;
     float *part_l1b = part_d + kL1Blocks;
-    if (((uintptr_t)scratch & 7) != 0) return GS_ERR_ARG;
+    unsigned int *done_ctr = reinterpret_cast<unsigned int *>(part_l1b + kL1Blocks);
     const double inv3p = 1.0 / (double)n3;
     LossSums sums{part_s, part_l1, part_d, 0, 0, 0, -(double)lambda * inv3p, (1.0 - lambda) * inv3p,
                   (double)disp_weight / (double)P, (double)lambda, loss};
@@ -435,6 +503,8 @@ extern "C" int gs_loss(const gs_plan *plan, const float *rgb, const float *targe
         sums.n_d = kL1Blocks;
     }
     if (lambda > 0.f) {
+        int rc = ssim_smem_setup();
+        if (rc) return rc;
         Planes pl;
         pl.V = plan->V;
         for (int v = 0; v < plan->V; ++v) {
@@ -443,12 +513,13 @@ extern "C" int gs_loss(const gs_plan *plan, const float *rgb, const float *targe
             pl.off[v] = plan->pix_off[v];
         }
         const Window win = make_window();
-        k_ssim_fwd<<<grid, kSsimThreads, 0, s>>>(pl, win, rgb, target, maps_ab, maps_c, part_s, part_l1);
         sums.n_s = nblk;
         sums.n_l1 = nblk;
-        k_ssim_bwd<<<grid, kSsimThreads, 0, s>>>(pl, win, rgb, target, maps_ab, maps_c,
-                                                 (float)((1.0 - lambda) * inv3p), (float)(-lambda * inv3p), dL_drgb,
-                                                 sums);
+        rc = check_cuda(cudaMemsetAsync(done_ctr, 0, sizeof(unsigned int), s));
+        if (rc) return rc;
+        k_ssim_fused<<<grid, kSsimThreads, sizeof(SsimSmem), s>>>(pl, win, rgb, target, (float)((1.0 - lambda) * inv3p),
+                                                                  (float)(-lambda * inv3p), dL_drgb, part_s, part_l1,
+                                                                  done_ctr, sums);
     } else {
         k_l1<<<kL1Blocks, 256, 0, s>>>(rgb, target, n3, (float)inv3p, dL_drgb, part_l1b);
         sums.part_l1 = part_l1b;

@@ -35,7 +35,8 @@ constexpr int kChild = GS_NG_CHILDREN;  // 10
 constexpr int kPer = 14;                // outputs per child
 constexpr int kOut = kChild * kPer;     // 140
 constexpr int kOutPad = 144;            // GEMM 2 N, backward GEMM K (9 x 16)
-constexpr int kThreads = 128;
+constexpr int kFwdThreads = kTileA;    // forward: one thread per anchor
+constexpr int kThreads = 2 * kTileA;  // backward: two threads per anchor
 constexpr int kTmemCols = 256;
 constexpr float kLogitFloor = -30.0f;
 constexpr float kOpacityCeil = 1.0f - 1e-6f;
@@ -247,10 +248,11 @@ __device__ __forceinline__ void anchor_input(const Args &A, int64_t a, bool vali
 
 // Block copy of a prepared operand (already in the canonical layout) into
 // shared memory, 16 bytes per thread and step.
+template <int kStride = kThreads>
 __device__ __forceinline__ void copy16(void *dst, const void *src, int bytes, int tid) {
     const uint4 *s = reinterpret_cast<const uint4 *>(src);
     uint4 *d = reinterpret_cast<uint4 *>(dst);
-    for (int i = tid; i < bytes / 16; i += kThreads) d[i] = s[i];
+    for (int i = tid; i < bytes / 16; i += kStride) d[i] = s[i];
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -278,7 +280,7 @@ struct FwdSmem {
     int fail;
 };
 
-__global__ void __launch_bounds__(kThreads) k_ng_fwd(Args A) {
+__global__ void __launch_bounds__(kFwdThreads) k_ng_fwd(Args A) {
     extern __shared__ uint8_t smem_raw[];
     FwdSmem &S = *reinterpret_cast<FwdSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -298,10 +300,10 @@ __global__ void __launch_bounds__(kThreads) k_ng_fwd(Args A) {
 #pragma unroll
         for (int k = 0; k < kInPad; ++k) S.X[canon(tid, k, kInPad)] = __float2bfloat16_rn(x[k]);
     }
-    copy16(S.W1, A.w1b, kHid * kInPad * 2, tid);
-    copy16(S.W2, A.w2b, kOutPad * kHid * 2, tid);
+    copy16<kFwdThreads>(S.W1, A.w1b, kHid * kInPad * 2, tid);
+    copy16<kFwdThreads>(S.W2, A.w2b, kOutPad * kHid * 2, tid);
     if (tid < kHid) S.b1[tid] = A.b1[tid];
-    for (int i = tid; i < kOutPad; i += kThreads) S.b2[i] = i < kOut ? A.b2[i] : 0.0f;
+    for (int i = tid; i < kOutPad; i += kFwdThreads) S.b2[i] = i < kOut ? A.b2[i] : 0.0f;
     for (int j = 0; j < 3; ++j) S.xyz[tid][j] = valid ? A.xyz[3 * a + j] : 0.0f;
     for (int j = 0; j < 6; ++j) S.ls[tid][j] = valid ? A.ls[6 * a + j] : 0.0f;
     fence_async_smem();
@@ -376,18 +378,18 @@ __global__ void __launch_bounds__(kThreads) k_ng_fwd(Args A) {
         const int na = (int)min((int64_t)kTileA, A.n - a0);
         const int nch = na * kChild;
         const int64_t c0 = a0 * kChild;
-        for (int i = tid; i < nch * 3; i += kThreads) {
+        for (int i = tid; i < nch * 3; i += kFwdThreads) {
             const int ch = i / 3, j = i - 3 * ch, r = ch / kChild, c = ch - r * kChild;
             const float u = S.Y[r][c * kPer + j];
             A.c_means[3 * c0 + i] = S.xyz[r][j] + tanhf(u) * expf(S.ls[r][j]);
             A.c_ls[3 * c0 + i] = S.ls[r][3 + j] + log_sigmoidf(S.Y[r][c * kPer + 7 + j]);
             A.c_sh[3 * c0 + i] = (sigmoidf_(S.Y[r][c * kPer + 4 + j]) - 0.5f) * kDcScale;
         }
-        for (int i = tid; i < nch * 4; i += kThreads) {
+        for (int i = tid; i < nch * 4; i += kFwdThreads) {
             const int ch = i >> 2, j = i & 3, r = ch / kChild, c = ch - r * kChild;
             A.c_quats[4 * c0 + i] = S.Y[r][c * kPer + 10 + j];
         }
-        for (int ch = tid; ch < nch; ch += kThreads) {
+        for (int ch = tid; ch < nch; ch += kFwdThreads) {
             const int r = ch / kChild, c = ch - r * kChild;
             const float o = tanhf(S.Y[r][c * kPer + 3]);
             const float oc = fminf(o, kOpacityCeil);
@@ -420,6 +422,9 @@ cleanup:
 // them as its remaining rows, whose results land in TMEM lanes nobody reads.
 // TMEM columns: y 0..143, then dh 0..31, dx 32..79, dW2 128..159 and
 // 160..191, dW1^T 192..223.
+// Two threads per anchor (warps w and w + 4 read the same TMEM lanes): the
+// per-child work, the operand packing and the TMEM read-backs are split
+// between the two halves of the CTA.
 struct BwdSmem {
     __nv_bfloat16 W2T[kHid * kOutPad];   // dh B (N = 32, K = 144)
     __nv_bfloat16 W1T[kInPad * kHid];    // dx B (N = 48, K = 32)
@@ -442,8 +447,8 @@ struct BwdSmem {
         } p2;
     } u;
     float Y[kTileA][kOutPad + 1];  // y, then dL/dy (fp32)
-    float xyz[kTileA][3], ls[kTileA][6], dls[kTileA][6];
-    float db1w[kThreads / 32][kHid];  // per-warp sums of db1
+    float xyz[kTileA][3], ls[kTileA][6], dls[2][kTileA][6];  // dls: per half of the children
+    float db1w[kTileA / 32][kHid];    // per-warp sums of db1
     float b2[kOutPad];
     uint64_t mbar, gbar;  // MMA completion; children's gradients copied in
     uint32_t tmem;
@@ -457,6 +462,7 @@ constexpr int kStO = kStQ + kTileA * kChild * 4, kStEnd = kStO + kTileA * kChild
 static_assert(offsetof(BwdSmem, DY) + 4 * kStEnd <= offsetof(BwdSmem, XT), "children's gradients fit the staging");
 static_assert(offsetof(BwdSmem, DYT2) + 2 * kTileA * kTileA <= sizeof(BwdSmem), "dW2 tail operand rows");
 static_assert(offsetof(BwdSmem, XT) + 2 * kTileA * kTileA <= sizeof(BwdSmem), "dW1 operand rows");
+static_assert(sizeof(BwdSmem) + 1024 <= 227 * 1024, "one backward CTA fits the shared memory of an SM");
 
 __device__ __forceinline__ float bf16f(__nv_bfloat16 v) { return __bfloat162float(v); }
 
@@ -464,8 +470,11 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     extern __shared__ uint8_t smem_raw[];
     BwdSmem &S = *reinterpret_cast<BwdSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // anchor row of the tile (= TMEM lane) and which half of its work this
+    // thread does; warps w and w + 4 share TMEM lanes 32 (w mod 4) ..
+    const int r = tid & (kTileA - 1), half = tid >> 7;
     const int64_t a0 = (int64_t)blockIdx.x * kTileA;
-    const int64_t a = a0 + tid;
+    const int64_t a = a0 + r;
     const bool valid = a < A.n;
     const int na = (int)min((int64_t)kTileA, A.n - a0);
     float *part = A.partial + (size_t)blockIdx.x * kPartial;
@@ -501,7 +510,7 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
         for (int i = tid; i < nch * 4; i += kThreads) stg[kStQ + i] = A.g_quats[4 * c0 + i];
         for (int i = tid; i < nch; i += kThreads) stg[kStO + i] = A.g_logits[c0 + i];
     }
-    {
+    if (half == 0) {
         // h of this anchor into the y GEMM's A (row = anchor) and the dW2
         // GEMM's B (row = hidden unit, K = anchors)
         const uint4 *src = reinterpret_cast<const uint4 *>(A.h_store + a * kHid);
@@ -512,29 +521,30 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int c = 8 * q + 2 * e;
-                *reinterpret_cast<uint32_t *>(&S.u.p1.H[canon(tid, c, kHid)]) = u[e];
-                S.HT[canon(c, tid, kTileA)] = __ushort_as_bfloat16((unsigned short)(u[e] & 0xffffu));
-                S.HT[canon(c + 1, tid, kTileA)] = __ushort_as_bfloat16((unsigned short)(u[e] >> 16));
+                *reinterpret_cast<uint32_t *>(&S.u.p1.H[canon(r, c, kHid)]) = u[e];
+                S.HT[canon(c, r, kTileA)] = __ushort_as_bfloat16((unsigned short)(u[e] & 0xffffu));
+                S.HT[canon(c + 1, r, kTileA)] = __ushort_as_bfloat16((unsigned short)(u[e] >> 16));
             }
         }
+        for (int j = 0; j < 3; ++j) S.xyz[r][j] = valid ? A.xyz[3 * a + j] : 0.0f;
+        for (int j = 0; j < 6; ++j) S.ls[r][j] = valid ? A.ls[6 * a + j] : 0.0f;
+    } else {
         // x of this anchor as the dW1^T GEMM's A (row = input, K = anchors)
         float x[kInPad];
         anchor_input(A, a, valid, x);
 #pragma unroll
-        for (int k = 0; k < kInPad; ++k) S.XT[canon(k, tid, kTileA)] = __float2bfloat16_rn(x[k]);
+        for (int k = 0; k < kInPad; ++k) S.XT[canon(k, r, kTileA)] = __float2bfloat16_rn(x[k]);
     }
     copy16(S.u.p1.W2, A.w2b, kOutPad * kHid * 2, tid);
     copy16(S.W2T, A.w2tb, kHid * kOutPad * 2, tid);
     copy16(S.W1T, A.w1tb, kInPad * kHid * 2, tid);
     for (int i = tid; i < kOutPad; i += kThreads) S.b2[i] = i < kOut ? A.b2[i] : 0.0f;
-    for (int j = 0; j < 3; ++j) S.xyz[tid][j] = valid ? A.xyz[3 * a + j] : 0.0f;
-    for (int j = 0; j < 6; ++j) S.ls[tid][j] = valid ? A.ls[6 * a + j] : 0.0f;
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem;
-    const uint32_t my_lanes = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t my_lanes = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 
     // y = W2 h + b2, recomputed exactly as in the forward
     if (tid == 0) {
@@ -549,16 +559,20 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     __syncthreads();
     if (S.fail) goto cleanup;
     {
+        // columns 0..63 by the first half, 64..143 by the second
         float v[32];
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
+        for (int cc = 0; cc < 2; ++cc) {
+            const int ch = 2 * half + cc;
             tmem_ld32(my_lanes + ch * 32, v);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) S.Y[tid][ch * 32 + c] = v[c] + S.b2[ch * 32 + c];
+            for (int c = 0; c < 32; ++c) S.Y[r][ch * 32 + c] = v[c] + S.b2[ch * 32 + c];
         }
-        tmem_ld16(my_lanes + 128, v);
+        if (half == 1) {
+            tmem_ld16(my_lanes + 128, v);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) S.Y[tid][128 + c] = v[c] + S.b2[128 + c];
+            for (int c = 0; c < 16; ++c) S.Y[r][128 + c] = v[c] + S.b2[128 + c];
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -586,17 +600,17 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
             for (int i = tid; i < nch; i += kThreads) A.g_logits[c0 + i] = 0.0f;
         }
     }
-    if (tid < na) {
-        // dL/dy of this anchor's children in place of y (every element
-        // depends on its own y only), and the anchor's log-scale gradients,
-        // children in order
-        float *yr = S.Y[tid];
+    if (r < na) {
+        // dL/dy of half of this anchor's children in place of y (every
+        // element depends on its own y only), and that half's share of the
+        // anchor's log-scale gradients, children in order
+        float *yr = S.Y[r];
         float so[3], dl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < 3; ++j) so[j] = expf(S.ls[tid][j]);
-#pragma unroll 2
-        for (int c = 0; c < kChild; ++c) {
-            const int ch = tid * kChild + c;
+        for (int j = 0; j < 3; ++j) so[j] = expf(S.ls[r][j]);
+#pragma unroll 1
+        for (int c = half * (kChild / 2); c < (half + 1) * (kChild / 2); ++c) {
+            const int ch = r * kChild + c;
             float *u = yr + c * kPer;
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
@@ -616,35 +630,38 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
             u[3] = (o > 0.0f && o < kOpacityCeil) ? stg[kStO + ch] / (oc * (1.0f - oc)) * (1.0f - o * o) : 0.0f;
         }
 #pragma unroll
-        for (int k = 0; k < 6; ++k) S.dls[tid][k] = dl[k];
+        for (int k = 0; k < 6; ++k) S.dls[half][r][k] = dl[k];
     }
     __syncthreads();
     // db2 (unrounded dy of the present anchors)
     for (int o = tid; o < kOut; o += kThreads) {
-        float s = 0.0f;
-        for (int r = 0; r < na; ++r) s += S.Y[r][o];
-        part[kOut * kHid + kHid * kIn + o] = s;
+        // four interleaved running sums (independent loads in flight), then
+        // combined in a fixed order
+        float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int rr = 0; rr < na; ++rr) s4[rr & 3] += S.Y[rr][o];
+        part[kOut * kHid + kHid * kIn + o] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
     __syncthreads();
     {
         // this anchor's rounded dy (zero for an absent anchor and the padding
         // outputs) as its row of the dh GEMM's A and its column (K index) of
         // the dW2 GEMMs' A operands
-        const bool live = tid < na;
+        const bool live = r < na;
+        constexpr int kHalfOut = kOutPad / 2;  // outputs per half (even)
 #pragma unroll 4
-        for (int o = 0; o < kOutPad; o += 2) {
-            const float v0 = live && o < kOut ? S.Y[tid][o] : 0.0f;
-            const float v1 = live && o + 1 < kOut ? S.Y[tid][o + 1] : 0.0f;
+        for (int o = half * kHalfOut; o < (half + 1) * kHalfOut; o += 2) {
+            const float v0 = live && o < kOut ? S.Y[r][o] : 0.0f;
+            const float v1 = live && o + 1 < kOut ? S.Y[r][o + 1] : 0.0f;
             const uint32_t pk = pack_bf16x2(v0, v1);
-            *reinterpret_cast<uint32_t *>(&S.DY[canon(tid, o, kOutPad)]) = pk;
+            *reinterpret_cast<uint32_t *>(&S.DY[canon(r, o, kOutPad)]) = pk;
             const __nv_bfloat16 b0 = __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
             const __nv_bfloat16 b1 = __ushort_as_bfloat16((unsigned short)(pk >> 16));
             if (o < kTileA) {
-                S.DYT[canon(o, tid, kTileA)] = b0;
-                S.DYT[canon(o + 1, tid, kTileA)] = b1;
+                S.DYT[canon(o, r, kTileA)] = b0;
+                S.DYT[canon(o + 1, r, kTileA)] = b1;
             } else {
-                S.DYT2[canon(o - kTileA, tid, kTileA)] = b0;
-                S.DYT2[canon(o + 1 - kTileA, tid, kTileA)] = b1;
+                S.DYT2[canon(o - kTileA, r, kTileA)] = b0;
+                S.DYT2[canon(o + 1 - kTileA, r, kTileA)] = b1;
             }
         }
     }
@@ -671,7 +688,7 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     tc_fence_after();
     __syncthreads();
     if (S.fail) goto cleanup;
-    {
+    if (half == 0) {
         // dh after the ReLU mask, rounded, as the dx GEMM's A (row = anchor)
         // and the dW1^T GEMM's B (row = hidden unit, K = anchors); the
         // y-recompute operands it overwrites are no longer read
@@ -679,24 +696,26 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
         tmem_ld32(my_lanes, v);
 #pragma unroll
         for (int c = 0; c < kHid; c += 2) {
-            const float d0 = bf16f(S.HT[canon(c, tid, kTileA)]) > 0.0f ? v[c] : 0.0f;
-            const float d1 = bf16f(S.HT[canon(c + 1, tid, kTileA)]) > 0.0f ? v[c + 1] : 0.0f;
+            const float d0 = bf16f(S.HT[canon(c, r, kTileA)]) > 0.0f ? v[c] : 0.0f;
+            const float d1 = bf16f(S.HT[canon(c + 1, r, kTileA)]) > 0.0f ? v[c + 1] : 0.0f;
             const float w0 = warp_sum(d0), w1 = warp_sum(d1);
             if (lane == 0) {
                 S.db1w[warp][c] = w0;
                 S.db1w[warp][c + 1] = w1;
             }
             const uint32_t pk = pack_bf16x2(d0, d1);
-            *reinterpret_cast<uint32_t *>(&S.u.p2.DH[canon(tid, c, kHid)]) = pk;
-            S.u.p2.DHT[canon(c, tid, kTileA)] = __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
-            S.u.p2.DHT[canon(c + 1, tid, kTileA)] = __ushort_as_bfloat16((unsigned short)(pk >> 16));
+            *reinterpret_cast<uint32_t *>(&S.u.p2.DH[canon(r, c, kHid)]) = pk;
+            S.u.p2.DHT[canon(c, r, kTileA)] = __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
+            S.u.p2.DHT[canon(c + 1, r, kTileA)] = __ushort_as_bfloat16((unsigned short)(pk >> 16));
         }
-        // this thread's row (output tid) of dW2
+    } else {
+        // this thread's row (output r) of dW2
+        float v[32];
         tmem_ld32(my_lanes + 128, v);
-        float4 *dst = reinterpret_cast<float4 *>(part + tid * kHid);
+        float4 *dst = reinterpret_cast<float4 *>(part + r * kHid);
 #pragma unroll
         for (int q = 0; q < kHid / 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        if (warp == 0) {  // outputs 128..139
+        if (warp == 4) {  // outputs 128..139
             tmem_ld32(my_lanes + 160, v);
             if (lane < kOut - kTileA) {
                 float4 *d2 = reinterpret_cast<float4 *>(part + (kTileA + lane) * kHid);
@@ -725,14 +744,14 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     if (tid < kHid) {  // db1, warps in order
         float sum = 0.0f;
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) sum += S.db1w[w][tid];
+        for (int w = 0; w < kTileA / 32; ++w) sum += S.db1w[w][tid];
         part[kOut * kHid + kHid * kIn + kOut + tid] = sum;
     }
     if (!mbar_wait(&S.mbar, 0)) S.fail = 1;
     tc_fence_after();
     __syncthreads();
     if (S.fail) goto cleanup;
-    {
+    if (half == 0) {
         float v[32];
         tmem_ld32(my_lanes + 32, v);
         if (valid) {
@@ -752,14 +771,14 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
                 for (int c = 0; c < kFeat; ++c) A.d_feat[a * kFeat + c] += v[c];
             }
 #pragma unroll
-            for (int j = 0; j < 6; ++j) A.d_ls[6 * a + j] += S.dls[tid][j];
+            for (int j = 0; j < 6; ++j) A.d_ls[6 * a + j] += S.dls[0][r][j] + S.dls[1][r][j];
         }
-        if (warp < 2) {  // dW1[h][i] = (dW1^T)[i][h] for the 35 inputs
-            tmem_ld32(my_lanes + 192, v);
-            if (tid < kIn)
+    } else if (warp < 6) {  // dW1[h][i] = (dW1^T)[i][h] for the 35 inputs (TMEM lanes 0..63)
+        float v[32];
+        tmem_ld32(my_lanes + 192, v);
+        if (r < kIn)
 #pragma unroll
-                for (int h = 0; h < kHid; ++h) part[kOut * kHid + h * kIn + tid] = v[h];
-        }
+            for (int h = 0; h < kHid; ++h) part[kOut * kHid + h * kIn + r] = v[h];
     }
 cleanup:
     if (S.fail) {
@@ -907,7 +926,7 @@ extern "C" int gs_ng_decode_fwd(const gs_ng_params *p, const gs_camera *cam, gs_
     A.c_logits = children->opacity_logits;
     A.c_sh = children->sh;
     const unsigned tiles = (unsigned)((p->n_anchors + ng::kTileA - 1) / ng::kTileA);
-    ng::k_ng_fwd<<<tiles, ng::kThreads, smem, s>>>(A);
+    ng::k_ng_fwd<<<tiles, ng::kFwdThreads, smem, s>>>(A);
     return launch_error();
 }
 

@@ -63,9 +63,9 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     const int32_t bucket = tuning && tuning->bucket ? tuning->bucket : kBucket;
     const int32_t bwd_warps = tuning && tuning->bwd_warps ? tuning->bwd_warps : 4;
     const int32_t chains = tuning ? tuning->bwd_chains : 0;
+    const int32_t fwd_pixels = tuning && tuning->fwd_pixels ? tuning->fwd_pixels : 1;
     if ((bucket != 32 && bucket != 64) || (bwd_warps != 1 && bwd_warps != 2 && bwd_warps != 4 && bwd_warps != 8) ||
-        chains < 0 ||
-        chains > 2)
+        chains < 0 || chains > 2 || (fwd_pixels != 1 && fwd_pixels != 2))
         return nullptr;
     if (n <= 0 || n >= (1ll << 31) || sh_degree < 0 || sh_degree > 3 || n_views < 1 ||
         n_views > GS_MAX_VIEWS || !widths || !heights || inst_capacity <= 0 ||
@@ -123,6 +123,7 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     p->bbox_3sigma = tuning && tuning->bbox_3sigma ? 1 : 0;
     p->bwd_per_pixel = tuning && tuning->bwd_per_pixel ? 1 : 0;
     p->bin_radix = tuning && tuning->bin_radix ? 1 : 0;
+    p->fwd_pixels = fwd_pixels;
     // the counting binning's (Gaussian, block) entries: at most one per
     // instance of capacity (an entry whose block holds no tile of its
     // Gaussian is rare), in the radix path's instance buffers and o_cval

@@ -14,9 +14,10 @@
 // accumulate in registers over all pixels; each lane then adds its splats'
 // 10 values to the per-(view, Gaussian) accumulator with float4 atomics.
 // Pixels whose blend ended before the bucket are compacted away first, so the
-// pipeline only steps through pixels the bucket can affect.  A CTA takes one
-// tile at a time, stages the tile's per-pixel gradients once and its warps
-// share the tile's buckets greedily.
+// pipeline only steps through pixels the bucket can affect.  A CTA of the
+// persistent grid claims one tile at a time from a counter (per-tile work is
+// uneven), stages the tile's per-pixel gradients once and its warps share the
+// tile's buckets greedily.
 //
 // Two kernels:
 //   k_render_bwd      32-splat buckets, one splat per lane; each lane walks
@@ -41,6 +42,7 @@ struct BwdShared {
     float2 ck[kWarps][kTilePix];              // per warp, compacted: (T, S) in front of its bucket
     uint8_t pix[kWarps][kTilePix];            // per warp, compacted: pixel index in the tile
     uint32_t next;                            // next unclaimed bucket of the tile
+    uint32_t tile;                            // the tile this CTA claimed
 };
 
 // Stage the tile's per-pixel data: the upstream gradient and
@@ -154,14 +156,22 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
              const uint32_t *__restrict__ tile_maxc, const float *__restrict__ ckpt,
              const uint32_t *__restrict__ n_contrib, const float *__restrict__ img_rgb,
              const float *__restrict__ img_disp, const float *__restrict__ dL_drgb,
-             const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d, int two_chain_min) {
+             const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d, int two_chain_min,
+             uint32_t *__restrict__ tile_ctr) {
     constexpr int kThreads = kWarps * 32;
     constexpr int kBucketSplats = 32;
     __shared__ BwdShared<kWarps> S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint8_t *spix = S.pix[warp];
 
-    for (int t = blockIdx.x; t < views.total_tiles; t += gridDim.x) {
+    for (;;) {
+        // tiles are claimed one at a time from a counter: per-tile work is
+        // uneven, so a CTA that finishes a light tile takes the next one
+        if (threadIdx.x == 0) S.tile = atomicAdd(tile_ctr, 1u);
+        __syncthreads();
+        const int t = (int)S.tile;
+        __syncthreads();  // every thread has read S.tile before the next claim
+        if (t >= views.total_tiles) break;
         const uint2 range = ranges[t];
         const uint32_t maxc = min(tile_maxc[t], range.y - range.x);
         const uint32_t nb = (maxc + kBucketSplats - 1) / kBucketSplats;  // buckets that hold blended splats
@@ -310,11 +320,6 @@ __device__ __forceinline__ int compact_live_grouped(const float4 *sg, const floa
 }
 
 // ---------------------------------------------------- packed 64-splat kernel
-__device__ __forceinline__ float fast_rcp(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 #ifndef GS_BWD_PK_MINB
 #define GS_BWD_PK_MINB 12
@@ -326,7 +331,7 @@ k_render_bwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
                 const uint32_t *__restrict__ tile_maxc, const float *__restrict__ ckpt,
                 const uint32_t *__restrict__ n_contrib, const float *__restrict__ img_rgb,
                 const float *__restrict__ img_disp, const float *__restrict__ dL_drgb,
-                const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d) {
+                const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d, uint32_t *__restrict__ tile_ctr) {
     constexpr int kThreads = kWarps * 32;
     constexpr int kBucketSplats = 64;
     __shared__ BwdShared<kWarps> S;
@@ -334,7 +339,14 @@ k_render_bwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
     const uint8_t *spix = S.pix[warp];
     const f2x kZero2 = pk2(0.f, 0.f);
 
-    for (int t = blockIdx.x; t < views.total_tiles; t += gridDim.x) {
+    for (;;) {
+        // tiles are claimed one at a time from a counter: per-tile work is
+        // uneven, so a CTA that finishes a light tile takes the next one
+        if (threadIdx.x == 0) S.tile = atomicAdd(tile_ctr, 1u);
+        __syncthreads();
+        const int t = (int)S.tile;
+        __syncthreads();  // every thread has read S.tile before the next claim
+        if (t >= views.total_tiles) break;
         const uint2 range = ranges[t];
         const uint32_t maxc = min(tile_maxc[t], range.y - range.x);
         const uint32_t nb = (maxc + kBucketSplats - 1) / kBucketSplats;
@@ -619,19 +631,22 @@ template <int kWarps>
 static int launch_bwd(const gs_plan *plan, void *ws, const float *d_rgb, const float *d_disp,
                       const float *d_dL_drgb, const float *d_dL_ddisp, float4 *g2d, cudaStream_t s) {
     const ViewsDev vd = make_views(plan, nullptr);
+    uint32_t *ctr = &ws_at<StatusDev>(ws, plan->o_status)->bwd_next_tile;
+    int rc = check_cuda(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), s));
+    if (rc) return rc;
     if (plan->bucket == 64) {
         k_render_bwd_pk<kWarps><<<persistent_grid(k_render_bwd_pk<kWarps>, kWarps * 32), kWarps * 32, 0, s>>>(
             vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
             ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off),
             ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt),
-            ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d);
+            ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, ctr);
         return launch_error();
     }
     k_render_bwd<kWarps><<<persistent_grid(k_render_bwd<kWarps>, kWarps * 32), kWarps * 32, 0, s>>>(
         vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
         ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off),
         ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt),
-        ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, plan->two_chain_min);
+        ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, plan->two_chain_min, ctr);
     return launch_error();
 }
 

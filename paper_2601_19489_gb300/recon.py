@@ -43,7 +43,7 @@ import numpy as np
 import torch
 
 from .api import Gaussians, NgParams
-from .autotune import autotune
+from .autotune import TUNED, autotune
 from .trainer import NgTrainer, Trainer, default_lrs, default_pose
 
 
@@ -116,7 +116,7 @@ def reconstruct(method: str, init, train_cams, train_rgb, train_disp, eval_cams,
             b_disp = [torch.cat([train_disp[i] for i in ix]) for ix in batches]
             b_cams = [[train_cams[i] for i in ix] for ix in batches]
             best, _ = autotune(params, b_cams[:2], b_rgb[:2], lam=lam, device=device)
-            tuning = {k: best[k] for k in ("bucket", "bwd_warps", "bwd_chains")}
+            tuning = {k: best[k] for k in TUNED}
             lb = best["load_balanced"]
         elif method not in ("plain", "densify", "pose"):
             raise ValueError(method)

@@ -260,21 +260,25 @@ def test_counting_binning_reports_overflow(gs, cap):
 # warp per CTA)
 TUNINGS = [None, {"bucket": 64, "bwd_warps": 2, "bwd_chains": 0}, {"bucket": 64, "bwd_warps": 8, "bwd_chains": 0},
            {"bucket": 32, "bwd_warps": 4, "bwd_chains": 0}, {"bucket": 32, "bwd_warps": 8, "bwd_chains": 2},
-           {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1}, {"bwd_per_pixel": 1}]
+           {"bucket": 32, "bwd_warps": 2, "bwd_chains": 1}, {"bwd_per_pixel": 1},
+           {"bucket": 64, "bwd_warps": 1, "fwd_pixels": 2}, {"bucket": 32, "bwd_warps": 4, "fwd_pixels": 2},
+           {"bwd_per_pixel": 1, "fwd_pixels": 2}]
 
 
+@pytest.mark.parametrize("fwd_pixels", [1, 2])
 @pytest.mark.parametrize("which", ["c1", "clustered_ragged"])
-def test_render_fwd_matches_oracle(gs, which, record_property):
+def test_render_fwd_matches_oracle(gs, which, fwd_pixels, record_property):
     """Every pixel against the oracle: colour, disparity and T within the
     per-pixel tolerance (plus the oracle's float32 bound), and the id of the
     last blended Gaussian bit-exact; at branch-flagged pixels the canonical
-    branch or one of the oracle's alternatives."""
+    branch or one of the oracle's alternatives.  Both forward kernels (one
+    pixel per thread; two pixels per thread in packed pairs)."""
     if which == "c1":
         scene, cam = synth.scene_c1(0), synth.camera_c1()
     else:
         scene = synth.scene_clustered(40000, seed=7, sh_degree=3)
         cam = synth.ring_cameras(4, 333, 187)[2]  # ragged: partial tiles on both edges
-    plan, params, rgb, disp, T = _run_forward(gs, scene, [cam])
+    plan, params, rgb, disp, T = _run_forward(gs, scene, [cam], tuning={"fwd_pixels": fwd_pixels})
     _, orec = _oracle_records(scene, cam)
     W, H = cam.width, cam.height
     ref = oren.render_fwd(orec, BG, (0, 0, W, H), amb=AMB)
@@ -284,6 +288,27 @@ def test_render_fwd_matches_oracle(gs, which, record_property):
     print(which, format_stats(st))
     record_property("parity", format_stats(st))
     assert_forward(st, MAX_BRANCH_FRAC)
+
+
+@pytest.mark.parametrize("bucket", [32, 64])
+def test_packed_forward_equals_scalar_forward(gs, bucket):
+    """The two-pixel packed forward performs each pixel's float32 operations
+    of the one-pixel kernel: images, disparity, transmittance and last
+    contributor are bit-identical, with the same number of checkpoint
+    buckets (multi-view plan, ragged sizes).  The backward parity tests read
+    the packed kernel's checkpoints."""
+    from paper_2601_19489_gb300 import _lib as L
+
+    scene = synth.scene_clustered(30000, seed=21, sh_degree=2)
+    cams = [synth.ring_cameras(4, 333, 187)[1], synth.ring_cameras(4, 272, 165)[3]]
+    out = []
+    for fp in (1, 2):
+        plan, params, rgb, disp, T = _run_forward(gs, scene, cams, tuning={"bucket": bucket, "fwd_pixels": fp})
+        nc = to_np(plan.view(L.GS_WS_N_CONTRIB, torch.int32))[: plan.pixels]
+        out.append((to_np(rgb), to_np(disp), to_np(T), nc, plan))
+    for a, b in zip(out[0][:4], out[1][:4]):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    assert out[0][4].status()["n_buckets"] == out[1][4].status()["n_buckets"]
 
 
 # -------------------------------------------------------------- backward
