@@ -633,6 +633,13 @@ def run_ours(args, rank, world):
             "explicit_instances_per_view": st2["n_instances"], "explicit_pairs_per_view": mean_pairs,
             "note": "both from their own initial state, the same warm-up and timed steps on the same views and "
                     "targets; per-step work differs (children whose decoded opacity is <= 0 reach no tile)"}
+        torch.cuda.empty_cache()
+        fz = run_ng(args, dev, max(1, args.n // 10), cams, targets_d, args.warmup, args.steps, lb, tuning,
+                    fused_decode=True)
+        ng["fused_decode_preprocess"] = {
+            "steps_per_s": fz["steps_per_s"], "ms_per_step": fz["ms_per_step"], "stages_ms": fz["stages_ms"],
+            "note": "decode and the children's preprocess in one launch (gs_ng_decode_preprocess), the same "
+                    "protocol; its 'decode' stage holds both, 'preprocess' is empty"}
         line["neural_gaussians"] = ng
         torch.cuda.empty_cache()
     if world == 1 and not args.no_pose:
@@ -777,7 +784,7 @@ def graph_vs_eager_small(args, dev, steps: int) -> dict:
 
 
 def run_ng(args, dev, n_anchors: int, cams, targets, warmup: int, steps: int, lb: bool = True,
-           tuning: dict | None = None) -> dict:
+           tuning: dict | None = None, fused_decode: bool = False) -> dict:
     """Neural-Gaussian step: n_anchors anchors subsampled from the clustered
     scene's points, 10 children each, the same ring views and targets as the
     headline, one view per step (decode, splat, loss, backward, decoder
@@ -787,7 +794,8 @@ def run_ng(args, dev, n_anchors: int, cams, targets, warmup: int, steps: int, lb
     (tile instances, pixel-splat pairs up to each pixel's last contributor)
     reported beside the time, since a decoder in training changes how many of
     its children reach the blend.  Binning and launch shapes are the
-    headline's (lb, tuning)."""
+    headline's (lb, tuning).  fused_decode: the decode and the children's
+    preprocess in one launch (its time is the decode stage's)."""
     import torch
 
     import synth
@@ -798,7 +806,7 @@ def run_ng(args, dev, n_anchors: int, cams, targets, warmup: int, steps: int, lb
     pts = synth.scene_clustered(args.n, seed=0, sh_degree=0).means
     d = synth.ng_anchors(pts, n_anchors, seed=0)
     tr = NgTrainer(api.NgParams.from_dict(d, device=dev), args.width, args.height, lam=args.lam,
-                   load_balanced=lb, tuning=tuning, device=dev)
+                   load_balanced=lb, tuning=tuning, fused_decode=fused_decode, device=dev)
     tr.ensure_capacity(cams)
     for s in range(warmup):
         tr.step(cams[s % len(cams)], targets[s % len(cams)])

@@ -400,6 +400,17 @@ GS_API size_t gs_ng_workspace_bytes(int64_t n_anchors);
  * coefficient (colour - 0.5) * 2 sqrt(pi). */
 GS_API int gs_ng_decode_fwd(const gs_ng_params *ng, const gs_camera *h_cam, gs_params *children, void *d_ws,
                             void *stream);
+/* Sec. 2.3 with NEXT-4's fusion: gs_ng_decode_fwd and gs_preprocess of the
+ * children in one launch.  The decoder's epilogue computes each child's
+ * parameters, writes them to `children` (as gs_ng_decode_fwd; the backward
+ * reads them) and preprocesses the child from registers into `plan_ws`,
+ * exactly as gs_preprocess(plan, plan_ws, children, h_cam) would (same
+ * records, tile counts, rectangles and depth keys, bit for bit).  `plan`:
+ * one view of h_cam's size, n = children->n, SH degree 0, no pose state
+ * attached (GS_ERR_ARG otherwise).  Follow with gs_bin_sort etc. as after
+ * gs_preprocess. */
+GS_API int gs_ng_decode_preprocess(const gs_ng_params *ng, const gs_camera *h_cam, gs_params *children, void *d_ws,
+                                   const gs_plan *plan, void *plan_ws, void *stream);
 /* Backward of gs_ng_decode_fwd for the same camera and workspace: maps the
  * children's parameter gradients to the anchors' feature and log-scale
  * gradients and the MLP gradients, ACCUMULATED (+=) into `grads` (its

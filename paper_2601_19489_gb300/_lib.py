@@ -33,7 +33,8 @@ EXPORTS = (
     "gs_loss_scratch_floats", "gs_loss", "gs_adam_step",
     "gs_adam_step_multi", "gs_adam_step_multi_dev", "gs_preprocess_bwd_adam", "gs_sort_scratch_bytes",
     "gs_sort_pairs_u32", "gs_sort_pairs_u32_noalloc",
-    "gs_ng_workspace_bytes", "gs_ng_decode_fwd", "gs_ng_decode_bwd", "gs_ng_read_status", "gs_ng_wait_probe",
+    "gs_ng_workspace_bytes", "gs_ng_decode_fwd", "gs_ng_decode_preprocess", "gs_ng_decode_bwd",
+    "gs_ng_read_status", "gs_ng_wait_probe",
     "gs_densify_scratch_bytes", "gs_densify_score", "gs_densify_plan", "gs_densify_apply",
     "gs_pose_init", "gs_plan_set_pose", "gs_pose_step",
 )
@@ -151,6 +152,8 @@ _SIGS = {
                                                  ctypes.c_int32, P]),
     "gs_ng_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "gs_ng_decode_fwd": (ctypes.c_int, [ctypes.POINTER(GsNgParams), P, ctypes.POINTER(GsParams), P, P]),
+    "gs_ng_decode_preprocess": (ctypes.c_int, [ctypes.POINTER(GsNgParams), P, ctypes.POINTER(GsParams), P, P, P,
+                                               P]),
     "gs_ng_decode_bwd": (ctypes.c_int, [ctypes.POINTER(GsNgParams), P, ctypes.POINTER(GsParams), ctypes.c_int32,
                                          ctypes.POINTER(GsNgParams), P, P]),
     "gs_ng_read_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), P]),

@@ -365,6 +365,16 @@ def gs_ng_decode_fwd(ng: NgParams, cam, children: "Gaussians", ws: torch.Tensor,
             "gs_ng_decode_fwd")
 
 
+def gs_ng_decode_preprocess(ng: NgParams, cam, children: "Gaussians", ws: torch.Tensor, plan: Plan,
+                            stream=None) -> None:
+    """gs_ng_decode_fwd and gs_preprocess of the children on `plan` in one launch."""
+    c = (L.GsCamera * 1)(camera_struct(cam))
+    p = ng.struct()
+    ch = children.struct()
+    L.check(L.lib().gs_ng_decode_preprocess(ctypes.byref(p), c, ctypes.byref(ch), ws.data_ptr(), plan.handle,
+                                            plan.ws.data_ptr(), _stream(stream)), "gs_ng_decode_preprocess")
+
+
 def gs_ng_decode_bwd(ng: NgParams, cam, child_grads: "Gaussians", grads: NgParams, ws: torch.Tensor,
                      zero_child_grads: bool = False, stream=None) -> None:
     c = (L.GsCamera * 1)(camera_struct(cam))

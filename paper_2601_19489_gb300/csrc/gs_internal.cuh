@@ -18,6 +18,7 @@ constexpr int kTilePix = kTile * kTile;    // 256 pixels
 constexpr int kBucket = GS_BUCKET;         // default splats per checkpoint
 constexpr int kTwoChainAuto = 128;         // automatic chain choice: two chains from 128 live pixels
 constexpr int kCkptCh = 5;                 // T, C.r, C.g, C.b, D
+constexpr int kTileClasses = 8;            // backward work classes of a tile (by its last contributor)
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
@@ -103,6 +104,8 @@ struct gs_plan {
     // offsets
     size_t o_status, o_rec, o_touched, o_rect, o_dkey[2], o_dval[2];
     size_t o_ikey[2], o_ival[2], o_ranges, o_tile_maxc, o_bucket_off, o_ncontrib;
+    size_t o_tile_order;  // kTileClasses x total_tiles: tile ids by work class, written by the forward
+    size_t o_tile_count;  // kTileClasses counts of those lists
     size_t o_ckpt, o_grad2d, o_sort_scratch, o_block_sums, o_bin;
     size_t o_brange, o_bchunk, o_btile, o_bbase, o_ccnt, o_cval;  // counting binning
     size_t o_final;  // per-pixel final T, then the background (per-pixel backward only)
@@ -121,6 +124,8 @@ __host__ __device__ inline T *ws_at(void *ws, size_t off) {
 }
 
 ViewsDev make_views(const gs_plan *plan, const gs_camera *cams);
+// GS_OK, or GS_ERR_ARG for a camera that does not match the plan's views.
+int check_cams(const gs_plan *plan, const gs_camera *cams);
 int check_cuda(cudaError_t e);
 int launch_error();
 
@@ -274,6 +279,14 @@ __device__ __forceinline__ float fast_exp2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Work class of a tile for the backward, from its largest last-contributor
+// position: 0 for >= 4096, one class per halving, 7 below 64.  The backward
+// takes the classes in order, heaviest first.
+__device__ __forceinline__ int tile_work_class(uint32_t maxc) {
+    const int lg = 31 - __clz((int)(maxc | 1u));  // floor(log2(maxc)), 0 for maxc <= 1
+    return min(kTileClasses - 1, max(0, 12 - lg));
 }
 
 // 1/x with the hardware approximation (PTX rcp.approx.ftz.f32: within one

@@ -22,6 +22,7 @@
 #include <stddef.h>
 
 #include "gs_internal.cuh"
+#include "preprocess_item.cuh"
 
 namespace gs {
 namespace ng {
@@ -192,6 +193,13 @@ struct Args {
     int feat_vec;  // feat and d_feat are 16-byte aligned (float4 rows)
     float *d_feat, *d_ls, *partial;
     int *err;
+    // fused decode + preprocess: the plan's view and its preprocess outputs
+    ViewDev view;
+    float4 *rec;
+    float2 *bin;
+    uint32_t *touched, *dkey, *dval;
+    uint2 *rects;
+    int box3;
 };
 
 // ------------------------------------------------------------ weight prep
@@ -280,6 +288,9 @@ struct FwdSmem {
     int fail;
 };
 
+// kPre: also the preprocess of every child (Sec. 2.3's decode fused with the
+// per-Gaussian preprocess, the children's parameters passed on in registers)
+template <bool kPre>
 __global__ void __launch_bounds__(kFwdThreads) k_ng_fwd(Args A) {
     extern __shared__ uint8_t smem_raw[];
     FwdSmem &S = *reinterpret_cast<FwdSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -378,22 +389,53 @@ __global__ void __launch_bounds__(kFwdThreads) k_ng_fwd(Args A) {
         const int na = (int)min((int64_t)kTileA, A.n - a0);
         const int nch = na * kChild;
         const int64_t c0 = a0 * kChild;
-        for (int i = tid; i < nch * 3; i += kFwdThreads) {
-            const int ch = i / 3, j = i - 3 * ch, r = ch / kChild, c = ch - r * kChild;
-            const float u = S.Y[r][c * kPer + j];
-            A.c_means[3 * c0 + i] = S.xyz[r][j] + tanhf(u) * expf(S.ls[r][j]);
-            A.c_ls[3 * c0 + i] = S.ls[r][3 + j] + log_sigmoidf(S.Y[r][c * kPer + 7 + j]);
-            A.c_sh[3 * c0 + i] = (sigmoidf_(S.Y[r][c * kPer + 4 + j]) - 0.5f) * kDcScale;
-        }
-        for (int i = tid; i < nch * 4; i += kFwdThreads) {
-            const int ch = i >> 2, j = i & 3, r = ch / kChild, c = ch - r * kChild;
-            A.c_quats[4 * c0 + i] = S.Y[r][c * kPer + 10 + j];
-        }
-        for (int ch = tid; ch < nch; ch += kFwdThreads) {
-            const int r = ch / kChild, c = ch - r * kChild;
-            const float o = tanhf(S.Y[r][c * kPer + 3]);
-            const float oc = fminf(o, kOpacityCeil);
-            A.c_logits[c0 + ch] = o > 0.0f ? logf(oc) - log1pf(-oc) : kLogitFloor;
+        if (!kPre) {
+            for (int i = tid; i < nch * 3; i += kFwdThreads) {
+                const int ch = i / 3, j = i - 3 * ch, r = ch / kChild, c = ch - r * kChild;
+                const float u = S.Y[r][c * kPer + j];
+                A.c_means[3 * c0 + i] = S.xyz[r][j] + tanhf(u) * expf(S.ls[r][j]);
+                A.c_ls[3 * c0 + i] = S.ls[r][3 + j] + log_sigmoidf(S.Y[r][c * kPer + 7 + j]);
+                A.c_sh[3 * c0 + i] = (sigmoidf_(S.Y[r][c * kPer + 4 + j]) - 0.5f) * kDcScale;
+            }
+            for (int i = tid; i < nch * 4; i += kFwdThreads) {
+                const int ch = i >> 2, j = i & 3, r = ch / kChild, c = ch - r * kChild;
+                A.c_quats[4 * c0 + i] = S.Y[r][c * kPer + 10 + j];
+            }
+            for (int ch = tid; ch < nch; ch += kFwdThreads) {
+                const int r = ch / kChild, c = ch - r * kChild;
+                const float o = tanhf(S.Y[r][c * kPer + 3]);
+                const float oc = fminf(o, kOpacityCeil);
+                A.c_logits[c0 + ch] = o > 0.0f ? logf(oc) - log1pf(-oc) : kLogitFloor;
+            }
+        } else {
+            // child by child: the same parameters (same expressions), written
+            // for the backward and preprocessed straight from registers
+            for (int ch = tid; ch < nch; ch += kFwdThreads) {
+                const int r = ch / kChild, c = ch - r * kChild;
+                const float *u = S.Y[r] + c * kPer;
+                const int64_t gi = c0 + ch;
+                float m[3], ls[3], sh[3];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    m[j] = S.xyz[r][j] + tanhf(u[j]) * expf(S.ls[r][j]);
+                    ls[j] = S.ls[r][3 + j] + log_sigmoidf(u[7 + j]);
+                    sh[j] = (sigmoidf_(u[4 + j]) - 0.5f) * kDcScale;
+                    A.c_means[3 * gi + j] = m[j];
+                    A.c_ls[3 * gi + j] = ls[j];
+                    A.c_sh[3 * gi + j] = sh[j];
+                }
+                const float4 q = make_float4(u[10], u[11], u[12], u[13]);
+                A.c_quats[4 * gi] = q.x;
+                A.c_quats[4 * gi + 1] = q.y;
+                A.c_quats[4 * gi + 2] = q.z;
+                A.c_quats[4 * gi + 3] = q.w;
+                const float o = tanhf(u[3]);
+                const float oc = fminf(o, kOpacityCeil);
+                const float logit = o > 0.0f ? logf(oc) - log1pf(-oc) : kLogitFloor;
+                A.c_logits[gi] = logit;
+                preprocess_item<0>(A.view, gi, make_float3(m[0], m[1], m[2]), q, make_float3(ls[0], ls[1], ls[2]), logit,
+                                   sh, A.rec, A.bin, A.touched, A.rects, A.dkey, A.dval, A.box3);
+            }
         }
     }
 cleanup:
@@ -911,7 +953,7 @@ extern "C" int gs_ng_decode_fwd(const gs_ng_params *p, const gs_camera *cam, gs_
     const size_t smem = sizeof(ng::FwdSmem) + 1024;
     static bool opted = false;
     if (!opted) {
-        rc = ng::smem_opt_in((const void *)ng::k_ng_fwd, smem);
+        rc = ng::smem_opt_in((const void *)ng::k_ng_fwd<false>, smem);
         if (rc) return rc;
         opted = true;
     }
@@ -926,7 +968,48 @@ extern "C" int gs_ng_decode_fwd(const gs_ng_params *p, const gs_camera *cam, gs_
     A.c_logits = children->opacity_logits;
     A.c_sh = children->sh;
     const unsigned tiles = (unsigned)((p->n_anchors + ng::kTileA - 1) / ng::kTileA);
-    ng::k_ng_fwd<<<tiles, ng::kFwdThreads, smem, s>>>(A);
+    ng::k_ng_fwd<false><<<tiles, ng::kFwdThreads, smem, s>>>(A);
+    return launch_error();
+}
+
+extern "C" int gs_ng_decode_preprocess(const gs_ng_params *p, const gs_camera *cam, gs_params *children, void *ws,
+                                       const gs_plan *plan, void *plan_ws, void *stream) {
+    int rc = ng::check_ng(p);
+    if (rc) return rc;
+    if (!cam || !ws || !children || children->n != p->n_anchors * ng::kChild || children->sh_degree != 0 ||
+        !children->means || !children->log_scales || !children->quats || !children->opacity_logits || !children->sh ||
+        !plan || !plan_ws || plan->V != 1 || plan->n != children->n || plan->sh_degree != 0 || plan->pose)
+        return GS_ERR_ARG;
+    rc = check_cams(plan, cam);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = sizeof(ng::FwdSmem) + 1024;
+    static bool opted = false;
+    if (!opted) {
+        rc = ng::smem_opt_in((const void *)ng::k_ng_fwd<true>, smem);
+        if (rc) return rc;
+        opted = true;
+    }
+    ng::Args A = ng::base_args(p, cam, ws);
+    char *w = (char *)ws;
+    const ng::Layout L = ng::layout(p->n_anchors);
+    ng::k_ng_prep<<<1, 256, 0, s>>>(p->w1, p->w2, (__nv_bfloat16 *)(w + L.w1b), (__nv_bfloat16 *)(w + L.w2b),
+                                    (__nv_bfloat16 *)(w + L.w2tb), (__nv_bfloat16 *)(w + L.w1tb));
+    A.c_means = children->means;
+    A.c_ls = children->log_scales;
+    A.c_quats = children->quats;
+    A.c_logits = children->opacity_logits;
+    A.c_sh = children->sh;
+    A.view = make_views(plan, cam).v[0];
+    A.rec = ws_at<float4>(plan_ws, plan->o_rec);
+    A.bin = ws_at<float2>(plan_ws, plan->o_bin);
+    A.touched = ws_at<uint32_t>(plan_ws, plan->o_touched);
+    A.rects = ws_at<uint2>(plan_ws, plan->o_rect);
+    A.dkey = ws_at<uint32_t>(plan_ws, plan->o_dkey[0]);
+    A.dval = ws_at<uint32_t>(plan_ws, plan->o_dval[0]);
+    A.box3 = plan->bbox_3sigma;
+    const unsigned tiles = (unsigned)((p->n_anchors + ng::kTileA - 1) / ng::kTileA);
+    ng::k_ng_fwd<true><<<tiles, ng::kFwdThreads, smem, s>>>(A);
     return launch_error();
 }
 

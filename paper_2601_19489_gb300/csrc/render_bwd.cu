@@ -102,6 +102,21 @@ __device__ __forceinline__ int compact_live(const float4 *sg, const float4 *sfin
     return m_total;
 }
 
+// The next tile of the backward: claim number i from the counter, mapped
+// through the forward's per-class tile lists (class 0 first); all ones once
+// every tile is taken.
+__device__ __forceinline__ uint32_t claim_tile(uint32_t *tile_ctr, const uint32_t *__restrict__ tile_order,
+                                               const uint32_t *class_count, int total_tiles) {
+    const uint32_t i = atomicAdd(tile_ctr, 1u);
+    uint32_t base = 0;
+    for (int c = 0; c < kTileClasses; ++c) {
+        const uint32_t n = class_count[c];
+        if (i < base + n) return tile_order[(size_t)c * total_tiles + (i - base)];
+        base += n;
+    }
+    return 0xffffffffu;
+}
+
 // Per-splat sums over its pixels; the mean's gradient is linear in
 // (dx, dy) with the splat's conic as coefficients, so only sx = sum dpw dx
 // and sy = sum dpw dy are accumulated and the conic is applied once.
@@ -157,7 +172,8 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
              const uint32_t *__restrict__ n_contrib, const float *__restrict__ img_rgb,
              const float *__restrict__ img_disp, const float *__restrict__ dL_drgb,
              const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d, int two_chain_min,
-             uint32_t *__restrict__ tile_ctr) {
+             uint32_t *__restrict__ tile_ctr, const uint32_t *__restrict__ tile_order,
+             const uint32_t *__restrict__ class_count) {
     constexpr int kThreads = kWarps * 32;
     constexpr int kBucketSplats = 32;
     __shared__ BwdShared<kWarps> S;
@@ -165,13 +181,16 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
     const uint8_t *spix = S.pix[warp];
 
     for (;;) {
-        // tiles are claimed one at a time from a counter: per-tile work is
-        // uneven, so a CTA that finishes a light tile takes the next one
-        if (threadIdx.x == 0) S.tile = atomicAdd(tile_ctr, 1u);
+        // tiles are claimed one at a time from a counter, in the forward's
+        // work classes (heaviest first): per-tile work is uneven, so a CTA
+        // that finishes a light tile takes the next one, and the longest
+        // tiles do not come last
+        if (threadIdx.x == 0) S.tile = claim_tile(tile_ctr, tile_order, class_count, views.total_tiles);
         __syncthreads();
-        const int t = (int)S.tile;
+        const uint32_t tt = S.tile;
         __syncthreads();  // every thread has read S.tile before the next claim
-        if (t >= views.total_tiles) break;
+        if (tt >= (uint32_t)views.total_tiles) break;
+        const int t = (int)tt;
         const uint2 range = ranges[t];
         const uint32_t maxc = min(tile_maxc[t], range.y - range.x);
         const uint32_t nb = (maxc + kBucketSplats - 1) / kBucketSplats;  // buckets that hold blended splats
@@ -331,7 +350,8 @@ k_render_bwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
                 const uint32_t *__restrict__ tile_maxc, const float *__restrict__ ckpt,
                 const uint32_t *__restrict__ n_contrib, const float *__restrict__ img_rgb,
                 const float *__restrict__ img_disp, const float *__restrict__ dL_drgb,
-                const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d, uint32_t *__restrict__ tile_ctr) {
+                const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d, uint32_t *__restrict__ tile_ctr,
+                const uint32_t *__restrict__ tile_order, const uint32_t *__restrict__ class_count) {
     constexpr int kThreads = kWarps * 32;
     constexpr int kBucketSplats = 64;
     __shared__ BwdShared<kWarps> S;
@@ -340,13 +360,16 @@ k_render_bwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
     const f2x kZero2 = pk2(0.f, 0.f);
 
     for (;;) {
-        // tiles are claimed one at a time from a counter: per-tile work is
-        // uneven, so a CTA that finishes a light tile takes the next one
-        if (threadIdx.x == 0) S.tile = atomicAdd(tile_ctr, 1u);
+        // tiles are claimed one at a time from a counter, in the forward's
+        // work classes (heaviest first): per-tile work is uneven, so a CTA
+        // that finishes a light tile takes the next one, and the longest
+        // tiles do not come last
+        if (threadIdx.x == 0) S.tile = claim_tile(tile_ctr, tile_order, class_count, views.total_tiles);
         __syncthreads();
-        const int t = (int)S.tile;
+        const uint32_t tt = S.tile;
         __syncthreads();  // every thread has read S.tile before the next claim
-        if (t >= views.total_tiles) break;
+        if (tt >= (uint32_t)views.total_tiles) break;
+        const int t = (int)tt;
         const uint2 range = ranges[t];
         const uint32_t maxc = min(tile_maxc[t], range.y - range.x);
         const uint32_t nb = (maxc + kBucketSplats - 1) / kBucketSplats;
@@ -631,7 +654,9 @@ template <int kWarps>
 static int launch_bwd(const gs_plan *plan, void *ws, const float *d_rgb, const float *d_disp,
                       const float *d_dL_drgb, const float *d_dL_ddisp, float4 *g2d, cudaStream_t s) {
     const ViewsDev vd = make_views(plan, nullptr);
-    uint32_t *ctr = &ws_at<StatusDev>(ws, plan->o_status)->bwd_next_tile;
+    StatusDev *st = ws_at<StatusDev>(ws, plan->o_status);
+    uint32_t *ctr = &st->bwd_next_tile;
+    const uint32_t *order = ws_at<uint32_t>(ws, plan->o_tile_order), *ccount = ws_at<uint32_t>(ws, plan->o_tile_count);
     int rc = check_cuda(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), s));
     if (rc) return rc;
     if (plan->bucket == 64) {
@@ -639,14 +664,15 @@ static int launch_bwd(const gs_plan *plan, void *ws, const float *d_rgb, const f
             vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
             ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off),
             ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt),
-            ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, ctr);
+            ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, ctr, order, ccount);
         return launch_error();
     }
     k_render_bwd<kWarps><<<persistent_grid(k_render_bwd<kWarps>, kWarps * 32), kWarps * 32, 0, s>>>(
         vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
         ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off),
         ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt),
-        ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, plan->two_chain_min, ctr);
+        ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, plan->two_chain_min, ctr,
+        order, ccount);
     return launch_error();
 }
 

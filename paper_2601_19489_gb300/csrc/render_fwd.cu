@@ -29,7 +29,7 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
              float bg_g, float bg_b, float *__restrict__ out_rgb, float *__restrict__ out_disp,
              float *__restrict__ out_T, uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ tile_maxc,
              float *__restrict__ ckpt, float *__restrict__ final_T, uint32_t *__restrict__ bucket_off,
-             StatusDev *st) {
+             uint32_t *__restrict__ tile_order, uint32_t *__restrict__ tile_count, StatusDev *st) {
     __shared__ float4 s_r0[kTilePix];
     __shared__ float4 s_r1[kTilePix];
     __shared__ float4 s_r2[kTilePix];
@@ -137,7 +137,13 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
     __syncthreads();
     if ((tid & 31) == 0) atomicMax(&s_maxc, m);
     __syncthreads();
-    if (tid == 0) tile_maxc[t] = s_maxc;
+    if (tid == 0) {
+        tile_maxc[t] = s_maxc;
+        if (ckpt) {  // the per-Gaussian backward takes the tiles by work class, heaviest first
+            const int c = tile_work_class(s_maxc);
+            tile_order[(size_t)c * views.total_tiles + atomicAdd(&tile_count[c], 1u)] = (uint32_t)t;
+        }
+    }
 }
 
 
@@ -160,7 +166,8 @@ k_render_fwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
                 const float4 *__restrict__ rec, int bucket_shift, float bg_r, float bg_g, float bg_b,
                 float *__restrict__ out_rgb, float *__restrict__ out_disp, float *__restrict__ out_T,
                 uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ tile_maxc, float *__restrict__ ckpt,
-                float *__restrict__ final_T, uint32_t *__restrict__ bucket_off, StatusDev *st) {
+                float *__restrict__ final_T, uint32_t *__restrict__ bucket_off, uint32_t *__restrict__ tile_order,
+                uint32_t *__restrict__ tile_count, StatusDev *st) {
     __shared__ ulonglong2 s_q0[kFwdPkBatch], s_q1[kFwdPkBatch], s_q2[kFwdPkBatch];
     __shared__ ulonglong2 s_c0[kFwdPkBatch], s_c1[kFwdPkBatch];
     __shared__ uint32_t s_maxc, s_boff;
@@ -305,7 +312,13 @@ k_render_fwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
     __syncthreads();
     if ((tid & 31) == 0) atomicMax(&s_maxc, m);
     __syncthreads();
-    if (tid == 0) tile_maxc[t] = s_maxc;
+    if (tid == 0) {
+        tile_maxc[t] = s_maxc;
+        if (ckpt) {  // the per-Gaussian backward takes the tiles by work class, heaviest first
+            const int c = tile_work_class(s_maxc);
+            tile_order[(size_t)c * views.total_tiles + atomicAdd(&tile_count[c], 1u)] = (uint32_t)t;
+        }
+    }
 }
 
 }  // namespace gs
@@ -318,8 +331,11 @@ extern "C" int gs_render_fwd(const gs_plan *plan, void *ws, const float *bg, flo
     cudaStream_t s = (cudaStream_t)stream;
     const ViewsDev vd = make_views(plan, nullptr);
     StatusDev *st = ws_at<StatusDev>(ws, plan->o_status);
-    // the bucket counter restarts with every forward
+    // the bucket counter and the tile classes restart with every forward
     int rc = check_cuda(cudaMemsetAsync(&st->n_buckets, 0, sizeof(uint32_t), s));
+    if (rc) return rc;
+    rc = check_cuda(cudaMemsetAsync(ws_at<uint32_t>(ws, plan->o_tile_count), 0,
+                                    kTileClasses * sizeof(uint32_t), s));
     if (rc) return rc;
     uint32_t *ncontrib = ws_at<uint32_t>(ws, plan->o_ncontrib), *tmaxc = ws_at<uint32_t>(ws, plan->o_tile_maxc);
     float *ck = plan->bwd_per_pixel ? nullptr : ws_at<float>(ws, plan->o_ckpt);
@@ -328,13 +344,14 @@ extern "C" int gs_render_fwd(const gs_plan *plan, void *ws, const float *bg, flo
     const uint32_t *items = ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]);
     const float4 *recs = ws_at<float4>(ws, plan->o_rec);
     uint32_t *boff = ws_at<uint32_t>(ws, plan->o_bucket_off);
+    uint32_t *order = ws_at<uint32_t>(ws, plan->o_tile_order), *tcount = ws_at<uint32_t>(ws, plan->o_tile_count);
     if (plan->fwd_pixels == 2)
         k_render_fwd_pk<<<plan->total_tiles, kFwdPkThreads, 0, s>>>(vd, rg, items, recs, plan->bucket_shift, bg[0],
                                                                      bg[1], bg[2], out_rgb, out_disp, out_T, ncontrib,
-                                                                     tmaxc, ck, fin, boff, st);
+                                                                     tmaxc, ck, fin, boff, order, tcount, st);
     else
         k_render_fwd<<<plan->total_tiles, kTilePix, 0, s>>>(vd, rg, items, recs, plan->bucket_shift, bg[0], bg[1],
                                                             bg[2], out_rgb, out_disp, out_T, ncontrib, tmaxc, ck, fin,
-                                                            boff, st);
+                                                            boff, order, tcount, st);
     return launch_error();
 }

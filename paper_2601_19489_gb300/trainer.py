@@ -265,17 +265,20 @@ class Trainer:
         ev(7)
         self._pose_tick(s)
 
-    def _splat_stages(self, cams, target, target_disp, s, ev, e0: int, with_pbwd: bool = True) -> None:
+    def _splat_stages(self, cams, target, target_disp, s, ev, e0: int, with_pbwd: bool = True,
+                      with_pre: bool = True) -> None:
         """preprocess .. preprocess backward of self.params on `cams`; the
         parameter gradients accumulate into self.grads.  Records events
         e0 .. e0 + 5 after each stage (without the preprocess backward:
-        stops after the blend backward, e0 + 4)."""
+        stops after the blend backward, e0 + 4).  with_pre=False: the
+        preprocess already ran (fused into the neural-Gaussian decode)."""
         lib = L.lib()
         sl = self.slot_for(cams)
         h, ws = sl.plan.handle, sl.plan.ws.data_ptr()
         c = self._cam(cams)
         use_disp = target_disp is not None and self.disp_weight > 0.0
-        L.check(lib.gs_preprocess(h, ws, ctypes.byref(self._pstruct), c, s), "gs_preprocess")
+        if with_pre:
+            L.check(lib.gs_preprocess(h, ws, ctypes.byref(self._pstruct), c, s), "gs_preprocess")
         ev(e0)
         L.check(lib.gs_bin_sort(h, ws, int(self.load_balanced), s), "gs_bin_sort")
         ev(e0 + 1)
@@ -500,8 +503,12 @@ class NgTrainer(Trainer):
                  "decode_bwd", "adam")
 
     def __init__(self, ng: NgParams, width: int | None = None, height: int | None = None, *,
-                 ng_lrs: dict | None = None, **kw):
+                 ng_lrs: dict | None = None, fused_decode: bool = False, **kw):
+        """fused_decode: decode and preprocess the children in one launch
+        (gs_ng_decode_preprocess) in the training step; the results are the
+        same bit for bit."""
         self.ng = ng
+        self.fused_decode = bool(fused_decode)
         self.ng_grads = ng.zeros_like()
         self.ng_m = ng.zeros_like()
         self.ng_v = ng.zeros_like()
@@ -565,9 +572,15 @@ class NgTrainer(Trainer):
         s = st.cuda_stream
         ev = (lambda i: events[i].record(st)) if events is not None else (lambda i: None)
         ev(0)
-        self._decode(cam[0], s)
+        if self.fused_decode:
+            sl = self.slot_for(cam)
+            L.check(L.lib().gs_ng_decode_preprocess(ctypes.byref(self._ngp), self._cam(cam), ctypes.byref(self._pstruct),
+                                                    self.ng_ws.data_ptr(), sl.plan.handle, sl.plan.ws.data_ptr(), s),
+                    "gs_ng_decode_preprocess")
+        else:
+            self._decode(cam[0], s)
         ev(1)
-        self._splat_stages(cam, target, target_disp, s, ev, 2)
+        self._splat_stages(cam, target, target_disp, s, ev, 2, with_pre=not self.fused_decode)
         c = self._cam(cam)
         L.check(L.lib().gs_ng_decode_bwd(ctypes.byref(self._ngp), c, ctypes.byref(self._gstruct), 1,
                                          ctypes.byref(self._ngg), self.ng_ws.data_ptr(), s), "gs_ng_decode_bwd")

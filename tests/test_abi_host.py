@@ -234,6 +234,22 @@ def test_more_argument_errors_are_caught_on_the_host(lib):
     ng.n_anchors = 4
     assert lib.gs_ng_decode_fwd(ctypes.byref(ng), ctypes.byref(L.GsCamera()), ctypes.byref(kids), fake,
                                 None) == ARG
+    # fused decode + preprocess: no plan; a plan of two views; a plan whose
+    # size differs from the children's; an SH-degree-3 plan
+    kids.n = 40
+    kids.means = kids.log_scales = kids.quats = kids.opacity_logits = kids.sh = 4096
+    assert lib.gs_ng_decode_preprocess(ctypes.byref(ng), ctypes.byref(L.GsCamera()), ctypes.byref(kids), fake,
+                                       None, fake, None) == ARG
+    for n, deg, views in ((40, 0, 2), (41, 0, 1), (40, 3, 1)):
+        ws_ = (ctypes.c_int32 * views)(*([64] * views))
+        hs_ = (ctypes.c_int32 * views)(*([48] * views))
+        pl = lib.gs_plan_create(n, deg, views, ws_, hs_, 1 << 12)
+        assert pl
+        try:
+            assert lib.gs_ng_decode_preprocess(ctypes.byref(ng), ctypes.byref(L.GsCamera()), ctypes.byref(kids),
+                                               fake, pl, fake, None) == ARG
+        finally:
+            lib.gs_plan_destroy(pl)
 
 
 def test_wait_probe_arguments_are_checked_on_the_host(lib):

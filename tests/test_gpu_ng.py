@@ -220,6 +220,68 @@ def test_ng_trainer_learns_and_replays_as_a_graph(gs):
     np.testing.assert_allclose(runs[1], runs[0], rtol=1e-3)
 
 
+@pytest.mark.parametrize("n_anchors,box3", [(1000, 0), (4177, 0), (1000, 1)])
+def test_fused_decode_preprocess_equals_two_launches(gs, n_anchors, box3):
+    """gs_ng_decode_preprocess against gs_ng_decode_fwd + gs_preprocess on
+    the same anchors and camera: the children's parameters, blend records,
+    level sets, tile counts and rectangles are bit-identical, and so are the
+    tile lists after the binning (so the depth keys are too)."""
+    from paper_2601_19489_gb300 import _lib as L
+    from paper_2601_19489_gb300 import api
+
+    d, cam = _setup(n_anchors, seed=n_anchors % 5 + 1)
+    ng = api.NgParams.from_dict(d)
+    out = []
+    for fused in (False, True):
+        ws = api.gs_ng_workspace(n_anchors)
+        ch = api.ng_children(n_anchors)
+        plan = api.Plan(ch.n, 0, [(cam.width, cam.height)], 1 << 22, tuning={"bbox_3sigma": box3})
+        if fused:
+            api.gs_ng_decode_preprocess(ng, cam, ch, ws, plan)
+        else:
+            api.gs_ng_decode_fwd(ng, cam, ch, ws)
+            api.gs_preprocess(plan, ch, [cam])
+        bufs = [to_np(plan.view(w, torch.int32)).copy() for w in (L.GS_WS_RECORDS, L.GS_WS_BIN,
+                                                                 L.GS_WS_TILES_TOUCHED, L.GS_WS_RECTS)]
+        api.gs_bin_sort(plan, True)
+        st = plan.status()
+        assert st["rc"] == 0 and st["n_instances"] > 0, st
+        ranges = to_np(plan.view(L.GS_WS_TILE_RANGES, torch.int32)).reshape(-1, 2).copy()
+        items = to_np(plan.view(L.GS_WS_INST_GID, torch.int32))[: st["n_instances"]].copy()
+        assert api.gs_ng_status(ws) == 0
+        out.append(([to_np(t).copy() for t in ch.tensors()], bufs, ranges, items))
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    for a, b in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][2], out[1][2]) and np.array_equal(out[0][3], out[1][3])
+
+
+def test_fused_decode_trainer_step_equals_unfused(gs):
+    """The neural-Gaussian training step with the fused decode + preprocess:
+    the first step's loss is bit-identical to the two-launch step, and both
+    keep training to the same losses (float32 atomics order aside)."""
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import NgTrainer
+
+    cam, d, target = _tiny_chain()
+    tgt = torch.from_numpy(np.clip(target - 1.8, 0.0, 1.0).reshape(-1).astype(np.float32)).cuda()
+    runs = []
+    for fused in (False, True):
+        tr = NgTrainer(api.NgParams.from_dict(d), cam.width, cam.height, lam=0.2, inst_capacity=1 << 16,
+                       fused_decode=fused)
+        tr.ensure_capacity([cam])
+        losses = []
+        for _ in range(10):
+            tr.step(cam, tgt)
+            losses.append(tr.loss.item())
+        torch.cuda.synchronize()
+        assert tr.status() == 0 and tr.plan.status()["rc"] == 0
+        runs.append(losses)
+    assert runs[0][0] == runs[1][0]
+    np.testing.assert_allclose(runs[1], runs[0], rtol=1e-3)
+
+
 @pytest.mark.slow
 def test_ng_decode_forward_at_full_size_on_sampled_anchors(gs):
     """The decoder at the benchmark's size (104,857 anchors -> 1,048,570
