@@ -127,8 +127,8 @@ GS_API gs_plan *gs_plan_create(int64_t n, int32_t sh_degree, int32_t n_views, co
  *              while the pipeline fills and drains), or 0: two when the
  *              bucket has at least 128 live pixels, else one.  Ignored at 64.
  * A zero field takes the default (32, 4, 0; fwd_pixels 1).  gs_plan_create
- * uses the defaults (the Python layer's default plan takes bucket 64, two
- * backward warps, chains 0 and fwd_pixels 2: the autotuner's pick at 1M
+ * uses the defaults (the Python layer's default plan takes bucket 64, one
+ * backward warp, chains 0 and fwd_pixels 2: the autotuner's pick at 1M
  * Gaussians and 1080p).
  * Returns NULL on the same conditions as gs_plan_create or an unsupported
  * choice. */

@@ -103,7 +103,7 @@ class Plan:
         V = len(self.sizes)
         ws_ = (ctypes.c_int32 * V)(*[w for w, _ in self.sizes])
         hs_ = (ctypes.c_int32 * V)(*[h for _, h in self.sizes])
-        self.tuning = {"bucket": 64, "bwd_warps": 2, "bwd_chains": 0, "bbox_3sigma": 0, "bwd_per_pixel": 0,
+        self.tuning = {"bucket": 64, "bwd_warps": 1, "bwd_chains": 0, "bbox_3sigma": 0, "bwd_per_pixel": 0,
                        "bin_radix": 0, "fwd_pixels": 2, **(tuning or {})}
         tu = L.GsTuning(*(int(self.tuning[k]) for k in ("bucket", "bwd_warps", "bwd_chains", "bbox_3sigma",
                                                         "bwd_per_pixel", "bin_radix", "fwd_pixels")))

@@ -19,6 +19,10 @@ constexpr int kBucket = GS_BUCKET;         // default splats per checkpoint
 constexpr int kTwoChainAuto = 128;         // automatic chain choice: two chains from 128 live pixels
 constexpr int kCkptCh = 5;                 // T, C.r, C.g, C.b, D
 constexpr int kTileClasses = 8;            // backward work classes of a tile (by its last contributor)
+#ifndef GS_BWD_CHUNK
+#define GS_BWD_CHUNK 8
+#endif
+constexpr int kBwdChunk = GS_BWD_CHUNK;    // buckets per backward work unit (a tile's buckets in chunks)
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
@@ -104,8 +108,9 @@ struct gs_plan {
     // offsets
     size_t o_status, o_rec, o_touched, o_rect, o_dkey[2], o_dval[2];
     size_t o_ikey[2], o_ival[2], o_ranges, o_tile_maxc, o_bucket_off, o_ncontrib;
-    size_t o_tile_order;  // kTileClasses x total_tiles: tile ids by work class, written by the forward
+    size_t o_tile_order;  // kTileClasses x unit_cap backward work units (tile, chunk) by class, from the forward
     size_t o_tile_count;  // kTileClasses counts of those lists
+    int64_t unit_cap;     // units a class list can hold: tiles + bucket_cap / kBwdChunk
     size_t o_ckpt, o_grad2d, o_sort_scratch, o_block_sums, o_bin;
     size_t o_brange, o_bchunk, o_btile, o_bbase, o_ccnt, o_cval;  // counting binning
     size_t o_final;  // per-pixel final T, then the background (per-pixel backward only)

@@ -155,7 +155,8 @@ extern "C" gs_plan *gs_plan_create_tuned(int64_t n, int32_t sh_degree, int32_t n
     p->o_ranges = take(T * sizeof(uint2));
     p->o_tile_maxc = take(T * sizeof(uint32_t));
     p->o_bucket_off = take((T + 1) * sizeof(uint32_t));
-    p->o_tile_order = take((size_t)kTileClasses * T * sizeof(uint32_t));
+    p->unit_cap = T + p->bucket_cap / kBwdChunk + 1;
+    p->o_tile_order = take((size_t)kTileClasses * p->unit_cap * sizeof(uint2));
     p->o_tile_count = take((size_t)kTileClasses * sizeof(uint32_t));
     p->o_ncontrib = take((size_t)pix * sizeof(uint32_t));
     p->o_final = take(p->bwd_per_pixel ? ((size_t)pix + 4) * sizeof(float) : 16);

@@ -15,9 +15,10 @@
 // 10 values to the per-(view, Gaussian) accumulator with float4 atomics.
 // Pixels whose blend ended before the bucket are compacted away first, so the
 // pipeline only steps through pixels the bucket can affect.  A CTA of the
-// persistent grid claims one tile at a time from a counter (per-tile work is
-// uneven), stages the tile's per-pixel gradients once and its warps share the
-// tile's buckets greedily.
+// persistent grid claims one work unit at a time from a counter: a tile and a
+// chunk of up to 8 of its buckets, in the forward's work classes (heaviest
+// tiles first; per-tile work is very uneven).  It stages the tile's
+// per-pixel gradients and its warps share the chunk's buckets greedily.
 //
 // Two kernels:
 //   k_render_bwd      32-splat buckets, one splat per lane; each lane walks
@@ -42,7 +43,7 @@ struct BwdShared {
     float2 ck[kWarps][kTilePix];              // per warp, compacted: (T, S) in front of its bucket
     uint8_t pix[kWarps][kTilePix];            // per warp, compacted: pixel index in the tile
     uint32_t next;                            // next unclaimed bucket of the tile
-    uint32_t tile;                            // the tile this CTA claimed
+    uint2 unit;                               // the work unit this CTA claimed: (tile, chunk)
 };
 
 // Stage the tile's per-pixel data: the upstream gradient and
@@ -102,19 +103,19 @@ __device__ __forceinline__ int compact_live(const float4 *sg, const float4 *sfin
     return m_total;
 }
 
-// The next tile of the backward: claim number i from the counter, mapped
-// through the forward's per-class tile lists (class 0 first); all ones once
-// every tile is taken.
-__device__ __forceinline__ uint32_t claim_tile(uint32_t *tile_ctr, const uint32_t *__restrict__ tile_order,
-                                               const uint32_t *class_count, int total_tiles) {
-    const uint32_t i = atomicAdd(tile_ctr, 1u);
+// The next work unit of the backward, (tile, chunk of kBwdChunk buckets):
+// claim number i from the counter, mapped through the forward's per-class
+// lists (class 0 first); x = all ones once every unit is taken.
+__device__ __forceinline__ uint2 claim_unit(uint32_t *unit_ctr, const uint2 *__restrict__ units,
+                                            const uint32_t *class_count, int64_t unit_cap) {
+    const uint32_t i = atomicAdd(unit_ctr, 1u);
     uint32_t base = 0;
     for (int c = 0; c < kTileClasses; ++c) {
         const uint32_t n = class_count[c];
-        if (i < base + n) return tile_order[(size_t)c * total_tiles + (i - base)];
+        if (i < base + n) return units[(size_t)c * unit_cap + (i - base)];
         base += n;
     }
-    return 0xffffffffu;
+    return make_uint2(0xffffffffu, 0u);
 }
 
 // Per-splat sums over its pixels; the mean's gradient is linear in
@@ -172,8 +173,8 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
              const uint32_t *__restrict__ n_contrib, const float *__restrict__ img_rgb,
              const float *__restrict__ img_disp, const float *__restrict__ dL_drgb,
              const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d, int two_chain_min,
-             uint32_t *__restrict__ tile_ctr, const uint32_t *__restrict__ tile_order,
-             const uint32_t *__restrict__ class_count) {
+             uint32_t *__restrict__ tile_ctr, const uint2 *__restrict__ tile_order,
+             const uint32_t *__restrict__ class_count, int64_t unit_cap) {
     constexpr int kThreads = kWarps * 32;
     constexpr int kBucketSplats = 32;
     __shared__ BwdShared<kWarps> S;
@@ -185,28 +186,30 @@ k_render_bwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
         // work classes (heaviest first): per-tile work is uneven, so a CTA
         // that finishes a light tile takes the next one, and the longest
         // tiles do not come last
-        if (threadIdx.x == 0) S.tile = claim_tile(tile_ctr, tile_order, class_count, views.total_tiles);
+        if (threadIdx.x == 0) S.unit = claim_unit(tile_ctr, tile_order, class_count, unit_cap);
         __syncthreads();
-        const uint32_t tt = S.tile;
-        __syncthreads();  // every thread has read S.tile before the next claim
-        if (tt >= (uint32_t)views.total_tiles) break;
-        const int t = (int)tt;
+        const uint2 unit = S.unit;
+        __syncthreads();  // every thread has read S.unit before the next claim
+        if (unit.x >= (uint32_t)views.total_tiles) break;
+        const int t = (int)unit.x;
+        const uint32_t lb0 = unit.y * kBwdChunk;  // this unit's buckets: lb0 .. lb0 + kBwdChunk - 1
         const uint2 range = ranges[t];
         const uint32_t maxc = min(tile_maxc[t], range.y - range.x);
         const uint32_t nb = (maxc + kBucketSplats - 1) / kBucketSplats;  // buckets that hold blended splats
-        if (nb == 0) continue;  // uniform
+        const uint32_t lb_end = min(nb, lb0 + kBwdChunk);
+        if (lb0 >= lb_end) continue;  // uniform
         int v = 0;
         while (v + 1 < views.V && t >= views.v[v + 1].tile_off) ++v;
         const ViewDev &cam = views.v[v];
         const int lt = t - cam.tile_off;
         const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
         stage_tile_pixels<kThreads>(cam, tx, ty, img_rgb, img_disp, dL_drgb, dL_ddisp, n_contrib, S.g, S.fin);
-        if (threadIdx.x == 0) S.next = kWarps;  // buckets 0..kWarps-1 are taken
+        if (threadIdx.x == 0) S.next = lb0 + kWarps;  // buckets lb0 .. lb0 + kWarps - 1 are taken
         __syncthreads();
 
         // ---- the warps take the tile's buckets greedily (the first, fullest
         // buckets first) without synchronising until the tile is done
-        for (uint32_t lb = warp; lb < nb;) {
+        for (uint32_t lb = lb0 + warp; lb < lb_end;) {
             const uint32_t j0 = lb * kBucketSplats;
             const float *ckb = ckpt + (size_t)(bucket_off[t] + lb) * (kCkptCh * kTilePix);
             const int m_total = compact_live(S.g, S.fin, ckb, j0, S.ck[warp], S.pix[warp]);
@@ -351,7 +354,7 @@ k_render_bwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
                 const uint32_t *__restrict__ n_contrib, const float *__restrict__ img_rgb,
                 const float *__restrict__ img_disp, const float *__restrict__ dL_drgb,
                 const float *__restrict__ dL_ddisp, float4 *__restrict__ grad2d, uint32_t *__restrict__ tile_ctr,
-                const uint32_t *__restrict__ tile_order, const uint32_t *__restrict__ class_count) {
+                const uint2 *__restrict__ tile_order, const uint32_t *__restrict__ class_count, int64_t unit_cap) {
     constexpr int kThreads = kWarps * 32;
     constexpr int kBucketSplats = 64;
     __shared__ BwdShared<kWarps> S;
@@ -364,26 +367,28 @@ k_render_bwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
         // work classes (heaviest first): per-tile work is uneven, so a CTA
         // that finishes a light tile takes the next one, and the longest
         // tiles do not come last
-        if (threadIdx.x == 0) S.tile = claim_tile(tile_ctr, tile_order, class_count, views.total_tiles);
+        if (threadIdx.x == 0) S.unit = claim_unit(tile_ctr, tile_order, class_count, unit_cap);
         __syncthreads();
-        const uint32_t tt = S.tile;
-        __syncthreads();  // every thread has read S.tile before the next claim
-        if (tt >= (uint32_t)views.total_tiles) break;
-        const int t = (int)tt;
+        const uint2 unit = S.unit;
+        __syncthreads();  // every thread has read S.unit before the next claim
+        if (unit.x >= (uint32_t)views.total_tiles) break;
+        const int t = (int)unit.x;
+        const uint32_t lb0 = unit.y * kBwdChunk;  // this unit's buckets: lb0 .. lb0 + kBwdChunk - 1
         const uint2 range = ranges[t];
         const uint32_t maxc = min(tile_maxc[t], range.y - range.x);
         const uint32_t nb = (maxc + kBucketSplats - 1) / kBucketSplats;
-        if (nb == 0) continue;  // uniform
+        const uint32_t lb_end = min(nb, lb0 + kBwdChunk);
+        if (lb0 >= lb_end) continue;  // uniform
         int v = 0;
         while (v + 1 < views.V && t >= views.v[v + 1].tile_off) ++v;
         const ViewDev &cam = views.v[v];
         const int lt = t - cam.tile_off;
         const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
         stage_tile_pixels<kThreads>(cam, tx, ty, img_rgb, img_disp, dL_drgb, dL_ddisp, n_contrib, S.g, S.fin);
-        if (threadIdx.x == 0) S.next = kWarps;
+        if (threadIdx.x == 0) S.next = lb0 + kWarps;
         __syncthreads();
 
-        for (uint32_t lb = warp; lb < nb;) {
+        for (uint32_t lb = lb0 + warp; lb < lb_end;) {
             const uint32_t j0 = lb * kBucketSplats;
             const float *ckb = ckpt + (size_t)(bucket_off[t] + lb) * (kCkptCh * kTilePix);
             int n_steps = 0;
@@ -656,7 +661,8 @@ static int launch_bwd(const gs_plan *plan, void *ws, const float *d_rgb, const f
     const ViewsDev vd = make_views(plan, nullptr);
     StatusDev *st = ws_at<StatusDev>(ws, plan->o_status);
     uint32_t *ctr = &st->bwd_next_tile;
-    const uint32_t *order = ws_at<uint32_t>(ws, plan->o_tile_order), *ccount = ws_at<uint32_t>(ws, plan->o_tile_count);
+    const uint2 *order = ws_at<uint2>(ws, plan->o_tile_order);
+    const uint32_t *ccount = ws_at<uint32_t>(ws, plan->o_tile_count);
     int rc = check_cuda(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), s));
     if (rc) return rc;
     if (plan->bucket == 64) {
@@ -664,7 +670,8 @@ static int launch_bwd(const gs_plan *plan, void *ws, const float *d_rgb, const f
             vd, ws_at<uint2>(ws, plan->o_ranges), ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]),
             ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off),
             ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt),
-            ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, ctr, order, ccount);
+            ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, ctr, order, ccount,
+            plan->unit_cap);
         return launch_error();
     }
     k_render_bwd<kWarps><<<persistent_grid(k_render_bwd<kWarps>, kWarps * 32), kWarps * 32, 0, s>>>(
@@ -672,7 +679,7 @@ static int launch_bwd(const gs_plan *plan, void *ws, const float *d_rgb, const f
         ws_at<float4>(ws, plan->o_rec), ws_at<uint32_t>(ws, plan->o_bucket_off),
         ws_at<uint32_t>(ws, plan->o_tile_maxc), ws_at<float>(ws, plan->o_ckpt),
         ws_at<uint32_t>(ws, plan->o_ncontrib), d_rgb, d_disp, d_dL_drgb, d_dL_ddisp, g2d, plan->two_chain_min, ctr,
-        order, ccount);
+        order, ccount, plan->unit_cap);
     return launch_error();
 }
 

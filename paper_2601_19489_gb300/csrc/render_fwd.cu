@@ -29,7 +29,7 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
              float bg_g, float bg_b, float *__restrict__ out_rgb, float *__restrict__ out_disp,
              float *__restrict__ out_T, uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ tile_maxc,
              float *__restrict__ ckpt, float *__restrict__ final_T, uint32_t *__restrict__ bucket_off,
-             uint32_t *__restrict__ tile_order, uint32_t *__restrict__ tile_count, StatusDev *st) {
+             uint2 *__restrict__ tile_order, uint32_t *__restrict__ tile_count, int64_t unit_cap, StatusDev *st) {
     __shared__ float4 s_r0[kTilePix];
     __shared__ float4 s_r1[kTilePix];
     __shared__ float4 s_r2[kTilePix];
@@ -139,9 +139,17 @@ k_render_fwd(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t *_
     __syncthreads();
     if (tid == 0) {
         tile_maxc[t] = s_maxc;
-        if (ckpt) {  // the per-Gaussian backward takes the tiles by work class, heaviest first
-            const int c = tile_work_class(s_maxc);
-            tile_order[(size_t)c * views.total_tiles + atomicAdd(&tile_count[c], 1u)] = (uint32_t)t;
+        if (ckpt) {
+            // the per-Gaussian backward's work units: the buckets it walks
+            // (up to the last contributor) in chunks of kBwdChunk, filed by
+            // the tile's work class, heaviest class first
+            const uint32_t nbw = (min(s_maxc, (uint32_t)n) + (1u << bucket_shift) - 1u) >> bucket_shift;
+            const uint32_t chunks = (nbw + kBwdChunk - 1) / kBwdChunk;
+            if (chunks) {
+                const int c = tile_work_class(s_maxc);
+                uint2 *dst = tile_order + (size_t)c * unit_cap + atomicAdd(&tile_count[c], chunks);
+                for (uint32_t k = 0; k < chunks; ++k) dst[k] = make_uint2((uint32_t)t, k);
+            }
         }
     }
 }
@@ -166,8 +174,8 @@ k_render_fwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
                 const float4 *__restrict__ rec, int bucket_shift, float bg_r, float bg_g, float bg_b,
                 float *__restrict__ out_rgb, float *__restrict__ out_disp, float *__restrict__ out_T,
                 uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ tile_maxc, float *__restrict__ ckpt,
-                float *__restrict__ final_T, uint32_t *__restrict__ bucket_off, uint32_t *__restrict__ tile_order,
-                uint32_t *__restrict__ tile_count, StatusDev *st) {
+                float *__restrict__ final_T, uint32_t *__restrict__ bucket_off, uint2 *__restrict__ tile_order,
+                uint32_t *__restrict__ tile_count, int64_t unit_cap, StatusDev *st) {
     __shared__ ulonglong2 s_q0[kFwdPkBatch], s_q1[kFwdPkBatch], s_q2[kFwdPkBatch];
     __shared__ ulonglong2 s_c0[kFwdPkBatch], s_c1[kFwdPkBatch];
     __shared__ uint32_t s_maxc, s_boff;
@@ -314,9 +322,17 @@ k_render_fwd_pk(ViewsDev views, const uint2 *__restrict__ ranges, const uint32_t
     __syncthreads();
     if (tid == 0) {
         tile_maxc[t] = s_maxc;
-        if (ckpt) {  // the per-Gaussian backward takes the tiles by work class, heaviest first
-            const int c = tile_work_class(s_maxc);
-            tile_order[(size_t)c * views.total_tiles + atomicAdd(&tile_count[c], 1u)] = (uint32_t)t;
+        if (ckpt) {
+            // the per-Gaussian backward's work units: the buckets it walks
+            // (up to the last contributor) in chunks of kBwdChunk, filed by
+            // the tile's work class, heaviest class first
+            const uint32_t nbw = (min(s_maxc, (uint32_t)n) + (1u << bucket_shift) - 1u) >> bucket_shift;
+            const uint32_t chunks = (nbw + kBwdChunk - 1) / kBwdChunk;
+            if (chunks) {
+                const int c = tile_work_class(s_maxc);
+                uint2 *dst = tile_order + (size_t)c * unit_cap + atomicAdd(&tile_count[c], chunks);
+                for (uint32_t k = 0; k < chunks; ++k) dst[k] = make_uint2((uint32_t)t, k);
+            }
         }
     }
 }
@@ -344,14 +360,15 @@ extern "C" int gs_render_fwd(const gs_plan *plan, void *ws, const float *bg, flo
     const uint32_t *items = ws_at<uint32_t>(ws, plan->o_ival[plan->inst_final]);
     const float4 *recs = ws_at<float4>(ws, plan->o_rec);
     uint32_t *boff = ws_at<uint32_t>(ws, plan->o_bucket_off);
-    uint32_t *order = ws_at<uint32_t>(ws, plan->o_tile_order), *tcount = ws_at<uint32_t>(ws, plan->o_tile_count);
+    uint2 *order = ws_at<uint2>(ws, plan->o_tile_order);
+    uint32_t *tcount = ws_at<uint32_t>(ws, plan->o_tile_count);
     if (plan->fwd_pixels == 2)
         k_render_fwd_pk<<<plan->total_tiles, kFwdPkThreads, 0, s>>>(vd, rg, items, recs, plan->bucket_shift, bg[0],
                                                                      bg[1], bg[2], out_rgb, out_disp, out_T, ncontrib,
-                                                                     tmaxc, ck, fin, boff, order, tcount, st);
+                                                                     tmaxc, ck, fin, boff, order, tcount, plan->unit_cap, st);
     else
         k_render_fwd<<<plan->total_tiles, kTilePix, 0, s>>>(vd, rg, items, recs, plan->bucket_shift, bg[0], bg[1],
                                                             bg[2], out_rgb, out_disp, out_T, ncontrib, tmaxc, ck, fin,
-                                                            boff, order, tcount, st);
+                                                            boff, order, tcount, plan->unit_cap, st);
     return launch_error();
 }
