@@ -9,7 +9,8 @@
 // i.e. the same symmetric window applied to three per-pixel maps.
 //
 // One launch does both (k_ssim_fused).  A CTA owns a strip of 32 output
-// columns and 120 output rows of one plane and walks down it in chunks of 16
+// columns and a segment of output rows of one plane (48 to 256 rows, chosen
+// per launch so the grid fills whole waves) and walks down it in chunks of 16
 // rows.  Per chunk it loads 16 new input rows, blurs them horizontally (five
 // sums per column, over the 42 statistic columns the strip needs), blurs the
 // horizontal sums vertically into the statistics of 16 map rows five rows
@@ -31,7 +32,7 @@ namespace gs {
 
 constexpr int kSsimT = 32;                    // output columns of a strip
 constexpr int kHalo = 5;                      // window radius
-constexpr int kSegH = 120;                    // output rows of a CTA
+constexpr int kSegHMin = 48, kSegHMax = 256;  // output rows of a CTA (chosen per launch)
 constexpr int kR = 16;                        // rows per chunk
 constexpr int kRing = 32;                     // rows of the horizontal-sum rings
 constexpr int kStatW = kSsimT + 2 * kHalo;    // 42 statistic / map columns
@@ -74,12 +75,12 @@ struct Planes {
 __device__ __forceinline__ float sgn(float d) { return (float)((d > 0.f) - (d < 0.f)); }
 
 // Plane (view, channel) of a block and its geometry.
-__device__ __forceinline__ bool plane_geom(const Planes &pl, int z, int *W, int *H, int64_t *base) {
+__device__ __forceinline__ bool plane_geom(const Planes &pl, int z, int seg_h, int *W, int *H, int64_t *base) {
     const int v = z / 3, c = z - 3 * v;
     *W = pl.W[v];
     *H = pl.H[v];
     *base = 3 * pl.off[v] + (int64_t)c * pl.W[v] * pl.H[v];
-    return (int)blockIdx.x * kSsimT < *W && (int)blockIdx.y * kSegH < *H;
+    return (int)blockIdx.x * kSsimT < *W && (int)blockIdx.y * seg_h < *H;
 }
 
 __device__ __forceinline__ f2x ld2(const float2 &v) { return *reinterpret_cast<const f2x *>(&v); }
@@ -137,7 +138,7 @@ __device__ __forceinline__ void reduce_loss(const LossSums &L) {
 // output rows [a - 10, a + 6) get their gradient (their windows need the
 // maps' horizontal sums of rows [a - 15, a + 11)).
 __global__ void __launch_bounds__(kSsimThreads, 4)
-k_ssim_fused(Planes pl, Window win, const float *__restrict__ x, const float *__restrict__ y, float c_l1,
+k_ssim_fused(Planes pl, Window win, int seg_h, const float *__restrict__ x, const float *__restrict__ y, float c_l1,
              float c_ssim, float *__restrict__ grad, float *__restrict__ part_s, float *__restrict__ part_l1,
              unsigned int *__restrict__ done_ctr, LossSums sums) {
     extern __shared__ __align__(16) unsigned char ssim_smem[];
@@ -148,12 +149,12 @@ k_ssim_fused(Planes pl, Window win, const float *__restrict__ x, const float *__
     int W, H;
     int64_t base;
     float acc_s = 0.f, acc_l1 = 0.f;
-    if (plane_geom(pl, blockIdx.z, &W, &H, &base)) {
+    if (plane_geom(pl, blockIdx.z, seg_h, &W, &H, &base)) {
         const float *__restrict__ xp = x + base;
         const float *__restrict__ yp = y + base;
         float *__restrict__ gp = grad + base;
-        const int c0 = blockIdx.x * kSsimT, y0 = blockIdx.y * kSegH;
-        const int y1 = min(y0 + kSegH, H);
+        const int c0 = blockIdx.x * kSsimT, y0 = blockIdx.y * seg_h;
+        const int y1 = min(y0 + seg_h, H);
         const int nchunks = (y1 - y0 + 4 + kR - 1) / kR + 1;
         f2x w2[11];
 #pragma unroll
@@ -439,13 +440,43 @@ static Window make_window() {
     return w;
 }
 
-static void ssim_grid(const gs_plan *plan, dim3 *grid) {
+// Grid of the fused SSIM pass: 32-column strips x segments of seg_h rows x
+// planes.  seg_h trades the first chunk's halo rows (20 input rows per
+// segment) against whole waves of CTAs (4 resident per SM): it minimises
+// waves x chunks per CTA.  seg_h = 0 gives the smallest height (the most
+// blocks, for sizing the scratch).
+static void ssim_grid(const gs_plan *plan, int sms, dim3 *grid, int *seg_h) {
     int mw = 0, mh = 0;
     for (int v = 0; v < plan->V; ++v) {
         mw = plan->W[v] > mw ? plan->W[v] : mw;
         mh = plan->H[v] > mh ? plan->H[v] : mh;
     }
-    *grid = dim3((mw + kSsimT - 1) / kSsimT, (mh + kSegH - 1) / kSegH, 3 * plan->V);
+    const int64_t strips = (int64_t)((mw + kSsimT - 1) / kSsimT) * 3 * plan->V;
+    int best = kSegHMin;
+    if (sms > 0) {
+        int64_t best_cost = -1;
+        for (int sh = kSegHMin; sh <= kSegHMax; sh += 4) {
+            const int64_t ctas = strips * ((mh + sh - 1) / sh);
+            const int64_t waves = (ctas + 4 * sms - 1) / (4 * sms);
+            const int64_t cost = waves * ((sh + 4 + kR - 1) / kR + 1);
+            if (best_cost < 0 || cost < best_cost) {
+                best_cost = cost;
+                best = sh;
+            }
+        }
+    }
+    *seg_h = best;
+    *grid = dim3((mw + kSsimT - 1) / kSsimT, (mh + best - 1) / best, 3 * plan->V);
+}
+
+static int device_sms() {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    if (dev < 0 || dev >= 64) return 152;
+    if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms[dev] = 152;
+    return sms[dev];
 }
 
 // The fused kernel's shared memory exceeds the 48 KB default: raise the
@@ -471,7 +502,8 @@ using namespace gs;
 extern "C" int64_t gs_loss_scratch_floats(const gs_plan *plan) {
     if (!plan) return 0;
     dim3 g;
-    ssim_grid(plan, &g);
+    int seg_h;
+    ssim_grid(plan, 0, &g, &seg_h);  // the most blocks any launch can have
     const int64_t nblk = (int64_t)g.x * g.y * g.z;
     return 2 * nblk + 2 * kL1Blocks + 64;
 }
@@ -487,7 +519,8 @@ extern "C" int gs_loss(const gs_plan *plan, const float *rgb, const float *targe
     const int64_t P = plan->total_pixels;
     const int64_t n3 = 3 * P;
     dim3 grid;
-    ssim_grid(plan, &grid);
+    int seg_h;
+    ssim_grid(plan, device_sms(), &grid, &seg_h);
     const int nblk = (int)(grid.x * grid.y * grid.z);
     float *part_s = scratch;
     float *part_l1 = part_s + nblk;
@@ -517,7 +550,8 @@ extern "C" int gs_loss(const gs_plan *plan, const float *rgb, const float *targe
         sums.n_l1 = nblk;
         rc = check_cuda(cudaMemsetAsync(done_ctr, 0, sizeof(unsigned int), s));
         if (rc) return rc;
-        k_ssim_fused<<<grid, kSsimThreads, sizeof(SsimSmem), s>>>(pl, win, rgb, target, (float)((1.0 - lambda) * inv3p),
+        k_ssim_fused<<<grid, kSsimThreads, sizeof(SsimSmem), s>>>(pl, win, seg_h, rgb, target,
+                                                                  (float)((1.0 - lambda) * inv3p),
                                                                   (float)(-lambda * inv3p), dL_drgb, part_s, part_l1,
                                                                   done_ctr, sums);
     } else {

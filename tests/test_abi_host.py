@@ -98,9 +98,10 @@ def test_plan_sizes(lib):
         seen.sort()
         for (a, na), (b, _) in zip(seen[:-1], seen[1:]):
             assert a + na <= b
-        # per-block partial sums of the fused SSIM pass (32 x 120 output
-        # pixels per block and channel) and of the L1 passes, and a counter
-        blocks = -(-1920 // 32) * -(-1080 // 120) * 3 * 2
+        # per-block partial sums of the fused SSIM pass (32 columns x at
+        # least 48 rows per block and channel) and of the L1 passes, and a
+        # counter
+        blocks = -(-1920 // 32) * -(-1080 // 48) * 3 * 2
         assert lib.gs_loss_scratch_floats(p) >= 2 * blocks + 2
     finally:
         lib.gs_plan_destroy(p)
