@@ -4,9 +4,10 @@ It exists for callers that cannot allocate device memory: plug-ins whose
 host framework owns every byte of device memory, code under a fixed
 device-memory budget, and loops that cannot afford cudaMalloc's implicit
 device synchronisation.  These tests call it through the C ABI and check that it
-returns exactly what the scratch-taking gs_sort_pairs_u32 returns, on two
-calls in a row (the second call reuses the static scratch the first one left
-behind), and that it refuses sizes beyond its stated maximum.
+returns exactly what the scratch-taking gs_sort_pairs_u32 returns, and the
+stable sort by the key bits, on two calls in a row (the second call reuses
+the static scratch the first one left behind), and that it refuses sizes
+beyond its stated maximum.
 
 The file is named so pytest collects it last.
 """
@@ -54,6 +55,11 @@ def test_noalloc_sort_matches_the_scratch_sort_on_two_calls():
         got_k, got_v = _sort_noalloc(lib, keys, vals, begin, end)
         np.testing.assert_array_equal(got_k, want_k)
         np.testing.assert_array_equal(got_v, want_v)
+        # and both are the stable sort by the key bits [begin, end)
+        digit = (keys.astype(np.uint64) >> np.uint64(begin)) & np.uint64((1 << (end - begin)) - 1)
+        order = np.argsort(digit, kind="stable")
+        np.testing.assert_array_equal(got_v, vals[order])
+        np.testing.assert_array_equal(got_k, keys[order])
 
 
 def test_noalloc_sort_refuses_sizes_beyond_its_maximum():
