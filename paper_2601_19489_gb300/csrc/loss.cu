@@ -39,6 +39,9 @@ constexpr int kStatW = kSsimT + 2 * kHalo;    // 42 statistic / map columns
 constexpr int kHGroups = (kStatW + 3) / 4;    // 11 groups of 4 horizontal outputs (44 columns)
 constexpr int kInW = 4 * kHGroups + 2 * kHalo;  // 54 input columns
 constexpr int kSsimThreads = 256;
+// outputs per thread in the two gradient passes: 2 keeps all 256 threads busy
+// (16 rows x 16 column pairs, 8 row pairs x 32 columns)
+constexpr int kGB = 2;
 // row strides in elements: odd, so that 16 consecutive rows of one column
 // fall in 16 different banks
 constexpr int kInS = 55, kHS = 45, kMpS = 43, kBhS = 33;
@@ -162,21 +165,21 @@ k_ssim_fused(Planes pl, Window win, int seg_h, const float *__restrict__ x, cons
         // ring row of an image row (rows from y0 - 20 on)
         auto ring = [y0](int row) { return (row - y0 + 64) & (kRing - 1); };
         // this thread's place in each phase
-        const int hr = tid & 15, hg = tid >> 4;              // horizontal passes: row, group of 4 columns
+        const int hr = tid & 15, hg = tid >> 4;              // horizontal passes: row, group of columns
         const int vq = tid / kStatW, vc = tid - vq * kStatW;  // statistics pass: row group, column
         const int gq = tid >> 5, gc = tid & 31;               // gradient pass: row group, column
         for (int k = 0; k < nchunks; ++k) {
             const int a = y0 - 2 * kHalo + kR * k;
             // (1) x, y of this thread's gradient pixels, fetched early
-            float gx_[4], gy_[4];
-            const int go0 = a - 2 * kHalo + 4 * gq;
+            float gx_[kGB], gy_[kGB];
+            const int go0 = a - 2 * kHalo + kGB * gq;
             const bool gcol = c0 + gc < W;
 #pragma unroll
-            for (int o = 0; o < 4; ++o) {
+            for (int o = 0; o < kGB; ++o) {
                 gx_[o] = 0.f;
                 gy_[o] = 0.f;
                 const int row = go0 + o;
-                if (k > 0 && tid < 4 * kSsimT && gcol && row >= y0 && row < y1) {
+                if (k > 0 && tid < (kR / kGB) * kSsimT && gcol && row >= y0 && row < y1) {
                     const int64_t p = (int64_t)row * W + c0 + gc;
                     gx_[o] = __ldg(xp + p);
                     gy_[o] = __ldg(yp + p);
@@ -299,21 +302,22 @@ k_ssim_fused(Planes pl, Window win, int seg_h, const float *__restrict__ x, cons
             }
             __syncthreads();
             // (5) horizontal sums of the maps of map row a - 5 + hr at output
-            // columns 4 hg .. 4 hg + 3, from map columns 4 hg .. 4 hg + 13
-            if (tid < kR * (kSsimT / 4)) {
-                f2x s2[4];
-                float s1[4];
+            // columns kGB hg .. kGB hg + kGB - 1, from map columns kGB hg ..
+            // kGB hg + kGB + 9
+            if (tid < kR * (kSsimT / kGB)) {
+                f2x s2[kGB];
+                float s1[kGB];
 #pragma unroll
-                for (int o = 0; o < 4; ++o) {
+                for (int o = 0; o < kGB; ++o) {
                     s2[o] = pk2(0.f, 0.f);
                     s1[o] = 0.f;
                 }
 #pragma unroll
-                for (int kk = 0; kk < 14; ++kk) {
-                    const f2x v = ld2(sm.u.mp.ab[hr][4 * hg + kk]);
-                    const float e = sm.u.mp.c[hr][4 * hg + kk];
+                for (int kk = 0; kk < 10 + kGB; ++kk) {
+                    const f2x v = ld2(sm.u.mp.ab[hr][kGB * hg + kk]);
+                    const float e = sm.u.mp.c[hr][kGB * hg + kk];
 #pragma unroll
-                    for (int o = 0; o < 4; ++o) {
+                    for (int o = 0; o < kGB; ++o) {
                         const int u = kk - o;
                         if (u >= 0 && u < 11) {
                             s2[o] = fma2(w2[u], v, s2[o]);
@@ -323,30 +327,30 @@ k_ssim_fused(Planes pl, Window win, int seg_h, const float *__restrict__ x, cons
                 }
                 const int rr = ring(a - kHalo + hr);
 #pragma unroll
-                for (int o = 0; o < 4; ++o) {
-                    sm.bh01[rr][4 * hg + o] = st2(s2[o]);
-                    sm.bh4[rr][4 * hg + o] = s1[o];
+                for (int o = 0; o < kGB; ++o) {
+                    sm.bh01[rr][kGB * hg + o] = st2(s2[o]);
+                    sm.bh4[rr][kGB * hg + o] = s1[o];
                 }
             }
             __syncthreads();
-            // (6) gradient of output rows go0 .. go0 + 3 at column gc
-            // (vertical sums over map rows go0 - 5 .. go0 + 8); the first
-            // chunk has no output rows inside the segment
-            if (k > 0 && tid < 4 * kSsimT) {
-                f2x s2[4];
-                float s1[4];
+            // (6) gradient of output rows go0 .. go0 + kGB - 1 at column gc
+            // (vertical sums over map rows go0 - 5 .. go0 + kGB + 4); the
+            // first chunk has no output rows inside the segment
+            if (k > 0 && tid < (kR / kGB) * kSsimT) {
+                f2x s2[kGB];
+                float s1[kGB];
 #pragma unroll
-                for (int o = 0; o < 4; ++o) {
+                for (int o = 0; o < kGB; ++o) {
                     s2[o] = pk2(0.f, 0.f);
                     s1[o] = 0.f;
                 }
 #pragma unroll
-                for (int kk = 0; kk < 14; ++kk) {
+                for (int kk = 0; kk < 10 + kGB; ++kk) {
                     const int rr = ring(go0 - kHalo + kk);
                     const f2x v = ld2(sm.bh01[rr][gc]);
                     const float e = sm.bh4[rr][gc];
 #pragma unroll
-                    for (int o = 0; o < 4; ++o) {
+                    for (int o = 0; o < kGB; ++o) {
                         const int u = kk - o;
                         if (u >= 0 && u < 11) {
                             s2[o] = fma2(w2[u], v, s2[o]);
@@ -355,7 +359,7 @@ k_ssim_fused(Planes pl, Window win, int seg_h, const float *__restrict__ x, cons
                     }
                 }
 #pragma unroll
-                for (int o = 0; o < 4; ++o) {
+                for (int o = 0; o < kGB; ++o) {
                     const int row = go0 + o;
                     if (gcol && row >= y0 && row < y1) {
                         float dmu, dxx;
