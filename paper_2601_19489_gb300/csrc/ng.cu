@@ -902,8 +902,17 @@ static int check_ng(const gs_ng_params *p) {
     return GS_OK;
 }
 
-static int smem_opt_in(const void *kernel, size_t bytes) {
-    return check_cuda(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+// Raise a kernel's dynamic shared-memory limit once per device (the
+// attribute is per device context); `done` is the caller's per-kernel table.
+static int smem_opt_in(const void *kernel, size_t bytes, bool *done) {
+    int dev = 0;
+    int rc = check_cuda(cudaGetDevice(&dev));
+    if (rc) return rc;
+    const bool cache = dev >= 0 && dev < 64;
+    if (cache && done[dev]) return GS_OK;
+    rc = check_cuda(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (rc == GS_OK && cache) done[dev] = true;
+    return rc;
 }
 
 static Args base_args(const gs_ng_params *p, const gs_camera *cam, void *ws) {
@@ -951,12 +960,9 @@ extern "C" int gs_ng_decode_fwd(const gs_ng_params *p, const gs_camera *cam, gs_
         return GS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t smem = sizeof(ng::FwdSmem) + 1024;
-    static bool opted = false;
-    if (!opted) {
-        rc = ng::smem_opt_in((const void *)ng::k_ng_fwd<false>, smem);
-        if (rc) return rc;
-        opted = true;
-    }
+    static bool opted[64] = {};
+    rc = ng::smem_opt_in((const void *)ng::k_ng_fwd<false>, smem, opted);
+    if (rc) return rc;
     ng::Args A = ng::base_args(p, cam, ws);
     char *w = (char *)ws;
     const ng::Layout L = ng::layout(p->n_anchors);
@@ -984,12 +990,9 @@ extern "C" int gs_ng_decode_preprocess(const gs_ng_params *p, const gs_camera *c
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t smem = sizeof(ng::FwdSmem) + 1024;
-    static bool opted = false;
-    if (!opted) {
-        rc = ng::smem_opt_in((const void *)ng::k_ng_fwd<true>, smem);
-        if (rc) return rc;
-        opted = true;
-    }
+    static bool opted[64] = {};
+    rc = ng::smem_opt_in((const void *)ng::k_ng_fwd<true>, smem, opted);
+    if (rc) return rc;
     ng::Args A = ng::base_args(p, cam, ws);
     char *w = (char *)ws;
     const ng::Layout L = ng::layout(p->n_anchors);
@@ -1024,12 +1027,9 @@ extern "C" int gs_ng_decode_bwd(const gs_ng_params *p, const gs_camera *cam, con
         return GS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t smem = sizeof(ng::BwdSmem) + 1024;
-    static bool opted = false;
-    if (!opted) {
-        rc = ng::smem_opt_in((const void *)ng::k_ng_bwd, smem);
-        if (rc) return rc;
-        opted = true;
-    }
+    static bool opted[64] = {};
+    rc = ng::smem_opt_in((const void *)ng::k_ng_bwd, smem, opted);
+    if (rc) return rc;
     ng::Args A = ng::base_args(p, cam, ws);
     A.g_means = child_grads->means;
     A.g_ls = child_grads->log_scales;
