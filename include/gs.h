@@ -239,7 +239,11 @@ GS_API int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, void *s
  * alpha < 1/255 and stopping before T (1 - alpha) < 1e-4; every 32 (or 64,
  * the plan's bucket) splats the per-pixel T, C and D are checkpointed in ws
  * for the backward (each tile takes its buckets from a counter the call
- * restarts, so the checkpoints belong to the last forward).
+ * restarts, so the checkpoints belong to the last forward), and each tile's
+ * backward work units (chunks of up to 8 buckets) are filed under one of 8
+ * work classes by log2 of its last contributor.  With fwd_pixels = 2 (the
+ * tuning field) a thread blends two adjacent pixels in packed float32 pairs;
+ * the results are identical.
  * h_bg: 3 floats (host) background colour.  Outputs (device, may not alias):
  * d_out_rgb  colour C + T bg, planar per view;  d_out_disp  blended
  * disparity sum(alpha T / z);  d_out_T  final transmittance. */
@@ -247,11 +251,13 @@ GS_API int gs_render_fwd(const gs_plan *plan, void *ws, const float *h_bg, float
                          float *d_out_disp, float *d_out_T, void *stream);
 
 /* ------------------------------------------- a7 + a8: backward
- * Sec. 2.2: per-Gaussian parallel backward.  One warp per 32-splat bucket,
- * lane = splat, iterates the tile's pixels seeded from the forward's
- * checkpoints, accumulates in registers and issues one atomic per splat
- * parameter; then the per-Gaussian preprocess backward chains the 2D
- * gradients to the parameters.
+ * Sec. 2.2: per-Gaussian parallel backward.  One warp per checkpoint
+ * bucket (lane = splat at 32 splats, two splats per lane in packed pairs at
+ * 64), iterates the tile's pixels seeded from the forward's checkpoints,
+ * accumulates in registers and issues one atomic per splat parameter; the
+ * persistent CTAs claim the forward's work units, heaviest class first.
+ * Then the per-Gaussian preprocess backward chains the 2D gradients to the
+ * parameters.
  * d_rgb, d_disp: the forward's outputs for the same ws (device).
  * d_dL_drgb, d_dL_ddisp: upstream gradients, same layouts (d_dL_ddisp may be
  * NULL: no disparity loss).  h_cams: the cameras given to gs_preprocess.
