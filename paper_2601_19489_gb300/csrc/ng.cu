@@ -37,7 +37,7 @@ constexpr int kPer = 14;                // outputs per child
 constexpr int kOut = kChild * kPer;     // 140
 constexpr int kOutPad = 144;            // GEMM 2 N, backward GEMM K (9 x 16)
 constexpr int kFwdThreads = kTileA;    // forward: one thread per anchor
-constexpr int kThreads = 2 * kTileA;  // backward: two threads per anchor
+constexpr int kThreads = 3 * kTileA;  // backward: three threads per anchor
 constexpr int kTmemCols = 256;
 constexpr float kLogitFloor = -30.0f;
 constexpr float kOpacityCeil = 1.0f - 1e-6f;
@@ -464,9 +464,9 @@ cleanup:
 // them as its remaining rows, whose results land in TMEM lanes nobody reads.
 // TMEM columns: y 0..143, then dh 0..31, dx 32..79, dW2 128..159 and
 // 160..191, dW1^T 192..223.
-// Two threads per anchor (warps w and w + 4 read the same TMEM lanes): the
-// per-child work, the operand packing and the TMEM read-backs are split
-// between the two halves of the CTA.
+// Three threads per anchor (warps w, w + 4 and w + 8 read the same TMEM
+// lanes): the per-child work, the operand packing and the TMEM read-backs
+// are split between the three thirds of the CTA.
 struct BwdSmem {
     __nv_bfloat16 W2T[kHid * kOutPad];   // dh B (N = 32, K = 144)
     __nv_bfloat16 W1T[kInPad * kHid];    // dx B (N = 48, K = 32)
@@ -489,7 +489,7 @@ struct BwdSmem {
         } p2;
     } u;
     float Y[kTileA][kOutPad + 1];  // y, then dL/dy (fp32)
-    float xyz[kTileA][3], ls[kTileA][6], dls[2][kTileA][6];  // dls: per half of the children
+    float xyz[kTileA][3], ls[kTileA][6], dls[3][kTileA][6];  // dls: per third of the children
     float db1w[kTileA / 32][kHid];    // per-warp sums of db1
     float b2[kOutPad];
     uint64_t mbar, gbar;  // MMA completion; children's gradients copied in
@@ -512,9 +512,9 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     extern __shared__ uint8_t smem_raw[];
     BwdSmem &S = *reinterpret_cast<BwdSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // anchor row of the tile (= TMEM lane) and which half of its work this
-    // thread does; warps w and w + 4 share TMEM lanes 32 (w mod 4) ..
-    const int r = tid & (kTileA - 1), half = tid >> 7;
+    // anchor row of the tile (= TMEM lane) and which third of its work this
+    // thread does; warps w, w + 4 and w + 8 share TMEM lanes 32 (w mod 4) ..
+    const int r = tid & (kTileA - 1), grp = tid >> 7;
     const int64_t a0 = (int64_t)blockIdx.x * kTileA;
     const int64_t a = a0 + r;
     const bool valid = a < A.n;
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
         for (int i = tid; i < nch * 4; i += kThreads) stg[kStQ + i] = A.g_quats[4 * c0 + i];
         for (int i = tid; i < nch; i += kThreads) stg[kStO + i] = A.g_logits[c0 + i];
     }
-    if (half == 0) {
+    if (grp == 0) {
         // h of this anchor into the y GEMM's A (row = anchor) and the dW2
         // GEMM's B (row = hidden unit, K = anchors)
         const uint4 *src = reinterpret_cast<const uint4 *>(A.h_store + a * kHid);
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
         }
         for (int j = 0; j < 3; ++j) S.xyz[r][j] = valid ? A.xyz[3 * a + j] : 0.0f;
         for (int j = 0; j < 6; ++j) S.ls[r][j] = valid ? A.ls[6 * a + j] : 0.0f;
-    } else {
+    } else if (grp == 1) {
         // x of this anchor as the dW1^T GEMM's A (row = input, K = anchors)
         float x[kInPad];
         anchor_input(A, a, valid, x);
@@ -601,16 +601,18 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     __syncthreads();
     if (S.fail) goto cleanup;
     {
-        // columns 0..63 by the first half, 64..143 by the second
+        // columns 0..63 by the first third, 64..127 by the second, 128..143
+        // by the last
         float v[32];
+        if (grp < 2) {
 #pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            const int ch = 2 * half + cc;
-            tmem_ld32(my_lanes + ch * 32, v);
+            for (int cc = 0; cc < 2; ++cc) {
+                const int ch = 2 * grp + cc;
+                tmem_ld32(my_lanes + ch * 32, v);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) S.Y[r][ch * 32 + c] = v[c] + S.b2[ch * 32 + c];
-        }
-        if (half == 1) {
+                for (int c = 0; c < 32; ++c) S.Y[r][ch * 32 + c] = v[c] + S.b2[ch * 32 + c];
+            }
+        } else {
             tmem_ld16(my_lanes + 128, v);
 #pragma unroll
             for (int c = 0; c < 16; ++c) S.Y[r][128 + c] = v[c] + S.b2[128 + c];
@@ -643,15 +645,16 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
         }
     }
     if (r < na) {
-        // dL/dy of half of this anchor's children in place of y (every
-        // element depends on its own y only), and that half's share of the
-        // anchor's log-scale gradients, children in order
+        // dL/dy of a third of this anchor's children (4, 3, 3) in place of y
+        // (every element depends on its own y only), and that third's share
+        // of the anchor's log-scale gradients, children in order
         float *yr = S.Y[r];
         float so[3], dl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int j = 0; j < 3; ++j) so[j] = expf(S.ls[r][j]);
 #pragma unroll 1
-        for (int c = half * (kChild / 2); c < (half + 1) * (kChild / 2); ++c) {
+        const int cb = grp == 0 ? 0 : (grp == 1 ? 4 : 7), ce = grp == 0 ? 4 : (grp == 1 ? 7 : kChild);
+        for (int c = cb; c < ce; ++c) {
             const int ch = r * kChild + c;
             float *u = yr + c * kPer;
 #pragma unroll
@@ -672,7 +675,7 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
             u[3] = (o > 0.0f && o < kOpacityCeil) ? stg[kStO + ch] / (oc * (1.0f - oc)) * (1.0f - o * o) : 0.0f;
         }
 #pragma unroll
-        for (int k = 0; k < 6; ++k) S.dls[half][r][k] = dl[k];
+        for (int k = 0; k < 6; ++k) S.dls[grp][r][k] = dl[k];
     }
     __syncthreads();
     // db2 (unrounded dy of the present anchors)
@@ -689,9 +692,10 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
         // outputs) as its row of the dh GEMM's A and its column (K index) of
         // the dW2 GEMMs' A operands
         const bool live = r < na;
-        constexpr int kHalfOut = kOutPad / 2;  // outputs per half (even)
+        constexpr int kPartOut = kOutPad / 3;  // outputs per third (even)
+        static_assert(kPartOut % 2 == 0 && 3 * kPartOut == kOutPad, "outputs split in thirds of pairs");
 #pragma unroll 4
-        for (int o = half * kHalfOut; o < (half + 1) * kHalfOut; o += 2) {
+        for (int o = grp * kPartOut; o < (grp + 1) * kPartOut; o += 2) {
             const float v0 = live && o < kOut ? S.Y[r][o] : 0.0f;
             const float v1 = live && o + 1 < kOut ? S.Y[r][o + 1] : 0.0f;
             const uint32_t pk = pack_bf16x2(v0, v1);
@@ -730,7 +734,7 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     tc_fence_after();
     __syncthreads();
     if (S.fail) goto cleanup;
-    if (half == 0) {
+    if (grp == 0) {
         // dh after the ReLU mask, rounded, as the dx GEMM's A (row = anchor)
         // and the dW1^T GEMM's B (row = hidden unit, K = anchors); the
         // y-recompute operands it overwrites are no longer read
@@ -750,14 +754,16 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
             S.u.p2.DHT[canon(c, r, kTileA)] = __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
             S.u.p2.DHT[canon(c + 1, r, kTileA)] = __ushort_as_bfloat16((unsigned short)(pk >> 16));
         }
-    } else {
+    } else if (grp == 1) {
         // this thread's row (output r) of dW2
         float v[32];
         tmem_ld32(my_lanes + 128, v);
         float4 *dst = reinterpret_cast<float4 *>(part + r * kHid);
 #pragma unroll
         for (int q = 0; q < kHid / 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        if (warp == 4) {  // outputs 128..139
+    } else {
+        float v[32];
+        if (warp == 8) {  // outputs 128..139
             tmem_ld32(my_lanes + 160, v);
             if (lane < kOut - kTileA) {
                 float4 *d2 = reinterpret_cast<float4 *>(part + (kTileA + lane) * kHid);
@@ -793,7 +799,7 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
     tc_fence_after();
     __syncthreads();
     if (S.fail) goto cleanup;
-    if (half == 0) {
+    if (grp == 0) {
         float v[32];
         tmem_ld32(my_lanes + 32, v);
         if (valid) {
@@ -813,7 +819,7 @@ __global__ void __launch_bounds__(kThreads) k_ng_bwd(Args A) {
                 for (int c = 0; c < kFeat; ++c) A.d_feat[a * kFeat + c] += v[c];
             }
 #pragma unroll
-            for (int j = 0; j < 6; ++j) A.d_ls[6 * a + j] += S.dls[0][r][j] + S.dls[1][r][j];
+            for (int j = 0; j < 6; ++j) A.d_ls[6 * a + j] += S.dls[0][r][j] + S.dls[1][r][j] + S.dls[2][r][j];
         }
     } else if (warp < 6) {  // dW1[h][i] = (dW1^T)[i][h] for the 35 inputs (TMEM lanes 0..63)
         float v[32];
