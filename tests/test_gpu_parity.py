@@ -400,6 +400,38 @@ def test_loss_matches_oracle(gs, lam):
     np.testing.assert_allclose(to_np(gdisp), gd, rtol=1e-5, atol=1e-12)
 
 
+@pytest.mark.parametrize("sizes", [[(1920, 1080)], [(45, 2000), (300, 17), (1, 1)]],
+                         ids=["1080p", "tall-ragged"])
+def test_loss_matches_oracle_at_full_size(gs, sizes):
+    """The bench's loss launch (one 1080p view: the segment height the grid
+    sizing picks for it) and ragged planes (a 2000-row strip 45 columns wide,
+    17 rows, a single pixel), every output against the oracle, on images
+    that agree up to noise (SSIM about 0.8)."""
+    from paper_2601_19489_gb300 import api
+
+    plan = api.Plan(16, 0, sizes, 1024)
+    P = plan.pixels
+    rng = np.random.default_rng(31)
+    x = rng.uniform(size=3 * P).astype(np.float32)
+    y = np.clip(x + 0.2 * rng.standard_normal(3 * P), 0.0, 1.0).astype(np.float32)
+    xt, yt = (torch.from_numpy(a).cuda() for a in (x, y))
+    grad = torch.empty_like(xt)
+    loss = torch.zeros(1, device="cuda")
+    api.gs_loss(plan, xt, yt, 0.2, grad, loss, api.gs_loss_scratch(plan))
+    torch.cuda.synchronize()
+    tot_loss, off = 0.0, 0
+    ref_grad = np.zeros(3 * P)
+    for (w, h) in sizes:
+        n = w * h
+        Li, gi = oloss.photometric(x[3 * off: 3 * (off + n)].reshape(3, h, w),
+                                   y[3 * off: 3 * (off + n)].reshape(3, h, w), 0.2)
+        tot_loss += Li * n / P
+        ref_grad[3 * off: 3 * (off + n)] = gi.reshape(-1) * (n / P)
+        off += n
+    np.testing.assert_allclose(loss.item(), tot_loss, rtol=1e-5)
+    assert grad_mismatch(to_np(grad), ref_grad).sum() == 0
+
+
 # ------------------------------------------------------------------ adam
 
 def test_adam_matches_oracle_and_torch(gs):
