@@ -133,6 +133,55 @@ def test_graph_replay_matches_eager_steps(gs):
     assert graphed.slot_for(cams).plan.status()["rc"] == 0
 
 
+def test_per_view_graphs_round_robin_match_eager_steps(gs):
+    """The benchmark's step loop: one captured graph per view on one trainer
+    (the views share its plan and buffers), replayed round robin, each view's
+    target refilled from pinned host memory on a side stream before its
+    replay, against the same single-view steps launched eagerly."""
+    from paper_2601_19489_gb300 import api
+    from paper_2601_19489_gb300.trainer import Trainer
+
+    W, H = 160, 90
+    scene = synth.scene_clustered(400, seed=1, sh_degree=1)
+    cams = synth.ring_cameras(5, W, H)[:3]
+    rng = np.random.default_rng(8)
+    tgt_h = [torch.from_numpy(rng.uniform(2.0, 2.5, size=3 * W * H).astype(np.float32)).pin_memory()
+             for _ in cams]
+    order = [0, 1, 2, 0, 1, 2, 0]
+    eager, graphed = (Trainer(api.Gaussians.from_scene(scene), W, H, lam=0.2, inst_capacity=1 << 20)
+                      for _ in range(2))
+    for tr in (eager, graphed):
+        tr.ensure_capacity(cams)
+    tgt_e = [t.cuda() for t in tgt_h]
+    losses = ([], [])
+    for v in order:
+        eager.step(cams[v], tgt_e[v])
+        losses[0].append(eager.loss.item())
+    # the graphs' target buffers start empty: every replay sees the refill
+    tgt_g = [torch.zeros_like(t) for t in tgt_e]
+    tgt_g[order[0]].copy_(tgt_h[order[0]])
+    graphed.step(cams[order[0]], tgt_g[order[0]])  # eager first: loads every kernel before capture
+    losses[1].append(graphed.loss.item())
+    graphs = [graphed.capture([c], t) for c, t in zip(cams, tgt_g)]
+    stream, side = torch.cuda.current_stream(), torch.cuda.Stream()
+    for v in order[1:]:
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            tgt_g[v].copy_(tgt_h[v], non_blocking=True)
+        stream.wait_stream(side)
+        graphs[v].replay()
+        losses[1].append(graphed.loss.item())
+    torch.cuda.synchronize()
+    assert graphed.step_count == len(order) and int(graphed.d_step.item()) == len(order)
+    np.testing.assert_allclose(losses[1], losses[0], rtol=1e-4)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        a = to_np(getattr(eager.params, k))
+        b = to_np(getattr(graphed.params, k))
+        off = np.abs(a - b) > 1e-6 * np.maximum(1.0, np.abs(a))
+        assert off.mean() < 0.01, (k, off.mean())
+    assert graphed.plan.status()["rc"] == 0
+
+
 def test_fused_preprocess_backward_adam_equals_unfused(gs):
     """The fused preprocess backward + Adam against the separate kernels on
     the same blend gradients, over three updates (moments evolving)."""
