@@ -498,7 +498,8 @@ def run_ours(args, rank, world):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for s in range(args.warmup):
+    # (at least one eager step: every kernel is loaded before a graph is captured)
+    for s in range(max(1, args.warmup)):
         trainer.step(cams[s % len(cams)], targets_d[s % len(cams)])
     barrier()
     st0 = trainer.plan.status()
