@@ -588,12 +588,18 @@ __global__ void __launch_bounds__(kFineWarps * 32)
 k_fine_mask(ViewsDev views, const uint32_t *__restrict__ cval, const uint2 *__restrict__ brange,
             const uint32_t *__restrict__ bchunk, const float4 *__restrict__ rec, const float2 *__restrict__ bin,
             const uint2 *__restrict__ rects, uint32_t *__restrict__ mlo, uint32_t *__restrict__ mhi,
-            uint32_t *__restrict__ ccnt, const StatusDev *st, int box3) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gw = blockIdx.x * kFineWarps + warp, nw = gridDim.x * kFineWarps;
+            uint32_t *__restrict__ ccnt, StatusDev *st, int box3) {
+    const int lane = threadIdx.x & 31;
     const int nblocks = views.total_blocks;
     const uint32_t n_chunks = st->n_chunks;
-    for (uint32_t c = (uint32_t)gw; c < n_chunks; c += (uint32_t)nw) {
+    // chunks claimed one at a time from a counter: their instance counts
+    // differ widely, so a fixed assignment leaves some SMs working long
+    // after the others
+    for (;;) {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(&st->next_mask_chunk, 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= n_chunks) break;
         const int b = chunk_block(bchunk, nblocks, c);
         const uint2 br = brange[b];
         const uint32_t e0 = br.x + (c - bchunk[b]) * (uint32_t)kChunk;
@@ -700,7 +706,7 @@ __global__ void __launch_bounds__(kFineWarps * 32)
 k_fine_scatter(ViewsDev views, const uint32_t *__restrict__ cval, const uint2 *__restrict__ brange,
                const uint32_t *__restrict__ bchunk, const uint32_t *__restrict__ mlo,
                const uint32_t *__restrict__ mhi, const uint32_t *__restrict__ ccnt,
-               const uint32_t *__restrict__ bbase, const uint2 *__restrict__ btile, const StatusDev *st,
+               const uint32_t *__restrict__ bbase, const uint2 *__restrict__ btile, StatusDev *st,
                int64_t capacity, uint32_t *__restrict__ inst_item, uint2 *__restrict__ ranges) {
     __shared__ uint32_t s_stage[kFineWarps][kBlkTiles * kStageStride];
     __shared__ uint32_t s_item[kFineWarps][32];
@@ -725,7 +731,11 @@ k_fine_scatter(ViewsDev views, const uint32_t *__restrict__ cval, const uint2 *_
     uint32_t *slot0 = s_stage[warp] + lane * kStageStride;
     uint32_t *slot1 = s_stage[warp] + (lane + 32) * kStageStride;
     const uint32_t n_chunks = st->n_chunks;
-    for (uint32_t c = (uint32_t)gw; c < n_chunks; c += (uint32_t)nw) {
+    for (;;) {  // chunks claimed one at a time, as in k_fine_mask
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(&st->next_scatter_chunk, 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= n_chunks) break;
         const int b = chunk_block(bchunk, nblocks, c);
         const uint2 br = brange[b];
         const uint32_t e0 = br.x + (c - bchunk[b]) * (uint32_t)kChunk;
@@ -937,8 +947,12 @@ extern "C" int gs_bin_sort(const gs_plan *plan, void *ws, int load_balanced, voi
     StatusDev *st = ws_at<StatusDev>(ws, plan->o_status);
     uint32_t *scratch = ws_at<uint32_t>(ws, plan->o_sort_scratch);
     // the error word, the finished-block counter of k_count, the entry and
-    // chunk counts and the finished-CTA counter of k_fine_offsets (adjacent)
-    int rc = check_cuda(cudaMemsetAsync(&st->error, 0, 5 * sizeof(int32_t), s));
+    // chunk counts, the finished-CTA counter of k_fine_offsets, the
+    // backward's unit counter (cleared again by its launch) and the chunk
+    // counters of k_fine_mask and k_fine_scatter (adjacent)
+    static_assert(offsetof(StatusDev, next_scatter_chunk) - offsetof(StatusDev, error) == 7 * sizeof(int32_t),
+                  "status words cleared together must be adjacent");
+    int rc = check_cuda(cudaMemsetAsync(&st->error, 0, 8 * sizeof(int32_t), s));
     if (rc) return rc;
 
     // 1. depth order of the items (keys were written by gs_preprocess)

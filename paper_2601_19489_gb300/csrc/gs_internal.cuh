@@ -74,7 +74,9 @@ struct StatusDev {
     uint32_t n_chunks;     // their chunks
     uint32_t done_offsets;  // k_fine_offsets: CTAs finished (cleared by gs_bin_sort)
     uint32_t bwd_next_tile;  // per-Gaussian backward: next unclaimed tile (cleared per launch)
-    uint32_t pad[55];
+    uint32_t next_mask_chunk;     // k_fine_mask: next unclaimed chunk (cleared by gs_bin_sort)
+    uint32_t next_scatter_chunk;  // k_fine_scatter: the same
+    uint32_t pad[53];
 };
 
 }  // namespace gs
