@@ -218,14 +218,19 @@ GS_API int gs_preprocess(const gs_plan *plan, void *ws, const gs_params *params,
  * load_balanced = 1 (default path, "counting binning"): tiles are grouped
  * in blocks of 8 x 8; one (block, Gaussian) entry per block the Gaussian's
  * SnugBox meets is written in depth order and stably sorted by block
- * (a radix sort over these few entries); each block's entries are cut into
- * chunks of 128, and a warp per chunk lays the chunk's in-block tile
- * columns out as one flat list, one column per lane (the load-balanced
- * column walk of Fig. 2), counts the chunk's instances per tile, and after
- * a scan of the counts (tiles of a block, chunks of a tile, blocks) walks
- * the columns again and writes each Gaussian id straight to its final
- * position, the rank among the warp's lanes that share a tile taken by
- * ballots.  Tile lists lie block by block in the instance list.
+ * (a radix sort over these few entries), so a Gaussian of any size is cut
+ * into pieces of at most 8 columns; each block's entries are cut into
+ * chunks of 128, which warps claim from a counter.  Per chunk, 32 entries
+ * at a time, one per lane: each lane computes its entry's 64-bit mask of
+ * the block's tiles it touches (the exact per-column test, the lanes
+ * visiting the columns in lockstep), and a 32 x 32 bit transpose across the
+ * warp turns the masks into per-tile entry sets whose sizes are the chunk's
+ * counts per tile.  After a scan of the counts (tiles of a block, chunks of
+ * a tile, blocks), a second pass transposes the masks again and each lane
+ * appends the entries that touch its two tiles, in entry order, to those
+ * tiles' runs, writing each Gaussian id straight to its final position (in
+ * whole 32-byte sectors).  Tile lists lie block by block in the instance
+ * list.
  * load_balanced = 0 ("Sq", and load_balanced = 1 with the plan's bin_radix):
  * one (tile, Gaussian) key per touched tile is written in depth order — by
  * one thread walking its Gaussian's columns (Sq), or by the load-balanced
