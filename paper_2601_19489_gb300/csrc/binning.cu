@@ -407,7 +407,8 @@ k_tile_ranges(const uint32_t *__restrict__ keys, const StatusDev *st, int64_t ca
 //  4. k_block_bounds: each block's [start, end) among the sorted entries;
 //  5. k_chunk_scan: each block's entries cut into chunks of kChunk, the
 //     chunks of all blocks numbered by a scan;
-//  6. k_fine_mask: a warp per chunk computes every entry's 64-bit mask of
+//  6. k_fine_mask: a warp per chunk (claimed from a counter) computes every
+//     entry's 64-bit mask of
 //     the block's tiles its Gaussian touches (exact column test), stores it
 //     and counts the chunk's instances per tile;
 //  7. k_fine_offsets: a CTA per block turns the counts into each chunk's
@@ -415,8 +416,8 @@ k_tile_ranges(const uint32_t *__restrict__ keys, const StatusDev *st, int64_t ca
 //     tile's chunks in order); the CTA that finishes last scans the block
 //     totals into block bases and checks their sum against the instance
 //     count;
-//  8. k_fine_scatter: a warp per chunk, a lane per tile, walks the chunk's
-//     entries in order and writes each item at the next position of every
+//  8. k_fine_scatter: a warp per chunk (claimed from a counter), a lane per
+//     two tiles, walks the chunk's entries in order and writes each item at the next position of every
 //     tile in its mask; the tile ranges come from the block bases.
 // Each tile's list therefore keeps the entries' order, which is the depth
 // order: the same lists as the radix path's.
